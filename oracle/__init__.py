@@ -1,0 +1,175 @@
+"""FP64 CPU oracle for pair counting -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, ``__graft_entry__.smoke()`` and bench.py's ``cpu_baseline`` /
+``--impl reference`` legs may import this package.  It shares no code with
+the CUDA library and never imports it.  The arithmetic lives in oracle.c
+(plain C, FP64, compiled with gcc); this module only marshals numpy arrays.
+
+Every function cites the passage of Alonso (2012) it follows; see oracle.c
+for the canonical formulas and the readings taken where the paper is silent.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+KINDS = {"mono": 0, "rmu": 1, "sigpi": 2, "theta": 3}
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        L.oracle_count.argtypes = [i32, i32, f64, P, i64, P, i64, i32, P, i32, P, i32,
+                                   P, P, P, P, P, i32]
+        L.oracle_count_cells.argtypes = [i32, i32, f64, P, i64, P, i64, i32, P, i32, P,
+                                         i32, P, P, P, P, P, P, i32]
+        L.oracle_grad_rows.argtypes = [i32, i32, f64, P, i64, P, i64, i32, P, i32, P, i32,
+                                       P, P, P, i64, P, i32]
+        L.oracle_xi_periodic.argtypes = [P, i64, P, i32, f64, P]
+        L.oracle_xi_natural.argtypes = [P, P, i64, i64, i32, P]
+        L.oracle_xi_ls.argtypes = [P, P, P, i64, i64, i32, P]
+        L.oracle_theta_to_chord.argtypes = [P, i32, P]
+        for f in ("oracle_count", "oracle_count_cells", "oracle_grad_rows",
+                  "oracle_xi_periodic", "oracle_xi_natural", "oracle_xi_ls",
+                  "oracle_theta_to_chord", "oracle_max_threads"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _xyz(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if x.ndim != 2 or x.shape[1] != 3:
+        raise ValueError("positions must be an (n, 3) array")
+    return x
+
+
+def _edges(e):
+    return None if e is None else np.ascontiguousarray(e, dtype=np.float64)
+
+
+def _w(w):
+    return None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+
+
+def max_threads() -> int:
+    return lib().oracle_max_threads()
+
+
+def count(kind, xa, xb=None, edges0=None, edges1=None, periodic=False, L=0.0,
+          wa=None, wb=None, weighted=False, cells=None, nthreads=0):
+    """Pair-count histogram (Eq. 11; serial loop of Sec. 3.1).
+
+    kind: 'mono' | 'rmu' | 'sigpi' | 'theta'.  xb None -> auto-correlation
+    (unique pairs i<j of xa); else cross-correlation (all xa x xb).
+    cells: None -> brute force over every pair; a 3-vector of per-axis reach
+    -> the cell-pruned form (Sec. 3.3), identical counts.
+    Returns (counts[n0, n1] uint64, oor, wsum or None)."""
+    k = KINDS[kind]
+    xa = _xyz(xa)
+    is_auto = xb is None
+    xb = xa if is_auto else _xyz(xb)
+    e0 = _edges(edges0)
+    e1 = _edges(edges1)
+    n0 = len(e0) - 1
+    n1 = (len(e1) - 1) if k in (1, 2) else 1
+    wa_, wb_ = _w(wa), _w(wb)
+    if weighted and is_auto:
+        wb_ = wa_
+    counts = np.zeros(n0 * n1, dtype=np.uint64)
+    oor = np.zeros(1, dtype=np.uint64)
+    wsum = np.zeros(n0 * n1, dtype=np.float64) if weighted else None
+    if cells is None:
+        rc = lib().oracle_count(k, int(periodic), float(L), _ptr(xa), len(xa), _ptr(xb), len(xb),
+                                int(is_auto), _ptr(e0), n0, _ptr(e1), n1 if k in (1, 2) else 0,
+                                _ptr(wa_), _ptr(wb_), _ptr(counts), _ptr(oor), _ptr(wsum),
+                                int(nthreads))
+    else:
+        reach = np.ascontiguousarray(cells, dtype=np.float64)
+        rc = lib().oracle_count_cells(k, int(periodic), float(L), _ptr(xa), len(xa), _ptr(xb),
+                                      len(xb), int(is_auto), _ptr(e0), n0, _ptr(e1),
+                                      n1 if k in (1, 2) else 0, _ptr(wa_), _ptr(wb_),
+                                      _ptr(reach), _ptr(counts), _ptr(oor), _ptr(wsum),
+                                      int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_count failed with status %d" % rc)
+    return counts.reshape(n0, n1), int(oor[0]), (None if wsum is None else wsum.reshape(n0, n1))
+
+
+def grad_rows(kind, xa, rows, G, wpartner, xb=None, edges0=None, edges1=None,
+              periodic=False, L=0.0, nthreads=0):
+    """d/dw_i of sum_b G_b W_b for the rows i of catalog A (weighted counts of
+    Sec. 3.4): sum over partners j of w_j G[bin(i, j)]."""
+    k = KINDS[kind]
+    xa = _xyz(xa)
+    is_auto = xb is None
+    xb = xa if is_auto else _xyz(xb)
+    e0, e1 = _edges(edges0), _edges(edges1)
+    n0 = len(e0) - 1
+    n1 = (len(e1) - 1) if k in (1, 2) else 0
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    G = np.ascontiguousarray(G, dtype=np.float64).ravel()
+    wp = _w(wpartner)
+    out = np.zeros(len(rows), dtype=np.float64)
+    rc = lib().oracle_grad_rows(k, int(periodic), float(L), _ptr(xa), len(xa), _ptr(xb), len(xb),
+                                int(is_auto), _ptr(e0), n0, _ptr(e1), n1, _ptr(wp), _ptr(G),
+                                _ptr(rows), len(rows), _ptr(out), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_grad_rows failed with status %d" % rc)
+    return out
+
+
+def xi_periodic(DD, N, edges, L):
+    """Eq. 13 with N(N-1)/2 unique pairs and the exact shell volume."""
+    DD = np.ascontiguousarray(DD, dtype=np.uint64).ravel()
+    e = _edges(edges)
+    out = np.zeros(len(DD), dtype=np.float64)
+    rc = lib().oracle_xi_periodic(_ptr(DD), int(N), _ptr(e), len(DD), float(L), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_xi_periodic failed")
+    return out
+
+
+def xi_natural(DD, RR, Nd, Nr):
+    """Eq. 14."""
+    DD = np.ascontiguousarray(DD, dtype=np.uint64).ravel()
+    RR = np.ascontiguousarray(RR, dtype=np.uint64).ravel()
+    out = np.zeros(len(DD), dtype=np.float64)
+    rc = lib().oracle_xi_natural(_ptr(DD), _ptr(RR), int(Nd), int(Nr), len(DD), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_xi_natural failed")
+    return out
+
+
+def xi_ls(DD, DR, RR, Nd, Nr):
+    """Eq. 15 (Landy-Szalay)."""
+    DD = np.ascontiguousarray(DD, dtype=np.uint64).ravel()
+    DR = np.ascontiguousarray(DR, dtype=np.uint64).ravel()
+    RR = np.ascontiguousarray(RR, dtype=np.uint64).ravel()
+    out = np.zeros(len(DD), dtype=np.float64)
+    rc = lib().oracle_xi_ls(_ptr(DD), _ptr(DR), _ptr(RR), int(Nd), int(Nr), len(DD), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_xi_ls failed")
+    return out
+
+
+def theta_to_chord(theta_deg):
+    """Chord 2 sin(theta/2) between unit vectors at angle theta (Eq. 7)."""
+    t = np.ascontiguousarray(theta_deg, dtype=np.float64)
+    out = np.zeros(len(t), dtype=np.float64)
+    rc = lib().oracle_theta_to_chord(_ptr(t), len(t), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_theta_to_chord failed")
+    return out

@@ -1,0 +1,302 @@
+"""Pins for the FP64 CPU oracle (no GPU).
+
+The oracle is the parity reference for the CUDA path, so it is itself pinned
+to things other than its own formulas: hand-counted fixtures (tests/golden),
+a third-party pair counter (scipy's cKDTree), independent formulas (pdist,
+arccos/atan2 angles, an explicit cosine), the analytic shell expectation for
+uniform periodic boxes (Eq. 12-13), the pair-total invariant, DR/RD symmetry,
+and the marginal relations between the (r,mu), (sigma,pi) and monopole
+histograms (Eq. 2, Eq. 4).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1210_1833_gb300 import synthetic
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def _unit(theta_deg, axis):
+    t = math.radians(theta_deg)
+    if axis == "x":
+        return [math.sin(t), 0.0, math.cos(t)]
+    if axis == "y":
+        return [0.0, math.sin(t), math.cos(t)]
+    return [0.0, 0.0, 1.0]
+
+
+# ------------------------------------------------------------------ fixtures
+@pytest.mark.parametrize("name", ["mono_line.json", "mono_edges.json", "mono_periodic.json",
+                                  "sigpi_square.json", "rmu_triplet.json"])
+def test_golden_counts(name):
+    g = _load(name)
+    x = np.array(g["points"], dtype=np.float64)
+    c, oor, _ = oracle.count(g["kind"], x, edges0=g["edges0"], edges1=g.get("edges1"),
+                             periodic=g["periodic"], L=g["L"])
+    assert c.ravel().tolist() == np.array(g["counts"]).ravel().tolist()
+    assert oor == g["oor"]
+
+
+def test_golden_theta():
+    g = _load("theta_triangle.json")
+    pts = []
+    for p in g["points_deg"]:
+        pts.append(_unit(0.0, "z") if p[0] == "z" else _unit(p[0], p[1]))
+    x = np.array(pts)
+    chord = oracle.theta_to_chord(g["theta_edges_deg"])
+    c, oor, _ = oracle.count("theta", x, edges0=chord)
+    assert c.ravel().tolist() == g["counts"]
+    assert oor == g["oor"]
+
+
+def test_golden_estimators():
+    g = _load("ls_numbers.json")
+    ls = oracle.xi_ls(g["DD"], g["DR"], g["RR"], g["Nd"], g["Nr"])
+    nat = oracle.xi_natural(g["DD"], g["RR"], g["Nd"], g["Nr"])
+    assert ls[0] == pytest.approx(g["xi_ls"], rel=1e-15)
+    assert nat[0] == pytest.approx(g["xi_natural"], rel=1e-15)
+
+
+def test_theta_to_chord_values():
+    c = oracle.theta_to_chord([0.0, 60.0, 180.0, 90.0])
+    assert c[0] == 0.0
+    assert c[1] == pytest.approx(1.0, rel=1e-15)
+    assert c[2] == pytest.approx(2.0, rel=1e-15)
+    assert c[3] == pytest.approx(math.sqrt(2.0), rel=1e-15)
+
+
+# ------------------------------------------------------------------ library pins
+def test_mono_open_matches_pdist_histogram():
+    scipy_sd = pytest.importorskip("scipy.spatial.distance")
+    rng = np.random.default_rng(11)
+    x = rng.uniform(0, 50, size=(600, 3))
+    edges = np.linspace(0, 30, 16)
+    c, oor, _ = oracle.count("mono", x, edges0=edges)
+    d = scipy_sd.pdist(x)
+    h, _ = np.histogram(d, bins=edges)
+    assert c.ravel().tolist() == h.tolist()
+    assert oor == len(d) - h.sum()
+
+
+def test_mono_periodic_matches_ckdtree():
+    spatial = pytest.importorskip("scipy.spatial")
+    rng = np.random.default_rng(12)
+    L = 100.0
+    x = rng.uniform(0, L, size=(800, 3))
+    y = rng.uniform(0, L, size=(500, 3))
+    edges = np.linspace(0, 30, 11)
+    ta, tb = spatial.cKDTree(x, boxsize=L), spatial.cKDTree(y, boxsize=L)
+    # cross: ordered pairs with edges[k-1] < d <= edges[k]
+    ref = ta.count_neighbors(tb, edges, cumulative=False)[1:]
+    c, oor, _ = oracle.count("mono", x, y, edges0=edges, periodic=True, L=L)
+    assert c.ravel().tolist() == ref.tolist()
+    # auto: cKDTree counts ordered pairs including i == j at d = 0
+    ref_auto = ta.count_neighbors(ta, edges, cumulative=False)
+    ref_auto[0] -= len(x)
+    ca, _, _ = oracle.count("mono", x, edges0=edges, periodic=True, L=L)
+    assert (2 * ca.ravel()).tolist() == ref_auto[1:].tolist()
+
+
+def test_theta_matches_atan2_angles():
+    rng = np.random.default_rng(13)
+    v = rng.normal(size=(400, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    v = v[v[:, 2] > 0.5]
+    theta_edges = np.linspace(0.0, 40.0, 21)
+    chord = oracle.theta_to_chord(theta_edges)
+    c, _, _ = oracle.count("theta", v, edges0=chord)
+    i, j = np.triu_indices(len(v), 1)
+    cr = np.linalg.norm(np.cross(v[i], v[j]), axis=1)
+    dt = np.einsum("ij,ij->i", v[i], v[j])
+    ang = np.degrees(np.arctan2(cr, dt))
+    h, _ = np.histogram(ang, bins=theta_edges)
+    assert c.ravel().tolist() == h.tolist()
+
+
+def test_rmu_matches_explicit_cosine():
+    rng = np.random.default_rng(14)
+    x = rng.uniform(-30, 30, size=(500, 3)) + np.array([0.0, 0.0, 300.0])
+    e0 = np.linspace(0, 40, 9)
+    e1 = np.linspace(0, 1, 11)
+    c, _, _ = oracle.count("rmu", x, edges0=e0, edges1=e1)
+    i, j = np.triu_indices(len(x), 1)
+    s = x[j] - x[i]
+    l = x[i] + x[j]
+    r = np.linalg.norm(s, axis=1)
+    mu = np.abs(np.einsum("ij,ij->i", s, l)) / (r * np.linalg.norm(l, axis=1))
+    ok = r < 40
+    h, _, _ = np.histogram2d(r[ok], np.minimum(mu[ok], 1.0 - 1e-15), bins=[e0, e1])
+    assert c.tolist() == h.astype(np.int64).tolist()
+
+
+# ------------------------------------------------------------------ invariants
+@pytest.mark.parametrize("kind,periodic", [("mono", True), ("mono", False), ("sigpi", True),
+                                           ("rmu", False), ("theta", False)])
+def test_pair_total_invariant(kind, periodic):
+    rng = np.random.default_rng(15)
+    L = 100.0
+    if kind == "theta":
+        a = rng.normal(size=(300, 3)); a /= np.linalg.norm(a, axis=1, keepdims=True)
+        b = rng.normal(size=(200, 3)); b /= np.linalg.norm(b, axis=1, keepdims=True)
+        e0, e1 = np.linspace(0, 0.5, 6), None
+    else:
+        a = rng.uniform(0, L, size=(300, 3))
+        b = rng.uniform(0, L, size=(200, 3))
+        if kind == "rmu":
+            a += 500; b += 500
+        e0 = np.linspace(0, 30, 7)
+        e1 = np.linspace(0, 1, 5) if kind == "rmu" else (np.linspace(0, 20, 5) if kind == "sigpi" else None)
+    ca, oa, _ = oracle.count(kind, a, edges0=e0, edges1=e1, periodic=periodic, L=L)
+    assert int(ca.sum()) + oa == len(a) * (len(a) - 1) // 2
+    cx, ox, _ = oracle.count(kind, a, b, edges0=e0, edges1=e1, periodic=periodic, L=L)
+    assert int(cx.sum()) + ox == len(a) * len(b)
+    # DR == RD bit-exactly (the canonical separation is symmetric)
+    cy, oy, _ = oracle.count(kind, b, a, edges0=e0, edges1=e1, periodic=periodic, L=L)
+    assert cx.tolist() == cy.tolist() and ox == oy
+
+
+def test_uniform_box_matches_shell_expectation():
+    """Eq. 12-13: for uniform points in a periodic box the expected count in a
+    shell is N(N-1)/2 * 4pi/3 (r2^3 - r1^3) / L^3."""
+    rng = np.random.default_rng(16)
+    L, N = 100.0, 4000
+    x = synthetic.uniform_box(N, L, rng)
+    e = np.linspace(0, 20, 11)
+    c, _, _ = oracle.count("mono", x, edges0=e, periodic=True, L=L)
+    expect = 0.5 * N * (N - 1) * (4 * math.pi / 3) * (e[1:] ** 3 - e[:-1] ** 3) / L ** 3
+    z = (c.ravel() - expect) / np.sqrt(expect)
+    assert np.all(np.abs(z) < 5), z
+    xi = oracle.xi_periodic(c.ravel(), N, e, L)
+    assert np.all(np.abs(xi) < 5 / np.sqrt(expect))
+
+
+def test_rmu_marginal_equals_monopole():
+    """Eq. 4: integrating over mu recovers the monopole.  For counts: summing
+    the (r, mu) histogram over all mu bins equals the r histogram exactly."""
+    w = synthetic.c2_rmu_lightcone(scale=0.0006)
+    c2, o2, _ = oracle.count("rmu", w.data, w.randoms, edges0=w.edges0, edges1=w.edges1)
+    c1, o1, _ = oracle.count("mono", w.data, w.randoms, edges0=w.edges0)
+    assert c2.sum(axis=1).tolist() == c1.ravel().tolist()
+    assert o1 == o2
+
+
+def test_sigpi_marginals_are_projected_monopoles():
+    """Eq. 2: sigma is the separation projected off the line of sight and pi
+    the part along it; a (sigma, pi) histogram with one pi bin covering every
+    separation is the monopole of the points projected on the sky plane."""
+    rng = np.random.default_rng(17)
+    L = 60.0
+    x = rng.uniform(0, L, size=(700, 3))
+    es = np.linspace(0, 20, 9)
+    big = np.array([0.0, L])  # pi in [0, L): every pair (|dz| <= L/2)
+    c, _, _ = oracle.count("sigpi", x, edges0=es, edges1=big, periodic=True, L=L)
+    proj = x.copy(); proj[:, 2] = 0.0
+    m, _, _ = oracle.count("mono", proj, edges0=es, periodic=True, L=L)
+    assert c[:, 0].tolist() == m.ravel().tolist()
+    c2, _, _ = oracle.count("sigpi", x, edges0=np.array([0.0, L]), edges1=es, periodic=True, L=L)
+    projz = x.copy(); projz[:, :2] = 0.0
+    m2, _, _ = oracle.count("mono", projz, edges0=es, periodic=True, L=L)
+    assert c2[0, :].tolist() == m2.ravel().tolist()
+
+
+@pytest.mark.parametrize("kind,periodic", [("mono", True), ("mono", False), ("sigpi", True),
+                                           ("rmu", False), ("theta", False)])
+def test_cells_equal_brute_force(kind, periodic):
+    rng = np.random.default_rng(18)
+    L = 200.0
+    if kind == "theta":
+        a = synthetic._cap_uniform(900, 0.9, rng)
+        b = synthetic._cap_uniform(700, 0.9, rng)
+        e0, e1 = oracle.theta_to_chord(np.linspace(0, 8, 9)), None
+        reach = [e0[-1]] * 3
+    else:
+        a = synthetic.uniform_box(900, L, rng)
+        b = synthetic.uniform_box(700, L, rng)
+        a = np.concatenate([a, synthetic.blobs_box(5, 40, L, 2.0, rng)])
+        if kind == "rmu":
+            a = a + 1000; b = b + 1000
+        e0 = np.linspace(0, 40, 9)
+        e1 = {"rmu": np.linspace(0, 1, 6), "sigpi": np.linspace(0, 30, 7)}.get(kind)
+        reach = [40, 40, 30] if kind == "sigpi" else [40, 40, 40]
+    for xb in (None, b):
+        ref = oracle.count(kind, a, xb, edges0=e0, edges1=e1, periodic=periodic, L=L)
+        got = oracle.count(kind, a, xb, edges0=e0, edges1=e1, periodic=periodic, L=L, cells=reach)
+        assert got[0].tolist() == ref[0].tolist()
+        assert got[1] == ref[1]
+
+
+# ------------------------------------------------------------------ weighted + gradient
+def test_weighted_unit_weights_equal_counts_and_pdist():
+    sd = pytest.importorskip("scipy.spatial.distance")
+    rng = np.random.default_rng(19)
+    x = rng.uniform(0, 40, size=(400, 3))
+    e = np.linspace(0, 20, 6)
+    ones = np.ones(len(x), np.float32)
+    c, _, w1 = oracle.count("mono", x, edges0=e, wa=ones, weighted=True)
+    assert w1.ravel().tolist() == c.ravel().astype(float).tolist()
+    w = np.exp(0.3 * rng.normal(size=len(x))).astype(np.float32)
+    _, _, ws = oracle.count("mono", x, edges0=e, wa=w, weighted=True)
+    d = sd.pdist(x)
+    prod = sd.pdist(w.astype(np.float64)[:, None], lambda u, v: u[0] * v[0])
+    ref, _ = np.histogram(d, bins=e, weights=prod)
+    np.testing.assert_allclose(ws.ravel(), ref, rtol=1e-13)
+
+
+@pytest.mark.parametrize("cross", [False, True])
+def test_grad_rows_match_finite_differences(cross):
+    """F(w) = sum_b G_b W_b is linear in each w_i (no self pairs), so the
+    central difference with h = w_i is exact up to rounding."""
+    rng = np.random.default_rng(20)
+    L = 50.0
+    a = synthetic.uniform_box(250, L, rng)
+    b = synthetic.uniform_box(180, L, rng) if cross else None
+    e = np.linspace(0, 15, 6)
+    wa = np.exp(0.3 * rng.normal(size=len(a))).astype(np.float32)
+    wb = np.exp(0.3 * rng.normal(size=180)).astype(np.float32) if cross else None
+    G = rng.normal(size=5)
+
+    def F(wa_):
+        _, _, ws = oracle.count("mono", a, b, edges0=e, periodic=True, L=L, wa=wa_,
+                                wb=wb, weighted=True)
+        return float(np.dot(G, ws.ravel()))
+
+    rows = np.array([0, 7, 100, 249])
+    g = oracle.grad_rows("mono", a, rows, G, wb if cross else wa, xb=b, edges0=e,
+                         periodic=True, L=L)
+    for r, gr in zip(rows, g):
+        h = float(wa[r])
+        wp = wa.copy(); wp[r] = np.float32(wa[r] * 2)
+        wm = wa.copy(); wm[r] = np.float32(0.0)
+        fd = (F(wp) - F(wm)) / (2 * h)
+        assert gr == pytest.approx(fd, rel=1e-9, abs=1e-12)
+    if not cross:
+        # Euler's theorem: F is homogeneous of degree 2 in w
+        allg = oracle.grad_rows("mono", a, np.arange(len(a)), G, wa, edges0=e, periodic=True, L=L)
+        assert float(np.dot(wa.astype(np.float64), allg)) == pytest.approx(2 * F(wa), rel=1e-10)
+
+
+def test_ls_equals_normalised_form():
+    """Eq. 15 with unique-pair counts equals (DDn - 2 DRn + RRn)/RRn where the
+    counts are normalised by Nd(Nd-1)/2, Nd Nr and Nr(Nr-1)/2."""
+    rng = np.random.default_rng(21)
+    Nd, Nr = 1234, 5678
+    DD = rng.integers(1, 10**6, size=20).astype(np.uint64)
+    DR = rng.integers(1, 10**7, size=20).astype(np.uint64)
+    RR = rng.integers(1, 10**7, size=20).astype(np.uint64)
+    xi = oracle.xi_ls(DD, DR, RR, Nd, Nr)
+    ddn = DD / (Nd * (Nd - 1) / 2)
+    drn = DR / (Nd * Nr)
+    rrn = RR / (Nr * (Nr - 1) / 2)
+    np.testing.assert_allclose(xi, (ddn - 2 * drn + rrn) / rrn, rtol=1e-12)
+    z = oracle.xi_ls(DD, DR, np.zeros(20, np.uint64), Nd, Nr)
+    assert np.all(np.isnan(z))
