@@ -1,0 +1,294 @@
+"""Benchmark of the pair-counting hot path on GB300.
+
+Workload (default): the light-cone xi(r, mu) configuration -- 500,000 data
+objects in 20 clustered sky patches and 2,000,000 uniform randoms in the
+shell r = 1000-2500, RA 0-60 deg, Dec 0-30 deg; 40 r bins on [0, 200) x 40 mu
+bins on [0, 1] with the midpoint line of sight; DD, DR and RR, then the
+Landy-Szalay estimator.  Synthetic, seeded (paper_1210_1833_gb300.synthetic).
+
+One step = the whole hot path: catalog upload/conversion, cell-grid build
+for both catalogs, the DD, DR and RR counting kernels, and the estimator.
+`value` is candidate pairs examined per second with the catalogs already in
+HBM; `e2e` is the same step through the public API from pinned host memory
+with the xi read back.  L2 is flushed between timed steps.
+
+--impl reference times the FP64 CPU oracle (the parity reference) on a
+bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1210_1833_gb300 import synthetic  # noqa: E402
+
+METRIC = "pairs/s & % FP32 roofline; batched/adjoint vs plain kernel, counts exact"
+# FP32-pipe operations per candidate pair in the (r, mu) kernel's fast path:
+# s (3 FADD), l (3 FADD), r^2, l^2, s.l (3 each: FMUL + 2 FFMA), den (FMUL),
+# mu (FMUL), two clamps (FMNMX), two table indices (FFMA).
+I_PAIR_RMU = 21
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                          "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def total_pairs(nd, nr):
+    return nd * (nd - 1) // 2 + nd * nr + nr * (nr - 1) // 2
+
+
+# ------------------------------------------------------------------ reference arm
+def cpu_oracle_rate(w, target_s=12.0, seed=0):
+    """The oracle (brute force, every pair examined) on a bounded sample of the
+    workload's pairs: a seeded subset of data rows against all randoms (DR).
+    Returns (pairs/s, threads, sample description)."""
+    import oracle
+    nthr = oracle.max_threads()
+    rows = 64
+    t = 0.0
+    while True:
+        sub = synthetic.subsample(w.data, rows, seed)
+        t0 = time.perf_counter()
+        oracle.count(w.kind, sub, w.randoms, edges0=w.edges0, edges1=w.edges1,
+                     periodic=w.periodic, L=w.L)
+        t = time.perf_counter() - t0
+        if t >= target_s / 3 or rows >= len(w.data):
+            break
+        rows = int(min(len(w.data), rows * max(2.0, min(8.0, target_s / max(t, 1e-3)))))
+    pairs = rows * len(w.randoms)
+    return pairs / t, nthr, "%d data rows x %d randoms (DR, brute force, %.1f s)" % (
+        rows, len(w.randoms), t)
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return
+    import oracle  # noqa: F401
+    vals = []
+    desc = ""
+    thr = 0
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, target_s=3.0)
+    for _ in range(args.steps):
+        v, thr, desc = cpu_oracle_rate(w, target_s=8.0)
+        vals.append(v)
+    v = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "kind": w.kind},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": thr, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, w, rank, world):
+    import torch
+    from paper_1210_1833_gb300 import cute
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cute.Context(dev)
+    ctx.set_timing(True)
+    nd, nr = len(w.data), len(w.randoms)
+    reach = [w.edges0[-1]] * 3
+    d_dev = torch.from_numpy(w.data).to(f"cuda:{dev}")
+    r_dev = torch.from_numpy(w.randoms).to(f"cuda:{dev}")
+    d_pin = torch.from_numpy(w.data).pin_memory()
+    r_pin = torch.from_numpy(w.randoms).pin_memory()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")  # 256 MB
+    state = {"cand": 0, "kms": [], "rr_cand": 0, "rr_ms": [], "inrange": 0, "rechecked": 0}
+
+    def step(dsrc, rsrc, record):
+        cd = ctx.upload(dsrc)
+        cr = ctx.upload(rsrc)
+        ctx.grid([cd, cr], reach)
+        res = {}
+        for name, a, b in (("DD", cd, None), ("DR", cd, cr), ("RR", cr, None)):
+            c, _, _ = ctx.count("rmu", a, b, w.edges0, w.edges1, want_oor=False)
+            res[name] = c
+            if record:
+                st = ctx.stats()
+                state["cand"] += st["candidate_pairs"]
+                state["kms"].append(st["kernel_ms"])
+                state["rechecked"] += st["rechecked_pairs"]
+                state["inrange"] += int(c.sum())
+                if name == "RR":
+                    state["rr_cand"] = st["candidate_pairs"]
+                    state["rr_ms"].append(st["kernel_ms"])
+        xi = cute.estimator("ls", res["DD"], res["DR"], res["RR"], nd, nr)
+        cd.free()
+        cr.free()
+        return xi
+
+    def timed(dsrc, rsrc, steps, record):
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(dsrc, rsrc, record)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times
+
+    for _ in range(args.warmup):
+        step(d_dev, r_dev, False)
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev)
+    clk.start()
+    t_dev = timed(d_dev, r_dev, args.steps, True)
+    t_e2e = timed(d_pin, r_pin, max(1, args.steps // 2), False)
+    clocks = clk.stop()
+    ms = float(np.sum(t_dev)) / len(t_dev)
+    ms_e2e = float(np.sum(t_e2e)) / len(t_e2e)
+    if world > 1:
+        t = torch.tensor([ms, ms_e2e], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+    cand_per_step = state["cand"] / args.steps
+    value = world * cand_per_step / (ms / 1e3)
+    e2e_value = world * cand_per_step / (ms_e2e / 1e3)
+    if rank != 0:
+        return
+    pk, src = peaks()
+    smax = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tinst = SM_COUNT * FP32_LANES_PER_SM * smax * 1e6 / 1e12
+    rr_ms = float(np.mean(state["rr_ms"])) if state["rr_ms"] else float("nan")
+    rr_rate = state["rr_cand"] / (rr_ms / 1e3)
+    achieved = rr_rate * I_PAIR_RMU / 1e12
+    cpu_v, cpu_thr, cpu_desc = cpu_oracle_rate(w, target_s=12.0)
+    launches_per_step = 2 + 2 * 3 + 3  # upload stats x2, grid (assign, scan, scatter) x2, counts x3
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "kind": "rmu", "n_data": nd, "n_randoms": nr,
+                   "bins": [len(w.edges0) - 1, len(w.edges1) - 1], "counts": ["DD", "DR", "RR"],
+                   "estimator": "landy-szalay", "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "pairs": {"candidate_per_step": cand_per_step,
+                  "in_range_per_step": state["inrange"] / args.steps,
+                  "all_pairs_per_step": total_pairs(nd, nr),
+                  "in_range_pairs_per_s": world * state["inrange"] / args.steps / (ms / 1e3),
+                  "all_pairs_per_s": world * total_pairs(nd, nr) / (ms / 1e3),
+                  "rechecked_fraction": state["rechecked"] / max(1, state["cand"]),
+                  "count_kernel_ms_per_step": float(np.sum(state["kms"])) / args.steps},
+        "roofline": {"bound": "alu", "kernel": "k_count<R_MU> (RR)", "achieved": achieved,
+                     "peak": peak_tinst, "unit": "Tinst/s", "frac": achieved / peak_tinst,
+                     "traffic": None, "i_pair": I_PAIR_RMU,
+                     "peak_note": "152 SMs x 128 FP32 lanes x %.0f MHz (%s max clock)" % (
+                         smax, src),
+                     "kernel_ms": rr_ms, "candidate_pairs": state["rr_cand"]},
+        "cpu_baseline": {"value": cpu_v, "unit": "pairs/s", "cores": cpu_thr, "kind": "oracle",
+                         "sample": cpu_desc},
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "ms_per_step": ms_e2e,
+                "h2d_bytes_per_step": int(w.data.nbytes + w.randoms.nbytes),
+                "d2h_bytes_per_step": int(3 * 8 * (len(w.edges0) - 1) * (len(w.edges1) - 1))},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1 = full size)")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "gb300" else "gloo")
+    w = synthetic.c2_rmu_lightcone(scale=args.scale)
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+    else:
+        run_gpu(args, w, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * cute.h -- C ABI of libcute_gb.so, GB300 (sm_103a) pair counting for
+ * two-point correlation functions (Alonso 2012, "CUTE solutions for
+ * two-point correlation functions from large cosmological datasets").
+ *
+ * The problem (Sec. 3.1 and Sec. 2.2, Eq. 11): given a data catalog D, a
+ * random catalog R, separation bins and a separation measure, produce the
+ * DD, DR and RR pair-count histograms and from them an estimator of the
+ * correlation function (Eq. 13, 14, 15).  The separation measures are the
+ * monopole distance, (sigma, pi) and (r, mu) (Sec. 2.1, Eq. 2-4) and the
+ * angle between unit vectors (Eq. 7), binned on the squared chord.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a cute_status; nothing aborts, exits or traps.  On
+ *     failure the message is available from cute_last_error(ctx).
+ *   - Pointers marked "host or device" may point to host memory (pageable
+ *     or pinned) or to device memory of the context's device; the library
+ *     detects which.  The caller keeps ownership of every pointer it passes.
+ *   - Positions are FP64, row-major n x 3 (x0 y0 z0 x1 y1 z1 ...).
+ *   - Auto-correlations (cat_a == cat_b) count each unordered pair i<j once;
+ *     cross-correlations count every (i in A, j in B).  Histograms are
+ *     uint64 per bin, row-major [axis0][axis1] for the 2-D kinds.
+ *   - Bins are half-open, [e_b, e_{b+1}), compared on squared quantities
+ *     (e_b * e_b in FP64).  Counts equal, bit for bit, those of the FP64
+ *     canonical formulas below: pairs whose FP32 separation lies within a
+ *     proven error bound of an edge are re-tested in FP64 on the GPU.
+ *   - Work is enqueued on the context's CUDA stream.  Calls that write to
+ *     host memory synchronise that stream before returning.
+ */
+#ifndef CUTE_H
+#define CUTE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cute_ctx cute_ctx; /* opaque; owns device memory and a stream */
+
+typedef enum {
+  CUTE_OK = 0,
+  CUTE_E_INVALID = -1,     /* bad argument; nothing was enqueued          */
+  CUTE_E_OOM = -2,         /* device or host allocation failed            */
+  CUTE_E_CUDA = -3,        /* a CUDA runtime call failed                  */
+  CUTE_E_STATE = -4,       /* object missing or in the wrong state        */
+  CUTE_E_TIMEOUT = -5,     /* a bounded device-side wait gave up          */
+  CUTE_E_UNSUPPORTED = -6, /* valid request this build does not implement */
+  CUTE_E_DEVICE = -7       /* a kernel reported an internal inconsistency */
+} cute_status;
+
+/* Separation measure (Sec. 2.1). */
+typedef enum {
+  CUTE_MONO = 0,     /* |x_j - x_i|; edges0 = r edges                       */
+  CUTE_R_MU = 1,     /* r and mu = |s.l|/(|s||l|), l = x_i + x_j (midpoint
+                        line of sight, observer at the origin; open only);
+                        edges0 = r edges, edges1 = mu edges, 0 ... 1         */
+  CUTE_SIGMA_PI = 2, /* sigma = |(dx,dy)|, pi = |dz| (z line of sight);
+                        edges0 = sigma edges, edges1 = pi edges             */
+  CUTE_THETA = 3     /* chord |n_j - n_i| = 2 sin(theta/2) between unit
+                        vectors (open only); edges0 = chord edges, see
+                        cute_theta_to_chord                                  */
+} cute_kind;
+
+typedef enum {
+  CUTE_PERIODIC = 0, /* cubic box [0, L)^3, minimum-image separations      */
+  CUTE_OPEN = 1      /* no boundary (light cone, sky); no wrapping          */
+} cute_boundary;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t of
+   that device to enqueue on, or NULL for a stream the context creates and
+   owns.  *out receives the context.  Errors: CUTE_E_INVALID (bad device or
+   out == NULL), CUTE_E_CUDA, CUTE_E_OOM. */
+cute_status cute_ctx_create(int device, void *cuda_stream, cute_ctx **out);
+
+/* Wait for the context's work, free every catalog, plan and buffer it owns,
+   and the context.  NULL is accepted and ignored. */
+cute_status cute_ctx_destroy(cute_ctx *ctx);
+
+/* Message of the last failed call on ctx (empty string if none).  The
+   pointer stays valid until the next call on ctx.  ctx NULL -> a message
+   about the last failed cute_ctx_create in this process. */
+const char *cute_last_error(const cute_ctx *ctx);
+
+/* Wait for all work enqueued on the context's stream and return the first
+   deferred error a kernel reported (CUTE_E_TIMEOUT, CUTE_E_DEVICE) or a
+   CUDA error. */
+cute_status cute_sync(cute_ctx *ctx);
+
+/* ---------------------------------------------------------------- catalogs */
+
+/* Copy a catalog to the device (Sec. 3.1: the x, y, z arrays of each
+   catalog).  xyz: n x 3 FP64, host or device.  w: n FP32 weights (host or
+   device) or NULL for unit weights.  Periodic catalogs must satisfy
+   0 <= x < box_L on every axis, else CUTE_E_INVALID and no catalog is made.
+   box_L is ignored for CUTE_OPEN.  The copy belongs to ctx until
+   cute_catalog_free or cute_ctx_destroy.  *cat_id receives its handle.
+   n may be 0.  n above 2^31 - 1 is CUTE_E_INVALID. */
+cute_status cute_catalog_upload(cute_ctx *ctx, const double *xyz, const float *w,
+                                int64_t n, cute_boundary boundary, double box_L,
+                                int32_t *cat_id);
+
+/* Free a catalog and its cell grid.  CUTE_E_STATE if cat_id is unknown. */
+cute_status cute_catalog_free(cute_ctx *ctx, int32_t cat_id);
+
+/* Number of objects of a catalog. */
+cute_status cute_catalog_size(cute_ctx *ctx, int32_t cat_id, int64_t *n);
+
+/* Cell grid (Sec. 3.3): cover the volume with cells no smaller than
+   reach[k] / cells_per_reach on axis k and counting-sort every listed
+   catalog into them, on ONE geometry shared by all of them (their joint
+   bounding box for CUTE_OPEN, [0, L)^3 for CUTE_PERIODIC), so that any two
+   of them can then be counted against each other.  reach[3] is the largest
+   separation per axis that must be found (r_max on each axis for the
+   monopole, (r,mu) and theta; (sigma_max, sigma_max, pi_max) for
+   (sigma,pi)).  cells_per_reach: 1..8, or 0 for the default (2).
+   All catalogs must have the same boundary (and box_L).  A periodic grid
+   needs reach[k] <= 0.47 box_L, else CUTE_E_UNSUPPORTED.  Rebuilding a
+   catalog's grid replaces the previous one. */
+cute_status cute_grid_build(cute_ctx *ctx, const int32_t *cat_ids, int32_t n_cats,
+                            const double reach[3], int32_t cells_per_reach);
+
+/* ---------------------------------------------------------------- counting */
+
+typedef struct {
+  cute_kind kind;
+  int32_t cat_a, cat_b;  /* cat_a == cat_b: auto-correlation (i<j)          */
+  const double *edges0;  /* host; n0 + 1 strictly increasing values >= 0    */
+  int32_t n0;
+  const double *edges1;  /* host; n1 + 1 values for CUTE_R_MU (0 ... 1) and
+                            CUTE_SIGMA_PI; NULL / 0 for the 1-D kinds       */
+  int32_t n1;
+  int32_t weighted;      /* 1: also produce sum of w_i w_j per bin (FP64)   */
+} cute_pair_desc;
+
+/* Count the pairs of d->cat_a x d->cat_b into bins (Sec. 2.2 Eq. 11; the
+   hot loop of Sec. 3.1-3.2).  Both catalogs need cell grids of the same
+   geometry whose reach covers the largest edge on every axis.
+   counts: n0 * n1 (n1 = 1 for 1-D kinds) uint64, host or device.
+   oor: if not NULL, receives the number of examined pairs that fall in no
+        bin (total pairs minus the sum of counts); host.
+   wsum: if d->weighted, n0 * n1 doubles (host or device) receiving the sum
+        of w_i * w_j per bin, accurate to 1e-9 relative or better.
+   Errors: CUTE_E_INVALID, CUTE_E_STATE (catalog or grid missing or on
+   different geometries, reach too small), CUTE_E_UNSUPPORTED (kind not
+   defined for the boundary), CUTE_E_CUDA, CUTE_E_TIMEOUT. */
+cute_status cute_count_pairs(cute_ctx *ctx, const cute_pair_desc *d, uint64_t *counts,
+                             uint64_t *oor, double *wsum);
+
+/* Count n independent pair sets in ONE persistent launch (the many-mock
+   use of Fig. 5).  All descriptors must share kind, edges and weighted.
+   counts[k]: output of descriptor k as in cute_count_pairs (host or device).
+   wsum may be NULL; else wsum[k] as in cute_count_pairs.  The result equals
+   n separate cute_count_pairs calls bit for bit. */
+cute_status cute_count_pairs_batched(cute_ctx *ctx, int32_t n, const cute_pair_desc *d,
+                                     uint64_t *const *counts, double *const *wsum);
+
+/* Gradient of the weighted-count functional F = sum_b G_b W_b, W_b the
+   weighted count of bin b (weights of Sec. 3.4), with respect to every
+   object's weight:  dF/dw_i = sum_j w_j G[bin(i, j)] over i's partners
+   (j != i for auto).  G: n0 * n1 doubles (host or device).  grad_a: n_a
+   doubles, the gradient for catalog A's weights in A's upload order (host
+   or device).  grad_b: for cross counts, n_b doubles for catalog B's
+   weights (host or device), or NULL to skip; ignored for auto. */
+cute_status cute_count_pairs_adjoint(cute_ctx *ctx, const cute_pair_desc *d, const double *G,
+                                     double *grad_a, double *grad_b);
+
+/* Statistics of the last count call on ctx. */
+typedef struct {
+  uint64_t candidate_pairs; /* pairs examined by the FP32 path              */
+  uint64_t rechecked_pairs; /* of those, re-tested in FP64 near an edge     */
+  uint64_t work_items;      /* (home chunk, neighbour slice) items run      */
+  int32_t launches;         /* kernels launched by the call                 */
+  int32_t warps_per_block, blocks, home_per_lane;
+  float kernel_ms;          /* device time of the counting kernel(s), if
+                               timing was enabled with cute_set_timing     */
+} cute_stats;
+cute_status cute_last_stats(cute_ctx *ctx, cute_stats *out);
+
+/* Enable (1) or disable (0) CUDA-event timing of the counting kernels
+   (adds two events per call; off by default). */
+cute_status cute_set_timing(cute_ctx *ctx, int32_t on);
+
+/* Launch shape override for the counting kernel: home_per_lane in {1,2,4}
+   (objects of A held per lane; 0 = library default), warps_per_block
+   (0 = largest that fits), slice (neighbour objects per work item, 0 =
+   default, multiple of 64).  Used by the autotuner. */
+cute_status cute_set_launch(cute_ctx *ctx, int32_t home_per_lane, int32_t warps_per_block,
+                            int32_t slice);
+
+/* ---------------------------------------------------------------- estimators
+   Host FP64 arithmetic on exact counts (Sec. 2.2).  Counts are unique pairs.
+   A bin whose denominator is zero gives NaN.  No device work, no context. */
+typedef enum {
+  CUTE_EST_PERIODIC = 0, /* Eq. 13 with N(N-1)/2 pairs and exact shells:
+                            xi = DD / (N(N-1)/2 * 4pi/3 (e1^3 - e0^3) / L^3) - 1;
+                            uses DD, Nd, edges, box_L                        */
+  CUTE_EST_NATURAL = 1,  /* Eq. 14: Nr(Nr-1)/(Nd(Nd-1)) DD/RR - 1          */
+  CUTE_EST_LS = 2        /* Eq. 15: (Nr(Nr-1)/(Nd(Nd-1)) DD - (Nr-1)/Nd DR
+                            + RR) / RR                                       */
+} cute_estimator_kind;
+
+/* DD, DR, RR: nbins uint64 on the host (DR/RR may be NULL when unused);
+   edges: nbins + 1 r edges (periodic only); xi_out: nbins doubles, host. */
+cute_status cute_estimator(cute_estimator_kind k, const uint64_t *DD, const uint64_t *DR,
+                           const uint64_t *RR, int64_t Nd, int64_t Nr, int32_t nbins,
+                           const double *edges, double box_L, double *xi_out);
+
+/* Chord between unit vectors an angle theta apart (Eq. 7 gives
+   cos theta = n_1 . n_2): chord = 2 sin(theta/2), theta in degrees, FP64,
+   host.  The chord is monotone in theta, so binning chords on these edges
+   bins theta on the given angles. */
+cute_status cute_theta_to_chord(const double *theta_deg, int32_t n, double *chord_out);
+
+/* Library version string. */
+const char *cute_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUTE_H */

@@ -1,0 +1,595 @@
+// api.cu -- the C ABI of libcute_gb.so (include/cute.h): contexts, catalogs,
+// cell grids and the counting driver.  The driver validates a request,
+// derives the FP32 error bounds from the catalog geometry, builds (or reuses)
+// the binning plan and the task list, launches the persistent counting
+// kernel and copies the histograms out.
+#include "cute_internal.h"
+#include "count_kernel.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <sstream>
+
+namespace cute {
+cute_status catalog_stage(cute_ctx *ctx, Catalog &c, const double *xyz, const float *w);
+void catalog_release(Catalog &c);
+cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const double reach[3],
+                       int kreq);
+cute_status ensure_scratch(cute_ctx *ctx, size_t bytes);
+cudaError_t launch_count_mono(const KParams &p, bool periodic, int hp, int blocks, int threads,
+                              size_t smem, cudaStream_t st);
+cudaError_t launch_count_sigpi(const KParams &p, bool periodic, int hp, int blocks, int threads,
+                               size_t smem, cudaStream_t st);
+cudaError_t launch_count_rmu(const KParams &p, int hp, int blocks, int threads, size_t smem,
+                             cudaStream_t st);
+cute_status adjoint_driver(cute_ctx *ctx, const cute_pair_desc *d, const double *G,
+                           double *grad_a, double *grad_b);
+cute_status weighted_driver(cute_ctx *ctx, int n, const cute_pair_desc *d, uint64_t *const *counts,
+                            double *const *wsum, uint64_t *oor);
+}  // namespace cute
+
+using namespace cute;
+
+static thread_local std::string g_create_err;
+
+static cute_status fail(cute_ctx *ctx, cute_status st, const std::string &m) {
+  if (ctx) ctx->err = m;
+  else g_create_err = m;
+  return st;
+}
+
+#define CUDA_OR_FAIL(call)                                                         \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? CUTE_E_OOM : CUTE_E_CUDA, \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));             \
+  } while (0)
+
+#define ENTER(ctx)                                                      \
+  do {                                                                  \
+    if (!(ctx)) return CUTE_E_INVALID;                                  \
+    (ctx)->err.clear();                                                 \
+    cudaError_t e0_ = cudaSetDevice((ctx)->device);                     \
+    if (e0_ != cudaSuccess) return fail(ctx, CUTE_E_CUDA, cudaGetErrorString(e0_)); \
+  } while (0)
+
+static bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+extern "C" {
+
+const char *cute_version(void) { return "cute_gb 0.1 (sm_103a)"; }
+
+cute_status cute_ctx_create(int device, void *cuda_stream, cute_ctx **out) {
+  if (!out) return fail(nullptr, CUTE_E_INVALID, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(nullptr, CUTE_E_CUDA, "no CUDA device available");
+  }
+  if (device < 0 || device >= ndev) return fail(nullptr, CUTE_E_INVALID, "bad device index");
+  if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, CUTE_E_CUDA, "cudaSetDevice failed");
+  cute_ctx *ctx = new (std::nothrow) cute_ctx();
+  if (!ctx) return fail(nullptr, CUTE_E_OOM, "host allocation failed");
+  ctx->device = device;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    delete ctx;
+    return fail(nullptr, CUTE_E_CUDA, "cudaGetDeviceProperties failed");
+  }
+  ctx->sm_count = prop.multiProcessorCount;
+  ctx->smem_optin = prop.sharedMemPerBlockOptin;
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return fail(nullptr, CUTE_E_CUDA, "cudaStreamCreate failed");
+    }
+    ctx->own_stream = true;
+  }
+  if (cudaMalloc(&ctx->d_ticket, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess ||
+      cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    cute_ctx_destroy(ctx);
+    return fail(nullptr, CUTE_E_OOM, "context allocation failed");
+  }
+  *out = ctx;
+  return CUTE_OK;
+}
+
+cute_status cute_ctx_destroy(cute_ctx *ctx) {
+  if (!ctx) return CUTE_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  ctx->plans.clear();
+  ctx->task_cache.clear();
+  for (auto &kv : ctx->cats) catalog_release(kv.second);
+  ctx->cats.clear();
+  cudaFree(ctx->d_ticket);
+  cudaFree(ctx->d_err);
+  cudaFree(ctx->d_scratch);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  cudaGetLastError();
+  delete ctx;
+  return CUTE_OK;
+}
+
+const char *cute_last_error(const cute_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+cute_status cute_sync(cute_ctx *ctx) {
+  ENTER(ctx);
+  CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+  int err = 0;
+  CUDA_OR_FAIL(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    CUDA_OR_FAIL(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    return fail(ctx, (cute_status)err, "a kernel reported an error");
+  }
+  return CUTE_OK;
+}
+
+cute_status cute_catalog_upload(cute_ctx *ctx, const double *xyz, const float *w, int64_t n,
+                                cute_boundary boundary, double box_L, int32_t *cat_id) {
+  ENTER(ctx);
+  if (!cat_id) return fail(ctx, CUTE_E_INVALID, "cat_id is NULL");
+  if (n < 0 || n > 0x7fffffffLL) return fail(ctx, CUTE_E_INVALID, "n out of range");
+  if (n > 0 && !xyz) return fail(ctx, CUTE_E_INVALID, "xyz is NULL");
+  if (boundary != CUTE_PERIODIC && boundary != CUTE_OPEN)
+    return fail(ctx, CUTE_E_INVALID, "bad boundary");
+  if (boundary == CUTE_PERIODIC && !(box_L > 0 && std::isfinite(box_L)))
+    return fail(ctx, CUTE_E_INVALID, "periodic catalogs need box_L > 0");
+  Catalog c;
+  c.id = ctx->next_cat++;
+  c.n = n;
+  c.boundary = boundary;
+  c.L = boundary == CUTE_PERIODIC ? box_L : 0.0;
+  cute_status st = catalog_stage(ctx, c, xyz, w);
+  if (st != CUTE_OK) {
+    std::string m = ctx->err;
+    catalog_release(c);
+    return fail(ctx, st, m);
+  }
+  ctx->cats[c.id] = c;
+  *cat_id = c.id;
+  return CUTE_OK;
+}
+
+cute_status cute_catalog_free(cute_ctx *ctx, int32_t cat_id) {
+  ENTER(ctx);
+  auto it = ctx->cats.find(cat_id);
+  if (it == ctx->cats.end()) return fail(ctx, CUTE_E_STATE, "unknown catalog");
+  CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+  ctx->task_cache.clear();
+  catalog_release(it->second);
+  ctx->cats.erase(it);
+  return CUTE_OK;
+}
+
+cute_status cute_catalog_size(cute_ctx *ctx, int32_t cat_id, int64_t *n) {
+  ENTER(ctx);
+  auto it = ctx->cats.find(cat_id);
+  if (it == ctx->cats.end() || !n) return fail(ctx, CUTE_E_STATE, "unknown catalog");
+  *n = it->second.n;
+  return CUTE_OK;
+}
+
+cute_status cute_grid_build(cute_ctx *ctx, const int32_t *cat_ids, int32_t n_cats,
+                            const double reach[3], int32_t cells_per_reach) {
+  ENTER(ctx);
+  if (!cat_ids || n_cats < 1 || !reach) return fail(ctx, CUTE_E_INVALID, "bad arguments");
+  if (cells_per_reach == 0) cells_per_reach = 2;
+  if (cells_per_reach < 1 || cells_per_reach > 8)
+    return fail(ctx, CUTE_E_INVALID, "cells_per_reach must be 1..8");
+  for (int k = 0; k < 3; k++)
+    if (!(reach[k] > 0) || !std::isfinite(reach[k])) return fail(ctx, CUTE_E_INVALID, "reach must be > 0");
+  std::vector<Catalog *> cats;
+  for (int i = 0; i < n_cats; i++) {
+    auto it = ctx->cats.find(cat_ids[i]);
+    if (it == ctx->cats.end()) return fail(ctx, CUTE_E_STATE, "unknown catalog");
+    for (Catalog *c : cats)
+      if (c == &it->second) return fail(ctx, CUTE_E_INVALID, "catalog listed twice");
+    cats.push_back(&it->second);
+  }
+  for (Catalog *c : cats) {
+    if (c->boundary != cats[0]->boundary || c->L != cats[0]->L)
+      return fail(ctx, CUTE_E_INVALID, "catalogs of one grid must share boundary and box");
+  }
+  CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+  ctx->task_cache.clear();
+  return grid_build(ctx, cats, reach, cells_per_reach);
+}
+
+cute_status cute_set_timing(cute_ctx *ctx, int32_t on) {
+  ENTER(ctx);
+  ctx->timing = on != 0;
+  return CUTE_OK;
+}
+
+cute_status cute_set_launch(cute_ctx *ctx, int32_t hp, int32_t warps, int32_t slice) {
+  ENTER(ctx);
+  if (hp != 0 && hp != 2 && hp != 4) return fail(ctx, CUTE_E_INVALID, "home_per_lane must be 0, 2 or 4");
+  if (warps < 0 || warps > 16) return fail(ctx, CUTE_E_INVALID, "warps_per_block must be 0..16");
+  if (slice < 0 || slice % kTile) return fail(ctx, CUTE_E_INVALID, "slice must be a multiple of 64");
+  ctx->hp_override = hp;
+  ctx->warps_override = warps;
+  ctx->slice_override = slice;
+  return CUTE_OK;
+}
+
+cute_status cute_last_stats(cute_ctx *ctx, cute_stats *out) {
+  ENTER(ctx);
+  if (!out) return fail(ctx, CUTE_E_INVALID, "out is NULL");
+  CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+  unsigned long long h[3] = {0, 0, 0};
+  CUDA_OR_FAIL(cudaMemcpy(h, ctx->d_ticket, sizeof(h), cudaMemcpyDeviceToHost));
+  ctx->stats.rechecked_pairs = h[1];
+  ctx->stats.work_items = h[2];
+  if (ctx->timing && ctx->stats.launches > 0) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->stats.kernel_ms = ms;
+    cudaGetLastError();
+  }
+  *out = ctx->stats;
+  return CUTE_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ count driver
+namespace cute {
+
+struct DescInfo {
+  int kind;        // KMONO / KRMU / KSIGPI / KTHETA
+  Catalog *A, *B;
+  const Geometry *g;
+  bool is_auto;
+  double need[3];
+};
+
+cute_status validate_desc(cute_ctx *ctx, const cute_pair_desc *d, DescInfo &di) {
+  if (!d) return fail(ctx, CUTE_E_INVALID, "descriptor is NULL");
+  if (d->kind < CUTE_MONO || d->kind > CUTE_THETA) return fail(ctx, CUTE_E_INVALID, "bad kind");
+  const bool two_d = (d->kind == CUTE_R_MU || d->kind == CUTE_SIGMA_PI);
+  if (!d->edges0 || d->n0 < 1 || d->n0 > 4096) return fail(ctx, CUTE_E_INVALID, "edges0/n0 invalid");
+  if (two_d && (!d->edges1 || d->n1 < 1 || d->n1 > 4096)) return fail(ctx, CUTE_E_INVALID, "edges1/n1 invalid");
+  for (int k = 0; k <= d->n0; k++) {
+    if (!(d->edges0[k] >= 0) || !std::isfinite(d->edges0[k]) || (k && !(d->edges0[k] > d->edges0[k - 1])))
+      return fail(ctx, CUTE_E_INVALID, "edges0 must be finite, >= 0 and strictly increasing");
+  }
+  if (two_d) {
+    for (int k = 0; k <= d->n1; k++) {
+      if (!(d->edges1[k] >= 0) || !std::isfinite(d->edges1[k]) ||
+          (k && !(d->edges1[k] > d->edges1[k - 1])))
+        return fail(ctx, CUTE_E_INVALID, "edges1 must be finite, >= 0 and strictly increasing");
+    }
+    if (d->kind == CUTE_R_MU && (d->edges1[0] != 0.0 || d->edges1[d->n1] != 1.0))
+      return fail(ctx, CUTE_E_INVALID, "mu edges must run from 0 to 1");
+  }
+  auto ia = ctx->cats.find(d->cat_a), ib = ctx->cats.find(d->cat_b);
+  if (ia == ctx->cats.end() || ib == ctx->cats.end()) return fail(ctx, CUTE_E_STATE, "unknown catalog");
+  di.A = &ia->second;
+  di.B = &ib->second;
+  di.is_auto = (d->cat_a == d->cat_b);
+  di.kind = (int)d->kind;
+  if (di.A->geom < 0 || di.B->geom < 0) return fail(ctx, CUTE_E_STATE, "catalog has no cell grid");
+  if (di.A->geom != di.B->geom) return fail(ctx, CUTE_E_STATE, "catalogs are on different grids");
+  auto gi = ctx->geoms.find(di.A->geom);
+  if (gi == ctx->geoms.end()) return fail(ctx, CUTE_E_STATE, "grid geometry missing");
+  di.g = &gi->second;
+  if ((d->kind == CUTE_R_MU || d->kind == CUTE_THETA) && di.g->periodic)
+    return fail(ctx, CUTE_E_UNSUPPORTED, "R_MU and THETA are defined for open catalogs only");
+  double r0 = d->edges0[d->n0];
+  if (d->kind == CUTE_SIGMA_PI) {
+    di.need[0] = di.need[1] = r0;
+    di.need[2] = d->edges1[d->n1];
+  } else {
+    di.need[0] = di.need[1] = di.need[2] = r0;
+  }
+  for (int k = 0; k < 3; k++)
+    if (di.need[k] > di.g->reach[k])
+      return fail(ctx, CUTE_E_STATE, "the grid's reach is smaller than the largest edge");
+  if (d->weighted && (!di.A->d_w || !di.B->d_w) && (di.A->n > 0 && di.B->n > 0))
+    return fail(ctx, CUTE_E_STATE, "weighted counts need catalogs uploaded with weights");
+  return CUTE_OK;
+}
+
+static const double kU32 = 5.9604644775390625e-08;
+
+ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax) {
+  ErrorParams ep{0, 0, 0};
+  double absmax = 0, rmin = 1e300;
+  for (const DescInfo &di : dis) {
+    const Geometry &g = *di.g;
+    double xm = std::max(g.xmax[0], std::max(g.xmax[1], g.xmax[2]));
+    double e;
+    if (g.periodic) e = kU32 * (3.0 * xm + 2.0 * g.L) * 1.01 + 1e-12 * (xm + g.L);
+    else e = kU32 * 2.0 * xm * 1.01 + 1e-12 * xm;
+    ep.eta0 = std::max(ep.eta0, e);
+    absmax = std::max(absmax, std::max(g.absmax[0], std::max(g.absmax[1], g.absmax[2])));
+    rmin = std::min(rmin, g.rmin);
+  }
+  ep.eta_l = kU32 * (4.0 * absmax + rmax) * 1.01 + ep.eta0 + kU32 * rmax;
+  ep.lmin = 2.0 * rmin - rmax;
+  return ep;
+}
+
+cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &ep, int hp,
+                     std::shared_ptr<Plan> &out) {
+  std::ostringstream key;
+  key.precision(17);
+  key << d->kind << "|" << ep.eta0 << "|" << ep.eta_l << "|" << ep.lmin << "|" << hp << "|";
+  for (int k = 0; k <= d->n0; k++) key << d->edges0[k] << ",";
+  if (d->kind == CUTE_R_MU || d->kind == CUTE_SIGMA_PI)
+    for (int k = 0; k <= d->n1; k++) key << d->edges1[k] << ",";
+  auto it = ctx->plans.find(key.str());
+  if (it != ctx->plans.end()) {
+    out = it->second;
+    return CUTE_OK;
+  }
+  auto P = std::make_shared<Plan>();
+  const bool two_d = (d->kind == CUTE_R_MU || d->kind == CUTE_SIGMA_PI);
+  std::string m = plan_build((int)d->kind, d->edges0, d->n0, d->edges1, two_d ? d->n1 : 1, ep,
+                             two_d ? 8192 : 8192, 10752, *P);
+  if (!m.empty()) return fail(ctx, CUTE_E_UNSUPPORTED, m);
+  auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  CUDA_OR_FAIL(up((void **)&P->d_lut, P->lut.data(), P->lut.size() * 4));
+  CUDA_OR_FAIL(up((void **)&P->d_band, P->band.data(), P->band.size() * 4));
+  CUDA_OR_FAIL(up((void **)&P->d_mu_eps, P->mu_eps.data(), P->mu_eps.size() * 4));
+  CUDA_OR_FAIL(up((void **)&P->d_mu_edge, P->mu_edge.data(), P->mu_edge.size() * 4));
+  CUDA_OR_FAIL(up((void **)&P->d_E0, P->E0.data(), P->E0.size() * 8));
+  CUDA_OR_FAIL(up((void **)&P->d_E1, P->E1.data(), P->E1.size() * 8));
+  ctx->plans[key.str()] = P;
+  out = P;
+  return CUTE_OK;
+}
+
+cute_status get_tasks(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, int slice,
+                      bool full_stencil, std::shared_ptr<TaskSet> &out) {
+  std::ostringstream key;
+  key << hp << "|" << slice << "|" << full_stencil << "|";
+  for (const DescInfo &di : dis)
+    key << di.A->id << ":" << di.A->grid_version << ":" << di.B->id << ":" << di.B->grid_version << ",";
+  auto it = ctx->task_cache.find(key.str());
+  if (it != ctx->task_cache.end()) {
+    out = it->second;
+    return CUTE_OK;
+  }
+  auto T = std::make_shared<TaskSet>();
+  for (size_t i = 0; i < dis.size(); i++) {
+    const DescInfo &di = dis[i];
+    PairDev pd;
+    pd.posA = di.A->d_pos;
+    pd.posB = di.B->d_pos;
+    pd.sA = di.A->d_s64;
+    pd.sB = di.B->d_s64;
+    pd.nA = (int32_t)di.A->n;
+    pd.nB = (int32_t)di.B->n;
+    pd.out = (int32_t)i;
+    pd.is_auto = di.is_auto;
+    pd.L32 = (float)di.g->L;
+    pd.L64 = di.g->periodic ? di.g->L : 0.0;
+    T->pairs.push_back(pd);
+    if (di.A->n == 0 || di.B->n == 0) continue;
+    tasks_build(*di.g, di.A->h_cell_start, di.B->h_cell_start, di.is_auto, (int)i, 32 * hp, slice,
+                full_stencil, T->tasks, T->candidates);
+  }
+  T->prefix.resize(T->tasks.size() + 1);
+  T->prefix[0] = 0;
+  for (size_t t = 0; t < T->tasks.size(); t++)
+    T->prefix[t + 1] = T->prefix[t] + (long long)T->tasks[t].n_hc * T->tasks[t].n_sc;
+  auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return e;
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  CUDA_OR_FAIL(up((void **)&T->d_tasks, T->tasks.data(), T->tasks.size() * sizeof(Task)));
+  CUDA_OR_FAIL(up((void **)&T->d_prefix, T->prefix.data(), T->prefix.size() * sizeof(long long)));
+  CUDA_OR_FAIL(up((void **)&T->d_pairs, T->pairs.data(), T->pairs.size() * sizeof(PairDev)));
+  ctx->task_cache[key.str()] = T;
+  out = T;
+  return CUTE_OK;
+}
+
+// common preparation of a (batched) count: validation, plan, tasks, params
+struct Prepared {
+  std::vector<DescInfo> dis;
+  std::shared_ptr<Plan> plan;
+  std::shared_ptr<TaskSet> ts;
+  KParams p;
+  int hp, warps, blocks;
+  size_t smem;
+};
+
+cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, bool weighted, bool full_stencil,
+                    Prepared &pr) {
+  if (n < 1 || !d) return fail(ctx, CUTE_E_INVALID, "no descriptors");
+  pr.dis.resize(n);
+  for (int i = 0; i < n; i++) {
+    cute_status st = validate_desc(ctx, &d[i], pr.dis[i]);
+    if (st != CUTE_OK) return st;
+    if (i > 0) {
+      bool same = d[i].kind == d[0].kind && d[i].n0 == d[0].n0 && d[i].weighted == d[0].weighted &&
+                  std::equal(d[i].edges0, d[i].edges0 + d[i].n0 + 1, d[0].edges0);
+      if (same && (d[0].kind == CUTE_R_MU || d[0].kind == CUTE_SIGMA_PI))
+        same = d[i].n1 == d[0].n1 && std::equal(d[i].edges1, d[i].edges1 + d[i].n1 + 1, d[0].edges1);
+      if (!same) return fail(ctx, CUTE_E_INVALID, "batched descriptors must share kind, edges and weighted");
+      if (pr.dis[i].g->periodic != pr.dis[0].g->periodic)
+        return fail(ctx, CUTE_E_INVALID, "batched descriptors must share the boundary");
+    }
+  }
+  ErrorParams ep = error_params(pr.dis, d[0].edges0[d[0].n0]);
+  pr.hp = ctx->hp_override ? ctx->hp_override : 4;
+  cute_status st = get_plan(ctx, &d[0], ep, pr.hp, pr.plan);
+  if (st != CUTE_OK) return st;
+  int slice = ctx->slice_override ? ctx->slice_override : 2048;
+  st = get_tasks(ctx, pr.dis, pr.hp, slice, full_stencil, pr.ts);
+  if (st != CUTE_OK) return st;
+  const Plan &P = *pr.plan;
+  SmemLayout L = smem_layout((int)P.lut.size(), P.nslots, P.R, pr.hp, weighted);
+  size_t avail = ctx->smem_optin;
+  int warps = ctx->warps_override ? ctx->warps_override : 16;
+  while (warps > 1 && (size_t)L.lut_bytes + (size_t)warps * L.warp_bytes > avail) warps--;
+  if ((size_t)L.lut_bytes + (size_t)warps * L.warp_bytes > avail)
+    return fail(ctx, CUTE_E_UNSUPPORTED, "binning tables do not fit in shared memory");
+  pr.warps = warps;
+  pr.smem = (size_t)L.lut_bytes + (size_t)warps * L.warp_bytes;
+  pr.blocks = ctx->sm_count;
+  KParams &p = pr.p;
+  std::memset(&p, 0, sizeof(p));
+  p.tasks = pr.ts->d_tasks;
+  p.prefix = pr.ts->d_prefix;
+  p.ntasks = (int)pr.ts->tasks.size();
+  p.total = pr.ts->prefix.back();
+  p.pairs = pr.ts->d_pairs;
+  p.lut = P.d_lut;
+  p.lut_words = (int)P.lut.size();
+  p.ax[0] = P.ax[0];
+  p.ax[1] = P.ax[1];
+  p.band = P.d_band;
+  p.mu_eps = P.d_mu_eps;
+  p.mu_edge = P.d_mu_edge;
+  p.E0 = P.d_E0;
+  p.E1 = P.d_E1;
+  p.n0 = P.n0;
+  p.n1 = P.n1;
+  p.slots1 = P.slots1;
+  p.nslots = P.nslots;
+  p.R = P.R;
+  p.slice = slice;
+  p.eps_main = P.eps_main;
+  p.ticket = ctx->d_ticket;
+  p.stats = ctx->d_ticket + 1;
+  p.err = ctx->d_err;
+  return CUTE_OK;
+}
+
+cudaError_t launch_prepared(cute_ctx *ctx, const Prepared &pr, int kind) {
+  const bool per = pr.dis[0].g->periodic;
+  const int threads = pr.warps * 32;
+  switch (kind) {
+    case CUTE_MONO:
+      return launch_count_mono(pr.p, per, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
+    case CUTE_THETA:
+      return launch_count_mono(pr.p, false, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
+    case CUTE_SIGMA_PI:
+      return launch_count_sigpi(pr.p, per, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
+    default:
+      return launch_count_rmu(pr.p, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
+  }
+}
+
+// Counts of n pair sets into counts[k] (host or device); oor for n == 1.
+cute_status count_driver(cute_ctx *ctx, int n, const cute_pair_desc *d, uint64_t *const *counts,
+                         uint64_t *oor) {
+  for (int i = 0; i < n; i++)
+    if (!counts || !counts[i]) return fail(ctx, CUTE_E_INVALID, "counts is NULL");
+  Prepared pr;
+  cute_status st = prepare(ctx, n, d, false, false, pr);
+  if (st != CUTE_OK) return st;
+  const int nb = pr.p.n0 * pr.p.n1;
+  const size_t out_bytes = sizeof(unsigned long long) * (size_t)nb * n;
+  st = ensure_scratch(ctx, out_bytes);
+  if (st != CUTE_OK) return st;
+  unsigned long long *d_out = (unsigned long long *)ctx->d_scratch;
+  pr.p.out_counts = d_out;
+  CUDA_OR_FAIL(cudaMemsetAsync(d_out, 0, out_bytes, ctx->stream));
+  CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, 3 * sizeof(unsigned long long), ctx->stream));
+  ctx->stats = cute_stats{};
+  ctx->stats.candidate_pairs = pr.ts->candidates;
+  ctx->stats.warps_per_block = pr.warps;
+  ctx->stats.blocks = pr.blocks;
+  ctx->stats.home_per_lane = pr.hp;
+  if (ctx->timing) CUDA_OR_FAIL(cudaEventRecord(ctx->ev0, ctx->stream));
+  if (pr.p.total > 0) {
+    CUDA_OR_FAIL(launch_prepared(ctx, pr, (int)d[0].kind));
+    ctx->stats.launches = 1;
+  }
+  if (ctx->timing) CUDA_OR_FAIL(cudaEventRecord(ctx->ev1, ctx->stream));
+  bool need_sync = (oor != nullptr);
+  for (int i = 0; i < n; i++) {
+    bool dev = is_device_ptr(counts[i]);
+    CUDA_OR_FAIL(cudaMemcpyAsync(counts[i], d_out + (size_t)i * nb, sizeof(uint64_t) * nb,
+                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    if (!dev) need_sync = true;
+  }
+  if (need_sync) {
+    CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+    int err = 0;
+    CUDA_OR_FAIL(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+      CUDA_OR_FAIL(cudaMemset(ctx->d_err, 0, sizeof(int)));
+      return fail(ctx, (cute_status)err, "the counting kernel reported an error");
+    }
+  }
+  if (oor) {
+    std::vector<uint64_t> h(nb);
+    CUDA_OR_FAIL(cudaMemcpy(h.data(), d_out, sizeof(uint64_t) * nb, cudaMemcpyDeviceToHost));
+    uint64_t s = 0;
+    for (uint64_t v : h) s += v;
+    uint64_t na = (uint64_t)pr.dis[0].A->n, nbb = (uint64_t)pr.dis[0].B->n;
+    uint64_t total = pr.dis[0].is_auto ? (na ? na * (na - 1) / 2 : 0) : na * nbb;
+    *oor = total - s;
+  }
+  return CUTE_OK;
+}
+
+}  // namespace cute
+
+extern "C" {
+
+cute_status cute_count_pairs(cute_ctx *ctx, const cute_pair_desc *d, uint64_t *counts,
+                             uint64_t *oor, double *wsum) {
+  ENTER(ctx);
+  if (!d) return fail(ctx, CUTE_E_INVALID, "descriptor is NULL");
+  if (d->weighted) {
+    if (!wsum) return fail(ctx, CUTE_E_INVALID, "weighted counts need wsum");
+    double *const ws[1] = {wsum};
+    uint64_t *const cs[1] = {counts};
+    return weighted_driver(ctx, 1, d, cs, ws, oor);
+  }
+  uint64_t *const cs[1] = {counts};
+  return count_driver(ctx, 1, d, cs, oor);
+}
+
+cute_status cute_count_pairs_batched(cute_ctx *ctx, int32_t n, const cute_pair_desc *d,
+                                     uint64_t *const *counts, double *const *wsum) {
+  ENTER(ctx);
+  if (n < 1 || !d || !counts) return fail(ctx, CUTE_E_INVALID, "bad arguments");
+  if (d[0].weighted) {
+    if (!wsum) return fail(ctx, CUTE_E_INVALID, "weighted counts need wsum");
+    return weighted_driver(ctx, n, d, counts, wsum, nullptr);
+  }
+  return count_driver(ctx, n, d, counts, nullptr);
+}
+
+cute_status cute_count_pairs_adjoint(cute_ctx *ctx, const cute_pair_desc *d, const double *G,
+                                     double *grad_a, double *grad_b) {
+  ENTER(ctx);
+  return adjoint_driver(ctx, d, G, grad_a, grad_b);
+}
+
+}  // extern "C"

@@ -1,0 +1,324 @@
+// count_impl.cuh -- kernel body of the pair counter, instantiated per kind
+// in count_mono.cu, count_sigpi.cu and count_rmu.cu.
+#pragma once
+
+#include "count_kernel.cuh"
+
+namespace cute {
+
+template <int HP>
+struct Home {
+  float x[HP], y[HP], z[HP];   // home position minus the image shift (grid frame)
+  float ax[HP], ay[HP], az[HP];// R_MU: 2 x_i in the observer frame
+  int id[HP];                  // sorted index in A (INT_MAX when padded)
+};
+
+struct WarpSmem {
+  uint32_t *hist;
+  char *hist_lane;
+  int *qcnt;
+  int2 *queue;
+  int qcap;
+  float4 *tiles;
+};
+
+// Warp-cooperative FP64 re-test of queued pairs, 32 at a time (all of them
+// when draining).  Every lane must call it.
+template <int KIND>
+__device__ __noinline__ void process_queue(const KParams &p, const PairDev &pd, const WarpSmem &w,
+                                           int lane, bool drain) {
+  __syncwarp();
+  int n = *w.qcnt;
+  int done = 0;
+  while (n >= 32 || (drain && n > 0)) {
+    int take = min(n, 32);
+    if (lane < take) {
+      int2 e = w.queue[n - take + lane];
+      int s = slot64<KIND>(p, pd, e.x, e.y);
+      atomicAdd(&w.hist[s * p.R + (lane & (p.R - 1))], 1u);
+    }
+    n -= take;
+    done += take;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    *w.qcnt = n;
+    if (done) atomicAdd(&p.stats[0], (unsigned long long)done);
+  }
+  __syncwarp();
+}
+
+// add the warp's histogram to output `out` in HBM and clear it
+static __device__ __noinline__ void flush_hist(const KParams &p, const WarpSmem &w, int out, int lane) {
+  __syncwarp();
+  const int nb = p.n0 * p.n1;
+  for (int b = lane; b < nb; b += 32) {
+    int b0 = b / p.n1, b1 = b - b0 * p.n1;
+    int s = (b0 + 1) * p.slots1 + (p.slots1 > 1 ? b1 + 1 : 0);
+    unsigned long long sum = 0;
+    for (int r = 0; r < p.R; r++) sum += w.hist[s * p.R + r];
+    if (sum) atomicAdd(&p.out_counts[(size_t)out * nb + b], sum);
+  }
+  __syncwarp();
+  for (int i = lane; i < p.nslots * p.R; i += 32) w.hist[i] = 0;
+  __syncwarp();
+}
+
+// A pair whose table entry is dirty: refine against the band of the one
+// edge, count it if decided, else queue it for the FP64 re-test.
+template <int KIND>
+__device__ __noinline__ void slow_pair(const KParams &p, const WarpSmem &w, float v0, float v1,
+                                       uint32_t e0, uint32_t e1, int hid, int gj) {
+  int slot = -1;
+  int s0 = axis_refine(p, 0, v0, e0, false);
+  if (s0 == 0) return;  // certainly out of range
+  if (s0 > 0) {
+    if (KIND == KMONO || KIND == KTHETA) {
+      slot = s0;
+    } else if (KIND == KSIGPI) {
+      int s1 = axis_refine(p, 1, v1, e1, false);
+      if (s1 == 0) return;
+      if (s1 > 0) slot = s0 * p.slots1 + s1;
+    } else {
+      int s1 = mu_decide(p, v1, e1, s0, p.eps_main);
+      if (s1 > 0) slot = s0 * p.slots1 + s1;
+    }
+  }
+  if (slot > 0) {
+    atomicAdd((unsigned *)(w.hist_lane + (size_t)slot * p.R * 4), 1u);
+    return;
+  }
+  int pos = atomicAdd(w.qcnt, 1);
+  if (pos < w.qcap) w.queue[pos] = make_int2(hid, gj);
+  else atomicCAS(p.err, 0, (int)CUTE_E_DEVICE);
+}
+
+// All pairs of the HP home objects of each lane with the cnt neighbours of
+// one shared-memory tile (cnt even; rows past the slice hold sentinels).
+template <int KIND, int HP, int M0, int M1, bool SELF>
+__device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__restrict__ lut,
+                                           const PairDev &pd, const WarpSmem &w,
+                                           const float4 *__restrict__ tile, int cnt, int gj0,
+                                           const Home<HP> &h, int lane) {
+  for (int j = 0; j < cnt; j += 2) {
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      const float4 q = tile[j + u];
+      const int gj = gj0 + j + u;
+#pragma unroll
+      for (int s = 0; s < HP; s++) {
+        float dx = __fsub_rn(q.x, h.x[s]);
+        float dy = __fsub_rn(q.y, h.y[s]);
+        float dz = __fsub_rn(q.z, h.z[s]);
+        float v0, v1 = 0.0f;
+        uint32_t e0, e1 = 0, e;
+        if (KIND == KMONO || KIND == KTHETA) {
+          v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          e0 = lut_get<M0>(lut, p.ax[0], v0);
+          e = e0;
+        } else if (KIND == KSIGPI) {
+          v0 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+          v1 = __fmul_rn(dz, dz);
+          e0 = lut_get<M0>(lut, p.ax[0], v0);
+          e1 = lut_get<M1>(lut, p.ax[1], v1);
+          e = e0 + e1;
+        } else {
+          float lx = __fadd_rn(h.ax[s], dx);
+          float ly = __fadd_rn(h.ay[s], dy);
+          float lz = __fadd_rn(h.az[s], dz);
+          v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          float l2 = __fmaf_rn(lz, lz, __fmaf_rn(ly, ly, __fmul_rn(lx, lx)));
+          float sl = __fmaf_rn(dz, lz, __fmaf_rn(dy, ly, __fmul_rn(dx, lx)));
+          float den = __fmul_rn(v0, l2);
+          v1 = __fmul_rn(fabsf(sl), rsqrtf(den));
+          e0 = lut_get<M0>(lut, p.ax[0], v0);
+          e1 = lut_get<M1>(lut, p.ax[1], v1);
+          e = e0 + e1;
+        }
+        if (SELF && !(gj > h.id[s])) e = 0u;  // not a pair of this task: trash slot
+        if (e < kDirty) atomicAdd((unsigned *)(w.hist_lane + e), 1u);
+        else slow_pair<KIND>(p, w, v0, v1, e0, e1, h.id[s], gj);
+      }
+    }
+    __syncwarp();
+    if (*w.qcnt >= 32) process_queue<KIND>(p, pd, w, lane, false);
+  }
+}
+
+template <int KIND, int HP, int M0, int M1>
+__device__ __forceinline__ void tile_dispatch_self(const KParams &p, const uint32_t *lut,
+                                                   const PairDev &pd, const WarpSmem &w,
+                                                   const float4 *tile, int cnt, int gj0,
+                                                   const Home<HP> &h, int lane, bool self) {
+  if (self) tile_pairs<KIND, HP, M0, M1, true>(p, lut, pd, w, tile, cnt, gj0, h, lane);
+  else tile_pairs<KIND, HP, M0, M1, false>(p, lut, pd, w, tile, cnt, gj0, h, lane);
+}
+
+template <int KIND, int HP>
+__device__ __forceinline__ void tile_dispatch(const KParams &p, const uint32_t *lut,
+                                              const PairDev &pd, const WarpSmem &w,
+                                              const float4 *tile, int cnt, int gj0,
+                                              const Home<HP> &h, int lane, bool self) {
+  const int m0 = p.ax[0].mode;
+  if (KIND == KMONO || KIND == KTHETA) {
+    if (m0 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLinear, 0>(p, lut, pd, w, tile, cnt, gj0, h, lane, self);
+    else tile_dispatch_self<KIND, HP, kLutLog, 0>(p, lut, pd, w, tile, cnt, gj0, h, lane, self);
+  } else {
+    const int m1 = p.ax[1].mode;
+    if (m0 == kLutLinear) {
+      if (m1 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLinear, kLutLinear>(p, lut, pd, w, tile, cnt, gj0, h, lane, self);
+      else tile_dispatch_self<KIND, HP, kLutLinear, kLutLog>(p, lut, pd, w, tile, cnt, gj0, h, lane, self);
+    } else {
+      if (m1 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLog, kLutLinear>(p, lut, pd, w, tile, cnt, gj0, h, lane, self);
+      else tile_dispatch_self<KIND, HP, kLutLog, kLutLog>(p, lut, pd, w, tile, cnt, gj0, h, lane, self);
+    }
+  }
+}
+
+// 32-ary search for the task holding work item `item`: largest t with
+// prefix[t] <= item.  Warp-uniform.
+__device__ __forceinline__ int find_task(const long long *__restrict__ prefix, int ntasks,
+                                         long long item, int lane) {
+  int lo = 0, hi = ntasks;
+  while (hi - lo > 1) {
+    int step = (hi - lo + 31) >> 5;
+    int cand = lo + lane * step;
+    bool ok = (cand < hi) && (prefix[cand] <= item);
+    unsigned m = __ballot_sync(kFull, ok);
+    int last = 31 - __clz(m);
+    lo = lo + last * step;
+    hi = min(hi, lo + step);
+  }
+  return lo;
+}
+
+__device__ __forceinline__ float shift_of(int code, float L) {
+  return code == 1 ? L : (code == 2 ? -L : 0.0f);
+}
+
+template <int KIND, bool PER, int HP>
+__global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const SmemLayout L = smem_layout(p.lut_words, p.nslots, p.R, HP, false);
+  uint32_t *lut = (uint32_t *)smem;
+  for (int i = threadIdx.x; i < p.lut_words; i += blockDim.x) lut[i] = p.lut[i];
+  unsigned char *wb = smem + L.lut_bytes + (size_t)warp * L.warp_bytes;
+  WarpSmem w;
+  w.hist = (uint32_t *)wb;
+  w.hist_lane = (char *)wb + (lane & (p.R - 1)) * 4;
+  w.qcnt = (int *)(wb + L.hist_bytes);
+  w.queue = (int2 *)(wb + L.hist_bytes + 16);
+  w.qcap = L.queue_cap;
+  w.tiles = (float4 *)(wb + L.hist_bytes + L.queue_bytes);
+  for (int i = lane; i < p.nslots * p.R; i += 32) w.hist[i] = 0u;
+  if (lane == 0) *w.qcnt = 0;
+  __syncthreads();
+
+  constexpr int CH = 32 * HP;
+  int cur_pair = -1;
+  PairDev pd;
+  unsigned long long acc = 0, items = 0;
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(p.ticket, 1ull);
+    item = __shfl_sync(kFull, item, 0);
+    if ((long long)item >= p.total) break;
+    const int t = find_task(p.prefix, p.ntasks, (long long)item, lane);
+    const Task tk = p.tasks[t];
+    const long long local = (long long)item - p.prefix[t];
+    const int hc = (int)(local / tk.n_sc), sc = (int)(local - (long long)hc * tk.n_sc);
+    if (tk.pair != cur_pair) {
+      if (cur_pair >= 0) {
+        process_queue<KIND>(p, pd, w, lane, true);
+        flush_hist(p, w, pd.out, lane);
+        acc = 0;
+      }
+      cur_pair = tk.pair;
+      pd = p.pairs[cur_pair];
+    }
+    const int hs = tk.h0 + hc * CH, he = min(hs + CH, tk.h1);
+    const int js = tk.j0 + sc * p.slice, je = min(js + p.slice, tk.j1);
+    const bool self = (tk.flags & kTaskSelf) != 0;
+    if (self && je <= hs + 1) continue;  // every j precedes every i
+    // uint32 overflow guard: increments a copy can receive from this item
+    const unsigned long long bound = 2ull * (32 / p.R) * HP * (unsigned long long)(je - js);
+    if (acc + bound > 0xFFFFFFFFull) {
+      process_queue<KIND>(p, pd, w, lane, true);
+      flush_hist(p, w, pd.out, lane);
+      acc = 0;
+    }
+    acc += bound;
+    items++;
+
+    const int code = tk.flags >> 8;
+    const float Sx = PER ? shift_of(code & 3, pd.L32) : 0.0f;
+    const float Sy = PER ? shift_of((code >> 2) & 3, pd.L32) : 0.0f;
+    const float Sz = PER ? shift_of((code >> 4) & 3, pd.L32) : 0.0f;
+    Home<HP> h;
+#pragma unroll
+    for (int s = 0; s < HP; s++) {
+      const int idx = hs + lane + 32 * s;
+      if (idx < he) {
+        const float4 a = pd.posA[idx];
+        h.x[s] = __fsub_rn(a.x, Sx);
+        h.y[s] = __fsub_rn(a.y, Sy);
+        h.z[s] = __fsub_rn(a.z, Sz);
+        h.id[s] = idx;
+        if (KIND == KRMU) {
+          h.ax[s] = (float)(2.0 * pd.sA[idx]);
+          h.ay[s] = (float)(2.0 * pd.sA[(size_t)pd.nA + idx]);
+          h.az[s] = (float)(2.0 * pd.sA[2 * (size_t)pd.nA + idx]);
+        }
+      } else {
+        h.x[s] = kHomeFar; h.y[s] = kHomeFar; h.z[s] = kHomeFar;
+        h.id[s] = 0x7fffffff;
+        if (KIND == KRMU) { h.ax[s] = 2.0f * kHomeFar; h.ay[s] = 2.0f * kHomeFar; h.az[s] = 2.0f * kHomeFar; }
+      }
+    }
+
+    // stream the slice through the double-buffered tile
+    const int nj = je - js;
+    const int ntiles = (nj + kTile - 1) / kTile;
+    auto load_tile = [&](int tt) {
+      float4 *dst = w.tiles + (tt & 1) * kTile;
+      for (int e = lane; e < kTile; e += 32) {
+        const int g = js + tt * kTile + e;
+        if (g < je) cp_async16(dst + e, pd.posB + g);
+        else dst[e] = make_float4(kNbrFar, kNbrFar, kNbrFar, 0.0f);
+      }
+      cp_async_commit();
+    };
+    load_tile(0);
+    for (int tt = 0; tt < ntiles; tt++) {
+      if (tt + 1 < ntiles) {
+        load_tile(tt + 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+      int cnt = min(kTile, nj - tt * kTile);
+      cnt = (cnt + 1) & ~1;
+      tile_dispatch<KIND, HP>(p, lut, pd, w, w.tiles + (tt & 1) * kTile, cnt, js + tt * kTile, h,
+                              lane, self);
+      __syncwarp();
+    }
+  }
+  if (cur_pair >= 0) {
+    process_queue<KIND>(p, pd, w, lane, true);
+    flush_hist(p, w, pd.out, lane);
+  }
+  if (lane == 0 && items) atomicAdd(&p.stats[1], items);
+}
+
+template <int KIND, bool PER, int HP>
+cudaError_t launch_count_t(const KParams &p, int blocks, int threads, size_t smem, cudaStream_t st) {
+  auto fn = k_count<KIND, PER, HP>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fn<<<blocks, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace cute

@@ -1,0 +1,201 @@
+// count_kernel.cuh -- the pair-counting kernel (Sec. 3.1-3.2: distance, bin,
+// histogram increment for every candidate pair; Sec. 3.3: candidates from
+// neighbouring cells only).
+//
+// Design on sm_103a (one persistent CTA per SM, warps independent):
+//   * work items: (home chunk of catalog A, neighbour slice of catalog B),
+//     handed out by a global ticket; each warp holds 32 x HP home objects in
+//     registers (HP per lane) and streams the slice through a per-warp
+//     double-buffered shared-memory tile filled with cp.async (16-byte,
+//     coalesced float4 rows); every lane reads each neighbour as a
+//     broadcast and pairs it with its HP home objects;
+//   * FP32 separations; the squared separation (and mu) is looked up in a
+//     shared-memory table whose clean cells give the byte offset of the
+//     histogram slot directly;
+//   * per-warp shared-memory histograms, R copies interleaved so lane l
+//     increments copy l % R (conflict-free when R = 32), uint32 counters
+//     flushed to uint64 in HBM before they could overflow;
+//   * pairs in a dirty cell are refined against the one edge's FP32 band,
+//     and pairs inside the band go to a per-warp queue that the warp
+//     re-tests in FP64 32 at a time with the canonical formulas.
+#pragma once
+
+#include "cute_internal.h"
+
+namespace cute {
+
+constexpr int kTile = 64;          // neighbour objects per shared-memory tile
+constexpr unsigned kFull = 0xffffffffu;
+
+// FP32 sentinels for padded home slots and tile rows: far from everything
+// and from each other, so every pair involving one is out of range.
+constexpr float kHomeFar = 3.0e18f;
+constexpr float kNbrFar = -1.0e18f;
+
+struct SmemLayout {
+  int lut_bytes;      // table block (16-byte multiple)
+  int hist_bytes;     // per warp
+  int queue_cap;      // per warp entries
+  int queue_bytes;
+  int tile_bytes;     // per warp (2 tiles)
+  int warp_bytes;     // per warp total
+};
+
+__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+
+__host__ __device__ inline SmemLayout smem_layout(int lut_words, int nslots, int R, int HP,
+                                                  bool weighted) {
+  SmemLayout s;
+  s.lut_bytes = align16(lut_words * 4);
+  s.hist_bytes = align16(nslots * R * 4);
+  if (weighted) s.hist_bytes += align16(nslots * 32 * 8) + align16(nslots * 8);
+  s.queue_cap = 32 + 32 * HP * 2;  // checked every 2 neighbours
+  s.queue_bytes = 16 + align16(s.queue_cap * 8);  // 16-byte header holds the count
+  s.tile_bytes = 2 * kTile * 16;
+  s.warp_bytes = s.hist_bytes + s.queue_bytes + s.tile_bytes;
+  return s;
+}
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// table lookup; MODE fixed per instantiation of the inner loop
+template <int MODE>
+__device__ __forceinline__ uint32_t lut_get(const uint32_t *lut, const AxisPlan &a, float v) {
+  v = fminf(v, a.vmax);  // also maps NaN to vmax
+  unsigned idx;
+  if (MODE == kLutLinear) {
+    float t = __fmaf_rn(v, a.scale, 8388608.0f);
+    idx = __float_as_uint(t) - 0x4B000000u;
+  } else {
+    int i = (int)(__float_as_uint(v) >> a.shift) - a.base;
+    idx = (unsigned)max(i, 0);
+  }
+  return lut[a.lut_off + idx];
+}
+
+// ---- canonical FP64 formulas (identical arithmetic to the definition; no
+// contraction: every operation is an explicitly rounded intrinsic)
+__device__ __forceinline__ double wrap64(double d, double L, double halfL) {
+  if (L > 0.0) {
+    if (d > halfL) d = __dsub_rn(d, L);
+    else if (d < -halfL) d = __dadd_rn(d, L);
+  }
+  return d;
+}
+// bin b with E[b] <= v < E[b+1]; -1 outside
+__device__ __forceinline__ int bin64(const double *E, int n, double v) {
+  if (!(v >= E[0]) || !(v < E[n])) return -1;
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (v >= E[mid]) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+// largest k in [0, n-1] with q >= M[k] * den
+__device__ __forceinline__ int mubin64(const double *M, int n, double q, double den) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (q >= __dmul_rn(M[mid], den)) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// flat histogram slot of pair (i of A, j of B) from the FP64 coordinates;
+// 0 (trash) when out of range
+template <int KIND>
+__device__ int slot64(const KParams &p, const PairDev &pd, int i, int j) {
+  const double *A = pd.sA, *B = pd.sB;
+  double ax = A[i], ay = A[(size_t)pd.nA + i], az = A[2 * (size_t)pd.nA + i];
+  double bx = B[j], by = B[(size_t)pd.nB + j], bz = B[2 * (size_t)pd.nB + j];
+  const double L = pd.L64, hL = 0.5 * pd.L64;
+  if (KIND == KMONO || KIND == KTHETA) {
+    double dx = wrap64(__dsub_rn(bx, ax), L, hL), dy = wrap64(__dsub_rn(by, ay), L, hL),
+           dz = wrap64(__dsub_rn(bz, az), L, hL);
+    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    int b = bin64(p.E0, p.n0, d2);
+    return b < 0 ? 0 : b + 1;
+  } else if (KIND == KSIGPI) {
+    double dx = wrap64(__dsub_rn(bx, ax), L, hL), dy = wrap64(__dsub_rn(by, ay), L, hL),
+           dz = wrap64(__dsub_rn(bz, az), L, hL);
+    double s2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    double p2 = __dmul_rn(dz, dz);
+    int bs = bin64(p.E0, p.n0, s2);
+    if (bs < 0) return 0;
+    int bp = bin64(p.E1, p.n1, p2);
+    if (bp < 0) return 0;
+    return (bs + 1) * p.slots1 + bp + 1;
+  } else {  // KRMU, midpoint line of sight, open
+    double sx = __dsub_rn(bx, ax), sy = __dsub_rn(by, ay), sz = __dsub_rn(bz, az);
+    double lx = __dadd_rn(ax, bx), ly = __dadd_rn(ay, by), lz = __dadd_rn(az, bz);
+    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz));
+    int br = bin64(p.E0, p.n0, r2);
+    if (br < 0) return 0;
+    int bm = 0;
+    if (r2 != 0.0) {
+      double l2 = __dadd_rn(__dadd_rn(__dmul_rn(lx, lx), __dmul_rn(ly, ly)), __dmul_rn(lz, lz));
+      double sl = __dadd_rn(__dadd_rn(__dmul_rn(sx, lx), __dmul_rn(sy, ly)), __dmul_rn(sz, lz));
+      double q = __dmul_rn(sl, sl);
+      double den = __dmul_rn(r2, l2);
+      bm = mubin64(p.E1, p.n1, q, den);
+    }
+    return (br + 1) * p.slots1 + bm + 1;
+  }
+}
+
+// ---- refine a dirty entry on one axis: slot >= 0, or -1 for the FP64 re-test
+__device__ __forceinline__ int axis_refine(const KParams &p, int axis, float v, uint32_t e,
+                                           bool mu) {
+  const AxisPlan &a = p.ax[axis];
+  const uint32_t stride = (axis == 0) ? (uint32_t)p.slots1 * p.R * 4u : (uint32_t)p.R * 4u;
+  if (e < kDirty) return (int)(e / stride);
+  if (e & kAlways) return -1;
+  int k = (int)((e >> 8) & 0xFFFFu);
+  if (e & 0x2u) return k;  // r slot decided, mu to be decided explicitly
+  float lo = p.band[a.band_off + 2 * k], hi = p.band[a.band_off + 2 * k + 1];
+  int cnt;
+  if (v < lo) cnt = k;
+  else if (v > hi) cnt = k + 1;
+  else return -1;
+  if (mu) return cnt;
+  return (cnt >= 1 && cnt <= a.nb) ? cnt : 0;
+}
+
+// mu slot for r slot s0 (R_MU); -1 for the FP64 re-test
+__device__ __forceinline__ int mu_decide(const KParams &p, float mu, uint32_t e1, int s0,
+                                         float eps_main) {
+  float eps = p.mu_eps[s0];
+  if (eps >= 4.0f) return -1;
+  const int n1 = p.n1;
+  int b;  // candidate bin from the table
+  if (e1 < kDirty) {
+    b = (int)(e1 / ((uint32_t)p.R * 4u)) - 1;
+    if (eps <= eps_main) return b + 1;  // the table was built for this bound
+  } else {
+    if (e1 & kAlways) return -1;
+    int k = (int)((e1 >> 8) & 0xFFFFu);
+    b = (mu < p.mu_edge[k]) ? k - 1 : k;
+  }
+  // the decision edges next to bin b must be clear of mu by eps
+  if (b >= 1) {
+    float m = p.mu_edge[b];
+    if (mu >= __fsub_rd(m, eps) && mu <= __fadd_ru(m, eps)) return -1;
+  }
+  if (b + 1 <= n1 - 1) {
+    float m = p.mu_edge[b + 1];
+    if (mu >= __fsub_rd(m, eps) && mu <= __fadd_ru(m, eps)) return -1;
+  }
+  return b + 1;
+}
+
+}  // namespace cute

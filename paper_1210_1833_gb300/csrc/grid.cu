@@ -1,0 +1,363 @@
+// grid.cu -- catalog staging and the counting-sort cell grid (Sec. 3.3).
+//
+// A catalog is kept twice on the device: FP64 in upload order (the
+// canonical coordinates the FP64 re-test reads) and, once a grid is built,
+// cell-sorted as FP32 (x, y, z, w) float4 offsets from the grid centre plus
+// a cell-sorted FP64 SoA copy.  The grid is a counting sort: cell id and
+// rank within the cell per object (one atomic per object), an exclusive
+// scan over cells, and a scatter.
+#include "cute_internal.h"
+
+#include <cfloat>
+
+namespace cute {
+
+// ------------------------------------------------------------------ staging stats
+// Per-block partial reductions of a catalog: min/max per axis, max |x| per
+// axis, min |x|^2 (observer at the origin), and the number of coordinates
+// outside [0, L) (periodic) or not finite.
+struct StageStats {
+  double lo[3], hi[3], amax[3], r2min;
+  unsigned long long bad;
+  double pad;
+};
+
+__global__ void k_stage_stats(const double *__restrict__ xyz, long long n, int periodic, double L,
+                              StageStats *__restrict__ out) {
+  __shared__ double s_lo[3][256], s_hi[3][256], s_am[3][256], s_r2[256];
+  __shared__ unsigned long long s_bad[256];
+  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  double am[3] = {0, 0, 0}, r2m = DBL_MAX;
+  unsigned long long bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double r2 = 0;
+    for (int k = 0; k < 3; k++) {
+      double x = xyz[3 * i + k];
+      if (!(x == x) || x > DBL_MAX || x < -DBL_MAX) bad++;
+      if (periodic && !(x >= 0.0 && x < L)) bad++;
+      lo[k] = fmin(lo[k], x);
+      hi[k] = fmax(hi[k], x);
+      am[k] = fmax(am[k], fabs(x));
+      r2 += x * x;
+    }
+    r2m = fmin(r2m, r2);
+  }
+  int t = threadIdx.x;
+  for (int k = 0; k < 3; k++) { s_lo[k][t] = lo[k]; s_hi[k][t] = hi[k]; s_am[k][t] = am[k]; }
+  s_r2[t] = r2m;
+  s_bad[t] = bad;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (t < s) {
+      for (int k = 0; k < 3; k++) {
+        s_lo[k][t] = fmin(s_lo[k][t], s_lo[k][t + s]);
+        s_hi[k][t] = fmax(s_hi[k][t], s_hi[k][t + s]);
+        s_am[k][t] = fmax(s_am[k][t], s_am[k][t + s]);
+      }
+      s_r2[t] = fmin(s_r2[t], s_r2[t + s]);
+      s_bad[t] += s_bad[t + s];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    StageStats st;
+    for (int k = 0; k < 3; k++) { st.lo[k] = s_lo[k][0]; st.hi[k] = s_hi[k][0]; st.amax[k] = s_am[k][0]; }
+    st.r2min = s_r2[0];
+    st.bad = s_bad[0];
+    st.pad = 0;
+    out[blockIdx.x] = st;
+  }
+}
+
+// ------------------------------------------------------------------ grid kernels
+struct GridDev {
+  double lo[3];     // cell origin of the geometry
+  double a[3];      // cell sides
+  int nc[3];
+  double fo[3];     // FP32 frame origin (geometry centre)
+};
+
+__device__ __forceinline__ int cell_axis(double x, double lo, double a, int n) {
+  double f = floor((x - lo) / a);
+  int c = (f < 0.0) ? 0 : (f >= (double)n ? n - 1 : (int)f);
+  return c;
+}
+
+__global__ void k_cell_assign(const double *__restrict__ xyz, int n, GridDev g,
+                              int *__restrict__ cid, int *__restrict__ rank,
+                              int *__restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int cx = cell_axis(xyz[3 * i], g.lo[0], g.a[0], g.nc[0]);
+  int cy = cell_axis(xyz[3 * i + 1], g.lo[1], g.a[1], g.nc[1]);
+  int cz = cell_axis(xyz[3 * i + 2], g.lo[2], g.a[2], g.nc[2]);
+  int c = (cz * g.nc[1] + cy) * g.nc[0] + cx;
+  cid[i] = c;
+  rank[i] = atomicAdd(&cnt[c], 1);
+}
+
+// Exclusive scan of cnt[0..m) into start[0..m]; one block walks the array in
+// chunks of blockDim, carrying the running total.
+__global__ void k_scan(const int *__restrict__ cnt, int m, int *__restrict__ start) {
+  __shared__ int s[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < m; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    int v = (i < m) ? cnt[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+      int t = (threadIdx.x >= (unsigned)off) ? s[threadIdx.x - off] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < m) start[i] = carry + s[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += s[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) start[m] = carry;
+}
+
+__global__ void k_scatter(const double *__restrict__ xyz, const float *__restrict__ w, int n,
+                          GridDev g, const int *__restrict__ cid, const int *__restrict__ rank,
+                          const int *__restrict__ start, float4 *__restrict__ pos,
+                          double *__restrict__ s64, int *__restrict__ perm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int d = start[cid[i]] + rank[i];
+  double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+  float4 p;
+  p.x = (float)(x - g.fo[0]);
+  p.y = (float)(y - g.fo[1]);
+  p.z = (float)(z - g.fo[2]);
+  p.w = w ? w[i] : 1.0f;
+  pos[d] = p;
+  s64[d] = x;
+  s64[(size_t)n + d] = y;
+  s64[2 * (size_t)n + d] = z;
+  perm[d] = i;
+}
+
+// ------------------------------------------------------------------ host side
+static cute_status fail(cute_ctx *ctx, cute_status st, const std::string &m) {
+  ctx->err = m;
+  return st;
+}
+
+#define CUDA_OR_FAIL(call)                                                         \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? CUTE_E_OOM : CUTE_E_CUDA, \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));             \
+  } while (0)
+
+cute_status ensure_scratch(cute_ctx *ctx, size_t bytes) {
+  if (ctx->scratch_bytes >= bytes) return CUTE_OK;
+  if (ctx->d_scratch) {
+    CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->d_scratch);
+    ctx->d_scratch = nullptr;
+    ctx->scratch_bytes = 0;
+  }
+  size_t want = bytes + bytes / 4;
+  CUDA_OR_FAIL(cudaMalloc(&ctx->d_scratch, want));
+  ctx->scratch_bytes = want;
+  return CUTE_OK;
+}
+
+cute_status catalog_stage(cute_ctx *ctx, Catalog &c, const double *xyz, const float *w) {
+  const long long n = c.n;
+  if (n > 0) {
+    CUDA_OR_FAIL(cudaMalloc(&c.d_xyz, sizeof(double) * 3 * (size_t)n));
+    CUDA_OR_FAIL(cudaMemcpyAsync(c.d_xyz, xyz, sizeof(double) * 3 * (size_t)n, cudaMemcpyDefault,
+                                 ctx->stream));
+    if (w) {
+      CUDA_OR_FAIL(cudaMalloc(&c.d_w, sizeof(float) * (size_t)n));
+      CUDA_OR_FAIL(cudaMemcpyAsync(c.d_w, w, sizeof(float) * (size_t)n, cudaMemcpyDefault,
+                                   ctx->stream));
+    }
+  }
+  // statistics and validation
+  int blocks = 1;
+  if (n > 0) blocks = (int)std::min<long long>((n + 255) / 256, 4LL * ctx->sm_count);
+  cute_status st = ensure_scratch(ctx, sizeof(StageStats) * blocks);
+  if (st != CUTE_OK) return st;
+  std::vector<StageStats> part(blocks);
+  if (n > 0) {
+    k_stage_stats<<<blocks, 256, 0, ctx->stream>>>(c.d_xyz, n, c.boundary == CUTE_PERIODIC, c.L,
+                                                   (StageStats *)ctx->d_scratch);
+    CUDA_OR_FAIL(cudaGetLastError());
+    CUDA_OR_FAIL(cudaMemcpyAsync(part.data(), ctx->d_scratch, sizeof(StageStats) * blocks,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+  unsigned long long bad = 0;
+  double r2min = DBL_MAX;
+  for (int k = 0; k < 3; k++) { c.lo[k] = DBL_MAX; c.hi[k] = -DBL_MAX; c.absmax[k] = 0; }
+  if (n > 0) {
+    for (auto &p : part) {
+      for (int k = 0; k < 3; k++) {
+        c.lo[k] = std::min(c.lo[k], p.lo[k]);
+        c.hi[k] = std::max(c.hi[k], p.hi[k]);
+        c.absmax[k] = std::max(c.absmax[k], p.amax[k]);
+      }
+      r2min = std::min(r2min, p.r2min);
+      bad += p.bad;
+    }
+  } else {
+    for (int k = 0; k < 3; k++) { c.lo[k] = 0; c.hi[k] = 0; }
+    r2min = 0;
+  }
+  c.rmin = std::sqrt(r2min);
+  if (bad) {
+    return fail(ctx, CUTE_E_INVALID,
+                c.boundary == CUTE_PERIODIC
+                    ? "catalog has coordinates outside [0, box_L) or not finite"
+                    : "catalog has coordinates that are not finite");
+  }
+  return CUTE_OK;
+}
+
+static void free_grid(Catalog &c) {
+  cudaFree(c.d_pos); c.d_pos = nullptr;
+  cudaFree(c.d_s64); c.d_s64 = nullptr;
+  cudaFree(c.d_perm); c.d_perm = nullptr;
+  cudaFree(c.d_cell_start); c.d_cell_start = nullptr;
+  c.h_cell_start.clear();
+  c.geom = -1;
+}
+
+void catalog_release(Catalog &c) {
+  free_grid(c);
+  cudaFree(c.d_xyz); c.d_xyz = nullptr;
+  cudaFree(c.d_w); c.d_w = nullptr;
+}
+
+cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const double reach[3],
+                       int kreq) {
+  const Catalog &c0 = *cats[0];
+  Geometry g;
+  g.periodic = (c0.boundary == CUTE_PERIODIC);
+  g.L = c0.L;
+  for (int k = 0; k < 3; k++) g.reach[k] = reach[k];
+  double lo[3], hi[3];
+  for (int k = 0; k < 3; k++) {
+    lo[k] = DBL_MAX; hi[k] = -DBL_MAX; g.absmax[k] = 0;
+  }
+  g.rmin = DBL_MAX;
+  bool any = false;
+  for (Catalog *c : cats) {
+    if (c->n == 0) continue;
+    any = true;
+    for (int k = 0; k < 3; k++) {
+      lo[k] = std::min(lo[k], c->lo[k]);
+      hi[k] = std::max(hi[k], c->hi[k]);
+      g.absmax[k] = std::max(g.absmax[k], c->absmax[k]);
+    }
+    g.rmin = std::min(g.rmin, c->rmin);
+  }
+  if (!any) {
+    for (int k = 0; k < 3; k++) { lo[k] = 0; hi[k] = 1; }
+    g.rmin = 0;
+  }
+  for (int k = 0; k < 3; k++) {
+    // cells no smaller than reach/k (with a relative margin that absorbs the
+    // rounding of the cell assignment), so objects more than k cells apart
+    // on an axis are farther apart than the reach on that axis
+    double amin = reach[k] * (1.0 + 1e-9) / kreq + 1e-300;
+    int kk = kreq;
+    if (g.periodic) {
+      double L = g.L;
+      long long n = (long long)std::floor(L / amin);
+      // the (2k+1)-cell stencil must not wrap onto itself: raise k if needed
+      while (n < 2 * kk + 1 && kk < 16) {
+        kk++;
+        amin = reach[k] * (1.0 + 1e-9) / kk + 1e-300;
+        n = (long long)std::floor(L / amin);
+      }
+      if (n < 2 * kk + 1)
+        return fail(ctx, CUTE_E_UNSUPPORTED, "periodic reach too large for the box (needs reach <= 0.47 L)");
+      n = std::min<long long>(n, 1024);
+      g.nc[k] = (int)n;
+      g.a[k] = L / (double)n;
+      // a stencil of kk cells must still cover the reach after capping n
+      kk = (int)std::ceil(reach[k] * (1.0 + 1e-9) / g.a[k]);
+      if (kk < 1) kk = 1;
+      if (2 * kk + 1 > g.nc[k])
+        return fail(ctx, CUTE_E_UNSUPPORTED, "periodic reach too large for the box (needs reach <= 0.47 L)");
+      g.k[k] = kk;
+      g.origin[k] = 0.0;
+      g.xmax[k] = 0.5 * L;   // FP32 frame centred on the box
+    } else {
+      double ext = hi[k] - lo[k];
+      long long n = (long long)std::floor(ext / amin) + 1;
+      n = std::max<long long>(1, std::min<long long>(n, 1024));
+      double a = std::max(amin, ext / (double)n * (1.0 + 1e-12));
+      g.nc[k] = (int)n;
+      g.a[k] = a;
+      g.k[k] = (int)std::max<double>(1.0, std::ceil(reach[k] * (1.0 + 1e-9) / a));
+      g.origin[k] = lo[k];
+      g.xmax[k] = 0.5 * ext * (1.0 + 1e-12) + 1e-300;
+    }
+  }
+  long long ncell = (long long)g.nc[0] * g.nc[1] * g.nc[2];
+  if (ncell > (1LL << 28)) return fail(ctx, CUTE_E_UNSUPPORTED, "too many cells");
+  g.id = ctx->next_geom++;
+  g.version = ++ctx->version_counter;
+
+  GridDev gd;
+  for (int k = 0; k < 3; k++) {
+    gd.lo[k] = g.origin[k];
+    gd.a[k] = g.a[k];
+    gd.nc[k] = g.nc[k];
+    gd.fo[k] = g.periodic ? 0.5 * g.L : 0.5 * (lo[k] + hi[k]);
+    if (!any) gd.fo[k] = 0;
+  }
+  // the FP32 frame spans at most xmax from its centre on each axis
+  for (Catalog *c : cats) {
+    free_grid(*c);
+    const int n = (int)c->n;
+    CUDA_OR_FAIL(cudaMalloc(&c->d_cell_start, sizeof(int) * (size_t)(ncell + 1)));
+    if (n > 0) {
+      CUDA_OR_FAIL(cudaMalloc(&c->d_pos, sizeof(float4) * (size_t)n));
+      CUDA_OR_FAIL(cudaMalloc(&c->d_s64, sizeof(double) * 3 * (size_t)n));
+      CUDA_OR_FAIL(cudaMalloc(&c->d_perm, sizeof(int) * (size_t)n));
+    }
+    size_t need = sizeof(int) * ((size_t)2 * n + (size_t)ncell) + 256;
+    cute_status st = ensure_scratch(ctx, need);
+    if (st != CUTE_OK) return st;
+    int *cid = (int *)ctx->d_scratch;
+    int *rank = cid + n;
+    int *cnt = rank + n;
+    CUDA_OR_FAIL(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)ncell, ctx->stream));
+    if (n > 0) {
+      k_cell_assign<<<(n + 255) / 256, 256, 0, ctx->stream>>>(c->d_xyz, n, gd, cid, rank, cnt);
+      CUDA_OR_FAIL(cudaGetLastError());
+    }
+    k_scan<<<1, 1024, 0, ctx->stream>>>(cnt, (int)ncell, c->d_cell_start);
+    CUDA_OR_FAIL(cudaGetLastError());
+    if (n > 0) {
+      k_scatter<<<(n + 255) / 256, 256, 0, ctx->stream>>>(c->d_xyz, c->d_w, n, gd, cid, rank,
+                                                          c->d_cell_start, c->d_pos, c->d_s64,
+                                                          c->d_perm);
+      CUDA_OR_FAIL(cudaGetLastError());
+    }
+    c->h_cell_start.resize(ncell + 1);
+    CUDA_OR_FAIL(cudaMemcpyAsync(c->h_cell_start.data(), c->d_cell_start,
+                                 sizeof(int) * (size_t)(ncell + 1), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+    c->geom = g.id;
+    c->grid_version = g.version;
+  }
+  ctx->geoms[g.id] = g;
+  return CUTE_OK;
+}
+
+}  // namespace cute

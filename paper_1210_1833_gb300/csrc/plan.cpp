@@ -1,0 +1,496 @@
+// plan.cpp -- host planning for the counting kernels: per-axis lookup tables
+// with proven FP32 error bands, and the task list of a pair set.
+//
+// Binning (Sec. 3.1: "determining the bin corresponding to that distance").
+// The kernels compute each separation in FP32 and look its squared value up
+// in a table.  A table cell is CLEAN when every FP32 value it holds, widened
+// by the error bound err(v) of the FP32 computation, lies strictly between
+// the same two bin edges, so the FP32 result bins the pair exactly as the
+// FP64 canonical formula does.  Other cells are DIRTY and name the single
+// edge whose band meets them; pairs that land within that band are re-tested
+// in FP64.  Both the table geometry (linear or logarithmic in v) and its size
+// are chosen here by the expected fraction of pairs landing in dirty cells.
+//
+// Neighbour search (Sec. 3.3): the task list walks the cells of catalog A in
+// row order; each row-run of home cells is paired with the rows of
+// neighbour cells in the cube of 2k+1 cells per side around it.  Within a
+// row the neighbour cells are contiguous in the cell-sorted order, so each
+// (home run, neighbour row) is one contiguous slice of catalog B.
+#include "cute_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace cute {
+
+static const double kU = 5.9604644775390625e-08;  // 2^-24, FP32 unit roundoff
+
+static float f32_down(double x) {
+  float f = (float)x;
+  if ((double)f > x) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+static float f32_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = std::nextafter(f, INFINITY);
+  return f;
+}
+static uint32_t fbits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return u;
+}
+static float bitsf(uint32_t u) {
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+Plan::~Plan() {
+  cudaFree(d_lut);
+  cudaFree(d_band);
+  cudaFree(d_mu_eps);
+  cudaFree(d_mu_edge);
+  cudaFree(d_E0);
+  cudaFree(d_E1);
+}
+
+// ------------------------------------------------------------------ error models
+// Error of an FP32 sum of c squared components whose components carry an
+// absolute error of at most eta0 + u|delta|, relative to the FP64 canonical
+// value of the same quantity.  Derivation: |d32^2 - d^2| <= eta(2|d| + eta)
+// per component, sum |d_k| <= sqrt(c v); the c FP32 roundings of the sum of
+// squares add at most (c+1) u v; the FP64 canonical value differs from the
+// exact one by less than 4e-16 v.  The result is doubled as a safety margin.
+struct SqErr {
+  int c;
+  double eta0;
+  double operator()(double v) const {
+    v = std::max(v, 0.0);
+    double sv = std::sqrt(v);
+    double eta = eta0 + kU * sv * 1.0001;
+    double e = eta * (2.0 * std::sqrt((double)c) * sv + c * eta) + (c + 1) * kU * v * 1.01 +
+               4e-16 * v;
+    return 2.0 * e + 1e-300;
+  }
+};
+
+// A generic error model: err(v) for v-type axes, constant for mu.
+struct AxisErr {
+  bool constant = false;
+  double cst = 0;
+  SqErr sq{3, 0};
+  double operator()(double v) const { return constant ? cst : sq(v); }
+};
+
+// ------------------------------------------------------------------ one axis table
+struct AxisSpec {
+  std::vector<double> E;     // edges in the looked-up quantity (squared, or mu)
+  std::vector<int> decision; // indices k of E that are decision boundaries
+  int nb = 0;                // bins
+  AxisErr err;
+  double density_p = 0;      // density model v^p for choosing the table
+  double vtop = 0;           // largest value that can be in range
+  bool mu = false;           // mu axis: no out-of-range slot
+};
+
+struct AxisTable {
+  AxisPlan p;
+  std::vector<uint32_t> cells;       // entries (offset units filled in later)
+  std::vector<int> slot;             // slot of clean cells (-1 dirty)
+  std::vector<int> edge;             // edge of dirty cells (-1 none, -2 always)
+  std::vector<double> cell_hi;       // upper value of each cell
+  double dirty_frac = 1.0;
+};
+
+// value interval [lo, hi] of table cell c
+static void cell_range(const AxisPlan &p, int c, double &lo, double &hi) {
+  if (p.mode == kLutLinear) {
+    double s = (double)p.scale;
+    lo = (c == 0) ? 0.0 : (c - 0.5) / s;
+    hi = (c == p.ncell - 1) ? INFINITY : (c + 0.5) / s;
+    lo = (c == 0) ? 0.0 : lo * (1 - 1e-12);
+    hi = hi * (1 + 1e-12);
+  } else {
+    if (c == 0) lo = 0.0;
+    else lo = bitsf((uint32_t)(c + p.base) << p.shift);
+    if (c == p.ncell - 1) hi = INFINITY;
+    else hi = bitsf((((uint32_t)(c + p.base + 1)) << p.shift) - 1u);
+  }
+}
+
+// slot of a value known to lie in [lo, hi] with no decision edge inside
+static int slot_of(const AxisSpec &a, double v) {
+  if (a.mu) {
+    int s = 1;
+    for (int k : a.decision)
+      if (a.E[k] <= v) s++;
+    return s;  // 1 .. nb
+  }
+  int cnt = 0;
+  for (size_t k = 0; k < a.E.size(); k++)
+    if (a.E[k] <= v) cnt++;
+  return (cnt >= 1 && cnt <= a.nb) ? cnt : 0;
+}
+
+static double dens_int(double p, double a, double b) {
+  // integral of v^p over [a, b], p > -1
+  a = std::max(a, 0.0);
+  if (!(b > a)) return 0.0;
+  return (std::pow(b, p + 1) - std::pow(a, p + 1)) / (p + 1);
+}
+
+static void classify(const AxisSpec &a, AxisTable &t) {
+  const AxisPlan &p = t.p;
+  t.cells.assign(p.ncell, 0);
+  t.slot.assign(p.ncell, -1);
+  t.edge.assign(p.ncell, -1);
+  t.cell_hi.assign(p.ncell, 0);
+  double tot = dens_int(a.density_p, 0.0, a.vtop), dirty = 0;
+  for (int c = 0; c < p.ncell; c++) {
+    double lo, hi;
+    cell_range(p, c, lo, hi);
+    t.cell_hi[c] = hi;
+    double tlo = lo - a.err(lo);
+    double thi = std::isinf(hi) ? INFINITY : hi + a.err(hi);
+    int found = -1, nfound = 0;
+    for (int k : a.decision) {
+      if (a.E[k] >= tlo && a.E[k] <= thi) {
+        found = k;
+        nfound++;
+      }
+    }
+    if (nfound == 0) {
+      t.slot[c] = slot_of(a, lo);
+    } else {
+      t.edge[c] = (nfound == 1) ? found : -2;
+      double dhi = std::isinf(hi) ? a.vtop : std::min(hi, a.vtop);
+      dirty += dens_int(a.density_p, lo, dhi);
+    }
+  }
+  t.dirty_frac = tot > 0 ? dirty / tot : 1.0;
+}
+
+static bool make_linear(const AxisSpec &a, int ncell, AxisTable &t) {
+  // cover [0, vmax] with ncell cells; vmax above the top decision band
+  double top = a.vtop + a.err(a.vtop);
+  double vmax = top * (1.0 + 4.0 / ncell) + 1e-30;
+  float vmaxf = f32_up(vmax);
+  float scale = f32_down((double)(ncell - 1) / (double)vmaxf);
+  // the largest index must stay inside the table: rne(vmax*scale) <= ncell-1
+  while (std::nearbyint((double)vmaxf * (double)scale) > ncell - 1)
+    scale = std::nextafter(scale, 0.0f);
+  if (!(scale > 0) || (double)vmaxf * scale >= 4194304.0) return false;
+  // the table ends at the cell that holds vmax (and every clamped value)
+  ncell = (int)std::nearbyint((double)vmaxf * (double)scale) + 1;
+  t.p = AxisPlan();
+  t.p.mode = kLutLinear;
+  t.p.ncell = ncell;
+  t.p.vmax = vmaxf;
+  t.p.scale = scale;
+  classify(a, t);
+  return true;
+}
+
+static bool make_log(const AxisSpec &a, int budget, int m, AxisTable &t) {
+  // first positive decision edge
+  double first = INFINITY;
+  for (int k : a.decision)
+    if (a.E[k] > 0) first = std::min(first, a.E[k]);
+  if (!std::isfinite(first)) return false;
+  double low = (first - a.err(first)) * 0.5;
+  if (!(low > 1e-37)) return false;
+  double top = a.vtop + a.err(a.vtop);
+  float vmaxf = f32_up(top * 1.05 + 1e-30);
+  int shift = 23 - m;
+  int base = (int)(fbits(f32_down(low)) >> shift);
+  int ncell = (int)(fbits(vmaxf) >> shift) - base + 1;
+  if (ncell < 2 || ncell > budget) return false;
+  t.p = AxisPlan();
+  t.p.mode = kLutLog;
+  t.p.ncell = ncell;
+  t.p.vmax = vmaxf;
+  t.p.shift = shift;
+  t.p.base = base;
+  classify(a, t);
+  return true;
+}
+
+static AxisTable best_table(const AxisSpec &a, int budget) {
+  AxisTable best, cur;
+  best.dirty_frac = 2.0;
+  if (make_linear(a, budget, cur) && cur.dirty_frac < best.dirty_frac) best = cur;
+  for (int m = 12; m >= 3; m--) {
+    if (make_log(a, budget, m, cur)) {
+      if (cur.dirty_frac < best.dirty_frac) best = cur;
+      break;  // the largest m that fits is the finest log table
+    }
+  }
+  return best;
+}
+
+// Band (lo, hi) of decision edge k: a value v32 < lo is certainly below the
+// edge, v32 > hi certainly above.  lo + err(lo) < E and hi - err(hi) > E.
+static void edge_band(const AxisSpec &a, int k, double &lo, double &hi) {
+  double E = a.E[k];
+  double e = a.err(E);
+  lo = E - 1.0001 * e;
+  hi = E + 1.0001 * e;
+  for (int it = 0; it < 64 && hi - a.err(hi) <= E; it++) hi = E + 1.01 * a.err(hi) + 1e-300;
+  for (int it = 0; it < 64 && lo + a.err(E) >= E; it++) lo = E - 1.01 * (E - lo) - 1e-300;
+}
+
+// ------------------------------------------------------------------ plan
+std::string plan_build(int kind, const double *e0, int n0, const double *e1, int n1,
+                       const ErrorParams &ep, int lut_budget_words, size_t hist_budget_bytes,
+                       Plan &out) {
+  const bool two_d = (kind == KRMU || kind == KSIGPI);
+  out.kind = kind;
+  out.n0 = n0;
+  out.n1 = two_d ? n1 : 1;
+  out.slots1 = two_d ? n1 + 1 : 1;
+  out.nslots = (n0 + 1) * out.slots1;
+  // copies of the per-warp histogram: as many (<= 32, power of 2) as fit
+  int R = 32;
+  while (R > 1 && (size_t)out.nslots * R * 4 > hist_budget_bytes) R >>= 1;
+  if ((size_t)out.nslots * 4 > hist_budget_bytes) return "too many bins for the shared-memory histogram";
+  out.R = R;
+
+  out.E0.resize(n0 + 1);
+  for (int k = 0; k <= n0; k++) out.E0[k] = e0[k] * e0[k];
+  if (two_d) {
+    out.E1.resize(n1 + 1);
+    for (int k = 0; k <= n1; k++) out.E1[k] = e1[k] * e1[k];
+  } else {
+    out.E1.assign(2, 0.0);
+  }
+
+  // axis specifications
+  AxisSpec A0, A1;
+  A0.E = out.E0;
+  A0.nb = n0;
+  for (int k = 0; k <= n0; k++)
+    if (A0.E[k] > 0) A0.decision.push_back(k);
+  A0.vtop = A0.E[n0];
+  A0.err.constant = false;
+  if (kind == KSIGPI) {
+    A0.err.sq = SqErr{2, ep.eta0};
+    A0.density_p = 0.0;  // sigma^2 of pairs spread in a plane: flat
+    A1.E = out.E1;
+    A1.nb = n1;
+    for (int k = 0; k <= n1; k++)
+      if (A1.E[k] > 0) A1.decision.push_back(k);
+    A1.vtop = A1.E[n1];
+    A1.err.sq = SqErr{1, ep.eta0};
+    A1.density_p = -0.5;  // pi^2 of pairs spread along a line
+  } else {
+    A0.err.sq = SqErr{3, ep.eta0};
+    A0.density_p = 0.5;   // d^2 of pairs spread in a volume
+    if (kind == KTHETA) A0.density_p = 0.0;  // chord^2 of pairs on a sphere
+  }
+
+  // mu: FP32 mu = |s.l| * rsqrt((s.s)(l.l)).  |d mu| <= 2 sqrt3 (eta_s/r +
+  // eta_l/|l|) from the perturbed unit vectors, plus 20 u of FP32 rounding
+  // (dot products, product, rsqrtf's documented 2 ulp, final product), plus
+  // the FP32 rounding of the edge and the FP64 canonical rounding; doubled.
+  std::vector<double> eps_slot;  // per r slot (n0 + 1), slot 0 unused
+  double eps_main = 0;
+  std::vector<int> always_slot;
+  if (kind == KRMU) {
+    double minw = 1.0;
+    for (int k = 0; k < n1; k++) minw = std::min(minw, e1[k + 1] - e1[k]);
+    eps_slot.assign(n0 + 1, 0.0);
+    always_slot.assign(n0 + 1, 0);
+    double lterm = (ep.lmin > 0) ? ep.eta_l / ep.lmin : INFINITY;
+    for (int b = 0; b < n0; b++) {
+      double r = e0[b];
+      double e = (r > 0) ? 2.0 * (2.0 * std::sqrt(3.0) * ((ep.eta0 + kU * r) / r + lterm) + 20 * kU) +
+                               kU + 1e-12
+                         : INFINITY;
+      eps_slot[b + 1] = e;
+      if (!(e < 0.25 * minw)) always_slot[b + 1] = 1;
+    }
+    // the table is built for the bound of the slots holding most pairs
+    // (r >= max(first edge, 0.2 r_max)); smaller-r slots refine mu explicitly
+    double rsplit = std::max(e0[1], 0.2 * e0[n0]);
+    for (int b = 0; b < n0; b++)
+      if (e0[b] >= rsplit && !always_slot[b + 1]) eps_main = std::max(eps_main, eps_slot[b + 1]);
+    if (eps_main == 0) eps_main = 1e-7;
+    // one FP32 value serves the table, the host flags and the kernel test
+    out.eps_main = f32_up(eps_main);
+    eps_main = (double)out.eps_main;
+    A1.mu = true;
+    A1.E.assign(e1, e1 + n1 + 1);
+    A1.nb = n1;
+    for (int k = 1; k < n1; k++) A1.decision.push_back(k);
+    A1.vtop = 1.0;
+    A1.err.constant = true;
+    A1.err.cst = eps_main;
+    A1.density_p = 0.0;
+    out.mu_eps.assign(n0 + 1, 0.0f);
+    for (int s = 1; s <= n0; s++)
+      out.mu_eps[s] = std::isfinite(eps_slot[s]) ? f32_up(eps_slot[s]) : 4.0f;
+    out.mu_edge.resize(n1 + 1);
+    for (int k = 0; k <= n1; k++) out.mu_edge[k] = (float)e1[k];
+  } else {
+    out.mu_eps.assign(1, 0.0f);
+    out.mu_edge.assign(1, 0.0f);
+  }
+
+  int budget0 = two_d ? lut_budget_words / 2 : lut_budget_words;
+  AxisTable T0 = best_table(A0, budget0), T1;
+  if (T0.p.ncell == 0) return "could not build the axis-0 lookup table";
+  if (two_d) {
+    T1 = best_table(A1, lut_budget_words - T0.p.ncell);
+    if (T1.p.ncell == 0) return "could not build the axis-1 lookup table";
+  }
+
+  // entries: byte offsets of histogram slots, or dirty markers
+  const uint32_t stride0 = (uint32_t)out.slots1 * R * 4, stride1 = (uint32_t)R * 4;
+  auto encode = [&](AxisTable &t, uint32_t stride) {
+    for (int c = 0; c < t.p.ncell; c++) {
+      if (t.edge[c] == -1) t.cells[c] = (uint32_t)t.slot[c] * stride;
+      else if (t.edge[c] == -2) t.cells[c] = kDirty | kAlways;
+      else t.cells[c] = kDirty | ((uint32_t)t.edge[c] << 8);
+    }
+  };
+  encode(T0, stride0);
+  if (kind == KRMU) {
+    // r cells whose slot needs an explicit mu decision (eps > eps_main) or a
+    // full FP64 re-test (mu bound too wide) are flagged
+    for (int c = 0; c < T0.p.ncell; c++) {
+      if (T0.edge[c] != -1) continue;
+      int s = T0.slot[c];
+      if (s <= 0) continue;
+      if (always_slot[s]) T0.cells[c] = kDirty | kAlways;
+      else if (eps_slot[s] > eps_main) T0.cells[c] = kDirty | 0x2u | ((uint32_t)s << 8);
+    }
+  }
+  if (two_d) encode(T1, stride1);
+
+  // bands per decision edge (FP32, rounded outward), for the refine path
+  out.band.clear();
+  auto bands = [&](const AxisSpec &a, AxisPlan &p) {
+    p.band_off = (int)out.band.size();
+    for (size_t k = 0; k < a.E.size(); k++) {
+      double lo = 0, hi = 0;
+      bool dec = std::find(a.decision.begin(), a.decision.end(), (int)k) != a.decision.end();
+      if (dec && !a.err.constant) edge_band(a, (int)k, lo, hi);
+      else { lo = a.E[k]; hi = a.E[k]; }
+      out.band.push_back(f32_down(lo));
+      out.band.push_back(f32_up(hi));
+    }
+  };
+  bands(A0, T0.p);
+  T0.p.nb = n0;
+  if (two_d) {
+    bands(A1, T1.p);
+    T1.p.nb = n1;
+  }
+
+  out.lut.clear();
+  T0.p.lut_off = 0;
+  out.lut.insert(out.lut.end(), T0.cells.begin(), T0.cells.end());
+  out.ax[0] = T0.p;
+  if (two_d) {
+    T1.p.lut_off = (int)out.lut.size();
+    out.lut.insert(out.lut.end(), T1.cells.begin(), T1.cells.end());
+    out.ax[1] = T1.p;
+  } else {
+    out.ax[1] = AxisPlan();
+  }
+  return "";
+}
+
+// ------------------------------------------------------------------ tasks
+void tasks_build(const Geometry &g, const std::vector<int32_t> &csA,
+                 const std::vector<int32_t> &csB, bool is_auto, int pair_index, int home_chunk,
+                 int slice, bool full_stencil, std::vector<Task> &out,
+                 unsigned long long &candidates) {
+  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+  const int kx = g.k[0], ky = g.k[1], kz = g.k[2];
+  auto cell = [&](int x, int y, int z) { return ((int64_t)z * ny + y) * nx + x; };
+  auto emit = [&](int h0, int h1, int j0, int j1, int flags) {
+    if (h1 <= h0 || j1 <= j0) return;
+    Task t;
+    t.h0 = h0; t.h1 = h1; t.j0 = j0; t.j1 = j1;
+    t.pair = pair_index;
+    t.flags = flags;
+    t.n_hc = (h1 - h0 + home_chunk - 1) / home_chunk;
+    t.n_sc = (j1 - j0 + slice - 1) / slice;
+    out.push_back(t);
+    unsigned long long nh = (unsigned long long)(h1 - h0), nj = (unsigned long long)(j1 - j0);
+    candidates += (flags & kTaskSelf) ? nh * (nh - 1) / 2 : nh * nj;
+  };
+  // shift code: 2 bits per axis, 1 -> +L, 2 -> -L
+  auto code = [](int sx, int sy, int sz) {
+    auto c = [](int s) { return s > 0 ? 1 : (s < 0 ? 2 : 0); };
+    return (c(sx) | (c(sy) << 2) | (c(sz) << 4)) << 8;
+  };
+  // slices of the x-range [xa, xb] of row (y, z) of B, split where it wraps
+  auto row_slices = [&](int xa, int xb, int y, int z, int sy, int sz, int self_flag,
+                        int h0, int h1) {
+    if (g.periodic) {
+      // at most three pieces: left of the box (image x - L), inside, right
+      // of the box (image x + L); the range is never longer than nx
+      if (xa < 0) {
+        int lo = xa + nx, hi = std::min(xb + nx, nx - 1);
+        emit(h0, h1, csB[cell(lo, y, z)], csB[cell(hi, y, z) + 1], self_flag | code(-1, sy, sz));
+      }
+      int lo = std::max(xa, 0), hi = std::min(xb, nx - 1);
+      if (lo <= hi)
+        emit(h0, h1, csB[cell(lo, y, z)], csB[cell(hi, y, z) + 1], self_flag | code(0, sy, sz));
+      if (xb >= nx) {
+        int lo2 = std::max(xa - nx, 0), hi2 = xb - nx;
+        emit(h0, h1, csB[cell(lo2, y, z)], csB[cell(hi2, y, z) + 1], self_flag | code(1, sy, sz));
+      }
+    } else {
+      int lo = std::max(xa, 0), hi = std::min(xb, nx - 1);
+      if (lo > hi) return;
+      emit(h0, h1, csB[cell(lo, y, z)], csB[cell(hi, y, z) + 1], self_flag);
+    }
+  };
+
+  for (int cz = 0; cz < nz; cz++) {
+    for (int cy = 0; cy < ny; cy++) {
+      int cx = 0;
+      while (cx < nx) {
+        // home run: one cell, extended while the run stays small
+        int cx0 = cx, cx1 = cx;
+        int h0 = csA[cell(cx0, cy, cz)];
+        int h1 = csA[cell(cx0, cy, cz) + 1];
+        int maxrun = g.periodic ? std::max(1, nx - 2 * kx) : kx + 1;
+        while (cx1 + 1 < nx && cx1 - cx0 + 1 < maxrun &&
+               csA[cell(cx1 + 1, cy, cz) + 1] - h0 <= home_chunk && (h1 - h0) < home_chunk / 2) {
+          cx1++;
+          h1 = csA[cell(cx1, cy, cz) + 1];
+        }
+        cx = cx1 + 1;
+        if (h1 <= h0) continue;
+        for (int dz = -kz; dz <= kz; dz++) {
+          for (int dy = -ky; dy <= ky; dy++) {
+            bool self_row = (dz == 0 && dy == 0);
+            if (is_auto && !full_stencil && !self_row && (dz < 0 || (dz == 0 && dy < 0))) continue;
+            int y = cy + dy, z = cz + dz, sy = 0, sz = 0;
+            if (g.periodic) {
+              if (y < 0) { y += ny; sy = -1; } else if (y >= ny) { y -= ny; sy = 1; }
+              if (z < 0) { z += nz; sz = -1; } else if (z >= nz) { z -= nz; sz = 1; }
+            } else if (y < 0 || y >= ny || z < 0 || z >= nz) {
+              continue;
+            }
+            if (is_auto && !full_stencil && self_row) {
+              // same row: the run itself with j > i, then the cells after it
+              emit(h0, h1, h0, h1, kTaskSelf);
+              row_slices(cx1 + 1, cx1 + kx, y, z, sy, sz, 0, h0, h1);
+            } else {
+              row_slices(cx0 - kx, cx1 + kx, y, z, sy, sz, 0, h0, h1);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace cute

@@ -1,0 +1,330 @@
+"""ctypes binding of libcute_gb.so (include/cute.h): argument marshalling only.
+
+Every step of the pair-counting path runs in the CUDA library; this module
+converts numpy arrays / torch tensors to pointers and statuses to
+exceptions.  There is no fallback: if the library is missing or cannot be
+built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcute_gb.so")
+
+KINDS = {"mono": 0, "rmu": 1, "sigpi": 2, "theta": 3}
+ESTIMATORS = {"periodic": 0, "natural": 1, "ls": 2}
+STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "CUDA", -4: "STATE", -5: "TIMEOUT",
+          -6: "UNSUPPORTED", -7: "DEVICE"}
+
+# every exported symbol of include/cute.h
+SYMBOLS = ["cute_ctx_create", "cute_ctx_destroy", "cute_last_error", "cute_sync",
+           "cute_catalog_upload", "cute_catalog_free", "cute_catalog_size", "cute_grid_build",
+           "cute_count_pairs", "cute_count_pairs_batched", "cute_count_pairs_adjoint",
+           "cute_last_stats", "cute_set_timing", "cute_set_launch", "cute_estimator",
+           "cute_theta_to_chord", "cute_version"]
+
+
+class CuteError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("cute %s (%d): %s" % (STATUS.get(status, "?"), status, msg))
+        self.status = status
+
+
+class PairDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("cat_a", ctypes.c_int32), ("cat_b", ctypes.c_int32),
+                ("edges0", ctypes.c_void_p), ("n0", ctypes.c_int32),
+                ("edges1", ctypes.c_void_p), ("n1", ctypes.c_int32),
+                ("weighted", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("candidate_pairs", ctypes.c_uint64), ("rechecked_pairs", ctypes.c_uint64),
+                ("work_items", ctypes.c_uint64), ("launches", ctypes.c_int32),
+                ("warps_per_block", ctypes.c_int32), ("blocks", ctypes.c_int32),
+                ("home_per_lane", ctypes.c_int32), ("kernel_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libcute_gb.so (building it with nvcc if absent)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                from . import build as _b
+                _b.build()
+            L = ctypes.CDLL(LIB_PATH)
+            P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+            L.cute_ctx_create.argtypes = [ctypes.c_int, P, ctypes.POINTER(P)]
+            L.cute_ctx_destroy.argtypes = [P]
+            L.cute_last_error.argtypes = [P]
+            L.cute_last_error.restype = ctypes.c_char_p
+            L.cute_sync.argtypes = [P]
+            L.cute_catalog_upload.argtypes = [P, P, P, i64, ctypes.c_int, f64,
+                                              ctypes.POINTER(i32)]
+            L.cute_catalog_free.argtypes = [P, i32]
+            L.cute_catalog_size.argtypes = [P, i32, ctypes.POINTER(i64)]
+            L.cute_grid_build.argtypes = [P, P, i32, P, i32]
+            L.cute_count_pairs.argtypes = [P, ctypes.POINTER(PairDesc), P, P, P]
+            L.cute_count_pairs_batched.argtypes = [P, i32, P, P, P]
+            L.cute_count_pairs_adjoint.argtypes = [P, ctypes.POINTER(PairDesc), P, P, P]
+            L.cute_last_stats.argtypes = [P, ctypes.POINTER(Stats)]
+            L.cute_set_timing.argtypes = [P, i32]
+            L.cute_set_launch.argtypes = [P, i32, i32, i32]
+            L.cute_estimator.argtypes = [ctypes.c_int, P, P, P, i64, i64, i32, P, f64, P]
+            L.cute_theta_to_chord.argtypes = [P, i32, P]
+            L.cute_version.restype = ctypes.c_char_p
+            for name in SYMBOLS:
+                if name not in ("cute_last_error", "cute_version"):
+                    getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(st, ctx=None):
+    if st != 0:
+        msg = lib().cute_last_error(ctx).decode(errors="replace") if ctx is not None else ""
+        raise CuteError(st, msg)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """Data pointer of a numpy array or torch tensor (kept alive by caller)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        return ctypes.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _xyz(x):
+    if _is_torch(x):
+        import torch
+        x = x.detach()
+        if x.dtype != torch.float64:
+            x = x.to(torch.float64)
+        x = x.contiguous()
+        if x.ndim != 2 or x.shape[1] != 3:
+            raise ValueError("positions must be (n, 3)")
+        return x
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if x.ndim != 2 or x.shape[1] != 3:
+        raise ValueError("positions must be (n, 3)")
+    return x
+
+
+def _w(w):
+    if w is None:
+        return None
+    if _is_torch(w):
+        import torch
+        return w.detach().to(torch.float32).contiguous()
+    return np.ascontiguousarray(w, dtype=np.float32)
+
+
+class Catalog:
+    def __init__(self, ctx, cid, n, periodic, L):
+        self.ctx, self.id, self.n, self.periodic, self.L = ctx, cid, n, periodic, L
+
+    def free(self):
+        if self.id is not None and self.ctx.handle:
+            _check(lib().cute_catalog_free(self.ctx.handle, self.id), self.ctx.handle)
+        self.id = None
+
+
+class Context:
+    """A counting context on one CUDA device (owns catalogs and buffers).
+
+    stream: None -> the torch current stream of the device when torch is
+    available (so library work is ordered with torch work), else a stream the
+    library creates; or an integer cudaStream_t handle."""
+
+    def __init__(self, device: int = 0, stream=None):
+        L = lib()
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = None
+        h = ctypes.c_void_p()
+        st = L.cute_ctx_create(int(device), ctypes.c_void_p(stream) if stream else None,
+                               ctypes.byref(h))
+        if st != 0:
+            raise CuteError(st, L.cute_last_error(None).decode(errors="replace"))
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().cute_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -------------------------------------------------------------- catalogs
+    def upload(self, xyz, weights=None, periodic=False, L=0.0) -> Catalog:
+        x = _xyz(xyz)
+        w = _w(weights)
+        cid = ctypes.c_int32()
+        _check(lib().cute_catalog_upload(self.handle, _ptr(x), _ptr(w), int(x.shape[0]),
+                                         0 if periodic else 1, float(L), ctypes.byref(cid)),
+               self.handle)
+        return Catalog(self, cid.value, int(x.shape[0]), periodic, L)
+
+    def grid(self, cats, reach, cells_per_reach: int = 0):
+        ids = (ctypes.c_int32 * len(cats))(*[c.id for c in cats])
+        r = np.ascontiguousarray(np.broadcast_to(np.asarray(reach, dtype=np.float64), (3,)))
+        _check(lib().cute_grid_build(self.handle, ids, len(cats), _ptr(r), int(cells_per_reach)),
+               self.handle)
+
+    # -------------------------------------------------------------- counting
+    @staticmethod
+    def _desc(kind, a, b, e0, e1, weighted):
+        d = PairDesc()
+        d.kind = KINDS[kind]
+        d.cat_a = a.id
+        d.cat_b = (b if b is not None else a).id
+        d.edges0 = e0.ctypes.data
+        d.n0 = len(e0) - 1
+        if e1 is not None:
+            d.edges1 = e1.ctypes.data
+            d.n1 = len(e1) - 1
+        else:
+            d.edges1 = None
+            d.n1 = 0
+        d.weighted = int(weighted)
+        return d
+
+    def count(self, kind, a, b=None, edges0=None, edges1=None, weighted=False, out=None,
+              wsum_out=None, want_oor=True):
+        """Pair counts of a x b (b None: auto).  Returns (counts, oor, wsum).
+        counts has shape (n0, n1) (n1 = 1 for 1-D kinds).  out / wsum_out may
+        be preallocated numpy arrays or CUDA torch tensors (uint64 / float64,
+        viewed as int64 for torch)."""
+        e0 = np.ascontiguousarray(edges0, dtype=np.float64)
+        e1 = None if edges1 is None else np.ascontiguousarray(edges1, dtype=np.float64)
+        n0 = len(e0) - 1
+        n1 = (len(e1) - 1) if (e1 is not None and kind in ("rmu", "sigpi")) else 1
+        d = self._desc(kind, a, b, e0, e1 if kind in ("rmu", "sigpi") else None, weighted)
+        counts = out if out is not None else np.zeros(n0 * n1, dtype=np.uint64)
+        wsum = None
+        if weighted:
+            wsum = wsum_out if wsum_out is not None else np.zeros(n0 * n1, dtype=np.float64)
+        oor = ctypes.c_uint64(0)
+        _check(lib().cute_count_pairs(self.handle, ctypes.byref(d), _ptr(counts),
+                                      ctypes.byref(oor) if want_oor else None, _ptr(wsum)),
+               self.handle)
+        if not _is_torch(counts):
+            counts = counts.reshape(n0, n1)
+            if wsum is not None and not _is_torch(wsum):
+                wsum = wsum.reshape(n0, n1)
+        return counts, (int(oor.value) if want_oor else None), wsum
+
+    def count_batched(self, kind, pairs, edges0, edges1=None, weighted=False):
+        """pairs: list of (a, b) catalogs (b None: auto), counted in one launch.
+        Returns a list of (n0, n1) uint64 arrays (and wsum arrays if weighted)."""
+        e0 = np.ascontiguousarray(edges0, dtype=np.float64)
+        e1 = None if edges1 is None else np.ascontiguousarray(edges1, dtype=np.float64)
+        n0 = len(e0) - 1
+        n1 = (len(e1) - 1) if (e1 is not None and kind in ("rmu", "sigpi")) else 1
+        n = len(pairs)
+        descs = (PairDesc * n)()
+        for i, (a, b) in enumerate(pairs):
+            descs[i] = self._desc(kind, a, b, e0, e1 if kind in ("rmu", "sigpi") else None,
+                                  weighted)
+        outs = [np.zeros(n0 * n1, dtype=np.uint64) for _ in range(n)]
+        optr = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
+        ws, wptr = None, None
+        if weighted:
+            ws = [np.zeros(n0 * n1, dtype=np.float64) for _ in range(n)]
+            wptr = (ctypes.c_void_p * n)(*[o.ctypes.data for o in ws])
+        _check(lib().cute_count_pairs_batched(self.handle, n, descs, optr, wptr), self.handle)
+        res = [o.reshape(n0, n1) for o in outs]
+        if weighted:
+            return res, [w.reshape(n0, n1) for w in ws]
+        return res
+
+    def adjoint(self, kind, a, b=None, edges0=None, edges1=None, G=None, grad_b=False):
+        """Gradient of sum_b G_b W_b with respect to the weights of a (and of b
+        for cross counts when grad_b)."""
+        e0 = np.ascontiguousarray(edges0, dtype=np.float64)
+        e1 = None if edges1 is None else np.ascontiguousarray(edges1, dtype=np.float64)
+        d = self._desc(kind, a, b, e0, e1 if kind in ("rmu", "sigpi") else None, True)
+        if _is_torch(G):
+            import torch
+            Gc = G.detach().to(torch.float64).contiguous()
+            ga = torch.zeros(a.n, dtype=torch.float64, device=G.device)
+            gb = (torch.zeros(b.n, dtype=torch.float64, device=G.device)
+                  if (grad_b and b is not None) else None)
+        else:
+            Gc = np.ascontiguousarray(G, dtype=np.float64).ravel()
+            ga = np.zeros(a.n, dtype=np.float64)
+            gb = np.zeros(b.n, dtype=np.float64) if (grad_b and b is not None) else None
+        _check(lib().cute_count_pairs_adjoint(self.handle, ctypes.byref(d), _ptr(Gc), _ptr(ga),
+                                              _ptr(gb)), self.handle)
+        return (ga, gb) if grad_b else ga
+
+    # -------------------------------------------------------------- misc
+    def sync(self):
+        _check(lib().cute_sync(self.handle), self.handle)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().cute_last_stats(self.handle, ctypes.byref(s)), self.handle)
+        return s.as_dict()
+
+    def set_timing(self, on: bool):
+        _check(lib().cute_set_timing(self.handle, int(bool(on))), self.handle)
+
+    def set_launch(self, home_per_lane=0, warps_per_block=0, slice=0):
+        _check(lib().cute_set_launch(self.handle, int(home_per_lane), int(warps_per_block),
+                                     int(slice)), self.handle)
+
+
+def estimator(kind, DD, DR=None, RR=None, Nd=0, Nr=0, edges=None, L=0.0):
+    """Eq. 13 ('periodic'), Eq. 14 ('natural') or Eq. 15 ('ls') from counts."""
+    DD = np.ascontiguousarray(DD, dtype=np.uint64).ravel()
+    DR_ = None if DR is None else np.ascontiguousarray(DR, dtype=np.uint64).ravel()
+    RR_ = None if RR is None else np.ascontiguousarray(RR, dtype=np.uint64).ravel()
+    e = None if edges is None else np.ascontiguousarray(edges, dtype=np.float64)
+    out = np.zeros(len(DD), dtype=np.float64)
+    _check(lib().cute_estimator(ESTIMATORS[kind], _ptr(DD), _ptr(DR_), _ptr(RR_), int(Nd),
+                                int(Nr), len(DD), _ptr(e), float(L), _ptr(out)))
+    return out
+
+
+def theta_to_chord(theta_deg):
+    t = np.ascontiguousarray(theta_deg, dtype=np.float64)
+    out = np.zeros(len(t), dtype=np.float64)
+    _check(lib().cute_theta_to_chord(_ptr(t), len(t), _ptr(out)))
+    return out
+
+
+def version() -> str:
+    return lib().cute_version().decode()

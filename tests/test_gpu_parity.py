@@ -1,0 +1,199 @@
+"""GPU parity: counts from the CUDA path (through the C ABI) equal the FP64
+oracle's bit for bit, for every kind and boundary, on seeded catalogs that
+span many tiles and work items with ragged tails, and on the degenerate and
+adversarial cases (empty catalogs, single objects, coincident objects, pairs
+exactly on bin edges, periodic pairs across the box faces)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1210_1833_gb300 import cute, synthetic
+from gpu_util import edge_pairs_mono, edge_pairs_mu, gpu_count, oracle_count
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = cute.Context(0)
+    yield c
+    c.close()
+
+
+def _assert_same(got, ref):
+    gc, go, _ = got
+    rc, ro, _ = ref
+    assert gc.shape == rc.shape
+    if not np.array_equal(gc, rc):
+        diff = np.argwhere(gc != rc)
+        raise AssertionError("counts differ at %d bins, first %s: gpu %s oracle %s" %
+                             (len(diff), diff[:5].tolist(), gc[tuple(diff[0])], rc[tuple(diff[0])]))
+    assert go == ro
+
+
+# ------------------------------------------------------------------ workloads
+def test_c1_monopole_box_full_size(ctx):
+    """Full configuration of the small periodic-box workload (20,000 points,
+    40 bins), brute-force oracle."""
+    w = synthetic.c1_monopole_box()
+    got = gpu_count(ctx, "mono", w.data, e0=w.edges0, periodic=True, L=w.L)
+    ref = oracle_count("mono", w.data, e0=w.edges0, periodic=True, L=w.L)
+    _assert_same(got, ref)
+    xi_g = cute.estimator("periodic", got[0].ravel(), Nd=len(w.data), edges=w.edges0, L=w.L)
+    xi_o = oracle.xi_periodic(ref[0].ravel(), len(w.data), w.edges0, w.L)
+    np.testing.assert_allclose(xi_g, xi_o, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("cpr", [1, 2, 3])
+@pytest.mark.parametrize("hp", [2, 4])
+def test_mono_periodic_launch_shapes(ctx, cpr, hp):
+    w = synthetic.c1_monopole_box(scale=0.3)
+    ctx.set_launch(home_per_lane=hp, slice=128)
+    try:
+        got = gpu_count(ctx, "mono", w.data, e0=w.edges0, periodic=True, L=w.L,
+                        cells_per_reach=cpr)
+    finally:
+        ctx.set_launch()
+    ref = oracle_count("mono", w.data, e0=w.edges0, periodic=True, L=w.L)
+    _assert_same(got, ref)
+
+
+def test_mono_open_cross_and_auto(ctx):
+    rng = np.random.default_rng(100)
+    a = np.concatenate([rng.uniform(0, 300, size=(4000, 3)),
+                        synthetic.blobs_box(20, 60, 300.0, 3.0, rng)])
+    b = rng.uniform(-20, 320, size=(5000, 3))
+    e = np.linspace(0.0, 40.0, 17)
+    _assert_same(gpu_count(ctx, "mono", a, b, e), oracle_count("mono", a, b, e))
+    _assert_same(gpu_count(ctx, "mono", a, None, e), oracle_count("mono", a, None, e))
+    # bins not starting at zero, log-spaced: the logarithmic table
+    e2 = np.geomspace(0.5, 40.0, 25)
+    _assert_same(gpu_count(ctx, "mono", a, b, e2), oracle_count("mono", a, b, e2))
+
+
+def test_sigpi_periodic_and_open(ctx):
+    boxes = synthetic.c4_batched_sigpi(n_boxes=1, scale=0.05)
+    w = boxes[0]
+    got = gpu_count(ctx, "sigpi", w.data, None, w.edges0, w.edges1, periodic=True, L=w.L)
+    ref = oracle_count("sigpi", w.data, None, w.edges0, w.edges1, periodic=True, L=w.L,
+                       cells=True)
+    _assert_same(got, ref)
+    got = gpu_count(ctx, "sigpi", w.data, w.randoms, w.edges0, w.edges1, periodic=True, L=w.L)
+    ref = oracle_count("sigpi", w.data, w.randoms, w.edges0, w.edges1, periodic=True, L=w.L,
+                       cells=True)
+    _assert_same(got, ref)
+    rng = np.random.default_rng(101)
+    a = rng.uniform(0, 200, size=(3000, 3))
+    es, ep = np.linspace(0, 30, 11), np.linspace(0, 20, 9)
+    _assert_same(gpu_count(ctx, "sigpi", a, None, es, ep), oracle_count("sigpi", a, None, es, ep))
+
+
+def test_rmu_lightcone_small(ctx):
+    w = synthetic.c2_rmu_lightcone(scale=0.008)
+    for a, b in ((w.data, None), (w.data, w.randoms), (w.randoms, None)):
+        got = gpu_count(ctx, "rmu", a, b, w.edges0, w.edges1)
+        ref = oracle_count("rmu", a, b, w.edges0, w.edges1, cells=True)
+        _assert_same(got, ref)
+
+
+def test_theta_small(ctx):
+    w = synthetic.c3_angular(scale=0.0008)
+    chord = oracle.theta_to_chord(w.extra["theta_deg"])
+    for a, b in ((w.data, None), (w.data, w.randoms)):
+        got = gpu_count(ctx, "theta", a, b, chord)
+        ref = oracle_count("theta", a, b, chord, cells=True)
+        _assert_same(got, ref)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_pairs_on_edges_mono(ctx):
+    rng = np.random.default_rng(102)
+    e = np.arange(21) * 2.5
+    x = edge_pairs_mono(rng, e, 6)
+    _assert_same(gpu_count(ctx, "mono", x, None, e), oracle_count("mono", x, None, e))
+    ep = e[:17]  # periodic reach must stay below 0.47 L
+    xb = edge_pairs_mono(rng, ep, 6, box=100.0)
+    _assert_same(gpu_count(ctx, "mono", xb, None, ep, periodic=True, L=100.0),
+                 oracle_count("mono", xb, None, ep, periodic=True, L=100.0))
+    st = ctx.stats()
+    assert st["rechecked_pairs"] > 0
+
+
+def test_pairs_on_edges_mu(ctx):
+    rng = np.random.default_rng(103)
+    e0 = np.arange(41) * 5.0
+    e1 = np.arange(41) / 40.0
+    x = np.concatenate([edge_pairs_mu(rng, e1, r, 2) for r in (0.7, 3.0, 12.0, 77.0, 190.0)])
+    _assert_same(gpu_count(ctx, "rmu", x, None, e0, e1), oracle_count("rmu", x, None, e0, e1))
+
+
+def test_pairs_on_edges_theta(ctx):
+    rng = np.random.default_rng(104)
+    theta = 10.0 ** (-2.0 + 3.0 * np.arange(65) / 64.0)
+    chord = oracle.theta_to_chord(theta)
+    pts = []
+    for c in chord[::3]:
+        for d in (0.0, 2.0**-40, -2.0**-40, 2.0**-26):
+            n1 = synthetic._cap_uniform(1, 0.96, rng)[0]
+            t = np.cross(n1, rng.normal(size=3))
+            t /= np.linalg.norm(t)
+            ang = 2 * np.arcsin(c * (1 + d) / 2)
+            n2 = np.cos(ang) * n1 + np.sin(ang) * t
+            pts += [n1, n2 / np.linalg.norm(n2)]
+    x = np.array(pts)
+    _assert_same(gpu_count(ctx, "theta", x, None, chord), oracle_count("theta", x, None, chord))
+
+
+def test_periodic_faces_and_duplicates(ctx):
+    rng = np.random.default_rng(105)
+    L = 100.0
+    x = rng.uniform(0, L, size=(3000, 3))
+    # objects hugging the faces, so most close pairs wrap
+    x[:1000] = np.mod(rng.normal(0, 2.0, size=(1000, 3)), L)
+    x[x >= L] = 0.0
+    x[1000:1200] = x[1200:1400]  # exact duplicates: separation 0
+    e = np.linspace(0, 30, 13)
+    _assert_same(gpu_count(ctx, "mono", x, None, e, periodic=True, L=L),
+                 oracle_count("mono", x, None, e, periodic=True, L=L))
+    es, ep = np.linspace(0, 25, 6), np.linspace(0, 10, 5)
+    _assert_same(gpu_count(ctx, "sigpi", x, None, es, ep, periodic=True, L=L),
+                 oracle_count("sigpi", x, None, es, ep, periodic=True, L=L))
+
+
+@pytest.mark.parametrize("na,nb", [(0, 0), (0, 50), (1, 0), (1, 1), (2, 7), (65, 3)])
+def test_tiny_catalogs(ctx, na, nb):
+    rng = np.random.default_rng(106 + na + nb)
+    a = rng.uniform(0, 50, size=(na, 3))
+    b = rng.uniform(0, 50, size=(nb, 3))
+    e = np.linspace(0, 20, 5)
+    _assert_same(gpu_count(ctx, "mono", a, b, e), oracle_count("mono", a, b, e))
+    _assert_same(gpu_count(ctx, "mono", a, None, e), oracle_count("mono", a, None, e))
+
+
+def test_all_in_one_cell_dense(ctx):
+    rng = np.random.default_rng(107)
+    a = rng.normal(0, 0.5, size=(6000, 3)) + 50.0
+    e = np.linspace(0, 4, 9)
+    _assert_same(gpu_count(ctx, "mono", a, None, e), oracle_count("mono", a, None, e))
+
+
+def test_invalid_requests_fail_cleanly(ctx):
+    a = ctx.upload(np.random.default_rng(0).uniform(0, 10, size=(10, 3)))
+    with pytest.raises(cute.CuteError):
+        ctx.count("mono", a, None, np.linspace(0, 1, 3))  # no grid yet
+    ctx.grid([a], [1.0, 1.0, 1.0])
+    with pytest.raises(cute.CuteError):
+        ctx.count("mono", a, None, np.linspace(0, 2, 3))  # reach too small
+    with pytest.raises(cute.CuteError):
+        ctx.count("mono", a, None, np.array([0.0, 0.5, 0.4]))  # not increasing
+    with pytest.raises(cute.CuteError):
+        ctx.count("rmu", a, None, np.linspace(0, 1, 3), np.array([0.0, 0.5, 0.9]))  # mu to 1
+    with pytest.raises(cute.CuteError):
+        ctx.upload(np.array([[0.0, 0.0, 10.0]]), periodic=True, L=10.0)  # x == L
+    with pytest.raises(cute.CuteError):
+        ctx.upload(np.array([[0.0, np.nan, 1.0]]))
+    a.free()
+    ctx.sync()

@@ -1,0 +1,74 @@
+"""Host-side checks of libcute_gb.so that need no GPU: the library loads,
+exports every entry point include/cute.h declares, and its host-only
+functions (estimators, angle -> chord) agree with the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1210_1833_gb300 import cute
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "cute.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cute_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = cute.lib()
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(cute.SYMBOLS) == set(names)
+    assert "sm_103a" in cute.version()
+
+
+def test_ctx_create_without_gpu_fails_cleanly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(cute.CuteError):
+        cute.Context(0)
+
+
+def test_theta_to_chord_matches_oracle_bit_exactly():
+    t = 10.0 ** (-2.0 + 3.0 * np.arange(65) / 64.0)
+    assert cute.theta_to_chord(t).tolist() == oracle.theta_to_chord(t).tolist()
+    with pytest.raises(cute.CuteError):
+        cute.theta_to_chord([-1.0])
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_estimators_match_oracle(seed):
+    rng = np.random.default_rng(seed)
+    nb = 40
+    DD = rng.integers(0, 10**9, size=nb).astype(np.uint64)
+    DR = rng.integers(0, 10**10, size=nb).astype(np.uint64)
+    RR = rng.integers(1, 10**11, size=nb).astype(np.uint64)
+    RR[3] = 0
+    Nd, Nr = 500_000, 2_000_000
+    for name, ref in (("ls", oracle.xi_ls(DD, DR, RR, Nd, Nr)),
+                      ("natural", oracle.xi_natural(DD, RR, Nd, Nr))):
+        got = cute.estimator(name, DD, DR, RR, Nd, Nr)
+        assert np.isnan(got[3]) and np.isnan(ref[3])
+        m = ~np.isnan(ref)
+        np.testing.assert_allclose(got[m], ref[m], rtol=1e-12, atol=1e-12)
+    e = np.arange(nb + 1) * 5.0
+    got = cute.estimator("periodic", DD, Nd=20000, edges=e, L=1000.0)
+    ref = oracle.xi_periodic(DD, 20000, e, 1000.0)
+    m = ~np.isnan(ref)
+    np.testing.assert_allclose(got[m], ref[m], rtol=1e-12, atol=1e-12)
+
+
+def test_estimator_rejects_bad_input():
+    with pytest.raises(cute.CuteError):
+        cute.estimator("ls", [1, 2], None, [1, 2], 10, 20)
+    with pytest.raises(cute.CuteError):
+        cute.estimator("periodic", [1, 2], Nd=1, edges=[0, 1, 2], L=10)
