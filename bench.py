@@ -173,6 +173,9 @@ def run_gpu(args, w, rank, world):
         ctx.grid([cd, cr], reach)
         res = {}
         for name, a, b in (("DD", cd, None), ("DR", cd, cr), ("RR", cr, None)):
+            if args.only and name not in args.only.split(","):
+                res[name] = np.ones((len(w.edges0) - 1, len(w.edges1) - 1), np.uint64)
+                continue
             c, _, _ = ctx.count("rmu", a, b, w.edges0, w.edges1, want_oor=False)
             res[name] = c
             if record:
@@ -230,7 +233,10 @@ def run_gpu(args, w, rank, world):
     rr_ms = float(np.mean(state["rr_ms"])) if state["rr_ms"] else float("nan")
     rr_rate = state["rr_cand"] / (rr_ms / 1e3)
     achieved = rr_rate * I_PAIR_RMU / 1e12
-    cpu_v, cpu_thr, cpu_desc = cpu_oracle_rate(w, target_s=12.0)
+    if args.no_cpu:
+        cpu_v, cpu_thr, cpu_desc = None, None, "skipped (--no-cpu)"
+    else:
+        cpu_v, cpu_thr, cpu_desc = cpu_oracle_rate(w, target_s=12.0)
     launches_per_step = 2 + 2 * 3 + 3  # upload stats x2, grid (assign, scan, scatter) x2, counts x3
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
@@ -273,6 +279,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1 = full size)")
+    ap.add_argument("--only", default="", help="profiling: run only these counts (e.g. RR)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle sample")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

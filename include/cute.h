@@ -172,6 +172,8 @@ cute_status cute_count_pairs_adjoint(cute_ctx *ctx, const cute_pair_desc *d, con
 typedef struct {
   uint64_t candidate_pairs; /* pairs examined by the FP32 path              */
   uint64_t rechecked_pairs; /* of those, re-tested in FP64 near an edge     */
+  uint64_t refined_pairs;   /* pairs in a dirty table cell, refined against
+                               the edge's FP32 error band                   */
   uint64_t work_items;      /* (home chunk, neighbour slice) items run      */
   int32_t launches;         /* kernels launched by the call                 */
   int32_t warps_per_block, blocks, home_per_lane;

@@ -238,10 +238,11 @@ cute_status cute_last_stats(cute_ctx *ctx, cute_stats *out) {
   ENTER(ctx);
   if (!out) return fail(ctx, CUTE_E_INVALID, "out is NULL");
   CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
-  unsigned long long h[3] = {0, 0, 0};
+  unsigned long long h[4] = {0, 0, 0, 0};
   CUDA_OR_FAIL(cudaMemcpy(h, ctx->d_ticket, sizeof(h), cudaMemcpyDeviceToHost));
   ctx->stats.rechecked_pairs = h[1];
   ctx->stats.work_items = h[2];
+  ctx->stats.refined_pairs = h[3];
   if (ctx->timing && ctx->stats.launches > 0) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->stats.kernel_ms = ms;
@@ -347,7 +348,7 @@ cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &
   auto P = std::make_shared<Plan>();
   const bool two_d = (d->kind == CUTE_R_MU || d->kind == CUTE_SIGMA_PI);
   std::string m = plan_build((int)d->kind, d->edges0, d->n0, d->edges1, two_d ? d->n1 : 1, ep,
-                             two_d ? 8192 : 8192, 10752, *P);
+                             two_d ? 8192 : 8192, 12288, *P);
   if (!m.empty()) return fail(ctx, CUTE_E_UNSUPPORTED, m);
   auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
     cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
@@ -356,8 +357,6 @@ cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &
   };
   CUDA_OR_FAIL(up((void **)&P->d_lut, P->lut.data(), P->lut.size() * 4));
   CUDA_OR_FAIL(up((void **)&P->d_band, P->band.data(), P->band.size() * 4));
-  CUDA_OR_FAIL(up((void **)&P->d_mu_eps, P->mu_eps.data(), P->mu_eps.size() * 4));
-  CUDA_OR_FAIL(up((void **)&P->d_mu_edge, P->mu_edge.data(), P->mu_edge.size() * 4));
   CUDA_OR_FAIL(up((void **)&P->d_E0, P->E0.data(), P->E0.size() * 8));
   CUDA_OR_FAIL(up((void **)&P->d_E1, P->E1.data(), P->E1.size() * 8));
   ctx->plans[key.str()] = P;
@@ -448,7 +447,8 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, bool weighted
   st = get_tasks(ctx, pr.dis, pr.hp, slice, full_stencil, pr.ts);
   if (st != CUTE_OK) return st;
   const Plan &P = *pr.plan;
-  SmemLayout L = smem_layout((int)P.lut.size(), P.nslots, P.R, pr.hp, weighted);
+  SmemLayout L = smem_layout((int)P.lut.size(), (int)P.band.size() / 2, P.nslots, P.R, pr.hp,
+                             weighted);
   size_t avail = ctx->smem_optin;
   int warps = ctx->warps_override ? ctx->warps_override : 16;
   while (warps > 1 && (size_t)L.lut_bytes + (size_t)warps * L.warp_bytes > avail) warps--;
@@ -468,9 +468,9 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, bool weighted
   p.lut_words = (int)P.lut.size();
   p.ax[0] = P.ax[0];
   p.ax[1] = P.ax[1];
-  p.band = P.d_band;
-  p.mu_eps = P.d_mu_eps;
-  p.mu_edge = P.d_mu_edge;
+  p.band = (const float2 *)P.d_band;
+  p.band_words = (int)P.band.size() / 2;
+  p.mu_eps_base = P.mu_eps_base;
   p.E0 = P.d_E0;
   p.E1 = P.d_E1;
   p.n0 = P.n0;
@@ -479,7 +479,6 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, bool weighted
   p.nslots = P.nslots;
   p.R = P.R;
   p.slice = slice;
-  p.eps_main = P.eps_main;
   p.ticket = ctx->d_ticket;
   p.stats = ctx->d_ticket + 1;
   p.err = ctx->d_err;
@@ -516,7 +515,7 @@ cute_status count_driver(cute_ctx *ctx, int n, const cute_pair_desc *d, uint64_t
   unsigned long long *d_out = (unsigned long long *)ctx->d_scratch;
   pr.p.out_counts = d_out;
   CUDA_OR_FAIL(cudaMemsetAsync(d_out, 0, out_bytes, ctx->stream));
-  CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, 3 * sizeof(unsigned long long), ctx->stream));
+  CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, 4 * sizeof(unsigned long long), ctx->stream));
   ctx->stats = cute_stats{};
   ctx->stats.candidate_pairs = pr.ts->candidates;
   ctx->stats.warps_per_block = pr.warps;

@@ -9,7 +9,8 @@ namespace cute {
 template <int HP>
 struct Home {
   float x[HP], y[HP], z[HP];   // home position minus the image shift (grid frame)
-  float ax[HP], ay[HP], az[HP];// R_MU: 2 x_i in the observer frame
+  float ax[HP], ay[HP], az[HP];// R_MU: x_i in the observer frame
+  float aq[HP];                // R_MU: 4 |x_i|^2
   int id[HP];                  // sorted index in A (INT_MAX when padded)
 };
 
@@ -64,80 +65,79 @@ static __device__ __noinline__ void flush_hist(const KParams &p, const WarpSmem 
   __syncwarp();
 }
 
-// A pair whose table entry is dirty: refine against the band of the one
-// edge, count it if decided, else queue it for the FP64 re-test.
-template <int KIND>
-__device__ __noinline__ void slow_pair(const KParams &p, const WarpSmem &w, float v0, float v1,
-                                       uint32_t e0, uint32_t e1, int hid, int gj) {
-  int slot = -1;
-  int s0 = axis_refine(p, 0, v0, e0, false);
-  if (s0 == 0) return;  // certainly out of range
-  if (s0 > 0) {
-    if (KIND == KMONO || KIND == KTHETA) {
-      slot = s0;
-    } else if (KIND == KSIGPI) {
-      int s1 = axis_refine(p, 1, v1, e1, false);
-      if (s1 == 0) return;
-      if (s1 > 0) slot = s0 * p.slots1 + s1;
-    } else {
-      int s1 = mu_decide(p, v1, e1, s0, p.eps_main);
-      if (s1 > 0) slot = s0 * p.slots1 + s1;
-    }
-  }
-  if (slot > 0) {
-    atomicAdd((unsigned *)(w.hist_lane + (size_t)slot * p.R * 4), 1u);
-    return;
-  }
-  int pos = atomicAdd(w.qcnt, 1);
-  if (pos < w.qcap) w.queue[pos] = make_int2(hid, gj);
-  else atomicCAS(p.err, 0, (int)CUTE_E_DEVICE);
-}
-
 // All pairs of the HP home objects of each lane with the cnt neighbours of
 // one shared-memory tile (cnt even; rows past the slice hold sentinels).
+// Two neighbours at a time: every table lookup of the 2 x HP pairs is issued
+// first, then the histogram increments; pairs inside an edge's error band
+// go to the warp's FP64 queue (rare, so the enqueue sits behind one vote).
 template <int KIND, int HP, int M0, int M1, bool SELF>
 __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__restrict__ lut,
-                                           const PairDev &pd, const WarpSmem &w,
-                                           const float4 *__restrict__ tile, int cnt, int gj0,
-                                           const Home<HP> &h, int lane) {
+                                           const float2 *__restrict__ band, const PairDev &pd,
+                                           const WarpSmem &w, const float4 *__restrict__ tile,
+                                           int cnt, int gj0, const Home<HP> &h, int lane,
+                                           unsigned &near_count) {
+  constexpr int NP = 2 * HP;
+  const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u, stride1 = (uint32_t)p.R * 4u;
   for (int j = 0; j < cnt; j += 2) {
+    uint32_t off[NP];
+    unsigned nmask = 0;
 #pragma unroll
     for (int u = 0; u < 2; u++) {
       const float4 q = tile[j + u];
-      const int gj = gj0 + j + u;
 #pragma unroll
       for (int s = 0; s < HP; s++) {
-        float dx = __fsub_rn(q.x, h.x[s]);
-        float dy = __fsub_rn(q.y, h.y[s]);
-        float dz = __fsub_rn(q.z, h.z[s]);
-        float v0, v1 = 0.0f;
-        uint32_t e0, e1 = 0, e;
+        const int k = u * HP + s;
+        const float dx = __fsub_rn(q.x, h.x[s]);
+        const float dy = __fsub_rn(q.y, h.y[s]);
+        const float dz = __fsub_rn(q.z, h.z[s]);
+        bool near;
+        uint32_t o;
         if (KIND == KMONO || KIND == KTHETA) {
-          v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-          e0 = lut_get<M0>(lut, p.ax[0], v0);
-          e = e0;
+          float v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          const uint32_t e0 = lut_get<M0>(lut, p.ax[0], v0);
+          o = axis_resolve(band, p.ax[0], v0, e0, stride0, near);
         } else if (KIND == KSIGPI) {
-          v0 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
-          v1 = __fmul_rn(dz, dz);
-          e0 = lut_get<M0>(lut, p.ax[0], v0);
-          e1 = lut_get<M1>(lut, p.ax[1], v1);
-          e = e0 + e1;
+          float v0 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+          float v1 = __fmul_rn(dz, dz);
+          const uint32_t e0 = lut_get<M0>(lut, p.ax[0], v0);
+          const uint32_t e1 = lut_get<M1>(lut, p.ax[1], v1);
+          bool n0, n1;
+          o = axis_resolve(band, p.ax[0], v0, e0, stride0, n0) +
+              axis_resolve(band, p.ax[1], v1, e1, stride1, n1);
+          near = n0 || n1;
         } else {
-          float lx = __fadd_rn(h.ax[s], dx);
-          float ly = __fadd_rn(h.ay[s], dy);
-          float lz = __fadd_rn(h.az[s], dz);
-          v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-          float l2 = __fmaf_rn(lz, lz, __fmaf_rn(ly, ly, __fmul_rn(lx, lx)));
-          float sl = __fmaf_rn(dz, lz, __fmaf_rn(dy, ly, __fmul_rn(dx, lx)));
-          float den = __fmul_rn(v0, l2);
-          v1 = __fmul_rn(fabsf(sl), rsqrtf(den));
-          e0 = lut_get<M0>(lut, p.ax[0], v0);
-          e1 = lut_get<M1>(lut, p.ax[1], v1);
-          e = e0 + e1;
+          // s = x_j - x_i; l = x_i + x_j = 2 x_i + s; s.l = 2 s.x_i + r^2;
+          // l.l = 4 |x_i|^2 + 4 s.x_i + r^2
+          float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          const float sx = __fmaf_rn(dz, h.az[s], __fmaf_rn(dy, h.ay[s], __fmul_rn(dx, h.ax[s])));
+          const float sl = __fmaf_rn(2.0f, sx, r2);
+          const float l2 = __fmaf_rn(4.0f, sx, __fadd_rn(h.aq[s], r2));
+          float mu = __fmul_rn(fabsf(sl), rsqrtf(__fmul_rn(r2, l2)));
+          const uint32_t e0 = lut_get<M0>(lut, p.ax[0], r2);
+          const uint32_t e1 = lut_get<M1>(lut, p.ax[1], mu);
+          const float eps = __int_as_float(__float_as_int(p.mu_eps_base) +
+                                           (int)(((e0 >> kClassShift) & 0xFu) << 23));
+          bool n0, n1;
+          o = axis_resolve(band, p.ax[0], r2, e0, stride0, n0) +
+              mu_resolve(band, p.ax[1], mu, e1, stride1, eps, n1);
+          near = n0 || n1;
         }
-        if (SELF && !(gj > h.id[s])) e = 0u;  // not a pair of this task: trash slot
-        if (e < kDirty) atomicAdd((unsigned *)(w.hist_lane + e), 1u);
-        else slow_pair<KIND>(p, w, v0, v1, e0, e1, h.id[s], gj);
+        if (SELF && !(gj0 + j + u > h.id[s])) { o = 0u; near = false; }  // not a pair of this task
+        if (near) { o = 0u; nmask |= 1u << k; }
+        off[k] = o;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NP; k++) atomicAdd((unsigned *)(w.hist_lane + off[k]), 1u);
+    if (__any_sync(kFull, nmask != 0u)) {
+#pragma unroll
+      for (int k = 0; k < NP; k++) {
+        if (nmask & (1u << k)) {
+          near_count++;
+          int pos = atomicAdd(w.qcnt, 1);
+          if (pos < w.qcap) w.queue[pos] = make_int2(h.id[k % HP], gj0 + j + k / HP);
+          else atomicCAS(p.err, 0, (int)CUTE_E_DEVICE);
+        }
       }
     }
     __syncwarp();
@@ -147,30 +147,34 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__r
 
 template <int KIND, int HP, int M0, int M1>
 __device__ __forceinline__ void tile_dispatch_self(const KParams &p, const uint32_t *lut,
+                                                   const float2 *band,
                                                    const PairDev &pd, const WarpSmem &w,
                                                    const float4 *tile, int cnt, int gj0,
-                                                   const Home<HP> &h, int lane, bool self) {
-  if (self) tile_pairs<KIND, HP, M0, M1, true>(p, lut, pd, w, tile, cnt, gj0, h, lane);
-  else tile_pairs<KIND, HP, M0, M1, false>(p, lut, pd, w, tile, cnt, gj0, h, lane);
+                                                   const Home<HP> &h, int lane, bool self,
+                                                   unsigned &dc) {
+  if (self) tile_pairs<KIND, HP, M0, M1, true>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, dc);
+  else tile_pairs<KIND, HP, M0, M1, false>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, dc);
 }
 
 template <int KIND, int HP>
 __device__ __forceinline__ void tile_dispatch(const KParams &p, const uint32_t *lut,
+                                              const float2 *band,
                                               const PairDev &pd, const WarpSmem &w,
                                               const float4 *tile, int cnt, int gj0,
-                                              const Home<HP> &h, int lane, bool self) {
+                                              const Home<HP> &h, int lane, bool self,
+                                              unsigned &dc) {
   const int m0 = p.ax[0].mode;
   if (KIND == KMONO || KIND == KTHETA) {
-    if (m0 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLinear, 0>(p, lut, pd, w, tile, cnt, gj0, h, lane, self);
-    else tile_dispatch_self<KIND, HP, kLutLog, 0>(p, lut, pd, w, tile, cnt, gj0, h, lane, self);
+    if (m0 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLinear, 0>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
+    else tile_dispatch_self<KIND, HP, kLutLog, 0>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
   } else {
     const int m1 = p.ax[1].mode;
     if (m0 == kLutLinear) {
-      if (m1 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLinear, kLutLinear>(p, lut, pd, w, tile, cnt, gj0, h, lane, self);
-      else tile_dispatch_self<KIND, HP, kLutLinear, kLutLog>(p, lut, pd, w, tile, cnt, gj0, h, lane, self);
+      if (m1 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLinear, kLutLinear>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
+      else tile_dispatch_self<KIND, HP, kLutLinear, kLutLog>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
     } else {
-      if (m1 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLog, kLutLinear>(p, lut, pd, w, tile, cnt, gj0, h, lane, self);
-      else tile_dispatch_self<KIND, HP, kLutLog, kLutLog>(p, lut, pd, w, tile, cnt, gj0, h, lane, self);
+      if (m1 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLog, kLutLinear>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
+      else tile_dispatch_self<KIND, HP, kLutLog, kLutLog>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
     }
   }
 }
@@ -200,9 +204,11 @@ template <int KIND, bool PER, int HP>
 __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const SmemLayout L = smem_layout(p.lut_words, p.nslots, p.R, HP, false);
+  const SmemLayout L = smem_layout(p.lut_words, p.band_words, p.nslots, p.R, HP, false);
   uint32_t *lut = (uint32_t *)smem;
   for (int i = threadIdx.x; i < p.lut_words; i += blockDim.x) lut[i] = p.lut[i];
+  float2 *band = (float2 *)(smem + align16(p.lut_words * 4));
+  for (int i = threadIdx.x; i < p.band_words; i += blockDim.x) band[i] = p.band[i];
   unsigned char *wb = smem + L.lut_bytes + (size_t)warp * L.warp_bytes;
   WarpSmem w;
   w.hist = (uint32_t *)wb;
@@ -219,6 +225,7 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
   int cur_pair = -1;
   PairDev pd;
   unsigned long long acc = 0, items = 0;
+  unsigned dirty_count = 0;
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(p.ticket, 1ull);
@@ -266,14 +273,17 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
         h.z[s] = __fsub_rn(a.z, Sz);
         h.id[s] = idx;
         if (KIND == KRMU) {
-          h.ax[s] = (float)(2.0 * pd.sA[idx]);
-          h.ay[s] = (float)(2.0 * pd.sA[(size_t)pd.nA + idx]);
-          h.az[s] = (float)(2.0 * pd.sA[2 * (size_t)pd.nA + idx]);
+          const double X = pd.sA[idx], Y = pd.sA[(size_t)pd.nA + idx],
+                       Z = pd.sA[2 * (size_t)pd.nA + idx];
+          h.ax[s] = (float)X;
+          h.ay[s] = (float)Y;
+          h.az[s] = (float)Z;
+          h.aq[s] = (float)(4.0 * (X * X + Y * Y + Z * Z));
         }
       } else {
         h.x[s] = kHomeFar; h.y[s] = kHomeFar; h.z[s] = kHomeFar;
         h.id[s] = 0x7fffffff;
-        if (KIND == KRMU) { h.ax[s] = 2.0f * kHomeFar; h.ay[s] = 2.0f * kHomeFar; h.az[s] = 2.0f * kHomeFar; }
+        if (KIND == KRMU) { h.ax[s] = kHomeFar; h.ay[s] = kHomeFar; h.az[s] = kHomeFar; h.aq[s] = kHomeFar; }
       }
     }
 
@@ -300,8 +310,8 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
       __syncwarp();
       int cnt = min(kTile, nj - tt * kTile);
       cnt = (cnt + 1) & ~1;
-      tile_dispatch<KIND, HP>(p, lut, pd, w, w.tiles + (tt & 1) * kTile, cnt, js + tt * kTile, h,
-                              lane, self);
+      tile_dispatch<KIND, HP>(p, lut, band, pd, w, w.tiles + (tt & 1) * kTile, cnt,
+                              js + tt * kTile, h, lane, self, dirty_count);
       __syncwarp();
     }
   }
@@ -310,6 +320,8 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
     flush_hist(p, w, pd.out, lane);
   }
   if (lane == 0 && items) atomicAdd(&p.stats[1], items);
+  for (int o = 16; o > 0; o >>= 1) dirty_count += __shfl_xor_sync(kFull, dirty_count, o);
+  if (lane == 0 && dirty_count) atomicAdd(&p.stats[2], (unsigned long long)dirty_count);
 }
 
 template <int KIND, bool PER, int HP>

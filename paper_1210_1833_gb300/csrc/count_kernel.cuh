@@ -33,7 +33,7 @@ constexpr float kHomeFar = 3.0e18f;
 constexpr float kNbrFar = -1.0e18f;
 
 struct SmemLayout {
-  int lut_bytes;      // table block (16-byte multiple)
+  int lut_bytes;      // table block: lookup tables, then bands (16-byte multiple)
   int hist_bytes;     // per warp
   int queue_cap;      // per warp entries
   int queue_bytes;
@@ -43,10 +43,10 @@ struct SmemLayout {
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline SmemLayout smem_layout(int lut_words, int nslots, int R, int HP,
-                                                  bool weighted) {
+__host__ __device__ inline SmemLayout smem_layout(int lut_words, int band_words, int nslots, int R,
+                                                  int HP, bool weighted) {
   SmemLayout s;
-  s.lut_bytes = align16(lut_words * 4);
+  s.lut_bytes = align16(lut_words * 4) + align16(band_words * 8);
   s.hist_bytes = align16(nslots * R * 4);
   if (weighted) s.hist_bytes += align16(nslots * 32 * 8) + align16(nslots * 8);
   s.queue_cap = 32 + 32 * HP * 2;  // checked every 2 neighbours
@@ -67,10 +67,11 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// table lookup; MODE fixed per instantiation of the inner loop
+// table lookup; MODE fixed per instantiation of the inner loop.  v is
+// clamped to the table's range in place (NaN becomes vmax).
 template <int MODE>
-__device__ __forceinline__ uint32_t lut_get(const uint32_t *lut, const AxisPlan &a, float v) {
-  v = fminf(v, a.vmax);  // also maps NaN to vmax
+__device__ __forceinline__ uint32_t lut_get(const uint32_t *lut, const AxisPlan &a, float &v) {
+  v = fminf(v, a.vmax);
   unsigned idx;
   if (MODE == kLutLinear) {
     float t = __fmaf_rn(v, a.scale, 8388608.0f);
@@ -80,6 +81,31 @@ __device__ __forceinline__ uint32_t lut_get(const uint32_t *lut, const AxisPlan 
     idx = (unsigned)max(i, 0);
   }
   return lut[a.lut_off + idx];
+}
+
+// Slot byte offset of value v on an axis whose bands are (lo, hi) pairs;
+// near is set when v lies inside the error band of the cell's edge.
+__device__ __forceinline__ uint32_t axis_resolve(const float2 *band, const AxisPlan &a, float v,
+                                                 uint32_t e, uint32_t stride, bool &near) {
+  const uint32_t b = e >> kBandShift;
+  uint32_t off = e & kOffMask;
+  float2 bd = make_float2(__int_as_float(0x7f800000), __int_as_float(0x7f800000));
+  if (b != 0u) bd = band[a.band_off + b];
+  const bool above = v > bd.y;
+  near = (v >= bd.x) && !above;
+  return above ? off + stride : off;
+}
+
+// The same for mu: the band holds the edge, the bound comes from the r slot.
+__device__ __forceinline__ uint32_t mu_resolve(const float2 *band, const AxisPlan &a, float mu,
+                                               uint32_t e, uint32_t stride, float eps, bool &near) {
+  const uint32_t b = e >> kBandShift;
+  uint32_t off = e & kOffMask;
+  float m = __int_as_float(0x7f800000);
+  if (b != 0u) m = band[a.band_off + b].x;
+  const float d = __fsub_rn(mu, m);
+  near = fabsf(d) <= eps;
+  return (d > eps) ? off + stride : off;
 }
 
 // ---- canonical FP64 formulas (identical arithmetic to the definition; no
@@ -151,51 +177,6 @@ __device__ int slot64(const KParams &p, const PairDev &pd, int i, int j) {
     }
     return (br + 1) * p.slots1 + bm + 1;
   }
-}
-
-// ---- refine a dirty entry on one axis: slot >= 0, or -1 for the FP64 re-test
-__device__ __forceinline__ int axis_refine(const KParams &p, int axis, float v, uint32_t e,
-                                           bool mu) {
-  const AxisPlan &a = p.ax[axis];
-  const uint32_t stride = (axis == 0) ? (uint32_t)p.slots1 * p.R * 4u : (uint32_t)p.R * 4u;
-  if (e < kDirty) return (int)(e / stride);
-  if (e & kAlways) return -1;
-  int k = (int)((e >> 8) & 0xFFFFu);
-  if (e & 0x2u) return k;  // r slot decided, mu to be decided explicitly
-  float lo = p.band[a.band_off + 2 * k], hi = p.band[a.band_off + 2 * k + 1];
-  int cnt;
-  if (v < lo) cnt = k;
-  else if (v > hi) cnt = k + 1;
-  else return -1;
-  if (mu) return cnt;
-  return (cnt >= 1 && cnt <= a.nb) ? cnt : 0;
-}
-
-// mu slot for r slot s0 (R_MU); -1 for the FP64 re-test
-__device__ __forceinline__ int mu_decide(const KParams &p, float mu, uint32_t e1, int s0,
-                                         float eps_main) {
-  float eps = p.mu_eps[s0];
-  if (eps >= 4.0f) return -1;
-  const int n1 = p.n1;
-  int b;  // candidate bin from the table
-  if (e1 < kDirty) {
-    b = (int)(e1 / ((uint32_t)p.R * 4u)) - 1;
-    if (eps <= eps_main) return b + 1;  // the table was built for this bound
-  } else {
-    if (e1 & kAlways) return -1;
-    int k = (int)((e1 >> 8) & 0xFFFFu);
-    b = (mu < p.mu_edge[k]) ? k - 1 : k;
-  }
-  // the decision edges next to bin b must be clear of mu by eps
-  if (b >= 1) {
-    float m = p.mu_edge[b];
-    if (mu >= __fsub_rd(m, eps) && mu <= __fadd_ru(m, eps)) return -1;
-  }
-  if (b + 1 <= n1 - 1) {
-    float m = p.mu_edge[b + 1];
-    if (mu >= __fsub_rd(m, eps) && mu <= __fadd_ru(m, eps)) return -1;
-  }
-  return b + 1;
 }
 
 }  // namespace cute

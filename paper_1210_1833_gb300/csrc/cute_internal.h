@@ -16,13 +16,19 @@ namespace cute {
 
 // ------------------------------------------------------------------ binning
 // Each binning axis maps an FP32 value v (a squared separation, or mu) to a
-// cell of a lookup table; the table entry is either the byte offset of the
-// histogram slot the pair belongs to ("clean" cell: every value in the cell,
-// widened by the proven FP32 error bound, lies strictly between the same two
-// edges) or a DIRTY marker naming the one edge whose error band meets the
-// cell.  Slot 0 of each axis collects out-of-range pairs; bin b is slot b+1.
-constexpr uint32_t kDirty = 0x40000000u;   // entry >= kDirty: refine
-constexpr uint32_t kAlways = 0x1u;         // with kDirty: always FP64 re-test
+// cell of a lookup table.  Every axis has slots 0..nb+1: slot 0 below the
+// first edge, slot b+1 for bin b, slot nb+1 above the last edge (0 and nb+1
+// collect out-of-range pairs and are never reported).  A table entry holds
+// the byte offset of a histogram slot (bits 0..19) and a band index (bits
+// 20..31).  Band 0: the cell is CLEAN -- every value in it, widened by the
+// proven FP32 error bound, lies strictly between the same two edges, so the
+// offset is the pair's slot.  Band k+1: the cell meets the error band of edge
+// k only; the offset is the slot just below edge k, values above the band
+// take the next slot, values inside it are re-tested in FP64.  The last band
+// index of an axis marks cells that always go to FP64.
+constexpr uint32_t kOffMask = 0xFFFFu;     // slot byte offset (bits 0..15)
+constexpr int kClassShift = 16;            // R_MU r entries: mu error class (bits 16..19)
+constexpr int kBandShift = 20;             // band index (bits 20..31)
 constexpr int kLutLinear = 0;              // idx = rne(v * scale)
 constexpr int kLutLog = 1;                 // idx = max((bits(v) >> shift) - base, 0)
 
@@ -35,8 +41,8 @@ struct AxisPlan {
   int base = 0;       // log mode
   int lut_off = 0;    // word offset of this axis in the table block
   int nb = 0;         // bins on the axis
-  int band_off = 0;   // offset (floats) of this axis's (lo, hi) band pairs
-  int decision_lo = 0;  // first edge index that is a decision boundary
+  int band_off = 0;   // float2 offset of this axis's bands in the band table
+  int nband = 0;      // bands of this axis (nb + 3: none, one per edge, always)
 };
 
 // Kinds as the kernels see them.
@@ -74,20 +80,20 @@ struct KParams {
   const uint32_t *lut;         // table words, all axes
   int lut_words;
   AxisPlan ax[2];
-  const float *band;           // (lo, hi) per edge per axis, FP32, outward rounded
-  const float *mu_eps;         // per r slot: FP32 error bound of mu (R_MU)
-  const float *mu_edge;        // FP32 mu edges (R_MU)
+  const float2 *band;          // (lo, hi) per band, both axes, FP32, outward rounded;
+                               // mu bands hold (edge, edge)
+  int band_words;              // float2 entries in band
+  float mu_eps_base;           // R_MU: mu error bound of class 0 (class c: x 2^c)
   const double *E0, *E1;       // FP64 squared edges (mu: squared mu edges)
   int n0, n1;                  // bins per axis (n1 = 1 for 1-D kinds)
-  int slots1;                  // axis-1 slots (n1 + 1), 1 for 1-D kinds
-  int nslots;                  // (n0 + 1) * slots1
+  int slots1;                  // axis-1 slots (n1 + 2), 1 for 1-D kinds
+  int nslots;                  // (n0 + 2) * slots1
   int R;                       // histogram copies per warp (power of 2, <= 32)
   int slice;                   // neighbour objects per work item
-  float eps_main;              // R_MU: mu error bound the mu table was built for
   unsigned long long *out_counts;  // [nout][n0 * n1]
   double *out_wsum;                // [nout][n0 * n1] or null
   unsigned long long *ticket;      // work-item counter
-  unsigned long long *stats;       // [0] rechecked pairs, [1] items run
+  unsigned long long *stats;       // [0] rechecked pairs, [1] items run, [2] refined pairs
   int *err;                        // first error code seen by a kernel
   // adjoint
   const double *G;                 // [n0 * n1] upstream gradient
@@ -185,16 +191,15 @@ struct Plan {
   int n0 = 0, n1 = 1;
   int slots1 = 1, nslots = 0;
   int R = 1;
-  float eps_main = 0;               // R_MU: mu bound of the mu table
   AxisPlan ax[2];
   std::vector<uint32_t> lut;        // all axes
-  std::vector<float> band;          // (lo, hi) per edge per axis
-  std::vector<float> mu_eps;        // per r slot
-  std::vector<float> mu_edge;       // FP32 mu edges
+  std::vector<float> band;          // (lo, hi) per band, both axes
+  float mu_eps_base = 0;            // R_MU
   std::vector<double> E0, E1;       // FP64 squared edges
+  double dirty_frac[2] = {0, 0};    // expected fraction of pairs in dirty cells
   // device copies
   uint32_t *d_lut = nullptr;
-  float *d_band = nullptr, *d_mu_eps = nullptr, *d_mu_edge = nullptr;
+  float *d_band = nullptr;
   double *d_E0 = nullptr, *d_E1 = nullptr;
   ~Plan();
 };

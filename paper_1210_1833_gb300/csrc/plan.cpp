@@ -50,8 +50,6 @@ static float bitsf(uint32_t u) {
 Plan::~Plan() {
   cudaFree(d_lut);
   cudaFree(d_band);
-  cudaFree(d_mu_eps);
-  cudaFree(d_mu_edge);
   cudaFree(d_E0);
   cudaFree(d_E1);
 }
@@ -131,7 +129,7 @@ static int slot_of(const AxisSpec &a, double v) {
   int cnt = 0;
   for (size_t k = 0; k < a.E.size(); k++)
     if (a.E[k] <= v) cnt++;
-  return (cnt >= 1 && cnt <= a.nb) ? cnt : 0;
+  return cnt;  // 0: below the first edge, nb+1: at or above the last
 }
 
 static double dens_int(double p, double a, double b) {
@@ -246,11 +244,12 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
                        const ErrorParams &ep, int lut_budget_words, size_t hist_budget_bytes,
                        Plan &out) {
   const bool two_d = (kind == KRMU || kind == KSIGPI);
+  if (n0 + 3 > 4095 || (two_d && n1 + 3 > 4095)) return "too many bins on one axis";
   out.kind = kind;
   out.n0 = n0;
   out.n1 = two_d ? n1 : 1;
-  out.slots1 = two_d ? n1 + 1 : 1;
-  out.nslots = (n0 + 1) * out.slots1;
+  out.slots1 = two_d ? n1 + 2 : 1;
+  out.nslots = (n0 + 2) * out.slots1;
   // copies of the per-warp histogram: as many (<= 32, power of 2) as fit
   int R = 32;
   while (R > 1 && (size_t)out.nslots * R * 4 > hist_budget_bytes) R >>= 1;
@@ -290,52 +289,48 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
     if (kind == KTHETA) A0.density_p = 0.0;  // chord^2 of pairs on a sphere
   }
 
-  // mu: FP32 mu = |s.l| * rsqrt((s.s)(l.l)).  |d mu| <= 2 sqrt3 (eta_s/r +
-  // eta_l/|l|) from the perturbed unit vectors, plus 20 u of FP32 rounding
-  // (dot products, product, rsqrtf's documented 2 ulp, final product), plus
-  // the FP32 rounding of the edge and the FP64 canonical rounding; doubled.
-  std::vector<double> eps_slot;  // per r slot (n0 + 1), slot 0 unused
-  double eps_main = 0;
-  std::vector<int> always_slot;
+  // mu: FP32 mu = |sl| * rsqrt(r^2 l^2) with sl = 2 s.x_i + r^2 and
+  // l^2 = 4|x_i|^2 + 4 s.x_i + r^2 (l = 2 x_i + s).  |d mu| <= 2 sqrt3
+  // (eta_s/r + eta_l/|l|) from the perturbed unit vectors, plus 40 u of FP32
+  // rounding (dot products, sums, rsqrtf's documented 2 ulp, final product,
+  // the kernel's subtraction of the edge), plus the FP64 canonical rounding;
+  // doubled.  The bound grows as 1/r: each r slot carries an error class c
+  // (bound = base * 2^c, base = the bound at r_max), r slots below
+  // r_floor = max(first nonzero edge, r_max / 40) are always re-tested in
+  // FP64, and the mu table is classified with the largest bound in use.
+  std::vector<int> always_slot(n0 + 2, 0), cls_slot(n0 + 2, 0);
   if (kind == KRMU) {
+    double lterm = (ep.lmin > 0) ? ep.eta_l / ep.lmin : INFINITY;
+    auto eps_at = [&](double r) {
+      return r > 0 ? 2.0 * (2.0 * std::sqrt(3.0) * ((ep.eta0 + kU * r) / r + lterm) + 40 * kU) + 1e-12
+                   : INFINITY;
+    };
+    double r_floor = e0[n0] / 40.0;
+    for (int k = 1; k <= n0; k++)
+      if (e0[k] > 0) { r_floor = std::max(r_floor, e0[k]); break; }
     double minw = 1.0;
     for (int k = 0; k < n1; k++) minw = std::min(minw, e1[k + 1] - e1[k]);
-    eps_slot.assign(n0 + 1, 0.0);
-    always_slot.assign(n0 + 1, 0);
-    double lterm = (ep.lmin > 0) ? ep.eta_l / ep.lmin : INFINITY;
+    const float base = f32_up(eps_at(e0[n0]));
+    out.mu_eps_base = base;
+    double eps_max = base;
     for (int b = 0; b < n0; b++) {
-      double r = e0[b];
-      double e = (r > 0) ? 2.0 * (2.0 * std::sqrt(3.0) * ((ep.eta0 + kU * r) / r + lterm) + 20 * kU) +
-                               kU + 1e-12
-                         : INFINITY;
-      eps_slot[b + 1] = e;
-      if (!(e < 0.25 * minw)) always_slot[b + 1] = 1;
+      if (e0[b] < r_floor) { always_slot[b + 1] = 1; continue; }
+      double e = eps_at(e0[b]);
+      int c = 0;
+      while (c < 15 && (double)base * std::ldexp(1.0, c) < e) c++;
+      if ((double)base * std::ldexp(1.0, c) < e) { always_slot[b + 1] = 1; continue; }
+      cls_slot[b + 1] = c;
+      eps_max = std::max(eps_max, (double)base * std::ldexp(1.0, c));
     }
-    // the table is built for the bound of the slots holding most pairs
-    // (r >= max(first edge, 0.2 r_max)); smaller-r slots refine mu explicitly
-    double rsplit = std::max(e0[1], 0.2 * e0[n0]);
-    for (int b = 0; b < n0; b++)
-      if (e0[b] >= rsplit && !always_slot[b + 1]) eps_main = std::max(eps_main, eps_slot[b + 1]);
-    if (eps_main == 0) eps_main = 1e-7;
-    // one FP32 value serves the table, the host flags and the kernel test
-    out.eps_main = f32_up(eps_main);
-    eps_main = (double)out.eps_main;
+    if (!(eps_max < 0.25 * minw)) return "mu error bound too wide for the mu bins";
     A1.mu = true;
     A1.E.assign(e1, e1 + n1 + 1);
     A1.nb = n1;
     for (int k = 1; k < n1; k++) A1.decision.push_back(k);
     A1.vtop = 1.0;
     A1.err.constant = true;
-    A1.err.cst = eps_main;
+    A1.err.cst = eps_max;
     A1.density_p = 0.0;
-    out.mu_eps.assign(n0 + 1, 0.0f);
-    for (int s = 1; s <= n0; s++)
-      out.mu_eps[s] = std::isfinite(eps_slot[s]) ? f32_up(eps_slot[s]) : 4.0f;
-    out.mu_edge.resize(n1 + 1);
-    for (int k = 0; k <= n1; k++) out.mu_edge[k] = (float)e1[k];
-  } else {
-    out.mu_eps.assign(1, 0.0f);
-    out.mu_edge.assign(1, 0.0f);
   }
 
   int budget0 = two_d ? lut_budget_words / 2 : lut_budget_words;
@@ -345,49 +340,77 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
     T1 = best_table(A1, lut_budget_words - T0.p.ncell);
     if (T1.p.ncell == 0) return "could not build the axis-1 lookup table";
   }
+  out.dirty_frac[0] = T0.dirty_frac;
+  out.dirty_frac[1] = two_d ? T1.dirty_frac : 0.0;
 
-  // entries: byte offsets of histogram slots, or dirty markers
-  const uint32_t stride0 = (uint32_t)out.slots1 * R * 4, stride1 = (uint32_t)R * 4;
-  auto encode = [&](AxisTable &t, uint32_t stride) {
-    for (int c = 0; c < t.p.ncell; c++) {
-      if (t.edge[c] == -1) t.cells[c] = (uint32_t)t.slot[c] * stride;
-      else if (t.edge[c] == -2) t.cells[c] = kDirty | kAlways;
-      else t.cells[c] = kDirty | ((uint32_t)t.edge[c] << 8);
-    }
-  };
-  encode(T0, stride0);
-  if (kind == KRMU) {
-    // r cells whose slot needs an explicit mu decision (eps > eps_main) or a
-    // full FP64 re-test (mu bound too wide) are flagged
-    for (int c = 0; c < T0.p.ncell; c++) {
-      if (T0.edge[c] != -1) continue;
-      int s = T0.slot[c];
-      if (s <= 0) continue;
-      if (always_slot[s]) T0.cells[c] = kDirty | kAlways;
-      else if (eps_slot[s] > eps_main) T0.cells[c] = kDirty | 0x2u | ((uint32_t)s << 8);
-    }
-  }
-  if (two_d) encode(T1, stride1);
-
-  // bands per decision edge (FP32, rounded outward), for the refine path
+  // bands: index 0 none (never near, never above), k+1 for edge k,
+  // nb+2 always near; FP32, rounded outward.  mu bands hold the FP32 edge
+  // twice: the kernel compares |mu - edge| with the pair's r-slot bound.
   out.band.clear();
   auto bands = [&](const AxisSpec &a, AxisPlan &p) {
-    p.band_off = (int)out.band.size();
-    for (size_t k = 0; k < a.E.size(); k++) {
+    p.band_off = (int)out.band.size() / 2;
+    p.nband = a.nb + 3;
+    out.band.push_back(INFINITY);
+    out.band.push_back(INFINITY);
+    for (int k = 0; k <= a.nb; k++) {
       double lo = 0, hi = 0;
-      bool dec = std::find(a.decision.begin(), a.decision.end(), (int)k) != a.decision.end();
-      if (dec && !a.err.constant) edge_band(a, (int)k, lo, hi);
-      else { lo = a.E[k]; hi = a.E[k]; }
+      bool dec = std::find(a.decision.begin(), a.decision.end(), k) != a.decision.end();
+      if (!dec) {
+        out.band.push_back(INFINITY);  // not a decision edge: never met
+        out.band.push_back(INFINITY);
+        continue;
+      }
+      if (a.mu) {
+        out.band.push_back((float)a.E[k]);
+        out.band.push_back((float)a.E[k]);
+        continue;
+      }
+      edge_band(a, k, lo, hi);
       out.band.push_back(f32_down(lo));
       out.band.push_back(f32_up(hi));
     }
+    out.band.push_back(-INFINITY);
+    out.band.push_back(INFINITY);
   };
   bands(A0, T0.p);
   T0.p.nb = n0;
   if (two_d) {
     bands(A1, T1.p);
     T1.p.nb = n1;
+    if (kind == KRMU)
+      for (int c = 0; c < T1.p.ncell; c++)
+        if (T1.edge[c] == -2) return "mu table too coarse for the mu bins";
   }
+
+  // entries
+  const uint32_t stride0 = (uint32_t)out.slots1 * R * 4, stride1 = (uint32_t)R * 4;
+  if ((size_t)out.nslots * R * 4 > kOffMask) return "histogram too large";
+  auto encode = [&](const AxisSpec &a, AxisTable &t, uint32_t stride, bool rmu_r) {
+    const uint32_t always_band = (uint32_t)(a.nb + 2) << kBandShift;
+    for (int c = 0; c < t.p.ncell; c++) {
+      if (t.edge[c] == -2) {
+        t.cells[c] = always_band;
+      } else if (t.edge[c] == -1) {
+        int sl = t.slot[c];
+        t.cells[c] = (uint32_t)sl * stride;
+        if (rmu_r && sl >= 1 && sl <= a.nb) {
+          if (always_slot[sl]) t.cells[c] = always_band;
+          else t.cells[c] |= (uint32_t)cls_slot[sl] << kClassShift;
+        }
+      } else {
+        int k = t.edge[c];
+        int below = k, above = k + 1;  // slots on either side of edge k
+        t.cells[c] = ((uint32_t)(k + 1) << kBandShift) | ((uint32_t)below * stride);
+        if (rmu_r) {
+          int lo = std::min(below, a.nb + 1), hi = std::min(above, a.nb + 1);
+          if (always_slot[lo] || always_slot[hi]) t.cells[c] = always_band;
+          else t.cells[c] |= (uint32_t)std::max(cls_slot[lo], cls_slot[hi]) << kClassShift;
+        }
+      }
+    }
+  };
+  encode(A0, T0, stride0, kind == KRMU);
+  if (two_d) encode(A1, T1, stride1, false);
 
   out.lut.clear();
   T0.p.lut_off = 0;
