@@ -8,9 +8,12 @@ Landy-Szalay estimator.  Synthetic, seeded (paper_1210_1833_gb300.synthetic).
 
 One step = the whole hot path: catalog upload/conversion, cell-grid build
 for both catalogs, the DD, DR and RR counting kernels, and the estimator.
-`value` is candidate pairs examined per second with the catalogs already in
-HBM; `e2e` is the same step through the public API from pinned host memory
-with the xi read back.  L2 is flushed between timed steps.
+`value` is pairs binned per second (pairs that fall in a bin of DD, DR or
+RR) with the catalogs already in HBM; it does not depend on how many
+candidate pairs the neighbour search examines.  The roofline is taken on the
+candidate pairs the dominant kernel examines.  `e2e` is the same step
+through the public API from pinned host memory with the xi read back.  L2 is
+flushed between timed steps.
 
 --impl reference times the FP64 CPU oracle (the parity reference) on a
 bounded sample of the same workload on the host cores.
@@ -32,10 +35,14 @@ sys.path.insert(0, ROOT)
 from paper_1210_1833_gb300 import synthetic  # noqa: E402
 
 METRIC = "pairs/s & % FP32 roofline; batched/adjoint vs plain kernel, counts exact"
-# FP32-pipe operations per candidate pair in the (r, mu) kernel's fast path:
-# s (3 FADD), l (3 FADD), r^2, l^2, s.l (3 each: FMUL + 2 FFMA), den (FMUL),
-# mu (FMUL), two clamps (FMNMX), two table indices (FFMA).
-I_PAIR_RMU = 21
+# FP32-pipe operations per candidate pair in the (r, mu) kernel with uniform
+# edges (arithmetic binning): s (3 FADD), r^2 (3), s.x_i (3), s.l (1 FFMA),
+# l.l (FADD + FFMA), guard add (1), r^2 l^2 (1), mu (1), r (1); per axis
+# t (FFMA), clamp (2 FMNMX), round (FADD), floor (FADD), offset (FADD) = 6 x 2;
+# mu bound (FFMA), two band sums (FADD), max (FMNMX), compare (FSETP) = 5.
+# Not counted: the 2 MUFU rsqrt, 2 IMAD slot offsets, the select and the
+# shared-memory atomic.
+I_PAIR_RMU = 34
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -105,7 +112,7 @@ def total_pairs(nd, nr):
 def cpu_oracle_rate(w, target_s=12.0, seed=0):
     """The oracle (brute force, every pair examined) on a bounded sample of the
     workload's pairs: a seeded subset of data rows against all randoms (DR).
-    Returns (pairs/s, threads, sample description)."""
+    Returns (binned pairs/s, threads, sample description)."""
     import oracle
     nthr = oracle.max_threads()
     rows = 64
@@ -113,15 +120,17 @@ def cpu_oracle_rate(w, target_s=12.0, seed=0):
     while True:
         sub = synthetic.subsample(w.data, rows, seed)
         t0 = time.perf_counter()
-        oracle.count(w.kind, sub, w.randoms, edges0=w.edges0, edges1=w.edges1,
-                     periodic=w.periodic, L=w.L)
+        c, _, _ = oracle.count(w.kind, sub, w.randoms, edges0=w.edges0, edges1=w.edges1,
+                               periodic=w.periodic, L=w.L)
         t = time.perf_counter() - t0
         if t >= target_s / 3 or rows >= len(w.data):
             break
         rows = int(min(len(w.data), rows * max(2.0, min(8.0, target_s / max(t, 1e-3)))))
-    pairs = rows * len(w.randoms)
-    return pairs / t, nthr, "%d data rows x %d randoms (DR, brute force, %.1f s)" % (
-        rows, len(w.randoms), t)
+    binned = int(c.sum())
+    return binned / t, nthr, ("%d data rows x %d randoms (DR, brute force: %d pairs examined, "
+                              "%d binned, %.1f s; %.3g examined pairs/s)" % (
+                                  rows, len(w.randoms), rows * len(w.randoms), binned, t,
+                                  rows * len(w.randoms) / t))
 
 
 def run_reference(args, w, rank, world):
@@ -165,12 +174,13 @@ def run_gpu(args, w, rank, world):
     d_pin = torch.from_numpy(w.data).pin_memory()
     r_pin = torch.from_numpy(w.randoms).pin_memory()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")  # 256 MB
-    state = {"cand": 0, "kms": [], "rr_cand": 0, "rr_ms": [], "inrange": 0, "rechecked": 0}
+    state = {"cand": 0, "kms": [], "rr_cand": 0, "rr_ms": [], "inrange": 0, "rechecked": 0,
+             "slots": 0, "per": {}}
 
     def step(dsrc, rsrc, record):
         cd = ctx.upload(dsrc)
         cr = ctx.upload(rsrc)
-        ctx.grid([cd, cr], reach)
+        ctx.grid([cd, cr], reach, args.cpr)
         res = {}
         for name, a, b in (("DD", cd, None), ("DR", cd, cr), ("RR", cr, None)):
             if args.only and name not in args.only.split(","):
@@ -182,7 +192,9 @@ def run_gpu(args, w, rank, world):
                 st = ctx.stats()
                 state["cand"] += st["candidate_pairs"]
                 state["kms"].append(st["kernel_ms"])
+                state["per"].setdefault(name, []).append(st["kernel_ms"])
                 state["rechecked"] += st["rechecked_pairs"]
+                state["slots"] += st["pair_slots"]
                 state["inrange"] += int(c.sum())
                 if name == "RR":
                     state["rr_cand"] = st["candidate_pairs"]
@@ -223,8 +235,9 @@ def run_gpu(args, w, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms, ms_e2e = float(t[0]), float(t[1])
     cand_per_step = state["cand"] / args.steps
-    value = world * cand_per_step / (ms / 1e3)
-    e2e_value = world * cand_per_step / (ms_e2e / 1e3)
+    inrange_per_step = state["inrange"] / args.steps
+    value = world * inrange_per_step / (ms / 1e3)
+    e2e_value = world * inrange_per_step / (ms_e2e / 1e3)
     if rank != 0:
         return
     pk, src = peaks()
@@ -246,13 +259,16 @@ def run_gpu(args, w, rank, world):
         "config": {"workload": w.name, "kind": "rmu", "n_data": nd, "n_randoms": nr,
                    "bins": [len(w.edges0) - 1, len(w.edges1) - 1], "counts": ["DD", "DR", "RR"],
                    "estimator": "landy-szalay", "l2": "flushed between steps (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "cells_per_reach": args.cpr},
         "pairs": {"candidate_per_step": cand_per_step,
-                  "in_range_per_step": state["inrange"] / args.steps,
+                  "in_range_per_step": inrange_per_step,
                   "all_pairs_per_step": total_pairs(nd, nr),
-                  "in_range_pairs_per_s": world * state["inrange"] / args.steps / (ms / 1e3),
+                  "candidate_pairs_per_s": world * cand_per_step / (ms / 1e3),
                   "all_pairs_per_s": world * total_pairs(nd, nr) / (ms / 1e3),
+                  "count_kernel_ms": {k: float(np.mean(v)) for k, v in state["per"].items()},
                   "rechecked_fraction": state["rechecked"] / max(1, state["cand"]),
+                  "slot_utilisation": state["cand"] / max(1, state["slots"]),
                   "count_kernel_ms_per_step": float(np.sum(state["kms"])) / args.steps},
         "roofline": {"bound": "alu", "kernel": "k_count<R_MU> (RR)", "achieved": achieved,
                      "peak": peak_tinst, "unit": "Tinst/s", "frac": achieved / peak_tinst,
@@ -281,6 +297,7 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1 = full size)")
     ap.add_argument("--only", default="", help="profiling: run only these counts (e.g. RR)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle sample")
+    ap.add_argument("--cpr", type=int, default=3, help="cells per reach of the grid")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -172,8 +172,8 @@ cute_status cute_count_pairs_adjoint(cute_ctx *ctx, const cute_pair_desc *d, con
 typedef struct {
   uint64_t candidate_pairs; /* pairs examined by the FP32 path              */
   uint64_t rechecked_pairs; /* of those, re-tested in FP64 near an edge     */
-  uint64_t refined_pairs;   /* pairs in a dirty table cell, refined against
-                               the edge's FP32 error band                   */
+  uint64_t pair_slots;      /* (home, neighbour) slots the kernel evaluated,
+                               including empty and padding slots            */
   uint64_t work_items;      /* (home chunk, neighbour slice) items run      */
   int32_t launches;         /* kernels launched by the call                 */
   int32_t warps_per_block, blocks, home_per_lane;
@@ -186,12 +186,14 @@ cute_status cute_last_stats(cute_ctx *ctx, cute_stats *out);
    (adds two events per call; off by default). */
 cute_status cute_set_timing(cute_ctx *ctx, int32_t on);
 
-/* Launch shape override for the counting kernel: home_per_lane in {1,2,4}
+/* Launch shape override for the counting kernel: home_per_lane in {2, 4}
    (objects of A held per lane; 0 = library default), warps_per_block
    (0 = largest that fits), slice (neighbour objects per work item, 0 =
-   default, multiple of 64).  Used by the autotuner. */
+   default, multiple of 64).  table_binning = 1 bins through lookup tables
+   even when the edges are uniform (0 = arithmetic binning for uniform
+   edges).  Used by the autotuner and by tests of both binning paths. */
 cute_status cute_set_launch(cute_ctx *ctx, int32_t home_per_lane, int32_t warps_per_block,
-                            int32_t slice);
+                            int32_t slice, int32_t table_binning);
 
 /* ---------------------------------------------------------------- estimators
    Host FP64 arithmetic on exact counts (Sec. 2.2).  Counts are unique pairs.

@@ -223,7 +223,8 @@ cute_status cute_set_timing(cute_ctx *ctx, int32_t on) {
   return CUTE_OK;
 }
 
-cute_status cute_set_launch(cute_ctx *ctx, int32_t hp, int32_t warps, int32_t slice) {
+cute_status cute_set_launch(cute_ctx *ctx, int32_t hp, int32_t warps, int32_t slice,
+                            int32_t table_binning) {
   ENTER(ctx);
   if (hp != 0 && hp != 2 && hp != 4) return fail(ctx, CUTE_E_INVALID, "home_per_lane must be 0, 2 or 4");
   if (warps < 0 || warps > 16) return fail(ctx, CUTE_E_INVALID, "warps_per_block must be 0..16");
@@ -231,6 +232,7 @@ cute_status cute_set_launch(cute_ctx *ctx, int32_t hp, int32_t warps, int32_t sl
   ctx->hp_override = hp;
   ctx->warps_override = warps;
   ctx->slice_override = slice;
+  ctx->table_binning = table_binning != 0;
   return CUTE_OK;
 }
 
@@ -238,11 +240,11 @@ cute_status cute_last_stats(cute_ctx *ctx, cute_stats *out) {
   ENTER(ctx);
   if (!out) return fail(ctx, CUTE_E_INVALID, "out is NULL");
   CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
-  unsigned long long h[4] = {0, 0, 0, 0};
+  unsigned long long h[5] = {0, 0, 0, 0, 0};
   CUDA_OR_FAIL(cudaMemcpy(h, ctx->d_ticket, sizeof(h), cudaMemcpyDeviceToHost));
   ctx->stats.rechecked_pairs = h[1];
   ctx->stats.work_items = h[2];
-  ctx->stats.refined_pairs = h[3];
+  ctx->stats.pair_slots = h[4];
   if (ctx->timing && ctx->stats.launches > 0) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->stats.kernel_ms = ms;
@@ -336,7 +338,8 @@ cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &
                      std::shared_ptr<Plan> &out) {
   std::ostringstream key;
   key.precision(17);
-  key << d->kind << "|" << ep.eta0 << "|" << ep.eta_l << "|" << ep.lmin << "|" << hp << "|";
+  key << d->kind << "|" << ep.eta0 << "|" << ep.eta_l << "|" << ep.lmin << "|" << hp << "|"
+      << ctx->table_binning << "|";
   for (int k = 0; k <= d->n0; k++) key << d->edges0[k] << ",";
   if (d->kind == CUTE_R_MU || d->kind == CUTE_SIGMA_PI)
     for (int k = 0; k <= d->n1; k++) key << d->edges1[k] << ",";
@@ -348,7 +351,7 @@ cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &
   auto P = std::make_shared<Plan>();
   const bool two_d = (d->kind == CUTE_R_MU || d->kind == CUTE_SIGMA_PI);
   std::string m = plan_build((int)d->kind, d->edges0, d->n0, d->edges1, two_d ? d->n1 : 1, ep,
-                             two_d ? 8192 : 8192, 12288, *P);
+                             two_d ? 8192 : 8192, 12288, !ctx->table_binning, *P);
   if (!m.empty()) return fail(ctx, CUTE_E_UNSUPPORTED, m);
   auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
     cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
@@ -367,9 +370,11 @@ cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &
 cute_status get_tasks(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, int slice,
                       bool full_stencil, std::shared_ptr<TaskSet> &out) {
   std::ostringstream key;
+  key.precision(17);
   key << hp << "|" << slice << "|" << full_stencil << "|";
   for (const DescInfo &di : dis)
-    key << di.A->id << ":" << di.A->grid_version << ":" << di.B->id << ":" << di.B->grid_version << ",";
+    key << di.A->id << ":" << di.A->grid_version << ":" << di.B->id << ":" << di.B->grid_version
+        << ":" << di.kind << ":" << di.need[0] << ":" << di.need[1] << ":" << di.need[2] << ",";
   auto it = ctx->task_cache.find(key.str());
   if (it != ctx->task_cache.end()) {
     out = it->second;
@@ -391,8 +396,9 @@ cute_status get_tasks(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, i
     pd.L64 = di.g->periodic ? di.g->L : 0.0;
     T->pairs.push_back(pd);
     if (di.A->n == 0 || di.B->n == 0) continue;
+    const int shape = (di.kind == CUTE_SIGMA_PI) ? kShapeDiskSlab : kShapeBall;
     tasks_build(*di.g, di.A->h_cell_start, di.B->h_cell_start, di.is_auto, (int)i, 32 * hp, slice,
-                full_stencil, T->tasks, T->candidates);
+                full_stencil, shape, di.need, T->tasks, T->candidates);
   }
   T->prefix.resize(T->tasks.size() + 1);
   T->prefix[0] = 0;
@@ -423,12 +429,17 @@ struct Prepared {
 };
 
 cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, bool weighted, bool full_stencil,
-                    Prepared &pr) {
+                    Prepared &pr, bool allow_swap = true) {
   if (n < 1 || !d) return fail(ctx, CUTE_E_INVALID, "no descriptors");
   pr.dis.resize(n);
   for (int i = 0; i < n; i++) {
     cute_status st = validate_desc(ctx, &d[i], pr.dis[i]);
     if (st != CUTE_OK) return st;
+    // every separation measure is symmetric in the pair (bit for bit: the
+    // canonical separation only changes sign), so a cross count may put the
+    // larger catalog on the home side, where fuller cells fill the lanes
+    if (allow_swap && !pr.dis[i].is_auto && pr.dis[i].B->n > pr.dis[i].A->n)
+      std::swap(pr.dis[i].A, pr.dis[i].B);
     if (i > 0) {
       bool same = d[i].kind == d[0].kind && d[i].n0 == d[0].n0 && d[i].weighted == d[0].weighted &&
                   std::equal(d[i].edges0, d[i].edges0 + d[i].n0 + 1, d[0].edges0);
@@ -440,7 +451,18 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, bool weighted
     }
   }
   ErrorParams ep = error_params(pr.dis, d[0].edges0[d[0].n0]);
-  pr.hp = ctx->hp_override ? ctx->hp_override : 4;
+  // home objects per lane: 4 when home cells hold enough objects to fill
+  // 128-object chunks, else 2
+  pr.hp = ctx->hp_override;
+  if (!pr.hp) {
+    double objs = 0, cells = 0;
+    for (const DescInfo &di : pr.dis) {
+      const std::vector<int32_t> &cs = di.A->h_cell_start;
+      for (size_t c = 0; c + 1 < cs.size(); c++)
+        if (cs[c + 1] > cs[c]) { objs += cs[c + 1] - cs[c]; cells += 1; }
+    }
+    pr.hp = (cells > 0 && objs / cells < 96.0) ? 2 : 4;
+  }
   cute_status st = get_plan(ctx, &d[0], ep, pr.hp, pr.plan);
   if (st != CUTE_OK) return st;
   int slice = ctx->slice_override ? ctx->slice_override : 2048;
@@ -515,7 +537,7 @@ cute_status count_driver(cute_ctx *ctx, int n, const cute_pair_desc *d, uint64_t
   unsigned long long *d_out = (unsigned long long *)ctx->d_scratch;
   pr.p.out_counts = d_out;
   CUDA_OR_FAIL(cudaMemsetAsync(d_out, 0, out_bytes, ctx->stream));
-  CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, 4 * sizeof(unsigned long long), ctx->stream));
+  CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, 5 * sizeof(unsigned long long), ctx->stream));
   ctx->stats = cute_stats{};
   ctx->stats.candidate_pairs = pr.ts->candidates;
   ctx->stats.warps_per_block = pr.warps;

@@ -92,7 +92,37 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__r
         const float dz = __fsub_rn(q.z, h.z[s]);
         bool near;
         uint32_t o;
-        if (KIND == KMONO || KIND == KTHETA) {
+        if ((KIND == KMONO || KIND == KTHETA) && M0 == kArith) {
+          const float v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          const float x0 = __fmul_rn(v0, rsqrtf(__fadd_rn(v0, 1e-30f)));
+          float h0;
+          const float tm0 = arith_t(p.ax[0], x0, h0);
+          near = fabsf(h0) + p.ax[0].thr_b >= 0.5f;
+          o = arith_off(tm0, stride0);
+        } else if (KIND == KSIGPI && M0 == kArith) {
+          const float v0 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+          const float x0 = __fmul_rn(v0, rsqrtf(__fadd_rn(v0, 1e-30f)));
+          float h0, h1;
+          const float tm0 = arith_t(p.ax[0], x0, h0);
+          const float tm1 = arith_t(p.ax[1], fabsf(dz), h1);
+          near = fmaxf(fabsf(h0) + p.ax[0].thr_b, fabsf(h1) + p.ax[1].thr_b) >= 0.5f;
+          o = arith_off(tm0, stride0) + arith_off(tm1, stride1);
+        } else if (KIND == KRMU && M0 == kArith) {
+          // s = x_j - x_i; l = x_i + x_j = 2 x_i + s; s.l = 2 s.x_i + r^2;
+          // l.l = 4 |x_i|^2 + 4 s.x_i + r^2
+          const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          const float sx = __fmaf_rn(dz, h.az[s], __fmaf_rn(dy, h.ay[s], __fmul_rn(dx, h.ax[s])));
+          const float sl = __fmaf_rn(2.0f, sx, r2);
+          const float l2 = __fmaf_rn(4.0f, sx, __fadd_rn(h.aq[s], r2));
+          const float rr = rsqrtf(__fadd_rn(r2, 1e-30f));
+          const float mu = __fmul_rn(fabsf(sl), rsqrtf(__fmul_rn(r2, l2)));
+          float h0, h1;
+          const float tm0 = arith_t(p.ax[0], __fmul_rn(r2, rr), h0);
+          const float tm1 = arith_t(p.ax[1], mu, h1);
+          const float thr1 = __fmaf_rn(rr, p.ax[1].thr_a, p.ax[1].thr_b);
+          near = fmaxf(fabsf(h0) + p.ax[0].thr_b, __fadd_rn(fabsf(h1), thr1)) >= 0.5f;
+          o = arith_off(tm0, stride0) + arith_off(tm1, stride1);
+        } else if (KIND == KMONO || KIND == KTHETA) {
           float v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
           const uint32_t e0 = lut_get<M0>(lut, p.ax[0], v0);
           o = axis_resolve(band, p.ax[0], v0, e0, stride0, near);
@@ -165,11 +195,14 @@ __device__ __forceinline__ void tile_dispatch(const KParams &p, const uint32_t *
                                               unsigned &dc) {
   const int m0 = p.ax[0].mode;
   if (KIND == KMONO || KIND == KTHETA) {
-    if (m0 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLinear, 0>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
+    if (m0 == kArith) tile_dispatch_self<KIND, HP, kArith, 0>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
+    else if (m0 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLinear, 0>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
     else tile_dispatch_self<KIND, HP, kLutLog, 0>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
   } else {
     const int m1 = p.ax[1].mode;
-    if (m0 == kLutLinear) {
+    if (m0 == kArith) {
+      tile_dispatch_self<KIND, HP, kArith, kArith>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
+    } else if (m0 == kLutLinear) {
       if (m1 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLinear, kLutLinear>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
       else tile_dispatch_self<KIND, HP, kLutLinear, kLutLog>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
     } else {
@@ -224,7 +257,7 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
   constexpr int CH = 32 * HP;
   int cur_pair = -1;
   PairDev pd;
-  unsigned long long acc = 0, items = 0;
+  unsigned long long acc = 0, items = 0, slots = 0;
   unsigned dirty_count = 0;
   for (;;) {
     unsigned long long item = 0;
@@ -263,6 +296,7 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
     const float Sy = PER ? shift_of((code >> 2) & 3, pd.L32) : 0.0f;
     const float Sz = PER ? shift_of((code >> 4) & 3, pd.L32) : 0.0f;
     Home<HP> h;
+    slots += (unsigned long long)(32 * HP) * (unsigned long long)((je - js + 1) & ~1);
 #pragma unroll
     for (int s = 0; s < HP; s++) {
       const int idx = hs + lane + 32 * s;
@@ -320,6 +354,7 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
     flush_hist(p, w, pd.out, lane);
   }
   if (lane == 0 && items) atomicAdd(&p.stats[1], items);
+  if (lane == 0 && slots) atomicAdd(&p.stats[3], slots);
   for (int o = 16; o > 0; o >>= 1) dirty_count += __shfl_xor_sync(kFull, dirty_count, o);
   if (lane == 0 && dirty_count) atomicAdd(&p.stats[2], (unsigned long long)dirty_count);
 }

@@ -96,6 +96,23 @@ __device__ __forceinline__ uint32_t axis_resolve(const float2 *band, const AxisP
   return above ? off + stride : off;
 }
 
+// Uniform edges: t - 1/2 = x * inv + cst clamped to [tlo, thi]; returns the
+// rounded value tm = 1.5 * 2^23 + floor(t) (its bits hold the bin) and h, the
+// signed distance of t - 1/2 to that integer (|h| = 1/2 on an edge).
+constexpr float kMagic = 12582912.0f;        // 1.5 * 2^23
+constexpr uint32_t kMagicBits = 0x4B400000u;
+__device__ __forceinline__ float arith_t(const AxisPlan &a, float x, float &h) {
+  float t = __fmaf_rn(x, a.inv, a.cst);
+  t = fmaxf(fminf(t, a.thi), a.tlo);  // NaN -> thi
+  const float tm = __fadd_rn(t, kMagic);
+  h = __fsub_rn(t, __fsub_rn(tm, kMagic));
+  return tm;
+}
+// slot byte offset of the bin held in tm (slot = bin + 1)
+__device__ __forceinline__ uint32_t arith_off(float tm, uint32_t stride) {
+  return (__float_as_uint(tm) - kMagicBits + 1u) * stride;
+}
+
 // The same for mu: the band holds the edge, the bound comes from the r slot.
 __device__ __forceinline__ uint32_t mu_resolve(const float2 *band, const AxisPlan &a, float mu,
                                                uint32_t e, uint32_t stride, float eps, bool &near) {

@@ -31,6 +31,7 @@ constexpr int kClassShift = 16;            // R_MU r entries: mu error class (bi
 constexpr int kBandShift = 20;             // band index (bits 20..31)
 constexpr int kLutLinear = 0;              // idx = rne(v * scale)
 constexpr int kLutLog = 1;                 // idx = max((bits(v) >> shift) - base, 0)
+constexpr int kArith = 2;                  // uniform edges: bin = floor((x - e0) / delta)
 
 struct AxisPlan {
   int mode = 0;
@@ -43,6 +44,11 @@ struct AxisPlan {
   int nb = 0;         // bins on the axis
   int band_off = 0;   // float2 offset of this axis's bands in the band table
   int nband = 0;      // bands of this axis (nb + 3: none, one per edge, always)
+  // kArith: t = x * inv + cst (cst already holds -e0/delta - 1/2), clamped to
+  // [tlo, thi]; the bin is rint(t) and the pair is near an edge when
+  // |t - rint(t)| + thr >= 1/2, with thr = thr_a / x_r + thr_b for mu
+  // (x_r the pair's r) and thr_b alone for the other axes.
+  float inv = 0, cst = 0, tlo = 0, thi = 0, thr_a = 0, thr_b = 0;
 };
 
 // Kinds as the kernels see them.
@@ -93,7 +99,7 @@ struct KParams {
   unsigned long long *out_counts;  // [nout][n0 * n1]
   double *out_wsum;                // [nout][n0 * n1] or null
   unsigned long long *ticket;      // work-item counter
-  unsigned long long *stats;       // [0] rechecked pairs, [1] items run, [2] refined pairs
+  unsigned long long *stats;       // [0] rechecked, [1] items, [2] near-band, [3] pair slots
   int *err;                        // first error code seen by a kernel
   // adjoint
   const double *G;                 // [n0 * n1] upstream gradient
@@ -175,6 +181,7 @@ struct cute_ctx {
   size_t scratch_bytes = 0;
   // launch overrides
   int hp_override = 0, warps_override = 0, slice_override = 0;
+  bool table_binning = false;
   bool timing = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cute_stats stats{};
@@ -213,12 +220,14 @@ struct ErrorParams {
 // Build the binning plan.  hist_budget_bytes: per-warp histogram budget.
 std::string plan_build(int kind, const double *e0, int n0, const double *e1, int n1,
                        const ErrorParams &ep, int lut_budget_words, size_t hist_budget_bytes,
-                       Plan &out);
+                       bool allow_arith, Plan &out);
 
-// Task list for one pair set of catalogs on a shared geometry.
+// Task list for one pair set of catalogs on a shared geometry.  shape: the
+// region of separations that can fall in a bin, used to trim neighbour rows.
+constexpr int kShapeBox = 0, kShapeBall = 1, kShapeDiskSlab = 2;
 void tasks_build(const Geometry &g, const std::vector<int32_t> &csA,
                  const std::vector<int32_t> &csB, bool is_auto, int pair_index, int home_chunk,
-                 int slice, bool full_stencil, std::vector<Task> &out,
-                 unsigned long long &candidates);
+                 int slice, bool full_stencil, int shape, const double need[3],
+                 std::vector<Task> &out, unsigned long long &candidates);
 
 }  // namespace cute

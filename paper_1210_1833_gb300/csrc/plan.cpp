@@ -239,10 +239,82 @@ static void edge_band(const AxisSpec &a, int k, double &lo, double &hi) {
   for (int it = 0; it < 64 && lo + a.err(E) >= E; it++) lo = E - 1.01 * (E - lo) - 1e-300;
 }
 
+// ------------------------------------------------------------------ uniform edges
+// Uniform edges e_k = e_0 + k delta allow binning by arithmetic: with
+// x = sqrt(v) (or |dz|, or mu) and t = (x - e_0)/delta, the bin is floor(t).
+// The canonical decision for edge k compares the FP64 value with e_k^2, i.e.
+// x with sqrt(fl(e_k^2)), which sits within db of t = k.  The FP32 t carries
+// the error of x (from the squared value's bound err(v), the documented
+// 2 ulp of rsqrtf and the product), of the FP32 constants and of the FMA.
+static bool uniform_edges(const double *e, int n, double &delta) {
+  delta = (e[n] - e[0]) / n;
+  if (!(delta > 0)) return false;
+  for (int k = 0; k <= n; k++)
+    if (std::fabs(e[k] - (e[0] + k * delta)) > 1e-9 * delta) return false;
+  return true;
+}
+
+// ARITH parameters of a value axis (x = sqrt(v), or x = |v| when lin).
+// squared: the canonical boundaries are sqrt(fl(e_k^2)); mu: m_k itself.
+static bool make_arith(const double *e, int n, const AxisErr &err, double eta0, bool squared,
+                       bool is_mu, bool lin, AxisPlan &p) {
+  double delta;
+  if (!uniform_edges(e, n, delta)) return false;
+  const double inv = 1.0 / delta, c = -e[0] / delta;
+  double db = 0;
+  for (int k = 0; k <= n; k++) {
+    long double b = squared ? sqrtl((long double)(e[k] * e[k])) : (long double)e[k];
+    db = std::max(db, (double)fabsl((b - (long double)e[0]) / (long double)delta - k));
+  }
+  db += 1e-12 * n;
+  const float inv32 = (float)inv;
+  const float c32 = (float)(c - 0.5);
+  // rounding of the FP32 constants, per unit of x and absolute
+  const double dinv = std::fabs((double)inv32 - inv);
+  const double dc = std::fabs((double)c32 - (c - 0.5));
+  p = AxisPlan();
+  p.mode = kArith;
+  p.nb = n;
+  p.inv = inv32;
+  p.cst = c32;
+  // non-decision edges are clamped to half-integers (never near): x >= 0
+  // makes edge 0 moot when e_0 = 0, and mu never leaves [0, 1]
+  const bool lo_decides = !(is_mu || e[0] == 0.0);
+  p.tlo = lo_decides ? -1.0f : 0.0f;                // t - 1/2 >= -1  (t >= -1/2)
+  p.thi = is_mu ? (float)(n - 1) : (float)n;        // t - 1/2 <= n (mu: n - 1)
+  if (is_mu) {
+    p.thr_a = 0;  // filled by the caller (depends on the r bound)
+    p.thr_b = (float)(db + 4.0 * kU * n + dc + 1e-6);
+    return true;
+  }
+  // sup over x in [0, e_n + delta] of the error of t, in t units
+  double T = 0;
+  const double xmax = e[n] + delta;
+  for (int i = 0; i <= 4000; i++) {
+    double x = xmax * std::pow(10.0, -12.0 * (1.0 - i / 4000.0));  // log grid to xmax
+    if (i == 0) x = 0;
+    double v = x * x;
+    double dx;
+    if (lin) {
+      dx = 2.0 * (eta0 + kU * x * 1.0001);  // |dz|: the component bound, doubled
+    } else {
+      double ev = err(v);
+      dx = (x > 0) ? std::min(ev / x, std::sqrt(ev)) : std::sqrt(ev);
+    }
+    if (!lin) dx += 6.0 * kU * x + 1e-11;  // rsqrtf (2 ulp), product, tiny-value guard
+    double t = x * inv + c;
+    double Tt = dx * inv + x * dinv + dc + kU * (std::fabs(t) + 1.0) + db;
+    T = std::max(T, Tt);
+  }
+  p.thr_a = 0;
+  p.thr_b = (float)(2.0 * T + 1e-6);
+  return p.thr_b < 0.2f;
+}
+
 // ------------------------------------------------------------------ plan
 std::string plan_build(int kind, const double *e0, int n0, const double *e1, int n1,
                        const ErrorParams &ep, int lut_budget_words, size_t hist_budget_bytes,
-                       Plan &out) {
+                       bool allow_arith, Plan &out) {
   const bool two_d = (kind == KRMU || kind == KSIGPI);
   if (n0 + 3 > 4095 || (two_d && n1 + 3 > 4095)) return "too many bins on one axis";
   out.kind = kind;
@@ -287,6 +359,39 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
     A0.err.sq = SqErr{3, ep.eta0};
     A0.density_p = 0.5;   // d^2 of pairs spread in a volume
     if (kind == KTHETA) A0.density_p = 0.0;  // chord^2 of pairs on a sphere
+  }
+
+  // uniform edges on every axis: arithmetic binning, no tables
+  if (allow_arith) {
+    AxisPlan P0, P1;
+    bool ok = false;
+    if (kind == KMONO || kind == KTHETA) {
+      ok = make_arith(e0, n0, A0.err, ep.eta0, true, false, false, P0);
+    } else if (kind == KSIGPI) {
+      ok = make_arith(e0, n0, A0.err, ep.eta0, true, false, false, P0) &&
+           make_arith(e1, n1, A1.err, ep.eta0, true, false, true, P1);
+    } else if (kind == KRMU) {
+      ok = make_arith(e0, n0, A0.err, ep.eta0, true, false, false, P0) &&
+           make_arith(e1, n1, A0.err, ep.eta0, false, true, false, P1);
+      if (ok) {
+        // mu bound in t units: n_mu * eps(r), eps(r) = a / r + b (see above)
+        double lterm = (ep.lmin > 0) ? ep.eta_l / ep.lmin : INFINITY;
+        double a = 2.0 * 2.0 * std::sqrt(3.0) * ep.eta0 * (1.0 + 1e-5);
+        double b = 2.0 * (2.0 * std::sqrt(3.0) * (kU + lterm) + 40 * kU) + 1e-12;
+        double nmu = n1 / (e1[n1] - e1[0]);
+        P1.thr_a = (float)(nmu * a * 1.0001);
+        P1.thr_b = (float)((double)P1.thr_b + nmu * b * 1.0001);
+        ok = std::isfinite(lterm) && (double)P1.thr_b < 0.2;
+      }
+    }
+    if (ok) {
+      out.ax[0] = P0;
+      out.ax[1] = two_d ? P1 : AxisPlan();
+      out.lut.clear();
+      out.band.assign(2, 0.0f);
+      out.dirty_frac[0] = out.dirty_frac[1] = 0;
+      return "";
+    }
   }
 
   // mu: FP32 mu = |sl| * rsqrt(r^2 l^2) with sl = 2 s.x_i + r^2 and
@@ -429,8 +534,8 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
 // ------------------------------------------------------------------ tasks
 void tasks_build(const Geometry &g, const std::vector<int32_t> &csA,
                  const std::vector<int32_t> &csB, bool is_auto, int pair_index, int home_chunk,
-                 int slice, bool full_stencil, std::vector<Task> &out,
-                 unsigned long long &candidates) {
+                 int slice, bool full_stencil, int shape, const double need[3],
+                 std::vector<Task> &out, unsigned long long &candidates) {
   const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
   const int kx = g.k[0], ky = g.k[1], kz = g.k[2];
   auto cell = [&](int x, int y, int z) { return ((int64_t)z * ny + y) * nx + x; };
@@ -494,6 +599,20 @@ void tasks_build(const Geometry &g, const std::vector<int32_t> &csA,
         for (int dz = -kz; dz <= kz; dz++) {
           for (int dy = -ky; dy <= ky; dy++) {
             bool self_row = (dz == 0 && dy == 0);
+            // objects in cells |d| apart on an axis are at least (|d| - 1) a
+            // apart there, so a row can only reach kxr cells along x: the
+            // in-range region is a ball of radius need (shape 1) or a disk
+            // of radius need[0] in x-y times a slab in z (shape 2)
+            int kxr = kx;
+            if (shape != kShapeBox) {
+              const double shrink = 1.0 - 1e-9;
+              double gy = std::max(std::abs(dy) - 1, 0) * g.a[1] * shrink / need[1];
+              double gz = std::max(std::abs(dz) - 1, 0) * g.a[2] * shrink / need[2];
+              double rem = 1.0 - gy * gy - (shape == kShapeBall ? gz * gz : 0.0);
+              if (shape == kShapeDiskSlab && gz >= 1.0) continue;
+              if (rem <= 0.0) continue;
+              kxr = std::min(kx, (int)std::ceil(std::sqrt(rem) * need[0] * (1.0 + 1e-9) / g.a[0]));
+            }
             if (is_auto && !full_stencil && !self_row && (dz < 0 || (dz == 0 && dy < 0))) continue;
             int y = cy + dy, z = cz + dz, sy = 0, sz = 0;
             if (g.periodic) {
@@ -505,9 +624,9 @@ void tasks_build(const Geometry &g, const std::vector<int32_t> &csA,
             if (is_auto && !full_stencil && self_row) {
               // same row: the run itself with j > i, then the cells after it
               emit(h0, h1, h0, h1, kTaskSelf);
-              row_slices(cx1 + 1, cx1 + kx, y, z, sy, sz, 0, h0, h1);
+              row_slices(cx1 + 1, cx1 + kxr, y, z, sy, sz, 0, h0, h1);
             } else {
-              row_slices(cx0 - kx, cx1 + kx, y, z, sy, sz, 0, h0, h1);
+              row_slices(cx0 - kxr, cx1 + kxr, y, z, sy, sz, 0, h0, h1);
             }
           }
         }

@@ -44,7 +44,7 @@ class PairDesc(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("candidate_pairs", ctypes.c_uint64), ("rechecked_pairs", ctypes.c_uint64),
-                ("refined_pairs", ctypes.c_uint64), ("work_items", ctypes.c_uint64), ("launches", ctypes.c_int32),
+                ("pair_slots", ctypes.c_uint64), ("work_items", ctypes.c_uint64), ("launches", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("blocks", ctypes.c_int32),
                 ("home_per_lane", ctypes.c_int32), ("kernel_ms", ctypes.c_float)]
 
@@ -81,7 +81,7 @@ def lib():
             L.cute_count_pairs_adjoint.argtypes = [P, ctypes.POINTER(PairDesc), P, P, P]
             L.cute_last_stats.argtypes = [P, ctypes.POINTER(Stats)]
             L.cute_set_timing.argtypes = [P, i32]
-            L.cute_set_launch.argtypes = [P, i32, i32, i32]
+            L.cute_set_launch.argtypes = [P, i32, i32, i32, i32]
             L.cute_estimator.argtypes = [ctypes.c_int, P, P, P, i64, i64, i32, P, f64, P]
             L.cute_theta_to_chord.argtypes = [P, i32, P]
             L.cute_version.restype = ctypes.c_char_p
@@ -302,9 +302,10 @@ class Context:
     def set_timing(self, on: bool):
         _check(lib().cute_set_timing(self.handle, int(bool(on))), self.handle)
 
-    def set_launch(self, home_per_lane=0, warps_per_block=0, slice=0):
+    def set_launch(self, home_per_lane=0, warps_per_block=0, slice=0, table_binning=False):
         _check(lib().cute_set_launch(self.handle, int(home_per_lane), int(warps_per_block),
-                                     int(slice)), self.handle)
+                                     int(slice), int(bool(table_binning))), self.handle)
+        self.table_binning = bool(table_binning)
 
 
 def estimator(kind, DD, DR=None, RR=None, Nd=0, Nr=0, edges=None, L=0.0):

@@ -14,11 +14,15 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["arith", "table"])
+def ctx(request):
+    """Every parity test runs twice: arithmetic binning where the edges are
+    uniform, and lookup-table binning forced for all edges."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     c = cute.Context(0)
+    if request.param == "table":
+        c.set_launch(table_binning=True)
     yield c
     c.close()
 
@@ -51,12 +55,13 @@ def test_c1_monopole_box_full_size(ctx):
 @pytest.mark.parametrize("hp", [2, 4])
 def test_mono_periodic_launch_shapes(ctx, cpr, hp):
     w = synthetic.c1_monopole_box(scale=0.3)
-    ctx.set_launch(home_per_lane=hp, slice=128)
+    table = ctx.table_binning if hasattr(ctx, "table_binning") else False
+    ctx.set_launch(home_per_lane=hp, slice=128, table_binning=table)
     try:
         got = gpu_count(ctx, "mono", w.data, e0=w.edges0, periodic=True, L=w.L,
                         cells_per_reach=cpr)
     finally:
-        ctx.set_launch()
+        ctx.set_launch(table_binning=table)
     ref = oracle_count("mono", w.data, e0=w.edges0, periodic=True, L=w.L)
     _assert_same(got, ref)
 
@@ -97,6 +102,20 @@ def test_rmu_lightcone_small(ctx):
         got = gpu_count(ctx, "rmu", a, b, w.edges0, w.edges1)
         ref = oracle_count("rmu", a, b, w.edges0, w.edges1, cells=True)
         _assert_same(got, ref)
+
+
+@pytest.mark.parametrize("cpr", [3, 4])
+def test_trimmed_stencils_2d(ctx, cpr):
+    """Neighbour rows trimmed to the reach ball (r, mu) or disk x slab
+    (sigma, pi) at finer cells."""
+    w = synthetic.c2_rmu_lightcone(scale=0.004)
+    got = gpu_count(ctx, "rmu", w.data, w.randoms, w.edges0, w.edges1, cells_per_reach=cpr)
+    _assert_same(got, oracle_count("rmu", w.data, w.randoms, w.edges0, w.edges1, cells=True))
+    b = synthetic.c4_batched_sigpi(n_boxes=1, scale=0.03)[0]
+    got = gpu_count(ctx, "sigpi", b.data, None, b.edges0, b.edges1[:31], periodic=True, L=b.L,
+                    cells_per_reach=cpr)
+    _assert_same(got, oracle_count("sigpi", b.data, None, b.edges0, b.edges1[:31], periodic=True,
+                                   L=b.L, cells=True))
 
 
 def test_theta_small(ctx):
