@@ -17,16 +17,12 @@ void catalog_release(Catalog &c);
 cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const double reach[3],
                        int kreq);
 cute_status ensure_scratch(cute_ctx *ctx, size_t bytes);
-cudaError_t launch_count_mono(const KParams &p, bool periodic, int hp, int blocks, int threads,
-                              size_t smem, cudaStream_t st);
-cudaError_t launch_count_sigpi(const KParams &p, bool periodic, int hp, int blocks, int threads,
-                               size_t smem, cudaStream_t st);
-cudaError_t launch_count_rmu(const KParams &p, int hp, int blocks, int threads, size_t smem,
-                             cudaStream_t st);
-cute_status adjoint_driver(cute_ctx *ctx, const cute_pair_desc *d, const double *G,
-                           double *grad_a, double *grad_b);
-cute_status weighted_driver(cute_ctx *ctx, int n, const cute_pair_desc *d, uint64_t *const *counts,
-                            double *const *wsum, uint64_t *oor);
+cudaError_t launch_count_mono(const KParams &p, bool periodic, int acc, int hp, int blocks,
+                              int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_count_sigpi(const KParams &p, bool periodic, int acc, int hp, int blocks,
+                               int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_count_rmu(const KParams &p, int acc, int hp, int blocks, int threads,
+                             size_t smem, cudaStream_t st);
 }  // namespace cute
 
 using namespace cute;
@@ -388,6 +384,7 @@ cute_status get_tasks(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, i
     pd.posB = di.B->d_pos;
     pd.sA = di.A->d_s64;
     pd.sB = di.B->d_s64;
+    pd.permA = di.A->d_perm;
     pd.nA = (int32_t)di.A->n;
     pd.nB = (int32_t)di.B->n;
     pd.out = (int32_t)i;
@@ -424,11 +421,11 @@ struct Prepared {
   std::shared_ptr<Plan> plan;
   std::shared_ptr<TaskSet> ts;
   KParams p;
-  int hp, warps, blocks;
+  int hp, warps, blocks, acc;
   size_t smem;
 };
 
-cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, bool weighted, bool full_stencil,
+cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool full_stencil,
                     Prepared &pr, bool allow_swap = true) {
   if (n < 1 || !d) return fail(ctx, CUTE_E_INVALID, "no descriptors");
   pr.dis.resize(n);
@@ -469,13 +466,15 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, bool weighted
   st = get_tasks(ctx, pr.dis, pr.hp, slice, full_stencil, pr.ts);
   if (st != CUTE_OK) return st;
   const Plan &P = *pr.plan;
-  SmemLayout L = smem_layout((int)P.lut.size(), (int)P.band.size() / 2, P.nslots, P.R, pr.hp,
-                             weighted);
+  SmemLayout L = smem_layout((int)P.lut.size(), (int)P.band.size() / 2, P.nslots, P.R, pr.hp, acc);
+  pr.acc = acc;
   size_t avail = ctx->smem_optin;
   int warps = ctx->warps_override ? ctx->warps_override : 16;
   while (warps > 1 && (size_t)L.lut_bytes + (size_t)warps * L.warp_bytes > avail) warps--;
   if ((size_t)L.lut_bytes + (size_t)warps * L.warp_bytes > avail)
-    return fail(ctx, CUTE_E_UNSUPPORTED, "binning tables do not fit in shared memory");
+    return fail(ctx, CUTE_E_UNSUPPORTED,
+                acc == 1 ? "too many bins for weighted counts (32 float-float columns per warp)"
+                         : "binning tables do not fit in shared memory");
   pr.warps = warps;
   pr.smem = (size_t)L.lut_bytes + (size_t)warps * L.warp_bytes;
   pr.blocks = ctx->sm_count;
@@ -512,31 +511,40 @@ cudaError_t launch_prepared(cute_ctx *ctx, const Prepared &pr, int kind) {
   const int threads = pr.warps * 32;
   switch (kind) {
     case CUTE_MONO:
-      return launch_count_mono(pr.p, per, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
+      return launch_count_mono(pr.p, per, pr.acc, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
     case CUTE_THETA:
-      return launch_count_mono(pr.p, false, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
+      return launch_count_mono(pr.p, false, pr.acc, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
     case CUTE_SIGMA_PI:
-      return launch_count_sigpi(pr.p, per, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
+      return launch_count_sigpi(pr.p, per, pr.acc, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
     default:
-      return launch_count_rmu(pr.p, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
+      return launch_count_rmu(pr.p, pr.acc, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
   }
 }
 
-// Counts of n pair sets into counts[k] (host or device); oor for n == 1.
+// Counts (and weighted sums) of n pair sets into counts[k] / wsum[k] (host
+// or device); oor for n == 1.
 cute_status count_driver(cute_ctx *ctx, int n, const cute_pair_desc *d, uint64_t *const *counts,
-                         uint64_t *oor) {
+                         double *const *wsum, uint64_t *oor) {
   for (int i = 0; i < n; i++)
     if (!counts || !counts[i]) return fail(ctx, CUTE_E_INVALID, "counts is NULL");
+  const bool weighted = d[0].weighted != 0;
+  if (weighted)
+    for (int i = 0; i < n; i++)
+      if (!wsum || !wsum[i]) return fail(ctx, CUTE_E_INVALID, "weighted counts need wsum");
   Prepared pr;
-  cute_status st = prepare(ctx, n, d, false, false, pr);
+  cute_status st = prepare(ctx, n, d, weighted ? 1 : 0, false, pr);
   if (st != CUTE_OK) return st;
   const int nb = pr.p.n0 * pr.p.n1;
-  const size_t out_bytes = sizeof(unsigned long long) * (size_t)nb * n;
-  st = ensure_scratch(ctx, out_bytes);
+  const size_t cnt_bytes = sizeof(unsigned long long) * (size_t)nb * n;
+  const size_t ws_bytes = weighted ? sizeof(double) * (size_t)nb * n : 0;
+  st = ensure_scratch(ctx, cnt_bytes + ws_bytes + 256);
   if (st != CUTE_OK) return st;
   unsigned long long *d_out = (unsigned long long *)ctx->d_scratch;
+  double *d_ws = weighted ? (double *)((char *)ctx->d_scratch + ((cnt_bytes + 255) & ~(size_t)255)) : nullptr;
   pr.p.out_counts = d_out;
-  CUDA_OR_FAIL(cudaMemsetAsync(d_out, 0, out_bytes, ctx->stream));
+  pr.p.out_wsum = d_ws;
+  CUDA_OR_FAIL(cudaMemsetAsync(d_out, 0, cnt_bytes, ctx->stream));
+  if (weighted) CUDA_OR_FAIL(cudaMemsetAsync(d_ws, 0, ws_bytes, ctx->stream));
   CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, 5 * sizeof(unsigned long long), ctx->stream));
   ctx->stats = cute_stats{};
   ctx->stats.candidate_pairs = pr.ts->candidates;
@@ -556,6 +564,13 @@ cute_status count_driver(cute_ctx *ctx, int n, const cute_pair_desc *d, uint64_t
                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                  ctx->stream));
     if (!dev) need_sync = true;
+    if (weighted) {
+      bool wdev = is_device_ptr(wsum[i]);
+      CUDA_OR_FAIL(cudaMemcpyAsync(wsum[i], d_ws + (size_t)i * nb, sizeof(double) * nb,
+                                   wdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+      if (!wdev) need_sync = true;
+    }
   }
   if (need_sync) {
     CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
@@ -578,6 +593,81 @@ cute_status count_driver(cute_ctx *ctx, int n, const cute_pair_desc *d, uint64_t
   return CUTE_OK;
 }
 
+// Gradient of sum_b G_b W_b with respect to the weights of one catalog: a
+// full-stencil pass with that catalog on the home side.
+static cute_status adjoint_pass(cute_ctx *ctx, const cute_pair_desc *d, const double *d_G,
+                                double *grad, bool *need_sync) {
+  Prepared pr;
+  cute_status st = prepare(ctx, 1, d, 2, true, pr, false);
+  if (st != CUTE_OK) return st;
+  const int64_t nA = pr.dis[0].A->n;
+  bool dev = is_device_ptr(grad);
+  double *d_grad = grad;
+  const size_t gbytes = sizeof(double) * (size_t)std::max<int64_t>(nA, 1);
+  if (!dev) {
+    st = ensure_scratch(ctx, gbytes + 256);
+    if (st != CUTE_OK) return st;
+    d_grad = (double *)ctx->d_scratch;
+  }
+  CUDA_OR_FAIL(cudaMemsetAsync(d_grad, 0, gbytes, ctx->stream));
+  CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, 5 * sizeof(unsigned long long), ctx->stream));
+  pr.p.G = d_G;
+  pr.p.grad = d_grad;
+  ctx->stats.candidate_pairs += pr.ts->candidates;
+  ctx->stats.warps_per_block = pr.warps;
+  ctx->stats.blocks = pr.blocks;
+  ctx->stats.home_per_lane = pr.hp;
+  if (pr.p.total > 0) {
+    CUDA_OR_FAIL(launch_prepared(ctx, pr, (int)d->kind));
+    ctx->stats.launches++;
+  }
+  if (!dev && nA > 0) {
+    CUDA_OR_FAIL(cudaMemcpyAsync(grad, d_grad, sizeof(double) * (size_t)nA, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    *need_sync = true;
+    CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+  }
+  return CUTE_OK;
+}
+
+cute_status adjoint_driver(cute_ctx *ctx, const cute_pair_desc *d, const double *G,
+                           double *grad_a, double *grad_b) {
+  if (!d || !G || !grad_a) return fail(ctx, CUTE_E_INVALID, "descriptor, G and grad_a are required");
+  DescInfo di;
+  cute_status st = validate_desc(ctx, d, di);
+  if (st != CUTE_OK) return st;
+  if (!di.A->d_w || !di.B->d_w)
+    if (di.A->n > 0 && di.B->n > 0)
+      return fail(ctx, CUTE_E_STATE, "the adjoint needs catalogs uploaded with weights");
+  const int nb = d->n0 * ((d->kind == CUTE_R_MU || d->kind == CUTE_SIGMA_PI) ? d->n1 : 1);
+  // G on the device, after the output buffers in the scratch area
+  double *d_G = nullptr;
+  CUDA_OR_FAIL(cudaMallocAsync((void **)&d_G, sizeof(double) * nb, ctx->stream));
+  CUDA_OR_FAIL(cudaMemcpyAsync(d_G, G, sizeof(double) * nb, cudaMemcpyDefault, ctx->stream));
+  ctx->stats = cute_stats{};
+  if (ctx->timing) CUDA_OR_FAIL(cudaEventRecord(ctx->ev0, ctx->stream));
+  bool need_sync = false;
+  st = adjoint_pass(ctx, d, d_G, grad_a, &need_sync);
+  if (st == CUTE_OK && !di.is_auto && grad_b) {
+    cute_pair_desc e = *d;
+    std::swap(e.cat_a, e.cat_b);
+    st = adjoint_pass(ctx, &e, d_G, grad_b, &need_sync);
+  }
+  if (ctx->timing) cudaEventRecord(ctx->ev1, ctx->stream);
+  cudaFreeAsync(d_G, ctx->stream);
+  if (st != CUTE_OK) return st;
+  if (need_sync) {
+    CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+    int err = 0;
+    CUDA_OR_FAIL(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+      CUDA_OR_FAIL(cudaMemset(ctx->d_err, 0, sizeof(int)));
+      return fail(ctx, (cute_status)err, "the adjoint kernel reported an error");
+    }
+  }
+  return CUTE_OK;
+}
+
 }  // namespace cute
 
 extern "C" {
@@ -586,25 +676,16 @@ cute_status cute_count_pairs(cute_ctx *ctx, const cute_pair_desc *d, uint64_t *c
                              uint64_t *oor, double *wsum) {
   ENTER(ctx);
   if (!d) return fail(ctx, CUTE_E_INVALID, "descriptor is NULL");
-  if (d->weighted) {
-    if (!wsum) return fail(ctx, CUTE_E_INVALID, "weighted counts need wsum");
-    double *const ws[1] = {wsum};
-    uint64_t *const cs[1] = {counts};
-    return weighted_driver(ctx, 1, d, cs, ws, oor);
-  }
   uint64_t *const cs[1] = {counts};
-  return count_driver(ctx, 1, d, cs, oor);
+  double *const ws[1] = {wsum};
+  return count_driver(ctx, 1, d, cs, ws, oor);
 }
 
 cute_status cute_count_pairs_batched(cute_ctx *ctx, int32_t n, const cute_pair_desc *d,
                                      uint64_t *const *counts, double *const *wsum) {
   ENTER(ctx);
   if (n < 1 || !d || !counts) return fail(ctx, CUTE_E_INVALID, "bad arguments");
-  if (d[0].weighted) {
-    if (!wsum) return fail(ctx, CUTE_E_INVALID, "weighted counts need wsum");
-    return weighted_driver(ctx, n, d, counts, wsum, nullptr);
-  }
-  return count_driver(ctx, n, d, counts, nullptr);
+  return count_driver(ctx, n, d, counts, wsum, nullptr);
 }
 
 cute_status cute_count_pairs_adjoint(cute_ctx *ctx, const cute_pair_desc *d, const double *G,

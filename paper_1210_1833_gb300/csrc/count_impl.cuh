@@ -1,42 +1,87 @@
 // count_impl.cuh -- kernel body of the pair counter, instantiated per kind
 // in count_mono.cu, count_sigpi.cu and count_rmu.cu.
+//
+// Three accumulation policies share the traversal and the binning:
+//   kAccCount    -- pair counts (Sec. 2.2 Eq. 11);
+//   kAccWeighted -- counts and, per bin, the sum of w_i w_j (the pixel and
+//                   density-grid weights of Sec. 3.4);
+//   kAccAdjoint  -- d/dw_i of sum_b G_b W_b = sum_j w_j G[bin(i, j)] for
+//                   every home object i (no counts).
 #pragma once
 
 #include "count_kernel.cuh"
 
 namespace cute {
 
+constexpr int kAccCount = 0, kAccWeighted = 1, kAccAdjoint = 2;
+
 template <int HP>
 struct Home {
   float x[HP], y[HP], z[HP];   // home position minus the image shift (grid frame)
   float ax[HP], ay[HP], az[HP];// R_MU: x_i in the observer frame
   float aq[HP];                // R_MU: 4 |x_i|^2
+  float w[HP];                 // weight (0 when padded)
+  float gh[HP], gl[HP];        // adjoint: float-float gradient accumulator
   int id[HP];                  // sorted index in A (INT_MAX when padded)
 };
 
 struct WarpSmem {
   uint32_t *hist;
   char *hist_lane;
+  float2 *wcol;                // weighted: this lane's float-float column
+  float2 *wall;                // weighted: all columns of the warp
+  int wstride;                 // weighted: float2 entries per column
+  const float2 *G;             // adjoint: G per slot, float-float
   int *qcnt;
   int2 *queue;
   int qcap;
   float4 *tiles;
 };
 
+// ------------------------------------------------------------------ float-float
+// Error-free transformations (Knuth's TwoSum, Dekker/Kahan's FastTwoSum,
+// and the FMA form of TwoProduct); the pair (hi, lo) represents hi + lo.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+// (hi, lo) += (ph + pl) with renormalisation
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float ph, float pl) {
+  float s, e;
+  two_sum(hi, ph, s, e);
+  const float t = __fadd_rn(lo, __fadd_rn(e, pl));
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// ------------------------------------------------------------------ queue
 // Warp-cooperative FP64 re-test of queued pairs, 32 at a time (all of them
 // when draining).  Every lane must call it.
-template <int KIND>
+template <int KIND, int ACC>
 __device__ __noinline__ void process_queue(const KParams &p, const PairDev &pd, const WarpSmem &w,
                                            int lane, bool drain) {
   __syncwarp();
   int n = *w.qcnt;
   int done = 0;
+  const int nb = p.n0 * p.n1;
   while (n >= 32 || (drain && n > 0)) {
     int take = min(n, 32);
     if (lane < take) {
       int2 e = w.queue[n - take + lane];
       int s = slot64<KIND>(p, pd, e.x, e.y);
-      atomicAdd(&w.hist[s * p.R + (lane & (p.R - 1))], 1u);
+      int s0 = s / p.slots1, s1 = s - s0 * p.slots1;
+      bool in = s0 >= 1 && s0 <= p.n0 && (p.slots1 == 1 || (s1 >= 1 && s1 <= p.n1));
+      int b = (s0 - 1) * p.n1 + (p.slots1 == 1 ? 0 : s1 - 1);
+      if (ACC != kAccAdjoint) atomicAdd(&w.hist[s * p.R + (lane & (p.R - 1))], 1u);
+      if (ACC == kAccWeighted && in) {
+        double prod = (double)pd.posA[e.x].w * (double)pd.posB[e.y].w;  // exact
+        atomicAdd(&p.out_wsum[(size_t)pd.out * nb + b], prod);
+      }
+      if (ACC == kAccAdjoint && in) {
+        double t = (double)pd.posB[e.y].w * p.G[b];
+        atomicAdd(&p.grad[pd.permA[e.x]], t);
+      }
     }
     n -= take;
     done += take;
@@ -65,25 +110,120 @@ static __device__ __noinline__ void flush_hist(const KParams &p, const WarpSmem 
   __syncwarp();
 }
 
+// add the warp's float-float weighted columns to output `out` and clear them
+static __device__ __noinline__ void flush_wsum(const KParams &p, const WarpSmem &w, int out,
+                                               int lane) {
+  __syncwarp();
+  const int nb = p.n0 * p.n1;
+  for (int b = lane; b < nb; b += 32) {
+    int b0 = b / p.n1, b1 = b - b0 * p.n1;
+    int s = (b0 + 1) * p.slots1 + (p.slots1 > 1 ? b1 + 1 : 0);
+    float hi = 0.0f, lo = 0.0f;
+    for (int c = 0; c < 32; c++) {
+      const float2 v = w.wall[c * w.wstride + s];
+      ff_add(hi, lo, v.x, v.y);
+    }
+    const double sum = (double)hi + (double)lo;
+    if (sum != 0.0) atomicAdd(&p.out_wsum[(size_t)out * nb + b], sum);
+  }
+  __syncwarp();
+  for (int i = lane; i < 32 * w.wstride; i += 32) w.wall[i] = make_float2(0.0f, 0.0f);
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------ binning
+// Slot byte offset (slot * R * 4) of one candidate pair, and whether it lies
+// inside an edge's FP32 error band (then it must be re-tested in FP64).
+template <int KIND, int HP, int M0, int M1>
+__device__ __forceinline__ uint32_t bin_pair(const KParams &p, const uint32_t *__restrict__ lut,
+                                             const float2 *__restrict__ band, float dx, float dy,
+                                             float dz, const Home<HP> &h, int s, bool &near) {
+  const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u, stride1 = (uint32_t)p.R * 4u;
+  uint32_t o;
+  if ((KIND == KMONO || KIND == KTHETA) && M0 == kArith) {
+    const float v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    const float x0 = __fmul_rn(v0, rsqrtf(__fadd_rn(v0, 1e-30f)));
+    float h0;
+    const float tm0 = arith_t(p.ax[0], x0, h0);
+    near = fabsf(h0) + p.ax[0].thr_b >= 0.5f;
+    o = arith_off(tm0, stride0);
+  } else if (KIND == KSIGPI && M0 == kArith) {
+    const float v0 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+    const float x0 = __fmul_rn(v0, rsqrtf(__fadd_rn(v0, 1e-30f)));
+    float h0, h1;
+    const float tm0 = arith_t(p.ax[0], x0, h0);
+    const float tm1 = arith_t(p.ax[1], fabsf(dz), h1);
+    near = fmaxf(fabsf(h0) + p.ax[0].thr_b, fabsf(h1) + p.ax[1].thr_b) >= 0.5f;
+    o = arith_off(tm0, stride0) + arith_off(tm1, stride1);
+  } else if (KIND == KRMU && M0 == kArith) {
+    // s = x_j - x_i; l = x_i + x_j = 2 x_i + s; s.l = 2 s.x_i + r^2;
+    // l.l = 4 |x_i|^2 + 4 s.x_i + r^2
+    const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    const float sx = __fmaf_rn(dz, h.az[s], __fmaf_rn(dy, h.ay[s], __fmul_rn(dx, h.ax[s])));
+    const float sl = __fmaf_rn(2.0f, sx, r2);
+    const float l2 = __fmaf_rn(4.0f, sx, __fadd_rn(h.aq[s], r2));
+    const float rr = rsqrtf(__fadd_rn(r2, 1e-30f));
+    const float mu = __fmul_rn(fabsf(sl), rsqrtf(__fmul_rn(r2, l2)));
+    float h0, h1;
+    const float tm0 = arith_t(p.ax[0], __fmul_rn(r2, rr), h0);
+    const float tm1 = arith_t(p.ax[1], mu, h1);
+    const float thr1 = __fmaf_rn(rr, p.ax[1].thr_a, p.ax[1].thr_b);
+    near = fmaxf(fabsf(h0) + p.ax[0].thr_b, __fadd_rn(fabsf(h1), thr1)) >= 0.5f;
+    o = arith_off(tm0, stride0) + arith_off(tm1, stride1);
+  } else if (KIND == KMONO || KIND == KTHETA) {
+    float v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    const uint32_t e0 = lut_get<M0>(lut, p.ax[0], v0);
+    o = axis_resolve(band, p.ax[0], v0, e0, stride0, near);
+  } else if (KIND == KSIGPI) {
+    float v0 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+    float v1 = __fmul_rn(dz, dz);
+    const uint32_t e0 = lut_get<M0>(lut, p.ax[0], v0);
+    const uint32_t e1 = lut_get<M1>(lut, p.ax[1], v1);
+    bool n0, n1;
+    o = axis_resolve(band, p.ax[0], v0, e0, stride0, n0) +
+        axis_resolve(band, p.ax[1], v1, e1, stride1, n1);
+    near = n0 || n1;
+  } else {
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    const float sx = __fmaf_rn(dz, h.az[s], __fmaf_rn(dy, h.ay[s], __fmul_rn(dx, h.ax[s])));
+    const float sl = __fmaf_rn(2.0f, sx, r2);
+    const float l2 = __fmaf_rn(4.0f, sx, __fadd_rn(h.aq[s], r2));
+    float mu = __fmul_rn(fabsf(sl), rsqrtf(__fmul_rn(r2, l2)));
+    const uint32_t e0 = lut_get<M0>(lut, p.ax[0], r2);
+    const uint32_t e1 = lut_get<M1>(lut, p.ax[1], mu);
+    const float eps = __int_as_float(__float_as_int(p.mu_eps_base) +
+                                     (int)(((e0 >> kClassShift) & 0xFu) << 23));
+    bool n0, n1;
+    o = axis_resolve(band, p.ax[0], r2, e0, stride0, n0) +
+        mu_resolve(band, p.ax[1], mu, e1, stride1, eps, n1);
+    near = n0 || n1;
+  }
+  return o;
+}
+
 // All pairs of the HP home objects of each lane with the cnt neighbours of
 // one shared-memory tile (cnt even; rows past the slice hold sentinels).
-// Two neighbours at a time: every table lookup of the 2 x HP pairs is issued
-// first, then the histogram increments; pairs inside an edge's error band
-// go to the warp's FP64 queue (rare, so the enqueue sits behind one vote).
-template <int KIND, int HP, int M0, int M1, bool SELF>
+// Two neighbours at a time: every binning of the 2 x HP pairs is issued
+// first, then the accumulation; pairs inside an edge's error band go to the
+// warp's FP64 queue (rare, so the enqueue sits behind one vote).
+// MASK: 1 -- only j > i counts (the home run against itself, unique pairs);
+//       2 -- every j != i counts (full-stencil adjoint of an auto count).
+template <int KIND, int HP, int M0, int M1, int MASK, int ACC>
 __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__restrict__ lut,
                                            const float2 *__restrict__ band, const PairDev &pd,
                                            const WarpSmem &w, const float4 *__restrict__ tile,
-                                           int cnt, int gj0, const Home<HP> &h, int lane,
+                                           int cnt, int gj0, Home<HP> &h, int lane,
                                            unsigned &near_count) {
   constexpr int NP = 2 * HP;
-  const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u, stride1 = (uint32_t)p.R * 4u;
+  const int slot_shift = 31 - __clz(p.R * 4);
   for (int j = 0; j < cnt; j += 2) {
     uint32_t off[NP];
+    float wj[2];
     unsigned nmask = 0;
 #pragma unroll
     for (int u = 0; u < 2; u++) {
       const float4 q = tile[j + u];
+      wj[u] = q.w;
 #pragma unroll
       for (int s = 0; s < HP; s++) {
         const int k = u * HP + s;
@@ -91,74 +231,41 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__r
         const float dy = __fsub_rn(q.y, h.y[s]);
         const float dz = __fsub_rn(q.z, h.z[s]);
         bool near;
-        uint32_t o;
-        if ((KIND == KMONO || KIND == KTHETA) && M0 == kArith) {
-          const float v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-          const float x0 = __fmul_rn(v0, rsqrtf(__fadd_rn(v0, 1e-30f)));
-          float h0;
-          const float tm0 = arith_t(p.ax[0], x0, h0);
-          near = fabsf(h0) + p.ax[0].thr_b >= 0.5f;
-          o = arith_off(tm0, stride0);
-        } else if (KIND == KSIGPI && M0 == kArith) {
-          const float v0 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
-          const float x0 = __fmul_rn(v0, rsqrtf(__fadd_rn(v0, 1e-30f)));
-          float h0, h1;
-          const float tm0 = arith_t(p.ax[0], x0, h0);
-          const float tm1 = arith_t(p.ax[1], fabsf(dz), h1);
-          near = fmaxf(fabsf(h0) + p.ax[0].thr_b, fabsf(h1) + p.ax[1].thr_b) >= 0.5f;
-          o = arith_off(tm0, stride0) + arith_off(tm1, stride1);
-        } else if (KIND == KRMU && M0 == kArith) {
-          // s = x_j - x_i; l = x_i + x_j = 2 x_i + s; s.l = 2 s.x_i + r^2;
-          // l.l = 4 |x_i|^2 + 4 s.x_i + r^2
-          const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-          const float sx = __fmaf_rn(dz, h.az[s], __fmaf_rn(dy, h.ay[s], __fmul_rn(dx, h.ax[s])));
-          const float sl = __fmaf_rn(2.0f, sx, r2);
-          const float l2 = __fmaf_rn(4.0f, sx, __fadd_rn(h.aq[s], r2));
-          const float rr = rsqrtf(__fadd_rn(r2, 1e-30f));
-          const float mu = __fmul_rn(fabsf(sl), rsqrtf(__fmul_rn(r2, l2)));
-          float h0, h1;
-          const float tm0 = arith_t(p.ax[0], __fmul_rn(r2, rr), h0);
-          const float tm1 = arith_t(p.ax[1], mu, h1);
-          const float thr1 = __fmaf_rn(rr, p.ax[1].thr_a, p.ax[1].thr_b);
-          near = fmaxf(fabsf(h0) + p.ax[0].thr_b, __fadd_rn(fabsf(h1), thr1)) >= 0.5f;
-          o = arith_off(tm0, stride0) + arith_off(tm1, stride1);
-        } else if (KIND == KMONO || KIND == KTHETA) {
-          float v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-          const uint32_t e0 = lut_get<M0>(lut, p.ax[0], v0);
-          o = axis_resolve(band, p.ax[0], v0, e0, stride0, near);
-        } else if (KIND == KSIGPI) {
-          float v0 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
-          float v1 = __fmul_rn(dz, dz);
-          const uint32_t e0 = lut_get<M0>(lut, p.ax[0], v0);
-          const uint32_t e1 = lut_get<M1>(lut, p.ax[1], v1);
-          bool n0, n1;
-          o = axis_resolve(band, p.ax[0], v0, e0, stride0, n0) +
-              axis_resolve(band, p.ax[1], v1, e1, stride1, n1);
-          near = n0 || n1;
-        } else {
-          // s = x_j - x_i; l = x_i + x_j = 2 x_i + s; s.l = 2 s.x_i + r^2;
-          // l.l = 4 |x_i|^2 + 4 s.x_i + r^2
-          float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-          const float sx = __fmaf_rn(dz, h.az[s], __fmaf_rn(dy, h.ay[s], __fmul_rn(dx, h.ax[s])));
-          const float sl = __fmaf_rn(2.0f, sx, r2);
-          const float l2 = __fmaf_rn(4.0f, sx, __fadd_rn(h.aq[s], r2));
-          float mu = __fmul_rn(fabsf(sl), rsqrtf(__fmul_rn(r2, l2)));
-          const uint32_t e0 = lut_get<M0>(lut, p.ax[0], r2);
-          const uint32_t e1 = lut_get<M1>(lut, p.ax[1], mu);
-          const float eps = __int_as_float(__float_as_int(p.mu_eps_base) +
-                                           (int)(((e0 >> kClassShift) & 0xFu) << 23));
-          bool n0, n1;
-          o = axis_resolve(band, p.ax[0], r2, e0, stride0, n0) +
-              mu_resolve(band, p.ax[1], mu, e1, stride1, eps, n1);
-          near = n0 || n1;
-        }
-        if (SELF && !(gj0 + j + u > h.id[s])) { o = 0u; near = false; }  // not a pair of this task
+        uint32_t o = bin_pair<KIND, HP, M0, M1>(p, lut, band, dx, dy, dz, h, s, near);
+        const int gj = gj0 + j + u;
+        if (MASK == 1 && !(gj > h.id[s])) { o = 0u; near = false; }   // not a pair of this task
+        if (MASK == 2 && gj == h.id[s]) { o = 0u; near = false; }     // no self pair
         if (near) { o = 0u; nmask |= 1u << k; }
         off[k] = o;
       }
     }
+    if (ACC != kAccAdjoint) {
 #pragma unroll
-    for (int k = 0; k < NP; k++) atomicAdd((unsigned *)(w.hist_lane + off[k]), 1u);
+      for (int k = 0; k < NP; k++) atomicAdd((unsigned *)(w.hist_lane + off[k]), 1u);
+    }
+    if (ACC == kAccWeighted) {
+      // lane-private float-float column: a read-modify-write, no atomics
+#pragma unroll
+      for (int k = 0; k < NP; k++) {
+        const float a = h.w[k % HP], b = wj[k / HP];
+        const float ph = __fmul_rn(a, b);
+        const float pl = __fmaf_rn(a, b, -ph);  // exact: a * b = ph + pl
+        float2 *c = w.wcol + (off[k] >> slot_shift);
+        float2 v = *c;
+        ff_add(v.x, v.y, ph, pl);
+        *c = v;
+      }
+    }
+    if (ACC == kAccAdjoint) {
+#pragma unroll
+      for (int k = 0; k < NP; k++) {
+        const float2 g = w.G[off[k] >> slot_shift];  // slot 0 and trash: G = 0
+        const float b = wj[k / HP];
+        const float th = __fmul_rn(b, g.x);
+        const float tl = __fmaf_rn(b, g.y, __fmaf_rn(b, g.x, -th));
+        ff_add(h.gh[k % HP], h.gl[k % HP], th, tl);
+      }
+    }
     if (__any_sync(kFull, nmask != 0u)) {
 #pragma unroll
       for (int k = 0; k < NP; k++) {
@@ -171,43 +278,43 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__r
       }
     }
     __syncwarp();
-    if (*w.qcnt >= 32) process_queue<KIND>(p, pd, w, lane, false);
+    if (*w.qcnt >= 32) process_queue<KIND, ACC>(p, pd, w, lane, false);
   }
 }
 
-template <int KIND, int HP, int M0, int M1>
-__device__ __forceinline__ void tile_dispatch_self(const KParams &p, const uint32_t *lut,
-                                                   const float2 *band,
-                                                   const PairDev &pd, const WarpSmem &w,
-                                                   const float4 *tile, int cnt, int gj0,
-                                                   const Home<HP> &h, int lane, bool self,
+template <int KIND, int HP, int M0, int M1, int ACC>
+__device__ __forceinline__ void tile_dispatch_mask(const KParams &p, const uint32_t *lut,
+                                                   const float2 *band, const PairDev &pd,
+                                                   const WarpSmem &w, const float4 *tile, int cnt,
+                                                   int gj0, Home<HP> &h, int lane, int mask,
                                                    unsigned &dc) {
-  if (self) tile_pairs<KIND, HP, M0, M1, true>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, dc);
-  else tile_pairs<KIND, HP, M0, M1, false>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, dc);
+  if (mask == 1) tile_pairs<KIND, HP, M0, M1, 1, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, dc);
+  else if (ACC == kAccAdjoint && mask == 2)
+    tile_pairs<KIND, HP, M0, M1, 2, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, dc);
+  else tile_pairs<KIND, HP, M0, M1, 0, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, dc);
 }
 
-template <int KIND, int HP>
+template <int KIND, int HP, int ACC>
 __device__ __forceinline__ void tile_dispatch(const KParams &p, const uint32_t *lut,
-                                              const float2 *band,
-                                              const PairDev &pd, const WarpSmem &w,
-                                              const float4 *tile, int cnt, int gj0,
-                                              const Home<HP> &h, int lane, bool self,
+                                              const float2 *band, const PairDev &pd,
+                                              const WarpSmem &w, const float4 *tile, int cnt,
+                                              int gj0, Home<HP> &h, int lane, int mask,
                                               unsigned &dc) {
   const int m0 = p.ax[0].mode;
   if (KIND == KMONO || KIND == KTHETA) {
-    if (m0 == kArith) tile_dispatch_self<KIND, HP, kArith, 0>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
-    else if (m0 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLinear, 0>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
-    else tile_dispatch_self<KIND, HP, kLutLog, 0>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
+    if (m0 == kArith) tile_dispatch_mask<KIND, HP, kArith, 0, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
+    else if (m0 == kLutLinear) tile_dispatch_mask<KIND, HP, kLutLinear, 0, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
+    else tile_dispatch_mask<KIND, HP, kLutLog, 0, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
   } else {
     const int m1 = p.ax[1].mode;
     if (m0 == kArith) {
-      tile_dispatch_self<KIND, HP, kArith, kArith>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
+      tile_dispatch_mask<KIND, HP, kArith, kArith, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
     } else if (m0 == kLutLinear) {
-      if (m1 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLinear, kLutLinear>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
-      else tile_dispatch_self<KIND, HP, kLutLinear, kLutLog>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
+      if (m1 == kLutLinear) tile_dispatch_mask<KIND, HP, kLutLinear, kLutLinear, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
+      else tile_dispatch_mask<KIND, HP, kLutLinear, kLutLog, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
     } else {
-      if (m1 == kLutLinear) tile_dispatch_self<KIND, HP, kLutLog, kLutLinear>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
-      else tile_dispatch_self<KIND, HP, kLutLog, kLutLog>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, self, dc);
+      if (m1 == kLutLinear) tile_dispatch_mask<KIND, HP, kLutLog, kLutLinear, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
+      else tile_dispatch_mask<KIND, HP, kLutLog, kLutLog, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
     }
   }
 }
@@ -233,24 +340,41 @@ __device__ __forceinline__ float shift_of(int code, float L) {
   return code == 1 ? L : (code == 2 ? -L : 0.0f);
 }
 
-template <int KIND, bool PER, int HP>
+template <int KIND, bool PER, int HP, int ACC>
 __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const SmemLayout L = smem_layout(p.lut_words, p.band_words, p.nslots, p.R, HP, false);
+  const SmemLayout L = smem_layout(p.lut_words, p.band_words, p.nslots, p.R, HP, ACC);
   uint32_t *lut = (uint32_t *)smem;
   for (int i = threadIdx.x; i < p.lut_words; i += blockDim.x) lut[i] = p.lut[i];
   float2 *band = (float2 *)(smem + align16(p.lut_words * 4));
   for (int i = threadIdx.x; i < p.band_words; i += blockDim.x) band[i] = p.band[i];
+  float2 *Gs = (float2 *)(smem + align16(p.lut_words * 4) + align16(p.band_words * 8));
+  if (ACC == kAccAdjoint) {
+    // G per slot as float-float; slot 0 and the out-of-range slots hold 0
+    for (int s = threadIdx.x; s < p.nslots; s += blockDim.x) {
+      int s0 = s / p.slots1, s1 = s - s0 * p.slots1;
+      bool in = s0 >= 1 && s0 <= p.n0 && (p.slots1 == 1 || (s1 >= 1 && s1 <= p.n1));
+      double g = in ? p.G[(s0 - 1) * p.n1 + (p.slots1 == 1 ? 0 : s1 - 1)] : 0.0;
+      float gh = (float)g;
+      Gs[s] = make_float2(gh, (float)(g - (double)gh));
+    }
+  }
   unsigned char *wb = smem + L.lut_bytes + (size_t)warp * L.warp_bytes;
   WarpSmem w;
   w.hist = (uint32_t *)wb;
   w.hist_lane = (char *)wb + (lane & (p.R - 1)) * 4;
+  w.wstride = p.nslots + 1;  // odd stride: the flush reads across columns conflict-free
+  w.wall = (float2 *)(wb + align16(p.nslots * p.R * 4));
+  w.wcol = w.wall + lane * w.wstride;
+  w.G = Gs;
   w.qcnt = (int *)(wb + L.hist_bytes);
   w.queue = (int2 *)(wb + L.hist_bytes + 16);
   w.qcap = L.queue_cap;
   w.tiles = (float4 *)(wb + L.hist_bytes + L.queue_bytes);
   for (int i = lane; i < p.nslots * p.R; i += 32) w.hist[i] = 0u;
+  if (ACC == kAccWeighted)
+    for (int i = lane; i < 32 * w.wstride; i += 32) w.wall[i] = make_float2(0.0f, 0.0f);
   if (lane == 0) *w.qcnt = 0;
   __syncthreads();
 
@@ -258,7 +382,7 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
   int cur_pair = -1;
   PairDev pd;
   unsigned long long acc = 0, items = 0, slots = 0;
-  unsigned dirty_count = 0;
+  unsigned near_count = 0;
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(p.ticket, 1ull);
@@ -270,8 +394,8 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
     const int hc = (int)(local / tk.n_sc), sc = (int)(local - (long long)hc * tk.n_sc);
     if (tk.pair != cur_pair) {
       if (cur_pair >= 0) {
-        process_queue<KIND>(p, pd, w, lane, true);
-        flush_hist(p, w, pd.out, lane);
+        process_queue<KIND, ACC>(p, pd, w, lane, true);
+        if (ACC != kAccAdjoint) flush_hist(p, w, pd.out, lane);
         acc = 0;
       }
       cur_pair = tk.pair;
@@ -279,32 +403,37 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
     }
     const int hs = tk.h0 + hc * CH, he = min(hs + CH, tk.h1);
     const int js = tk.j0 + sc * p.slice, je = min(js + p.slice, tk.j1);
-    const bool self = (tk.flags & kTaskSelf) != 0;
-    if (self && je <= hs + 1) continue;  // every j precedes every i
+    const int mask = (tk.flags & kTaskSelf) ? 1 : ((tk.flags & kTaskNoSelfPair) ? 2 : 0);
+    if (mask == 1 && je <= hs + 1) continue;  // every j precedes every i
     // uint32 overflow guard: increments a copy can receive from this item
-    const unsigned long long bound = 2ull * (32 / p.R) * HP * (unsigned long long)(je - js);
-    if (acc + bound > 0xFFFFFFFFull) {
-      process_queue<KIND>(p, pd, w, lane, true);
-      flush_hist(p, w, pd.out, lane);
-      acc = 0;
+    if (ACC != kAccAdjoint) {
+      const unsigned long long bound = 2ull * (32 / p.R) * HP * (unsigned long long)(je - js);
+      if (acc + bound > 0xFFFFFFFFull) {
+        process_queue<KIND, ACC>(p, pd, w, lane, true);
+        flush_hist(p, w, pd.out, lane);
+        acc = 0;
+      }
+      acc += bound;
     }
-    acc += bound;
     items++;
+    slots += (unsigned long long)(32 * HP) * (unsigned long long)((je - js + 1) & ~1);
 
     const int code = tk.flags >> 8;
     const float Sx = PER ? shift_of(code & 3, pd.L32) : 0.0f;
     const float Sy = PER ? shift_of((code >> 2) & 3, pd.L32) : 0.0f;
     const float Sz = PER ? shift_of((code >> 4) & 3, pd.L32) : 0.0f;
     Home<HP> h;
-    slots += (unsigned long long)(32 * HP) * (unsigned long long)((je - js + 1) & ~1);
 #pragma unroll
     for (int s = 0; s < HP; s++) {
       const int idx = hs + lane + 32 * s;
+      h.gh[s] = 0.0f;
+      h.gl[s] = 0.0f;
       if (idx < he) {
         const float4 a = pd.posA[idx];
         h.x[s] = __fsub_rn(a.x, Sx);
         h.y[s] = __fsub_rn(a.y, Sy);
         h.z[s] = __fsub_rn(a.z, Sz);
+        h.w[s] = a.w;
         h.id[s] = idx;
         if (KIND == KRMU) {
           const double X = pd.sA[idx], Y = pd.sA[(size_t)pd.nA + idx],
@@ -316,6 +445,7 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
         }
       } else {
         h.x[s] = kHomeFar; h.y[s] = kHomeFar; h.z[s] = kHomeFar;
+        h.w[s] = 0.0f;
         h.id[s] = 0x7fffffff;
         if (KIND == KRMU) { h.ax[s] = kHomeFar; h.ay[s] = kHomeFar; h.az[s] = kHomeFar; h.aq[s] = kHomeFar; }
       }
@@ -344,28 +474,52 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
       __syncwarp();
       int cnt = min(kTile, nj - tt * kTile);
       cnt = (cnt + 1) & ~1;
-      tile_dispatch<KIND, HP>(p, lut, band, pd, w, w.tiles + (tt & 1) * kTile, cnt,
-                              js + tt * kTile, h, lane, self, dirty_count);
+      tile_dispatch<KIND, HP, ACC>(p, lut, band, pd, w, w.tiles + (tt & 1) * kTile, cnt,
+                                   js + tt * kTile, h, lane, mask, near_count);
       __syncwarp();
+    }
+    if (ACC == kAccWeighted) flush_wsum(p, w, pd.out, lane);
+    if (ACC == kAccAdjoint) {
+#pragma unroll
+      for (int s = 0; s < HP; s++) {
+        const int idx = hs + lane + 32 * s;
+        const double g = (double)h.gh[s] + (double)h.gl[s];
+        if (idx < he && g != 0.0) atomicAdd(&p.grad[pd.permA[idx]], g);
+      }
     }
   }
   if (cur_pair >= 0) {
-    process_queue<KIND>(p, pd, w, lane, true);
-    flush_hist(p, w, pd.out, lane);
+    process_queue<KIND, ACC>(p, pd, w, lane, true);
+    if (ACC != kAccAdjoint) flush_hist(p, w, pd.out, lane);
   }
   if (lane == 0 && items) atomicAdd(&p.stats[1], items);
   if (lane == 0 && slots) atomicAdd(&p.stats[3], slots);
-  for (int o = 16; o > 0; o >>= 1) dirty_count += __shfl_xor_sync(kFull, dirty_count, o);
-  if (lane == 0 && dirty_count) atomicAdd(&p.stats[2], (unsigned long long)dirty_count);
+  for (int o = 16; o > 0; o >>= 1) near_count += __shfl_xor_sync(kFull, near_count, o);
+  if (lane == 0 && near_count) atomicAdd(&p.stats[2], (unsigned long long)near_count);
 }
 
-template <int KIND, bool PER, int HP>
+template <int KIND, bool PER, int HP, int ACC>
 cudaError_t launch_count_t(const KParams &p, int blocks, int threads, size_t smem, cudaStream_t st) {
-  auto fn = k_count<KIND, PER, HP>;
+  auto fn = k_count<KIND, PER, HP, ACC>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<blocks, threads, smem, st>>>(p);
   return cudaGetLastError();
+}
+
+template <int KIND, bool PER, int ACC>
+cudaError_t launch_count_hp(const KParams &p, int hp, int blocks, int threads, size_t smem,
+                            cudaStream_t st) {
+  if (hp == 2) return launch_count_t<KIND, PER, 2, ACC>(p, blocks, threads, smem, st);
+  return launch_count_t<KIND, PER, 4, ACC>(p, blocks, threads, smem, st);
+}
+
+template <int KIND, bool PER>
+cudaError_t launch_count_acc(const KParams &p, int acc, int hp, int blocks, int threads,
+                             size_t smem, cudaStream_t st) {
+  if (acc == kAccWeighted) return launch_count_hp<KIND, PER, kAccWeighted>(p, hp, blocks, threads, smem, st);
+  if (acc == kAccAdjoint) return launch_count_hp<KIND, PER, kAccAdjoint>(p, hp, blocks, threads, smem, st);
+  return launch_count_hp<KIND, PER, kAccCount>(p, hp, blocks, threads, smem, st);
 }
 
 }  // namespace cute

@@ -3,13 +3,9 @@
 #include "count_impl.cuh"
 
 namespace cute {
-cudaError_t launch_count_mono(const KParams &p, bool periodic, int hp, int blocks, int threads,
-                              size_t smem, cudaStream_t st) {
-  if (periodic) {
-    if (hp == 2) return launch_count_t<KMONO, true, 2>(p, blocks, threads, smem, st);
-    return launch_count_t<KMONO, true, 4>(p, blocks, threads, smem, st);
-  }
-  if (hp == 2) return launch_count_t<KMONO, false, 2>(p, blocks, threads, smem, st);
-  return launch_count_t<KMONO, false, 4>(p, blocks, threads, smem, st);
+cudaError_t launch_count_mono(const KParams &p, bool periodic, int acc, int hp, int blocks,
+                              int threads, size_t smem, cudaStream_t st) {
+  if (periodic) return launch_count_acc<KMONO, true>(p, acc, hp, blocks, threads, smem, st);
+  return launch_count_acc<KMONO, false>(p, acc, hp, blocks, threads, smem, st);
 }
 }  // namespace cute

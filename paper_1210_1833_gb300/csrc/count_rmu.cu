@@ -3,9 +3,8 @@
 #include "count_impl.cuh"
 
 namespace cute {
-cudaError_t launch_count_rmu(const KParams &p, int hp, int blocks, int threads, size_t smem,
-                             cudaStream_t st) {
-  if (hp == 2) return launch_count_t<KRMU, false, 2>(p, blocks, threads, smem, st);
-  return launch_count_t<KRMU, false, 4>(p, blocks, threads, smem, st);
+cudaError_t launch_count_rmu(const KParams &p, int acc, int hp, int blocks, int threads,
+                             size_t smem, cudaStream_t st) {
+  return launch_count_acc<KRMU, false>(p, acc, hp, blocks, threads, smem, st);
 }
 }  // namespace cute

@@ -2,13 +2,9 @@
 #include "count_impl.cuh"
 
 namespace cute {
-cudaError_t launch_count_sigpi(const KParams &p, bool periodic, int hp, int blocks, int threads,
-                               size_t smem, cudaStream_t st) {
-  if (periodic) {
-    if (hp == 2) return launch_count_t<KSIGPI, true, 2>(p, blocks, threads, smem, st);
-    return launch_count_t<KSIGPI, true, 4>(p, blocks, threads, smem, st);
-  }
-  if (hp == 2) return launch_count_t<KSIGPI, false, 2>(p, blocks, threads, smem, st);
-  return launch_count_t<KSIGPI, false, 4>(p, blocks, threads, smem, st);
+cudaError_t launch_count_sigpi(const KParams &p, bool periodic, int acc, int hp, int blocks,
+                               int threads, size_t smem, cudaStream_t st) {
+  if (periodic) return launch_count_acc<KSIGPI, true>(p, acc, hp, blocks, threads, smem, st);
+  return launch_count_acc<KSIGPI, false>(p, acc, hp, blocks, threads, smem, st);
 }
 }  // namespace cute

@@ -64,12 +64,14 @@ struct Task {
   int32_t flags;   // bit 0: self (only j > i); bits 8..13: image shift code
   int32_t n_hc, n_sc;
 };
-constexpr int kTaskSelf = 1;
+constexpr int kTaskSelf = 1;        // only j > i (unique pairs of a run with itself)
+constexpr int kTaskNoSelfPair = 2;  // every j != i (full-stencil adjoint of an auto count)
 
 // One pair set (cat_a, cat_b) of a (possibly batched) count.
 struct PairDev {
   const float4 *posA, *posB;   // cell-sorted FP32 (x, y, z, w), grid frame
   const double *sA, *sB;       // cell-sorted FP64 SoA (x[n], y[n], z[n])
+  const int32_t *permA;        // cell-sorted index -> upload index of A
   int32_t nA, nB;
   int32_t out;                 // output histogram index
   int32_t is_auto;

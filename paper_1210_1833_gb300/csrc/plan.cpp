@@ -626,7 +626,9 @@ void tasks_build(const Geometry &g, const std::vector<int32_t> &csA,
               emit(h0, h1, h0, h1, kTaskSelf);
               row_slices(cx1 + 1, cx1 + kxr, y, z, sy, sz, 0, h0, h1);
             } else {
-              row_slices(cx0 - kxr, cx1 + kxr, y, z, sy, sz, 0, h0, h1);
+              // full stencil of an auto count: the home run meets itself
+              const int f = (is_auto && self_row) ? kTaskNoSelfPair : 0;
+              row_slices(cx0 - kxr, cx1 + kxr, y, z, sy, sz, f, h0, h1);
             }
           }
         }
