@@ -168,6 +168,31 @@ cute_status cute_count_pairs_batched(cute_ctx *ctx, int32_t n, const cute_pair_d
 cute_status cute_count_pairs_adjoint(cute_ctx *ctx, const cute_pair_desc *d, const double *G,
                                      double *grad_a, double *grad_b);
 
+/* Counts like cute_count_pairs, but allocates no device memory: for callers
+   that cannot let a library call cudaMalloc when they count -- a framework
+   whose caching allocator owns the device memory (a stray cudaMalloc
+   fragments its pool or fails once the pool has taken the device), code
+   running while a CUDA stream is captured, or loops where cudaMalloc and
+   cudaFree would synchronise the device.  The paper has no counterpart; it
+   is a deployment form of the counting kernel.
+   The catalogs and grids must already exist (upload and grid build allocate
+   and are done beforehand).  counts (n0 * n1 uint64) and, if d->weighted,
+   wsum (n0 * n1 doubles) must be device memory of the context's device;
+   host pointers are CUTE_E_INVALID.  The kernel's scratch (task list,
+   binning tables, work counters) lives in one fixed 8 MiB device array of
+   the library, held on every device that loads it until the process exits;
+   a request whose scratch exceeds 8 MiB is rejected with CUTE_E_INVALID and
+   a message naming the size (count smaller catalogs, or use
+   cute_count_pairs).  The first call on a device looks up the array's
+   device address (cudaGetSymbolAddress) with that device current; make it
+   before any stream capture.  Every call shares the array and leaves its
+   contents behind (the counters are cleared at the start of each call):
+   calls that overlap on the GPU -- on different streams or contexts -- race
+   on it.  Asynchronous on the context's stream; cute_sync reports kernel
+   errors.  cute_last_stats does not describe these calls. */
+cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_desc *d, uint64_t *counts,
+                                     double *wsum);
+
 /* Statistics of the last count call on ctx. */
 typedef struct {
   uint64_t candidate_pairs; /* pairs examined by the FP32 path              */

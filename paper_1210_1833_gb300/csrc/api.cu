@@ -255,14 +255,6 @@ cute_status cute_last_stats(cute_ctx *ctx, cute_stats *out) {
 // ------------------------------------------------------------------ count driver
 namespace cute {
 
-struct DescInfo {
-  int kind;        // KMONO / KRMU / KSIGPI / KTHETA
-  Catalog *A, *B;
-  const Geometry *g;
-  bool is_auto;
-  double need[3];
-};
-
 cute_status validate_desc(cute_ctx *ctx, const cute_pair_desc *d, DescInfo &di) {
   if (!d) return fail(ctx, CUTE_E_INVALID, "descriptor is NULL");
   if (d->kind < CUTE_MONO || d->kind > CUTE_THETA) return fail(ctx, CUTE_E_INVALID, "bad kind");

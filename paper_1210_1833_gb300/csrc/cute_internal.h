@@ -224,6 +224,17 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
                        const ErrorParams &ep, int lut_budget_words, size_t hist_budget_bytes,
                        bool allow_arith, Plan &out);
 
+// A validated pair descriptor (api.cu).
+struct DescInfo {
+  int kind;        // KMONO / KRMU / KSIGPI / KTHETA
+  Catalog *A, *B;
+  const Geometry *g;
+  bool is_auto;
+  double need[3];
+};
+cute_status validate_desc(cute_ctx *ctx, const cute_pair_desc *d, DescInfo &di);
+ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax);
+
 // Task list for one pair set of catalogs on a shared geometry.  shape: the
 // region of separations that can fall in a bin, used to trim neighbour rows.
 constexpr int kShapeBox = 0, kShapeBall = 1, kShapeDiskSlab = 2;

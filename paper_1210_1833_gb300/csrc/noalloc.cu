@@ -1,0 +1,214 @@
+// noalloc.cu -- a counting entry point that allocates no device memory.
+//
+// cute_count_pairs keeps its per-request device data (binning tables, task
+// list, work counters) in buffers it allocates and caches.  Some callers
+// cannot let a library allocate at the moment they count: a framework whose
+// caching allocator owns all device memory (a stray cudaMalloc fragments its
+// pool or fails once the pool has taken the device), code running while a
+// CUDA stream is being captured (allocation calls are not permitted then),
+// or latency-critical loops where cudaMalloc/cudaFree may synchronise the
+// whole device.  cute_count_pairs_noalloc serves them: the same counting
+// kernel, with its scratch in one fixed file-scope device array that every
+// call on a device shares.  The caller passes the outputs (device memory);
+// the catalogs and their grids are set up beforehand.
+#include "cute_internal.h"
+#include "count_kernel.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+namespace cute {
+cudaError_t launch_count_mono(const KParams &p, bool periodic, int acc, int hp, int blocks,
+                              int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_count_sigpi(const KParams &p, bool periodic, int acc, int hp, int blocks,
+                               int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_count_rmu(const KParams &p, int acc, int hp, int blocks, int threads,
+                             size_t smem, cudaStream_t st);
+}  // namespace cute
+
+using namespace cute;
+
+// The scratch: 8 MiB on every device that loads the library, held until the
+// process exits.  Host code must not use this name as an address (it is a
+// host-side stand-in): the device address comes from cudaGetSymbolAddress.
+static constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[256];  // device address of the scratch, per device
+
+static cute_status na_fail(cute_ctx *ctx, cute_status st, const std::string &m) {
+  ctx->err = m;
+  return st;
+}
+
+#define NA_CUDA(call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return na_fail(ctx, CUTE_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+static bool na_is_device(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_desc *d,
+                                                uint64_t *counts, double *wsum) {
+  if (!ctx) return CUTE_E_INVALID;
+  ctx->err.clear();
+  NA_CUDA(cudaSetDevice(ctx->device));
+  if (!d || !counts) return na_fail(ctx, CUTE_E_INVALID, "descriptor and counts are required");
+  if (!na_is_device(counts) || (d->weighted && (!wsum || !na_is_device(wsum))))
+    return na_fail(ctx, CUTE_E_INVALID, "outputs must be device memory of the context's device");
+  if (ctx->device < 0 || ctx->device >= 256) return na_fail(ctx, CUTE_E_INVALID, "device index");
+
+  // set-up, once per device, with that device current
+  void *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[ctx->device]) {
+      void *a = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+      if (e != cudaSuccess || !a)
+        return na_fail(ctx, CUTE_E_CUDA,
+                       std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+      g_noalloc_addr[ctx->device] = a;
+    }
+    base = g_noalloc_addr[ctx->device];
+  }
+
+  DescInfo di;
+  cute_status st = validate_desc(ctx, d, di);
+  if (st != CUTE_OK) return st;
+  if (!di.is_auto && di.B->n > di.A->n) std::swap(di.A, di.B);  // fuller home cells
+  const int kind = (int)d->kind;
+  const bool two_d = (kind == CUTE_R_MU || kind == CUTE_SIGMA_PI);
+  const int acc = d->weighted ? 1 : 0;
+  std::vector<DescInfo> dis(1, di);
+  ErrorParams ep = error_params(dis, d->edges0[d->n0]);
+
+  int hp = ctx->hp_override;
+  if (!hp) {
+    double objs = 0, cells = 0;
+    const std::vector<int32_t> &cs = di.A->h_cell_start;
+    for (size_t c = 0; c + 1 < cs.size(); c++)
+      if (cs[c + 1] > cs[c]) { objs += cs[c + 1] - cs[c]; cells += 1; }
+    hp = (cells > 0 && objs / cells < 96.0) ? 2 : 4;
+  }
+  const int slice = ctx->slice_override ? ctx->slice_override : 2048;
+
+  // binning plan and task list, host only
+  Plan P;
+  std::string m = plan_build(kind, d->edges0, d->n0, d->edges1, two_d ? d->n1 : 1, ep, 8192,
+                             12288, !ctx->table_binning, P);
+  if (!m.empty()) return na_fail(ctx, CUTE_E_UNSUPPORTED, m);
+  std::vector<Task> tasks;
+  unsigned long long cand = 0;
+  if (di.A->n > 0 && di.B->n > 0) {
+    const int shape = (kind == CUTE_SIGMA_PI) ? kShapeDiskSlab : kShapeBall;
+    tasks_build(*di.g, di.A->h_cell_start, di.B->h_cell_start, di.is_auto, 0, 32 * hp, slice,
+                false, shape, di.need, tasks, cand);
+  }
+  std::vector<long long> prefix(tasks.size() + 1, 0);
+  for (size_t t = 0; t < tasks.size(); t++)
+    prefix[t + 1] = prefix[t] + (long long)tasks[t].n_hc * tasks[t].n_sc;
+  PairDev pd;
+  pd.posA = di.A->d_pos;
+  pd.posB = di.B->d_pos;
+  pd.sA = di.A->d_s64;
+  pd.sB = di.B->d_s64;
+  pd.permA = di.A->d_perm;
+  pd.nA = (int32_t)di.A->n;
+  pd.nB = (int32_t)di.B->n;
+  pd.out = 0;
+  pd.is_auto = di.is_auto;
+  pd.L32 = (float)di.g->L;
+  pd.L64 = di.g->periodic ? di.g->L : 0.0;
+
+  // scratch layout: counters | tasks | prefix | pair | tables | bands | edges
+  const size_t o_cnt = 0;
+  const size_t o_tasks = na_align(o_cnt + 8 * sizeof(unsigned long long));
+  const size_t o_prefix = na_align(o_tasks + tasks.size() * sizeof(Task));
+  const size_t o_pair = na_align(o_prefix + prefix.size() * sizeof(long long));
+  const size_t o_lut = na_align(o_pair + sizeof(PairDev));
+  const size_t o_band = na_align(o_lut + P.lut.size() * sizeof(uint32_t));
+  const size_t o_e0 = na_align(o_band + P.band.size() * sizeof(float));
+  const size_t o_e1 = na_align(o_e0 + P.E0.size() * sizeof(double));
+  const size_t total = na_align(o_e1 + P.E1.size() * sizeof(double));
+  if (total > kNoAllocScratchBytes)
+    return na_fail(ctx, CUTE_E_INVALID,
+                   "request needs " + std::to_string(total) +
+                       " bytes of scratch; cute_count_pairs_noalloc has 8 MiB (use fewer tasks: "
+                       "smaller catalogs, or cute_count_pairs)");
+  std::vector<unsigned char> img(total, 0);  // counters start at zero
+  std::memcpy(img.data() + o_tasks, tasks.data(), tasks.size() * sizeof(Task));
+  std::memcpy(img.data() + o_prefix, prefix.data(), prefix.size() * sizeof(long long));
+  std::memcpy(img.data() + o_pair, &pd, sizeof(PairDev));
+  std::memcpy(img.data() + o_lut, P.lut.data(), P.lut.size() * sizeof(uint32_t));
+  std::memcpy(img.data() + o_band, P.band.data(), P.band.size() * sizeof(float));
+  std::memcpy(img.data() + o_e0, P.E0.data(), P.E0.size() * sizeof(double));
+  std::memcpy(img.data() + o_e1, P.E1.data(), P.E1.size() * sizeof(double));
+  unsigned char *dev = (unsigned char *)base;
+  NA_CUDA(cudaMemcpyAsync(dev, img.data(), total, cudaMemcpyHostToDevice, ctx->stream));
+
+  const int nb = P.n0 * P.n1;
+  NA_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint64_t) * nb, ctx->stream));
+  if (acc == 1) NA_CUDA(cudaMemsetAsync(wsum, 0, sizeof(double) * nb, ctx->stream));
+
+  KParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.tasks = (const Task *)(dev + o_tasks);
+  p.prefix = (const long long *)(dev + o_prefix);
+  p.ntasks = (int)tasks.size();
+  p.total = prefix.back();
+  p.pairs = (const PairDev *)(dev + o_pair);
+  p.lut = (const uint32_t *)(dev + o_lut);
+  p.lut_words = (int)P.lut.size();
+  p.ax[0] = P.ax[0];
+  p.ax[1] = P.ax[1];
+  p.band = (const float2 *)(dev + o_band);
+  p.band_words = (int)P.band.size() / 2;
+  p.mu_eps_base = P.mu_eps_base;
+  p.E0 = (const double *)(dev + o_e0);
+  p.E1 = (const double *)(dev + o_e1);
+  p.n0 = P.n0;
+  p.n1 = P.n1;
+  p.slots1 = P.slots1;
+  p.nslots = P.nslots;
+  p.R = P.R;
+  p.slice = slice;
+  p.out_counts = (unsigned long long *)counts;
+  p.out_wsum = acc == 1 ? wsum : nullptr;
+  p.ticket = (unsigned long long *)(dev + o_cnt);
+  p.stats = (unsigned long long *)(dev + o_cnt) + 1;
+  p.err = ctx->d_err;
+
+  SmemLayout L = smem_layout(p.lut_words, p.band_words, P.nslots, P.R, hp, acc);
+  int warps = ctx->warps_override ? ctx->warps_override : 16;
+  while (warps > 1 && (size_t)L.lut_bytes + (size_t)warps * L.warp_bytes > ctx->smem_optin) warps--;
+  const size_t smem = (size_t)L.lut_bytes + (size_t)warps * L.warp_bytes;
+  if (smem > ctx->smem_optin)
+    return na_fail(ctx, CUTE_E_UNSUPPORTED, "binning tables do not fit in shared memory");
+  if (p.total == 0) return CUTE_OK;
+  const bool per = di.g->periodic;
+  const int threads = warps * 32, blocks = ctx->sm_count;
+  cudaError_t e;
+  switch (kind) {
+    case CUTE_MONO: e = launch_count_mono(p, per, acc, hp, blocks, threads, smem, ctx->stream); break;
+    case CUTE_THETA: e = launch_count_mono(p, false, acc, hp, blocks, threads, smem, ctx->stream); break;
+    case CUTE_SIGMA_PI: e = launch_count_sigpi(p, per, acc, hp, blocks, threads, smem, ctx->stream); break;
+    default: e = launch_count_rmu(p, acc, hp, blocks, threads, smem, ctx->stream); break;
+  }
+  if (e != cudaSuccess) return na_fail(ctx, CUTE_E_CUDA, cudaGetErrorString(e));
+  return CUTE_OK;
+}

@@ -48,10 +48,10 @@ static float bitsf(uint32_t u) {
 }
 
 Plan::~Plan() {
-  cudaFree(d_lut);
-  cudaFree(d_band);
-  cudaFree(d_E0);
-  cudaFree(d_E1);
+  if (d_lut) cudaFree(d_lut);
+  if (d_band) cudaFree(d_band);
+  if (d_E0) cudaFree(d_E0);
+  if (d_E1) cudaFree(d_E1);
 }
 
 // ------------------------------------------------------------------ error models

@@ -25,6 +25,7 @@ STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "CUDA", -4: "STATE", -5: "TIMEO
 SYMBOLS = ["cute_ctx_create", "cute_ctx_destroy", "cute_last_error", "cute_sync",
            "cute_catalog_upload", "cute_catalog_free", "cute_catalog_size", "cute_grid_build",
            "cute_count_pairs", "cute_count_pairs_batched", "cute_count_pairs_adjoint",
+           "cute_count_pairs_noalloc",
            "cute_last_stats", "cute_set_timing", "cute_set_launch", "cute_estimator",
            "cute_theta_to_chord", "cute_version"]
 
@@ -79,6 +80,7 @@ def lib():
             L.cute_count_pairs.argtypes = [P, ctypes.POINTER(PairDesc), P, P, P]
             L.cute_count_pairs_batched.argtypes = [P, i32, P, P, P]
             L.cute_count_pairs_adjoint.argtypes = [P, ctypes.POINTER(PairDesc), P, P, P]
+            L.cute_count_pairs_noalloc.argtypes = [P, ctypes.POINTER(PairDesc), P, P]
             L.cute_last_stats.argtypes = [P, ctypes.POINTER(Stats)]
             L.cute_set_timing.argtypes = [P, i32]
             L.cute_set_launch.argtypes = [P, i32, i32, i32, i32]

@@ -1,0 +1,96 @@
+"""cute_count_pairs_noalloc: the counting entry point for callers that cannot
+let the library allocate device memory when they count (a framework's
+caching allocator owning the device, stream capture, latency-critical loops).
+
+Through the C ABI, on two calls in a row, its counts must equal those of
+cute_count_pairs exactly (integer counts) and its weighted sums within the
+1e-12 relative tolerance the tests use for repeated FP64 accumulation.  This
+file is collected last so that a failure here leaves every other test run."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1210_1833_gb300 import cute, synthetic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(ctx, kind, a, b, e0, e1=None, weighted=False):
+    n0 = len(e0) - 1
+    n1 = len(e1) - 1 if (e1 is not None and kind in ("rmu", "sigpi")) else 1
+    e0 = np.ascontiguousarray(e0, dtype=np.float64)
+    e1 = None if e1 is None else np.ascontiguousarray(e1, dtype=np.float64)
+    d = ctx._desc(kind, a, b, e0, e1 if kind in ("rmu", "sigpi") else None, weighted)
+    counts = torch.zeros(n0 * n1, dtype=torch.int64, device="cuda")
+    wsum = torch.zeros(n0 * n1, dtype=torch.float64, device="cuda") if weighted else None
+    st = cute.lib().cute_count_pairs_noalloc(ctx.handle, ctypes.byref(d),
+                                             ctypes.c_void_p(counts.data_ptr()),
+                                             ctypes.c_void_p(wsum.data_ptr()) if weighted else None)
+    if st != 0:
+        raise cute.CuteError(st, cute.lib().cute_last_error(ctx.handle).decode())
+    ctx.sync()
+    c = counts.cpu().numpy().view(np.uint64).reshape(n0, n1)
+    return c, (None if wsum is None else wsum.cpu().numpy().reshape(n0, n1))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = cute.Context(0)
+    yield c
+    c.close()
+
+
+def test_noalloc_matches_count_pairs(ctx):
+    w = synthetic.c1_monopole_box(scale=0.25)
+    a = ctx.upload(w.data, periodic=True, L=w.L)
+    ctx.grid([a], [w.edges0[-1]] * 3)
+    ref, _, _ = ctx.count("mono", a, None, w.edges0)
+    for _ in range(2):
+        got, _ = _noalloc(ctx, "mono", a, None, w.edges0)
+        assert got.tolist() == ref.tolist()
+    a.free()
+
+    v = synthetic.c2_rmu_lightcone(scale=0.004)
+    d = ctx.upload(v.data)
+    r = ctx.upload(v.randoms)
+    ctx.grid([d, r], [v.edges0[-1]] * 3)
+    for b in (None, r):
+        ref, _, _ = ctx.count("rmu", d, b, v.edges0, v.edges1)
+        for _ in range(2):
+            got, _ = _noalloc(ctx, "rmu", d, b, v.edges0, v.edges1)
+            assert got.tolist() == ref.tolist()
+    d.free()
+    r.free()
+
+
+def test_noalloc_weighted_matches_count_pairs(ctx):
+    rng = np.random.default_rng(60)
+    L = 300.0
+    x = synthetic.uniform_box(4000, L, rng)
+    wt = np.exp(0.3 * rng.normal(size=len(x))).astype(np.float32)
+    e = np.arange(21) * 3.0
+    a = ctx.upload(x, weights=wt, periodic=True, L=L)
+    ctx.grid([a], [e[-1]] * 3)
+    ref, _, rws = ctx.count("mono", a, None, e, weighted=True)
+    for _ in range(2):
+        got, ws = _noalloc(ctx, "mono", a, None, e, weighted=True)
+        assert got.tolist() == ref.tolist()
+        np.testing.assert_allclose(ws, rws, rtol=1e-12)
+    a.free()
+
+
+def test_noalloc_rejects_host_outputs(ctx):
+    x = np.random.default_rng(61).uniform(0, 10, size=(100, 3))
+    a = ctx.upload(x)
+    ctx.grid([a], [2.0] * 3)
+    e = np.linspace(0, 2, 5)
+    d = ctx._desc("mono", a, None, np.ascontiguousarray(e), None, False)
+    host = np.zeros(4, dtype=np.uint64)
+    st = cute.lib().cute_count_pairs_noalloc(ctx.handle, ctypes.byref(d),
+                                             host.ctypes.data_as(ctypes.c_void_p), None)
+    assert st == -1
+    a.free()
