@@ -104,6 +104,25 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def traffic_record(key):
+    """DRAM bytes per launch of a kernel from profiles/traffic.json, only if
+    the counting-kernel sources still hash to what was captured."""
+    import glob
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(key)
+    if not rec:
+        return None
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1210_1833_gb300", "csrc", "count_*.cu*")) +
+                   [os.path.join(ROOT, "paper_1210_1833_gb300", "csrc", "cute_internal.h")])
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(f, "rb").read())
+    return rec["per_launch_bytes"] if h.hexdigest()[:16] == rec["kernel_source_hash"] else None
+
+
 def total_pairs(nd, nr):
     return nd * (nd - 1) // 2 + nd * nr + nr * (nr - 1) // 2
 
@@ -272,7 +291,7 @@ def run_gpu(args, w, rank, world):
                   "count_kernel_ms_per_step": float(np.sum(state["kms"])) / args.steps},
         "roofline": {"bound": "alu", "kernel": "k_count<R_MU> (RR)", "achieved": achieved,
                      "peak": peak_tinst, "unit": "Tinst/s", "frac": achieved / peak_tinst,
-                     "traffic": None, "i_pair": I_PAIR_RMU,
+                     "traffic": traffic_record("k_count_rmu_RR_c2"), "i_pair": I_PAIR_RMU,
                      "peak_note": "152 SMs x 128 FP32 lanes x %.0f MHz (%s max clock)" % (
                          smax, src),
                      "kernel_ms": rr_ms, "candidate_pairs": state["rr_cand"]},
