@@ -154,7 +154,10 @@ cute_status cute_count_pairs(cute_ctx *ctx, const cute_pair_desc *d, uint64_t *c
    use of Fig. 5).  All descriptors must share kind, edges and weighted.
    counts[k]: output of descriptor k as in cute_count_pairs (host or device).
    wsum may be NULL; else wsum[k] as in cute_count_pairs.  The result equals
-   n separate cute_count_pairs calls bit for bit. */
+   n separate cute_count_pairs calls bit for bit.  When every output is
+   device memory, the call's work (counter resets, the kernel, the output
+   copies) is captured once into a CUDA graph and replayed by later calls
+   with the same descriptors and outputs. */
 cute_status cute_count_pairs_batched(cute_ctx *ctx, int32_t n, const cute_pair_desc *d,
                                      uint64_t *const *counts, double *const *wsum);
 
@@ -219,6 +222,21 @@ cute_status cute_set_timing(cute_ctx *ctx, int32_t on);
    edges).  Used by the autotuner and by tests of both binning paths. */
 cute_status cute_set_launch(cute_ctx *ctx, int32_t home_per_lane, int32_t warps_per_block,
                             int32_t slice, int32_t table_binning);
+
+/* Autotuner: picks the launch shape of the counting kernel for the given
+   descriptors (all sharing kind, edges and weighting) by timing candidates
+   on the GPU -- home objects per lane {2, 4}, warps per block {8, 12, 16}
+   (within shared memory), neighbour slice {1024, 2048, 4096} -- each on at
+   most max_items work items; if tune_cells, it also rebuilds the grids of
+   the descriptors' catalogs at 2, 3 and 4 cells per reach and keeps the
+   fastest.  The choice is remembered for these catalogs and used by later
+   counts (cute_set_launch overrides it).  *out (may be NULL) receives it. */
+typedef struct {
+  int32_t cells_per_reach, home_per_lane, warps_per_block, slice;
+  float ms; /* time of the chosen shape on the timed items */
+} cute_tuning;
+cute_status cute_autotune(cute_ctx *ctx, int32_t n, const cute_pair_desc *d, int32_t tune_cells,
+                          int64_t max_items, cute_tuning *out);
 
 /* ---------------------------------------------------------------- estimators
    Host FP64 arithmetic on exact counts (Sec. 2.2).  Counts are unique pairs.

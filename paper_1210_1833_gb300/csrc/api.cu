@@ -95,7 +95,8 @@ cute_status cute_ctx_create(int device, void *cuda_stream, cute_ctx **out) {
     }
     ctx->own_stream = true;
   }
-  if (cudaMalloc(&ctx->d_ticket, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+  if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&ctx->d_ticket, 8 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess ||
       cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess ||
       cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
@@ -112,7 +113,7 @@ cute_status cute_ctx_destroy(cute_ctx *ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ctx->plans.clear();
-  ctx->task_cache.clear();
+  ctx->clear_caches();
   for (auto &kv : ctx->cats) catalog_release(kv.second);
   ctx->cats.clear();
   cudaFree(ctx->d_ticket);
@@ -173,7 +174,7 @@ cute_status cute_catalog_free(cute_ctx *ctx, int32_t cat_id) {
   auto it = ctx->cats.find(cat_id);
   if (it == ctx->cats.end()) return fail(ctx, CUTE_E_STATE, "unknown catalog");
   CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
-  ctx->task_cache.clear();
+  ctx->clear_caches();
   catalog_release(it->second);
   ctx->cats.erase(it);
   return CUTE_OK;
@@ -209,7 +210,7 @@ cute_status cute_grid_build(cute_ctx *ctx, const int32_t *cat_ids, int32_t n_cat
       return fail(ctx, CUTE_E_INVALID, "catalogs of one grid must share boundary and box");
   }
   CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
-  ctx->task_cache.clear();
+  ctx->clear_caches();
   return grid_build(ctx, cats, reach, cells_per_reach);
 }
 
@@ -407,6 +408,17 @@ cute_status get_tasks(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, i
   return CUTE_OK;
 }
 
+// identity of a request for the autotuner's memory: kind, catalogs (and
+// their grid versions), accumulation policy, stencil
+std::string tuning_key(const std::vector<DescInfo> &dis, int acc, bool full_stencil) {
+  std::ostringstream k;
+  k << acc << "|" << full_stencil << "|";
+  for (const DescInfo &di : dis)
+    k << di.kind << ":" << di.A->id << ":" << di.A->grid_version << ":" << di.B->id << ":"
+      << di.B->grid_version << ",";
+  return k.str();
+}
+
 // common preparation of a (batched) count: validation, plan, tasks, params
 struct Prepared {
   std::vector<DescInfo> dis;
@@ -452,16 +464,25 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
     }
     pr.hp = (cells > 0 && objs / cells < 96.0) ? 2 : 4;
   }
+  int slice = ctx->slice_override ? ctx->slice_override : 2048;
+  int warps_tuned = 0;
+  {
+    auto it = ctx->tuned.find(tuning_key(pr.dis, acc, full_stencil));
+    if (it != ctx->tuned.end()) {
+      if (!ctx->hp_override) pr.hp = it->second.home_per_lane;
+      if (!ctx->slice_override) slice = it->second.slice;
+      warps_tuned = it->second.warps_per_block;
+    }
+  }
   cute_status st = get_plan(ctx, &d[0], ep, pr.hp, pr.plan);
   if (st != CUTE_OK) return st;
-  int slice = ctx->slice_override ? ctx->slice_override : 2048;
   st = get_tasks(ctx, pr.dis, pr.hp, slice, full_stencil, pr.ts);
   if (st != CUTE_OK) return st;
   const Plan &P = *pr.plan;
   SmemLayout L = smem_layout((int)P.lut.size(), (int)P.band.size() / 2, P.nslots, P.R, pr.hp, acc);
   pr.acc = acc;
   size_t avail = ctx->smem_optin;
-  int warps = ctx->warps_override ? ctx->warps_override : 16;
+  int warps = ctx->warps_override ? ctx->warps_override : (warps_tuned ? warps_tuned : 16);
   while (warps > 1 && (size_t)L.lut_bytes + (size_t)warps * L.warp_bytes > avail) warps--;
   if ((size_t)L.lut_bytes + (size_t)warps * L.warp_bytes > avail)
     return fail(ctx, CUTE_E_UNSUPPORTED,
@@ -498,19 +519,55 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
   return CUTE_OK;
 }
 
-cudaError_t launch_prepared(cute_ctx *ctx, const Prepared &pr, int kind) {
+cudaError_t launch_prepared(cute_ctx *ctx, const Prepared &pr, int kind,
+                            cudaStream_t stream = nullptr) {
   const bool per = pr.dis[0].g->periodic;
   const int threads = pr.warps * 32;
+  cudaStream_t st = stream ? stream : ctx->stream;
   switch (kind) {
     case CUTE_MONO:
-      return launch_count_mono(pr.p, per, pr.acc, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
+      return launch_count_mono(pr.p, per, pr.acc, pr.hp, pr.blocks, threads, pr.smem, st);
     case CUTE_THETA:
-      return launch_count_mono(pr.p, false, pr.acc, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
+      return launch_count_mono(pr.p, false, pr.acc, pr.hp, pr.blocks, threads, pr.smem, st);
     case CUTE_SIGMA_PI:
-      return launch_count_sigpi(pr.p, per, pr.acc, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
+      return launch_count_sigpi(pr.p, per, pr.acc, pr.hp, pr.blocks, threads, pr.smem, st);
     default:
-      return launch_count_rmu(pr.p, pr.acc, pr.hp, pr.blocks, threads, pr.smem, ctx->stream);
+      return launch_count_rmu(pr.p, pr.acc, pr.hp, pr.blocks, threads, pr.smem, st);
   }
+}
+
+// Capture the device work of a batched count into a CUDA graph (on the
+// private capture stream) and return its executable, or null if capture is
+// not possible here (the caller then launches normally).
+static cudaGraphExec_t capture_batched(cute_ctx *ctx, const Prepared &pr, int kind, int n, int nb,
+                                       bool weighted, unsigned long long *d_out, double *d_ws,
+                                       uint64_t *const *counts, double *const *wsum) {
+  cudaStream_t cs = ctx->cap_stream;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  bool ok = true;
+  ok = ok && cudaMemsetAsync(ctx->d_ticket, 0, 5 * sizeof(unsigned long long), cs) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(d_out, 0, sizeof(unsigned long long) * (size_t)nb * n, cs) == cudaSuccess;
+  if (weighted) ok = ok && cudaMemsetAsync(d_ws, 0, sizeof(double) * (size_t)nb * n, cs) == cudaSuccess;
+  if (ok && pr.p.total > 0) ok = launch_prepared(ctx, pr, kind, cs) == cudaSuccess;
+  for (int i = 0; ok && i < n; i++) {
+    ok = cudaMemcpyAsync(counts[i], d_out + (size_t)i * nb, sizeof(uint64_t) * nb,
+                         cudaMemcpyDeviceToDevice, cs) == cudaSuccess;
+    if (ok && weighted)
+      ok = cudaMemcpyAsync(wsum[i], d_ws + (size_t)i * nb, sizeof(double) * nb,
+                           cudaMemcpyDeviceToDevice, cs) == cudaSuccess;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  cudaGraphExec_t ex = nullptr;
+  if (ok && e == cudaSuccess && g) {
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  return ex;
 }
 
 // Counts (and weighted sums) of n pair sets into counts[k] / wsum[k] (host
@@ -543,6 +600,31 @@ cute_status count_driver(cute_ctx *ctx, int n, const cute_pair_desc *d, uint64_t
   ctx->stats.warps_per_block = pr.warps;
   ctx->stats.blocks = pr.blocks;
   ctx->stats.home_per_lane = pr.hp;
+  // batched counts into device outputs: replay a captured graph
+  bool all_dev = n > 1 && oor == nullptr;
+  for (int i = 0; all_dev && i < n; i++)
+    all_dev = is_device_ptr(counts[i]) && (!weighted || is_device_ptr(wsum[i]));
+  if (all_dev) {
+    std::ostringstream gk;
+    gk << tuning_key(pr.dis, weighted ? 1 : 0, false) << "|" << (const void *)pr.plan.get() << "|"
+       << (const void *)pr.ts.get() << "|" << pr.hp << "|" << pr.warps << "|" << pr.p.slice << "|"
+       << (const void *)d_out << "|" << (const void *)d_ws;
+    for (int i = 0; i < n; i++) gk << "|" << (const void *)counts[i] << "," << (const void *)(weighted ? wsum[i] : nullptr);
+    auto it = ctx->graphs.find(gk.str());
+    cudaGraphExec_t ex = (it != ctx->graphs.end()) ? it->second : nullptr;
+    if (!ex) {
+      CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+      ex = capture_batched(ctx, pr, (int)d[0].kind, n, nb, weighted, d_out, d_ws, counts, wsum);
+      if (ex) ctx->graphs[gk.str()] = ex;
+    }
+    if (ex) {
+      if (ctx->timing) CUDA_OR_FAIL(cudaEventRecord(ctx->ev0, ctx->stream));
+      CUDA_OR_FAIL(cudaGraphLaunch(ex, ctx->stream));
+      if (ctx->timing) CUDA_OR_FAIL(cudaEventRecord(ctx->ev1, ctx->stream));
+      ctx->stats.launches = pr.p.total > 0 ? 1 : 0;
+      return CUTE_OK;
+    }
+  }
   if (ctx->timing) CUDA_OR_FAIL(cudaEventRecord(ctx->ev0, ctx->stream));
   if (pr.p.total > 0) {
     CUDA_OR_FAIL(launch_prepared(ctx, pr, (int)d[0].kind));
@@ -684,6 +766,98 @@ cute_status cute_count_pairs_adjoint(cute_ctx *ctx, const cute_pair_desc *d, con
                                      double *grad_a, double *grad_b) {
   ENTER(ctx);
   return adjoint_driver(ctx, d, G, grad_a, grad_b);
+}
+
+
+cute_status cute_autotune(cute_ctx *ctx, int32_t n, const cute_pair_desc *d, int32_t tune_cells,
+                          int64_t max_items, cute_tuning *out) {
+  ENTER(ctx);
+  if (n < 1 || !d) return fail(ctx, CUTE_E_INVALID, "no descriptors");
+  if (max_items <= 0) max_items = (int64_t)1 << 40;
+  const int acc = d[0].weighted ? 1 : 0;
+  // catalogs grouped by grid geometry, to rebuild each group together
+  std::map<int, std::vector<int32_t>> groups;
+  for (int i = 0; i < n; i++) {
+    for (int32_t id : {d[i].cat_a, d[i].cat_b}) {
+      auto it = ctx->cats.find(id);
+      if (it == ctx->cats.end() || it->second.geom < 0)
+        return fail(ctx, CUTE_E_STATE, "descriptor catalog missing or without grid");
+      auto &g = groups[it->second.geom];
+      if (std::find(g.begin(), g.end(), id) == g.end()) g.push_back(id);
+    }
+  }
+  auto rebuild = [&](int k) -> cute_status {
+    std::map<int, std::vector<int32_t>> next;
+    for (auto &kv : groups) {
+      const Geometry g = ctx->geoms[kv.first];
+      std::vector<Catalog *> cs;
+      for (int32_t id : kv.second) cs.push_back(&ctx->cats[id]);
+      CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+      ctx->clear_caches();
+      cute_status st = grid_build(ctx, cs, g.reach, k);
+      if (st != CUTE_OK) return st;
+      next[cs[0]->geom] = kv.second;
+    }
+    groups.swap(next);
+    return CUTE_OK;
+  };
+  const int k0 = ctx->geoms[groups.begin()->first].kreq;
+  std::vector<int> ks = tune_cells ? std::vector<int>{2, 3, 4} : std::vector<int>{k0};
+  const int save_hp = ctx->hp_override, save_w = ctx->warps_override, save_s = ctx->slice_override;
+  cute_tuning best{k0, 0, 0, 0, INFINITY};
+  cute_status st = CUTE_OK;
+  for (int k : ks) {
+    if (tune_cells && (st = rebuild(k)) != CUTE_OK) break;
+    for (int hp : {2, 4})
+      for (int warps : {8, 12, 16})
+        for (int slice : {1024, 2048, 4096}) {
+          ctx->hp_override = hp;
+          ctx->warps_override = warps;
+          ctx->slice_override = slice;
+          Prepared pr;
+          if (prepare(ctx, n, d, acc, false, pr) != CUTE_OK) continue;
+          if (pr.warps != warps) continue;  // did not fit in shared memory
+          const int nb = pr.p.n0 * pr.p.n1;
+          const size_t cnt = sizeof(unsigned long long) * (size_t)nb * n;
+          const size_t ws = acc ? sizeof(double) * (size_t)nb * n : 0;
+          if (ensure_scratch(ctx, cnt + ws + 256) != CUTE_OK) continue;
+          pr.p.out_counts = (unsigned long long *)ctx->d_scratch;
+          pr.p.out_wsum = acc ? (double *)((char *)ctx->d_scratch + ((cnt + 255) & ~(size_t)255)) : nullptr;
+          pr.p.total = std::min<long long>(pr.p.total, max_items);
+          if (pr.p.total <= 0) continue;
+          float ms = 0;
+          for (int rep = 0; rep < 2; rep++) {  // the first run warms up
+            CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, 5 * sizeof(unsigned long long), ctx->stream));
+            CUDA_OR_FAIL(cudaEventRecord(ctx->ev0, ctx->stream));
+            CUDA_OR_FAIL(launch_prepared(ctx, pr, (int)d[0].kind));
+            CUDA_OR_FAIL(cudaEventRecord(ctx->ev1, ctx->stream));
+            CUDA_OR_FAIL(cudaEventSynchronize(ctx->ev1));
+            CUDA_OR_FAIL(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+          }
+          // compare by time per item so shapes with different item sizes
+          // are judged on the same work: scale to the full item count
+          const double full = (double)ms * ((double)pr.ts->prefix.back() / (double)pr.p.total);
+          if (full < best.ms) best = cute_tuning{k, hp, warps, slice, (float)full};
+        }
+  }
+  ctx->hp_override = save_hp;
+  ctx->warps_override = save_w;
+  ctx->slice_override = save_s;
+  if (st != CUTE_OK) return st;
+  if (!std::isfinite(best.ms)) return fail(ctx, CUTE_E_UNSUPPORTED, "no launch shape could run");
+  if (tune_cells && best.cells_per_reach != ks.back()) {
+    st = rebuild(best.cells_per_reach);
+    if (st != CUTE_OK) return st;
+  }
+  std::vector<DescInfo> dis(n);
+  for (int i = 0; i < n; i++) {
+    st = validate_desc(ctx, &d[i], dis[i]);
+    if (st != CUTE_OK) return st;
+    if (!dis[i].is_auto && dis[i].B->n > dis[i].A->n) std::swap(dis[i].A, dis[i].B);
+  }
+  ctx->tuned[tuning_key(dis, acc, false)] = best;
+  if (out) *out = best;
+  return CUTE_OK;
 }
 
 }  // extern "C"

@@ -117,6 +117,7 @@ struct Geometry {
   double a[3] = {1, 1, 1};
   int nc[3] = {1, 1, 1};
   int k[3] = {1, 1, 1};       // cells per reach on each axis
+  int kreq = 2;               // cells per reach requested
   double reach[3] = {0, 0, 0};
   double xmax[3] = {0, 0, 0}; // largest |x - origin| per axis over its catalogs
   double absmax[3] = {0, 0, 0}; // largest |x| (observer frame) per axis
@@ -190,6 +191,17 @@ struct cute_ctx {
   // caches
   std::map<std::string, std::shared_ptr<cute::Plan>> plans;
   std::map<std::string, std::shared_ptr<cute::TaskSet>> task_cache;
+  // autotuned launch shapes per (kind, catalogs, policy)
+  std::map<std::string, cute_tuning> tuned;
+  // CUDA graphs of batched counts with device outputs, replayed when the
+  // same request comes again; captured on a private stream
+  cudaStream_t cap_stream = nullptr;
+  std::map<std::string, cudaGraphExec_t> graphs;
+  void clear_caches() {
+    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+    task_cache.clear();
+  }
 };
 
 namespace cute {

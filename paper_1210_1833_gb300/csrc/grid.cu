@@ -310,6 +310,7 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
   if (ncell > (1LL << 28)) return fail(ctx, CUTE_E_UNSUPPORTED, "too many cells");
   g.id = ctx->next_geom++;
   g.version = ++ctx->version_counter;
+  g.kreq = kreq;
 
   GridDev gd;
   for (int k = 0; k < 3; k++) {

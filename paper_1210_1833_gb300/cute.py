@@ -26,7 +26,8 @@ SYMBOLS = ["cute_ctx_create", "cute_ctx_destroy", "cute_last_error", "cute_sync"
            "cute_catalog_upload", "cute_catalog_free", "cute_catalog_size", "cute_grid_build",
            "cute_count_pairs", "cute_count_pairs_batched", "cute_count_pairs_adjoint",
            "cute_count_pairs_noalloc",
-           "cute_last_stats", "cute_set_timing", "cute_set_launch", "cute_estimator",
+           "cute_last_stats", "cute_set_timing", "cute_set_launch", "cute_autotune",
+           "cute_estimator",
            "cute_theta_to_chord", "cute_version"]
 
 
@@ -41,6 +42,15 @@ class PairDesc(ctypes.Structure):
                 ("edges0", ctypes.c_void_p), ("n0", ctypes.c_int32),
                 ("edges1", ctypes.c_void_p), ("n1", ctypes.c_int32),
                 ("weighted", ctypes.c_int32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("cells_per_reach", ctypes.c_int32), ("home_per_lane", ctypes.c_int32),
+                ("warps_per_block", ctypes.c_int32), ("slice", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Stats(ctypes.Structure):
@@ -84,6 +94,7 @@ def lib():
             L.cute_last_stats.argtypes = [P, ctypes.POINTER(Stats)]
             L.cute_set_timing.argtypes = [P, i32]
             L.cute_set_launch.argtypes = [P, i32, i32, i32, i32]
+            L.cute_autotune.argtypes = [P, i32, P, i32, i64, ctypes.POINTER(Tuning)]
             L.cute_estimator.argtypes = [ctypes.c_int, P, P, P, i64, i64, i32, P, f64, P]
             L.cute_theta_to_chord.argtypes = [P, i32, P]
             L.cute_version.restype = ctypes.c_char_p
@@ -248,9 +259,11 @@ class Context:
                 wsum = wsum.reshape(n0, n1)
         return counts, (int(oor.value) if want_oor else None), wsum
 
-    def count_batched(self, kind, pairs, edges0, edges1=None, weighted=False):
+    def count_batched(self, kind, pairs, edges0, edges1=None, weighted=False, device=False):
         """pairs: list of (a, b) catalogs (b None: auto), counted in one launch.
-        Returns a list of (n0, n1) uint64 arrays (and wsum arrays if weighted)."""
+        Returns a list of (n0, n1) uint64 arrays (and wsum arrays if weighted).
+        device=True: outputs are CUDA tensors (int64 viewing uint64 counts);
+        repeated identical calls then replay a captured CUDA graph."""
         e0 = np.ascontiguousarray(edges0, dtype=np.float64)
         e1 = None if edges1 is None else np.ascontiguousarray(edges1, dtype=np.float64)
         n0 = len(e0) - 1
@@ -260,6 +273,19 @@ class Context:
         for i, (a, b) in enumerate(pairs):
             descs[i] = self._desc(kind, a, b, e0, e1 if kind in ("rmu", "sigpi") else None,
                                   weighted)
+        if device:
+            import torch
+            if not hasattr(self, "_dev_outs") or self._dev_outs[0] != (n, n0 * n1, weighted):
+                outs = [torch.zeros(n0 * n1, dtype=torch.int64, device="cuda") for _ in range(n)]
+                wso = ([torch.zeros(n0 * n1, dtype=torch.float64, device="cuda") for _ in range(n)]
+                       if weighted else None)
+                self._dev_outs = ((n, n0 * n1, weighted), outs, wso)
+            _, outs, ws = self._dev_outs
+            optr = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+            wptr = (ctypes.c_void_p * n)(*[o.data_ptr() for o in ws]) if weighted else None
+            _check(lib().cute_count_pairs_batched(self.handle, n, descs, optr, wptr), self.handle)
+            res = [o.view(n0, n1) for o in outs]
+            return (res, [w.view(n0, n1) for w in ws]) if weighted else res
         outs = [np.zeros(n0 * n1, dtype=np.uint64) for _ in range(n)]
         optr = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
         ws, wptr = None, None
@@ -291,6 +317,21 @@ class Context:
         _check(lib().cute_count_pairs_adjoint(self.handle, ctypes.byref(d), _ptr(Gc), _ptr(ga),
                                               _ptr(gb)), self.handle)
         return (ga, gb) if grad_b else ga
+
+    def autotune(self, kind, pairs, edges0, edges1=None, weighted=False, tune_cells=True,
+                 max_items=20000):
+        """Time launch shapes (and 2, 3, 4 cells per reach if tune_cells) on
+        these pair sets and keep the fastest for later counts."""
+        e0 = np.ascontiguousarray(edges0, dtype=np.float64)
+        e1 = None if edges1 is None else np.ascontiguousarray(edges1, dtype=np.float64)
+        descs = (PairDesc * len(pairs))()
+        for i, (a, b) in enumerate(pairs):
+            descs[i] = self._desc(kind, a, b, e0, e1 if kind in ("rmu", "sigpi") else None,
+                                  weighted)
+        t = Tuning()
+        _check(lib().cute_autotune(self.handle, len(pairs), descs, int(bool(tune_cells)),
+                                   int(max_items), ctypes.byref(t)), self.handle)
+        return t.as_dict()
 
     # -------------------------------------------------------------- misc
     def sync(self):

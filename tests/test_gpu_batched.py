@@ -64,3 +64,42 @@ def test_batched_weighted_equal_plain(ctx):
         np.testing.assert_allclose(ws[k], w1, rtol=1e-12)
     for a in cats:
         a.free()
+
+
+def test_batched_device_outputs_replay_graph(ctx):
+    """Device outputs: the first call captures a CUDA graph, later calls
+    replay it; every replay equals the plain counts."""
+    boxes = synthetic.c4_batched_sigpi(n_boxes=4, scale=0.02)
+    reach = [boxes[0].edges0[-1], boxes[0].edges0[-1], boxes[0].edges1[-1]]
+    cats, pairs = [], []
+    for b in boxes:
+        d = ctx.upload(b.data, periodic=True, L=b.L)
+        r = ctx.upload(b.randoms, periodic=True, L=b.L)
+        ctx.grid([d, r], reach)
+        cats.append((d, r))
+        pairs += [(d, None), (d, r), (r, None)]
+    e0, e1 = boxes[0].edges0, boxes[0].edges1
+    plain = [ctx.count("sigpi", a, b, e0, e1)[0] for a, b in pairs]
+    for _ in range(3):
+        out = ctx.count_batched("sigpi", pairs, e0, e1, device=True)
+        torch.cuda.synchronize()
+        for k in range(len(pairs)):
+            got = out[k].cpu().numpy().view(np.uint64)
+            assert got.tolist() == plain[k].tolist()
+    for d, r in cats:
+        d.free(); r.free()
+
+
+def test_autotune_keeps_counts_exact(ctx):
+    w = synthetic.c2_rmu_lightcone(scale=0.01)
+    d = ctx.upload(w.data)
+    r = ctx.upload(w.randoms)
+    ctx.grid([d, r], [w.edges0[-1]] * 3)
+    ref = [ctx.count("rmu", a, b, w.edges0, w.edges1)[0] for a, b in ((d, None), (d, r))]
+    t = ctx.autotune("rmu", [(d, r)], w.edges0, w.edges1, tune_cells=True, max_items=2000)
+    assert t["cells_per_reach"] in (2, 3, 4) and t["home_per_lane"] in (2, 4)
+    assert t["warps_per_block"] in (8, 12, 16) and t["slice"] in (1024, 2048, 4096)
+    got = [ctx.count("rmu", a, b, w.edges0, w.edges1)[0] for a, b in ((d, None), (d, r))]
+    for g, f in zip(got, ref):
+        assert g.tolist() == f.tolist()
+    d.free(); r.free()
