@@ -303,8 +303,92 @@ def run_gpu(args, w, rank, world):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
+    if not args.no_extras and not args.only:
+        line["rows"] = run_extras(ctx, dev)
     print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def run_extras(ctx, dev, reps=3, which="all"):
+    """The other rows of the path, measured beside the plain kernel:
+    batched xi(sigma, pi) of 64 periodic boxes in one persistent launch
+    (replayed CUDA graph) vs 192 separate counts, and the weighted forward
+    and the adjoint of 4M weighted objects vs the plain count."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, n=reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    out = {}
+    if which in ("all", "batched"):
+        out.update(_row_batched(ctx, dev, timed))
+    if which in ("all", "weighted"):
+        out.update(_row_weighted(ctx, dev, timed))
+    return out
+
+
+def _row_batched(ctx, dev, timed):
+    import torch
+    out = {}
+    boxes = synthetic.c4_batched_sigpi()
+    e0, e1 = boxes[0].edges0, boxes[0].edges1
+    reach = [e0[-1], e0[-1], e1[-1]]
+    cats, pairs = [], []
+    for b in boxes:
+        d = ctx.upload(b.data, periodic=True, L=b.L)
+        r = ctx.upload(b.randoms, periodic=True, L=b.L)
+        ctx.grid([d, r], reach, 3)
+        cats.append((d, r))
+        pairs += [(d, None), (d, r), (r, None)]
+    nb = (len(e0) - 1) * (len(e1) - 1)
+    plain_out = [torch.zeros(nb, dtype=torch.int64, device=f"cuda:{dev}") for _ in pairs]
+    t_b = timed(lambda: ctx.count_batched("sigpi", pairs, e0, e1, device=True))
+    t_p = timed(lambda: [ctx.count("sigpi", a, b, e0, e1, out=o, want_oor=False)
+                         for (a, b), o in zip(pairs, plain_out)])
+    binned = sum(int(c.sum()) for c in ctx.count_batched("sigpi", pairs, e0, e1, device=True))
+    out["batched_sigpi_64_boxes"] = {
+        "batched_ms": t_b, "plain_ms": t_p, "plain_over_batched": t_p / t_b,
+        "launches": {"batched": 1, "plain": len(pairs)}, "binned_pairs": binned,
+        "binned_pairs_per_s": binned / (t_b / 1e3), "graph_replay": True}
+    for d, r in cats:
+        d.free(); r.free()
+    return out
+
+
+def _row_weighted(ctx, dev, timed):
+    import torch
+    out = {}
+    w = synthetic.c5_weighted()
+    e = w.edges0
+    A = ctx.upload(w.data, weights=w.weights, periodic=True, L=w.L)
+    ctx.grid([A], [e[-1]] * 3, 3)
+    cnt = torch.zeros(len(e) - 1, dtype=torch.int64, device=f"cuda:{dev}")
+    ws = torch.zeros(len(e) - 1, dtype=torch.float64, device=f"cuda:{dev}")
+    G = torch.from_numpy(w.extra["G"]).to(f"cuda:{dev}")
+    t_plain = timed(lambda: ctx.count("mono", A, None, e, out=cnt, want_oor=False))
+    st = ctx.stats()
+    t_w = timed(lambda: ctx.count("mono", A, None, e, weighted=True, out=cnt, wsum_out=ws,
+                                  want_oor=False))
+    t_adj = timed(lambda: ctx.adjoint("mono", A, None, e, G=G))
+    binned = int(cnt.sum())
+    out["weighted_adjoint_4M"] = {
+        "plain_ms": t_plain, "weighted_ms": t_w, "adjoint_ms": t_adj,
+        "weighted_over_plain": t_w / t_plain, "adjoint_over_plain": t_adj / t_plain,
+        "binned_pairs": binned, "plain_binned_pairs_per_s": binned / (t_plain / 1e3),
+        "plain_candidate_pairs": st["candidate_pairs"], "plain_kernel_ms": st["kernel_ms"],
+        "plain_home_per_lane": st["home_per_lane"],
+        "plain_candidate_pairs_per_s": st["candidate_pairs"] / (st["kernel_ms"] / 1e3)}
+    A.free()
+    return out
 
 
 def main():
@@ -317,12 +401,27 @@ def main():
     ap.add_argument("--only", default="", help="profiling: run only these counts (e.g. RR)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle sample")
     ap.add_argument("--cpr", type=int, default=3, help="cells per reach of the grid")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched / weighted / adjoint measurements")
+    ap.add_argument("--row", default="", choices=["", "batched", "weighted"],
+                    help="profiling: run only this row (64-box batched sigma-pi, or the 4M "
+                         "weighted forward and adjoint) and print it")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if args.impl == "gb300" else "gloo")
+    if args.row and args.impl == "gb300":
+        import torch
+        from paper_1210_1833_gb300 import cute
+        dev = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(dev)
+        ctx = cute.Context(dev)
+        ctx.set_timing(True)
+        print(json.dumps(run_extras(ctx, dev, reps=max(1, args.steps), which=args.row)), flush=True)
+        ctx.close()
+        return
     w = synthetic.c2_rmu_lightcone(scale=args.scale)
     if args.impl == "reference":
         run_reference(args, w, rank, world)

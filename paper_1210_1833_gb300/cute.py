@@ -166,6 +166,10 @@ class Context:
     available (so library work is ordered with torch work), else a stream the
     library creates; or an integer cudaStream_t handle."""
 
+    # cudaStreamLegacy: the handle of the legacy default stream, whose
+    # cudaStream_t value 0 the C ABI reads as "create a stream"
+    _LEGACY_STREAM = 0x1
+
     def __init__(self, device: int = 0, stream=None):
         L = lib()
         if stream is None:
@@ -173,6 +177,8 @@ class Context:
                 import torch
                 if torch.cuda.is_available():
                     stream = torch.cuda.current_stream(device).cuda_stream
+                    if stream == 0:
+                        stream = self._LEGACY_STREAM
             except Exception:
                 stream = None
         h = ctypes.c_void_p()
