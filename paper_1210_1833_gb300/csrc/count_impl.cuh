@@ -214,14 +214,15 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__r
                                            const WarpSmem &w, const float4 *__restrict__ tile,
                                            int cnt, int gj0, Home<HP> &h, int lane,
                                            unsigned &near_count) {
-  constexpr int NP = 2 * HP;
+  constexpr int U = 8 / HP;  // neighbours per step: 8 pairs per lane per step
+  constexpr int NP = U * HP;
   const int slot_shift = 31 - __clz(p.R * 4);
-  for (int j = 0; j < cnt; j += 2) {
+  for (int j = 0; j < cnt; j += U) {
     uint32_t off[NP];
-    float wj[2];
+    float wj[U];
     unsigned nmask = 0;
 #pragma unroll
-    for (int u = 0; u < 2; u++) {
+    for (int u = 0; u < U; u++) {
       const float4 q = tile[j + u];
       wj[u] = q.w;
 #pragma unroll
@@ -266,6 +267,8 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__r
         ff_add(h.gh[k % HP], h.gl[k % HP], th, tl);
       }
     }
+    // rare: pairs inside an edge's error band join the warp's FP64 queue; the
+    // queue only grows here, so it is drained here when it holds 32
     if (__any_sync(kFull, nmask != 0u)) {
 #pragma unroll
       for (int k = 0; k < NP; k++) {
@@ -276,9 +279,9 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__r
           else atomicCAS(p.err, 0, (int)CUTE_E_DEVICE);
         }
       }
+      __syncwarp();
+      if (*w.qcnt >= 32) process_queue<KIND, ACC>(p, pd, w, lane, false);
     }
-    __syncwarp();
-    if (*w.qcnt >= 32) process_queue<KIND, ACC>(p, pd, w, lane, false);
   }
 }
 
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
       acc += bound;
     }
     items++;
-    slots += (unsigned long long)(32 * HP) * (unsigned long long)((je - js + 1) & ~1);
+    slots += (unsigned long long)(32 * HP) * (unsigned long long)((je - js + (8 / HP) - 1) & ~((8 / HP) - 1));
 
     const int code = tk.flags >> 8;
     const float Sx = PER ? shift_of(code & 3, pd.L32) : 0.0f;
@@ -473,7 +476,7 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
       }
       __syncwarp();
       int cnt = min(kTile, nj - tt * kTile);
-      cnt = (cnt + 1) & ~1;
+      cnt = (cnt + (8 / HP) - 1) & ~((8 / HP) - 1);  // whole steps; padded rows are sentinels
       tile_dispatch<KIND, HP, ACC>(p, lut, band, pd, w, w.tiles + (tt & 1) * kTile, cnt,
                                    js + tt * kTile, h, lane, mask, near_count);
       __syncwarp();
