@@ -242,6 +242,33 @@ def run_gpu(args, w, rank, world):
     for _ in range(args.warmup):
         step(d_dev, r_dev, False)
     torch.cuda.synchronize()
+    tuning = {}
+    if args.tune:
+        # cells per reach by whole steps, then each count's launch shape by
+        # the library's autotuner (remembered per problem shape, so the
+        # re-uploaded catalogs of the timed steps use it)
+        best = None
+        for cpr in (2, 3, 4):
+            args.cpr = cpr
+            step(d_dev, r_dev, False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step(d_dev, r_dev, False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if best is None or dt < best[0]:
+                best = (dt, cpr)
+        args.cpr = best[1]
+        cd, cr = ctx.upload(d_dev), ctx.upload(r_dev)
+        ctx.grid([cd, cr], reach, args.cpr)
+        for name, a, b in (("DD", cd, None), ("DR", cd, cr), ("RR", cr, None)):
+            tuning[name] = ctx.autotune("rmu", [(a, b)], w.edges0, w.edges1, tune_cells=False,
+                                        max_items=30000)
+        cd.free()
+        cr.free()
+        tuning["cells_per_reach"] = args.cpr
+        step(d_dev, r_dev, False)
+        torch.cuda.synchronize()
     clk = ClockSampler(dev)
     clk.start()
     t_dev = timed(d_dev, r_dev, args.steps, True)
@@ -279,7 +306,7 @@ def run_gpu(args, w, rank, world):
                    "bins": [len(w.edges0) - 1, len(w.edges1) - 1], "counts": ["DD", "DR", "RR"],
                    "estimator": "landy-szalay", "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "cells_per_reach": args.cpr},
+                   "cells_per_reach": args.cpr, "autotuned": tuning or None},
         "pairs": {"candidate_per_step": cand_per_step,
                   "in_range_per_step": inrange_per_step,
                   "all_pairs_per_step": total_pairs(nd, nr),
@@ -401,6 +428,8 @@ def main():
     ap.add_argument("--only", default="", help="profiling: run only these counts (e.g. RR)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle sample")
     ap.add_argument("--cpr", type=int, default=3, help="cells per reach of the grid")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="skip the warm-up autotuning (cells per reach, launch shapes)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched / weighted / adjoint measurements")
     ap.add_argument("--row", default="", choices=["", "batched", "weighted"],

@@ -411,11 +411,13 @@ cute_status get_tasks(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, i
 // identity of a request for the autotuner's memory: kind, catalogs (and
 // their grid versions), accumulation policy, stencil
 std::string tuning_key(const std::vector<DescInfo> &dis, int acc, bool full_stencil) {
+  // by problem shape (kind, sizes, cell grid), so re-uploaded catalogs of
+  // the same workload keep their tuning
   std::ostringstream k;
   k << acc << "|" << full_stencil << "|";
   for (const DescInfo &di : dis)
-    k << di.kind << ":" << di.A->id << ":" << di.A->grid_version << ":" << di.B->id << ":"
-      << di.B->grid_version << ",";
+    k << di.kind << ":" << di.is_auto << ":" << di.A->n << ":" << di.B->n << ":" << di.g->nc[0]
+      << "x" << di.g->nc[1] << "x" << di.g->nc[2] << ",";
   return k.str();
 }
 
@@ -775,17 +777,19 @@ cute_status cute_autotune(cute_ctx *ctx, int32_t n, const cute_pair_desc *d, int
   if (n < 1 || !d) return fail(ctx, CUTE_E_INVALID, "no descriptors");
   if (max_items <= 0) max_items = (int64_t)1 << 40;
   const int acc = d[0].weighted ? 1 : 0;
-  // catalogs grouped by grid geometry, to rebuild each group together
+  // the geometries the descriptors use, each with every catalog on it (all
+  // of them are rebuilt together, so counts between them stay possible)
   std::map<int, std::vector<int32_t>> groups;
   for (int i = 0; i < n; i++) {
     for (int32_t id : {d[i].cat_a, d[i].cat_b}) {
       auto it = ctx->cats.find(id);
       if (it == ctx->cats.end() || it->second.geom < 0)
         return fail(ctx, CUTE_E_STATE, "descriptor catalog missing or without grid");
-      auto &g = groups[it->second.geom];
-      if (std::find(g.begin(), g.end(), id) == g.end()) g.push_back(id);
+      groups[it->second.geom];
     }
   }
+  for (auto &kv : ctx->cats)
+    if (groups.count(kv.second.geom)) groups[kv.second.geom].push_back(kv.first);
   auto rebuild = [&](int k) -> cute_status {
     std::map<int, std::vector<int32_t>> next;
     for (auto &kv : groups) {

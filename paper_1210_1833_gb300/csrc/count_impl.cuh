@@ -23,11 +23,15 @@ struct Home {
   float w[HP];                 // weight (0 when padded)
   float gh[HP], gl[HP];        // adjoint: float-float gradient accumulator
   int id[HP];                  // sorted index in A (INT_MAX when padded)
+  float2 nx2[(HP + 1) / 2], ny2[(HP + 1) / 2], nz2[(HP + 1) / 2];  // -(x_2k, x_2k+1): packed math
 };
 
 struct WarpSmem {
   uint32_t *hist;
   char *hist_lane;
+  uint32_t s_hist_lane;        // shared-space address of hist_lane
+  uint32_t s_wcol;             // shared-space address of wcol
+  uint32_t s_G;                // shared-space address of G
   float2 *wcol;                // weighted: this lane's float-float column
   float2 *wall;                // weighted: all columns of the warp
   int wstride;                 // weighted: float2 entries per column
@@ -135,21 +139,21 @@ static __device__ __noinline__ void flush_wsum(const KParams &p, const WarpSmem 
 // Slot byte offset (slot * R * 4) of one candidate pair, and whether it lies
 // inside an edge's FP32 error band (then it must be re-tested in FP64).
 template <int KIND, int HP, int M0, int M1>
-__device__ __forceinline__ uint32_t bin_pair(const KParams &p, const uint32_t *__restrict__ lut,
-                                             const float2 *__restrict__ band, float dx, float dy,
-                                             float dz, const Home<HP> &h, int s, bool &near) {
+__device__ __forceinline__ uint32_t bin_pair(const KParams &p, uint32_t lut, uint32_t band,
+                                             float dx, float dy, float dz, const Home<HP> &h,
+                                             int s, bool &near) {
   const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u, stride1 = (uint32_t)p.R * 4u;
   uint32_t o;
   if ((KIND == KMONO || KIND == KTHETA) && M0 == kArith) {
     const float v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    const float x0 = __fmul_rn(v0, rsqrtf(__fadd_rn(v0, 1e-30f)));
+    const float x0 = __fmul_rn(v0, rsqrtf(v0));  // NaN for v0 = 0: see arith_t
     float h0;
     const float tm0 = arith_t(p.ax[0], x0, h0);
-    near = fabsf(h0) + p.ax[0].thr_b >= 0.5f;
+    near = fabsf(h0) >= p.ax[0].near_at;
     o = arith_off(tm0, stride0);
   } else if (KIND == KSIGPI && M0 == kArith) {
     const float v0 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
-    const float x0 = __fmul_rn(v0, rsqrtf(__fadd_rn(v0, 1e-30f)));
+    const float x0 = __fmul_rn(v0, rsqrtf(v0));  // NaN for v0 = 0: see arith_t
     float h0, h1;
     const float tm0 = arith_t(p.ax[0], x0, h0);
     const float tm1 = arith_t(p.ax[1], fabsf(dz), h1);
@@ -201,6 +205,27 @@ __device__ __forceinline__ uint32_t bin_pair(const KParams &p, const uint32_t *_
   return o;
 }
 
+// Monopole with uniform edges, two home objects at once with the packed
+// FP32 instructions of sm_100+ (element-wise IEEE round-to-nearest: each
+// element is rounded exactly as the scalar path rounds it).
+__device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2 qy, float2 qz,
+                                            float2 nx, float2 ny, float2 nz, uint32_t stride,
+                                            uint32_t &o0, uint32_t &o1, bool &n0, bool &n1) {
+  const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
+  const float2 v = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+  const float2 x = __fmul2_rn(v, make_float2(rsqrtf(v.x), rsqrtf(v.y)));  // NaN for v = 0
+  float2 t = __ffma2_rn(x, make_float2(a.inv, a.inv), make_float2(a.cst, a.cst));
+  t.x = fminf(fmaxf(t.x, a.tlo), a.thi);  // NaN -> tlo, the x = 0 side
+  t.y = fminf(fmaxf(t.y, a.tlo), a.thi);
+  const float2 tm = __fadd2_rn(t, make_float2(kMagic, kMagic));
+  const float2 fl = __fadd2_rn(tm, make_float2(-kMagic, -kMagic));
+  const float2 h = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), t);  // t - floor, exact
+  n0 = fabsf(h.x) >= a.near_at;
+  n1 = fabsf(h.y) >= a.near_at;
+  o0 = arith_off(tm.x, stride);
+  o1 = arith_off(tm.y, stride);
+}
+
 // All pairs of the HP home objects of each lane with the cnt neighbours of
 // one shared-memory tile (cnt even; rows past the slice hold sentinels).
 // Two neighbours at a time: every binning of the 2 x HP pairs is issued
@@ -209,9 +234,8 @@ __device__ __forceinline__ uint32_t bin_pair(const KParams &p, const uint32_t *_
 // MASK: 1 -- only j > i counts (the home run against itself, unique pairs);
 //       2 -- every j != i counts (full-stencil adjoint of an auto count).
 template <int KIND, int HP, int M0, int M1, int MASK, int ACC>
-__device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__restrict__ lut,
-                                           const float2 *__restrict__ band, const PairDev &pd,
-                                           const WarpSmem &w, const float4 *__restrict__ tile,
+__device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint32_t band,
+                                           const PairDev &pd, const WarpSmem &w, uint32_t tile,
                                            int cnt, int gj0, Home<HP> &h, int lane,
                                            unsigned &near_count) {
   constexpr int U = 8 / HP;  // neighbours per step: 8 pairs per lane per step
@@ -223,8 +247,30 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__r
     unsigned nmask = 0;
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      const float4 q = tile[j + u];
+      const float4 q = lds_f4(tile + 16u * (j + u));
       wj[u] = q.w;
+      if ((KIND == KMONO || KIND == KTHETA) && M0 == kArith && (HP % 2) == 0) {
+        const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
+                     qz = make_float2(q.z, q.z);
+        const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u;
+#pragma unroll
+        for (int sp = 0; sp < HP / 2; sp++) {
+          uint32_t o[2];
+          bool nr[2];
+          mono_arith2(p.ax[0], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], stride0, o[0], o[1],
+                      nr[0], nr[1]);
+#pragma unroll
+          for (int e = 0; e < 2; e++) {
+            const int s = 2 * sp + e, k = u * HP + s;
+            const int gj = gj0 + j + u;
+            if (MASK == 1 && !(gj > h.id[s])) { o[e] = 0u; nr[e] = false; }
+            if (MASK == 2 && gj == h.id[s]) { o[e] = 0u; nr[e] = false; }
+            if (nr[e]) { o[e] = 0u; nmask |= 1u << k; }
+            off[k] = o[e];
+          }
+        }
+        continue;
+      }
 #pragma unroll
       for (int s = 0; s < HP; s++) {
         const int k = u * HP + s;
@@ -242,7 +288,7 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__r
     }
     if (ACC != kAccAdjoint) {
 #pragma unroll
-      for (int k = 0; k < NP; k++) atomicAdd((unsigned *)(w.hist_lane + off[k]), 1u);
+      for (int k = 0; k < NP; k++) red_add1(w.s_hist_lane + off[k]);
     }
     if (ACC == kAccWeighted) {
       // lane-private float-float column: a read-modify-write, no atomics
@@ -251,16 +297,16 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__r
         const float a = h.w[k % HP], b = wj[k / HP];
         const float ph = __fmul_rn(a, b);
         const float pl = __fmaf_rn(a, b, -ph);  // exact: a * b = ph + pl
-        float2 *c = w.wcol + (off[k] >> slot_shift);
-        float2 v = *c;
+        const uint32_t c = w.s_wcol + 8u * (off[k] >> slot_shift);
+        float2 v = lds_f2(c);
         ff_add(v.x, v.y, ph, pl);
-        *c = v;
+        sts_f2(c, v);
       }
     }
     if (ACC == kAccAdjoint) {
 #pragma unroll
       for (int k = 0; k < NP; k++) {
-        const float2 g = w.G[off[k] >> slot_shift];  // slot 0 and trash: G = 0
+        const float2 g = lds_f2(w.s_G + 8u * (off[k] >> slot_shift));  // slot 0, trash: 0
         const float b = wj[k / HP];
         const float th = __fmul_rn(b, g.x);
         const float tl = __fmaf_rn(b, g.y, __fmaf_rn(b, g.x, -th));
@@ -286,9 +332,9 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, const uint32_t *__r
 }
 
 template <int KIND, int HP, int M0, int M1, int ACC>
-__device__ __forceinline__ void tile_dispatch_mask(const KParams &p, const uint32_t *lut,
-                                                   const float2 *band, const PairDev &pd,
-                                                   const WarpSmem &w, const float4 *tile, int cnt,
+__device__ __forceinline__ void tile_dispatch_mask(const KParams &p, uint32_t lut,
+                                                   uint32_t band, const PairDev &pd,
+                                                   const WarpSmem &w, uint32_t tile, int cnt,
                                                    int gj0, Home<HP> &h, int lane, int mask,
                                                    unsigned &dc) {
   if (mask == 1) tile_pairs<KIND, HP, M0, M1, 1, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, dc);
@@ -298,9 +344,9 @@ __device__ __forceinline__ void tile_dispatch_mask(const KParams &p, const uint3
 }
 
 template <int KIND, int HP, int ACC>
-__device__ __forceinline__ void tile_dispatch(const KParams &p, const uint32_t *lut,
-                                              const float2 *band, const PairDev &pd,
-                                              const WarpSmem &w, const float4 *tile, int cnt,
+__device__ __forceinline__ void tile_dispatch(const KParams &p, uint32_t lut,
+                                              uint32_t band, const PairDev &pd,
+                                              const WarpSmem &w, uint32_t tile, int cnt,
                                               int gj0, Home<HP> &h, int lane, int mask,
                                               unsigned &dc) {
   const int m0 = p.ax[0].mode;
@@ -375,6 +421,10 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
   w.queue = (int2 *)(wb + L.hist_bytes + 16);
   w.qcap = L.queue_cap;
   w.tiles = (float4 *)(wb + L.hist_bytes + L.queue_bytes);
+  w.s_hist_lane = smem_addr(w.hist_lane);
+  w.s_wcol = smem_addr(w.wcol);
+  w.s_G = smem_addr(w.G);
+  const uint32_t s_lut = smem_addr(lut), s_band = smem_addr(band);
   for (int i = lane; i < p.nslots * p.R; i += 32) w.hist[i] = 0u;
   if (ACC == kAccWeighted)
     for (int i = lane; i < 32 * w.wstride; i += 32) w.wall[i] = make_float2(0.0f, 0.0f);
@@ -453,6 +503,12 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
         if (KIND == KRMU) { h.ax[s] = kHomeFar; h.ay[s] = kHomeFar; h.az[s] = kHomeFar; h.aq[s] = kHomeFar; }
       }
     }
+#pragma unroll
+    for (int sp = 0; sp < HP / 2; sp++) {
+      h.nx2[sp] = make_float2(-h.x[2 * sp], -h.x[2 * sp + 1]);
+      h.ny2[sp] = make_float2(-h.y[2 * sp], -h.y[2 * sp + 1]);
+      h.nz2[sp] = make_float2(-h.z[2 * sp], -h.z[2 * sp + 1]);
+    }
 
     // stream the slice through the double-buffered tile
     const int nj = je - js;
@@ -477,8 +533,8 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
       __syncwarp();
       int cnt = min(kTile, nj - tt * kTile);
       cnt = (cnt + (8 / HP) - 1) & ~((8 / HP) - 1);  // whole steps; padded rows are sentinels
-      tile_dispatch<KIND, HP, ACC>(p, lut, band, pd, w, w.tiles + (tt & 1) * kTile, cnt,
-                                   js + tt * kTile, h, lane, mask, near_count);
+      tile_dispatch<KIND, HP, ACC>(p, s_lut, s_band, pd, w, smem_addr(w.tiles + (tt & 1) * kTile),
+                                   cnt, js + tt * kTile, h, lane, mask, near_count);
       __syncwarp();
     }
     if (ACC == kAccWeighted) flush_wsum(p, w, pd.out, lane);

@@ -68,10 +68,38 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Shared-memory accesses of the hot loop on 32-bit shared-space addresses
+// (explicit state space: no generic-address resolution per access).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ float4 lds_f4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float2 lds_f2(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts_f2(uint32_t a, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void red_add1(uint32_t a) {
+  asm volatile("red.shared.add.u32 [%0], 1;\n" ::"r"(a) : "memory");
+}
+
 // table lookup; MODE fixed per instantiation of the inner loop.  v is
 // clamped to the table's range in place (NaN becomes vmax).
 template <int MODE>
-__device__ __forceinline__ uint32_t lut_get(const uint32_t *lut, const AxisPlan &a, float &v) {
+__device__ __forceinline__ uint32_t lut_get(uint32_t lut, const AxisPlan &a, float &v) {
   v = fminf(v, a.vmax);
   unsigned idx;
   if (MODE == kLutLinear) {
@@ -81,17 +109,17 @@ __device__ __forceinline__ uint32_t lut_get(const uint32_t *lut, const AxisPlan 
     int i = (int)(__float_as_uint(v) >> a.shift) - a.base;
     idx = (unsigned)max(i, 0);
   }
-  return lut[a.lut_off + idx];
+  return lds_u32(lut + 4u * (a.lut_off + idx));
 }
 
 // Slot byte offset of value v on an axis whose bands are (lo, hi) pairs;
 // near is set when v lies inside the error band of the cell's edge.
-__device__ __forceinline__ uint32_t axis_resolve(const float2 *band, const AxisPlan &a, float v,
+__device__ __forceinline__ uint32_t axis_resolve(uint32_t band, const AxisPlan &a, float v,
                                                  uint32_t e, uint32_t stride, bool &near) {
   const uint32_t b = e >> kBandShift;
   uint32_t off = e & kOffMask;
   float2 bd = make_float2(__int_as_float(0x7f800000), __int_as_float(0x7f800000));
-  if (b != 0u) bd = band[a.band_off + b];
+  if (b != 0u) bd = lds_f2(band + 8u * (a.band_off + b));
   const bool above = v > bd.y;
   near = (v >= bd.x) && !above;
   return above ? off + stride : off;
@@ -104,7 +132,9 @@ constexpr float kMagic = 12582912.0f;        // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
 __device__ __forceinline__ float arith_t(const AxisPlan &a, float x, float &h) {
   float t = __fmaf_rn(x, a.inv, a.cst);
-  t = fmaxf(fminf(t, a.thi), a.tlo);  // NaN -> thi
+  // NaN -> tlo: x = v rsqrt(v) is NaN only for v = 0, i.e. x = 0, and tlo is
+  // the clamp on the x = 0 side (bin 0 when e_0 = 0, below range otherwise)
+  t = fminf(fmaxf(t, a.tlo), a.thi);
   const float tm = __fadd_rn(t, kMagic);
   h = __fsub_rn(t, __fsub_rn(tm, kMagic));
   return tm;
@@ -115,12 +145,12 @@ __device__ __forceinline__ uint32_t arith_off(float tm, uint32_t stride) {
 }
 
 // The same for mu: the band holds the edge, the bound comes from the r slot.
-__device__ __forceinline__ uint32_t mu_resolve(const float2 *band, const AxisPlan &a, float mu,
+__device__ __forceinline__ uint32_t mu_resolve(uint32_t band, const AxisPlan &a, float mu,
                                                uint32_t e, uint32_t stride, float eps, bool &near) {
   const uint32_t b = e >> kBandShift;
   uint32_t off = e & kOffMask;
   float m = __int_as_float(0x7f800000);
-  if (b != 0u) m = band[a.band_off + b].x;
+  if (b != 0u) m = lds_f2(band + 8u * (a.band_off + b)).x;
   const float d = __fsub_rn(mu, m);
   near = fabsf(d) <= eps;
   return (d > eps) ? off + stride : off;

@@ -49,6 +49,7 @@ struct AxisPlan {
   // |t - rint(t)| + thr >= 1/2, with thr = thr_a / x_r + thr_b for mu
   // (x_r the pair's r) and thr_b alone for the other axes.
   float inv = 0, cst = 0, tlo = 0, thi = 0, thr_a = 0, thr_b = 0;
+  float near_at = 0;  // 1/2 - thr_b rounded down: near when |h| >= near_at
 };
 
 // Kinds as the kernels see them.
