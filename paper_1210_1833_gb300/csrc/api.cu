@@ -237,11 +237,12 @@ cute_status cute_last_stats(cute_ctx *ctx, cute_stats *out) {
   ENTER(ctx);
   if (!out) return fail(ctx, CUTE_E_INVALID, "out is NULL");
   CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
-  unsigned long long h[5] = {0, 0, 0, 0, 0};
+  unsigned long long h[kCounterWords] = {0, 0, 0, 0, 0, 0};
   CUDA_OR_FAIL(cudaMemcpy(h, ctx->d_ticket, sizeof(h), cudaMemcpyDeviceToHost));
   ctx->stats.rechecked_pairs = h[1];
   ctx->stats.work_items = h[2];
   ctx->stats.pair_slots = h[4];
+  ctx->stats.candidate_pairs = h[5];
   if (ctx->timing && ctx->stats.launches > 0) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->stats.kernel_ms = ms;
@@ -369,10 +370,34 @@ cute_status get_tasks(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, i
     out = it->second;
     return CUTE_OK;
   }
+  if (dis.size() > 65536) return fail(ctx, CUTE_E_UNSUPPORTED, "more than 65536 pair sets");
   auto T = std::make_shared<TaskSet>();
+  const int home_chunk = 32 * hp;
+  std::vector<std::vector<int4>> chunks(dis.size()), stencils(dis.size());
+  size_t nch = 0, nst = 0;
+  T->ebase.assign(1, 0);
+  long long entries = 0;
+  for (size_t i = 0; i < dis.size(); i++) {
+    const DescInfo &di = dis[i];
+    if (di.A->n > 0 && di.B->n > 0) {
+      const int shape = (di.kind == CUTE_SIGMA_PI) ? kShapeDiskSlab : kShapeBall;
+      chunks_build(*di.g, di.A->h_cell_start, home_chunk, chunks[i]);
+      stencil_build(*di.g, di.is_auto, full_stencil, shape, di.need, stencils[i]);
+    }
+    nch += chunks[i].size();
+    nst += stencils[i].size();
+    entries += (long long)chunks[i].size() * (long long)stencils[i].size();
+    if (entries > (1LL << 30)) return fail(ctx, CUTE_E_UNSUPPORTED, "too many work entries");
+    T->ebase.push_back((int)entries);
+  }
+  T->nentries = (int)entries;
+  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_chunks, std::max<size_t>(nch, 1) * sizeof(int4)));
+  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_stencil, std::max<size_t>(nst, 1) * sizeof(int4)));
+  size_t oc = 0, os = 0;
   for (size_t i = 0; i < dis.size(); i++) {
     const DescInfo &di = dis[i];
     PairDev pd;
+    std::memset(&pd, 0, sizeof(pd));
     pd.posA = di.A->d_pos;
     pd.posB = di.B->d_pos;
     pd.sA = di.A->d_s64;
@@ -384,25 +409,51 @@ cute_status get_tasks(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, i
     pd.is_auto = di.is_auto;
     pd.L32 = (float)di.g->L;
     pd.L64 = di.g->periodic ? di.g->L : 0.0;
+    PairWork pw;
+    std::memset(&pw, 0, sizeof(pw));
+    pw.chunks = T->d_chunks + oc;
+    pw.stencil = T->d_stencil + os;
+    pw.csB = di.B->d_cell_start;
+    pw.nchunks = (int32_t)chunks[i].size();
+    pw.nstencil = std::max<int32_t>(1, (int32_t)stencils[i].size());
+    pw.nx = di.g->nc[0];
+    pw.ny = di.g->nc[1];
+    pw.nz = di.g->nc[2];
+    pw.mode = !di.is_auto ? kModeCross : (full_stencil ? kModeAutoFull : kModeAutoHalf);
+    pw.periodic = di.g->periodic;
+    T->work.push_back(pw);
     T->pairs.push_back(pd);
-    if (di.A->n == 0 || di.B->n == 0) continue;
-    const int shape = (di.kind == CUTE_SIGMA_PI) ? kShapeDiskSlab : kShapeBall;
-    tasks_build(*di.g, di.A->h_cell_start, di.B->h_cell_start, di.is_auto, (int)i, 32 * hp, slice,
-                full_stencil, shape, di.need, T->tasks, T->candidates);
+    if (!chunks[i].empty())
+      CUDA_OR_FAIL(cudaMemcpyAsync(T->d_chunks + oc, chunks[i].data(), chunks[i].size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+    if (!stencils[i].empty())
+      CUDA_OR_FAIL(cudaMemcpyAsync(T->d_stencil + os, stencils[i].data(),
+                                   stencils[i].size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    oc += chunks[i].size();
+    os += stencils[i].size();
   }
-  T->prefix.resize(T->tasks.size() + 1);
-  T->prefix[0] = 0;
-  for (size_t t = 0; t < T->tasks.size(); t++)
-    T->prefix[t + 1] = T->prefix[t] + (long long)T->tasks[t].n_hc * T->tasks[t].n_sc;
-  auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
-    cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
-    if (e != cudaSuccess) return e;
-    if (bytes == 0) return cudaSuccess;
-    return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
-  };
-  CUDA_OR_FAIL(up((void **)&T->d_tasks, T->tasks.data(), T->tasks.size() * sizeof(Task)));
-  CUDA_OR_FAIL(up((void **)&T->d_prefix, T->prefix.data(), T->prefix.size() * sizeof(long long)));
-  CUDA_OR_FAIL(up((void **)&T->d_pairs, T->pairs.data(), T->pairs.size() * sizeof(PairDev)));
+  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_pairs, T->pairs.size() * sizeof(PairDev)));
+  CUDA_OR_FAIL(cudaMemcpyAsync(T->d_pairs, T->pairs.data(), T->pairs.size() * sizeof(PairDev),
+                               cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_work, T->work.size() * sizeof(PairWork)));
+  CUDA_OR_FAIL(cudaMemcpyAsync(T->d_work, T->work.data(), T->work.size() * sizeof(PairWork),
+                               cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_ebase, T->ebase.size() * sizeof(int)));
+  CUDA_OR_FAIL(cudaMemcpyAsync(T->d_ebase, T->ebase.data(), T->ebase.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_cnt, std::max(T->nentries, 1) * sizeof(int)));
+  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_bsum, work_bsum_words(T->nentries) * sizeof(long long)));
+  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_eprefix, (T->nentries + 1) * sizeof(long long)));
+  CUDA_OR_FAIL(work_count(T->d_work, T->d_ebase, (int)T->pairs.size(), T->nentries, slice,
+                          T->d_cnt, T->d_bsum, T->d_eprefix, ctx->stream));
+  // the item count sizes the record list: one round trip per work list
+  CUDA_OR_FAIL(cudaMemcpyAsync(&T->items, T->d_eprefix + T->nentries, sizeof(long long),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_items, std::max<long long>(T->items, 1) * sizeof(int4)));
+  CUDA_OR_FAIL(work_write(T->d_work, T->d_ebase, (int)T->pairs.size(), T->nentries, slice,
+                          T->d_eprefix, T->d_items, ctx->stream));
   ctx->task_cache[key.str()] = T;
   out = T;
   return CUTE_OK;
@@ -495,10 +546,8 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
   pr.blocks = ctx->sm_count;
   KParams &p = pr.p;
   std::memset(&p, 0, sizeof(p));
-  p.tasks = pr.ts->d_tasks;
-  p.prefix = pr.ts->d_prefix;
-  p.ntasks = (int)pr.ts->tasks.size();
-  p.total = pr.ts->prefix.back();
+  p.items = pr.ts->d_items;
+  p.total = pr.ts->items;
   p.pairs = pr.ts->d_pairs;
   p.lut = P.d_lut;
   p.lut_words = (int)P.lut.size();
@@ -550,7 +599,7 @@ static cudaGraphExec_t capture_batched(cute_ctx *ctx, const Prepared &pr, int ki
     return nullptr;
   }
   bool ok = true;
-  ok = ok && cudaMemsetAsync(ctx->d_ticket, 0, 5 * sizeof(unsigned long long), cs) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(ctx->d_ticket, 0, kCounterWords * sizeof(unsigned long long), cs) == cudaSuccess;
   ok = ok && cudaMemsetAsync(d_out, 0, sizeof(unsigned long long) * (size_t)nb * n, cs) == cudaSuccess;
   if (weighted) ok = ok && cudaMemsetAsync(d_ws, 0, sizeof(double) * (size_t)nb * n, cs) == cudaSuccess;
   if (ok && pr.p.total > 0) ok = launch_prepared(ctx, pr, kind, cs) == cudaSuccess;
@@ -596,9 +645,8 @@ cute_status count_driver(cute_ctx *ctx, int n, const cute_pair_desc *d, uint64_t
   pr.p.out_wsum = d_ws;
   CUDA_OR_FAIL(cudaMemsetAsync(d_out, 0, cnt_bytes, ctx->stream));
   if (weighted) CUDA_OR_FAIL(cudaMemsetAsync(d_ws, 0, ws_bytes, ctx->stream));
-  CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, 5 * sizeof(unsigned long long), ctx->stream));
+  CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, kCounterWords * sizeof(unsigned long long), ctx->stream));
   ctx->stats = cute_stats{};
-  ctx->stats.candidate_pairs = pr.ts->candidates;
   ctx->stats.warps_per_block = pr.warps;
   ctx->stats.blocks = pr.blocks;
   ctx->stats.home_per_lane = pr.hp;
@@ -686,10 +734,10 @@ static cute_status adjoint_pass(cute_ctx *ctx, const cute_pair_desc *d, const do
     d_grad = (double *)ctx->d_scratch;
   }
   CUDA_OR_FAIL(cudaMemsetAsync(d_grad, 0, gbytes, ctx->stream));
-  CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, 5 * sizeof(unsigned long long), ctx->stream));
+  // the ticket only: the statistics add up over the passes
+  CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, sizeof(unsigned long long), ctx->stream));
   pr.p.G = d_G;
   pr.p.grad = d_grad;
-  ctx->stats.candidate_pairs += pr.ts->candidates;
   ctx->stats.warps_per_block = pr.warps;
   ctx->stats.blocks = pr.blocks;
   ctx->stats.home_per_lane = pr.hp;
@@ -721,6 +769,7 @@ cute_status adjoint_driver(cute_ctx *ctx, const cute_pair_desc *d, const double 
   CUDA_OR_FAIL(cudaMallocAsync((void **)&d_G, sizeof(double) * nb, ctx->stream));
   CUDA_OR_FAIL(cudaMemcpyAsync(d_G, G, sizeof(double) * nb, cudaMemcpyDefault, ctx->stream));
   ctx->stats = cute_stats{};
+  CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, kCounterWords * sizeof(unsigned long long), ctx->stream));
   if (ctx->timing) CUDA_OR_FAIL(cudaEventRecord(ctx->ev0, ctx->stream));
   bool need_sync = false;
   st = adjoint_pass(ctx, d, d_G, grad_a, &need_sync);
@@ -831,7 +880,7 @@ cute_status cute_autotune(cute_ctx *ctx, int32_t n, const cute_pair_desc *d, int
           if (pr.p.total <= 0) continue;
           float ms = 0;
           for (int rep = 0; rep < 2; rep++) {  // the first run warms up
-            CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, 5 * sizeof(unsigned long long), ctx->stream));
+            CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, kCounterWords * sizeof(unsigned long long), ctx->stream));
             CUDA_OR_FAIL(cudaEventRecord(ctx->ev0, ctx->stream));
             CUDA_OR_FAIL(launch_prepared(ctx, pr, (int)d[0].kind));
             CUDA_OR_FAIL(cudaEventRecord(ctx->ev1, ctx->stream));
@@ -840,7 +889,7 @@ cute_status cute_autotune(cute_ctx *ctx, int32_t n, const cute_pair_desc *d, int
           }
           // compare by time per item so shapes with different item sizes
           // are judged on the same work: scale to the full item count
-          const double full = (double)ms * ((double)pr.ts->prefix.back() / (double)pr.p.total);
+          const double full = (double)ms * ((double)pr.ts->items / (double)pr.p.total);
           if (full < best.ms) best = cute_tuning{k, hp, warps, slice, (float)full};
         }
   }

@@ -368,23 +368,6 @@ __device__ __forceinline__ void tile_dispatch(const KParams &p, uint32_t lut,
   }
 }
 
-// 32-ary search for the task holding work item `item`: largest t with
-// prefix[t] <= item.  Warp-uniform.
-__device__ __forceinline__ int find_task(const long long *__restrict__ prefix, int ntasks,
-                                         long long item, int lane) {
-  int lo = 0, hi = ntasks;
-  while (hi - lo > 1) {
-    int step = (hi - lo + 31) >> 5;
-    int cand = lo + lane * step;
-    bool ok = (cand < hi) && (prefix[cand] <= item);
-    unsigned m = __ballot_sync(kFull, ok);
-    int last = 31 - __clz(m);
-    lo = lo + last * step;
-    hi = min(hi, lo + step);
-  }
-  return lo;
-}
-
 __device__ __forceinline__ float shift_of(int code, float L) {
   return code == 1 ? L : (code == 2 ? -L : 0.0f);
 }
@@ -434,29 +417,26 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
   constexpr int CH = 32 * HP;
   int cur_pair = -1;
   PairDev pd;
-  unsigned long long acc = 0, items = 0, slots = 0;
+  unsigned long long acc = 0, items = 0, slots = 0, cand = 0;
   unsigned near_count = 0;
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(p.ticket, 1ull);
     item = __shfl_sync(kFull, item, 0);
     if ((long long)item >= p.total) break;
-    const int t = find_task(p.prefix, p.ntasks, (long long)item, lane);
-    const Task tk = p.tasks[t];
-    const long long local = (long long)item - p.prefix[t];
-    const int hc = (int)(local / tk.n_sc), sc = (int)(local - (long long)hc * tk.n_sc);
-    if (tk.pair != cur_pair) {
+    const int4 rec = p.items[item];
+    const int pi = (int)((unsigned)rec.w >> 16);
+    if (pi != cur_pair) {
       if (cur_pair >= 0) {
         process_queue<KIND, ACC>(p, pd, w, lane, true);
         if (ACC != kAccAdjoint) flush_hist(p, w, pd.out, lane);
         acc = 0;
       }
-      cur_pair = tk.pair;
+      cur_pair = pi;
       pd = p.pairs[cur_pair];
     }
-    const int hs = tk.h0 + hc * CH, he = min(hs + CH, tk.h1);
-    const int js = tk.j0 + sc * p.slice, je = min(js + p.slice, tk.j1);
-    const int mask = (tk.flags & kTaskSelf) ? 1 : ((tk.flags & kTaskNoSelfPair) ? 2 : 0);
+    const int hs = rec.x, he = hs + (rec.w & 0xff), js = rec.y, je = rec.z;
+    const int mask = (rec.w >> 8) & 3;
     if (mask == 1 && je <= hs + 1) continue;  // every j precedes every i
     // uint32 overflow guard: increments a copy can receive from this item
     if (ACC != kAccAdjoint) {
@@ -471,7 +451,7 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
     items++;
     slots += (unsigned long long)(32 * HP) * (unsigned long long)((je - js + (8 / HP) - 1) & ~((8 / HP) - 1));
 
-    const int code = tk.flags >> 8;
+    const int code = (rec.w >> 10) & 63;
     const float Sx = PER ? shift_of(code & 3, pd.L32) : 0.0f;
     const float Sy = PER ? shift_of((code >> 2) & 3, pd.L32) : 0.0f;
     const float Sz = PER ? shift_of((code >> 4) & 3, pd.L32) : 0.0f;
@@ -488,6 +468,10 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
         h.z[s] = __fsub_rn(a.z, Sz);
         h.w[s] = a.w;
         h.id[s] = idx;
+        // candidate pairs: j in [js, je), with j > i (self) or j != i
+        const int nj = je - js;
+        cand += mask == 1 ? (unsigned)max(0, je - max(js, idx + 1))
+                          : (unsigned)(nj - (mask == 2 && idx >= js && idx < je ? 1 : 0));
         if (KIND == KRMU) {
           const double X = pd.sA[idx], Y = pd.sA[(size_t)pd.nA + idx],
                        Z = pd.sA[2 * (size_t)pd.nA + idx];
@@ -553,6 +537,8 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
   }
   if (lane == 0 && items) atomicAdd(&p.stats[1], items);
   if (lane == 0 && slots) atomicAdd(&p.stats[3], slots);
+  for (int o = 16; o > 0; o >>= 1) cand += __shfl_xor_sync(kFull, cand, o);
+  if (lane == 0 && cand) atomicAdd(&p.stats[4], cand);
   for (int o = 16; o > 0; o >>= 1) near_count += __shfl_xor_sync(kFull, near_count, o);
   if (lane == 0 && near_count) atomicAdd(&p.stats[2], (unsigned long long)near_count);
 }

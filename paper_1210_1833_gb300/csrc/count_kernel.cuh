@@ -32,6 +32,90 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr float kHomeFar = 3.0e18f;
 constexpr float kNbrFar = -1.0e18f;
 
+// ------------------------------------------------------------------ work entries
+// One contiguous range [j0, j1) of catalog B that a home chunk meets, with
+// its flags (kTaskSelf / kTaskNoSelfPair, image shift code in bits 8..13).
+struct Seg {
+  int j0, j1, flags;
+};
+
+// Segments of work entry (chunk c, stencil row r) of pair set pd, in a fixed
+// order; returns their number (0..3).  cs is catalog B's cell_start (device
+// or host copy).  Every pair of objects within reach is met by exactly one
+// entry: cross counts and full stencils pair each chunk with the whole
+// x-range of every stencil row; the half stencil of an auto count pairs a
+// chunk with its own cell run (j > i) and the cells after it on the home row,
+// and with the later rows in full.
+__host__ __device__ inline int entry_segments(const PairWork &pd, const int32_t *cs, int4 c, int4 r,
+                                              Seg s[3]) {
+  const int nx = pd.nx, ny = pd.ny, nz = pd.nz;
+  const bool per = pd.periodic != 0;
+  const int cx0 = c.z & 0xffff, cx1 = c.z >> 16, cy = c.w & 0xffff, cz = c.w >> 16;
+  int y = cy + r.x, z = cz + r.y, sy = 0, sz = 0;
+  if (per) {
+    if (y < 0) { y += ny; sy = 2; } else if (y >= ny) { y -= ny; sy = 1; }
+    if (z < 0) { z += nz; sz = 2; } else if (z >= nz) { z -= nz; sz = 1; }
+  } else if (y < 0 || y >= ny || z < 0 || z >= nz) {
+    return 0;
+  }
+  const int32_t *row = cs + ((size_t)z * ny + y) * nx;
+  const int syz = (sy << 2) | (sz << 4);
+  int n = 0, xa, xb, f;
+  if (r.w && pd.mode == kModeAutoHalf) {
+    // A and B are one catalog: the chunk against the rest of its cell run
+    const int e = row[cx1 + 1];
+    if (e > c.x) s[n++] = Seg{c.x, e, kTaskSelf};
+    xa = cx1 + 1;
+    xb = cx1 + r.z;
+    f = 0;
+  } else {
+    xa = cx0 - r.z;
+    xb = cx1 + r.z;
+    f = (r.w && pd.mode == kModeAutoFull) ? kTaskNoSelfPair : 0;
+  }
+  const int lo = xa > 0 ? xa : 0, hi = xb < nx - 1 ? xb : nx - 1;
+  if (per) {
+    // the range is never longer than nx: at most the part left of the box
+    // (image x - L), the part inside, the part right of it (image x + L)
+    if (xa < 0) {
+      const int j0 = row[xa + nx], j1 = row[(xb + nx < nx - 1 ? xb + nx : nx - 1) + 1];
+      if (j1 > j0) s[n++] = Seg{j0, j1, f | ((2 | syz) << 8)};
+    }
+    if (lo <= hi) {
+      const int j0 = row[lo], j1 = row[hi + 1];
+      if (j1 > j0) s[n++] = Seg{j0, j1, f | (syz << 8)};
+    }
+    if (xb >= nx && n < 3) {
+      const int j0 = row[xa - nx > 0 ? xa - nx : 0], j1 = row[xb - nx + 1];
+      if (j1 > j0) s[n++] = Seg{j0, j1, f | ((1 | syz) << 8)};
+    }
+  } else if (lo <= hi) {
+    const int j0 = row[lo], j1 = row[hi + 1];
+    if (j1 > j0) s[n++] = Seg{j0, j1, f};
+  }
+  return n;
+}
+
+// Work item record (int4): home objects [x, x + (w & 0xff)) of pair set
+// w >> 16 against neighbours [y, z); bits 8..9 of w: kTaskSelf /
+// kTaskNoSelfPair, bits 10..15: image shift code.
+__host__ __device__ inline int4 item_record(int hs, int he, const Seg &g, int js, int je,
+                                            int pair) {
+  return make_int4(hs, js, je,
+                   (he - hs) | ((g.flags & 3) << 8) | (((g.flags >> 8) & 63) << 10) |
+                       (int)((unsigned)pair << 16));
+}
+
+// Locate entry e: its pair set (largest p with ebase[p] <= e).
+__device__ __forceinline__ int pair_of_entry(const int *__restrict__ ebase, int npairs, int e) {
+  int lo = 0, hi = npairs;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (ebase[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 struct SmemLayout {
   int lut_bytes;      // table block: lookup tables, then bands (16-byte multiple)
   int hist_bytes;     // per warp

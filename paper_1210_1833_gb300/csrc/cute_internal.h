@@ -55,20 +55,24 @@ struct AxisPlan {
 // Kinds as the kernels see them.
 constexpr int KMONO = 0, KRMU = 1, KSIGPI = 2, KTHETA = 3;
 
-// A task: the home objects [h0,h1) of catalog A (a run of cells of one row)
-// against one contiguous slice [j0,j1) of catalog B (one row of neighbour
-// cells), with one periodic image shift.  The kernel splits it into
-// n_hc x n_sc work items of at most (32 x home_per_lane) x slice pairs.
-struct Task {
-  int32_t h0, h1, j0, j1;
-  int32_t pair;    // index of the PairDev this task belongs to
-  int32_t flags;   // bit 0: self (only j > i); bits 8..13: image shift code
-  int32_t n_hc, n_sc;
-};
+// Work decomposition.  Catalog A is cut into home CHUNKS of at most
+// 32 x home_per_lane objects that lie in one row of cells (cx0..cx1, cy, cz);
+// the STENCIL lists the neighbour rows (dy, dz) a chunk can reach, each with
+// the x-extent kxr.  A work ENTRY is (chunk, stencil row): the chunk against
+// the objects of catalog B in that row, in at most three contiguous
+// SEGMENTS (the home cell run itself with j > i on the home row of an auto
+// count, and the row's x-range split where it wraps around a periodic box).
+// A segment splits into slices of at most `slice` neighbours: one work item
+// each, written as a 16-byte record (item_record) on the GPU.
+//   chunk int4: (h0, h1, cx0 | cx1 << 16, cy | cz << 16)
+//   stencil row int4: (dy, dz, kxr, 1 on the home row)
 constexpr int kTaskSelf = 1;        // only j > i (unique pairs of a run with itself)
 constexpr int kTaskNoSelfPair = 2;  // every j != i (full-stencil adjoint of an auto count)
+constexpr int kCounterWords = 6;  // work ticket + 5 statistics words
+constexpr int kModeCross = 0, kModeAutoHalf = 1, kModeAutoFull = 2;
 
-// One pair set (cat_a, cat_b) of a (possibly batched) count.
+// One pair set (cat_a, cat_b) of a (possibly batched) count, as the
+// counting kernel sees it.
 struct PairDev {
   const float4 *posA, *posB;   // cell-sorted FP32 (x, y, z, w), grid frame
   const double *sA, *sB;       // cell-sorted FP64 SoA (x[n], y[n], z[n])
@@ -80,11 +84,20 @@ struct PairDev {
   double L64;                  // periodic box in FP64, 0 for open
 };
 
+// The same pair set as the work builder sees it.
+struct PairWork {
+  const int4 *chunks;          // home chunks of A
+  const int4 *stencil;         // stencil rows
+  const int32_t *csB;          // cell_start of B (ncell + 1)
+  int32_t nchunks, nstencil;
+  int32_t nx, ny, nz;          // cells per axis
+  int32_t mode;                // kModeCross / kModeAutoHalf / kModeAutoFull
+  int32_t periodic;
+};
+
 struct KParams {
-  const Task *tasks;
-  const long long *prefix;     // ntasks + 1 work-item prefix sums
-  int ntasks;
-  long long total;             // work items
+  const int4 *items;           // work item records
+  long long total;             // work items handed out
   const PairDev *pairs;
   const uint32_t *lut;         // table words, all axes
   int lut_words;
@@ -102,7 +115,9 @@ struct KParams {
   unsigned long long *out_counts;  // [nout][n0 * n1]
   double *out_wsum;                // [nout][n0 * n1] or null
   unsigned long long *ticket;      // work-item counter
-  unsigned long long *stats;       // [0] rechecked, [1] items, [2] near-band, [3] pair slots
+  unsigned long long *stats;       // [0] rechecked, [1] items, [2] near-band, [3] pair slots,
+                                   // [4] candidate pairs
+  // (ticket and stats are kCounterWords consecutive words, zeroed per launch)
   int *err;                        // first error code seen by a kernel
   // adjoint
   const double *G;                 // [n0 * n1] upstream gradient
@@ -147,20 +162,34 @@ struct Catalog {
 
 struct Plan;  // binning plan (plan.cpp)
 
-// Device copy of the tasks, work-item prefix sums and pair descriptors of a
-// (possibly batched) count; cached per set of catalogs and launch shape.
+// The work decomposition of a (possibly batched) count on the device:
+// chunks, stencils and pair descriptors built on the host, entry item counts
+// and their prefix sums computed on the GPU.  Cached per set of catalogs and
+// launch shape.
 struct TaskSet {
-  std::vector<Task> tasks;
-  std::vector<long long> prefix;
   std::vector<PairDev> pairs;
-  unsigned long long candidates = 0;
-  Task *d_tasks = nullptr;
-  long long *d_prefix = nullptr;
+  std::vector<PairWork> work;
+  std::vector<int> ebase;          // npairs + 1
+  int nentries = 0;
+  int4 *d_chunks = nullptr, *d_stencil = nullptr;
   PairDev *d_pairs = nullptr;
+  PairWork *d_work = nullptr;
+  int *d_ebase = nullptr;
+  int *d_cnt = nullptr;            // items per entry
+  long long *d_bsum = nullptr;     // scan block sums
+  long long *d_eprefix = nullptr;  // nentries + 1
+  long long items = 0;             // work items
+  int4 *d_items = nullptr;         // their records
   ~TaskSet() {
-    cudaFree(d_tasks);
-    cudaFree(d_prefix);
+    cudaFree(d_chunks);
+    cudaFree(d_stencil);
     cudaFree(d_pairs);
+    cudaFree(d_work);
+    cudaFree(d_ebase);
+    cudaFree(d_cnt);
+    cudaFree(d_bsum);
+    cudaFree(d_eprefix);
+    cudaFree(d_items);
   }
 };
 
@@ -248,12 +277,28 @@ struct DescInfo {
 cute_status validate_desc(cute_ctx *ctx, const cute_pair_desc *d, DescInfo &di);
 ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax);
 
-// Task list for one pair set of catalogs on a shared geometry.  shape: the
-// region of separations that can fall in a bin, used to trim neighbour rows.
+// Home chunks of catalog A (plan.cpp): each row of cells cut into chunks of
+// home_chunk objects (the last one of a row shorter), spanning at most
+// `maxrun` cells (chunks_maxrun).
+int chunks_maxrun(const Geometry &g);
+void chunks_build(const Geometry &g, const std::vector<int32_t> &csA, int home_chunk,
+                  std::vector<int4> &out);
+// Neighbour stencil (plan.cpp).  shape: the region of separations that can
+// fall in a bin, used to trim neighbour rows.  Auto counts without
+// full_stencil keep the home row and the rows after it.
 constexpr int kShapeBox = 0, kShapeBall = 1, kShapeDiskSlab = 2;
-void tasks_build(const Geometry &g, const std::vector<int32_t> &csA,
-                 const std::vector<int32_t> &csB, bool is_auto, int pair_index, int home_chunk,
-                 int slice, bool full_stencil, int shape, const double need[3],
-                 std::vector<Task> &out, unsigned long long &candidates);
+void stencil_build(const Geometry &g, bool is_auto, bool full_stencil, int shape,
+                   const double need[3], std::vector<int4> &out);
+
+// Work entries on the GPU (work.cu): work_count computes the item count of
+// every entry and their exclusive prefix sums into eprefix[0..nentries]
+// (bsum needs work_bsum_words(nentries) words); work_write then writes the
+// item records of every entry at its prefix.
+int work_bsum_words(int nentries);
+cudaError_t work_count(const PairWork *d_pairs, const int *d_ebase, int npairs, int nentries,
+                       int slice, int *d_cnt, long long *d_bsum, long long *d_eprefix,
+                       cudaStream_t st);
+cudaError_t work_write(const PairWork *d_pairs, const int *d_ebase, int npairs, int nentries,
+                       int slice, const long long *d_eprefix, int4 *d_items, cudaStream_t st);
 
 }  // namespace cute

@@ -1,7 +1,7 @@
 // noalloc.cu -- a counting entry point that allocates no device memory.
 //
-// cute_count_pairs keeps its per-request device data (binning tables, task
-// list, work counters) in buffers it allocates and caches.  Some callers
+// cute_count_pairs keeps its per-request device data (binning tables, work
+// lists, work counters) in buffers it allocates and caches.  Some callers
 // cannot let a library allocate at the moment they count: a framework whose
 // caching allocator owns all device memory (a stray cudaMalloc fragments its
 // pool or fails once the pool has taken the device), code running while a
@@ -107,22 +107,19 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   }
   const int slice = ctx->slice_override ? ctx->slice_override : 2048;
 
-  // binning plan and task list, host only
+  // binning plan, chunks and stencil on the host
   Plan P;
   std::string m = plan_build(kind, d->edges0, d->n0, d->edges1, two_d ? d->n1 : 1, ep, 8192,
                              12288, !ctx->table_binning, P);
   if (!m.empty()) return na_fail(ctx, CUTE_E_UNSUPPORTED, m);
-  std::vector<Task> tasks;
-  unsigned long long cand = 0;
+  std::vector<int4> chunks, stencil;
   if (di.A->n > 0 && di.B->n > 0) {
     const int shape = (kind == CUTE_SIGMA_PI) ? kShapeDiskSlab : kShapeBall;
-    tasks_build(*di.g, di.A->h_cell_start, di.B->h_cell_start, di.is_auto, 0, 32 * hp, slice,
-                false, shape, di.need, tasks, cand);
+    chunks_build(*di.g, di.A->h_cell_start, 32 * hp, chunks);
+    stencil_build(*di.g, di.is_auto, false, shape, di.need, stencil);
   }
-  std::vector<long long> prefix(tasks.size() + 1, 0);
-  for (size_t t = 0; t < tasks.size(); t++)
-    prefix[t + 1] = prefix[t] + (long long)tasks[t].n_hc * tasks[t].n_sc;
   PairDev pd;
+  std::memset(&pd, 0, sizeof(pd));
   pd.posA = di.A->d_pos;
   pd.posB = di.B->d_pos;
   pd.sA = di.A->d_s64;
@@ -134,13 +131,32 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   pd.is_auto = di.is_auto;
   pd.L32 = (float)di.g->L;
   pd.L64 = di.g->periodic ? di.g->L : 0.0;
+  PairWork pw;
+  std::memset(&pw, 0, sizeof(pw));
+  pw.nchunks = (int32_t)chunks.size();
+  pw.nstencil = (int32_t)stencil.size();
+  pw.nx = di.g->nc[0];
+  pw.ny = di.g->nc[1];
+  pw.nz = di.g->nc[2];
+  pw.mode = di.is_auto ? kModeAutoHalf : kModeCross;
+  pw.periodic = di.g->periodic;
+  // the item records, on the host (the same segments as the GPU builder)
+  std::vector<int4> items;
+  const int32_t *csh = di.B->h_cell_start.data();
+  for (const int4 &c : chunks)
+    for (const int4 &r : stencil) {
+      Seg sg[3];
+      const int ns = entry_segments(pw, csh, c, r, sg);
+      for (int k = 0; k < ns; k++)
+        for (int js = sg[k].j0; js < sg[k].j1; js += slice)
+          items.push_back(item_record(c.x, c.y, sg[k], js, std::min(js + slice, sg[k].j1), 0));
+    }
 
-  // scratch layout: counters | tasks | prefix | pair | tables | bands | edges
+  // scratch layout: counters | pair | item records | tables | bands | edges
   const size_t o_cnt = 0;
-  const size_t o_tasks = na_align(o_cnt + 8 * sizeof(unsigned long long));
-  const size_t o_prefix = na_align(o_tasks + tasks.size() * sizeof(Task));
-  const size_t o_pair = na_align(o_prefix + prefix.size() * sizeof(long long));
-  const size_t o_lut = na_align(o_pair + sizeof(PairDev));
+  const size_t o_pair = na_align(o_cnt + kCounterWords * sizeof(unsigned long long));
+  const size_t o_items = na_align(o_pair + sizeof(PairDev));
+  const size_t o_lut = na_align(o_items + items.size() * sizeof(int4));
   const size_t o_band = na_align(o_lut + P.lut.size() * sizeof(uint32_t));
   const size_t o_e0 = na_align(o_band + P.band.size() * sizeof(float));
   const size_t o_e1 = na_align(o_e0 + P.E0.size() * sizeof(double));
@@ -148,17 +164,16 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   if (total > kNoAllocScratchBytes)
     return na_fail(ctx, CUTE_E_INVALID,
                    "request needs " + std::to_string(total) +
-                       " bytes of scratch; cute_count_pairs_noalloc has 8 MiB (use fewer tasks: "
-                       "smaller catalogs, or cute_count_pairs)");
+                       " bytes of scratch; cute_count_pairs_noalloc has 8 MiB (use fewer work "
+                       "items: smaller catalogs, or cute_count_pairs)");
+  unsigned char *dev = (unsigned char *)base;
   std::vector<unsigned char> img(total, 0);  // counters start at zero
-  std::memcpy(img.data() + o_tasks, tasks.data(), tasks.size() * sizeof(Task));
-  std::memcpy(img.data() + o_prefix, prefix.data(), prefix.size() * sizeof(long long));
   std::memcpy(img.data() + o_pair, &pd, sizeof(PairDev));
+  std::memcpy(img.data() + o_items, items.data(), items.size() * sizeof(int4));
   std::memcpy(img.data() + o_lut, P.lut.data(), P.lut.size() * sizeof(uint32_t));
   std::memcpy(img.data() + o_band, P.band.data(), P.band.size() * sizeof(float));
   std::memcpy(img.data() + o_e0, P.E0.data(), P.E0.size() * sizeof(double));
   std::memcpy(img.data() + o_e1, P.E1.data(), P.E1.size() * sizeof(double));
-  unsigned char *dev = (unsigned char *)base;
   NA_CUDA(cudaMemcpyAsync(dev, img.data(), total, cudaMemcpyHostToDevice, ctx->stream));
 
   const int nb = P.n0 * P.n1;
@@ -167,10 +182,8 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
 
   KParams p;
   std::memset(&p, 0, sizeof(p));
-  p.tasks = (const Task *)(dev + o_tasks);
-  p.prefix = (const long long *)(dev + o_prefix);
-  p.ntasks = (int)tasks.size();
-  p.total = prefix.back();
+  p.items = (const int4 *)(dev + o_items);
+  p.total = (long long)items.size();
   p.pairs = (const PairDev *)(dev + o_pair);
   p.lut = (const uint32_t *)(dev + o_lut);
   p.lut_words = (int)P.lut.size();

@@ -533,108 +533,69 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
   return "";
 }
 
-// ------------------------------------------------------------------ tasks
-void tasks_build(const Geometry &g, const std::vector<int32_t> &csA,
-                 const std::vector<int32_t> &csB, bool is_auto, int pair_index, int home_chunk,
-                 int slice, bool full_stencil, int shape, const double need[3],
-                 std::vector<Task> &out, unsigned long long &candidates) {
-  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-  const int kx = g.k[0], ky = g.k[1], kz = g.k[2];
-  auto cell = [&](int x, int y, int z) { return ((int64_t)z * ny + y) * nx + x; };
-  auto emit = [&](int h0, int h1, int j0, int j1, int flags) {
-    if (h1 <= h0 || j1 <= j0) return;
-    Task t;
-    t.h0 = h0; t.h1 = h1; t.j0 = j0; t.j1 = j1;
-    t.pair = pair_index;
-    t.flags = flags;
-    t.n_hc = (h1 - h0 + home_chunk - 1) / home_chunk;
-    t.n_sc = (j1 - j0 + slice - 1) / slice;
-    out.push_back(t);
-    unsigned long long nh = (unsigned long long)(h1 - h0), nj = (unsigned long long)(j1 - j0);
-    candidates += (flags & kTaskSelf) ? nh * (nh - 1) / 2 : nh * nj;
-  };
-  // shift code: 2 bits per axis, 1 -> +L, 2 -> -L
-  auto code = [](int sx, int sy, int sz) {
-    auto c = [](int s) { return s > 0 ? 1 : (s < 0 ? 2 : 0); };
-    return (c(sx) | (c(sy) << 2) | (c(sz) << 4)) << 8;
-  };
-  // slices of the x-range [xa, xb] of row (y, z) of B, split where it wraps
-  auto row_slices = [&](int xa, int xb, int y, int z, int sy, int sz, int self_flag,
-                        int h0, int h1) {
-    if (g.periodic) {
-      // at most three pieces: left of the box (image x - L), inside, right
-      // of the box (image x + L); the range is never longer than nx
-      if (xa < 0) {
-        int lo = xa + nx, hi = std::min(xb + nx, nx - 1);
-        emit(h0, h1, csB[cell(lo, y, z)], csB[cell(hi, y, z) + 1], self_flag | code(-1, sy, sz));
-      }
-      int lo = std::max(xa, 0), hi = std::min(xb, nx - 1);
-      if (lo <= hi)
-        emit(h0, h1, csB[cell(lo, y, z)], csB[cell(hi, y, z) + 1], self_flag | code(0, sy, sz));
-      if (xb >= nx) {
-        int lo2 = std::max(xa - nx, 0), hi2 = xb - nx;
-        emit(h0, h1, csB[cell(lo2, y, z)], csB[cell(hi2, y, z) + 1], self_flag | code(1, sy, sz));
-      }
-    } else {
-      int lo = std::max(xa, 0), hi = std::min(xb, nx - 1);
-      if (lo > hi) return;
-      emit(h0, h1, csB[cell(lo, y, z)], csB[cell(hi, y, z) + 1], self_flag);
-    }
-  };
+// ------------------------------------------------------------------ work decomposition
+// A home chunk spans at most this many cells of its row: on a periodic
+// axis the chunk's neighbour x-range (its cells widened by k on each side)
+// must not wrap onto itself, and on an open axis wider runs only add
+// candidates.
+int chunks_maxrun(const Geometry &g) {
+  const int nx = g.nc[0], kx = g.k[0];
+  return g.periodic ? std::max(1, nx - 2 * kx) : kx + 1;
+}
 
+// Each row of cells is cut into chunks of exactly home_chunk objects (the
+// last one of the row shorter); a chunk may straddle cells, so every lane's
+// home slots stay occupied, and its neighbour x-range is taken from its
+// first and last cells.
+void chunks_build(const Geometry &g, const std::vector<int32_t> &csA, int home_chunk,
+                  std::vector<int4> &out) {
+  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+  const int maxrun = chunks_maxrun(g);
+  auto cell = [&](int x, int y, int z) { return ((int64_t)z * ny + y) * nx + x; };
   for (int cz = 0; cz < nz; cz++) {
     for (int cy = 0; cy < ny; cy++) {
-      int cx = 0;
-      while (cx < nx) {
-        // home run: one cell, extended while the run stays small
-        int cx0 = cx, cx1 = cx;
-        int h0 = csA[cell(cx0, cy, cz)];
-        int h1 = csA[cell(cx0, cy, cz) + 1];
-        int maxrun = g.periodic ? std::max(1, nx - 2 * kx) : kx + 1;
-        while (cx1 + 1 < nx && cx1 - cx0 + 1 < maxrun &&
-               csA[cell(cx1 + 1, cy, cz) + 1] - h0 <= home_chunk && (h1 - h0) < home_chunk / 2) {
-          cx1++;
+      const int row_lo = csA[cell(0, cy, cz)], row_hi = csA[cell(nx - 1, cy, cz) + 1];
+      int pos = row_lo, cxc = 0;
+      while (pos < row_hi) {
+        while (csA[cell(cxc, cy, cz) + 1] <= pos) cxc++;  // cell of the chunk's first object
+        const int cx0 = cxc;
+        int h1 = std::min(pos + home_chunk, row_hi);
+        int cx1 = cx0;
+        while (cx1 + 1 < nx && csA[cell(cx1, cy, cz) + 1] < h1) cx1++;  // cell of its last object
+        if (cx1 - cx0 + 1 > maxrun) {  // cap the span: stop at the end of a cell
+          cx1 = cx0 + maxrun - 1;
           h1 = csA[cell(cx1, cy, cz) + 1];
         }
-        cx = cx1 + 1;
-        if (h1 <= h0) continue;
-        for (int dz = -kz; dz <= kz; dz++) {
-          for (int dy = -ky; dy <= ky; dy++) {
-            bool self_row = (dz == 0 && dy == 0);
-            // objects in cells |d| apart on an axis are at least (|d| - 1) a
-            // apart there, so a row can only reach kxr cells along x: the
-            // in-range region is a ball of radius need (shape 1) or a disk
-            // of radius need[0] in x-y times a slab in z (shape 2)
-            int kxr = kx;
-            if (shape != kShapeBox) {
-              const double shrink = 1.0 - 1e-9;
-              double gy = std::max(std::abs(dy) - 1, 0) * g.a[1] * shrink / need[1];
-              double gz = std::max(std::abs(dz) - 1, 0) * g.a[2] * shrink / need[2];
-              double rem = 1.0 - gy * gy - (shape == kShapeBall ? gz * gz : 0.0);
-              if (shape == kShapeDiskSlab && gz >= 1.0) continue;
-              if (rem <= 0.0) continue;
-              kxr = std::min(kx, (int)std::ceil(std::sqrt(rem) * need[0] * (1.0 + 1e-9) / g.a[0]));
-            }
-            if (is_auto && !full_stencil && !self_row && (dz < 0 || (dz == 0 && dy < 0))) continue;
-            int y = cy + dy, z = cz + dz, sy = 0, sz = 0;
-            if (g.periodic) {
-              if (y < 0) { y += ny; sy = -1; } else if (y >= ny) { y -= ny; sy = 1; }
-              if (z < 0) { z += nz; sz = -1; } else if (z >= nz) { z -= nz; sz = 1; }
-            } else if (y < 0 || y >= ny || z < 0 || z >= nz) {
-              continue;
-            }
-            if (is_auto && !full_stencil && self_row) {
-              // same row: the run itself with j > i, then the cells after it
-              emit(h0, h1, h0, h1, kTaskSelf);
-              row_slices(cx1 + 1, cx1 + kxr, y, z, sy, sz, 0, h0, h1);
-            } else {
-              // full stencil of an auto count: the home run meets itself
-              const int f = (is_auto && self_row) ? kTaskNoSelfPair : 0;
-              row_slices(cx0 - kxr, cx1 + kxr, y, z, sy, sz, f, h0, h1);
-            }
-          }
-        }
+        out.push_back(make_int4(pos, h1, cx0 | (cx1 << 16), cy | (cz << 16)));
+        pos = h1;
       }
+    }
+  }
+}
+
+// Objects in cells |d| apart on an axis are at least (|d| - 1) a apart
+// there, so a row can only reach kxr cells along x: the in-range region is a
+// ball of radius need (shape 1) or a disk of radius need[0] in x-y times a
+// slab in z (shape 2).  The half stencil of an auto count keeps the home row
+// (whose earlier cells the chunk order covers) and the rows after it.
+void stencil_build(const Geometry &g, bool is_auto, bool full_stencil, int shape,
+                   const double need[3], std::vector<int4> &out) {
+  const int kx = g.k[0], ky = g.k[1], kz = g.k[2];
+  for (int dz = -kz; dz <= kz; dz++) {
+    for (int dy = -ky; dy <= ky; dy++) {
+      const bool self_row = (dz == 0 && dy == 0);
+      int kxr = kx;
+      if (shape != kShapeBox) {
+        const double shrink = 1.0 - 1e-9;
+        double gy = std::max(std::abs(dy) - 1, 0) * g.a[1] * shrink / need[1];
+        double gz = std::max(std::abs(dz) - 1, 0) * g.a[2] * shrink / need[2];
+        double rem = 1.0 - gy * gy - (shape == kShapeBall ? gz * gz : 0.0);
+        if (shape == kShapeDiskSlab && gz >= 1.0) continue;
+        if (rem <= 0.0) continue;
+        kxr = std::min(kx, (int)std::ceil(std::sqrt(rem) * need[0] * (1.0 + 1e-9) / g.a[0]));
+      }
+      if (is_auto && !full_stencil && !self_row && (dz < 0 || (dz == 0 && dy < 0))) continue;
+      out.push_back(make_int4(dy, dz, kxr, self_row ? 1 : 0));
     }
   }
 }
