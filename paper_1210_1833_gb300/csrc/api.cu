@@ -257,6 +257,17 @@ cute_status cute_last_stats(cute_ctx *ctx, cute_stats *out) {
 // ------------------------------------------------------------------ count driver
 namespace cute {
 
+// Objects per reach-length of an occupied row of cells: 128-object home
+// chunks (4 per lane) pay off where rows are dense enough that a chunk spans
+// little more than the cells a 64-object chunk would.
+double row_density(const Catalog &A, const Geometry &g) {
+  const std::vector<int32_t> &cs = A.h_cell_start;
+  double objs = 0, cells = 0;
+  for (size_t c = 0; c + 1 < cs.size(); c++)
+    if (cs[c + 1] > cs[c]) { objs += cs[c + 1] - cs[c]; cells += 1; }
+  return cells > 0 ? objs / cells * g.k[0] : 0.0;
+}
+
 cute_status validate_desc(cute_ctx *ctx, const cute_pair_desc *d, DescInfo &di) {
   if (!d) return fail(ctx, CUTE_E_INVALID, "descriptor is NULL");
   if (d->kind < CUTE_MONO || d->kind > CUTE_THETA) return fail(ctx, CUTE_E_INVALID, "bad kind");
@@ -509,13 +520,13 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
   // 128-object chunks, else 2
   pr.hp = ctx->hp_override;
   if (!pr.hp) {
-    double objs = 0, cells = 0;
+    // object-weighted mean over the pair sets of a batch
+    double dens = 0, objs = 0;
     for (const DescInfo &di : pr.dis) {
-      const std::vector<int32_t> &cs = di.A->h_cell_start;
-      for (size_t c = 0; c + 1 < cs.size(); c++)
-        if (cs[c + 1] > cs[c]) { objs += cs[c + 1] - cs[c]; cells += 1; }
+      dens += (double)di.A->n * row_density(*di.A, *di.g);
+      objs += (double)di.A->n;
     }
-    pr.hp = (cells > 0 && objs / cells < 96.0) ? 2 : 4;
+    pr.hp = (objs > 0 && dens / objs >= 2000.0) ? 4 : 2;
   }
   int slice = ctx->slice_override ? ctx->slice_override : 2048;
   int warps_tuned = 0;

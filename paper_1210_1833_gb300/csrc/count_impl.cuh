@@ -17,16 +17,24 @@ constexpr int kAccCount = 0, kAccWeighted = 1, kAccAdjoint = 2;
 
 template <int HP>
 struct Home {
-  float x[HP], y[HP], z[HP];   // home position minus the image shift (grid frame)
-  float ax[HP], ay[HP], az[HP];// R_MU: x_i in the observer frame
-  float aq[HP];                // R_MU: 4 |x_i|^2
+  static_assert(HP % 2 == 0, "home slots come in pairs (packed FP32 math)");
+  // slots 2k and 2k+1 share a float2 (packed math); scalar access by slot
+  float2 nx2[HP / 2], ny2[HP / 2], nz2[HP / 2];  // -(home position - image shift), grid frame
+  float2 ax2[HP / 2], ay2[HP / 2], az2[HP / 2];  // R_MU: x_i in the observer frame
+  float2 aq2[HP / 2];                            // R_MU: 4 |x_i|^2
   float w[HP];                 // weight (0 when padded)
   float gh[HP], gl[HP];        // adjoint: float-float gradient accumulator
   int id[HP];                  // sorted index in A (INT_MAX when padded)
-  float2 nx2[(HP + 1) / 2], ny2[(HP + 1) / 2], nz2[(HP + 1) / 2];  // -(x_2k, x_2k+1): packed math
+  __device__ __forceinline__ static float get(const float2 *a, int s) {
+    return (s & 1) ? a[s >> 1].y : a[s >> 1].x;
+  }
+  __device__ __forceinline__ static void put(float2 *a, int s, float v) {
+    if (s & 1) a[s >> 1].y = v; else a[s >> 1].x = v;
+  }
 };
 
 struct WarpSmem {
+  int gje;                     // end of the current item's neighbour range
   uint32_t *hist;
   char *hist_lane;
   uint32_t s_hist_lane;        // shared-space address of hist_lane
@@ -163,9 +171,10 @@ __device__ __forceinline__ uint32_t bin_pair(const KParams &p, uint32_t lut, uin
     // s = x_j - x_i; l = x_i + x_j = 2 x_i + s; s.l = 2 s.x_i + r^2;
     // l.l = 4 |x_i|^2 + 4 s.x_i + r^2
     const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    const float sx = __fmaf_rn(dz, h.az[s], __fmaf_rn(dy, h.ay[s], __fmul_rn(dx, h.ax[s])));
+    const float sx = __fmaf_rn(dz, Home<HP>::get(h.az2, s),
+                               __fmaf_rn(dy, Home<HP>::get(h.ay2, s), __fmul_rn(dx, Home<HP>::get(h.ax2, s))));
     const float sl = __fmaf_rn(2.0f, sx, r2);
-    const float l2 = __fmaf_rn(4.0f, sx, __fadd_rn(h.aq[s], r2));
+    const float l2 = __fmaf_rn(4.0f, sx, __fadd_rn(Home<HP>::get(h.aq2, s), r2));
     const float rr = rsqrtf(__fadd_rn(r2, 1e-30f));
     const float mu = __fmul_rn(fabsf(sl), rsqrtf(__fmul_rn(r2, l2)));
     float h0, h1;
@@ -189,9 +198,10 @@ __device__ __forceinline__ uint32_t bin_pair(const KParams &p, uint32_t lut, uin
     near = n0 || n1;
   } else {
     float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    const float sx = __fmaf_rn(dz, h.az[s], __fmaf_rn(dy, h.ay[s], __fmul_rn(dx, h.ax[s])));
+    const float sx = __fmaf_rn(dz, Home<HP>::get(h.az2, s),
+                               __fmaf_rn(dy, Home<HP>::get(h.ay2, s), __fmul_rn(dx, Home<HP>::get(h.ax2, s))));
     const float sl = __fmaf_rn(2.0f, sx, r2);
-    const float l2 = __fmaf_rn(4.0f, sx, __fadd_rn(h.aq[s], r2));
+    const float l2 = __fmaf_rn(4.0f, sx, __fadd_rn(Home<HP>::get(h.aq2, s), r2));
     float mu = __fmul_rn(fabsf(sl), rsqrtf(__fmul_rn(r2, l2)));
     const uint32_t e0 = lut_get<M0>(lut, p.ax[0], r2);
     const uint32_t e1 = lut_get<M1>(lut, p.ax[1], mu);
@@ -233,6 +243,44 @@ __device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2
 // warp's FP64 queue (rare, so the enqueue sits behind one vote).
 // MASK: 1 -- only j > i counts (the home run against itself, unique pairs);
 //       2 -- every j != i counts (full-stencil adjoint of an auto count).
+// Two (r, mu) pairs at once with uniform edges on both axes: the packed
+// form of bin_pair's R_MU arithmetic branch, operation for operation (the
+// same roundings, hence the same bins and near flags).
+__device__ __forceinline__ float2 clamp2(float2 t, float lo, float hi) {
+  return make_float2(fminf(fmaxf(t.x, lo), hi), fminf(fmaxf(t.y, lo), hi));
+}
+__device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a1, float2 qx,
+                                           float2 qy, float2 qz, float2 nx, float2 ny, float2 nz,
+                                           float2 ax, float2 ay, float2 az, float2 aq,
+                                           uint32_t stride0, uint32_t stride1, uint32_t &o0,
+                                           uint32_t &o1, bool &n0, bool &n1) {
+  const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
+  const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+  const float2 sx = __ffma2_rn(dz, az, __ffma2_rn(dy, ay, __fmul2_rn(dx, ax)));
+  const float2 sl = __ffma2_rn(sx, make_float2(2.0f, 2.0f), r2);
+  const float2 l2 = __ffma2_rn(sx, make_float2(4.0f, 4.0f), __fadd2_rn(aq, r2));
+  const float2 r2e = __fadd2_rn(r2, make_float2(1e-30f, 1e-30f));
+  const float2 rr = make_float2(rsqrtf(r2e.x), rsqrtf(r2e.y));
+  const float2 pl = __fmul2_rn(r2, l2);
+  const float2 mu = __fmul2_rn(make_float2(fabsf(sl.x), fabsf(sl.y)),
+                               make_float2(rsqrtf(pl.x), rsqrtf(pl.y)));
+  // NaN -> tlo on both axes, as arith_t
+  const float2 t0 = clamp2(__ffma2_rn(__fmul2_rn(r2, rr), make_float2(a0.inv, a0.inv),
+                                      make_float2(a0.cst, a0.cst)), a0.tlo, a0.thi);
+  const float2 t1 = clamp2(__ffma2_rn(mu, make_float2(a1.inv, a1.inv), make_float2(a1.cst, a1.cst)),
+                           a1.tlo, a1.thi);
+  const float2 m2 = make_float2(kMagic, kMagic), nm2 = make_float2(-kMagic, -kMagic),
+               neg = make_float2(-1.0f, -1.0f);
+  const float2 tm0 = __fadd2_rn(t0, m2), tm1 = __fadd2_rn(t1, m2);
+  const float2 h0 = __ffma2_rn(__fadd2_rn(tm0, nm2), neg, t0);  // t - floor, exact
+  const float2 h1 = __ffma2_rn(__fadd2_rn(tm1, nm2), neg, t1);
+  const float2 thr1 = __ffma2_rn(rr, make_float2(a1.thr_a, a1.thr_a), make_float2(a1.thr_b, a1.thr_b));
+  n0 = fmaxf(fabsf(h0.x) + a0.thr_b, __fadd_rn(fabsf(h1.x), thr1.x)) >= 0.5f;
+  n1 = fmaxf(fabsf(h0.y) + a0.thr_b, __fadd_rn(fabsf(h1.y), thr1.y)) >= 0.5f;
+  o0 = arith_off(tm0.x, stride0) + arith_off(tm1.x, stride1);
+  o1 = arith_off(tm0.y, stride0) + arith_off(tm1.y, stride1);
+}
+
 template <int KIND, int HP, int M0, int M1, int MASK, int ACC>
 __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint32_t band,
                                            const PairDev &pd, const WarpSmem &w, uint32_t tile,
@@ -271,12 +319,35 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
         }
         continue;
       }
+      if (KIND == KRMU && M0 == kArith && M1 == kArith && (HP % 2) == 0) {
+        const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
+                     qz = make_float2(q.z, q.z);
+        const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u, stride1 = (uint32_t)p.R * 4u;
+#pragma unroll
+        for (int sp = 0; sp < HP / 2; sp++) {
+          uint32_t o[2];
+          bool nr[2];
+          rmu_arith2(p.ax[0], p.ax[1], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], h.ax2[sp],
+                     h.ay2[sp], h.az2[sp], h.aq2[sp], stride0, stride1, o[0], o[1], nr[0], nr[1]);
+#pragma unroll
+          for (int e = 0; e < 2; e++) {
+            const int s = 2 * sp + e, k = u * HP + s;
+            const int gj = gj0 + j + u;
+            if (MASK == 1 && !(gj > h.id[s])) { o[e] = 0u; nr[e] = false; }
+            if (MASK == 2 && gj == h.id[s]) { o[e] = 0u; nr[e] = false; }
+            if (nr[e]) { o[e] = 0u; nmask |= 1u << k; }
+            off[k] = o[e];
+          }
+        }
+        continue;
+      }
 #pragma unroll
       for (int s = 0; s < HP; s++) {
         const int k = u * HP + s;
-        const float dx = __fsub_rn(q.x, h.x[s]);
-        const float dy = __fsub_rn(q.y, h.y[s]);
-        const float dz = __fsub_rn(q.z, h.z[s]);
+        // x_j - x_i as x_j + (-x_i): the same rounding
+        const float dx = __fadd_rn(q.x, Home<HP>::get(h.nx2, s));
+        const float dy = __fadd_rn(q.y, Home<HP>::get(h.ny2, s));
+        const float dz = __fadd_rn(q.z, Home<HP>::get(h.nz2, s));
         bool near;
         uint32_t o = bin_pair<KIND, HP, M0, M1>(p, lut, band, dx, dy, dz, h, s, near);
         const int gj = gj0 + j + u;
@@ -318,7 +389,9 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
     if (__any_sync(kFull, nmask != 0u)) {
 #pragma unroll
       for (int k = 0; k < NP; k++) {
-        if (nmask & (1u << k)) {
+        // (a padded home slot or tile row is never a pair, whatever its
+        // arithmetic gave)
+        if ((nmask & (1u << k)) && h.id[k % HP] != 0x7fffffff && gj0 + j + k / HP < w.gje) {
           near_count++;
           int pos = atomicAdd(w.qcnt, 1);
           if (pos < w.qcap) w.queue[pos] = make_int2(h.id[k % HP], gj0 + j + k / HP);
@@ -463,9 +536,9 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
       h.gl[s] = 0.0f;
       if (idx < he) {
         const float4 a = pd.posA[idx];
-        h.x[s] = __fsub_rn(a.x, Sx);
-        h.y[s] = __fsub_rn(a.y, Sy);
-        h.z[s] = __fsub_rn(a.z, Sz);
+        Home<HP>::put(h.nx2, s, -__fsub_rn(a.x, Sx));
+        Home<HP>::put(h.ny2, s, -__fsub_rn(a.y, Sy));
+        Home<HP>::put(h.nz2, s, -__fsub_rn(a.z, Sz));
         h.w[s] = a.w;
         h.id[s] = idx;
         // candidate pairs: j in [js, je), with j > i (self) or j != i
@@ -475,24 +548,26 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
         if (KIND == KRMU) {
           const double X = pd.sA[idx], Y = pd.sA[(size_t)pd.nA + idx],
                        Z = pd.sA[2 * (size_t)pd.nA + idx];
-          h.ax[s] = (float)X;
-          h.ay[s] = (float)Y;
-          h.az[s] = (float)Z;
-          h.aq[s] = (float)(4.0 * (X * X + Y * Y + Z * Z));
+          Home<HP>::put(h.ax2, s, (float)X);
+          Home<HP>::put(h.ay2, s, (float)Y);
+          Home<HP>::put(h.az2, s, (float)Z);
+          Home<HP>::put(h.aq2, s, (float)(4.0 * (X * X + Y * Y + Z * Z)));
         }
       } else {
-        h.x[s] = kHomeFar; h.y[s] = kHomeFar; h.z[s] = kHomeFar;
+        Home<HP>::put(h.nx2, s, -kHomeFar);
+        Home<HP>::put(h.ny2, s, -kHomeFar);
+        Home<HP>::put(h.nz2, s, -kHomeFar);
         h.w[s] = 0.0f;
         h.id[s] = 0x7fffffff;
-        if (KIND == KRMU) { h.ax[s] = kHomeFar; h.ay[s] = kHomeFar; h.az[s] = kHomeFar; h.aq[s] = kHomeFar; }
+        if (KIND == KRMU) {
+          Home<HP>::put(h.ax2, s, kHomeFar);
+          Home<HP>::put(h.ay2, s, kHomeFar);
+          Home<HP>::put(h.az2, s, kHomeFar);
+          Home<HP>::put(h.aq2, s, kHomeFar);
+        }
       }
     }
-#pragma unroll
-    for (int sp = 0; sp < HP / 2; sp++) {
-      h.nx2[sp] = make_float2(-h.x[2 * sp], -h.x[2 * sp + 1]);
-      h.ny2[sp] = make_float2(-h.y[2 * sp], -h.y[2 * sp + 1]);
-      h.nz2[sp] = make_float2(-h.z[2 * sp], -h.z[2 * sp + 1]);
-    }
+    w.gje = je;
 
     // stream the slice through the double-buffered tile
     const int nj = je - js;

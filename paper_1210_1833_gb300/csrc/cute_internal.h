@@ -125,6 +125,9 @@ struct KParams {
 };
 
 // ------------------------------------------------------------------ host objects
+// x cells per y/z cell size (grid.cu): rows of cells run along x
+constexpr int kXFine = 8;
+
 struct Geometry {
   int id = 0;
   int periodic = 0;
@@ -275,6 +278,7 @@ struct DescInfo {
   double need[3];
 };
 cute_status validate_desc(cute_ctx *ctx, const cute_pair_desc *d, DescInfo &di);
+double row_density(const Catalog &A, const Geometry &g);
 ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax);
 
 // Home chunks of catalog A (plan.cpp): each row of cells cut into chunks of

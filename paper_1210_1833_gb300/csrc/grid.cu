@@ -269,21 +269,26 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
   for (int k = 0; k < 3; k++) {
     // cells no smaller than reach/k (with a relative margin that absorbs the
     // rounding of the cell assignment), so objects more than k cells apart
-    // on an axis are farther apart than the reach on that axis
-    double amin = reach[k] * (1.0 + 1e-9) / kreq + 1e-300;
-    int kk = kreq;
+    // on an axis are farther apart than the reach on that axis.  Rows of
+    // cells run along x and a neighbour row is a contiguous range of objects
+    // whatever its length, so x is cut kXFine times finer: the ends of each
+    // row range then follow the reach closely at no cost in work items.
+    const int kx_req = (k == 0) ? kreq * kXFine : kreq;
+    const long long ncap = (k == 0) ? 8192 : 1024;
+    double amin = reach[k] * (1.0 + 1e-9) / kx_req + 1e-300;
+    int kk = kx_req;
     if (g.periodic) {
       double L = g.L;
       long long n = (long long)std::floor(L / amin);
       // the (2k+1)-cell stencil must not wrap onto itself: raise k if needed
-      while (n < 2 * kk + 1 && kk < 16) {
+      while (n < 2 * kk + 1 && kk < 16 * kx_req) {
         kk++;
         amin = reach[k] * (1.0 + 1e-9) / kk + 1e-300;
         n = (long long)std::floor(L / amin);
       }
       if (n < 2 * kk + 1)
         return fail(ctx, CUTE_E_UNSUPPORTED, "periodic reach too large for the box (needs reach <= 0.47 L)");
-      n = std::min<long long>(n, 1024);
+      n = std::min<long long>(n, ncap);
       g.nc[k] = (int)n;
       g.a[k] = L / (double)n;
       // a stencil of kk cells must still cover the reach after capping n
@@ -297,7 +302,7 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
     } else {
       double ext = hi[k] - lo[k];
       long long n = (long long)std::floor(ext / amin) + 1;
-      n = std::max<long long>(1, std::min<long long>(n, 1024));
+      n = std::max<long long>(1, std::min<long long>(n, ncap));
       double a = std::max(amin, ext / (double)n * (1.0 + 1e-12));
       g.nc[k] = (int)n;
       g.a[k] = a;

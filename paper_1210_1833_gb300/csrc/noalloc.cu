@@ -98,13 +98,7 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   ErrorParams ep = error_params(dis, d->edges0[d->n0]);
 
   int hp = ctx->hp_override;
-  if (!hp) {
-    double objs = 0, cells = 0;
-    const std::vector<int32_t> &cs = di.A->h_cell_start;
-    for (size_t c = 0; c + 1 < cs.size(); c++)
-      if (cs[c + 1] > cs[c]) { objs += cs[c + 1] - cs[c]; cells += 1; }
-    hp = (cells > 0 && objs / cells < 96.0) ? 2 : 4;
-  }
+  if (!hp) hp = row_density(*di.A, *di.g) < 2000.0 ? 2 : 4;
   const int slice = ctx->slice_override ? ctx->slice_override : 2048;
 
   // binning plan, chunks and stencil on the host

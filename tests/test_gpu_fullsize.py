@@ -1,5 +1,5 @@
 """Parity at the full sizes of the five workloads, in the launch
-configuration bench.py uses (3 cells per reach, library-chosen shape).
+configuration bench.py uses (4 cells per reach, library-chosen shape).
 
 Where the FP64 oracle cannot finish a full count in seconds, the check is on
 sampled rows: a seeded subset S of one catalog is uploaded as its own
@@ -19,7 +19,7 @@ from paper_1210_1833_gb300 import cute, synthetic
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
-CPR = 3  # bench.py's cells per reach
+CPR = 4  # bench.py's cells per reach
 
 
 @pytest.fixture(scope="module")
