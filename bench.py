@@ -248,7 +248,7 @@ def run_gpu(args, w, rank, world):
         # the library's autotuner (remembered per problem shape, so the
         # re-uploaded catalogs of the timed steps use it)
         best = None
-        for cpr in (2, 3, 4):
+        for cpr in (3, 4, 5):
             args.cpr = cpr
             step(d_dev, r_dev, False)
             torch.cuda.synchronize()
@@ -296,7 +296,10 @@ def run_gpu(args, w, rank, world):
         cpu_v, cpu_thr, cpu_desc = None, None, "skipped (--no-cpu)"
     else:
         cpu_v, cpu_thr, cpu_desc = cpu_oracle_rate(w, target_s=12.0)
-    launches_per_step = 2 + 2 * 3 + 3  # upload stats x2, grid (assign, scan, scatter) x2, counts x3
+    # upload stats x2; grid x2 (assign, 3 scan passes, scatter); per count
+    # (x3) the work list (entry counts, 2 scan passes, record write) and the
+    # counting kernel
+    launches_per_step = 2 + 2 * 5 + 3 * 5
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -373,7 +376,7 @@ def _row_batched(ctx, dev, timed):
     for b in boxes:
         d = ctx.upload(b.data, periodic=True, L=b.L)
         r = ctx.upload(b.randoms, periodic=True, L=b.L)
-        ctx.grid([d, r], reach, 3)
+        ctx.grid([d, r], reach)  # cells per reach from the density
         cats.append((d, r))
         pairs += [(d, None), (d, r), (r, None)]
     nb = (len(e0) - 1) * (len(e1) - 1)
@@ -408,7 +411,7 @@ def _row_weighted(ctx, dev, timed):
     w = synthetic.c5_weighted()
     e = w.edges0
     A = ctx.upload(w.data, weights=w.weights, periodic=True, L=w.L)
-    ctx.grid([A], [e[-1]] * 3, 3)
+    ctx.grid([A], [e[-1]] * 3)  # cells per reach from the density
     cnt = torch.zeros(len(e) - 1, dtype=torch.int64, device=f"cuda:{dev}")
     ws = torch.zeros(len(e) - 1, dtype=torch.float64, device=f"cuda:{dev}")
     G = torch.from_numpy(w.extra["G"]).to(f"cuda:{dev}")

@@ -116,7 +116,9 @@ cute_status cute_catalog_size(cute_ctx *ctx, int32_t cat_id, int64_t *n);
    of them can then be counted against each other.  reach[3] is the largest
    separation per axis that must be found (r_max on each axis for the
    monopole, (r,mu) and theta; (sigma_max, sigma_max, pi_max) for
-   (sigma,pi)).  cells_per_reach: 1..8, or 0 for the default (2).
+   (sigma,pi)).  cells_per_reach: 1..8, or 0 to choose from the mean
+   number of objects in a reach-sized box (below 600: 2, below 3000: 3,
+   else 4).  Cells along x are 8 times finer (rows of cells run along x).
    All catalogs must have the same boundary (and box_L).  A periodic grid
    needs reach[k] <= 0.47 box_L, else CUTE_E_UNSUPPORTED.  Rebuilding a
    catalog's grid replaces the previous one. */

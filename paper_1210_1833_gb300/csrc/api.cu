@@ -192,9 +192,8 @@ cute_status cute_grid_build(cute_ctx *ctx, const int32_t *cat_ids, int32_t n_cat
                             const double reach[3], int32_t cells_per_reach) {
   ENTER(ctx);
   if (!cat_ids || n_cats < 1 || !reach) return fail(ctx, CUTE_E_INVALID, "bad arguments");
-  if (cells_per_reach == 0) cells_per_reach = 2;
-  if (cells_per_reach < 1 || cells_per_reach > 8)
-    return fail(ctx, CUTE_E_INVALID, "cells_per_reach must be 1..8");
+  if (cells_per_reach < 0 || cells_per_reach > 8)
+    return fail(ctx, CUTE_E_INVALID, "cells_per_reach must be 1..8, or 0");
   for (int k = 0; k < 3; k++)
     if (!(reach[k] > 0) || !std::isfinite(reach[k])) return fail(ctx, CUTE_E_INVALID, "reach must be > 0");
   std::vector<Catalog *> cats;
@@ -204,6 +203,19 @@ cute_status cute_grid_build(cute_ctx *ctx, const int32_t *cat_ids, int32_t n_cat
     for (Catalog *c : cats)
       if (c == &it->second) return fail(ctx, CUTE_E_INVALID, "catalog listed twice");
     cats.push_back(&it->second);
+  }
+  if (cells_per_reach == 0) {
+    // from the mean number of objects in a reach-sized box: dense catalogs
+    // gain from finer cells (the candidate volume tightens around the
+    // reach), sparse ones lose (every home chunk then spans more cells)
+    double per_box = 0;
+    for (Catalog *c : cats) {
+      double vol = 1.0;
+      for (int k = 0; k < 3; k++)
+        vol *= c->boundary == CUTE_PERIODIC ? c->L : std::max(c->hi[k] - c->lo[k], reach[k]);
+      if (c->n > 0) per_box = std::max(per_box, (double)c->n / vol * reach[0] * reach[1] * reach[2]);
+    }
+    cells_per_reach = per_box < 600.0 ? 2 : (per_box < 3000.0 ? 3 : 4);
   }
   for (Catalog *c : cats) {
     if (c->boundary != cats[0]->boundary || c->L != cats[0]->L)
@@ -261,11 +273,7 @@ namespace cute {
 // chunks (4 per lane) pay off where rows are dense enough that a chunk spans
 // little more than the cells a 64-object chunk would.
 double row_density(const Catalog &A, const Geometry &g) {
-  const std::vector<int32_t> &cs = A.h_cell_start;
-  double objs = 0, cells = 0;
-  for (size_t c = 0; c + 1 < cs.size(); c++)
-    if (cs[c + 1] > cs[c]) { objs += cs[c + 1] - cs[c]; cells += 1; }
-  return cells > 0 ? objs / cells * g.k[0] : 0.0;
+  return A.occupied_cells > 0 ? (double)A.n / (double)A.occupied_cells * g.k[0] : 0.0;
 }
 
 cute_status validate_desc(cute_ctx *ctx, const cute_pair_desc *d, DescInfo &di) {

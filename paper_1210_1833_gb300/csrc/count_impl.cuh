@@ -152,38 +152,9 @@ __device__ __forceinline__ uint32_t bin_pair(const KParams &p, uint32_t lut, uin
                                              int s, bool &near) {
   const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u, stride1 = (uint32_t)p.R * 4u;
   uint32_t o;
-  if ((KIND == KMONO || KIND == KTHETA) && M0 == kArith) {
-    const float v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    const float x0 = __fmul_rn(v0, rsqrtf(v0));  // NaN for v0 = 0: see arith_t
-    float h0;
-    const float tm0 = arith_t(p.ax[0], x0, h0);
-    near = fabsf(h0) >= p.ax[0].near_at;
-    o = arith_off(tm0, stride0);
-  } else if (KIND == KSIGPI && M0 == kArith) {
-    const float v0 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
-    const float x0 = __fmul_rn(v0, rsqrtf(v0));  // NaN for v0 = 0: see arith_t
-    float h0, h1;
-    const float tm0 = arith_t(p.ax[0], x0, h0);
-    const float tm1 = arith_t(p.ax[1], fabsf(dz), h1);
-    near = fmaxf(fabsf(h0) + p.ax[0].thr_b, fabsf(h1) + p.ax[1].thr_b) >= 0.5f;
-    o = arith_off(tm0, stride0) + arith_off(tm1, stride1);
-  } else if (KIND == KRMU && M0 == kArith) {
-    // s = x_j - x_i; l = x_i + x_j = 2 x_i + s; s.l = 2 s.x_i + r^2;
-    // l.l = 4 |x_i|^2 + 4 s.x_i + r^2
-    const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    const float sx = __fmaf_rn(dz, Home<HP>::get(h.az2, s),
-                               __fmaf_rn(dy, Home<HP>::get(h.ay2, s), __fmul_rn(dx, Home<HP>::get(h.ax2, s))));
-    const float sl = __fmaf_rn(2.0f, sx, r2);
-    const float l2 = __fmaf_rn(4.0f, sx, __fadd_rn(Home<HP>::get(h.aq2, s), r2));
-    const float rr = rsqrtf(__fadd_rn(r2, 1e-30f));
-    const float mu = __fmul_rn(fabsf(sl), rsqrtf(__fmul_rn(r2, l2)));
-    float h0, h1;
-    const float tm0 = arith_t(p.ax[0], __fmul_rn(r2, rr), h0);
-    const float tm1 = arith_t(p.ax[1], mu, h1);
-    const float thr1 = __fmaf_rn(rr, p.ax[1].thr_a, p.ax[1].thr_b);
-    near = fmaxf(fabsf(h0) + p.ax[0].thr_b, __fadd_rn(fabsf(h1), thr1)) >= 0.5f;
-    o = arith_off(tm0, stride0) + arith_off(tm1, stride1);
-  } else if (KIND == KMONO || KIND == KTHETA) {
+  // (uniform edges take the packed functions above: mono_arith2,
+  // sigpi_arith2, rmu_arith2)
+  if (KIND == KMONO || KIND == KTHETA) {
     float v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
     const uint32_t e0 = lut_get<M0>(lut, p.ax[0], v0);
     o = axis_resolve(band, p.ax[0], v0, e0, stride0, near);
@@ -274,9 +245,38 @@ __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a
   const float2 tm0 = __fadd2_rn(t0, m2), tm1 = __fadd2_rn(t1, m2);
   const float2 h0 = __ffma2_rn(__fadd2_rn(tm0, nm2), neg, t0);  // t - floor, exact
   const float2 h1 = __ffma2_rn(__fadd2_rn(tm1, nm2), neg, t1);
-  const float2 thr1 = __ffma2_rn(rr, make_float2(a1.thr_a, a1.thr_a), make_float2(a1.thr_b, a1.thr_b));
-  n0 = fmaxf(fabsf(h0.x) + a0.thr_b, __fadd_rn(fabsf(h1.x), thr1.x)) >= 0.5f;
-  n1 = fmaxf(fabsf(h0.y) + a0.thr_b, __fadd_rn(fabsf(h1.y), thr1.y)) >= 0.5f;
+  // near an edge: |h| within the error bound of 1/2 on either axis (the mu
+  // bound thr_a / r + thr_b, with the 1/r that rr already holds)
+  const float2 lim1 = __ffma2_rn(rr, make_float2(-a1.thr_a, -a1.thr_a),
+                                 make_float2(a1.near_c, a1.near_c));
+  n0 = (fabsf(h0.x) >= a0.near_at) | (fabsf(h1.x) >= lim1.x);  // no short circuit: no branch
+  n1 = (fabsf(h0.y) >= a0.near_at) | (fabsf(h1.y) >= lim1.y);
+  o0 = arith_off(tm0.x, stride0) + arith_off(tm1.x, stride1);
+  o1 = arith_off(tm0.y, stride0) + arith_off(tm1.y, stride1);
+}
+
+// Two (sigma, pi) pairs at once with uniform edges on both axes (the packed
+// form of bin_pair's SIGMA_PI arithmetic branch; the near test compares |h|
+// with 1/2 - thr_b rounded down, as the monopole's).
+__device__ __forceinline__ void sigpi_arith2(const AxisPlan &a0, const AxisPlan &a1, float2 qx,
+                                             float2 qy, float2 qz, float2 nx, float2 ny,
+                                             float2 nz, uint32_t stride0, uint32_t stride1,
+                                             uint32_t &o0, uint32_t &o1, bool &n0, bool &n1) {
+  const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
+  const float2 v0 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
+  const float2 x0 = __fmul2_rn(v0, make_float2(rsqrtf(v0.x), rsqrtf(v0.y)));  // NaN for v0 = 0
+  const float2 t0 = clamp2(__ffma2_rn(x0, make_float2(a0.inv, a0.inv), make_float2(a0.cst, a0.cst)),
+                           a0.tlo, a0.thi);
+  const float2 t1 = clamp2(__ffma2_rn(make_float2(fabsf(dz.x), fabsf(dz.y)),
+                                      make_float2(a1.inv, a1.inv), make_float2(a1.cst, a1.cst)),
+                           a1.tlo, a1.thi);
+  const float2 m2 = make_float2(kMagic, kMagic), nm2 = make_float2(-kMagic, -kMagic),
+               neg = make_float2(-1.0f, -1.0f);
+  const float2 tm0 = __fadd2_rn(t0, m2), tm1 = __fadd2_rn(t1, m2);
+  const float2 h0 = __ffma2_rn(__fadd2_rn(tm0, nm2), neg, t0);
+  const float2 h1 = __ffma2_rn(__fadd2_rn(tm1, nm2), neg, t1);
+  n0 = (fabsf(h0.x) >= a0.near_at) | (fabsf(h1.x) >= a1.near_at);
+  n1 = (fabsf(h0.y) >= a0.near_at) | (fabsf(h1.y) >= a1.near_at);
   o0 = arith_off(tm0.x, stride0) + arith_off(tm1.x, stride1);
   o1 = arith_off(tm0.y, stride0) + arith_off(tm1.y, stride1);
 }
@@ -297,7 +297,7 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
     for (int u = 0; u < U; u++) {
       const float4 q = lds_f4(tile + 16u * (j + u));
       wj[u] = q.w;
-      if ((KIND == KMONO || KIND == KTHETA) && M0 == kArith && (HP % 2) == 0) {
+      if constexpr ((KIND == KMONO || KIND == KTHETA) && M0 == kArith) {
         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
                      qz = make_float2(q.z, q.z);
         const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u;
@@ -317,9 +317,27 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
             off[k] = o[e];
           }
         }
-        continue;
-      }
-      if (KIND == KRMU && M0 == kArith && M1 == kArith && (HP % 2) == 0) {
+      } else if constexpr (KIND == KSIGPI && M0 == kArith) {
+        const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
+                     qz = make_float2(q.z, q.z);
+        const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u, stride1 = (uint32_t)p.R * 4u;
+#pragma unroll
+        for (int sp = 0; sp < HP / 2; sp++) {
+          uint32_t o[2];
+          bool nr[2];
+          sigpi_arith2(p.ax[0], p.ax[1], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], stride0,
+                       stride1, o[0], o[1], nr[0], nr[1]);
+#pragma unroll
+          for (int e = 0; e < 2; e++) {
+            const int s = 2 * sp + e, k = u * HP + s;
+            const int gj = gj0 + j + u;
+            if (MASK == 1 && !(gj > h.id[s])) { o[e] = 0u; nr[e] = false; }
+            if (MASK == 2 && gj == h.id[s]) { o[e] = 0u; nr[e] = false; }
+            if (nr[e]) { o[e] = 0u; nmask |= 1u << k; }
+            off[k] = o[e];
+          }
+        }
+      } else if constexpr (KIND == KRMU && M0 == kArith) {
         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
                      qz = make_float2(q.z, q.z);
         const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u, stride1 = (uint32_t)p.R * 4u;
@@ -339,22 +357,22 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
             off[k] = o[e];
           }
         }
-        continue;
-      }
+      } else {
 #pragma unroll
-      for (int s = 0; s < HP; s++) {
-        const int k = u * HP + s;
-        // x_j - x_i as x_j + (-x_i): the same rounding
-        const float dx = __fadd_rn(q.x, Home<HP>::get(h.nx2, s));
-        const float dy = __fadd_rn(q.y, Home<HP>::get(h.ny2, s));
-        const float dz = __fadd_rn(q.z, Home<HP>::get(h.nz2, s));
-        bool near;
-        uint32_t o = bin_pair<KIND, HP, M0, M1>(p, lut, band, dx, dy, dz, h, s, near);
-        const int gj = gj0 + j + u;
-        if (MASK == 1 && !(gj > h.id[s])) { o = 0u; near = false; }   // not a pair of this task
-        if (MASK == 2 && gj == h.id[s]) { o = 0u; near = false; }     // no self pair
-        if (near) { o = 0u; nmask |= 1u << k; }
-        off[k] = o;
+        for (int s = 0; s < HP; s++) {
+          const int k = u * HP + s;
+          // x_j - x_i as x_j + (-x_i): the same rounding
+          const float dx = __fadd_rn(q.x, Home<HP>::get(h.nx2, s));
+          const float dy = __fadd_rn(q.y, Home<HP>::get(h.ny2, s));
+          const float dz = __fadd_rn(q.z, Home<HP>::get(h.nz2, s));
+          bool near;
+          uint32_t o = bin_pair<KIND, HP, M0, M1>(p, lut, band, dx, dy, dz, h, s, near);
+          const int gj = gj0 + j + u;
+          if (MASK == 1 && !(gj > h.id[s])) { o = 0u; near = false; }   // not a pair of this item
+          if (MASK == 2 && gj == h.id[s]) { o = 0u; near = false; }     // no self pair
+          if (near) { o = 0u; nmask |= 1u << k; }
+          off[k] = o;
+        }
       }
     }
     if (ACC != kAccAdjoint) {
@@ -492,12 +510,20 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
   PairDev pd;
   unsigned long long acc = 0, items = 0, slots = 0, cand = 0;
   unsigned near_count = 0;
+  // Work items in a two-deep pipeline: while an item runs, the record of
+  // the next one is in flight and the ticket of the one after it has been
+  // drawn (lane 0 holds it until it is needed).
+  const int4 rec_none = make_int4(0, 0, 0, 0);
+  unsigned long long tk = (lane == 0) ? atomicAdd(p.ticket, 1ull) : 0ull;
+  long long it = (long long)__shfl_sync(kFull, tk, 0);
+  int4 rec_next = it < p.total ? p.items[it] : rec_none;
+  tk = (lane == 0 && it < p.total) ? atomicAdd(p.ticket, 1ull) : 0ull;
   for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(p.ticket, 1ull);
-    item = __shfl_sync(kFull, item, 0);
-    if ((long long)item >= p.total) break;
-    const int4 rec = p.items[item];
+    if (it >= p.total) break;
+    const int4 rec = rec_next;
+    it = (long long)__shfl_sync(kFull, tk, 0);
+    rec_next = it < p.total ? p.items[it] : rec_none;
+    tk = (lane == 0 && it < p.total) ? atomicAdd(p.ticket, 1ull) : 0ull;
     const int pi = (int)((unsigned)rec.w >> 16);
     if (pi != cur_pair) {
       if (cur_pair >= 0) {
@@ -524,6 +550,19 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
     items++;
     slots += (unsigned long long)(32 * HP) * (unsigned long long)((je - js + (8 / HP) - 1) & ~((8 / HP) - 1));
 
+    // the first tile is in flight while the home objects load
+    const int nj = je - js;
+    const int ntiles = (nj + kTile - 1) / kTile;
+    auto load_tile = [&](int tt) {
+      float4 *dst = w.tiles + (tt & 1) * kTile;
+      for (int e = lane; e < kTile; e += 32) {
+        const int g = js + tt * kTile + e;
+        if (g < je) cp_async16(dst + e, pd.posB + g);
+        else dst[e] = make_float4(kNbrFar, kNbrFar, kNbrFar, 0.0f);
+      }
+      cp_async_commit();
+    };
+    load_tile(0);
     const int code = (rec.w >> 10) & 63;
     const float Sx = PER ? shift_of(code & 3, pd.L32) : 0.0f;
     const float Sy = PER ? shift_of((code >> 2) & 3, pd.L32) : 0.0f;
@@ -542,7 +581,6 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
         h.w[s] = a.w;
         h.id[s] = idx;
         // candidate pairs: j in [js, je), with j > i (self) or j != i
-        const int nj = je - js;
         cand += mask == 1 ? (unsigned)max(0, je - max(js, idx + 1))
                           : (unsigned)(nj - (mask == 2 && idx >= js && idx < je ? 1 : 0));
         if (KIND == KRMU) {
@@ -569,19 +607,6 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
     }
     w.gje = je;
 
-    // stream the slice through the double-buffered tile
-    const int nj = je - js;
-    const int ntiles = (nj + kTile - 1) / kTile;
-    auto load_tile = [&](int tt) {
-      float4 *dst = w.tiles + (tt & 1) * kTile;
-      for (int e = lane; e < kTile; e += 32) {
-        const int g = js + tt * kTile + e;
-        if (g < je) cp_async16(dst + e, pd.posB + g);
-        else dst[e] = make_float4(kNbrFar, kNbrFar, kNbrFar, 0.0f);
-      }
-      cp_async_commit();
-    };
-    load_tile(0);
     for (int tt = 0; tt < ntiles; tt++) {
       if (tt + 1 < ntiles) {
         load_tile(tt + 1);

@@ -50,6 +50,9 @@ struct AxisPlan {
   // (x_r the pair's r) and thr_b alone for the other axes.
   float inv = 0, cst = 0, tlo = 0, thi = 0, thr_a = 0, thr_b = 0;
   float near_at = 0;  // 1/2 - thr_b rounded down: near when |h| >= near_at
+  // mu: 1/2 - thr_b - 2^-22 rounded down; near when |h| >= near_c - thr_a * rr
+  // (one FMA, its rounding covered by the 2^-22)
+  float near_c = 0;
 };
 
 // Kinds as the kernels see them.
@@ -161,6 +164,7 @@ struct Catalog {
   int32_t *d_perm = nullptr;   // sorted -> upload index
   int32_t *d_cell_start = nullptr;
   std::vector<int32_t> h_cell_start;
+  int64_t occupied_cells = 0;  // cells holding at least one object
 };
 
 struct Plan;  // binning plan (plan.cpp)

@@ -97,30 +97,77 @@ __global__ void k_cell_assign(const double *__restrict__ xyz, int n, GridDev g,
   rank[i] = atomicAdd(&cnt[c], 1);
 }
 
-// Exclusive scan of cnt[0..m) into start[0..m]; one block walks the array in
-// chunks of blockDim, carrying the running total.
-__global__ void k_scan(const int *__restrict__ cnt, int m, int *__restrict__ start) {
-  __shared__ int s[1024];
-  __shared__ int carry;
-  if (threadIdx.x == 0) carry = 0;
+// Exclusive scan of cnt[0..m) into start[0..m], in three passes: the sum of
+// every block of kScanBlock cells, an exclusive scan of those sums in one
+// block, then each block's own scan offset by its sum's prefix.
+constexpr int kScanThreads = 512, kScanPer = 8, kScanBlock = kScanThreads * kScanPer;
+
+// block-wide exclusive scan of one int per thread; returns the block total
+__device__ int block_scan_int(int v, int &excl) {
+  __shared__ int warp_tot[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
   __syncthreads();
-  for (int base = 0; base < m; base += blockDim.x) {
-    int i = base + threadIdx.x;
-    int v = (i < m) ? cnt[i] : 0;
-    s[threadIdx.x] = v;
-    __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-      int t = (threadIdx.x >= (unsigned)off) ? s[threadIdx.x - off] : 0;
-      __syncthreads();
-      s[threadIdx.x] += t;
-      __syncthreads();
-    }
-    if (i < m) start[i] = carry + s[threadIdx.x] - v;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry += s[threadIdx.x];
-    __syncthreads();
+  int off = 0, tot = 0;
+  for (int w = 0; w < kScanThreads / 32; w++) {
+    if (w < warp) off += warp_tot[w];
+    tot += warp_tot[w];
+  }
+  __syncthreads();
+  excl = off + x - v;
+  return tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const int *__restrict__ cnt, int m,
+                                                            int *__restrict__ bsum) {
+  const int base = blockIdx.x * kScanBlock;
+  int v = 0;
+  for (int k = 0; k < kScanPer; k++) {
+    const int i = base + k * kScanThreads + threadIdx.x;
+    if (i < m) v += cnt[i];
+  }
+  int excl;
+  const int tot = block_scan_int(v, excl);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(int *__restrict__ bsum, int nblocks,
+                                                           int *__restrict__ start, int m) {
+  int carry = 0;
+  for (int b0 = 0; b0 < nblocks; b0 += kScanThreads) {
+    const int b = b0 + threadIdx.x;
+    const int v = b < nblocks ? bsum[b] : 0;
+    int excl;
+    const int tot = block_scan_int(v, excl);
+    if (b < nblocks) bsum[b] = carry + excl;
+    carry += tot;
   }
   if (threadIdx.x == 0) start[m] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restrict__ cnt, int m,
+                                                             const int *__restrict__ bsum,
+                                                             int *__restrict__ start) {
+  const int base = blockIdx.x * kScanBlock + threadIdx.x * kScanPer;  // consecutive cells
+  int v[kScanPer], sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; k++) {
+    v[k] = base + k < m ? cnt[base + k] : 0;
+    sum += v[k];
+  }
+  int excl;
+  block_scan_int(sum, excl);
+  int run = bsum[blockIdx.x] + excl;
+#pragma unroll
+  for (int k = 0; k < kScanPer; k++) {
+    if (base + k < m) start[base + k] = run;
+    run += v[k];
+  }
 }
 
 __global__ void k_scatter(const double *__restrict__ xyz, const float *__restrict__ w, int n,
@@ -335,18 +382,22 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
       CUDA_OR_FAIL(cudaMalloc(&c->d_s64, sizeof(double) * 3 * (size_t)n));
       CUDA_OR_FAIL(cudaMalloc(&c->d_perm, sizeof(int) * (size_t)n));
     }
-    size_t need = sizeof(int) * ((size_t)2 * n + (size_t)ncell) + 256;
+    const int nsb = (int)((ncell + kScanBlock - 1) / kScanBlock);
+    size_t need = sizeof(int) * ((size_t)2 * n + (size_t)ncell + (size_t)nsb) + 256;
     cute_status st = ensure_scratch(ctx, need);
     if (st != CUTE_OK) return st;
     int *cid = (int *)ctx->d_scratch;
     int *rank = cid + n;
     int *cnt = rank + n;
+    int *bsum = cnt + ncell;
     CUDA_OR_FAIL(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)ncell, ctx->stream));
     if (n > 0) {
       k_cell_assign<<<(n + 255) / 256, 256, 0, ctx->stream>>>(c->d_xyz, n, gd, cid, rank, cnt);
       CUDA_OR_FAIL(cudaGetLastError());
     }
-    k_scan<<<1, 1024, 0, ctx->stream>>>(cnt, (int)ncell, c->d_cell_start);
+    k_scan_sums<<<nsb, kScanThreads, 0, ctx->stream>>>(cnt, (int)ncell, bsum);
+    k_scan_top<<<1, kScanThreads, 0, ctx->stream>>>(bsum, nsb, c->d_cell_start, (int)ncell);
+    k_scan_apply<<<nsb, kScanThreads, 0, ctx->stream>>>(cnt, (int)ncell, bsum, c->d_cell_start);
     CUDA_OR_FAIL(cudaGetLastError());
     if (n > 0) {
       k_scatter<<<(n + 255) / 256, 256, 0, ctx->stream>>>(c->d_xyz, c->d_w, n, gd, cid, rank,
@@ -359,6 +410,8 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
                                  sizeof(int) * (size_t)(ncell + 1), cudaMemcpyDeviceToHost,
                                  ctx->stream));
     CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+    c->occupied_cells = 0;
+    for (long long q = 0; q < ncell; q++) c->occupied_cells += c->h_cell_start[q + 1] > c->h_cell_start[q];
     c->geom = g.id;
     c->grid_version = g.version;
   }

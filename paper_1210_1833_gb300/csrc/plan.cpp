@@ -387,6 +387,7 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
     if (ok) {
       P0.near_at = f32_down(0.5 - (double)P0.thr_b);
       P1.near_at = f32_down(0.5 - (double)P1.thr_b);
+      P1.near_c = f32_down(0.5 - (double)P1.thr_b - std::ldexp(1.0, -22));
       out.ax[0] = P0;
       out.ax[1] = two_d ? P1 : AxisPlan();
       out.lut.clear();

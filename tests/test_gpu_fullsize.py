@@ -1,5 +1,6 @@
 """Parity at the full sizes of the five workloads, in the launch
-configuration bench.py uses (4 cells per reach, library-chosen shape).
+configuration bench.py uses (4 cells per reach for the light cone, the
+library's density-based choice elsewhere; library-chosen shape).
 
 Where the FP64 oracle cannot finish a full count in seconds, the check is on
 sampled rows: a seeded subset S of one catalog is uploaded as its own
@@ -71,7 +72,7 @@ def test_c3_angular_full(ctx):
     sd = w.data[_rows(len(w.data), 300, 72)]
     sr = w.randoms[_rows(len(w.randoms), 150, 73)]
     D, R, SD, SR = (ctx.upload(x) for x in (w.data, w.randoms, sd, sr))
-    ctx.grid([D, R, SD, SR], [chord[-1]] * 3, CPR)
+    ctx.grid([D, R, SD, SR], [chord[-1]] * 3)
     dd, _, _ = ctx.count("theta", D, None, chord)
     assert int(dd.sum()) > 0
     for S, xs, B, xb in ((SD, sd, D, w.data), (SD, sd, R, w.randoms), (SR, sr, R, w.randoms)):
@@ -90,7 +91,7 @@ def test_c4_batched_sigpi_full(ctx):
     for b in boxes:
         d = ctx.upload(b.data, periodic=True, L=b.L)
         r = ctx.upload(b.randoms, periodic=True, L=b.L)
-        ctx.grid([d, r], reach, CPR)
+        ctx.grid([d, r], reach)
         cats.append((d, r))
         pairs += [(d, None), (d, r), (r, None)]
     batched = ctx.count_batched("sigpi", pairs, e0, e1)
@@ -114,7 +115,7 @@ def test_c5_weighted_and_adjoint_full(ctx):
     e, G, idx = w.edges0, w.extra["G"], w.extra["fd_idx"]
     A = ctx.upload(w.data, weights=w.weights, periodic=True, L=w.L)
     S = ctx.upload(w.data[idx], weights=np.ones(len(idx), np.float32), periodic=True, L=w.L)
-    ctx.grid([A, S], [e[-1]] * 3, CPR)
+    ctx.grid([A, S], [e[-1]] * 3)
     counts, _, ws = ctx.count("mono", A, None, e, weighted=True)
     plain, _, _ = ctx.count("mono", A, None, e)
     assert counts.tolist() == plain.tolist()
