@@ -35,14 +35,15 @@ sys.path.insert(0, ROOT)
 from paper_1210_1833_gb300 import synthetic  # noqa: E402
 
 METRIC = "pairs/s & % FP32 roofline; batched/adjoint vs plain kernel, counts exact"
-# FP32-pipe operations per candidate pair in the (r, mu) kernel with uniform
-# edges (arithmetic binning): s (3 FADD), r^2 (3), s.x_i (3), s.l (1 FFMA),
-# l.l (FADD + FFMA), guard add (1), r^2 l^2 (1), mu (1), r (1); per axis
-# t (FFMA), clamp (2 FMNMX), round (FADD), floor (FADD), offset (FADD) = 6 x 2;
-# mu bound (FFMA), two band sums (FADD), max (FMNMX), compare (FSETP) = 5.
-# Not counted: the 2 MUFU rsqrt, 2 IMAD slot offsets, the select and the
-# shared-memory atomic.
-I_PAIR_RMU = 34
+# Algorithmic FP32-pipe instructions per candidate pair, by separation
+# measure: what the plain formula needs to separate, test and bin one pair
+# (separation 3 FADD, squared norm FMUL + 2 FFMA, compare to the largest
+# edge, scale and magic-number round to a bin index), plus the minimum image
+# per axis (FADD + FMNMX) for periodic boxes, the second axis's index for
+# (sigma, pi), and for (r, mu) the line of sight and the s.l, l.l products;
+# theta on squared chords with a table index.  The kernel's own count (its
+# near-edge tests and clamps included) is reported beside it from ncu.
+I_PAIR = {"mono_open": 9, "mono_periodic": 15, "sigpi_periodic": 17, "rmu": 22, "theta": 10}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -104,23 +105,48 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def traffic_record(key):
-    """DRAM bytes per launch of a kernel from profiles/traffic.json, only if
-    the counting-kernel sources still hash to what was captured."""
+def _kernel_hash():
     import glob
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
-        return None
-    rec = json.load(open(path)).get(key)
-    if not rec:
-        return None
     files = sorted(glob.glob(os.path.join(ROOT, "paper_1210_1833_gb300", "csrc", "count_*.cu*")) +
                    [os.path.join(ROOT, "paper_1210_1833_gb300", "csrc", "cute_internal.h")])
     h = hashlib.sha256()
     for f in files:
         h.update(open(f, "rb").read())
-    return rec["per_launch_bytes"] if h.hexdigest()[:16] == rec["kernel_source_hash"] else None
+    return h.hexdigest()[:16]
+
+
+def _counters(key):
+    """A kernel's ncu counters from profiles/counters.json, only if the
+    counting-kernel sources still hash to what was captured."""
+    path = os.path.join(ROOT, "profiles", "counters.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(key)
+    if not rec or rec.get("kernel_source_hash") != _kernel_hash():
+        return None
+    return rec
+
+
+def traffic_record(key):
+    """DRAM bytes (read + write) per launch of a kernel, from ncu."""
+    rec = _counters(key)
+    return rec["per_launch_bytes"] if rec and "per_launch_bytes" in rec else None
+
+
+def counted_record(key, cand_rate, peak):
+    """The kernel's own FP32-pipe work per candidate pair, counted by ncu
+    (scalar FADD/FMUL/FFMA thread instructions plus twice the packed ones,
+    divided by the candidate pairs of the captured launch), and the FP32
+    utilisation it implies at the measured rate; None once the kernel
+    sources differ from the captured ones."""
+    rec = _counters(key)
+    if not rec or "fp32_ops_per_candidate" not in rec:
+        return None
+    i_c = rec["fp32_ops_per_candidate"]
+    return {"i_pair": i_c, "frac": cand_rate * i_c / 1e12 / peak,
+            "fma_pipe_active_pct": rec.get("fma_pipe_active_pct"),
+            "source": "profiles/" + rec.get("summary", "")}
 
 
 def total_pairs(nd, nr):
@@ -291,7 +317,7 @@ def run_gpu(args, w, rank, world):
     peak_tinst = SM_COUNT * FP32_LANES_PER_SM * smax * 1e6 / 1e12
     rr_ms = float(np.mean(state["rr_ms"])) if state["rr_ms"] else float("nan")
     rr_rate = state["rr_cand"] / (rr_ms / 1e3)
-    achieved = rr_rate * I_PAIR_RMU / 1e12
+    achieved = rr_rate * I_PAIR["rmu"] / 1e12
     if args.no_cpu:
         cpu_v, cpu_thr, cpu_desc = None, None, "skipped (--no-cpu)"
     else:
@@ -321,7 +347,8 @@ def run_gpu(args, w, rank, world):
                   "count_kernel_ms_per_step": float(np.sum(state["kms"])) / args.steps},
         "roofline": {"bound": "alu", "kernel": "k_count<R_MU> (RR)", "achieved": achieved,
                      "peak": peak_tinst, "unit": "Tinst/s", "frac": achieved / peak_tinst,
-                     "traffic": traffic_record("k_count_rmu_RR_c2"), "i_pair": I_PAIR_RMU,
+                     "traffic": traffic_record("k_count_rmu_RR_c2"), "i_pair": I_PAIR["rmu"],
+                     "counted": counted_record("k_count_rmu_RR_c2", rr_rate, peak_tinst),
                      "peak_note": "152 SMs x 128 FP32 lanes x %.0f MHz (%s max clock)" % (
                          smax, src),
                      "kernel_ms": rr_ms, "candidate_pairs": state["rr_cand"]},
@@ -395,14 +422,29 @@ def _row_batched(ctx, dev, timed):
     plain()
     t_b = timed(batched)
     t_p = timed(plain)
+    batched()
+    torch.cuda.synchronize()
+    st = ctx.stats()
     binned = sum(int(c.sum()) for c in ctx.count_batched("sigpi", pairs, e0, e1, device=True))
     out["batched_sigpi_64_boxes"] = {
         "batched_ms": t_b, "plain_ms": t_p, "plain_over_batched": t_p / t_b,
         "launches": {"batched": 1, "plain": len(pairs)}, "binned_pairs": binned,
-        "binned_pairs_per_s": binned / (t_b / 1e3), "graph_replay": True}
+        "binned_pairs_per_s": binned / (t_b / 1e3), "graph_replay": True,
+        "batched_candidate_pairs": st["candidate_pairs"], "batched_kernel_ms": st["kernel_ms"],
+        "batched_roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
+                                          "sigpi_periodic")}
     for d, r in cats:
         d.free(); r.free()
     return out
+
+
+def _alu_roofline(cand_rate, kind):
+    """Algorithmic FP32 roofline fraction of a counting kernel."""
+    pk, src = peaks()
+    peak = SM_COUNT * FP32_LANES_PER_SM * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    ach = cand_rate * I_PAIR[kind] / 1e12
+    return {"bound": "alu", "i_pair": I_PAIR[kind], "achieved": ach, "peak": peak,
+            "unit": "Tinst/s", "frac": ach / peak}
 
 
 def _row_weighted(ctx, dev, timed):
@@ -427,7 +469,9 @@ def _row_weighted(ctx, dev, timed):
         "binned_pairs": binned, "plain_binned_pairs_per_s": binned / (t_plain / 1e3),
         "plain_candidate_pairs": st["candidate_pairs"], "plain_kernel_ms": st["kernel_ms"],
         "plain_home_per_lane": st["home_per_lane"],
-        "plain_candidate_pairs_per_s": st["candidate_pairs"] / (st["kernel_ms"] / 1e3)}
+        "plain_candidate_pairs_per_s": st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
+        "plain_roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
+                                        "mono_periodic")}
     A.free()
     return out
 

@@ -191,7 +191,8 @@ __device__ __forceinline__ uint32_t bin_pair(const KParams &p, uint32_t lut, uin
 // element is rounded exactly as the scalar path rounds it).
 __device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2 qy, float2 qz,
                                             float2 nx, float2 ny, float2 nz, uint32_t stride,
-                                            uint32_t &o0, uint32_t &o1, bool &n0, bool &n1) {
+                                            uint32_t c, uint32_t &o0, uint32_t &o1, bool &n0,
+                                            bool &n1) {
   const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
   const float2 v = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
   const float2 x = __fmul2_rn(v, make_float2(rsqrtf(v.x), rsqrtf(v.y)));  // NaN for v = 0
@@ -203,8 +204,8 @@ __device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2
   const float2 h = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), t);  // t - floor, exact
   n0 = fabsf(h.x) >= a.near_at;
   n1 = fabsf(h.y) >= a.near_at;
-  o0 = arith_off(tm.x, stride);
-  o1 = arith_off(tm.y, stride);
+  o0 = __float_as_uint(tm.x) * stride + c;
+  o1 = __float_as_uint(tm.y) * stride + c;
 }
 
 // All pairs of the HP home objects of each lane with the cnt neighbours of
@@ -223,8 +224,8 @@ __device__ __forceinline__ float2 clamp2(float2 t, float lo, float hi) {
 __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a1, float2 qx,
                                            float2 qy, float2 qz, float2 nx, float2 ny, float2 nz,
                                            float2 ax, float2 ay, float2 az, float2 aq,
-                                           uint32_t stride0, uint32_t stride1, uint32_t &o0,
-                                           uint32_t &o1, bool &n0, bool &n1) {
+                                           uint32_t stride0, uint32_t stride1, uint32_t c,
+                                           uint32_t &o0, uint32_t &o1, bool &n0, bool &n1) {
   const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
   const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
   const float2 sx = __ffma2_rn(dz, az, __ffma2_rn(dy, ay, __fmul2_rn(dx, ax)));
@@ -235,7 +236,7 @@ __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a
   const float2 pl = __fmul2_rn(r2, l2);
   const float2 mu = __fmul2_rn(make_float2(fabsf(sl.x), fabsf(sl.y)),
                                make_float2(rsqrtf(pl.x), rsqrtf(pl.y)));
-  // NaN -> tlo on both axes, as arith_t
+  // NaN -> tlo on both axes
   const float2 t0 = clamp2(__ffma2_rn(__fmul2_rn(r2, rr), make_float2(a0.inv, a0.inv),
                                       make_float2(a0.cst, a0.cst)), a0.tlo, a0.thi);
   const float2 t1 = clamp2(__ffma2_rn(mu, make_float2(a1.inv, a1.inv), make_float2(a1.cst, a1.cst)),
@@ -251,8 +252,8 @@ __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a
                                  make_float2(a1.near_c, a1.near_c));
   n0 = (fabsf(h0.x) >= a0.near_at) | (fabsf(h1.x) >= lim1.x);  // no short circuit: no branch
   n1 = (fabsf(h0.y) >= a0.near_at) | (fabsf(h1.y) >= lim1.y);
-  o0 = arith_off(tm0.x, stride0) + arith_off(tm1.x, stride1);
-  o1 = arith_off(tm0.y, stride0) + arith_off(tm1.y, stride1);
+  o0 = __float_as_uint(tm0.x) * stride0 + (__float_as_uint(tm1.x) * stride1 + c);
+  o1 = __float_as_uint(tm0.y) * stride0 + (__float_as_uint(tm1.y) * stride1 + c);
 }
 
 // Two (sigma, pi) pairs at once with uniform edges on both axes (the packed
@@ -261,7 +262,8 @@ __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a
 __device__ __forceinline__ void sigpi_arith2(const AxisPlan &a0, const AxisPlan &a1, float2 qx,
                                              float2 qy, float2 qz, float2 nx, float2 ny,
                                              float2 nz, uint32_t stride0, uint32_t stride1,
-                                             uint32_t &o0, uint32_t &o1, bool &n0, bool &n1) {
+                                             uint32_t c, uint32_t &o0, uint32_t &o1, bool &n0,
+                                             bool &n1) {
   const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
   const float2 v0 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
   const float2 x0 = __fmul2_rn(v0, make_float2(rsqrtf(v0.x), rsqrtf(v0.y)));  // NaN for v0 = 0
@@ -277,8 +279,8 @@ __device__ __forceinline__ void sigpi_arith2(const AxisPlan &a0, const AxisPlan 
   const float2 h1 = __ffma2_rn(__fadd2_rn(tm1, nm2), neg, t1);
   n0 = (fabsf(h0.x) >= a0.near_at) | (fabsf(h1.x) >= a1.near_at);
   n1 = (fabsf(h0.y) >= a0.near_at) | (fabsf(h1.y) >= a1.near_at);
-  o0 = arith_off(tm0.x, stride0) + arith_off(tm1.x, stride1);
-  o1 = arith_off(tm0.y, stride0) + arith_off(tm1.y, stride1);
+  o0 = __float_as_uint(tm0.x) * stride0 + (__float_as_uint(tm1.x) * stride1 + c);
+  o1 = __float_as_uint(tm0.y) * stride0 + (__float_as_uint(tm1.y) * stride1 + c);
 }
 
 template <int KIND, int HP, int M0, int M1, int MASK, int ACC>
@@ -289,6 +291,14 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
   constexpr int U = 8 / HP;  // neighbours per step: 8 pairs per lane per step
   constexpr int NP = U * HP;
   const int slot_shift = 31 - __clz(p.R * 4);
+  // Plain counts add straight to the lane's histogram copy: its shared
+  // address is folded into the offset constants (slot k = bits - magic + 1
+  // on each axis), and a pair that is not counted here goes to slot 0
+  // (below range, never reported).
+  const uint32_t zoff = (ACC == kAccCount) ? w.s_hist_lane : 0u;
+  const uint32_t st0 = (uint32_t)p.slots1 * p.R * 4u, st1 = (uint32_t)p.R * 4u;
+  const uint32_t c1d = (1u - kMagicBits) * st0 + zoff;
+  const uint32_t c2d = (1u - kMagicBits) * (st0 + st1) + zoff;
   for (int j = 0; j < cnt; j += U) {
     uint32_t off[NP];
     float wj[U];
@@ -300,60 +310,57 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
       if constexpr ((KIND == KMONO || KIND == KTHETA) && M0 == kArith) {
         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
                      qz = make_float2(q.z, q.z);
-        const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u;
 #pragma unroll
         for (int sp = 0; sp < HP / 2; sp++) {
           uint32_t o[2];
           bool nr[2];
-          mono_arith2(p.ax[0], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], stride0, o[0], o[1],
+          mono_arith2(p.ax[0], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], st0, c1d, o[0], o[1],
                       nr[0], nr[1]);
 #pragma unroll
           for (int e = 0; e < 2; e++) {
             const int s = 2 * sp + e, k = u * HP + s;
             const int gj = gj0 + j + u;
-            if (MASK == 1 && !(gj > h.id[s])) { o[e] = 0u; nr[e] = false; }
-            if (MASK == 2 && gj == h.id[s]) { o[e] = 0u; nr[e] = false; }
-            if (nr[e]) { o[e] = 0u; nmask |= 1u << k; }
+            if (MASK == 1 && !(gj > h.id[s])) { o[e] = zoff; nr[e] = false; }
+            if (MASK == 2 && gj == h.id[s]) { o[e] = zoff; nr[e] = false; }
+            if (nr[e]) { o[e] = zoff; nmask |= 1u << k; }
             off[k] = o[e];
           }
         }
       } else if constexpr (KIND == KSIGPI && M0 == kArith) {
         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
                      qz = make_float2(q.z, q.z);
-        const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u, stride1 = (uint32_t)p.R * 4u;
 #pragma unroll
         for (int sp = 0; sp < HP / 2; sp++) {
           uint32_t o[2];
           bool nr[2];
-          sigpi_arith2(p.ax[0], p.ax[1], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], stride0,
-                       stride1, o[0], o[1], nr[0], nr[1]);
+          sigpi_arith2(p.ax[0], p.ax[1], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], st0, st1,
+                       c2d, o[0], o[1], nr[0], nr[1]);
 #pragma unroll
           for (int e = 0; e < 2; e++) {
             const int s = 2 * sp + e, k = u * HP + s;
             const int gj = gj0 + j + u;
-            if (MASK == 1 && !(gj > h.id[s])) { o[e] = 0u; nr[e] = false; }
-            if (MASK == 2 && gj == h.id[s]) { o[e] = 0u; nr[e] = false; }
-            if (nr[e]) { o[e] = 0u; nmask |= 1u << k; }
+            if (MASK == 1 && !(gj > h.id[s])) { o[e] = zoff; nr[e] = false; }
+            if (MASK == 2 && gj == h.id[s]) { o[e] = zoff; nr[e] = false; }
+            if (nr[e]) { o[e] = zoff; nmask |= 1u << k; }
             off[k] = o[e];
           }
         }
       } else if constexpr (KIND == KRMU && M0 == kArith) {
         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
                      qz = make_float2(q.z, q.z);
-        const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u, stride1 = (uint32_t)p.R * 4u;
 #pragma unroll
         for (int sp = 0; sp < HP / 2; sp++) {
           uint32_t o[2];
           bool nr[2];
           rmu_arith2(p.ax[0], p.ax[1], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], h.ax2[sp],
-                     h.ay2[sp], h.az2[sp], h.aq2[sp], stride0, stride1, o[0], o[1], nr[0], nr[1]);
+                     h.ay2[sp], h.az2[sp], h.aq2[sp], st0, st1, c2d, o[0], o[1], nr[0], nr[1]);
 #pragma unroll
           for (int e = 0; e < 2; e++) {
             const int s = 2 * sp + e, k = u * HP + s;
             const int gj = gj0 + j + u;
-            if (MASK == 1 && !(gj > h.id[s])) { o[e] = 0u; nr[e] = false; }
-            if (MASK == 2 && gj == h.id[s]) { o[e] = 0u; nr[e] = false; }
-            if (nr[e]) { o[e] = 0u; nmask |= 1u << k; }
+            if (MASK == 1 && !(gj > h.id[s])) { o[e] = zoff; nr[e] = false; }
+            if (MASK == 2 && gj == h.id[s]) { o[e] = zoff; nr[e] = false; }
+            if (nr[e]) { o[e] = zoff; nmask |= 1u << k; }
             off[k] = o[e];
           }
         }
@@ -366,18 +373,18 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
           const float dy = __fadd_rn(q.y, Home<HP>::get(h.ny2, s));
           const float dz = __fadd_rn(q.z, Home<HP>::get(h.nz2, s));
           bool near;
-          uint32_t o = bin_pair<KIND, HP, M0, M1>(p, lut, band, dx, dy, dz, h, s, near);
+          uint32_t o = bin_pair<KIND, HP, M0, M1>(p, lut, band, dx, dy, dz, h, s, near) + zoff;
           const int gj = gj0 + j + u;
-          if (MASK == 1 && !(gj > h.id[s])) { o = 0u; near = false; }   // not a pair of this item
-          if (MASK == 2 && gj == h.id[s]) { o = 0u; near = false; }     // no self pair
-          if (near) { o = 0u; nmask |= 1u << k; }
+          if (MASK == 1 && !(gj > h.id[s])) { o = zoff; near = false; }   // not a pair of this item
+          if (MASK == 2 && gj == h.id[s]) { o = zoff; near = false; }     // no self pair
+          if (near) { o = zoff; nmask |= 1u << k; }
           off[k] = o;
         }
       }
     }
     if (ACC != kAccAdjoint) {
 #pragma unroll
-      for (int k = 0; k < NP; k++) red_add1(w.s_hist_lane + off[k]);
+      for (int k = 0; k < NP; k++) red_add1(ACC == kAccCount ? off[k] : w.s_hist_lane + off[k]);
     }
     if (ACC == kAccWeighted) {
       // lane-private float-float column: a read-modify-write, no atomics

@@ -214,19 +214,12 @@ __device__ __forceinline__ uint32_t axis_resolve(uint32_t band, const AxisPlan &
 // signed distance of t - 1/2 to that integer (|h| = 1/2 on an edge).
 constexpr float kMagic = 12582912.0f;        // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
-__device__ __forceinline__ float arith_t(const AxisPlan &a, float x, float &h) {
-  float t = __fmaf_rn(x, a.inv, a.cst);
-  // NaN -> tlo: x = v rsqrt(v) is NaN only for v = 0, i.e. x = 0, and tlo is
-  // the clamp on the x = 0 side (bin 0 when e_0 = 0, below range otherwise)
-  t = fminf(fmaxf(t, a.tlo), a.thi);
-  const float tm = __fadd_rn(t, kMagic);
-  h = __fsub_rn(t, __fsub_rn(tm, kMagic));
-  return tm;
-}
-// slot byte offset of the bin held in tm (slot = bin + 1)
-__device__ __forceinline__ uint32_t arith_off(float tm, uint32_t stride) {
-  return (__float_as_uint(tm) - kMagicBits + 1u) * stride;
-}
+// Uniform edges (kArith): t = x * inv + cst, clamped to [tlo, thi] (a NaN
+// from x = v rsqrt(v) at v = 0 goes to tlo, the x = 0 side: bin 0 when
+// e_0 = 0, below range otherwise); tm = t + kMagic holds rint(t) in its low
+// mantissa bits, so the slot (bin + 1) is bits(tm) - kMagicBits + 1, and
+// h = t - (tm - kMagic) is exact.  mono_arith2 / sigpi_arith2 / rmu_arith2
+// (count_impl.cuh) apply this to two pairs at once.
 
 // The same for mu: the band holds the edge, the bound comes from the r slot.
 __device__ __forceinline__ uint32_t mu_resolve(uint32_t band, const AxisPlan &a, float mu,
