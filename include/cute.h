@@ -264,6 +264,21 @@ cute_status cute_estimator(cute_estimator_kind k, const uint64_t *DD, const uint
    bins theta on the given angles. */
 cute_status cute_theta_to_chord(const double *theta_deg, int32_t n, double *chord_out);
 
+/* Multipoles of xi(r, mu) (Eq. 3: xi(r, mu) = sum_l xi_l(r) P_l(mu), whose
+   l = 0 term is the monopole of Eq. 4).  With mu = |cos| in [0, 1] the even
+   multipoles are xi_l(r) = (2l + 1) * integral_0^1 xi(r, mu) P_l(mu) dmu,
+   and xi is taken constant within each mu bin, so bin k contributes
+   xi(r, k) * [P_{l+1} - P_{l-1}] from m_k to m_{k+1} (l >= 1; for l = 0 the
+   bin width).  xi: n_r x n_mu doubles, row-major [r][mu] (as
+   cute_count_pairs and cute_estimator give them); mu_edges: n_mu + 1
+   increasing values from 0 to 1; ells: n_ell even multipole orders in
+   0..16; out: n_ell x n_r doubles, [ell][r].  A NaN bin makes that r's
+   multipoles NaN.  FP64, host.  Errors: CUTE_E_INVALID (null pointers,
+   sizes < 1, edges not covering [0, 1] in increasing order, odd or out of
+   range orders). */
+cute_status cute_multipoles(const double *xi, int32_t n_r, int32_t n_mu, const double *mu_edges,
+                            int32_t n_ell, const int32_t *ells, double *out);
+
 /* Library version string. */
 const char *cute_version(void);
 

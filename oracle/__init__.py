@@ -173,3 +173,21 @@ def theta_to_chord(theta_deg):
     if rc != 0:
         raise ValueError("oracle_theta_to_chord failed")
     return out
+
+
+def multipoles(xi, mu_edges, ells=(0, 2, 4)):
+    """Even multipoles of a binned xi(r, mu), Sec. 2.1 Eq. 3 (xi(r, mu) =
+    sum_l xi_l(r) P_l(mu)) inverted by the orthogonality of the Legendre
+    polynomials: xi_l(r) = (2l + 1)/2 * integral_{-1}^{1} xi P_l dmu, which
+    for xi even in mu (mu = |cos|) is (2l + 1) * integral_0^1 xi P_l dmu;
+    xi is constant within each mu bin, and P_l is integrated exactly over
+    each bin with numpy's Legendre-series antiderivative.  l = 0 is Eq. 4."""
+    from numpy.polynomial import legendre
+    xi = np.asarray(xi, dtype=np.float64)
+    m = np.asarray(mu_edges, dtype=np.float64)
+    out = np.zeros((len(ells), xi.shape[0]))
+    for q, l in enumerate(ells):
+        anti = legendre.Legendre.basis(l).integ()
+        w = (2 * l + 1) * (anti(m[1:]) - anti(m[:-1]))
+        out[q] = xi @ w
+    return out

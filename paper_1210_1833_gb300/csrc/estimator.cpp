@@ -1,9 +1,11 @@
 // estimator.cpp -- correlation-function estimators on exact pair counts
-// (Sec. 2.2) and the angle -> chord helper.  Host FP64 arithmetic only,
+// (Sec. 2.2), multipoles of xi(r, mu) (Sec. 2.1, Eq. 3-4) and the angle ->
+// chord helper.  Host FP64 arithmetic only,
 // compiled without floating-point contraction.
 #include "cute_internal.h"
 
 #include <cmath>
+#include <vector>
 
 extern "C" {
 
@@ -54,6 +56,45 @@ cute_status cute_theta_to_chord(const double *theta_deg, int32_t n, double *chor
     if (!(theta_deg[i] >= 0 && theta_deg[i] <= 180)) return CUTE_E_INVALID;
     chord_out[i] = 2.0 * std::sin(0.5 * theta_deg[i] * (pi / 180.0));
   }
+  return CUTE_OK;
+}
+
+// Legendre polynomials P_0..P_{lmax}(x) by Bonnet's recurrence
+// (n + 1) P_{n+1} = (2n + 1) x P_n - n P_{n-1}.
+static void legendre_all(double x, int lmax, double *P) {
+  P[0] = 1.0;
+  if (lmax >= 1) P[1] = x;
+  for (int n = 1; n < lmax; n++) P[n + 1] = ((2.0 * n + 1.0) * x * P[n] - n * P[n - 1]) / (n + 1.0);
+}
+
+cute_status cute_multipoles(const double *xi, int32_t n_r, int32_t n_mu, const double *mu_edges,
+                            int32_t n_ell, const int32_t *ells, double *out) {
+  if (!xi || !mu_edges || !ells || !out || n_r < 1 || n_mu < 1 || n_ell < 1) return CUTE_E_INVALID;
+  if (mu_edges[0] != 0.0 || mu_edges[n_mu] != 1.0) return CUTE_E_INVALID;
+  for (int k = 0; k < n_mu; k++)
+    if (!(mu_edges[k + 1] > mu_edges[k])) return CUTE_E_INVALID;
+  int lmax = 0;
+  for (int q = 0; q < n_ell; q++) {
+    if (ells[q] < 0 || ells[q] > 16 || (ells[q] & 1)) return CUTE_E_INVALID;
+    lmax = ells[q] > lmax ? ells[q] : lmax;
+  }
+  // weights c[q][k]: (2l + 1) times the integral of P_l over mu bin k
+  std::vector<double> P0(lmax + 2), P1(lmax + 2), c((size_t)n_ell * n_mu);
+  for (int k = 0; k < n_mu; k++) {
+    legendre_all(mu_edges[k], lmax + 1, P0.data());
+    legendre_all(mu_edges[k + 1], lmax + 1, P1.data());
+    for (int q = 0; q < n_ell; q++) {
+      const int l = ells[q];
+      c[(size_t)q * n_mu + k] = l == 0 ? mu_edges[k + 1] - mu_edges[k]
+                                       : (P1[l + 1] - P1[l - 1]) - (P0[l + 1] - P0[l - 1]);
+    }
+  }
+  for (int q = 0; q < n_ell; q++)
+    for (int i = 0; i < n_r; i++) {
+      double s = 0.0;
+      for (int k = 0; k < n_mu; k++) s += xi[(size_t)i * n_mu + k] * c[(size_t)q * n_mu + k];
+      out[(size_t)q * n_r + i] = s;
+    }
   return CUTE_OK;
 }
 

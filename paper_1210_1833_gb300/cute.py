@@ -27,7 +27,7 @@ SYMBOLS = ["cute_ctx_create", "cute_ctx_destroy", "cute_last_error", "cute_sync"
            "cute_count_pairs", "cute_count_pairs_batched", "cute_count_pairs_adjoint",
            "cute_count_pairs_noalloc",
            "cute_last_stats", "cute_set_timing", "cute_set_launch", "cute_autotune",
-           "cute_estimator",
+           "cute_estimator", "cute_multipoles",
            "cute_theta_to_chord", "cute_version"]
 
 
@@ -97,6 +97,7 @@ def lib():
             L.cute_autotune.argtypes = [P, i32, P, i32, i64, ctypes.POINTER(Tuning)]
             L.cute_estimator.argtypes = [ctypes.c_int, P, P, P, i64, i64, i32, P, f64, P]
             L.cute_theta_to_chord.argtypes = [P, i32, P]
+            L.cute_multipoles.argtypes = [P, i32, i32, P, i32, P, P]
             L.cute_version.restype = ctypes.c_char_p
             for name in SYMBOLS:
                 if name not in ("cute_last_error", "cute_version"):
@@ -369,6 +370,22 @@ def estimator(kind, DD, DR=None, RR=None, Nd=0, Nr=0, edges=None, L=0.0):
     return out
 
 
+def multipoles(xi, mu_edges, ells=(0, 2, 4)):
+    """Even multipoles xi_l(r) of a binned xi(r, mu) (Eq. 3), xi of shape
+    (n_r, n_mu) on mu edges from 0 to 1.  Returns (len(ells), n_r)."""
+    x = np.ascontiguousarray(xi, dtype=np.float64)
+    if x.ndim != 2:
+        raise ValueError("xi must be (n_r, n_mu)")
+    m = np.ascontiguousarray(mu_edges, dtype=np.float64)
+    if len(m) != x.shape[1] + 1:
+        raise ValueError("mu_edges must have n_mu + 1 values")
+    ls = np.ascontiguousarray(ells, dtype=np.int32)
+    out = np.zeros((len(ls), x.shape[0]), dtype=np.float64)
+    _check(lib().cute_multipoles(_ptr(x), x.shape[0], x.shape[1], _ptr(m), len(ls), _ptr(ls),
+                                 _ptr(out)))
+    return out
+
+
 def theta_to_chord(theta_deg):
     t = np.ascontiguousarray(theta_deg, dtype=np.float64)
     out = np.zeros(len(t), dtype=np.float64)
@@ -378,3 +395,66 @@ def theta_to_chord(theta_deg):
 
 def version() -> str:
     return lib().cute_version().decode()
+
+
+def _make_weighted_count():
+    import torch
+
+    class CuteWeightedCount(torch.autograd.Function):
+        """W_b = sum of w_i w_j over the pairs in bin b (auto: unique pairs of
+        one catalog; cross: all pairs of two), differentiable in the weights.
+
+        forward: upload + grid + cute_count_pairs (weighted), outputs on the
+        weights' device; backward: cute_count_pairs_adjoint with the upstream
+        gradient G = dL/dW, giving dL/dw_i = sum_j w_j G[bin(i, j)].
+
+        apply(wa, wb, ctx, kind, xyz_a, xyz_b, edges0, edges1, periodic, L,
+        reach, cells_per_reach): wb / xyz_b None for an auto count; edges1
+        None for 1-D kinds; reach as for Context.grid.  Returns W as an
+        (n0, n1) float64 tensor."""
+
+        @staticmethod
+        def forward(fctx, wa, wb, ctx, kind, xyz_a, xyz_b, edges0, edges1, periodic, L, reach,
+                    cells_per_reach=0):
+            A = ctx.upload(xyz_a, weights=wa, periodic=periodic, L=L)
+            B = ctx.upload(xyz_b, weights=wb, periodic=periodic, L=L) if xyz_b is not None else None
+            ctx.grid([A] if B is None else [A, B], reach, cells_per_reach)
+            e0 = np.ascontiguousarray(edges0, dtype=np.float64)
+            e1 = None if edges1 is None else np.ascontiguousarray(edges1, dtype=np.float64)
+            n0 = len(e0) - 1
+            n1 = (len(e1) - 1) if (e1 is not None and kind in ("rmu", "sigpi")) else 1
+            cnt = torch.zeros(n0 * n1, dtype=torch.int64, device=wa.device)
+            W = torch.zeros(n0 * n1, dtype=torch.float64, device=wa.device)
+            ctx.count(kind, A, B, e0, e1, weighted=True, out=cnt, wsum_out=W, want_oor=False)
+            if fctx.needs_input_grad[0] or fctx.needs_input_grad[1]:
+                fctx.cute = (ctx, kind, A, B, e0, e1, wa.dtype, None if wb is None else wb.dtype)
+            else:
+                A.free()
+                if B is not None:
+                    B.free()
+            return W.view(n0, n1)
+
+        @staticmethod
+        def backward(fctx, gW):
+            ctx, kind, A, B, e0, e1, da, db = fctx.cute
+            G = gW.detach().to(torch.float64).contiguous().view(-1)
+            if B is None:
+                ga, gb = ctx.adjoint(kind, A, None, e0, e1, G=G), None
+            else:
+                ga, gb = ctx.adjoint(kind, A, B, e0, e1, G=G, grad_b=True)
+            A.free()
+            if B is not None:
+                B.free()
+            fctx.cute = None
+            return (ga.to(da), None if gb is None else gb.to(db)) + (None,) * 10
+
+    return CuteWeightedCount
+
+
+def __getattr__(name):
+    # torch is imported only when the autograd wrapper is asked for
+    if name == "CuteWeightedCount":
+        cls = _make_weighted_count()
+        globals()[name] = cls
+        return cls
+    raise AttributeError(name)

@@ -160,3 +160,38 @@ def test_adjoint_rmu_and_sigpi(ctx):
                           edges1=v.edges1)
     assert np.all(np.abs(ga[rows] - ref) <= 1e-9 * sc + 1e-300)
     d.free(); r.free()
+
+
+@pytest.mark.parametrize("cross", [False, True])
+def test_autograd_weighted_count(ctx, cross):
+    """CuteWeightedCount: W from the forward equals the oracle's weighted
+    counts, and w.grad after backward equals the oracle's gradient rows for
+    every weight (the adjoint), on device tensors."""
+    x, w = _case(3000, seed=33)
+    y, wy = _case(2000, seed=34) if cross else (None, None)
+    L = 400.0
+    e = np.arange(31) * 5.0
+    G = np.random.default_rng(35).normal(size=30)
+    wa = torch.tensor(w, device="cuda", requires_grad=True)
+    wb = torch.tensor(wy, device="cuda", requires_grad=True) if cross else None
+    W = cute.CuteWeightedCount.apply(wa, wb, ctx, "mono", x, y, e, None, True, L, [e[-1]] * 3, 0)
+    assert W.shape == (30, 1) and W.dtype == torch.float64
+    _, _, rws = oracle.count("mono", x, y, edges0=e, periodic=True, L=L, wa=w, wb=wy,
+                             weighted=True)
+    np.testing.assert_allclose(W.detach().cpu().numpy(), rws, rtol=1e-9, atol=0)
+    (W.view(-1) * torch.tensor(G, device="cuda")).sum().backward()
+    rows = np.arange(len(x))
+    ref = oracle.grad_rows("mono", x, rows, G, wy if cross else w, xb=y, edges0=e, periodic=True,
+                           L=L)
+    scale = oracle.grad_rows("mono", x, rows, np.abs(G), wy if cross else w, xb=y, edges0=e,
+                             periodic=True, L=L)
+    got = wa.grad.detach().cpu().numpy().astype(np.float64)
+    # float32 gradient of float32 weights: relative to the absolute-G scale
+    assert np.all(np.abs(got - ref) <= 1e-6 * scale + 1e-30)
+    if cross:
+        refb = oracle.grad_rows("mono", y, np.arange(len(y)), G, w, xb=x, edges0=e,
+                                periodic=True, L=L)
+        scaleb = oracle.grad_rows("mono", y, np.arange(len(y)), np.abs(G), w, xb=x, edges0=e,
+                                  periodic=True, L=L)
+        gotb = wb.grad.detach().cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(gotb - refb) <= 1e-6 * scaleb + 1e-30)

@@ -72,3 +72,37 @@ def test_estimator_rejects_bad_input():
         cute.estimator("ls", [1, 2], None, [1, 2], 10, 20)
     with pytest.raises(cute.CuteError):
         cute.estimator("periodic", [1, 2], Nd=1, edges=[0, 1, 2], L=10)
+
+
+def test_weighted_count_is_an_autograd_function():
+    """The binding's differentiable weighted count (forward: weighted count,
+    backward: adjoint) is a torch.autograd.Function."""
+    torch = pytest.importorskip("torch")
+    assert issubclass(cute.CuteWeightedCount, torch.autograd.Function)
+
+
+def test_multipoles_match_oracle():
+    """cute_multipoles (Bonnet recurrence, bin-edge differences) equals the
+    oracle (numpy Legendre antiderivatives) on uneven mu bins."""
+    rng = np.random.default_rng(82)
+    m = np.sort(np.concatenate([[0.0, 1.0], rng.uniform(0, 1, 38)]))
+    xi = rng.normal(size=(40, 39))
+    ells = (0, 2, 4, 6, 8)
+    got = cute.multipoles(xi, m, ells)
+    ref = oracle.multipoles(xi, m, ells)
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("bad", ["edges", "odd", "range"])
+def test_multipoles_reject_bad_input(bad):
+    xi = np.zeros((3, 4))
+    m = np.linspace(0, 1, 5)
+    ells = (0, 2)
+    if bad == "edges":
+        m = np.linspace(0, 0.9, 5)
+    elif bad == "odd":
+        ells = (1,)
+    else:
+        ells = (18,)
+    with pytest.raises(cute.CuteError):
+        cute.multipoles(xi, m, ells)

@@ -300,3 +300,46 @@ def test_ls_equals_normalised_form():
     np.testing.assert_allclose(xi, (ddn - 2 * drn + rrn) / rrn, rtol=1e-12)
     z = oracle.xi_ls(DD, DR, np.zeros(20, np.uint64), Nd, Nr)
     assert np.all(np.isnan(z))
+
+
+# ---------------------------------------------------------------- multipoles
+def test_multipoles_of_piecewise_constant_xi_by_quadrature():
+    """The binned xi(r, mu) is constant on each mu bin; its multipoles
+    (2l + 1) * integral_0^1 xi P_l dmu (Eq. 3 by orthogonality), with P_l
+    integrated over each bin by 8-point Gauss quadrature (exact to degree
+    15) of scipy's P_l, equal the oracle's."""
+    from scipy.special import eval_legendre
+    gx, gw = np.polynomial.legendre.leggauss(8)
+    rng = np.random.default_rng(80)
+    m = np.sort(np.concatenate([[0.0, 1.0], rng.uniform(0, 1, 14)]))
+    xi = rng.normal(size=(3, 15))
+    ells = (0, 2, 4, 6)
+    ref = np.zeros((len(ells), 3))
+    for q, l in enumerate(ells):
+        half, mid = 0.5 * np.diff(m), 0.5 * (m[1:] + m[:-1])
+        w = np.array([half[k] * np.dot(gw, eval_legendre(l, mid[k] + half[k] * gx))
+                      for k in range(15)])
+        ref[q] = (2 * l + 1) * xi @ w
+    np.testing.assert_allclose(oracle.multipoles(xi, m, ells), ref, rtol=1e-11, atol=1e-13)
+
+
+def test_multipoles_recover_legendre_coefficients_on_fine_bins():
+    """Eq. 3: xi(r, mu) = sum a_l P_l(mu) (l = 0, 2, 4, 6) sampled at 2000
+    mu-bin midpoints gives back the a_l up to the O(dmu^2) binning error."""
+    from scipy.special import eval_legendre
+    rng = np.random.default_rng(81)
+    m = np.linspace(0, 1, 2001)
+    mid = 0.5 * (m[1:] + m[:-1])
+    a = rng.normal(size=(3, 4))
+    xi = np.stack([sum(c[q] * eval_legendre(2 * q, mid) for q in range(4)) for c in a])
+    np.testing.assert_allclose(oracle.multipoles(xi, m, (0, 2, 4, 6)).T, a, atol=5e-5)
+
+
+def test_multipoles_of_constant_and_monopole_average():
+    """A mu-independent xi has xi_0 = xi and no l > 0 part; xi_0 of any xi is
+    its bin-width-weighted mean over [0, 1] (Eq. 4 for xi even in mu)."""
+    m = np.array([0.0, 0.1, 0.35, 0.5, 0.9, 1.0])
+    got = oracle.multipoles(np.full((2, 5), 0.7), m, (0, 2, 4))
+    np.testing.assert_allclose(got, [[0.7, 0.7], [0, 0], [0, 0]], atol=1e-15)
+    xi = np.random.default_rng(82).normal(size=(4, 5))
+    np.testing.assert_allclose(oracle.multipoles(xi, m, (0,))[0], xi @ np.diff(m), rtol=1e-14)
