@@ -390,6 +390,10 @@ def run_extras(ctx, dev, reps=3, which="all"):
         out.update(_row_batched(ctx, dev, timed))
     if which in ("all", "weighted"):
         out.update(_row_weighted(ctx, dev, timed))
+    if which in ("all", "monopole"):
+        out.update(_row_monopole(ctx, dev, timed))
+    if which in ("angular",):  # minutes of work: only on request
+        out.update(_row_angular(ctx, dev, timed))
     return out
 
 
@@ -447,6 +451,54 @@ def _alu_roofline(cand_rate, kind):
             "unit": "Tinst/s", "frac": ach / peak}
 
 
+def _row_monopole(ctx, dev, timed):
+    """c1: monopole DD of 20,000 points in a periodic box (grid build and
+    count per call), against its algorithmic roofline."""
+    import torch
+    w = synthetic.c1_monopole_box()
+    A = ctx.upload(w.data, periodic=True, L=w.L)
+    cnt = torch.zeros(len(w.edges0) - 1, dtype=torch.int64, device=f"cuda:{dev}")
+
+    def step():
+        ctx.grid([A], [w.edges0[-1]] * 3)
+        ctx.count("mono", A, None, w.edges0, out=cnt, want_oor=False)
+
+    t = timed(step)
+    st = ctx.stats()
+    out = {"monopole_c1_20k": {
+        "step_ms": t, "kernel_ms": st["kernel_ms"], "candidate_pairs": st["candidate_pairs"],
+        "binned_pairs": int(cnt.sum()),
+        "roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
+                                  "mono_periodic")}}
+    A.free()
+    return out
+
+
+def _row_angular(ctx, dev, timed):
+    """c3: w(theta) DD, DR and RR of 5M data and 20M randoms on a 1000 sq-deg
+    cap (64 log theta bins, binned on chords), each count timed once after a
+    warm-up count on a 2% sample."""
+    import torch
+    w = synthetic.c3_angular()
+    from paper_1210_1833_gb300 import cute
+    chord = cute.theta_to_chord(w.extra["theta_deg"])
+    D, R = ctx.upload(w.data), ctx.upload(w.randoms)
+    S = ctx.upload(w.data[: len(w.data) // 50])
+    ctx.grid([D, R, S], [chord[-1]] * 3)
+    ctx.count("theta", S, None, chord, want_oor=False)
+    res = {}
+    for name, a, b in (("DD", D, None), ("DR", D, R), ("RR", R, None)):
+        c, _, _ = ctx.count("theta", a, b, chord, want_oor=False)
+        st = ctx.stats()
+        res[name] = {"kernel_ms": st["kernel_ms"], "candidate_pairs": st["candidate_pairs"],
+                     "binned_pairs": int(c.sum()),
+                     "roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
+                                               "theta")}
+    for c in (D, R, S):
+        c.free()
+    return {"angular_c3_5M_20M": res}
+
+
 def _row_weighted(ctx, dev, timed):
     import torch
     out = {}
@@ -490,7 +542,7 @@ def main():
                     help="skip the warm-up autotuning (cells per reach, launch shapes)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched / weighted / adjoint measurements")
-    ap.add_argument("--row", default="", choices=["", "batched", "weighted"],
+    ap.add_argument("--row", default="", choices=["", "batched", "weighted", "monopole", "angular"],
                     help="profiling: run only this row (64-box batched sigma-pi, or the 4M "
                          "weighted forward and adjoint) and print it")
     args = ap.parse_args()

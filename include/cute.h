@@ -264,6 +264,31 @@ cute_status cute_estimator(cute_estimator_kind k, const uint64_t *DD, const uint
    bins theta on the given angles. */
 cute_status cute_theta_to_chord(const double *theta_deg, int32_t n, double *chord_out);
 
+/* ---------------------------------------------------------------- sky input */
+
+/* Background cosmology for comoving distances: present-day matter and
+   dark-energy densities (curvature 1 - omega_m - omega_l) and a constant
+   dark-energy equation of state w0 (-1: a cosmological constant). */
+typedef struct {
+  double omega_m, omega_l, w0;
+} cute_cosmology;
+
+/* Positions from sky coordinates, on the GPU.  ra, dec: n angles in
+   degrees; z: n redshifts in [0, 20], or NULL for unit vectors (the
+   projection onto the unit sphere of Sec. 3.4.2, for CUTE_THETA).  xyz: n x 3
+   doubles, row-major, = chi(z) (cos dec cos ra, cos dec sin ra, sin dec) in
+   Mpc/h, chi(z) = (c/H0) integral_0^z dz'/E(z') the radial comoving
+   distance of Sec. 2.1, c/H0 = 2997.92458 Mpc/h, E(z)^2 = omega_m (1+z)^3 +
+   (1 - omega_m - omega_l) (1+z)^2 + omega_l (1+z)^(3 (1 + w0)); positions
+   are placed along n at that distance (the flat-space separations of
+   Eq. 9).  chi is interpolated from an FP64 table (relative error below
+   1e-12).  All four arrays on the device of ctx, or all on the host; the
+   call returns when xyz is written.  Errors: CUTE_E_INVALID (null
+   pointers, n < 0, z without cosmology, E(z) <= 0 below z = 20, a redshift
+   outside [0, 20] or NaN), CUTE_E_OOM, CUTE_E_CUDA. */
+cute_status cute_sky_to_xyz(cute_ctx *ctx, const double *ra, const double *dec, const double *z,
+                            int64_t n, const cute_cosmology *cosmo, double *xyz);
+
 /* Multipoles of xi(r, mu) (Eq. 3: xi(r, mu) = sum_l xi_l(r) P_l(mu), whose
    l = 0 term is the monopole of Eq. 4).  With mu = |cos| in [0, 1] the even
    multipoles are xi_l(r) = (2l + 1) * integral_0^1 xi(r, mu) P_l(mu) dmu,

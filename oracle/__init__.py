@@ -191,3 +191,42 @@ def multipoles(xi, mu_edges, ells=(0, 2, 4)):
         w = (2 * l + 1) * (anti(m[1:]) - anti(m[:-1]))
         out[q] = xi @ w
     return out
+
+
+C_OVER_H0 = 2997.92458  # c / H0 in Mpc/h
+
+
+def comoving_distance(z, omega_m, omega_l, w0=-1.0):
+    """Radial comoving distance chi(z) of Sec. 2.1 in Mpc/h: (c/H0) times the
+    integral of 1/E from 0 to z, E^2 = Om (1+z)^3 + Ok (1+z)^2 + OL (1+z)^(3(1+w)),
+    Ok = 1 - Om - OL; integrated with scipy's adaptive quadrature between
+    consecutive sorted redshifts."""
+    from scipy.integrate import quad
+    z = np.asarray(z, dtype=np.float64)
+    ok = 1.0 - omega_m - omega_l
+
+    def inv_e(x):
+        a = 1.0 + x
+        return 1.0 / np.sqrt(omega_m * a ** 3 + ok * a ** 2 + omega_l * a ** (3.0 * (1.0 + w0)))
+
+    order = np.argsort(z, kind="stable")
+    out = np.empty_like(z)
+    acc, prev = 0.0, 0.0
+    for i in order:
+        if z[i] > prev:
+            acc += quad(inv_e, prev, z[i], epsabs=1e-15, epsrel=1e-13, limit=200)[0]
+            prev = z[i]
+        out[i] = C_OVER_H0 * acc
+    return out
+
+
+def sky_to_xyz(ra_deg, dec_deg, z=None, omega_m=0.3, omega_l=0.7, w0=-1.0):
+    """Positions chi(z) n from (RA, Dec) in degrees and redshifts (None: the
+    unit vectors n of the projection onto the unit sphere, Sec. 3.4.2),
+    n = (cos dec cos ra, cos dec sin ra, sin dec)."""
+    ra = np.radians(np.asarray(ra_deg, dtype=np.float64))
+    dec = np.radians(np.asarray(dec_deg, dtype=np.float64))
+    n = np.stack([np.cos(dec) * np.cos(ra), np.cos(dec) * np.sin(ra), np.sin(dec)], axis=1)
+    if z is None:
+        return n
+    return n * comoving_distance(z, omega_m, omega_l, w0)[:, None]

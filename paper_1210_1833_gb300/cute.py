@@ -27,7 +27,7 @@ SYMBOLS = ["cute_ctx_create", "cute_ctx_destroy", "cute_last_error", "cute_sync"
            "cute_count_pairs", "cute_count_pairs_batched", "cute_count_pairs_adjoint",
            "cute_count_pairs_noalloc",
            "cute_last_stats", "cute_set_timing", "cute_set_launch", "cute_autotune",
-           "cute_estimator", "cute_multipoles",
+           "cute_estimator", "cute_multipoles", "cute_sky_to_xyz",
            "cute_theta_to_chord", "cute_version"]
 
 
@@ -51,6 +51,11 @@ class Tuning(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Cosmology(ctypes.Structure):
+    _fields_ = [("omega_m", ctypes.c_double), ("omega_l", ctypes.c_double),
+                ("w0", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -98,6 +103,7 @@ def lib():
             L.cute_estimator.argtypes = [ctypes.c_int, P, P, P, i64, i64, i32, P, f64, P]
             L.cute_theta_to_chord.argtypes = [P, i32, P]
             L.cute_multipoles.argtypes = [P, i32, i32, P, i32, P, P]
+            L.cute_sky_to_xyz.argtypes = [P, P, P, P, i64, P, P]
             L.cute_version.restype = ctypes.c_char_p
             for name in SYMBOLS:
                 if name not in ("cute_last_error", "cute_version"):
@@ -339,6 +345,29 @@ class Context:
         _check(lib().cute_autotune(self.handle, len(pairs), descs, int(bool(tune_cells)),
                                    int(max_items), ctypes.byref(t)), self.handle)
         return t.as_dict()
+
+    # -------------------------------------------------------------- sky input
+    def sky_to_xyz(self, ra, dec, z=None, omega_m=0.3, omega_l=0.7, w0=-1.0):
+        """(RA, Dec) in degrees and redshifts z (None: unit vectors) -> (n, 3)
+        float64 comoving positions in Mpc/h, on the GPU.  numpy in, numpy
+        out; CUDA tensors in, CUDA tensor out."""
+        cos = Cosmology(omega_m, omega_l, w0)
+        if _is_torch(ra):
+            import torch
+            conv = lambda a: a.detach().to(torch.float64).contiguous()
+            r, d = conv(ra), conv(dec)
+            zz = conv(z) if z is not None else None
+            out = torch.empty((r.shape[0], 3), dtype=torch.float64, device=r.device)
+        else:
+            r = np.ascontiguousarray(ra, dtype=np.float64)
+            d = np.ascontiguousarray(dec, dtype=np.float64)
+            zz = None if z is None else np.ascontiguousarray(z, dtype=np.float64)
+            out = np.empty((len(r), 3), dtype=np.float64)
+        if len(d) != len(r) or (zz is not None and len(zz) != len(r)):
+            raise ValueError("ra, dec and z must have the same length")
+        _check(lib().cute_sky_to_xyz(self.handle, _ptr(r), _ptr(d), _ptr(zz), len(r),
+                                     ctypes.byref(cos), _ptr(out)), self.handle)
+        return out
 
     # -------------------------------------------------------------- misc
     def sync(self):

@@ -343,3 +343,26 @@ def test_multipoles_of_constant_and_monopole_average():
     np.testing.assert_allclose(got, [[0.7, 0.7], [0, 0], [0, 0]], atol=1e-15)
     xi = np.random.default_rng(82).normal(size=(4, 5))
     np.testing.assert_allclose(oracle.multipoles(xi, m, (0,))[0], xi @ np.diff(m), rtol=1e-14)
+
+
+# ---------------------------------------------------------------- sky coordinates
+def test_comoving_distance_closed_forms():
+    """chi(z) (Sec. 2.1) in three cosmologies with closed forms:
+    Einstein-de Sitter 2 (c/H0)(1 - 1/sqrt(1+z)), the empty universe
+    (c/H0) ln(1+z), de Sitter (c/H0) z."""
+    z = np.array([0.0, 0.1, 0.5, 1.0, 2.5, 7.0])
+    ch = oracle.C_OVER_H0
+    np.testing.assert_allclose(oracle.comoving_distance(z, 1.0, 0.0),
+                               2 * ch * (1 - 1 / np.sqrt(1 + z)), rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(oracle.comoving_distance(z, 0.0, 0.0), ch * np.log1p(z),
+                               rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(oracle.comoving_distance(z, 0.0, 1.0), ch * z, rtol=1e-12,
+                               atol=1e-9)
+
+
+def test_sky_unit_vectors():
+    """RA/Dec axes land on the coordinate axes, and every n has unit norm."""
+    n = oracle.sky_to_xyz([0.0, 90.0, 0.0, 180.0, 33.0], [0.0, 0.0, 90.0, -30.0, 61.0])
+    np.testing.assert_allclose(n[:3], np.eye(3), atol=1e-15)
+    np.testing.assert_allclose(n[3], [-np.cos(np.radians(30)), 0.0, -0.5], atol=1e-15)
+    np.testing.assert_allclose(np.linalg.norm(n, axis=1), 1.0, rtol=1e-15)
