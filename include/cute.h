@@ -289,6 +289,38 @@ typedef struct {
 cute_status cute_sky_to_xyz(cute_ctx *ctx, const double *ra, const double *dec, const double *z,
                             int64_t n, const cute_cosmology *cosmo, double *xyz);
 
+/* ---------------------------------------------------------------- pixel maps */
+
+/* Pixel map of an angular catalog (Sec. 3.4.2: correlate pixels weighted by
+   the objects they hold instead of the objects), on the GPU.  Pixelisation:
+   HEALPix RING (12 nside^2 equal-area pixels; the paper leaves the scheme
+   open).  xyz: n x 3 unit vectors (|x|^2 within 1e-6 of 1, else
+   CUTE_E_INVALID); w: n object weights or NULL for 1; map: 12 nside^2
+   doubles, overwritten with the summed weight of every pixel.  nside: a power
+   of 2 up to 8192.  All arrays on the device of ctx, or all on the host;
+   returns when map is written.  Pixel weights become FP32 catalog weights
+   when the pixels are uploaded (exact for integer counts below 2^24). */
+cute_status cute_pixel_map(cute_ctx *ctx, const double *xyz, const float *w, int64_t n,
+                           int32_t nside, double *map);
+
+/* Centres of HEALPix RING pixels pix[0..m) as unit vectors xyz (m x 3), on
+   the GPU; arrays both on the device or both on the host.  CUTE_E_INVALID
+   for an index outside 0 .. 12 nside^2 - 1. */
+cute_status cute_pixel_centres(cute_ctx *ctx, int32_t nside, const int64_t *pix, int64_t m,
+                               double *xyz);
+
+/* Estimators on weighted pair sums (pixel maps, weighted catalogs): Eq. 14
+   (CUTE_EST_NATURAL) or Eq. 15 (CUTE_EST_LS) with every count divided by its
+   total pair weight: DD by (S_d^2 - Q_d) / 2, DR by S_d S_r, RR by
+   (S_r^2 - Q_r) / 2, where S and Q are the sums of the weights and of their
+   squares (unit weights give the unique-pair normalisation of
+   cute_estimator).  DD, DR (LS only), RR: nbins doubles, host.  NaN where
+   RR = 0.  Errors: CUTE_E_INVALID (null pointers, nbins < 1, a non-positive
+   total pair weight, CUTE_EST_PERIODIC). */
+cute_status cute_estimator_weighted(cute_estimator_kind k, const double *DD, const double *DR,
+                                    const double *RR, double s_d, double q_d, double s_r,
+                                    double q_r, int32_t nbins, double *xi_out);
+
 /* Multipoles of xi(r, mu) (Eq. 3: xi(r, mu) = sum_l xi_l(r) P_l(mu), whose
    l = 0 term is the monopole of Eq. 4).  With mu = |cos| in [0, 1] the even
    multipoles are xi_l(r) = (2l + 1) * integral_0^1 xi(r, mu) P_l(mu) dmu,

@@ -230,3 +230,81 @@ def sky_to_xyz(ra_deg, dec_deg, z=None, omega_m=0.3, omega_l=0.7, w0=-1.0):
     if z is None:
         return n
     return n * comoving_distance(z, omega_m, omega_l, w0)[:, None]
+
+
+def healpix_ang2pix_ring(nside, xyz):
+    """Pixel index (HEALPix RING scheme, Gorski et al. 2005) of unit vectors,
+    the pixelisation taken for the pixel maps of Sec. 3.4.2: equatorial belt
+    |z| <= 2/3 located by the two families of pixel edge lines, polar caps by
+    the same lines in sqrt(3 (1 - |z|)) scaled coordinates."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    ns = int(nside)
+    x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+    phi = np.arctan2(y, x)
+    phi = np.where(phi < 0, phi + 2 * np.pi, phi)
+    tt = np.mod(phi / (0.5 * np.pi), 4.0)
+    za = np.abs(z)
+    npix, ncap = 12 * ns * ns, 2 * ns * (ns - 1)
+    out = np.empty(len(z), dtype=np.int64)
+    eq = za <= 2.0 / 3.0
+    # equatorial belt
+    t1, t2 = ns * (0.5 + tt[eq]), ns * z[eq] * 0.75
+    jp, jm = np.floor(t1 - t2).astype(np.int64), np.floor(t1 + t2).astype(np.int64)
+    ir = ns + 1 + jp - jm
+    kshift = 1 - (ir & 1)
+    ip = np.mod((jp + jm - ns + kshift + 1) // 2, 4 * ns)
+    out[eq] = ncap + (ir - 1) * 4 * ns + ip
+    # polar caps
+    pc = ~eq
+    tp = tt[pc] - np.floor(tt[pc])
+    tmp = ns * np.sqrt(3.0 * (1.0 - za[pc]))
+    jp, jm = np.floor(tp * tmp).astype(np.int64), np.floor((1.0 - tp) * tmp).astype(np.int64)
+    ir = jp + jm + 1
+    ip = np.mod(np.floor(tt[pc] * ir).astype(np.int64), 4 * ir)
+    out[pc] = np.where(z[pc] > 0, 2 * ir * (ir - 1) + ip, npix - 2 * ir * (ir + 1) + ip)
+    return out
+
+
+def healpix_pix2vec_ring(nside, pix):
+    """Centres of HEALPix RING pixels as unit vectors: ring i of the north
+    cap holds pixels 2i(i-1) .. 2i(i+1)-1 at z = 1 - i^2/(3 nside^2); the
+    belt rings hold 4 nside pixels at z = (2 nside - i) 2/(3 nside), every
+    other ring shifted by half a pixel; the south cap mirrors the north."""
+    ns = int(nside)
+    p = np.asarray(pix, dtype=np.int64)
+    npix, ncap = 12 * ns * ns, 2 * ns * (ns - 1)
+    z = np.empty(len(p))
+    phi = np.empty(len(p))
+    n = p < ncap
+    i = (1 + np.floor(np.sqrt(1 + 2 * p[n] + 0.5)).astype(np.int64)) // 2
+    j = p[n] + 1 - 2 * i * (i - 1)
+    z[n], phi[n] = 1.0 - i * i / (3.0 * ns * ns), (j - 0.5) * np.pi / (2.0 * i)
+    e = (p >= ncap) & (p < npix - ncap)
+    q = p[e] - ncap
+    i = q // (4 * ns) + ns
+    j = q % (4 * ns) + 1
+    shift = np.where((i + ns) & 1, 1.0, 0.5)
+    z[e], phi[e] = (2 * ns - i) * 2.0 / (3.0 * ns), (j - shift) * np.pi / (2.0 * ns)
+    s = p >= npix - ncap
+    q = npix - p[s]
+    i = (1 + np.floor(np.sqrt(2 * q - 1 + 0.5)).astype(np.int64)) // 2
+    j = 4 * i + 1 - (q - 2 * i * (i - 1))
+    z[s], phi[s] = -1.0 + i * i / (3.0 * ns * ns), (j - 0.5) * np.pi / (2.0 * i)
+    st = np.sqrt((1.0 - z) * (1.0 + z))
+    return np.stack([st * np.cos(phi), st * np.sin(phi), z], axis=1)
+
+
+def xi_weighted(kind, DD, DR, RR, s_d, q_d, s_r, q_r):
+    """Eq. 14 / Eq. 15 on weighted pair sums: DD over the total data-data
+    pair weight (S_d^2 - Q_d)/2, DR over S_d S_r, RR over (S_r^2 - Q_r)/2."""
+    DD = np.asarray(DD, dtype=np.float64)
+    RR = np.asarray(RR, dtype=np.float64)
+    dd = DD / (0.5 * (s_d * s_d - q_d))
+    rr = RR / (0.5 * (s_r * s_r - q_r))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        if kind == "natural":
+            out = dd / rr - 1.0
+        else:
+            dr = np.asarray(DR, dtype=np.float64) / (s_d * s_r)
+            out = (dd - 2.0 * dr + rr) / rr
+    return np.where(RR != 0, out, np.nan)

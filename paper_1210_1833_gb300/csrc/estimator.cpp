@@ -98,4 +98,25 @@ cute_status cute_multipoles(const double *xi, int32_t n_r, int32_t n_mu, const d
   return CUTE_OK;
 }
 
+cute_status cute_estimator_weighted(cute_estimator_kind k, const double *DD, const double *DR,
+                                    const double *RR, double s_d, double q_d, double s_r,
+                                    double q_r, int32_t nbins, double *xi_out) {
+  if (!DD || !RR || !xi_out || nbins < 1) return CUTE_E_INVALID;
+  if (k != CUTE_EST_NATURAL && k != CUTE_EST_LS) return CUTE_E_INVALID;
+  const double ndd = 0.5 * (s_d * s_d - q_d), nrr = 0.5 * (s_r * s_r - q_r), ndr = s_d * s_r;
+  if (!(ndd > 0) || !(nrr > 0) || !(ndr > 0)) return CUTE_E_INVALID;
+  if (k == CUTE_EST_LS && !DR) return CUTE_E_INVALID;
+  for (int b = 0; b < nbins; b++) {
+    const double rr = RR[b] / nrr;
+    if (!(RR[b] != 0.0)) {
+      xi_out[b] = NAN;
+    } else if (k == CUTE_EST_NATURAL) {  // Eq. 14
+      xi_out[b] = (DD[b] / ndd) / rr - 1.0;
+    } else {  // Eq. 15
+      xi_out[b] = (DD[b] / ndd - 2.0 * (DR[b] / ndr) + rr) / rr;
+    }
+  }
+  return CUTE_OK;
+}
+
 }  // extern "C"

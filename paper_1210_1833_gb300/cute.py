@@ -27,7 +27,8 @@ SYMBOLS = ["cute_ctx_create", "cute_ctx_destroy", "cute_last_error", "cute_sync"
            "cute_count_pairs", "cute_count_pairs_batched", "cute_count_pairs_adjoint",
            "cute_count_pairs_noalloc",
            "cute_last_stats", "cute_set_timing", "cute_set_launch", "cute_autotune",
-           "cute_estimator", "cute_multipoles", "cute_sky_to_xyz",
+           "cute_estimator", "cute_multipoles", "cute_sky_to_xyz", "cute_pixel_map",
+           "cute_pixel_centres", "cute_estimator_weighted",
            "cute_theta_to_chord", "cute_version"]
 
 
@@ -104,6 +105,10 @@ def lib():
             L.cute_theta_to_chord.argtypes = [P, i32, P]
             L.cute_multipoles.argtypes = [P, i32, i32, P, i32, P, P]
             L.cute_sky_to_xyz.argtypes = [P, P, P, P, i64, P, P]
+            L.cute_pixel_map.argtypes = [P, P, P, i64, i32, P]
+            L.cute_pixel_centres.argtypes = [P, i32, P, i64, P]
+            L.cute_estimator_weighted.argtypes = [ctypes.c_int, P, P, P, f64, f64, f64, f64,
+                                                  i32, P]
             L.cute_version.restype = ctypes.c_char_p
             for name in SYMBOLS:
                 if name not in ("cute_last_error", "cute_version"):
@@ -369,6 +374,36 @@ class Context:
                                      ctypes.byref(cos), _ptr(out)), self.handle)
         return out
 
+    # -------------------------------------------------------------- pixel maps
+    def pixel_map(self, xyz, weights=None, nside=256):
+        """HEALPix RING map (12 nside^2 doubles) of unit vectors, each pixel
+        the summed weight of its objects.  numpy in -> numpy out, CUDA
+        tensors in -> CUDA tensor out."""
+        x = _xyz(xyz)
+        w = _w(weights)
+        npix = 12 * nside * nside
+        if _is_torch(x):
+            import torch
+            out = torch.zeros(npix, dtype=torch.float64, device=x.device)
+        else:
+            out = np.zeros(npix, dtype=np.float64)
+        _check(lib().cute_pixel_map(self.handle, _ptr(x), _ptr(w), int(x.shape[0]), int(nside),
+                                    _ptr(out)), self.handle)
+        return out
+
+    def pixel_centres(self, nside, pix):
+        """Unit-vector centres (m, 3) of HEALPix RING pixels."""
+        if _is_torch(pix):
+            import torch
+            p = pix.detach().to(torch.int64).contiguous()
+            out = torch.empty((p.shape[0], 3), dtype=torch.float64, device=p.device)
+        else:
+            p = np.ascontiguousarray(pix, dtype=np.int64)
+            out = np.empty((len(p), 3), dtype=np.float64)
+        _check(lib().cute_pixel_centres(self.handle, int(nside), _ptr(p), len(p), _ptr(out)),
+               self.handle)
+        return out
+
     # -------------------------------------------------------------- misc
     def sync(self):
         _check(lib().cute_sync(self.handle), self.handle)
@@ -412,6 +447,19 @@ def multipoles(xi, mu_edges, ells=(0, 2, 4)):
     out = np.zeros((len(ls), x.shape[0]), dtype=np.float64)
     _check(lib().cute_multipoles(_ptr(x), x.shape[0], x.shape[1], _ptr(m), len(ls), _ptr(ls),
                                  _ptr(out)))
+    return out
+
+
+def estimator_weighted(kind, DD, DR, RR, s_d, q_d, s_r, q_r):
+    """Eq. 14 ('natural') or Eq. 15 ('ls') on weighted pair sums, each
+    normalised by its total pair weight (S: sum of weights, Q: of squares)."""
+    DD = np.ascontiguousarray(DD, dtype=np.float64).ravel()
+    DR_ = None if DR is None else np.ascontiguousarray(DR, dtype=np.float64).ravel()
+    RR = np.ascontiguousarray(RR, dtype=np.float64).ravel()
+    out = np.zeros(len(DD), dtype=np.float64)
+    _check(lib().cute_estimator_weighted(ESTIMATORS[kind], _ptr(DD), _ptr(DR_), _ptr(RR),
+                                         float(s_d), float(q_d), float(s_r), float(q_r), len(DD),
+                                         _ptr(out)))
     return out
 
 

@@ -106,3 +106,16 @@ def test_multipoles_reject_bad_input(bad):
         ells = (18,)
     with pytest.raises(cute.CuteError):
         cute.multipoles(xi, m, ells)
+
+
+def test_weighted_estimators_match_oracle():
+    rng = np.random.default_rng(85)
+    DD, DR, RR = (rng.uniform(1, 1e6, 30) for _ in range(3))
+    RR[3] = 0.0
+    args = (1234.5, 2001.25, 8765.0, 9000.5)
+    for kind in ("natural", "ls"):
+        got = cute.estimator_weighted(kind, DD, DR, RR, *args)
+        ref = oracle.xi_weighted(kind, DD, DR, RR, *args)
+        np.testing.assert_allclose(got, ref, rtol=1e-13, equal_nan=True)
+    with pytest.raises(cute.CuteError):
+        cute.estimator_weighted("periodic", DD, DR, RR, *args)

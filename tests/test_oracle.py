@@ -366,3 +366,61 @@ def test_sky_unit_vectors():
     np.testing.assert_allclose(n[:3], np.eye(3), atol=1e-15)
     np.testing.assert_allclose(n[3], [-np.cos(np.radians(30)), 0.0, -0.5], atol=1e-15)
     np.testing.assert_allclose(np.linalg.norm(n, axis=1), 1.0, rtol=1e-15)
+
+
+# ---------------------------------------------------------------- pixel maps
+def test_healpix_base_pixels():
+    """nside = 1: the 12 base pixels, 4 at z = 2/3 and 4 at z = -2/3 centred
+    on phi = pi/4 + k pi/2, 4 on the equator centred on phi = k pi/2."""
+    c = oracle.healpix_pix2vec_ring(1, np.arange(12))
+    z = np.repeat([2 / 3, 0.0, -2 / 3], 4)
+    phi = np.concatenate([np.pi / 4 + np.arange(4) * np.pi / 2, np.arange(4) * np.pi / 2,
+                          np.pi / 4 + np.arange(4) * np.pi / 2])
+    st = np.sqrt(1 - z * z)
+    ref = np.stack([st * np.cos(phi), st * np.sin(phi), z], axis=1)
+    np.testing.assert_allclose(c, ref, atol=1e-15)
+    np.testing.assert_array_equal(oracle.healpix_ang2pix_ring(1, ref), np.arange(12))
+
+
+@pytest.mark.parametrize("nside", [1, 2, 4, 16, 64])
+def test_healpix_round_trip_and_rings(nside):
+    """Every pixel's centre lies in that pixel; the centres sit on 4 nside - 1
+    rings with 4i pixels on the i-th ring from either pole (i < nside) and
+    4 nside on the belt rings."""
+    p = np.arange(12 * nside * nside)
+    c = oracle.healpix_pix2vec_ring(nside, p)
+    np.testing.assert_allclose(np.linalg.norm(c, axis=1), 1.0, rtol=1e-14)
+    np.testing.assert_array_equal(oracle.healpix_ang2pix_ring(nside, c), p)
+    zs, counts = np.unique(np.round(c[:, 2], 12), return_counts=True)
+    assert len(zs) == 4 * nside - 1
+    expect = [4 * min(i, 4 * nside - i, nside) for i in range(1, 4 * nside)]
+    assert sorted(counts.tolist()) == sorted(expect)
+
+
+def test_healpix_equal_area_and_locality():
+    """Pixels have equal area: 2M uniform points on the sphere fill the 192
+    pixels of nside = 4 evenly (chi^2 within 5 sigma); every point lies
+    within 1.5 pixel radii of its pixel's centre."""
+    rng = np.random.default_rng(83)
+    v = rng.normal(size=(2_000_000, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    p = oracle.healpix_ang2pix_ring(4, v)
+    cnt = np.bincount(p, minlength=192)
+    mean = len(v) / 192
+    chi2 = float(((cnt - mean) ** 2 / mean).sum())
+    assert abs(chi2 - 191) < 5 * np.sqrt(2 * 191)
+    c = oracle.healpix_pix2vec_ring(4, p[:20000])
+    ang = np.arccos(np.clip(np.sum(c * v[:20000], axis=1), -1, 1))
+    assert ang.max() < 1.5 * np.sqrt(4 * np.pi / 192)
+
+
+def test_weighted_estimators_reduce_to_unweighted():
+    """Unit weights turn the weighted estimators into Eq. 14 / Eq. 15 on
+    unique-pair counts."""
+    rng = np.random.default_rng(84)
+    DD, DR, RR = (rng.integers(1, 10**6, 20).astype(np.uint64) for _ in range(3))
+    nd, nr = 5000, 20000
+    nat = oracle.xi_weighted("natural", DD, None, RR, nd, nd, nr, nr)
+    ls = oracle.xi_weighted("ls", DD, DR, RR, nd, nd, nr, nr)
+    np.testing.assert_allclose(nat, oracle.xi_natural(DD, RR, nd, nr), rtol=1e-13)
+    np.testing.assert_allclose(ls, oracle.xi_ls(DD, DR, RR, nd, nr), rtol=1e-12)
