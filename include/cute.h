@@ -321,6 +321,27 @@ cute_status cute_estimator_weighted(cute_estimator_kind k, const double *DD, con
                                     const double *RR, double s_d, double q_d, double s_r,
                                     double q_r, int32_t nbins, double *xi_out);
 
+/* ---------------------------------------------------------------- density grid */
+
+/* Monopole of a periodic box from a density grid (Sec. 3.4.4), on the GPU:
+   the objects (xyz: n_obj x 3 in [0, box_L), w: weights or NULL for 1) are
+   interpolated to an ngrid^3 grid (grid points at multiples of
+   a = box_L / ngrid) with the triangular-shaped-cloud kernel, the
+   overdensity delta = rho / mean(rho) - 1 is formed, and xi_b is the mean of
+   delta_i delta_j over the pairs of distinct grid points whose separation r
+   (periodic, squared in FP64) falls in [e_b, e_b+1).  ngrid: a multiple of
+   32 in 32..1024; r_max = edges[nbins] below box_L / 2 and at least a.
+   xi_out: nbins doubles (NaN for a bin no lag falls in); lags_out (or NULL):
+   the number of lag vectors per bin (each unordered pair direction once).
+   xyz and w both on the device of ctx or both on the host; outputs on the
+   host; returns when done.  Results are FP32 lag sums with float-float
+   accumulation: relative error about 1e-6 of the sum of |delta_i delta_j|.
+   Errors: CUTE_E_INVALID (arguments, positions outside the box, total weight
+   <= 0), CUTE_E_OOM, CUTE_E_CUDA. */
+cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, const float *w, int64_t n_obj,
+                                 double box_L, int32_t ngrid, const double *edges, int32_t nbins,
+                                 double *xi_out, double *lags_out);
+
 /* Multipoles of xi(r, mu) (Eq. 3: xi(r, mu) = sum_l xi_l(r) P_l(mu), whose
    l = 0 term is the monopole of Eq. 4).  With mu = |cos| in [0, 1] the even
    multipoles are xi_l(r) = (2l + 1) * integral_0^1 xi(r, mu) P_l(mu) dmu,

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libcute_gb.so")
 BUILD = os.path.join(HERE, "_build")
 
-SOURCES = ["api.cu", "grid.cu", "count_mono.cu", "count_sigpi.cu", "count_rmu.cu", "noalloc.cu", "work.cu", "sky.cu", "pixel.cu",
+SOURCES = ["api.cu", "grid.cu", "count_mono.cu", "count_sigpi.cu", "count_rmu.cu", "noalloc.cu", "work.cu", "sky.cu", "pixel.cu", "density.cu",
            "plan.cpp", "estimator.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1,0 +1,309 @@
+// density.cu -- the density-grid estimate of the monopole in a periodic box
+// (Sec. 3.4.4).
+//
+// The catalog is interpolated to an n^3 grid with the triangular-shaped-
+// cloud (TSC) kernel, the overdensity delta = rho / mean(rho) - 1 is formed
+// at every grid point, and xi(r) is the mean of delta_i delta_j over the
+// pairs of distinct grid points whose separation falls in each bin.  On a
+// regular periodic grid the pairs at a lag vector d all share one
+// separation, so the work is the lag correlation
+//     C(d) = sum_i delta_i delta_{i + d}
+// for every lag of the half ball |d| a < r_max (each unordered pair once),
+// and xi_b = sum_{d in b} C(d) / (n^3 * #lags in b).
+//
+// Kernels:
+//   k_tsc       27 FP64 atomic adds per object into the grid;
+//   k_delta     rho -> FP32 delta;
+//   k_lagcorr   one CTA per (dy, dz) lag column, 64-lag dx window and z slab:
+//               the rows delta[:, y, z] and delta[:, y + dy, z + dz] (plus
+//               the dx halo) are staged in shared memory, and each thread
+//               sums 8 consecutive dx lags over every 32nd x; FP32 partial
+//               sums over 16 rows (n/2 terms) are folded into float-float
+//               accumulators, so a lag sum carries about the FP32 rounding of
+//               those partials.
+#include "cute_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+namespace cute {
+
+namespace {
+
+constexpr int kMaxGrid = 1024;
+constexpr int kLagThreads = 256;  // 32 x-segments x 8 lag groups
+constexpr int kLagPer = 8;        // lags per thread
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// TSC weights of a particle at grid coordinate u (grid points at integers):
+// nearest point i0 = rint(u), d = u - i0 in [-1/2, 1/2]:
+// w(i0 - 1) = (1/2 - d)^2 / 2, w(i0) = 3/4 - d^2, w(i0 + 1) = (1/2 + d)^2 / 2
+__device__ __forceinline__ void tsc1(double u, int n, int idx[3], double w[3]) {
+  const double i0 = rint(u);
+  const double d = u - i0;
+  const int c = (int)i0;
+  idx[0] = wrapi(c - 1, n);
+  idx[1] = wrapi(c >= n ? c - n : c, n);
+  idx[2] = wrapi(c + 1 >= n ? c + 1 - n : c + 1, n);
+  w[0] = 0.5 * (0.5 - d) * (0.5 - d);
+  w[1] = 0.75 - d * d;
+  w[2] = 0.5 * (0.5 + d) * (0.5 + d);
+}
+
+__global__ void k_tsc(const double *__restrict__ xyz, const float *__restrict__ wt, long long np,
+                      int n, double inv_a, double *__restrict__ rho, int *__restrict__ bad,
+                      double box) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  int ix[3], iy[3], iz[3];
+  double wx[3], wy[3], wz[3];
+  const double x = xyz[3 * p], y = xyz[3 * p + 1], z = xyz[3 * p + 2];
+  if (!(x >= 0.0 && x < box && y >= 0.0 && y < box && z >= 0.0 && z < box)) {
+    atomicExch(bad, 1);
+    return;
+  }
+  tsc1(x * inv_a, n, ix, wx);
+  tsc1(y * inv_a, n, iy, wy);
+  tsc1(z * inv_a, n, iz, wz);
+  const double m = wt ? (double)wt[p] : 1.0;
+  for (int c = 0; c < 3; c++)
+    for (int b = 0; b < 3; b++) {
+      const double wzy = m * wz[c] * wy[b];
+      const long long row = ((long long)iz[c] * n + iy[b]) * n;
+      for (int a = 0; a < 3; a++) atomicAdd(&rho[row + ix[a]], wzy * wx[a]);
+    }
+}
+
+__global__ void k_delta(const double *__restrict__ rho, long long m, double inv_mean,
+                        float *__restrict__ delta) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) delta[i] = (float)(rho[i] * inv_mean - 1.0);
+}
+
+__device__ __forceinline__ void ff_acc(float &hi, float &lo, float v) {
+  // float-float accumulation (TwoSum of hi and v, low parts summed)
+  const float s = hi + v;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (v - bb);
+  hi = s;
+  lo += err;
+}
+
+// One CTA: lag column (dy, dz) = cols[blockIdx.x], lags dx in
+// [dx0, dx0 + 64) of that column (blockIdx.y picks the 64-lag window), rows
+// z in [z0, z1) (blockIdx.z picks the slab).  out[col][dx - dxmin] += C.
+__global__ void __launch_bounds__(kLagThreads) k_lagcorr(const float *__restrict__ delta, int n,
+                                                         const int4 *__restrict__ cols,
+                                                         int zslab, double *__restrict__ out,
+                                                         int out_stride) {
+  extern __shared__ float sm[];  // rowA[n], rowB[n + 64 + 8]
+  const int4 col = cols[blockIdx.x];  // (dy, dz, dxmin, dxmax)
+  const int dy = col.x, dz = col.y, dxmin = col.z, dxmax = col.w;
+  const int dx0 = dxmin + 64 * (int)blockIdx.y;
+  if (dx0 > dxmax) return;
+  const int z0 = blockIdx.z * zslab, z1 = min(n, z0 + zslab);
+  float *rowA = sm;
+  float *rowB = sm + n;
+  const int lg = threadIdx.x >> 5;   // lag group: lags dx0 + 8 lg .. + 7
+  const int xs = threadIdx.x & 31;   // x segment
+  float hi[kLagPer], lo[kLagPer], part[kLagPer];
+#pragma unroll
+  for (int k = 0; k < kLagPer; k++) hi[k] = lo[k] = part[k] = 0.0f;
+  int rows = 0;
+  const int span = n + 64 + 8;
+  for (int z = z0; z < z1; z++) {
+    const int zb = wrapi(z + dz, n);
+    for (int y = 0; y < n; y++) {
+      const int yb = wrapi(y + dy, n);
+      const float *A = delta + ((long long)z * n + y) * n;
+      const float *B = delta + ((long long)zb * n + yb) * n;
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += kLagThreads) rowA[i] = A[i];
+      for (int i = threadIdx.x; i < span; i += kLagThreads) {
+        int xb = i + dx0;  // rowB[i] = delta[x = i + dx0 (wrapped)]
+        xb %= n;
+        if (xb < 0) xb += n;
+        rowB[i] = B[xb];
+      }
+      __syncthreads();
+      // thread: x = xs + 32 q, lags dx0 + 8 lg + k
+      for (int x = xs; x < n; x += 32) {
+        const float a = rowA[x];
+        const float *b = rowB + x + 8 * lg;  // delta[x + dx0 + 8 lg + k]
+#pragma unroll
+        for (int k = 0; k < kLagPer; k++) part[k] = fmaf(a, b[k], part[k]);
+      }
+      if (++rows == 16) {
+#pragma unroll
+        for (int k = 0; k < kLagPer; k++) {
+          ff_acc(hi[k], lo[k], part[k]);
+          part[k] = 0.0f;
+        }
+        rows = 0;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kLagPer; k++) ff_acc(hi[k], lo[k], part[k]);
+  // reduce the 32 x segments of each lag group (a warp) and add to out
+#pragma unroll
+  for (int k = 0; k < kLagPer; k++) {
+    double v = (double)hi[k] + (double)lo[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int dx = dx0 + 8 * lg + k;
+    if (xs == 0 && dx <= dxmax) atomicAdd(&out[(size_t)blockIdx.x * out_stride + (dx - dxmin)], v);
+  }
+}
+
+}  // namespace
+
+}  // namespace cute
+
+using namespace cute;
+
+extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, const float *w,
+                                            int64_t n_obj, double box_L, int32_t ngrid,
+                                            const double *edges, int32_t nbins, double *xi_out,
+                                            double *lags_out) {
+  if (!ctx) return CUTE_E_INVALID;
+  ctx->err.clear();
+  auto fail = [&](cute_status st, const std::string &m) {
+    ctx->err = m;
+    return st;
+  };
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(CUTE_E_CUDA, "cudaSetDevice");
+  if (n_obj < 1 || !xyz || !edges || !xi_out || nbins < 1 || !(box_L > 0) || ngrid < 8 ||
+      ngrid > kMaxGrid || ngrid % 32)
+    return fail(CUTE_E_INVALID, "bad arguments (ngrid: a multiple of 32 in 32..1024)");
+  for (int b = 0; b < nbins; b++)
+    if (!(edges[b + 1] > edges[b]) || !(edges[0] >= 0))
+      return fail(CUTE_E_INVALID, "edges must be increasing and >= 0");
+  const double a = box_L / ngrid;
+  const double rmax = edges[nbins];
+  if (!(rmax < 0.5 * box_L)) return fail(CUTE_E_INVALID, "r_max must be below L/2");
+  const int R = (int)std::floor(rmax / a);  // largest |d| component that can be in range
+  if (R < 1) return fail(CUTE_E_INVALID, "r_max must be at least one grid cell");
+  // half-ball lag columns (dy, dz) with their dx ranges; a lag is in range
+  // when its squared length (in FP64, a^2 |d|^2) is below r_max^2
+  std::vector<int4> cols;
+  const double r2max = rmax * rmax;
+  for (int dz = -R; dz <= R; dz++)
+    for (int dy = -R; dy <= R; dy++) {
+      if (dz < 0 || (dz == 0 && dy < 0)) continue;  // half space (the other half mirrors)
+      const double q = ((double)dy * dy + (double)dz * dz) * a * a;
+      if (q >= r2max) continue;
+      int xm = 0;
+      while ((double)(xm + 1) * (xm + 1) * a * a + q < r2max) xm++;
+      const int lo = (dz == 0 && dy == 0) ? 1 : -xm;  // d = 0 excluded, dx > 0 half line
+      if (lo > xm) continue;
+      cols.push_back(make_int4(dy, dz, lo, xm));
+    }
+  int maxw = 1;
+  for (const int4 &c : cols) maxw = std::max(maxw, c.w - c.z + 1);
+  const long long m = (long long)ngrid * ngrid * ngrid;
+  const bool dev = [&] {
+    cudaPointerAttributes at;
+    const bool d = cudaPointerGetAttributes(&at, xyz) == cudaSuccess &&
+                   (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    return d;
+  }();
+  const size_t xb = (size_t)n_obj * 3 * sizeof(double), wb = w ? (size_t)n_obj * sizeof(float) : 0;
+  const size_t ob = cols.size() * (size_t)maxw * sizeof(double);
+  const size_t need = 256 + m * sizeof(double) + m * sizeof(float) + cols.size() * sizeof(int4) +
+                      ob + (dev ? 0 : xb + wb) + 1024;
+  char *buf = nullptr;
+  if (cudaMalloc(&buf, need) != cudaSuccess) return fail(CUTE_E_OOM, "cudaMalloc");
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  int *d_bad = (int *)buf;
+  double *d_rho = (double *)(buf + 256);
+  float *d_delta = (float *)((char *)d_rho + al(m * sizeof(double)));
+  int4 *d_cols = (int4 *)((char *)d_delta + al(m * sizeof(float)));
+  double *d_out = (double *)((char *)d_cols + al(cols.size() * sizeof(int4)));
+  const double *d_xyz = xyz;
+  const float *d_w = w;
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+  if (!dev) {
+    char *p = (char *)d_out + al(ob);
+    d_xyz = (const double *)p;
+    d_w = w ? (const float *)(p + al(xb)) : nullptr;
+    if (e == cudaSuccess) e = cudaMemcpyAsync((void *)d_xyz, xyz, xb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && w) e = cudaMemcpyAsync((void *)d_w, w, wb, cudaMemcpyHostToDevice, st);
+  } else if (w) {
+    cudaPointerAttributes at;
+    const bool wd = cudaPointerGetAttributes(&at, w) == cudaSuccess &&
+                    (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    if (!wd) {
+      cudaFree(buf);
+      return fail(CUTE_E_INVALID, "xyz and w must both be device or both host memory");
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_rho, 0, m * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_out, 0, ob, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_cols, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+  // total weight for the mean density
+  double wsum = (double)n_obj;
+  if (w) {
+    std::vector<float> hw(n_obj);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hw.data(), d_w, wb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    wsum = 0;
+    for (float v : hw) wsum += v;
+  }
+  if (e == cudaSuccess && !(wsum > 0)) {
+    cudaFree(buf);
+    return fail(CUTE_E_INVALID, "total weight must be positive");
+  }
+  if (e == cudaSuccess) {
+    k_tsc<<<(unsigned)((n_obj + 255) / 256), 256, 0, st>>>(d_xyz, d_w, n_obj, ngrid, 1.0 / a, d_rho,
+                                                           d_bad, box_L);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    k_delta<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(d_rho, m, (double)m / wsum, d_delta);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const int zslab = std::max(1, ngrid / 8);
+    dim3 grid((unsigned)cols.size(), (unsigned)((maxw + 63) / 64), (unsigned)((ngrid + zslab - 1) / zslab));
+    const size_t smem = (size_t)(2 * ngrid + 64 + 8) * sizeof(float);
+    if (smem > 48 * 1024)
+      e = cudaFuncSetAttribute(k_lagcorr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      k_lagcorr<<<grid, kLagThreads, smem, st>>>(d_delta, ngrid, d_cols, zslab, d_out, maxw);
+      e = cudaGetLastError();
+    }
+  }
+  std::vector<double> C(cols.size() * (size_t)maxw);
+  int bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(C.data(), d_out, ob, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(CUTE_E_CUDA, cudaGetErrorString(e));
+  if (bad) return fail(CUTE_E_INVALID, "positions must lie in [0, L)");
+  // bin the lags: half-open bins on the squared separation a^2 |d|^2
+  std::vector<double> E2(nbins + 1), sum(nbins, 0.0), cnt(nbins, 0.0);
+  for (int b = 0; b <= nbins; b++) E2[b] = edges[b] * edges[b];
+  for (size_t c = 0; c < cols.size(); c++) {
+    const int4 col = cols[c];
+    for (int dx = col.z; dx <= col.w; dx++) {
+      const double r2 = ((double)dx * dx + (double)col.x * col.x + (double)col.y * col.y) * a * a;
+      if (r2 < E2[0] || r2 >= E2[nbins]) continue;
+      const int b = (int)(std::upper_bound(E2.begin(), E2.end(), r2) - E2.begin()) - 1;
+      sum[b] += C[c * maxw + (dx - col.z)];
+      cnt[b] += 1.0;
+    }
+  }
+  for (int b = 0; b < nbins; b++) {
+    xi_out[b] = cnt[b] > 0 ? sum[b] / (cnt[b] * (double)m) : NAN;
+    if (lags_out) lags_out[b] = cnt[b];
+  }
+  return CUTE_OK;
+}

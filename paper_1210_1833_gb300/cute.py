@@ -28,7 +28,7 @@ SYMBOLS = ["cute_ctx_create", "cute_ctx_destroy", "cute_last_error", "cute_sync"
            "cute_count_pairs_noalloc",
            "cute_last_stats", "cute_set_timing", "cute_set_launch", "cute_autotune",
            "cute_estimator", "cute_multipoles", "cute_sky_to_xyz", "cute_pixel_map",
-           "cute_pixel_centres", "cute_estimator_weighted",
+           "cute_pixel_centres", "cute_estimator_weighted", "cute_density_grid_xi",
            "cute_theta_to_chord", "cute_version"]
 
 
@@ -107,6 +107,7 @@ def lib():
             L.cute_sky_to_xyz.argtypes = [P, P, P, P, i64, P, P]
             L.cute_pixel_map.argtypes = [P, P, P, i64, i32, P]
             L.cute_pixel_centres.argtypes = [P, i32, P, i64, P]
+            L.cute_density_grid_xi.argtypes = [P, P, P, i64, f64, i32, P, i32, P, P]
             L.cute_estimator_weighted.argtypes = [ctypes.c_int, P, P, P, f64, f64, f64, f64,
                                                   i32, P]
             L.cute_version.restype = ctypes.c_char_p
@@ -403,6 +404,20 @@ class Context:
         _check(lib().cute_pixel_centres(self.handle, int(nside), _ptr(p), len(p), _ptr(out)),
                self.handle)
         return out
+
+    # -------------------------------------------------------------- density grid
+    def density_grid_xi(self, xyz, L, ngrid, edges, weights=None):
+        """xi(r) of a periodic box from a TSC density grid (Sec. 3.4.4).
+        Returns (xi, lag vectors per bin)."""
+        x = _xyz(xyz)
+        w = _w(weights)
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        xi = np.zeros(len(e) - 1)
+        lags = np.zeros(len(e) - 1)
+        _check(lib().cute_density_grid_xi(self.handle, _ptr(x), _ptr(w), int(x.shape[0]), float(L),
+                                          int(ngrid), _ptr(e), len(e) - 1, _ptr(xi), _ptr(lags)),
+               self.handle)
+        return xi, lags
 
     # -------------------------------------------------------------- misc
     def sync(self):

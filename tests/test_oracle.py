@@ -424,3 +424,50 @@ def test_weighted_estimators_reduce_to_unweighted():
     ls = oracle.xi_weighted("ls", DD, DR, RR, nd, nd, nr, nr)
     np.testing.assert_allclose(nat, oracle.xi_natural(DD, RR, nd, nr), rtol=1e-13)
     np.testing.assert_allclose(ls, oracle.xi_ls(DD, DR, RR, nd, nr), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- density grid
+def test_tsc_weights():
+    """TSC (Sec. 3.4.4): mass is conserved; a particle on a grid point gives
+    1/8, 3/4, 1/8 along each axis; one midway between two points gives 1/2,
+    1/2; a full lattice of particles on the grid points gives a flat field."""
+    L, n = 16.0, 16
+    rng = np.random.default_rng(86)
+    x = rng.uniform(0, L, (500, 3))
+    w = rng.uniform(0.5, 2, 500)
+    assert oracle.tsc_density(x, L, n, w).sum() == pytest.approx(w.sum(), rel=1e-13)
+    rho = oracle.tsc_density(np.array([[3.0, 5.0, 7.0]]), L, n)
+    line = rho[7, 5, 2:5]
+    np.testing.assert_allclose(line, np.array([1 / 8, 3 / 4, 1 / 8]) * 9 / 16, rtol=1e-15)
+    rho = oracle.tsc_density(np.array([[3.5, 5.0, 7.0]]), L, n)
+    np.testing.assert_allclose(rho[7, 5, 3:5], np.array([0.5, 0.5]) * 9 / 16, rtol=1e-15)
+    g = np.stack(np.meshgrid(*[np.arange(n) * 1.0] * 3, indexing="ij"), -1).reshape(-1, 3)
+    np.testing.assert_allclose(oracle.tsc_density(g, L, n), 1.0, rtol=1e-14)
+
+
+def test_lag_xi_of_a_plane_wave():
+    """delta = A cos(2 pi k.x / n) on a full-period grid has
+    <delta(x) delta(x + d)> = A^2/2 cos(2 pi k.d / n) exactly, so each bin
+    holds the mean of that over its lags."""
+    n, L, A = 16, 32.0, 0.7
+    k = np.array([1, 2, 3])
+    idx = np.indices((n, n, n))  # (z, y, x)
+    phase = 2 * np.pi * (k[0] * idx[2] + k[1] * idx[1] + k[2] * idx[0]) / n
+    delta = A * np.cos(phase)
+    edges = np.array([0.0, 3.0, 6.0, 9.5])
+    xi, lags = oracle.lag_xi(delta, L, edges)
+    a = L / n
+    R = int(np.floor(edges[-1] / a))
+    ref_s, ref_c = np.zeros(3), np.zeros(3)
+    for dz in range(0, R + 1):
+        for dy in range(-R, R + 1):
+            for dx in range(-R, R + 1):
+                if (dz == 0 and dy < 0) or (dz == 0 and dy == 0 and dx <= 0):
+                    continue
+                r = a * np.sqrt(dx * dx + dy * dy + dz * dz)
+                b = np.searchsorted(edges, r, side="right") - 1
+                if 0 <= b < 3:
+                    ref_s[b] += 0.5 * A * A * np.cos(2 * np.pi * (k[0] * dx + k[1] * dy + k[2] * dz) / n)
+                    ref_c[b] += 1
+    np.testing.assert_allclose(lags, ref_c)
+    np.testing.assert_allclose(xi, ref_s / ref_c, rtol=1e-12, atol=1e-14)
