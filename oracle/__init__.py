@@ -2,8 +2,10 @@
 
 Only tests/, ``__graft_entry__.smoke()`` and bench.py's ``cpu_baseline`` /
 ``--impl reference`` legs may import this package.  It shares no code with
-the CUDA library and never imports it.  The arithmetic lives in oracle.c
-(plain C, FP64, compiled with gcc); this module only marshals numpy arrays.
+the CUDA library and never imports it.  The pair counts, gradient rows and
+estimators live in oracle.c (plain C, FP64, compiled with gcc) and are
+marshalled here; the multipoles, comoving distances, HEALPix pixels, TSC
+density grid and lag correlations are plain numpy/scipy below.
 
 Every function cites the passage of Alonso (2012) it follows; see oracle.c
 for the canonical formulas and the readings taken where the paper is silent.

@@ -47,7 +47,7 @@ def test_density_grid_device_inputs_and_errors(ctx):
     edges = np.linspace(0, 30, 7)
     a, la = ctx.density_grid_xi(x, L, 32, edges)
     b, lb = ctx.density_grid_xi(torch.from_numpy(x).cuda(), L, 32, edges)
-    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-9)  # atomics add in any order
     with pytest.raises(cute.CuteError):
         ctx.density_grid_xi(x, L, 32, np.linspace(0, 60, 7))  # r_max >= L/2
     with pytest.raises(cute.CuteError):
