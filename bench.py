@@ -392,6 +392,10 @@ def run_extras(ctx, dev, reps=3, which="all"):
         out.update(_row_weighted(ctx, dev, timed))
     if which in ("all", "monopole"):
         out.update(_row_monopole(ctx, dev, timed))
+    if which in ("all", "density"):
+        out.update(_row_density(ctx, dev, timed))
+    if which in ("all", "pixel"):
+        out.update(_row_pixel(ctx, dev, timed))
     if which in ("angular",):  # minutes of work: only on request
         out.update(_row_angular(ctx, dev, timed))
     return out
@@ -474,6 +478,65 @@ def _row_monopole(ctx, dev, timed):
     return out
 
 
+def _row_density(ctx, dev, timed):
+    """Density-grid monopole of the c5 box (4M weighted objects, L = 2000):
+    TSC to 256^3, lag correlations to r = 150 (30 bins); one FP32 FMA per
+    (grid point, lag) pair is the algorithmic work."""
+    import torch
+    w = synthetic.c5_weighted()
+    x = torch.from_numpy(w.data).to(f"cuda:{dev}")
+    wt = torch.from_numpy(w.weights).to(f"cuda:{dev}")
+    ng = 256
+    res = {}
+    t = timed(lambda: res.__setitem__("v", ctx.density_grid_xi(x, w.L, ng, w.edges0, weights=wt)))
+    kms = ctx.stats()["kernel_ms"]  # the lag-correlation kernel alone
+    lags = float(res["v"][1].sum())
+    fma = lags * ng ** 3
+    pk, src = peaks()
+    peak = SM_COUNT * FP32_LANES_PER_SM * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    return {"density_grid_c5_256": {
+        "call_ms": t, "lag_kernel_ms": kms, "grid": ng, "lags": lags, "fma": fma,
+        "roofline": {"bound": "alu", "i_per_unit": 1, "unit_of_work": "grid point x lag",
+                     "achieved": fma / (kms / 1e3) / 1e12, "peak": peak, "unit": "Tinst/s",
+                     "frac": fma / (kms / 1e3) / 1e12 / peak,
+                     "note": "lag-correlation kernel (CUDA events); the call adds TSC, "
+                             "overdensity and binning"}}}
+
+
+def _row_pixel(ctx, dev, timed):
+    """w_pix: the c3 data (5M unit vectors) as a HEALPix nside 1024 map,
+    its occupied pixels correlated with their counts as weights."""
+    import torch
+    from paper_1210_1833_gb300 import cute
+    w = synthetic.c3_angular()
+    chord = cute.theta_to_chord(w.extra["theta_deg"])
+    x = torch.from_numpy(w.data).to(f"cuda:{dev}")
+    ns = 1024
+    state = {}
+
+    def make_map():
+        m = ctx.pixel_map(x, None, ns)
+        pix = torch.nonzero(m).view(-1)
+        state["cen"] = ctx.pixel_centres(ns, pix)
+        state["wt"] = m[pix].to(torch.float32)
+
+    t_map = timed(make_map)
+    P = ctx.upload(state["cen"], weights=state["wt"])
+    ctx.grid([P], [chord[-1]] * 3)
+    cnt = torch.zeros(len(chord) - 1, dtype=torch.int64, device=f"cuda:{dev}")
+    ws = torch.zeros(len(chord) - 1, dtype=torch.float64, device=f"cuda:{dev}")
+    t_cnt = timed(lambda: ctx.count("theta", P, None, chord, weighted=True, out=cnt,
+                                    wsum_out=ws, want_oor=False))
+    st = ctx.stats()
+    out = {"pixel_map_c3_nside1024": {
+        "objects": len(w.data), "pixels": int(state["cen"].shape[0]), "map_ms": t_map,
+        "weighted_count_ms": t_cnt, "kernel_ms": st["kernel_ms"],
+        "candidate_pairs": st["candidate_pairs"],
+        "roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3), "theta")}}
+    P.free()
+    return out
+
+
 def _row_angular(ctx, dev, timed):
     """c3: w(theta) DD, DR and RR of 5M data and 20M randoms on a 1000 sq-deg
     cap (64 log theta bins, binned on chords), each count timed once after a
@@ -542,7 +605,8 @@ def main():
                     help="skip the warm-up autotuning (cells per reach, launch shapes)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched / weighted / adjoint measurements")
-    ap.add_argument("--row", default="", choices=["", "batched", "weighted", "monopole", "angular"],
+    ap.add_argument("--row", default="",
+                    choices=["", "batched", "weighted", "monopole", "density", "pixel", "angular"],
                     help="profiling: run only this row (64-box batched sigma-pi, or the 4M "
                          "weighted forward and adjoint) and print it")
     args = ap.parse_args()

@@ -195,7 +195,7 @@ __device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2
                                             bool &n1) {
   const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
   const float2 v = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-  const float2 x = __fmul2_rn(v, make_float2(rsqrtf(v.x), rsqrtf(v.y)));  // NaN for v = 0
+  const float2 x = __fmul2_rn(v, make_float2(rsqrt_hw(v.x), rsqrt_hw(v.y)));  // NaN for v = 0
   float2 t = __ffma2_rn(x, make_float2(a.inv, a.inv), make_float2(a.cst, a.cst));
   t.x = fminf(fmaxf(t.x, a.tlo), a.thi);  // NaN -> tlo, the x = 0 side
   t.y = fminf(fmaxf(t.y, a.tlo), a.thi);
@@ -232,10 +232,10 @@ __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a
   const float2 sl = __ffma2_rn(sx, make_float2(2.0f, 2.0f), r2);
   const float2 l2 = __ffma2_rn(sx, make_float2(4.0f, 4.0f), __fadd2_rn(aq, r2));
   const float2 r2e = __fadd2_rn(r2, make_float2(1e-30f, 1e-30f));
-  const float2 rr = make_float2(rsqrtf(r2e.x), rsqrtf(r2e.y));
+  const float2 rr = make_float2(rsqrt_hw(r2e.x), rsqrt_hw(r2e.y));
   const float2 pl = __fmul2_rn(r2, l2);
   const float2 mu = __fmul2_rn(make_float2(fabsf(sl.x), fabsf(sl.y)),
-                               make_float2(rsqrtf(pl.x), rsqrtf(pl.y)));
+                               make_float2(rsqrt_hw(pl.x), rsqrt_hw(pl.y)));
   // NaN -> tlo on both axes
   const float2 t0 = clamp2(__ffma2_rn(__fmul2_rn(r2, rr), make_float2(a0.inv, a0.inv),
                                       make_float2(a0.cst, a0.cst)), a0.tlo, a0.thi);
@@ -266,7 +266,7 @@ __device__ __forceinline__ void sigpi_arith2(const AxisPlan &a0, const AxisPlan 
                                              bool &n1) {
   const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
   const float2 v0 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
-  const float2 x0 = __fmul2_rn(v0, make_float2(rsqrtf(v0.x), rsqrtf(v0.y)));  // NaN for v0 = 0
+  const float2 x0 = __fmul2_rn(v0, make_float2(rsqrt_hw(v0.x), rsqrt_hw(v0.y)));  // NaN for v0 = 0
   const float2 t0 = clamp2(__ffma2_rn(x0, make_float2(a0.inv, a0.inv), make_float2(a0.cst, a0.cst)),
                            a0.tlo, a0.thi);
   const float2 t1 = clamp2(__ffma2_rn(make_float2(fabsf(dz.x), fabsf(dz.y)),
@@ -362,6 +362,30 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
             if (MASK == 2 && gj == h.id[s]) { o[e] = zoff; nr[e] = false; }
             if (nr[e]) { o[e] = zoff; nmask |= 1u << k; }
             off[k] = o[e];
+          }
+        }
+      } else if constexpr (KIND == KMONO || KIND == KTHETA) {
+        // table binning: the squared separations of two pairs in packed FP32
+        // (the roundings of bin_pair's), then a lookup for each
+        const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
+                     qz = make_float2(q.z, q.z);
+#pragma unroll
+        for (int sp = 0; sp < HP / 2; sp++) {
+          const float2 dx = __fadd2_rn(qx, h.nx2[sp]), dy = __fadd2_rn(qy, h.ny2[sp]),
+                       dz = __fadd2_rn(qz, h.nz2[sp]);
+          const float2 v2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+#pragma unroll
+          for (int e = 0; e < 2; e++) {
+            const int s = 2 * sp + e, k = u * HP + s;
+            float v = e ? v2.y : v2.x;
+            const uint32_t ent = lut_get<M0>(lut, p.ax[0], v);
+            bool near;
+            uint32_t o = axis_resolve(band, p.ax[0], v, ent, st0, near) + zoff;
+            const int gj = gj0 + j + u;
+            if (MASK == 1 && !(gj > h.id[s])) { o = zoff; near = false; }
+            if (MASK == 2 && gj == h.id[s]) { o = zoff; near = false; }
+            if (near) { o = zoff; nmask |= 1u << k; }
+            off[k] = o;
           }
         }
       } else {

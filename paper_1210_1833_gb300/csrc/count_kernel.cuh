@@ -214,6 +214,18 @@ __device__ __forceinline__ uint32_t axis_resolve(uint32_t band, const AxisPlan &
 // signed distance of t - 1/2 to that integer (|h| = 1/2 on an edge).
 constexpr float kMagic = 12582912.0f;        // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
+// 1/sqrt(x) by the hardware approximation (PTX rsqrt.approx.ftz.f32), the
+// one rsqrtf() uses for normal inputs; rsqrtf() adds a rescaling for
+// subnormal ones, which never occur here (squared separations of FP32
+// coordinates are 0 or far above the subnormal range, and the guarded
+// operands carry a 1e-30 floor).  The error bounds use rsqrtf's documented
+// 2 ulp.
+__device__ __forceinline__ float rsqrt_hw(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Uniform edges (kArith): t = x * inv + cst, clamped to [tlo, thi] (a NaN
 // from x = v rsqrt(v) at v = 0 goes to tlo, the x = 0 side: bin 0 when
 // e_0 = 0, below range otherwise); tm = t + kMagic holds rint(t) in its low

@@ -16,12 +16,14 @@
 //   k_delta     rho -> FP32 delta;
 //   k_lagcorr   one CTA per (dy, dz) lag column, 64-lag dx window and z slab:
 //               the rows delta[:, y, z] and delta[:, y + dy, z + dz] (plus
-//               the dx halo) are staged in shared memory, and each thread
-//               sums 8 consecutive dx lags over every 32nd x; FP32 partial
-//               sums over 16 rows (n/2 terms) are folded into float-float
+//               the dx halo), 4 rows per barrier, are staged in shared
+//               memory; each thread sums 8 consecutive dx lags over its
+//               blocks of 8 consecutive x (register blocks of 8 x 8); FP32 partial sums
+//               over 16 rows (n/2 terms) are folded into float-float
 //               accumulators, so a lag sum carries about the FP32 rounding of
 //               those partials.
 #include "cute_internal.h"
+#include "count_kernel.cuh"  // cp.async helpers
 
 #include <algorithm>
 #include <cmath>
@@ -92,69 +94,109 @@ __device__ __forceinline__ void ff_acc(float &hi, float &lo, float v) {
   lo += err;
 }
 
-// One CTA: lag column (dy, dz) = cols[blockIdx.x], lags dx in
-// [dx0, dx0 + 64) of that column (blockIdx.y picks the 64-lag window), rows
-// z in [z0, z1) (blockIdx.z picks the slab).  out[col][dx - dxmin] += C.
+constexpr int kRowsPerStage = 4;  // row pairs staged in shared memory per barrier
+
+// One CTA of 32 G threads: lag column (dy, dz) = cols[blockIdx.x] with lags
+// dxmin..dxmax, window dx in [dx0, dx0 + 8 G) (dx0 = dxmin rounded down to a
+// multiple of 4, plus 8 G blockIdx.y), rows z in [z0, z1) (blockIdx.z).
+// Thread (lag group lg, x group xg) owns lags dx0 + 8 lg .. + 7 and the
+// blocks of 8 consecutive x starting at 8 xg + 256 j: per block it loads 8
+// delta_A and 16 delta_B values (float4 loads) for 64 FMAs.  Rows arrive by
+// 16-byte cp.async into two stage buffers, the next stage in flight while
+// the current one is summed.  out[col][dx - dxmin] += C(dx).
 __global__ void __launch_bounds__(kLagThreads) k_lagcorr(const float *__restrict__ delta, int n,
                                                          const int4 *__restrict__ cols,
                                                          int zslab, double *__restrict__ out,
                                                          int out_stride) {
-  extern __shared__ float sm[];  // rowA[n], rowB[n + 64 + 8]
+  extern __shared__ __align__(16) float sm[];  // [2 stages][kRowsPerStage][A n | B n + 64]
   const int4 col = cols[blockIdx.x];  // (dy, dz, dxmin, dxmax)
   const int dy = col.x, dz = col.y, dxmin = col.z, dxmax = col.w;
-  const int dx0 = dxmin + 64 * (int)blockIdx.y;
+  const int G = blockDim.x >> 5;
+  const int dx0 = (dxmin >= 0 ? dxmin & ~3 : -((-dxmin + 3) & ~3)) + 8 * G * (int)blockIdx.y;
   if (dx0 > dxmax) return;
   const int z0 = blockIdx.z * zslab, z1 = min(n, z0 + zslab);
-  float *rowA = sm;
-  float *rowB = sm + n;
-  const int lg = threadIdx.x >> 5;   // lag group: lags dx0 + 8 lg .. + 7
-  const int xs = threadIdx.x & 31;   // x segment
+  const int stride = 2 * n + 64;    // floats per staged row pair (a multiple of 32)
+  const int lg = threadIdx.x >> 5;  // lag group: lags dx0 + 8 lg .. + 7
+  const int xg = threadIdx.x & 31;  // x group: blocks of 8 x starting at 8 xg + 256 j
+  const bool live = dx0 + 8 * lg <= dxmax && dx0 + 8 * lg + 7 >= dxmin;
   float hi[kLagPer], lo[kLagPer], part[kLagPer];
 #pragma unroll
   for (int k = 0; k < kLagPer; k++) hi[k] = lo[k] = part[k] = 0.0f;
-  int rows = 0;
-  const int span = n + 64 + 8;
-  for (int z = z0; z < z1; z++) {
-    const int zb = wrapi(z + dz, n);
-    for (int y = 0; y < n; y++) {
-      const int yb = wrapi(y + dy, n);
+  const long long nrows = (long long)(z1 - z0) * n;  // rows (y, z) of the slab
+  const long long nstage = (nrows + kRowsPerStage - 1) / kRowsPerStage;
+  // stage s: rows r0 = s * kRowsPerStage .., into buffer s & 1
+  auto issue = [&](long long s) {
+    const int r0 = (int)(s * kRowsPerStage);  // < 2^20: 32-bit index arithmetic
+    const int nr = min(kRowsPerStage, (int)nrows - r0);
+    float *base = sm + (size_t)(s & 1) * kRowsPerStage * stride;
+    int z = z0 + r0 / n, y = r0 - (r0 / n) * n;
+    for (int q = 0; q < nr; q++, y++) {
+      if (y == n) {
+        y = 0;
+        z++;
+      }
+      const int zb = wrapi(z + dz, n), yb = wrapi(y + dy, n);
       const float *A = delta + ((long long)z * n + y) * n;
       const float *B = delta + ((long long)zb * n + yb) * n;
-      __syncthreads();
-      for (int i = threadIdx.x; i < n; i += kLagThreads) rowA[i] = A[i];
-      for (int i = threadIdx.x; i < span; i += kLagThreads) {
-        int xb = i + dx0;  // rowB[i] = delta[x = i + dx0 (wrapped)]
-        xb %= n;
-        if (xb < 0) xb += n;
-        rowB[i] = B[xb];
+      float *sa = base + q * stride, *sb = sa + n;
+      for (int c = threadIdx.x; c < (n >> 2); c += blockDim.x) cp_async16(sa + 4 * c, A + 4 * c);
+      // sb[i] = delta_B[(dx0 + i) mod n], i < n + 64, in 16-byte pieces
+      for (int c = threadIdx.x; c < ((n + 64) >> 2); c += blockDim.x) {
+        int xb = 4 * c + dx0;
+        while (xb < 0) xb += n;
+        while (xb >= n) xb -= n;
+        cp_async16(sb + 4 * c, B + xb);
       }
-      __syncthreads();
-      // thread: x = xs + 32 q, lags dx0 + 8 lg + k
-      for (int x = xs; x < n; x += 32) {
-        const float a = rowA[x];
-        const float *b = rowB + x + 8 * lg;  // delta[x + dx0 + 8 lg + k]
+    }
+    cp_async_commit();
+  };
+  int since = 0;
+  issue(0);
+  for (long long s = 0; s < nstage; s++) {
+    if (s + 1 < nstage) {
+      issue(s + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const int nr = (int)min((long long)kRowsPerStage, nrows - s * kRowsPerStage);
+    const float *base = sm + (size_t)(s & 1) * kRowsPerStage * stride;
+    for (int q = 0; q < nr && live; q++) {
+      const float *sa = base + q * stride, *sb = sa + n;
+      for (int xb0 = 8 * xg; xb0 < n; xb0 += 256) {
+        float a[8], b[16];
+        *(float4 *)&a[0] = *(const float4 *)&sa[xb0];
+        *(float4 *)&a[4] = *(const float4 *)&sa[xb0 + 4];
 #pragma unroll
-        for (int k = 0; k < kLagPer; k++) part[k] = fmaf(a, b[k], part[k]);
+        for (int v = 0; v < 4; v++) *(float4 *)&b[4 * v] = *(const float4 *)&sb[xb0 + 8 * lg + 4 * v];
+        // part[k] += sum_i delta_A[x + i] delta_B[x + i + dx0 + 8 lg + k]
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+#pragma unroll
+          for (int k = 0; k < kLagPer; k++) part[k] = fmaf(a[i], b[i + k], part[k]);
       }
-      if (++rows == 16) {
+      if (++since == 16) {  // fold the FP32 partials every 16 rows
 #pragma unroll
         for (int k = 0; k < kLagPer; k++) {
           ff_acc(hi[k], lo[k], part[k]);
           part[k] = 0.0f;
         }
-        rows = 0;
+        since = 0;
       }
     }
+    __syncthreads();  // the buffer is refilled by the next issue
   }
 #pragma unroll
   for (int k = 0; k < kLagPer; k++) ff_acc(hi[k], lo[k], part[k]);
-  // reduce the 32 x segments of each lag group (a warp) and add to out
+  // reduce the 32 x groups of each lag group (a warp) and add to out
 #pragma unroll
   for (int k = 0; k < kLagPer; k++) {
     double v = (double)hi[k] + (double)lo[k];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int dx = dx0 + 8 * lg + k;
-    if (xs == 0 && dx <= dxmax) atomicAdd(&out[(size_t)blockIdx.x * out_stride + (dx - dxmin)], v);
+    if (live && xg == 0 && dx >= dxmin && dx <= dxmax)
+      atomicAdd(&out[(size_t)blockIdx.x * out_stride + (dx - dxmin)], v);
   }
 }
 
@@ -271,12 +313,24 @@ extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, co
   }
   if (e == cudaSuccess) {
     const int zslab = std::max(1, ngrid / 8);
-    dim3 grid((unsigned)cols.size(), (unsigned)((maxw + 63) / 64), (unsigned)((ngrid + zslab - 1) / zslab));
-    const size_t smem = (size_t)(2 * ngrid + 64 + 8) * sizeof(float);
+    // 8 lags per warp, as many warps as the widest column needs (up to 8);
+    // windows start at dxmin rounded down to a multiple of 4 (16-byte rows)
+    const int wmax = maxw + 3;
+    const int G = std::min(8, (wmax + 7) / 8);
+    dim3 grid((unsigned)cols.size(), (unsigned)((wmax + 8 * G - 1) / (8 * G)),
+              (unsigned)((ngrid + zslab - 1) / zslab));
+    const size_t smem = (size_t)2 * kRowsPerStage * (2 * ngrid + 64) * sizeof(float);
     if (smem > 48 * 1024)
       e = cudaFuncSetAttribute(k_lagcorr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-      k_lagcorr<<<grid, kLagThreads, smem, st>>>(d_delta, ngrid, d_cols, zslab, d_out, maxw);
+      ctx->stats = cute_stats{};
+      cudaMemsetAsync(ctx->d_ticket, 0, kCounterWords * sizeof(unsigned long long), st);
+      ctx->stats.launches = 1;
+      ctx->stats.blocks = (int)(grid.x * grid.y * grid.z);
+      ctx->stats.warps_per_block = G;
+      if (ctx->timing) cudaEventRecord(ctx->ev0, st);
+      k_lagcorr<<<grid, 32 * G, smem, st>>>(d_delta, ngrid, d_cols, zslab, d_out, maxw);
+      if (ctx->timing) cudaEventRecord(ctx->ev1, st);
       e = cudaGetLastError();
     }
   }
