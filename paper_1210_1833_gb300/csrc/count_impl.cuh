@@ -144,51 +144,60 @@ static __device__ __noinline__ void flush_wsum(const KParams &p, const WarpSmem 
 }
 
 // ------------------------------------------------------------------ binning
-// Slot byte offset (slot * R * 4) of one candidate pair, and whether it lies
-// inside an edge's FP32 error band (then it must be re-tested in FP64).
-template <int KIND, int HP, int M0, int M1>
-__device__ __forceinline__ uint32_t bin_pair(const KParams &p, uint32_t lut, uint32_t band,
-                                             float dx, float dy, float dz, const Home<HP> &h,
-                                             int s, bool &near) {
+// Table binning (non-uniform edges): slot byte offset (slot * R * 4) of one
+// pair from its FP32 values -- the squared separation v (monopole, theta),
+// sigma^2 and pi^2, or r^2 and mu -- and whether it lies inside an edge's
+// FP32 error band (then it is re-tested in FP64).
+template <int KIND, int M0, int M1>
+__device__ __forceinline__ uint32_t table_slot(const KParams &p, uint32_t lut, uint32_t band,
+                                               float a, float b, bool &near) {
   const uint32_t stride0 = (uint32_t)p.slots1 * p.R * 4u, stride1 = (uint32_t)p.R * 4u;
-  uint32_t o;
-  // (uniform edges take the packed functions above: mono_arith2,
-  // sigpi_arith2, rmu_arith2)
   if (KIND == KMONO || KIND == KTHETA) {
-    float v0 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    const uint32_t e0 = lut_get<M0>(lut, p.ax[0], v0);
-    o = axis_resolve(band, p.ax[0], v0, e0, stride0, near);
+    const uint32_t e0 = lut_get<M0>(lut, p.ax[0], a);
+    return axis_resolve(band, p.ax[0], a, e0, stride0, near);
   } else if (KIND == KSIGPI) {
-    float v0 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
-    float v1 = __fmul_rn(dz, dz);
-    const uint32_t e0 = lut_get<M0>(lut, p.ax[0], v0);
-    const uint32_t e1 = lut_get<M1>(lut, p.ax[1], v1);
+    const uint32_t e0 = lut_get<M0>(lut, p.ax[0], a);
+    const uint32_t e1 = lut_get<M1>(lut, p.ax[1], b);
     bool n0, n1;
-    o = axis_resolve(band, p.ax[0], v0, e0, stride0, n0) +
-        axis_resolve(band, p.ax[1], v1, e1, stride1, n1);
+    const uint32_t o = axis_resolve(band, p.ax[0], a, e0, stride0, n0) +
+                       axis_resolve(band, p.ax[1], b, e1, stride1, n1);
     near = n0 || n1;
+    return o;
   } else {
-    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    const float sx = __fmaf_rn(dz, Home<HP>::get(h.az2, s),
-                               __fmaf_rn(dy, Home<HP>::get(h.ay2, s), __fmul_rn(dx, Home<HP>::get(h.ax2, s))));
-    const float sl = __fmaf_rn(2.0f, sx, r2);
-    const float l2 = __fmaf_rn(4.0f, sx, __fadd_rn(Home<HP>::get(h.aq2, s), r2));
-    float mu = __fmul_rn(fabsf(sl), rsqrtf(__fmul_rn(r2, l2)));
-    const uint32_t e0 = lut_get<M0>(lut, p.ax[0], r2);
-    const uint32_t e1 = lut_get<M1>(lut, p.ax[1], mu);
+    const uint32_t e0 = lut_get<M0>(lut, p.ax[0], a);
+    const uint32_t e1 = lut_get<M1>(lut, p.ax[1], b);
+    // the mu bound of the pair's r slot: class c scales the base by 2^c
     const float eps = __int_as_float(__float_as_int(p.mu_eps_base) +
                                      (int)(((e0 >> kClassShift) & 0xFu) << 23));
     bool n0, n1;
-    o = axis_resolve(band, p.ax[0], r2, e0, stride0, n0) +
-        mu_resolve(band, p.ax[1], mu, e1, stride1, eps, n1);
+    const uint32_t o = axis_resolve(band, p.ax[0], a, e0, stride0, n0) +
+                       mu_resolve(band, p.ax[1], b, e1, stride1, eps, n1);
     near = n0 || n1;
+    return o;
   }
-  return o;
 }
 
-// Monopole with uniform edges, two home objects at once with the packed
-// FP32 instructions of sm_100+ (element-wise IEEE round-to-nearest: each
-// element is rounded exactly as the scalar path rounds it).
+// (r, mu) values of two pairs in packed FP32: s = x_j - x_i, r^2 = s.s,
+// s.l = 2 s.x_i + r^2 and l.l = 4 |x_i|^2 + 4 s.x_i + r^2 with l = x_i + x_j
+// (x_i in the observer frame), mu = |s.l| / sqrt(r^2 l.l).
+struct Rmu2 {
+  float2 r2, sl, l2;
+};
+__device__ __forceinline__ Rmu2 rmu_values2(float2 qx, float2 qy, float2 qz, float2 nx, float2 ny,
+                                            float2 nz, float2 ax, float2 ay, float2 az,
+                                            float2 aq) {
+  const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
+  Rmu2 v;
+  v.r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+  const float2 sx = __ffma2_rn(dz, az, __ffma2_rn(dy, ay, __fmul2_rn(dx, ax)));
+  v.sl = __ffma2_rn(sx, make_float2(2.0f, 2.0f), v.r2);
+  v.l2 = __ffma2_rn(sx, make_float2(4.0f, 4.0f), __fadd2_rn(aq, v.r2));
+  return v;
+}
+
+// Uniform edges, two home objects at once with the packed FP32 instructions
+// of sm_100+ (element-wise IEEE round-to-nearest: each element is rounded
+// as the scalar formula would be).  Monopole (and theta on chords):
 __device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2 qy, float2 qz,
                                             float2 nx, float2 ny, float2 nz, uint32_t stride,
                                             uint32_t c, uint32_t &o0, uint32_t &o1, bool &n0,
@@ -208,16 +217,7 @@ __device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2
   o1 = __float_as_uint(tm.y) * stride + c;
 }
 
-// All pairs of the HP home objects of each lane with the cnt neighbours of
-// one shared-memory tile (cnt even; rows past the slice hold sentinels).
-// Two neighbours at a time: every binning of the 2 x HP pairs is issued
-// first, then the accumulation; pairs inside an edge's error band go to the
-// warp's FP64 queue (rare, so the enqueue sits behind one vote).
-// MASK: 1 -- only j > i counts (the home run against itself, unique pairs);
-//       2 -- every j != i counts (full-stencil adjoint of an auto count).
-// Two (r, mu) pairs at once with uniform edges on both axes: the packed
-// form of bin_pair's R_MU arithmetic branch, operation for operation (the
-// same roundings, hence the same bins and near flags).
+// Two (r, mu) pairs at once with uniform edges on both axes.
 __device__ __forceinline__ float2 clamp2(float2 t, float lo, float hi) {
   return make_float2(fminf(fmaxf(t.x, lo), hi), fminf(fmaxf(t.y, lo), hi));
 }
@@ -226,11 +226,8 @@ __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a
                                            float2 ax, float2 ay, float2 az, float2 aq,
                                            uint32_t stride0, uint32_t stride1, uint32_t c,
                                            uint32_t &o0, uint32_t &o1, bool &n0, bool &n1) {
-  const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
-  const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-  const float2 sx = __ffma2_rn(dz, az, __ffma2_rn(dy, ay, __fmul2_rn(dx, ax)));
-  const float2 sl = __ffma2_rn(sx, make_float2(2.0f, 2.0f), r2);
-  const float2 l2 = __ffma2_rn(sx, make_float2(4.0f, 4.0f), __fadd2_rn(aq, r2));
+  const Rmu2 v = rmu_values2(qx, qy, qz, nx, ny, nz, ax, ay, az, aq);
+  const float2 r2 = v.r2, sl = v.sl, l2 = v.l2;
   const float2 r2e = __fadd2_rn(r2, make_float2(1e-30f, 1e-30f));
   const float2 rr = make_float2(rsqrt_hw(r2e.x), rsqrt_hw(r2e.y));
   const float2 pl = __fmul2_rn(r2, l2);
@@ -256,9 +253,8 @@ __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a
   o1 = __float_as_uint(tm0.y) * stride0 + (__float_as_uint(tm1.y) * stride1 + c);
 }
 
-// Two (sigma, pi) pairs at once with uniform edges on both axes (the packed
-// form of bin_pair's SIGMA_PI arithmetic branch; the near test compares |h|
-// with 1/2 - thr_b rounded down, as the monopole's).
+// Two (sigma, pi) pairs at once with uniform edges on both axes (the near
+// test compares |h| with 1/2 - thr_b rounded down, as the monopole's).
 __device__ __forceinline__ void sigpi_arith2(const AxisPlan &a0, const AxisPlan &a1, float2 qx,
                                              float2 qy, float2 qz, float2 nx, float2 ny,
                                              float2 nz, uint32_t stride0, uint32_t stride1,
@@ -283,6 +279,13 @@ __device__ __forceinline__ void sigpi_arith2(const AxisPlan &a0, const AxisPlan 
   o1 = __float_as_uint(tm0.y) * stride0 + (__float_as_uint(tm1.y) * stride1 + c);
 }
 
+// All pairs of the HP home objects of each lane with the cnt neighbours of
+// one shared-memory tile (cnt even; rows past the slice hold sentinels).
+// Two neighbours at a time: every binning of the 2 x HP pairs is issued
+// first, then the accumulation; pairs inside an edge's error band go to the
+// warp's FP64 queue (rare, so the enqueue sits behind one vote).
+// MASK: 1 -- only j > i counts (the home run against itself, unique pairs);
+//       2 -- every j != i counts (full-stencil adjoint of an auto count).
 template <int KIND, int HP, int M0, int M1, int MASK, int ACC>
 __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint32_t band,
                                            const PairDev &pd, const WarpSmem &w, uint32_t tile,
@@ -364,45 +367,44 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
             off[k] = o[e];
           }
         }
-      } else if constexpr (KIND == KMONO || KIND == KTHETA) {
-        // table binning: the squared separations of two pairs in packed FP32
-        // (the roundings of bin_pair's), then a lookup for each
+      } else {
+        // table binning: the values of two pairs in packed FP32, then a
+        // lookup for each
         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
                      qz = make_float2(q.z, q.z);
 #pragma unroll
         for (int sp = 0; sp < HP / 2; sp++) {
-          const float2 dx = __fadd2_rn(qx, h.nx2[sp]), dy = __fadd2_rn(qy, h.ny2[sp]),
-                       dz = __fadd2_rn(qz, h.nz2[sp]);
-          const float2 v2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+          float2 va, vb;
+          if constexpr (KIND == KRMU) {
+            const Rmu2 v = rmu_values2(qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], h.ax2[sp],
+                                       h.ay2[sp], h.az2[sp], h.aq2[sp]);
+            const float2 pl = __fmul2_rn(v.r2, v.l2);
+            va = v.r2;
+            vb = __fmul2_rn(make_float2(fabsf(v.sl.x), fabsf(v.sl.y)),
+                            make_float2(rsqrt_hw(pl.x), rsqrt_hw(pl.y)));
+          } else {
+            const float2 dx = __fadd2_rn(qx, h.nx2[sp]), dy = __fadd2_rn(qy, h.ny2[sp]),
+                         dz = __fadd2_rn(qz, h.nz2[sp]);
+            if constexpr (KIND == KSIGPI) {
+              va = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
+              vb = __fmul2_rn(dz, dz);
+            } else {
+              va = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+              vb = va;
+            }
+          }
 #pragma unroll
           for (int e = 0; e < 2; e++) {
             const int s = 2 * sp + e, k = u * HP + s;
-            float v = e ? v2.y : v2.x;
-            const uint32_t ent = lut_get<M0>(lut, p.ax[0], v);
             bool near;
-            uint32_t o = axis_resolve(band, p.ax[0], v, ent, st0, near) + zoff;
+            uint32_t o = table_slot<KIND, M0, M1>(p, lut, band, e ? va.y : va.x,
+                                                  e ? vb.y : vb.x, near) + zoff;
             const int gj = gj0 + j + u;
-            if (MASK == 1 && !(gj > h.id[s])) { o = zoff; near = false; }
-            if (MASK == 2 && gj == h.id[s]) { o = zoff; near = false; }
+            if (MASK == 1 && !(gj > h.id[s])) { o = zoff; near = false; }  // not a pair of this item
+            if (MASK == 2 && gj == h.id[s]) { o = zoff; near = false; }    // no self pair
             if (near) { o = zoff; nmask |= 1u << k; }
             off[k] = o;
           }
-        }
-      } else {
-#pragma unroll
-        for (int s = 0; s < HP; s++) {
-          const int k = u * HP + s;
-          // x_j - x_i as x_j + (-x_i): the same rounding
-          const float dx = __fadd_rn(q.x, Home<HP>::get(h.nx2, s));
-          const float dy = __fadd_rn(q.y, Home<HP>::get(h.ny2, s));
-          const float dz = __fadd_rn(q.z, Home<HP>::get(h.nz2, s));
-          bool near;
-          uint32_t o = bin_pair<KIND, HP, M0, M1>(p, lut, band, dx, dy, dz, h, s, near) + zoff;
-          const int gj = gj0 + j + u;
-          if (MASK == 1 && !(gj > h.id[s])) { o = zoff; near = false; }   // not a pair of this item
-          if (MASK == 2 && gj == h.id[s]) { o = zoff; near = false; }     // no self pair
-          if (near) { o = zoff; nmask |= 1u << k; }
-          off[k] = o;
         }
       }
     }

@@ -216,3 +216,18 @@ def test_invalid_requests_fail_cleanly(ctx):
         ctx.upload(np.array([[0.0, np.nan, 1.0]]))
     a.free()
     ctx.sync()
+
+
+def test_rmu_duplicates_and_log_bins(ctx):
+    """(r, mu) on an open catalog with exact duplicates (separation 0: r bin
+    0, mu bin 0) and on log-spaced r edges (table binning for r)."""
+    rng = np.random.default_rng(108)
+    x = rng.uniform(500, 700, size=(4000, 3))
+    x[3000:3300] = x[3300:3600]
+    e1 = np.linspace(0, 1, 9)
+    e0 = np.linspace(0, 30, 7)
+    _assert_same(gpu_count(ctx, "rmu", x, None, e0, e1), oracle_count("rmu", x, None, e0, e1))
+    elog = np.concatenate([[0.0], np.geomspace(0.5, 30, 8)])
+    _assert_same(gpu_count(ctx, "rmu", x, None, elog, e1), oracle_count("rmu", x, None, elog, e1))
+    _assert_same(gpu_count(ctx, "sigpi", x, None, elog, np.linspace(0, 20, 5)),
+                 oracle_count("sigpi", x, None, elog, np.linspace(0, 20, 5)))
