@@ -467,11 +467,14 @@ def _row_monopole(ctx, dev, timed):
         ctx.grid([A], [w.edges0[-1]] * 3)
         ctx.count("mono", A, None, w.edges0, out=cnt, want_oor=False)
 
+    # a small count: let the autotuner pick home objects, warps and slice
+    ctx.grid([A], [w.edges0[-1]] * 3)
+    tuned = ctx.autotune("mono", [(A, None)], w.edges0, tune_cells=False, max_items=1 << 30)
     t = timed(step)
     st = ctx.stats()
     out = {"monopole_c1_20k": {
         "step_ms": t, "kernel_ms": st["kernel_ms"], "candidate_pairs": st["candidate_pairs"],
-        "binned_pairs": int(cnt.sum()),
+        "binned_pairs": int(cnt.sum()), "tuned": tuned,
         "roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
                                   "mono_periodic")}}
     A.free()

@@ -177,7 +177,8 @@ __device__ __forceinline__ uint32_t table_slot(const KParams &p, uint32_t lut, u
   }
 }
 
-// (r, mu) values of two pairs in packed FP32: s = x_j - x_i, r^2 = s.s,
+// (r, mu) values of two pairs in packed FP32: s = x_j - x_i, r^2 = s.s
+// (floored at 1e-30, so 1/r and mu stay finite),
 // s.l = 2 s.x_i + r^2 and l.l = 4 |x_i|^2 + 4 s.x_i + r^2 with l = x_i + x_j
 // (x_i in the observer frame), mu = |s.l| / sqrt(r^2 l.l).
 struct Rmu2 {
@@ -188,7 +189,7 @@ __device__ __forceinline__ Rmu2 rmu_values2(float2 qx, float2 qy, float2 qz, flo
                                             float2 aq) {
   const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
   Rmu2 v;
-  v.r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+  v.r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, make_float2(kVFloor, kVFloor))));
   const float2 sx = __ffma2_rn(dz, az, __ffma2_rn(dy, ay, __fmul2_rn(dx, ax)));
   v.sl = __ffma2_rn(sx, make_float2(2.0f, 2.0f), v.r2);
   v.l2 = __ffma2_rn(sx, make_float2(4.0f, 4.0f), __fadd2_rn(aq, v.r2));
@@ -203,11 +204,13 @@ __device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2
                                             uint32_t c, uint32_t &o0, uint32_t &o1, bool &n0,
                                             bool &n1) {
   const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
-  const float2 v = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-  const float2 x = __fmul2_rn(v, make_float2(rsqrt_hw(v.x), rsqrt_hw(v.y)));  // NaN for v = 0
+  // v >= 1e-30 (a floor far below any nonzero squared separation of FP32
+  // coordinates), so x = v / sqrt(v) is finite and t >= -1/2
+  const float2 v = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, make_float2(kVFloor, kVFloor))));
+  const float2 x = __fmul2_rn(v, make_float2(rsqrt_hw(v.x), rsqrt_hw(v.y)));
   float2 t = __ffma2_rn(x, make_float2(a.inv, a.inv), make_float2(a.cst, a.cst));
-  t.x = fminf(fmaxf(t.x, a.tlo), a.thi);  // NaN -> tlo, the x = 0 side
-  t.y = fminf(fmaxf(t.y, a.tlo), a.thi);
+  t.x = fminf(t.x, a.thi);  // above the last edge (and far sentinels): the top slot
+  t.y = fminf(t.y, a.thi);
   const float2 tm = __fadd2_rn(t, make_float2(kMagic, kMagic));
   const float2 fl = __fadd2_rn(tm, make_float2(-kMagic, -kMagic));
   const float2 h = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), t);  // t - floor, exact
@@ -218,8 +221,8 @@ __device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2
 }
 
 // Two (r, mu) pairs at once with uniform edges on both axes.
-__device__ __forceinline__ float2 clamp2(float2 t, float lo, float hi) {
-  return make_float2(fminf(fmaxf(t.x, lo), hi), fminf(fmaxf(t.y, lo), hi));
+__device__ __forceinline__ float2 clampt(float2 t, float hi) {
+  return make_float2(fminf(t.x, hi), fminf(t.y, hi));
 }
 __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a1, float2 qx,
                                            float2 qy, float2 qz, float2 nx, float2 ny, float2 nz,
@@ -228,16 +231,15 @@ __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a
                                            uint32_t &o0, uint32_t &o1, bool &n0, bool &n1) {
   const Rmu2 v = rmu_values2(qx, qy, qz, nx, ny, nz, ax, ay, az, aq);
   const float2 r2 = v.r2, sl = v.sl, l2 = v.l2;
-  const float2 r2e = __fadd2_rn(r2, make_float2(1e-30f, 1e-30f));
-  const float2 rr = make_float2(rsqrt_hw(r2e.x), rsqrt_hw(r2e.y));
-  const float2 pl = __fmul2_rn(r2, l2);
+  const float2 rr = make_float2(rsqrt_hw(r2.x), rsqrt_hw(r2.y));
+  const float2 pl = __fmul2_rn(r2, l2);  // > 0 (or +inf for padded slots): mu finite
   const float2 mu = __fmul2_rn(make_float2(fabsf(sl.x), fabsf(sl.y)),
                                make_float2(rsqrt_hw(pl.x), rsqrt_hw(pl.y)));
-  // NaN -> tlo on both axes
-  const float2 t0 = clamp2(__ffma2_rn(__fmul2_rn(r2, rr), make_float2(a0.inv, a0.inv),
-                                      make_float2(a0.cst, a0.cst)), a0.tlo, a0.thi);
-  const float2 t1 = clamp2(__ffma2_rn(mu, make_float2(a1.inv, a1.inv), make_float2(a1.cst, a1.cst)),
-                           a1.tlo, a1.thi);
+  // t >= -1/2 on both axes (e_0 = 0); clamped above only
+  const float2 t0 = clampt(__ffma2_rn(__fmul2_rn(r2, rr), make_float2(a0.inv, a0.inv),
+                                      make_float2(a0.cst, a0.cst)), a0.thi);
+  const float2 t1 = clampt(__ffma2_rn(mu, make_float2(a1.inv, a1.inv), make_float2(a1.cst, a1.cst)),
+                           a1.thi);
   const float2 m2 = make_float2(kMagic, kMagic), nm2 = make_float2(-kMagic, -kMagic),
                neg = make_float2(-1.0f, -1.0f);
   const float2 tm0 = __fadd2_rn(t0, m2), tm1 = __fadd2_rn(t1, m2);
@@ -261,13 +263,13 @@ __device__ __forceinline__ void sigpi_arith2(const AxisPlan &a0, const AxisPlan 
                                              uint32_t c, uint32_t &o0, uint32_t &o1, bool &n0,
                                              bool &n1) {
   const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
-  const float2 v0 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
-  const float2 x0 = __fmul2_rn(v0, make_float2(rsqrt_hw(v0.x), rsqrt_hw(v0.y)));  // NaN for v0 = 0
-  const float2 t0 = clamp2(__ffma2_rn(x0, make_float2(a0.inv, a0.inv), make_float2(a0.cst, a0.cst)),
-                           a0.tlo, a0.thi);
-  const float2 t1 = clamp2(__ffma2_rn(make_float2(fabsf(dz.x), fabsf(dz.y)),
+  const float2 v0 = __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, make_float2(kVFloor, kVFloor)));
+  const float2 x0 = __fmul2_rn(v0, make_float2(rsqrt_hw(v0.x), rsqrt_hw(v0.y)));
+  const float2 t0 = clampt(__ffma2_rn(x0, make_float2(a0.inv, a0.inv), make_float2(a0.cst, a0.cst)),
+                           a0.thi);
+  const float2 t1 = clampt(__ffma2_rn(make_float2(fabsf(dz.x), fabsf(dz.y)),
                                       make_float2(a1.inv, a1.inv), make_float2(a1.cst, a1.cst)),
-                           a1.tlo, a1.thi);
+                           a1.thi);
   const float2 m2 = make_float2(kMagic, kMagic), nm2 = make_float2(-kMagic, -kMagic),
                neg = make_float2(-1.0f, -1.0f);
   const float2 tm0 = __fadd2_rn(t0, m2), tm1 = __fadd2_rn(t1, m2);
@@ -630,11 +632,11 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
         Home<HP>::put(h.nz2, s, -kHomeFar);
         h.w[s] = 0.0f;
         h.id[s] = 0x7fffffff;
-        if (KIND == KRMU) {
-          Home<HP>::put(h.ax2, s, kHomeFar);
-          Home<HP>::put(h.ay2, s, kHomeFar);
-          Home<HP>::put(h.az2, s, kHomeFar);
-          Home<HP>::put(h.aq2, s, kHomeFar);
+        if (KIND == KRMU) {  // x_i = 0 in the observer frame: l = s, mu = 1
+          Home<HP>::put(h.ax2, s, 0.0f);
+          Home<HP>::put(h.ay2, s, 0.0f);
+          Home<HP>::put(h.az2, s, 0.0f);
+          Home<HP>::put(h.aq2, s, 0.0f);
         }
       }
     }

@@ -29,8 +29,14 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // FP32 sentinels for padded home slots and tile rows: far from everything
 // and from each other, so every pair involving one is out of range.
-constexpr float kHomeFar = 3.0e18f;
-constexpr float kNbrFar = -1.0e18f;
+// The grid frame holds |x| <= 1e8 (checked when the grid is built; image
+// shifts of a periodic box add at most 2e8), so every pair with a sentinel is
+// more than 5e8 apart: beyond any reach, with squared
+// separations and (r, mu) products that stay finite in FP32, and (r, mu)
+// sentinels give mu = 1 (see the padded home slots), which the top clamp
+// keeps away from every edge band.
+constexpr float kHomeFar = 1.0e9f;
+constexpr float kNbrFar = -1.0e9f;
 
 // ------------------------------------------------------------------ work entries
 // One contiguous range [j0, j1) of catalog B that a home chunk meets, with
@@ -209,9 +215,7 @@ __device__ __forceinline__ uint32_t axis_resolve(uint32_t band, const AxisPlan &
   return above ? off + stride : off;
 }
 
-// Uniform edges: t - 1/2 = x * inv + cst clamped to [tlo, thi]; returns the
-// rounded value tm = 1.5 * 2^23 + floor(t) (its bits hold the bin) and h, the
-// signed distance of t - 1/2 to that integer (|h| = 1/2 on an edge).
+constexpr float kVFloor = 1e-30f;            // floor of squared separations (finite 1/r)
 constexpr float kMagic = 12582912.0f;        // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
 // 1/sqrt(x) by the hardware approximation (PTX rsqrt.approx.ftz.f32), the
@@ -226,12 +230,13 @@ __device__ __forceinline__ float rsqrt_hw(float x) {
   return y;
 }
 
-// Uniform edges (kArith): t = x * inv + cst, clamped to [tlo, thi] (a NaN
-// from x = v rsqrt(v) at v = 0 goes to tlo, the x = 0 side: bin 0 when
-// e_0 = 0, below range otherwise); tm = t + kMagic holds rint(t) in its low
-// mantissa bits, so the slot (bin + 1) is bits(tm) - kMagicBits + 1, and
-// h = t - (tm - kMagic) is exact.  mono_arith2 / sigpi_arith2 / rmu_arith2
-// (count_impl.cuh) apply this to two pairs at once.
+// Uniform edges from 0 (kArith): t = x * inv + cst >= -1/2 for x >= 0 (the
+// squared separations carry the kVFloor floor, so x and mu are finite),
+// clamped from above to thi (pairs beyond the last edge, padded slots);
+// tm = t + kMagic holds rint(t) in its low mantissa bits, so the slot
+// (bin + 1) is bits(tm) - kMagicBits + 1, and h = t - (tm - kMagic) is exact.
+// mono_arith2 / sigpi_arith2 / rmu_arith2 (count_impl.cuh) apply this to two
+// pairs at once.
 
 // The same for mu: the band holds the edge, the bound comes from the r slot.
 __device__ __forceinline__ uint32_t mu_resolve(uint32_t band, const AxisPlan &a, float mu,

@@ -360,6 +360,11 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
   }
   long long ncell = (long long)g.nc[0] * g.nc[1] * g.nc[2];
   if (ncell > (1LL << 28)) return fail(ctx, CUTE_E_UNSUPPORTED, "too many cells");
+  // the counting kernels' padding sentinels sit at 1e9 in the FP32 grid
+  // frame (offsets from the grid centre): real objects must stay within 1e8
+  for (int k = 0; k < 3; k++)
+    if (!(g.xmax[k] <= 1e8))
+      return fail(ctx, CUTE_E_UNSUPPORTED, "catalog extent beyond 2e8 on an axis");
   g.id = ctx->next_geom++;
   g.version = ++ctx->version_counter;
   g.kreq = kreq;

@@ -260,6 +260,9 @@ static bool make_arith(const double *e, int n, const AxisErr &err, double eta0, 
                        bool is_mu, bool lin, AxisPlan &p) {
   double delta;
   if (!uniform_edges(e, n, delta)) return false;
+  // the kernels clamp t only from above: with x >= 0 and e_0 = 0, t >= -1/2
+  // (slot >= 1) holds without a lower clamp; other edges take the tables
+  if (e[0] != 0.0) return false;
   const double inv = 1.0 / delta, c = -e[0] / delta;
   double db = 0;
   for (int k = 0; k <= n; k++) {
