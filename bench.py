@@ -575,6 +575,7 @@ def _row_weighted(ctx, dev, timed):
     cnt = torch.zeros(len(e) - 1, dtype=torch.int64, device=f"cuda:{dev}")
     ws = torch.zeros(len(e) - 1, dtype=torch.float64, device=f"cuda:{dev}")
     G = torch.from_numpy(w.extra["G"]).to(f"cuda:{dev}")
+    tuned = ctx.autotune("mono", [(A, None)], e, tune_cells=False, max_items=30000)
     t_plain = timed(lambda: ctx.count("mono", A, None, e, out=cnt, want_oor=False))
     st = ctx.stats()
     t_w = timed(lambda: ctx.count("mono", A, None, e, weighted=True, out=cnt, wsum_out=ws,
@@ -586,7 +587,7 @@ def _row_weighted(ctx, dev, timed):
         "weighted_over_plain": t_w / t_plain, "adjoint_over_plain": t_adj / t_plain,
         "binned_pairs": binned, "plain_binned_pairs_per_s": binned / (t_plain / 1e3),
         "plain_candidate_pairs": st["candidate_pairs"], "plain_kernel_ms": st["kernel_ms"],
-        "plain_home_per_lane": st["home_per_lane"],
+        "plain_home_per_lane": st["home_per_lane"], "plain_tuned": tuned,
         "plain_candidate_pairs_per_s": st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
         "plain_roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
                                         "mono_periodic")}
