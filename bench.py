@@ -182,25 +182,34 @@ def run_reference(args, w, rank, world):
     if rank != 0:
         return
     import oracle  # noqa: F401
-    vals = []
+    vals, times = [], []
     desc = ""
     thr = 0
     for _ in range(args.warmup):
         cpu_oracle_rate(w, target_s=3.0)
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         v, thr, desc = cpu_oracle_rate(w, target_s=8.0)
+        times.append((time.perf_counter() - t0) * 1e3)
         vals.append(v)
     v = float(np.median(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": float(np.median(times)), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "kind": w.kind},
+            "config": dict(workload_config(w), sample="each step a bounded DR sample (below)"),
             "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": thr, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def workload_config(w):
+    """The workload part of the JSON config, shared by both arms."""
+    return {"workload": w.name, "kind": w.kind, "n_data": len(w.data), "n_randoms": len(w.randoms),
+            "bins": [len(w.edges0) - 1, len(w.edges1) - 1], "counts": ["DD", "DR", "RR"],
+            "estimator": "landy-szalay"}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -331,9 +340,7 @@ def run_gpu(args, w, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": w.name, "kind": "rmu", "n_data": nd, "n_randoms": nr,
-                   "bins": [len(w.edges0) - 1, len(w.edges1) - 1], "counts": ["DD", "DR", "RR"],
-                   "estimator": "landy-szalay", "l2": "flushed between steps (256 MB write)",
+        "config": {**workload_config(w), "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single",
                    "cells_per_reach": args.cpr, "autotuned": tuning or None},
         "pairs": {"candidate_per_step": cand_per_step,

@@ -14,12 +14,12 @@
 // Kernels:
 //   k_tsc       27 FP64 atomic adds per object into the grid;
 //   k_delta     rho -> FP32 delta;
-//   k_lagcorr   one CTA per (dy, dz) lag column, 64-lag dx window and z slab:
-//               the rows delta[:, y, z] and delta[:, y + dy, z + dz] (plus
-//               the dx halo), 4 rows per barrier, are staged in shared
-//               memory; each thread sums 8 consecutive dx lags over its
-//               blocks of 8 consecutive x (register blocks of 8 x 8); FP32 partial sums
-//               over 16 rows (n/2 terms) are folded into float-float
+//   k_lagcorr   one CTA per (dy, dz) lag column, lag window and z slab: the
+//               rows delta[:, y, z] and delta[:, y + dy, z + dz] (plus the dx
+//               halo) are staged in skewed shared memory by cp.async, two
+//               stages in flight; each lane sums 16 consecutive dx lags over
+//               its blocks of 16 consecutive x (register blocks of 16 x 16);
+//               FP32 partial sums over 8 rows are folded into float-float
 //               accumulators, so a lag sum carries about the FP32 rounding of
 //               those partials.
 #include "cute_internal.h"
@@ -35,8 +35,6 @@ namespace cute {
 namespace {
 
 constexpr int kMaxGrid = 1024;
-constexpr int kLagThreads = 256;  // 32 x-segments x 8 lag groups
-constexpr int kLagPer = 8;        // lags per thread
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
@@ -94,41 +92,47 @@ __device__ __forceinline__ void ff_acc(float &hi, float &lo, float v) {
   lo += err;
 }
 
-constexpr int kRowsPerStage = 4;  // row pairs staged in shared memory per barrier
+// Shared-memory rows are skewed by 4 floats after every 16 (index i lives at
+// i + 4 (i / 16)): 16-float blocks read by consecutive lanes then fall on
+// distinct banks.
+__device__ __forceinline__ int skew(int i) { return i + 4 * (i >> 4); }
 
-// One CTA of 32 G threads: lag column (dy, dz) = cols[blockIdx.x] with lags
-// dxmin..dxmax, window dx in [dx0, dx0 + 8 G) (dx0 = dxmin rounded down to a
-// multiple of 4, plus 8 G blockIdx.y), rows z in [z0, z1) (blockIdx.z).
-// Thread (lag group lg, x group xg) owns lags dx0 + 8 lg .. + 7 and the
-// blocks of 8 consecutive x starting at 8 xg + 256 j: per block it loads 8
-// delta_A and 16 delta_B values (float4 loads) for 64 FMAs.  Rows arrive by
-// 16-byte cp.async into two stage buffers, the next stage in flight while
-// the current one is summed.  out[col][dx - dxmin] += C(dx).
-__global__ void __launch_bounds__(kLagThreads) k_lagcorr(const float *__restrict__ delta, int n,
-                                                         const int4 *__restrict__ cols,
-                                                         int zslab, double *__restrict__ out,
-                                                         int out_stride) {
-  extern __shared__ __align__(16) float sm[];  // [2 stages][kRowsPerStage][A n | B n + 64]
+// One CTA of G warps: lag column (dy, dz) = cols[blockIdx.x] with lags
+// dxmin..dxmax, window dx in [dx0, dx0 + 16 G) (dx0 = dxmin rounded down to
+// a multiple of 4, plus 16 G blockIdx.y), rows z in [z0, z1) (blockIdx.z).
+// Warp g owns lags dx0 + 16 g .. + 15; its lanes split each row into blocks
+// of 16 consecutive x (lpr lanes per row, 32 / lpr rows side by side).  Per
+// block a lane loads 16 delta_A and 32 delta_B values (float4 loads) for
+// 256 FMAs.  Rows arrive by 16-byte cp.async into two stage buffers, the
+// next stage in flight while the current one is summed; FP32 partials are
+// folded into float-float accumulators every 8 rows.
+__global__ void __launch_bounds__(128, 4) k_lagcorr(const float *__restrict__ delta, int n,
+                                                    const int4 *__restrict__ cols, int zslab,
+                                                    double *__restrict__ out, int out_stride) {
+  extern __shared__ __align__(16) float sm[];
   const int4 col = cols[blockIdx.x];  // (dy, dz, dxmin, dxmax)
   const int dy = col.x, dz = col.y, dxmin = col.z, dxmax = col.w;
   const int G = blockDim.x >> 5;
-  const int dx0 = (dxmin >= 0 ? dxmin & ~3 : -((-dxmin + 3) & ~3)) + 8 * G * (int)blockIdx.y;
+  const int dx0 = (dxmin >= 0 ? dxmin & ~3 : -((-dxmin + 3) & ~3)) + 16 * G * (int)blockIdx.y;
   if (dx0 > dxmax) return;
   const int z0 = blockIdx.z * zslab, z1 = min(n, z0 + zslab);
-  const int stride = 2 * n + 64;    // floats per staged row pair (a multiple of 32)
-  const int lg = threadIdx.x >> 5;  // lag group: lags dx0 + 8 lg .. + 7
-  const int xg = threadIdx.x & 31;  // x group: blocks of 8 x starting at 8 xg + 256 j
-  const bool live = dx0 + 8 * lg <= dxmax && dx0 + 8 * lg + 7 >= dxmin;
-  float hi[kLagPer], lo[kLagPer], part[kLagPer];
+  const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lpr = min(32, n >> 4);            // lanes per row
+  const int rpw = 32 / lpr;                   // rows side by side in a warp
+  const int srows = 4 * rpw;                  // rows per stage
+  const int sa_len = skew(n), sb_len = skew(n + 64);
+  const int stride = sa_len + sb_len;         // floats per staged row pair
+  const int rs = lane / lpr, xl = lane % lpr;
+  const bool live = dx0 + 16 * g <= dxmax && dx0 + 16 * g + 15 >= dxmin;
+  float hi[16], lo[16], part[16];
 #pragma unroll
-  for (int k = 0; k < kLagPer; k++) hi[k] = lo[k] = part[k] = 0.0f;
-  const long long nrows = (long long)(z1 - z0) * n;  // rows (y, z) of the slab
-  const long long nstage = (nrows + kRowsPerStage - 1) / kRowsPerStage;
-  // stage s: rows r0 = s * kRowsPerStage .., into buffer s & 1
-  auto issue = [&](long long s) {
-    const int r0 = (int)(s * kRowsPerStage);  // < 2^20: 32-bit index arithmetic
-    const int nr = min(kRowsPerStage, (int)nrows - r0);
-    float *base = sm + (size_t)(s & 1) * kRowsPerStage * stride;
+  for (int k = 0; k < 16; k++) hi[k] = lo[k] = part[k] = 0.0f;
+  const int nrows = (z1 - z0) * n;
+  const int nstage = (nrows + srows - 1) / srows;
+  auto issue = [&](int s) {
+    const int r0 = s * srows;
+    const int nr = min(srows, nrows - r0);
+    float *base = sm + (size_t)(s & 1) * srows * stride;
     int z = z0 + r0 / n, y = r0 - (r0 / n) * n;
     for (int q = 0; q < nr; q++, y++) {
       if (y == n) {
@@ -138,21 +142,21 @@ __global__ void __launch_bounds__(kLagThreads) k_lagcorr(const float *__restrict
       const int zb = wrapi(z + dz, n), yb = wrapi(y + dy, n);
       const float *A = delta + ((long long)z * n + y) * n;
       const float *B = delta + ((long long)zb * n + yb) * n;
-      float *sa = base + q * stride, *sb = sa + n;
-      for (int c = threadIdx.x; c < (n >> 2); c += blockDim.x) cp_async16(sa + 4 * c, A + 4 * c);
-      // sb[i] = delta_B[(dx0 + i) mod n], i < n + 64, in 16-byte pieces
+      float *sa = base + q * stride, *sb = sa + sa_len;
+      for (int c = threadIdx.x; c < (n >> 2); c += blockDim.x) cp_async16(sa + skew(4 * c), A + 4 * c);
+      // sb holds delta_B[(dx0 + i) mod n] at skew(i), i < n + 64
       for (int c = threadIdx.x; c < ((n + 64) >> 2); c += blockDim.x) {
         int xb = 4 * c + dx0;
         while (xb < 0) xb += n;
         while (xb >= n) xb -= n;
-        cp_async16(sb + 4 * c, B + xb);
+        cp_async16(sb + skew(4 * c), B + xb);
       }
     }
     cp_async_commit();
   };
   int since = 0;
   issue(0);
-  for (long long s = 0; s < nstage; s++) {
+  for (int s = 0; s < nstage; s++) {
     if (s + 1 < nstage) {
       issue(s + 1);
       cp_async_wait<1>();
@@ -160,42 +164,48 @@ __global__ void __launch_bounds__(kLagThreads) k_lagcorr(const float *__restrict
       cp_async_wait<0>();
     }
     __syncthreads();
-    const int nr = (int)min((long long)kRowsPerStage, nrows - s * kRowsPerStage);
-    const float *base = sm + (size_t)(s & 1) * kRowsPerStage * stride;
-    for (int q = 0; q < nr && live; q++) {
-      const float *sa = base + q * stride, *sb = sa + n;
-      for (int xb0 = 8 * xg; xb0 < n; xb0 += 256) {
-        float a[8], b[16];
-        *(float4 *)&a[0] = *(const float4 *)&sa[xb0];
-        *(float4 *)&a[4] = *(const float4 *)&sa[xb0 + 4];
+    const int nr = min(srows, nrows - s * srows);
+    const float *base = sm + (size_t)(s & 1) * srows * stride;
+    if (live) {
+      for (int q = rs; q < nr; q += rpw) {
+        const float *sa = base + q * stride, *sb = sa + sa_len;
+        for (int xb0 = 16 * xl; xb0 < n; xb0 += 16 * lpr) {
+          float a[16], b[32];
+          const float *pa = sa + skew(xb0);
+          const float *pb0 = sb + skew(xb0 + 16 * g), *pb1 = sb + skew(xb0 + 16 * g + 16);
 #pragma unroll
-        for (int v = 0; v < 4; v++) *(float4 *)&b[4 * v] = *(const float4 *)&sb[xb0 + 8 * lg + 4 * v];
-        // part[k] += sum_i delta_A[x + i] delta_B[x + i + dx0 + 8 lg + k]
+          for (int v = 0; v < 4; v++) {
+            *(float4 *)&a[4 * v] = *(const float4 *)(pa + 4 * v);
+            *(float4 *)&b[4 * v] = *(const float4 *)(pb0 + 4 * v);
+            *(float4 *)&b[16 + 4 * v] = *(const float4 *)(pb1 + 4 * v);
+          }
+          // part[k] += sum_i delta_A[x + i] delta_B[x + i + dx0 + 16 g + k]
 #pragma unroll
-        for (int i = 0; i < 8; i++)
+          for (int i = 0; i < 16; i++)
 #pragma unroll
-          for (int k = 0; k < kLagPer; k++) part[k] = fmaf(a[i], b[i + k], part[k]);
-      }
-      if (++since == 16) {  // fold the FP32 partials every 16 rows
-#pragma unroll
-        for (int k = 0; k < kLagPer; k++) {
-          ff_acc(hi[k], lo[k], part[k]);
-          part[k] = 0.0f;
+            for (int k = 0; k < 16; k++) part[k] = fmaf(a[i], b[i + k], part[k]);
         }
-        since = 0;
+        if (++since == 8) {  // fold the FP32 partials every 8 rows
+#pragma unroll
+          for (int k = 0; k < 16; k++) {
+            ff_acc(hi[k], lo[k], part[k]);
+            part[k] = 0.0f;
+          }
+          since = 0;
+        }
       }
     }
     __syncthreads();  // the buffer is refilled by the next issue
   }
 #pragma unroll
-  for (int k = 0; k < kLagPer; k++) ff_acc(hi[k], lo[k], part[k]);
-  // reduce the 32 x groups of each lag group (a warp) and add to out
+  for (int k = 0; k < 16; k++) ff_acc(hi[k], lo[k], part[k]);
+  // reduce the lanes of the warp (all hold lags dx0 + 16 g + k) and add to out
 #pragma unroll
-  for (int k = 0; k < kLagPer; k++) {
+  for (int k = 0; k < 16; k++) {
     double v = (double)hi[k] + (double)lo[k];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int dx = dx0 + 8 * lg + k;
-    if (live && xg == 0 && dx >= dxmin && dx <= dxmax)
+    const int dx = dx0 + 16 * g + k;
+    if (live && lane == 0 && dx >= dxmin && dx <= dxmax)
       atomicAdd(&out[(size_t)blockIdx.x * out_stride + (dx - dxmin)], v);
   }
 }
@@ -243,6 +253,12 @@ extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, co
       if (lo > xm) continue;
       cols.push_back(make_int4(dy, dz, lo, xm));
     }
+  // group the columns by the warps their lag window needs (16 lags per warp,
+  // the window starting at dxmin rounded down to a multiple of 4), one
+  // launch per group, so short columns do not run wide windows
+  auto warps_of = [](const int4 &c) { return std::min(4, (c.w - c.z + 1 + 3 + 15) / 16); };
+  std::stable_sort(cols.begin(), cols.end(),
+                   [&](const int4 &p, const int4 &q) { return warps_of(p) < warps_of(q); });
   int maxw = 1;
   for (const int4 &c : cols) maxw = std::max(maxw, c.w - c.z + 1);
   const long long m = (long long)ngrid * ngrid * ngrid;
@@ -313,25 +329,34 @@ extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, co
   }
   if (e == cudaSuccess) {
     const int zslab = std::max(1, ngrid / 8);
-    // 8 lags per warp, as many warps as the widest column needs (up to 8);
-    // windows start at dxmin rounded down to a multiple of 4 (16-byte rows)
-    const int wmax = maxw + 3;
-    const int G = std::min(8, (wmax + 7) / 8);
-    dim3 grid((unsigned)cols.size(), (unsigned)((wmax + 8 * G - 1) / (8 * G)),
-              (unsigned)((ngrid + zslab - 1) / zslab));
-    const size_t smem = (size_t)2 * kRowsPerStage * (2 * ngrid + 64) * sizeof(float);
+    auto skew_h = [](int i) { return i + 4 * (i >> 4); };
+    const int srows = 4 * (32 / std::min(32, ngrid / 16));
+    const size_t smem = (size_t)2 * srows * (skew_h(ngrid) + skew_h(ngrid + 64)) * sizeof(float);
     if (smem > 48 * 1024)
       e = cudaFuncSetAttribute(k_lagcorr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
       ctx->stats = cute_stats{};
       cudaMemsetAsync(ctx->d_ticket, 0, kCounterWords * sizeof(unsigned long long), st);
-      ctx->stats.launches = 1;
-      ctx->stats.blocks = (int)(grid.x * grid.y * grid.z);
-      ctx->stats.warps_per_block = G;
+      ctx->stats.launches = 0;
       if (ctx->timing) cudaEventRecord(ctx->ev0, st);
-      k_lagcorr<<<grid, 32 * G, smem, st>>>(d_delta, ngrid, d_cols, zslab, d_out, maxw);
+      for (size_t c0 = 0; c0 < cols.size() && e == cudaSuccess;) {
+        const int G = warps_of(cols[c0]);
+        size_t c1 = c0;
+        int wgrp = 1;
+        while (c1 < cols.size() && warps_of(cols[c1]) == G) {
+          wgrp = std::max(wgrp, cols[c1].w - cols[c1].z + 1 + 3);
+          c1++;
+        }
+        dim3 grid((unsigned)(c1 - c0), (unsigned)((wgrp + 16 * G - 1) / (16 * G)),
+                  (unsigned)((ngrid + zslab - 1) / zslab));
+        k_lagcorr<<<grid, 32 * G, smem, st>>>(d_delta, ngrid, d_cols + c0, zslab,
+                                              d_out + c0 * (size_t)maxw, maxw);
+        e = cudaGetLastError();
+        ctx->stats.launches++;
+        ctx->stats.blocks += (int)(grid.x * grid.y * grid.z);
+        c0 = c1;
+      }
       if (ctx->timing) cudaEventRecord(ctx->ev1, st);
-      e = cudaGetLastError();
     }
   }
   std::vector<double> C(cols.size() * (size_t)maxw);
