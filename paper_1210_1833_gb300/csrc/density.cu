@@ -97,6 +97,8 @@ __device__ __forceinline__ void ff_acc(float &hi, float &lo, float v) {
 // distinct banks.
 __device__ __forceinline__ int skew(int i) { return i + 4 * (i >> 4); }
 
+constexpr int kStageRowSets = 2;  // rows per lane per stage (smem: occupancy)
+
 // One CTA of G warps: lag column (dy, dz) = cols[blockIdx.x] with lags
 // dxmin..dxmax, window dx in [dx0, dx0 + 16 G) (dx0 = dxmin rounded down to
 // a multiple of 4, plus 16 G blockIdx.y), rows z in [z0, z1) (blockIdx.z).
@@ -106,7 +108,7 @@ __device__ __forceinline__ int skew(int i) { return i + 4 * (i >> 4); }
 // 256 FMAs.  Rows arrive by 16-byte cp.async into two stage buffers, the
 // next stage in flight while the current one is summed; FP32 partials are
 // folded into float-float accumulators every 8 rows.
-__global__ void __launch_bounds__(128, 4) k_lagcorr(const float *__restrict__ delta, int n,
+__global__ void __launch_bounds__(128, 6) k_lagcorr(const float *__restrict__ delta, int n,
                                                     const int4 *__restrict__ cols, int zslab,
                                                     double *__restrict__ out, int out_stride) {
   extern __shared__ __align__(16) float sm[];
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(128, 4) k_lagcorr(const float *__restrict__ de
   const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lpr = min(32, n >> 4);            // lanes per row
   const int rpw = 32 / lpr;                   // rows side by side in a warp
-  const int srows = 4 * rpw;                  // rows per stage
+  const int srows = kStageRowSets * rpw;      // rows per stage
   const int sa_len = skew(n), sb_len = skew(n + 64);
   const int stride = sa_len + sb_len;         // floats per staged row pair
   const int rs = lane / lpr, xl = lane % lpr;
@@ -253,12 +255,6 @@ extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, co
       if (lo > xm) continue;
       cols.push_back(make_int4(dy, dz, lo, xm));
     }
-  // group the columns by the warps their lag window needs (16 lags per warp,
-  // the window starting at dxmin rounded down to a multiple of 4), one
-  // launch per group, so short columns do not run wide windows
-  auto warps_of = [](const int4 &c) { return std::min(4, (c.w - c.z + 1 + 3 + 15) / 16); };
-  std::stable_sort(cols.begin(), cols.end(),
-                   [&](const int4 &p, const int4 &q) { return warps_of(p) < warps_of(q); });
   int maxw = 1;
   for (const int4 &c : cols) maxw = std::max(maxw, c.w - c.z + 1);
   const long long m = (long long)ngrid * ngrid * ngrid;
@@ -329,34 +325,28 @@ extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, co
   }
   if (e == cudaSuccess) {
     const int zslab = std::max(1, ngrid / 8);
+    // 16 lags per warp, as many warps as the widest column's window needs
+    // (it starts at dxmin rounded down to a multiple of 4); warps past a
+    // narrower column's end only help staging
+    const int wmax = maxw + 3;
+    const int G = std::min(4, (wmax + 15) / 16);
+    dim3 grid((unsigned)cols.size(), (unsigned)((wmax + 16 * G - 1) / (16 * G)),
+              (unsigned)((ngrid + zslab - 1) / zslab));
     auto skew_h = [](int i) { return i + 4 * (i >> 4); };
-    const int srows = 4 * (32 / std::min(32, ngrid / 16));
+    const int srows = kStageRowSets * (32 / std::min(32, ngrid / 16));
     const size_t smem = (size_t)2 * srows * (skew_h(ngrid) + skew_h(ngrid + 64)) * sizeof(float);
     if (smem > 48 * 1024)
       e = cudaFuncSetAttribute(k_lagcorr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
       ctx->stats = cute_stats{};
       cudaMemsetAsync(ctx->d_ticket, 0, kCounterWords * sizeof(unsigned long long), st);
-      ctx->stats.launches = 0;
+      ctx->stats.launches = 1;
+      ctx->stats.blocks = (int)(grid.x * grid.y * grid.z);
+      ctx->stats.warps_per_block = G;
       if (ctx->timing) cudaEventRecord(ctx->ev0, st);
-      for (size_t c0 = 0; c0 < cols.size() && e == cudaSuccess;) {
-        const int G = warps_of(cols[c0]);
-        size_t c1 = c0;
-        int wgrp = 1;
-        while (c1 < cols.size() && warps_of(cols[c1]) == G) {
-          wgrp = std::max(wgrp, cols[c1].w - cols[c1].z + 1 + 3);
-          c1++;
-        }
-        dim3 grid((unsigned)(c1 - c0), (unsigned)((wgrp + 16 * G - 1) / (16 * G)),
-                  (unsigned)((ngrid + zslab - 1) / zslab));
-        k_lagcorr<<<grid, 32 * G, smem, st>>>(d_delta, ngrid, d_cols + c0, zslab,
-                                              d_out + c0 * (size_t)maxw, maxw);
-        e = cudaGetLastError();
-        ctx->stats.launches++;
-        ctx->stats.blocks += (int)(grid.x * grid.y * grid.z);
-        c0 = c1;
-      }
+      k_lagcorr<<<grid, 32 * G, smem, st>>>(d_delta, ngrid, d_cols, zslab, d_out, maxw);
       if (ctx->timing) cudaEventRecord(ctx->ev1, st);
+      e = cudaGetLastError();
     }
   }
   std::vector<double> C(cols.size() * (size_t)maxw);
