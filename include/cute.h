@@ -119,6 +119,8 @@ cute_status cute_catalog_size(cute_ctx *ctx, int32_t cat_id, int64_t *n);
    (sigma,pi)).  cells_per_reach: 1..8, or 0 to choose from the mean
    number of objects in a reach-sized box (below 600: 2, below 3000: 3,
    else 4).  Cells along x are 8 times finer (rows of cells run along x).
+   The catalogs' joint extent must stay within 2e8 on every axis
+   (CUTE_E_UNSUPPORTED otherwise: the kernels' padding sits at 1e9).
    All catalogs must have the same boundary (and box_L).  A periodic grid
    needs reach[k] <= 0.47 box_L, else CUTE_E_UNSUPPORTED.  Rebuilding a
    catalog's grid replaces the previous one. */

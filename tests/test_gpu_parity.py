@@ -231,3 +231,13 @@ def test_rmu_duplicates_and_log_bins(ctx):
     _assert_same(gpu_count(ctx, "rmu", x, None, elog, e1), oracle_count("rmu", x, None, elog, e1))
     _assert_same(gpu_count(ctx, "sigpi", x, None, elog, np.linspace(0, 20, 5)),
                  oracle_count("sigpi", x, None, elog, np.linspace(0, 20, 5)))
+
+
+def test_extent_limit_is_rejected(ctx):
+    """A joint extent beyond 2e8 on an axis is refused at grid build (the
+    kernels' padding sentinels sit at 1e9 in the grid frame)."""
+    x = np.array([[0.0, 0.0, 0.0], [3e8, 1.0, 1.0], [1.0, 2.0, 3.0]])
+    a = ctx.upload(x)
+    with pytest.raises(cute.CuteError):
+        ctx.grid([a], [10.0] * 3)
+    a.free()
