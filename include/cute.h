@@ -185,7 +185,7 @@ cute_status cute_count_pairs_adjoint(cute_ctx *ctx, const cute_pair_desc *d, con
    The catalogs and grids must already exist (upload and grid build allocate
    and are done beforehand).  counts (n0 * n1 uint64) and, if d->weighted,
    wsum (n0 * n1 doubles) must be device memory of the context's device;
-   host pointers are CUTE_E_INVALID.  The kernel's scratch (task list,
+   host pointers are CUTE_E_INVALID.  The kernel's scratch (work items,
    binning tables, work counters) lives in one fixed 8 MiB device array of
    the library, held on every device that loads it until the process exits;
    a request whose scratch exceeds 8 MiB is rejected with CUTE_E_INVALID and

@@ -21,7 +21,7 @@
  *     sight, and the angle between unit vectors (Eq. 7), measured here by the
  *     chord length |n_j - n_i| = 2 sin(theta/2), a monotone function of theta.
  *   * periodic boxes wrap each separation component to its minimum image
- *     (Sec. 2.2, the estimator of Eq. 13 and Sec. 3.4 "The monopole in a box").
+ *     (Sec. 2.2, the estimator of Eq. 13, and Sec. 3.4.4).
  *   * weighted counts sum w_i w_j over the pairs of each bin (the pixel and
  *     density-grid weights of Sec. 3.4), and the gradient of a weighted-count
  *     functional with respect to one object's weight.

@@ -1,7 +1,7 @@
 // api.cu -- the C ABI of libcute_gb.so (include/cute.h): contexts, catalogs,
 // cell grids and the counting driver.  The driver validates a request,
 // derives the FP32 error bounds from the catalog geometry, builds (or reuses)
-// the binning plan and the task list, launches the persistent counting
+// the binning plan and the work list, launches the persistent counting
 // kernel and copies the histograms out.
 #include "cute_internal.h"
 #include "count_kernel.cuh"
@@ -376,21 +376,21 @@ cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &
   return CUTE_OK;
 }
 
-cute_status get_tasks(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, int slice,
-                      bool full_stencil, std::shared_ptr<TaskSet> &out) {
+cute_status get_work(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, int slice,
+                      bool full_stencil, std::shared_ptr<WorkSet> &out) {
   std::ostringstream key;
   key.precision(17);
   key << hp << "|" << slice << "|" << full_stencil << "|";
   for (const DescInfo &di : dis)
     key << di.A->id << ":" << di.A->grid_version << ":" << di.B->id << ":" << di.B->grid_version
         << ":" << di.kind << ":" << di.need[0] << ":" << di.need[1] << ":" << di.need[2] << ",";
-  auto it = ctx->task_cache.find(key.str());
-  if (it != ctx->task_cache.end()) {
+  auto it = ctx->work_cache.find(key.str());
+  if (it != ctx->work_cache.end()) {
     out = it->second;
     return CUTE_OK;
   }
   if (dis.size() > 65536) return fail(ctx, CUTE_E_UNSUPPORTED, "more than 65536 pair sets");
-  auto T = std::make_shared<TaskSet>();
+  auto T = std::make_shared<WorkSet>();
   const int home_chunk = 32 * hp;
   std::vector<std::vector<int4>> chunks(dis.size()), stencils(dis.size());
   size_t nch = 0, nst = 0;
@@ -473,7 +473,7 @@ cute_status get_tasks(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, i
   CUDA_OR_FAIL(cudaMalloc((void **)&T->d_items, std::max<long long>(T->items, 1) * sizeof(int4)));
   CUDA_OR_FAIL(work_write(T->d_work, T->d_ebase, (int)T->pairs.size(), T->nentries, slice,
                           T->d_eprefix, T->d_items, ctx->stream));
-  ctx->task_cache[key.str()] = T;
+  ctx->work_cache[key.str()] = T;
   out = T;
   return CUTE_OK;
 }
@@ -491,11 +491,11 @@ std::string tuning_key(const std::vector<DescInfo> &dis, int acc, bool full_sten
   return k.str();
 }
 
-// common preparation of a (batched) count: validation, plan, tasks, params
+// common preparation of a (batched) count: validation, plan, work list, params
 struct Prepared {
   std::vector<DescInfo> dis;
   std::shared_ptr<Plan> plan;
-  std::shared_ptr<TaskSet> ts;
+  std::shared_ptr<WorkSet> ts;
   KParams p;
   int hp, warps, blocks, acc;
   size_t smem;
@@ -548,7 +548,7 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
   }
   cute_status st = get_plan(ctx, &d[0], ep, pr.hp, pr.plan);
   if (st != CUTE_OK) return st;
-  st = get_tasks(ctx, pr.dis, pr.hp, slice, full_stencil, pr.ts);
+  st = get_work(ctx, pr.dis, pr.hp, slice, full_stencil, pr.ts);
   if (st != CUTE_OK) return st;
   const Plan &P = *pr.plan;
   SmemLayout L = smem_layout((int)P.lut.size(), (int)P.band.size() / 2, P.nslots, P.R, pr.hp, acc);

@@ -40,7 +40,7 @@ constexpr float kNbrFar = -1.0e9f;
 
 // ------------------------------------------------------------------ work entries
 // One contiguous range [j0, j1) of catalog B that a home chunk meets, with
-// its flags (kTaskSelf / kTaskNoSelfPair, image shift code in bits 8..13).
+// its flags (kSegSelf / kSegNoSelfPair, image shift code in bits 8..13).
 struct Seg {
   int j0, j1, flags;
 };
@@ -70,14 +70,14 @@ __host__ __device__ inline int entry_segments(const PairWork &pd, const int32_t 
   if (r.w && pd.mode == kModeAutoHalf) {
     // A and B are one catalog: the chunk against the rest of its cell run
     const int e = row[cx1 + 1];
-    if (e > c.x) s[n++] = Seg{c.x, e, kTaskSelf};
+    if (e > c.x) s[n++] = Seg{c.x, e, kSegSelf};
     xa = cx1 + 1;
     xb = cx1 + r.z;
     f = 0;
   } else {
     xa = cx0 - r.z;
     xb = cx1 + r.z;
-    f = (r.w && pd.mode == kModeAutoFull) ? kTaskNoSelfPair : 0;
+    f = (r.w && pd.mode == kModeAutoFull) ? kSegNoSelfPair : 0;
   }
   const int lo = xa > 0 ? xa : 0, hi = xb < nx - 1 ? xb : nx - 1;
   if (per) {
@@ -103,8 +103,8 @@ __host__ __device__ inline int entry_segments(const PairWork &pd, const int32_t 
 }
 
 // Work item record (int4): home objects [x, x + (w & 0xff)) of pair set
-// w >> 16 against neighbours [y, z); bits 8..9 of w: kTaskSelf /
-// kTaskNoSelfPair, bits 10..15: image shift code.
+// w >> 16 against neighbours [y, z); bits 8..9 of w: kSegSelf /
+// kSegNoSelfPair, bits 10..15: image shift code.
 __host__ __device__ inline int4 item_record(int hs, int he, const Seg &g, int js, int je,
                                             int pair) {
   return make_int4(hs, js, je,

@@ -69,8 +69,8 @@ constexpr int KMONO = 0, KRMU = 1, KSIGPI = 2, KTHETA = 3;
 // each, written as a 16-byte record (item_record) on the GPU.
 //   chunk int4: (h0, h1, cx0 | cx1 << 16, cy | cz << 16)
 //   stencil row int4: (dy, dz, kxr, 1 on the home row)
-constexpr int kTaskSelf = 1;        // only j > i (unique pairs of a run with itself)
-constexpr int kTaskNoSelfPair = 2;  // every j != i (full-stencil adjoint of an auto count)
+constexpr int kSegSelf = 1;        // only j > i (unique pairs of a run with itself)
+constexpr int kSegNoSelfPair = 2;  // every j != i (full-stencil adjoint of an auto count)
 constexpr int kCounterWords = 6;  // work ticket + 5 statistics words
 constexpr int kModeCross = 0, kModeAutoHalf = 1, kModeAutoFull = 2;
 
@@ -173,7 +173,7 @@ struct Plan;  // binning plan (plan.cpp)
 // chunks, stencils and pair descriptors built on the host, entry item counts
 // and their prefix sums computed on the GPU.  Cached per set of catalogs and
 // launch shape.
-struct TaskSet {
+struct WorkSet {
   std::vector<PairDev> pairs;
   std::vector<PairWork> work;
   std::vector<int> ebase;          // npairs + 1
@@ -187,7 +187,7 @@ struct TaskSet {
   long long *d_eprefix = nullptr;  // nentries + 1
   long long items = 0;             // work items
   int4 *d_items = nullptr;         // their records
-  ~TaskSet() {
+  ~WorkSet() {
     cudaFree(d_chunks);
     cudaFree(d_stencil);
     cudaFree(d_pairs);
@@ -227,7 +227,7 @@ struct cute_ctx {
   cute_stats stats{};
   // caches
   std::map<std::string, std::shared_ptr<cute::Plan>> plans;
-  std::map<std::string, std::shared_ptr<cute::TaskSet>> task_cache;
+  std::map<std::string, std::shared_ptr<cute::WorkSet>> work_cache;
   // autotuned launch shapes per (kind, catalogs, policy)
   std::map<std::string, cute_tuning> tuned;
   // CUDA graphs of batched counts with device outputs, replayed when the
@@ -237,7 +237,7 @@ struct cute_ctx {
   void clear_caches() {
     for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
-    task_cache.clear();
+    work_cache.clear();
   }
 };
 

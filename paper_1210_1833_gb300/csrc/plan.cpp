@@ -1,8 +1,9 @@
 // plan.cpp -- host planning for the counting kernels: per-axis lookup tables
-// with proven FP32 error bands, and the task list of a pair set.
+// with proven FP32 error bands, arithmetic binning of uniform edges, and the
+// home chunks and neighbour stencil of a pair set.
 //
-// Binning (Sec. 3.1: "determining the bin corresponding to that distance").
-// The kernels compute each separation in FP32 and look its squared value up
+// Binning (the bin of each pair's separation, Sec. 3.1).  For non-uniform
+// edges the kernels compute each separation in FP32 and look its squared value up
 // in a table.  A table cell is CLEAN when every FP32 value it holds, widened
 // by the error bound err(v) of the FP32 computation, lies strictly between
 // the same two bin edges, so the FP32 result bins the pair exactly as the
@@ -11,11 +12,11 @@
 // in FP64.  Both the table geometry (linear or logarithmic in v) and its size
 // are chosen here by the expected fraction of pairs landing in dirty cells.
 //
-// Neighbour search (Sec. 3.3): the task list walks the cells of catalog A in
-// row order; each row-run of home cells is paired with the rows of
-// neighbour cells in the cube of 2k+1 cells per side around it.  Within a
-// row the neighbour cells are contiguous in the cell-sorted order, so each
-// (home run, neighbour row) is one contiguous slice of catalog B.
+// Neighbour search (Sec. 3.3): catalog A is cut, row of cells by row, into
+// home chunks; each chunk is paired with the rows of neighbour cells of the
+// stencil around it.  Within a row the neighbour cells are contiguous in the
+// cell-sorted order, so each (chunk, neighbour row) is at most a few
+// contiguous ranges of catalog B (work.cu turns them into work items).
 #include "cute_internal.h"
 
 #include <algorithm>
