@@ -408,6 +408,9 @@ def run_extras(ctx, dev, reps=3, which="all"):
     return out
 
 
+_ROW_TUNE = True  # --no-tune: the rows' counts keep the library's default launch shape
+
+
 def _row_batched(ctx, dev, timed):
     import torch
     out = {}
@@ -476,7 +479,8 @@ def _row_monopole(ctx, dev, timed):
 
     # a small count: let the autotuner pick home objects, warps and slice
     ctx.grid([A], [w.edges0[-1]] * 3)
-    tuned = ctx.autotune("mono", [(A, None)], w.edges0, tune_cells=False, max_items=1 << 30)
+    tuned = (ctx.autotune("mono", [(A, None)], w.edges0, tune_cells=False, max_items=1 << 30)
+             if _ROW_TUNE else None)
     t = timed(step)
     st = ctx.stats()
     out = {"monopole_c1_20k": {
@@ -582,7 +586,8 @@ def _row_weighted(ctx, dev, timed):
     cnt = torch.zeros(len(e) - 1, dtype=torch.int64, device=f"cuda:{dev}")
     ws = torch.zeros(len(e) - 1, dtype=torch.float64, device=f"cuda:{dev}")
     G = torch.from_numpy(w.extra["G"]).to(f"cuda:{dev}")
-    tuned = ctx.autotune("mono", [(A, None)], e, tune_cells=False, max_items=30000)
+    tuned = (ctx.autotune("mono", [(A, None)], e, tune_cells=False, max_items=30000)
+             if _ROW_TUNE else None)
     t_plain = timed(lambda: ctx.count("mono", A, None, e, out=cnt, want_oor=False))
     st = ctx.stats()
     t_w = timed(lambda: ctx.count("mono", A, None, e, weighted=True, out=cnt, wsum_out=ws,
@@ -621,6 +626,8 @@ def main():
                     help="profiling: run only this row (64-box batched sigma-pi, or the 4M "
                          "weighted forward and adjoint) and print it")
     args = ap.parse_args()
+    global _ROW_TUNE
+    _ROW_TUNE = args.tune
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:

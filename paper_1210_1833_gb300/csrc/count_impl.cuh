@@ -198,11 +198,13 @@ __device__ __forceinline__ Rmu2 rmu_values2(float2 qx, float2 qy, float2 qz, flo
 
 // Uniform edges, two home objects at once with the packed FP32 instructions
 // of sm_100+ (element-wise IEEE round-to-nearest: each element is rounded
-// as the scalar formula would be).  Monopole (and theta on chords):
+// as the scalar formula would be).  Each gives the byte offsets of the two
+// pairs' slots and a near score per pair: the pair lies inside an edge's
+// error band (and is re-tested in FP64) when its score reaches the kind's
+// threshold, near_thr.  Monopole (and theta on chords):
 __device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2 qy, float2 qz,
                                             float2 nx, float2 ny, float2 nz, uint32_t stride,
-                                            uint32_t c, uint32_t &o0, uint32_t &o1, bool &n0,
-                                            bool &n1) {
+                                            uint32_t c, uint32_t &o0, uint32_t &o1, float2 &sc) {
   const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
   // v >= 1e-30 (a floor far below any nonzero squared separation of FP32
   // coordinates), so x = v / sqrt(v) is finite and t >= -1/2
@@ -214,8 +216,7 @@ __device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2
   const float2 tm = __fadd2_rn(t, make_float2(kMagic, kMagic));
   const float2 fl = __fadd2_rn(tm, make_float2(-kMagic, -kMagic));
   const float2 h = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), t);  // t - floor, exact
-  n0 = fabsf(h.x) >= a.near_at;
-  n1 = fabsf(h.y) >= a.near_at;
+  sc = make_float2(fabsf(h.x), fabsf(h.y));  // near when >= near_at
   o0 = __float_as_uint(tm.x) * stride + c;
   o1 = __float_as_uint(tm.y) * stride + c;
 }
@@ -227,15 +228,16 @@ __device__ __forceinline__ float2 clampt(float2 t, float hi) {
 __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a1, float2 qx,
                                            float2 qy, float2 qz, float2 nx, float2 ny, float2 nz,
                                            float2 ax, float2 ay, float2 az, float2 aq,
-                                           uint32_t stride0, uint32_t stride1, uint32_t c,
-                                           uint32_t &o0, uint32_t &o1, bool &n0, bool &n1) {
+                                           float sl1, uint32_t stride1, uint32_t c,
+                                           uint32_t &o0, uint32_t &o1, float2 &sc) {
   const Rmu2 v = rmu_values2(qx, qy, qz, nx, ny, nz, ax, ay, az, aq);
   const float2 r2 = v.r2, sl = v.sl, l2 = v.l2;
   const float2 rr = make_float2(rsqrt_hw(r2.x), rsqrt_hw(r2.y));
   const float2 pl = __fmul2_rn(r2, l2);  // > 0 (or +inf for padded slots): mu finite
   const float2 mu = __fmul2_rn(make_float2(fabsf(sl.x), fabsf(sl.y)),
                                make_float2(rsqrt_hw(pl.x), rsqrt_hw(pl.y)));
-  // t >= -1/2 on both axes (e_0 = 0); clamped above only
+  // t >= -1/2 on both axes (e_0 = 0); clamped above only (mu too: a
+  // candidate beyond the reach may have l near 0, and a NaN clamps to thi)
   const float2 t0 = clampt(__ffma2_rn(__fmul2_rn(r2, rr), make_float2(a0.inv, a0.inv),
                                       make_float2(a0.cst, a0.cst)), a0.thi);
   const float2 t1 = clampt(__ffma2_rn(mu, make_float2(a1.inv, a1.inv), make_float2(a1.cst, a1.cst)),
@@ -243,25 +245,27 @@ __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a
   const float2 m2 = make_float2(kMagic, kMagic), nm2 = make_float2(-kMagic, -kMagic),
                neg = make_float2(-1.0f, -1.0f);
   const float2 tm0 = __fadd2_rn(t0, m2), tm1 = __fadd2_rn(t1, m2);
-  const float2 h0 = __ffma2_rn(__fadd2_rn(tm0, nm2), neg, t0);  // t - floor, exact
+  const float2 f0 = __fadd2_rn(tm0, nm2);                        // rint(t0)
+  const float2 h0 = __ffma2_rn(f0, neg, t0);                     // t - rint(t), exact
   const float2 h1 = __ffma2_rn(__fadd2_rn(tm1, nm2), neg, t1);
+  // magic + rint(t0) * slots1 + rint(t1): exact (an integer below 2^24)
+  const float2 tc = __ffma2_rn(f0, make_float2(sl1, sl1), tm1);
   // near an edge: |h| within the error bound of 1/2 on either axis (the mu
-  // bound thr_a / r + thr_b, with the 1/r that rr already holds)
-  const float2 lim1 = __ffma2_rn(rr, make_float2(-a1.thr_a, -a1.thr_a),
-                                 make_float2(a1.near_c, a1.near_c));
-  n0 = (fabsf(h0.x) >= a0.near_at) | (fabsf(h1.x) >= lim1.x);  // no short circuit: no branch
-  n1 = (fabsf(h0.y) >= a0.near_at) | (fabsf(h1.y) >= lim1.y);
-  o0 = __float_as_uint(tm0.x) * stride0 + (__float_as_uint(tm1.x) * stride1 + c);
-  o1 = __float_as_uint(tm0.y) * stride0 + (__float_as_uint(tm1.y) * stride1 + c);
+  // bound thr_a / r + thr_b, with the 1/r that rr already holds): the score
+  // max(|h0|, |h1| + thr_a rr) reaches min(near_at, near_c) (one FMA, its
+  // rounding covered by near_c's 2^-22 margin)
+  sc = make_float2(fmaxf(fabsf(h0.x), fmaf(rr.x, a1.thr_a, fabsf(h1.x))),
+                   fmaxf(fabsf(h0.y), fmaf(rr.y, a1.thr_a, fabsf(h1.y))));
+  o0 = __float_as_uint(tc.x) * stride1 + c;
+  o1 = __float_as_uint(tc.y) * stride1 + c;
 }
 
-// Two (sigma, pi) pairs at once with uniform edges on both axes (the near
-// test compares |h| with 1/2 - thr_b rounded down, as the monopole's).
+// Two (sigma, pi) pairs at once with uniform edges on both axes (near when
+// |h| reaches near_at on either axis, pi's |h| rescaled to sigma's).
 __device__ __forceinline__ void sigpi_arith2(const AxisPlan &a0, const AxisPlan &a1, float2 qx,
                                              float2 qy, float2 qz, float2 nx, float2 ny,
-                                             float2 nz, uint32_t stride0, uint32_t stride1,
-                                             uint32_t c, uint32_t &o0, uint32_t &o1, bool &n0,
-                                             bool &n1) {
+                                             float2 nz, float sl1, uint32_t stride1,
+                                             uint32_t c, uint32_t &o0, uint32_t &o1, float2 &sc) {
   const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
   const float2 v0 = __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, make_float2(kVFloor, kVFloor)));
   const float2 x0 = __fmul2_rn(v0, make_float2(rsqrt_hw(v0.x), rsqrt_hw(v0.y)));
@@ -273,19 +277,57 @@ __device__ __forceinline__ void sigpi_arith2(const AxisPlan &a0, const AxisPlan 
   const float2 m2 = make_float2(kMagic, kMagic), nm2 = make_float2(-kMagic, -kMagic),
                neg = make_float2(-1.0f, -1.0f);
   const float2 tm0 = __fadd2_rn(t0, m2), tm1 = __fadd2_rn(t1, m2);
-  const float2 h0 = __ffma2_rn(__fadd2_rn(tm0, nm2), neg, t0);
+  const float2 f0 = __fadd2_rn(tm0, nm2);
+  const float2 h0 = __ffma2_rn(f0, neg, t0);
   const float2 h1 = __ffma2_rn(__fadd2_rn(tm1, nm2), neg, t1);
-  n0 = (fabsf(h0.x) >= a0.near_at) | (fabsf(h1.x) >= a1.near_at);
-  n1 = (fabsf(h0.y) >= a0.near_at) | (fabsf(h1.y) >= a1.near_at);
-  o0 = __float_as_uint(tm0.x) * stride0 + (__float_as_uint(tm1.x) * stride1 + c);
-  o1 = __float_as_uint(tm0.y) * stride0 + (__float_as_uint(tm1.y) * stride1 + c);
+  const float2 tc = __ffma2_rn(f0, make_float2(sl1, sl1), tm1);  // as for (r, mu)
+  // pi's |h| scaled to sigma's threshold (rounded up: never fewer flags)
+  const float2 g1 = __fmul2_rn(h1, make_float2(a1.near_scale, a1.near_scale));
+  sc = make_float2(fmaxf(fabsf(h0.x), fabsf(g1.x)), fmaxf(fabsf(h0.y), fabsf(g1.y)));
+  o0 = __float_as_uint(tc.x) * stride1 + c;
+  o1 = __float_as_uint(tc.y) * stride1 + c;
+}
+
+// Stores two pairs' slot offsets and near scores from the arithmetic
+// binning: pairs that are not pairs of this item (MASK) go to the unused
+// slot 0 with score 0; without the lazy count, near pairs also go to
+// slot 0 and are marked in nmask at once.
+template <int HP, int MASK, bool LAZY, int NP>
+__device__ __forceinline__ void arith_pair_out(float2 s2, uint32_t (&o)[2], int u, int sp, int gj,
+                                               const Home<HP> &h, uint32_t zoff, float thr,
+                                               uint32_t (&off)[NP], float (&sc)[NP],
+                                               unsigned &nmask) {
+#pragma unroll
+  for (int e = 0; e < 2; e++) {
+    const int s = 2 * sp + e, k = u * HP + s;
+    float v = e ? s2.y : s2.x;
+    if (MASK == 1 && !(gj > h.id[s])) { o[e] = zoff; v = 0.0f; }
+    if (MASK == 2 && gj == h.id[s]) { o[e] = zoff; v = 0.0f; }
+    if (!LAZY && v >= thr) { o[e] = zoff; nmask |= 1u << k; }
+    off[k] = o[e];
+    sc[k] = v;
+  }
+}
+
+// Score threshold of the arithmetic binning: |h| >= near_at of axis 0
+// (monopole, theta; sigma, pi with pi rescaled), or the smaller of near_at
+// of r and near_c of mu (r, mu: a few more flags than the exact per-axis
+// tests, all decided by the FP64 re-test).
+template <int KIND>
+__device__ __forceinline__ float near_thr(const KParams &p) {
+  if (KIND == KRMU) return fminf(p.ax[0].near_at, p.ax[1].near_c);
+  return p.ax[0].near_at;
 }
 
 // All pairs of the HP home objects of each lane with the cnt neighbours of
 // one shared-memory tile (cnt even; rows past the slice hold sentinels).
 // Two neighbours at a time: every binning of the 2 x HP pairs is issued
 // first, then the accumulation; pairs inside an edge's error band go to the
-// warp's FP64 queue (rare, so the enqueue sits behind one vote).
+// warp's FP64 queue (rare, so the enqueue sits behind one vote).  Plain
+// counts with arithmetic binning add every pair to the slot its FP32 value
+// gives and vote on the step's largest near score; a flagged step (rare)
+// takes the near pairs' increments back before queueing them, so the
+// common step carries no per-pair selects.
 // MASK: 1 -- only j > i counts (the home run against itself, unique pairs);
 //       2 -- every j != i counts (full-stencil adjoint of an auto count).
 template <int KIND, int HP, int M0, int M1, int MASK, int ACC>
@@ -295,6 +337,8 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
                                            unsigned &near_count) {
   constexpr int U = 8 / HP;  // neighbours per step: 8 pairs per lane per step
   constexpr int NP = U * HP;
+  constexpr bool kLazy = ACC == kAccCount && M0 == kArith;
+  const float thr = near_thr<KIND>(p);
   const int slot_shift = 31 - __clz(p.R * 4);
   // Plain counts add straight to the lane's histogram copy: its shared
   // address is folded into the offset constants (slot k = bits - magic + 1
@@ -303,9 +347,13 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
   const uint32_t zoff = (ACC == kAccCount) ? w.s_hist_lane : 0u;
   const uint32_t st0 = (uint32_t)p.slots1 * p.R * 4u, st1 = (uint32_t)p.R * 4u;
   const uint32_t c1d = (1u - kMagicBits) * st0 + zoff;
-  const uint32_t c2d = (1u - kMagicBits) * (st0 + st1) + zoff;
+  // 2-D: slot (rint(t0) + 1) * slots1 + rint(t1) + 1 from the bits of
+  // magic + rint(t0) * slots1 + rint(t1)
+  const float sl1 = (float)p.slots1;
+  const uint32_t c2d = ((uint32_t)p.slots1 + 1u - kMagicBits) * st1 + zoff;
   for (int j = 0; j < cnt; j += U) {
     uint32_t off[NP];
+    float sc[NP];  // arithmetic binning: near scores
     float wj[U];
     unsigned nmask = 0;
 #pragma unroll
@@ -318,18 +366,10 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
 #pragma unroll
         for (int sp = 0; sp < HP / 2; sp++) {
           uint32_t o[2];
-          bool nr[2];
+          float2 s2;
           mono_arith2(p.ax[0], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], st0, c1d, o[0], o[1],
-                      nr[0], nr[1]);
-#pragma unroll
-          for (int e = 0; e < 2; e++) {
-            const int s = 2 * sp + e, k = u * HP + s;
-            const int gj = gj0 + j + u;
-            if (MASK == 1 && !(gj > h.id[s])) { o[e] = zoff; nr[e] = false; }
-            if (MASK == 2 && gj == h.id[s]) { o[e] = zoff; nr[e] = false; }
-            if (nr[e]) { o[e] = zoff; nmask |= 1u << k; }
-            off[k] = o[e];
-          }
+                      s2);
+          arith_pair_out<HP, MASK, kLazy>(s2, o, u, sp, gj0 + j + u, h, zoff, thr, off, sc, nmask);
         }
       } else if constexpr (KIND == KSIGPI && M0 == kArith) {
         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
@@ -337,18 +377,10 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
 #pragma unroll
         for (int sp = 0; sp < HP / 2; sp++) {
           uint32_t o[2];
-          bool nr[2];
-          sigpi_arith2(p.ax[0], p.ax[1], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], st0, st1,
-                       c2d, o[0], o[1], nr[0], nr[1]);
-#pragma unroll
-          for (int e = 0; e < 2; e++) {
-            const int s = 2 * sp + e, k = u * HP + s;
-            const int gj = gj0 + j + u;
-            if (MASK == 1 && !(gj > h.id[s])) { o[e] = zoff; nr[e] = false; }
-            if (MASK == 2 && gj == h.id[s]) { o[e] = zoff; nr[e] = false; }
-            if (nr[e]) { o[e] = zoff; nmask |= 1u << k; }
-            off[k] = o[e];
-          }
+          float2 s2;
+          sigpi_arith2(p.ax[0], p.ax[1], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], sl1, st1,
+                       c2d, o[0], o[1], s2);
+          arith_pair_out<HP, MASK, kLazy>(s2, o, u, sp, gj0 + j + u, h, zoff, thr, off, sc, nmask);
         }
       } else if constexpr (KIND == KRMU && M0 == kArith) {
         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
@@ -356,18 +388,10 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
 #pragma unroll
         for (int sp = 0; sp < HP / 2; sp++) {
           uint32_t o[2];
-          bool nr[2];
+          float2 s2;
           rmu_arith2(p.ax[0], p.ax[1], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], h.ax2[sp],
-                     h.ay2[sp], h.az2[sp], h.aq2[sp], st0, st1, c2d, o[0], o[1], nr[0], nr[1]);
-#pragma unroll
-          for (int e = 0; e < 2; e++) {
-            const int s = 2 * sp + e, k = u * HP + s;
-            const int gj = gj0 + j + u;
-            if (MASK == 1 && !(gj > h.id[s])) { o[e] = zoff; nr[e] = false; }
-            if (MASK == 2 && gj == h.id[s]) { o[e] = zoff; nr[e] = false; }
-            if (nr[e]) { o[e] = zoff; nmask |= 1u << k; }
-            off[k] = o[e];
-          }
+                     h.ay2[sp], h.az2[sp], h.aq2[sp], sl1, st1, c2d, o[0], o[1], s2);
+          arith_pair_out<HP, MASK, kLazy>(s2, o, u, sp, gj0 + j + u, h, zoff, thr, off, sc, nmask);
         }
       } else {
         // table binning: the values of two pairs in packed FP32, then a
@@ -437,14 +461,30 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
         ff_add(h.gh[k % HP], h.gl[k % HP], th, tl);
       }
     }
+    bool flagged;
+    if constexpr (kLazy) {
+      // the step's largest score (a tree: short dependency chains)
+      float m[NP];
+#pragma unroll
+      for (int k = 0; k < NP; k++) m[k] = sc[k];
+#pragma unroll
+      for (int d = 1; d < NP; d *= 2)
+#pragma unroll
+        for (int k = 0; k + d < NP; k += 2 * d) m[k] = fmaxf(m[k], m[k + d]);
+      flagged = __any_sync(kFull, m[0] >= thr);
+    } else {
+      flagged = __any_sync(kFull, nmask != 0u);
+    }
     // rare: pairs inside an edge's error band join the warp's FP64 queue; the
     // queue only grows here, so it is drained here when it holds 32
-    if (__any_sync(kFull, nmask != 0u)) {
+    if (flagged) {
 #pragma unroll
       for (int k = 0; k < NP; k++) {
+        const bool nk = kLazy ? (sc[k] >= thr) : ((nmask >> k) & 1u) != 0u;
+        if (kLazy && nk) red_add_u32(off[k], 0xffffffffu);  // take back the FP32 slot's count
         // (a padded home slot or tile row is never a pair, whatever its
         // arithmetic gave)
-        if ((nmask & (1u << k)) && h.id[k % HP] != 0x7fffffff && gj0 + j + k / HP < w.gje) {
+        if (nk && h.id[k % HP] != 0x7fffffff && gj0 + j + k / HP < w.gje) {
           near_count++;
           int pos = atomicAdd(w.qcnt, 1);
           if (pos < w.qcap) w.queue[pos] = make_int2(h.id[k % HP], gj0 + j + k / HP);

@@ -185,6 +185,9 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
 __device__ __forceinline__ void red_add1(uint32_t a) {
   asm volatile("red.shared.add.u32 [%0], 1;\n" ::"r"(a) : "memory");
 }
+__device__ __forceinline__ void red_add_u32(uint32_t a, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;\n" ::"r"(a), "r"(v) : "memory");
+}
 
 // table lookup; MODE fixed per instantiation of the inner loop.  v is
 // clamped to the table's range in place (NaN becomes vmax).
@@ -232,7 +235,8 @@ __device__ __forceinline__ float rsqrt_hw(float x) {
 
 // Uniform edges from 0 (kArith): t = x * inv + cst >= -1/2 for x >= 0 (the
 // squared separations carry the kVFloor floor, so x and mu are finite),
-// clamped from above to thi (pairs beyond the last edge, padded slots);
+// clamped from above to thi (pairs beyond the last edge, padded slots, and
+// any non-finite mu);
 // tm = t + kMagic holds rint(t) in its low mantissa bits, so the slot
 // (bin + 1) is bits(tm) - kMagicBits + 1, and h = t - (tm - kMagic) is exact.
 // mono_arith2 / sigpi_arith2 / rmu_arith2 (count_impl.cuh) apply this to two
@@ -251,13 +255,43 @@ __device__ __forceinline__ uint32_t mu_resolve(uint32_t band, const AxisPlan &a,
 }
 
 // ---- canonical FP64 formulas (identical arithmetic to the definition; no
-// contraction: every operation is an explicitly rounded intrinsic)
-__device__ __forceinline__ double wrap64(double d, double L, double halfL) {
-  if (L > 0.0) {
-    if (d > halfL) d = __dsub_rn(d, L);
-    else if (d < -halfL) d = __dadd_rn(d, L);
+// contraction: every operation is an explicitly rounded intrinsic).  FP64
+// runs at a small fraction of the FP32 rate here, so the re-test spends
+// FP64 operations only on the canonical values and their edge comparisons.
+//
+// Minimum image.  The test |d| > L/2 compares the high words (integer
+// order of non-negative doubles), which differs from the FP64 test only
+// when |d| is within 2^-20 of L/2 -- a separation beyond every reach
+// (reach <= 0.47 L), out of range whichever image is taken.
+// hi_half: high word of L/2 (periodic), negative for open boundaries.
+__device__ __forceinline__ double wrap64(double d, double L, int hi_half) {
+  if (hi_half >= 0) {
+    const int hi = __double2hiint(d);
+    if ((hi & 0x7fffffff) > hi_half) d = (hi < 0) ? __dadd_rn(d, L) : __dsub_rn(d, L);
   }
   return d;
+}
+
+// FP32 value of a non-negative double from its high word (relative error
+// below 2^-20; 0 below the FP32 normal range, FLT_MAX above it).
+__device__ __forceinline__ float approx_f32(double v) {
+  const int hi = __double2hiint(v);
+  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return __int_as_float(0x7f7fffff);
+  return __int_as_float((e << 23) | ((hi & 0xfffff) << 3));
+}
+
+// Uniform edges from 0: the edge nearest sqrt(v) (v a squared separation),
+// in [0, n].  The canonical bin is k or k - 1: the estimate is far closer
+// to sqrt(v) than half a bin.
+__device__ __forceinline__ int arith_edge(float x, float inv, int n) {
+  const int k = __float2int_rn(x * inv);  // NaN gives 0, overflow saturates
+  return min(max(k, 0), n);
+}
+__device__ __forceinline__ float approx_sqrt(double v) {
+  const float f = approx_f32(v);
+  return f * rsqrt_hw(fmaxf(f, 1e-30f));
 }
 // bin b with E[b] <= v < E[b+1]; -1 outside
 __device__ __forceinline__ int bin64(const double *E, int n, double v) {
@@ -279,6 +313,15 @@ __device__ __forceinline__ int mubin64(const double *M, int n, double q, double 
   return lo;
 }
 
+// bin of a squared separation on axis a (edges E, n bins): one comparison
+// with uniform edges, the binary search otherwise; -1 outside
+__device__ __forceinline__ int axis_bin64(const AxisPlan &a, const double *E, int n, double v) {
+  if (a.mode != kArith) return bin64(E, n, v);
+  const int k = arith_edge(approx_sqrt(v), a.inv, n);
+  const int b = (v >= E[k]) ? k : k - 1;  // E[0] = 0 <= v: b >= 0
+  return b < n ? b : -1;
+}
+
 // flat histogram slot of pair (i of A, j of B) from the FP64 coordinates;
 // 0 (trash) when out of range
 template <int KIND>
@@ -286,28 +329,30 @@ __device__ int slot64(const KParams &p, const PairDev &pd, int i, int j) {
   const double *A = pd.sA, *B = pd.sB;
   double ax = A[i], ay = A[(size_t)pd.nA + i], az = A[2 * (size_t)pd.nA + i];
   double bx = B[j], by = B[(size_t)pd.nB + j], bz = B[2 * (size_t)pd.nB + j];
-  const double L = pd.L64, hL = 0.5 * pd.L64;
+  const double L = pd.L64;
+  // L/2 halves the exponent field of L (a normal positive double)
+  const int hh = pd.L32 > 0.0f ? __double2hiint(pd.L64) - (1 << 20) : -1;
   if (KIND == KMONO || KIND == KTHETA) {
-    double dx = wrap64(__dsub_rn(bx, ax), L, hL), dy = wrap64(__dsub_rn(by, ay), L, hL),
-           dz = wrap64(__dsub_rn(bz, az), L, hL);
+    double dx = wrap64(__dsub_rn(bx, ax), L, hh), dy = wrap64(__dsub_rn(by, ay), L, hh),
+           dz = wrap64(__dsub_rn(bz, az), L, hh);
     double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    int b = bin64(p.E0, p.n0, d2);
+    int b = axis_bin64(p.ax[0], p.E0, p.n0, d2);
     return b < 0 ? 0 : b + 1;
   } else if (KIND == KSIGPI) {
-    double dx = wrap64(__dsub_rn(bx, ax), L, hL), dy = wrap64(__dsub_rn(by, ay), L, hL),
-           dz = wrap64(__dsub_rn(bz, az), L, hL);
+    double dx = wrap64(__dsub_rn(bx, ax), L, hh), dy = wrap64(__dsub_rn(by, ay), L, hh),
+           dz = wrap64(__dsub_rn(bz, az), L, hh);
     double s2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
     double p2 = __dmul_rn(dz, dz);
-    int bs = bin64(p.E0, p.n0, s2);
+    int bs = axis_bin64(p.ax[0], p.E0, p.n0, s2);
     if (bs < 0) return 0;
-    int bp = bin64(p.E1, p.n1, p2);
+    int bp = axis_bin64(p.ax[1], p.E1, p.n1, p2);
     if (bp < 0) return 0;
     return (bs + 1) * p.slots1 + bp + 1;
   } else {  // KRMU, midpoint line of sight, open
     double sx = __dsub_rn(bx, ax), sy = __dsub_rn(by, ay), sz = __dsub_rn(bz, az);
     double lx = __dadd_rn(ax, bx), ly = __dadd_rn(ay, by), lz = __dadd_rn(az, bz);
     double r2 = __dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz));
-    int br = bin64(p.E0, p.n0, r2);
+    int br = axis_bin64(p.ax[0], p.E0, p.n0, r2);
     if (br < 0) return 0;
     int bm = 0;
     if (r2 != 0.0) {
@@ -315,7 +360,18 @@ __device__ int slot64(const KParams &p, const PairDev &pd, int i, int j) {
       double sl = __dadd_rn(__dadd_rn(__dmul_rn(sx, lx), __dmul_rn(sy, ly)), __dmul_rn(sz, lz));
       double q = __dmul_rn(sl, sl);
       double den = __dmul_rn(r2, l2);
-      bm = mubin64(p.E1, p.n1, q, den);
+      if (p.ax[1].mode != kArith) {
+        bm = mubin64(p.E1, p.n1, q, den);
+      } else if (__double2hiint(den) == 0 && __double2loint(den) == 0) {
+        bm = p.n1 - 1;  // q = den = 0: every edge test holds
+      } else {
+        // uniform mu edges from 0: the edge nearest the FP32 estimate of
+        // mu = sqrt(q / den) decides with one canonical test
+        const float mu = sqrtf(approx_f32(q) / approx_f32(den));
+        const int k = arith_edge(mu, p.ax[1].inv, p.n1);
+        bm = (q >= __dmul_rn(p.E1[k], den)) ? k : k - 1;
+        bm = min(max(bm, 0), p.n1 - 1);
+      }
     }
     return (br + 1) * p.slots1 + bm + 1;
   }

@@ -44,8 +44,9 @@ struct AxisPlan {
   int nb = 0;         // bins on the axis
   int band_off = 0;   // float2 offset of this axis's bands in the band table
   int nband = 0;      // bands of this axis (nb + 3: none, one per edge, always)
-  // kArith: t = x * inv + cst (cst already holds -e0/delta - 1/2), clamped to
-  // [tlo, thi]; the bin is rint(t) and the pair is near an edge when
+  // kArith: t = x * inv + cst (cst already holds -e0/delta - 1/2), clamped
+  // above to thi (tlo is the planner's bookkeeping only);
+  // the bin is rint(t) and the pair is near an edge when
   // |t - rint(t)| + thr >= 1/2, with thr = thr_a / x_r + thr_b for mu
   // (x_r the pair's r) and thr_b alone for the other axes.
   float inv = 0, cst = 0, tlo = 0, thi = 0, thr_a = 0, thr_b = 0;
@@ -53,6 +54,8 @@ struct AxisPlan {
   // mu: 1/2 - thr_b - 2^-22 rounded down; near when |h| >= near_c - thr_a * rr
   // (one FMA, its rounding covered by the 2^-22)
   float near_c = 0;
+  // (sigma, pi), axis 1: near_at(axis 0) / near_at(axis 1) rounded up
+  float near_scale = 1;
 };
 
 // Kinds as the kernels see them.

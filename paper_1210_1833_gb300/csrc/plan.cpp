@@ -392,6 +392,9 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
       P0.near_at = f32_down(0.5 - (double)P0.thr_b);
       P1.near_at = f32_down(0.5 - (double)P1.thr_b);
       P1.near_c = f32_down(0.5 - (double)P1.thr_b - std::ldexp(1.0, -22));
+      // (sigma, pi): |h1| * near_scale >= near_at of axis 0 whenever
+      // |h1| >= near_at of axis 1 (one threshold for both axes)
+      if (kind == KSIGPI) P1.near_scale = f32_up((double)P0.near_at / (double)P1.near_at);
       out.ax[0] = P0;
       out.ax[1] = two_d ? P1 : AxisPlan();
       out.lut.clear();

@@ -118,6 +118,29 @@ def test_trimmed_stencils_2d(ctx, cpr):
                                    L=b.L, cells=True))
 
 
+@pytest.mark.parametrize("hp", [2, 4])
+def test_home_per_lane_all_kinds(ctx, hp):
+    """Each home-objects-per-lane width is its own kernel instantiation:
+    (r, mu), (sigma, pi) and theta counts at 2 and 4 home objects per
+    lane, with chunk tails that leave padded home slots."""
+    table = ctx.table_binning if hasattr(ctx, "table_binning") else False
+    ctx.set_launch(home_per_lane=hp, table_binning=table)
+    try:
+        w = synthetic.c2_rmu_lightcone(scale=0.004)
+        got = gpu_count(ctx, "rmu", w.data, w.randoms, w.edges0, w.edges1)
+        _assert_same(got, oracle_count("rmu", w.data, w.randoms, w.edges0, w.edges1, cells=True))
+        b = synthetic.c4_batched_sigpi(n_boxes=1, scale=0.03)[0]
+        got = gpu_count(ctx, "sigpi", b.data, None, b.edges0, b.edges1, periodic=True, L=b.L)
+        _assert_same(got, oracle_count("sigpi", b.data, None, b.edges0, b.edges1, periodic=True,
+                                       L=b.L, cells=True))
+        a = synthetic.c3_angular(scale=0.0005)
+        chord = oracle.theta_to_chord(a.extra["theta_deg"])
+        got = gpu_count(ctx, "theta", a.data, a.randoms, chord)
+        _assert_same(got, oracle_count("theta", a.data, a.randoms, chord, cells=True))
+    finally:
+        ctx.set_launch(table_binning=table)
+
+
 def test_theta_small(ctx):
     w = synthetic.c3_angular(scale=0.0008)
     chord = oracle.theta_to_chord(w.extra["theta_deg"])
