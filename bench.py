@@ -228,7 +228,7 @@ def run_gpu(args, w, rank, world):
     d_pin = torch.from_numpy(w.data).pin_memory()
     r_pin = torch.from_numpy(w.randoms).pin_memory()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")  # 256 MB
-    state = {"cand": 0, "kms": [], "rr_cand": 0, "rr_ms": [], "inrange": 0, "rechecked": 0,
+    state = {"cand": 0, "kms": [], "rr_cand": 0, "rr_ms": [], "inrange": 0, "rechecked": 0, "fp64": 0,
              "slots": 0, "per": {}}
 
     def step(dsrc, rsrc, record):
@@ -248,6 +248,7 @@ def run_gpu(args, w, rank, world):
                 state["kms"].append(st["kernel_ms"])
                 state["per"].setdefault(name, []).append(st["kernel_ms"])
                 state["rechecked"] += st["rechecked_pairs"]
+                state["fp64"] += st["fp64_pairs"]
                 state["slots"] += st["pair_slots"]
                 state["inrange"] += int(c.sum())
                 if name == "RR":
@@ -350,6 +351,7 @@ def run_gpu(args, w, rank, world):
                   "all_pairs_per_s": world * total_pairs(nd, nr) / (ms / 1e3),
                   "count_kernel_ms": {k: float(np.mean(v)) for k, v in state["per"].items()},
                   "rechecked_fraction": state["rechecked"] / max(1, state["cand"]),
+                  "fp64_fraction": state["fp64"] / max(1, state["cand"]),
                   "slot_utilisation": state["cand"] / max(1, state["slots"]),
                   "count_kernel_ms_per_step": float(np.sum(state["kms"])) / args.steps},
         "roofline": {"bound": "alu", "kernel": "k_count<R_MU> (RR)", "achieved": achieved,

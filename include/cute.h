@@ -203,7 +203,9 @@ cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_desc *d, uin
 /* Statistics of the last count call on ctx. */
 typedef struct {
   uint64_t candidate_pairs; /* pairs examined by the FP32 path              */
-  uint64_t rechecked_pairs; /* of those, re-tested in FP64 near an edge     */
+  uint64_t rechecked_pairs; /* of those, re-tested near an edge            */
+  uint64_t fp64_pairs;      /* of those, decided by the FP64 formula (the
+                               double-float stage left them open)          */
   uint64_t pair_slots;      /* (home, neighbour) slots the kernel evaluated,
                                including empty and padding slots            */
   uint64_t work_items;      /* (home chunk, neighbour slice) items run      */

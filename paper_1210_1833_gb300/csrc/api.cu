@@ -4,6 +4,7 @@
 // the binning plan and the work list, launches the persistent counting
 // kernel and copies the histograms out.
 #include "cute_internal.h"
+#include "df_stage.h"
 #include "count_kernel.cuh"
 
 #include <algorithm>
@@ -249,9 +250,10 @@ cute_status cute_last_stats(cute_ctx *ctx, cute_stats *out) {
   ENTER(ctx);
   if (!out) return fail(ctx, CUTE_E_INVALID, "out is NULL");
   CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
-  unsigned long long h[kCounterWords] = {0, 0, 0, 0, 0, 0};
+  unsigned long long h[kCounterWords] = {0, 0, 0, 0, 0, 0, 0};
   CUDA_OR_FAIL(cudaMemcpy(h, ctx->d_ticket, sizeof(h), cudaMemcpyDeviceToHost));
   ctx->stats.rechecked_pairs = h[1];
+  ctx->stats.fp64_pairs = h[6];
   ctx->stats.work_items = h[2];
   ctx->stats.pair_slots = h[4];
   ctx->stats.candidate_pairs = h[5];
@@ -325,6 +327,40 @@ cute_status validate_desc(cute_ctx *ctx, const cute_pair_desc *d, DescInfo &di) 
 
 static const double kU32 = 5.9604644775390625e-08;
 
+// largest separation component that can decide a bin: the top edge of r,
+// chord or sigma, and of pi
+double decision_reach(const cute_pair_desc *d) {
+  double r = d->edges0[d->n0];
+  if (d->kind == CUTE_SIGMA_PI) r = std::max(r, d->edges1[d->n1]);
+  return r;
+}
+
+// The double-float view of a pair set: remainders, and the error bounds of
+// its separation and line-of-sight components (df_stage.h).
+PairDF pair_df(const DescInfo &di) {
+  const Geometry &g = *di.g;
+  PairDF f;
+  std::memset(&f, 0, sizeof(f));
+  f.loA = di.A->d_lo;
+  f.loB = di.B->d_lo;
+  double xm = std::max(g.xmax[0], std::max(g.xmax[1], g.xmax[2]));
+  double fom = std::max(std::fabs(g.fo[0]), std::max(std::fabs(g.fo[1]), std::fabs(g.fo[2])));
+  double am = std::max(g.absmax[0], std::max(g.absmax[1], g.absmax[2]));
+  const double Lp = g.periodic ? g.L : 0.0;
+  f.eta = (float)dfs::eta_sep(xm, Lp);
+  f.eta_l = (float)dfs::eta_los(xm, fom, am);
+  if (g.periodic) {
+    f.Lh = (float)g.L;
+    f.Ll = (float)(g.L - (double)f.Lh);
+  }
+  for (int k = 0; k < 3; k++) {
+    const double t = 2.0 * g.fo[k];
+    f.fo2h[k] = (float)t;
+    f.fo2l[k] = (float)(t - (double)f.fo2h[k]);
+  }
+  return f;
+}
+
 ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax) {
   ErrorParams ep{0, 0, 0};
   double absmax = 0, rmin = 1e300;
@@ -332,8 +368,15 @@ ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax) {
     const Geometry &g = *di.g;
     double xm = std::max(g.xmax[0], std::max(g.xmax[1], g.xmax[2]));
     double e;
-    if (g.periodic) e = kU32 * (3.0 * xm + 2.0 * g.L) * 1.01 + 1e-12 * (xm + g.L);
-    else e = kU32 * 2.0 * xm * 1.01 + 1e-12 * xm;
+    if (g.periodic) {
+      // per component of d = q - (a - S): FP32 frame offsets of both objects
+      // (|q|, |a| <= xm), the home's image a - S (|a - S| <= |q| + |d|, and
+      // only |d| up to the reach decides a bin), the FP32 box size L32 = S
+      const double dL = std::fabs((double)(float)g.L - g.L);
+      e = kU32 * (3.0 * xm + 2.0 * rmax) * 1.01 + dL * 1.01 + 1e-12 * (xm + g.L);
+    } else {
+      e = kU32 * 2.0 * xm * 1.01 + 1e-12 * xm;
+    }
     ep.eta0 = std::max(ep.eta0, e);
     absmax = std::max(absmax, std::max(g.absmax[0], std::max(g.absmax[1], g.absmax[2])));
     rmin = std::min(rmin, g.rmin);
@@ -371,6 +414,8 @@ cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &
   CUDA_OR_FAIL(up((void **)&P->d_band, P->band.data(), P->band.size() * 4));
   CUDA_OR_FAIL(up((void **)&P->d_E0, P->E0.data(), P->E0.size() * 8));
   CUDA_OR_FAIL(up((void **)&P->d_E1, P->E1.data(), P->E1.size() * 8));
+  CUDA_OR_FAIL(up((void **)&P->d_E0df, P->E0df.data(), P->E0df.size() * 4));
+  CUDA_OR_FAIL(up((void **)&P->d_E1df, P->E1df.data(), P->E1df.size() * 4));
   ctx->plans[key.str()] = P;
   out = P;
   return CUTE_OK;
@@ -411,6 +456,7 @@ cute_status get_work(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, in
   }
   T->nentries = (int)entries;
   CUDA_OR_FAIL(cudaMalloc((void **)&T->d_chunks, std::max<size_t>(nch, 1) * sizeof(int4)));
+  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_pdf, dis.size() * sizeof(PairDF)));
   CUDA_OR_FAIL(cudaMalloc((void **)&T->d_stencil, std::max<size_t>(nst, 1) * sizeof(int4)));
   size_t oc = 0, os = 0;
   for (size_t i = 0; i < dis.size(); i++) {
@@ -428,6 +474,8 @@ cute_status get_work(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, in
     pd.is_auto = di.is_auto;
     pd.L32 = (float)di.g->L;
     pd.L64 = di.g->periodic ? di.g->L : 0.0;
+    pd.df = T->d_pdf + i;
+    T->pdf.push_back(pair_df(di));
     PairWork pw;
     std::memset(&pw, 0, sizeof(pw));
     pw.chunks = T->d_chunks + oc;
@@ -452,6 +500,8 @@ cute_status get_work(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, in
     oc += chunks[i].size();
     os += stencils[i].size();
   }
+  CUDA_OR_FAIL(cudaMemcpyAsync(T->d_pdf, T->pdf.data(), T->pdf.size() * sizeof(PairDF),
+                               cudaMemcpyHostToDevice, ctx->stream));
   CUDA_OR_FAIL(cudaMalloc((void **)&T->d_pairs, T->pairs.size() * sizeof(PairDev)));
   CUDA_OR_FAIL(cudaMemcpyAsync(T->d_pairs, T->pairs.data(), T->pairs.size() * sizeof(PairDev),
                                cudaMemcpyHostToDevice, ctx->stream));
@@ -523,7 +573,7 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
         return fail(ctx, CUTE_E_INVALID, "batched descriptors must share the boundary");
     }
   }
-  ErrorParams ep = error_params(pr.dis, d[0].edges0[d[0].n0]);
+  ErrorParams ep = error_params(pr.dis, decision_reach(&d[0]));
   // home objects per lane: 4 when home cells hold enough objects to fill
   // 128-object chunks, else 2
   pr.hp = ctx->hp_override;
@@ -577,6 +627,8 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
   p.mu_eps_base = P.mu_eps_base;
   p.E0 = P.d_E0;
   p.E1 = P.d_E1;
+  p.E0df = (const float2 *)P.d_E0df;
+  p.E1df = (const float2 *)P.d_E1df;
   p.n0 = P.n0;
   p.n1 = P.n1;
   p.slots1 = P.slots1;

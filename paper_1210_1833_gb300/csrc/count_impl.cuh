@@ -51,37 +51,37 @@ struct WarpSmem {
 };
 
 // ------------------------------------------------------------------ float-float
-// Error-free transformations (Knuth's TwoSum, Dekker/Kahan's FastTwoSum,
-// and the FMA form of TwoProduct); the pair (hi, lo) represents hi + lo.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  const float bp = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
-}
-// (hi, lo) += (ph + pl) with renormalisation
+// The pair (hi, lo) represents hi + lo.  (hi, lo) += (ph + pl): Knuth's
+// TwoSum (df_stage.h), then Dekker/Kahan's FastTwoSum to renormalise.
 __device__ __forceinline__ void ff_add(float &hi, float &lo, float ph, float pl) {
   float s, e;
-  two_sum(hi, ph, s, e);
+  dfs::two_sum(hi, ph, s, e);
   const float t = __fadd_rn(lo, __fadd_rn(e, pl));
   hi = __fadd_rn(s, t);
   lo = __fsub_rn(t, __fsub_rn(hi, s));
 }
 
 // ------------------------------------------------------------------ queue
-// Warp-cooperative FP64 re-test of queued pairs, 32 at a time (all of them
-// when draining).  Every lane must call it.
+// Warp-cooperative re-test of queued pairs, 32 at a time (all of them when
+// draining): the double-float stage, then the FP64 formula for the pairs
+// it leaves open.  Every lane must call it.
 template <int KIND, int ACC>
 __device__ __noinline__ void process_queue(const KParams &p, const PairDev &pd, const WarpSmem &w,
                                            int lane, bool drain) {
   __syncwarp();
   int n = *w.qcnt;
   int done = 0;
+  unsigned fp64 = 0;
   const int nb = p.n0 * p.n1;
   while (n >= 32 || (drain && n > 0)) {
     int take = min(n, 32);
     if (lane < take) {
       int2 e = w.queue[n - take + lane];
-      int s = slot64<KIND>(p, pd, e.x, e.y);
+      int s;
+      if (!slot_df<KIND>(p, pd, e.x, e.y, s)) {
+        s = slot64<KIND>(p, pd, e.x, e.y);
+        fp64++;
+      }
       int s0 = s / p.slots1, s1 = s - s0 * p.slots1;
       bool in = s0 >= 1 && s0 <= p.n0 && (p.slots1 == 1 || (s1 >= 1 && s1 <= p.n1));
       int b = (s0 - 1) * p.n1 + (p.slots1 == 1 ? 0 : s1 - 1);
@@ -99,6 +99,7 @@ __device__ __noinline__ void process_queue(const KParams &p, const PairDev &pd, 
     done += take;
   }
   __syncwarp();
+  if (fp64) atomicAdd(&p.stats[5], (unsigned long long)fp64);
   if (lane == 0) {
     *w.qcnt = n;
     if (done) atomicAdd(&p.stats[0], (unsigned long long)done);
@@ -475,8 +476,8 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
     } else {
       flagged = __any_sync(kFull, nmask != 0u);
     }
-    // rare: pairs inside an edge's error band join the warp's FP64 queue; the
-    // queue only grows here, so it is drained here when it holds 32
+    // rare: pairs inside an edge's error band join the warp's re-test queue;
+    // the queue only grows here, so it is drained here when it holds 32
     if (flagged) {
 #pragma unroll
       for (int k = 0; k < NP; k++) {

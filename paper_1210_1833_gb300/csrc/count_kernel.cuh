@@ -21,6 +21,7 @@
 #pragma once
 
 #include "cute_internal.h"
+#include "df_stage.h"
 
 namespace cute {
 
@@ -375,6 +376,32 @@ __device__ int slot64(const KParams &p, const PairDev &pd, int i, int j) {
     }
     return (br + 1) * p.slots1 + bm + 1;
   }
+}
+
+// ---- double-float first stage of the re-test (df_stage.h): the slot of
+// pair (i, j) when the stage decides it; false when it leaves a decision
+// open (or an axis uses tables), the FP64 formula then decides.
+template <int KIND>
+__device__ bool slot_df(const KParams &p, const PairDev &pd, int i, int j, int &slot) {
+  if (p.ax[0].mode != kArith || ((KIND == KSIGPI || KIND == KRMU) && p.ax[1].mode != kArith))
+    return false;
+  const PairDF &f = *pd.df;
+  const float4 a = pd.posA[i], b = pd.posB[j], la = f.loA[i], lb = f.loB[j];
+  const float pa[3] = {a.x, a.y, a.z}, pb[3] = {b.x, b.y, b.z};
+  const float lav[3] = {la.x, la.y, la.z}, lbv[3] = {lb.x, lb.y, lb.z};
+  const float *E0 = (const float *)p.E0df, *E1 = (const float *)p.E1df;
+  int s;
+  if (KIND == KMONO || KIND == KTHETA)
+    s = dfs::mono_slot(pa, lav, pb, lbv, f.eta, f.Lh, f.Ll, p.ax[0].inv, E0, p.n0);
+  else if (KIND == KSIGPI)
+    s = dfs::sigpi_slot(pa, lav, pb, lbv, f.eta, f.Lh, f.Ll, p.ax[0].inv, E0, p.n0, p.ax[1].inv,
+                        E1, p.n1);
+  else
+    s = dfs::rmu_slot(pa, lav, pb, lbv, f.eta, f.eta_l, f.fo2h, f.fo2l, p.ax[0].inv, E0, p.n0,
+                      p.ax[1].inv, E1, p.n1);
+  if (s == -2) return false;
+  slot = s;
+  return true;
 }
 
 }  // namespace cute

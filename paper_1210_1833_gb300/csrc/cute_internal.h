@@ -74,14 +74,27 @@ constexpr int KMONO = 0, KRMU = 1, KSIGPI = 2, KTHETA = 3;
 //   stencil row int4: (dy, dz, kxr, 1 on the home row)
 constexpr int kSegSelf = 1;        // only j > i (unique pairs of a run with itself)
 constexpr int kSegNoSelfPair = 2;  // every j != i (full-stencil adjoint of an auto count)
-constexpr int kCounterWords = 6;  // work ticket + 5 statistics words
+constexpr int kCounterWords = 7;  // work ticket + 6 statistics words
 constexpr int kModeCross = 0, kModeAutoHalf = 1, kModeAutoFull = 2;
 
 // One pair set (cat_a, cat_b) of a (possibly batched) count, as the
 // counting kernel sees it.
+// Double-float view of a pair set for the first stage of the re-test: the
+// FP32 frame offsets plus their FP32 remainders (pos + lo = x - fo to
+// about 2^-48 |x - fo|) and the absolute error bounds of the separation and
+// line-of-sight components formed from them.
+struct PairDF {
+  const float4 *loA, *loB;     // cell-sorted remainders (x, y, z, 0)
+  float eta;                   // bound on the error of a separation component
+  float eta_l;                 // R_MU: of a line-of-sight component (x_i + x_j)
+  float Lh, Ll;                // periodic box as hi + lo (0 when open)
+  float fo2h[3], fo2l[3];      // R_MU: twice the frame centre (observer frame), hi + lo
+};
+
 struct PairDev {
   const float4 *posA, *posB;   // cell-sorted FP32 (x, y, z, w), grid frame
   const double *sA, *sB;       // cell-sorted FP64 SoA (x[n], y[n], z[n])
+  const PairDF *df;            // double-float view (re-test first stage)
   const int32_t *permA;        // cell-sorted index -> upload index of A
   int32_t nA, nB;
   int32_t out;                 // output histogram index
@@ -113,6 +126,7 @@ struct KParams {
   int band_words;              // float2 entries in band
   float mu_eps_base;           // R_MU: mu error bound of class 0 (class c: x 2^c)
   const double *E0, *E1;       // FP64 squared edges (mu: squared mu edges)
+  const float2 *E0df, *E1df;   // the same as FP32 hi + lo
   int n0, n1;                  // bins per axis (n1 = 1 for 1-D kinds)
   int slots1;                  // axis-1 slots (n1 + 2), 1 for 1-D kinds
   int nslots;                  // (n0 + 2) * slots1
@@ -122,7 +136,7 @@ struct KParams {
   double *out_wsum;                // [nout][n0 * n1] or null
   unsigned long long *ticket;      // work-item counter
   unsigned long long *stats;       // [0] rechecked, [1] items, [2] near-band, [3] pair slots,
-                                   // [4] candidate pairs
+                                   // [4] candidate pairs, [5] decided by the FP64 formula
   // (ticket and stats are kCounterWords consecutive words, zeroed per launch)
   int *err;                        // first error code seen by a kernel
   // adjoint
@@ -144,7 +158,8 @@ struct Geometry {
   int k[3] = {1, 1, 1};       // cells per reach on each axis
   int kreq = 2;               // cells per reach requested
   double reach[3] = {0, 0, 0};
-  double xmax[3] = {0, 0, 0}; // largest |x - origin| per axis over its catalogs
+  double xmax[3] = {0, 0, 0}; // largest |x - fo| per axis over its catalogs
+  double fo[3] = {0, 0, 0};   // centre of the FP32 frame
   double absmax[3] = {0, 0, 0}; // largest |x| (observer frame) per axis
   double rmin = 0;            // smallest |x| over its catalogs (observer frame)
   long long version = 0;
@@ -163,6 +178,7 @@ struct Catalog {
   int geom = -1;
   long long grid_version = 0;
   float4 *d_pos = nullptr;     // sorted FP32
+  float4 *d_lo = nullptr;      // sorted FP32 remainders of the frame offsets
   double *d_s64 = nullptr;     // sorted FP64 SoA
   int32_t *d_perm = nullptr;   // sorted -> upload index
   int32_t *d_cell_start = nullptr;
@@ -178,11 +194,13 @@ struct Plan;  // binning plan (plan.cpp)
 // launch shape.
 struct WorkSet {
   std::vector<PairDev> pairs;
+  std::vector<PairDF> pdf;
   std::vector<PairWork> work;
   std::vector<int> ebase;          // npairs + 1
   int nentries = 0;
   int4 *d_chunks = nullptr, *d_stencil = nullptr;
   PairDev *d_pairs = nullptr;
+  PairDF *d_pdf = nullptr;
   PairWork *d_work = nullptr;
   int *d_ebase = nullptr;
   int *d_cnt = nullptr;            // items per entry
@@ -194,6 +212,7 @@ struct WorkSet {
     cudaFree(d_chunks);
     cudaFree(d_stencil);
     cudaFree(d_pairs);
+    cudaFree(d_pdf);
     cudaFree(d_work);
     cudaFree(d_ebase);
     cudaFree(d_cnt);
@@ -262,6 +281,8 @@ struct Plan {
   uint32_t *d_lut = nullptr;
   float *d_band = nullptr;
   double *d_E0 = nullptr, *d_E1 = nullptr;
+  std::vector<float> E0df, E1df;    // (hi, lo) per edge
+  float *d_E0df = nullptr, *d_E1df = nullptr;
   ~Plan();
 };
 
@@ -287,6 +308,8 @@ struct DescInfo {
 cute_status validate_desc(cute_ctx *ctx, const cute_pair_desc *d, DescInfo &di);
 double row_density(const Catalog &A, const Geometry &g);
 ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax);
+double decision_reach(const cute_pair_desc *d);
+PairDF pair_df(const DescInfo &di);
 
 // Home chunks of catalog A (plan.cpp): each row of cells cut into chunks of
 // home_chunk objects (the last one of a row shorter), spanning at most

@@ -173,17 +173,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restri
 __global__ void k_scatter(const double *__restrict__ xyz, const float *__restrict__ w, int n,
                           GridDev g, const int *__restrict__ cid, const int *__restrict__ rank,
                           const int *__restrict__ start, float4 *__restrict__ pos,
-                          double *__restrict__ s64, int *__restrict__ perm) {
+                          float4 *__restrict__ lo, double *__restrict__ s64,
+                          int *__restrict__ perm) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int d = start[cid[i]] + rank[i];
   double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+  // FP32 frame offsets and their remainders (offset - FP32 offset is exact
+  // in FP64; its FP32 rounding leaves pos + lo within 2^-48 of the offset)
+  const double ox = x - g.fo[0], oy = y - g.fo[1], oz = z - g.fo[2];
   float4 p;
-  p.x = (float)(x - g.fo[0]);
-  p.y = (float)(y - g.fo[1]);
-  p.z = (float)(z - g.fo[2]);
+  p.x = (float)ox;
+  p.y = (float)oy;
+  p.z = (float)oz;
   p.w = w ? w[i] : 1.0f;
   pos[d] = p;
+  lo[d] = make_float4((float)(ox - (double)p.x), (float)(oy - (double)p.y),
+                      (float)(oz - (double)p.z), 0.0f);
   s64[d] = x;
   s64[(size_t)n + d] = y;
   s64[2 * (size_t)n + d] = z;
@@ -273,6 +279,7 @@ cute_status catalog_stage(cute_ctx *ctx, Catalog &c, const double *xyz, const fl
 
 static void free_grid(Catalog &c) {
   cudaFree(c.d_pos); c.d_pos = nullptr;
+  cudaFree(c.d_lo); c.d_lo = nullptr;
   cudaFree(c.d_s64); c.d_s64 = nullptr;
   cudaFree(c.d_perm); c.d_perm = nullptr;
   cudaFree(c.d_cell_start); c.d_cell_start = nullptr;
@@ -376,6 +383,7 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
     gd.nc[k] = g.nc[k];
     gd.fo[k] = g.periodic ? 0.5 * g.L : 0.5 * (lo[k] + hi[k]);
     if (!any) gd.fo[k] = 0;
+    g.fo[k] = gd.fo[k];
   }
   // the FP32 frame spans at most xmax from its centre on each axis
   for (Catalog *c : cats) {
@@ -384,6 +392,7 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
     CUDA_OR_FAIL(cudaMalloc(&c->d_cell_start, sizeof(int) * (size_t)(ncell + 1)));
     if (n > 0) {
       CUDA_OR_FAIL(cudaMalloc(&c->d_pos, sizeof(float4) * (size_t)n));
+      CUDA_OR_FAIL(cudaMalloc(&c->d_lo, sizeof(float4) * (size_t)n));
       CUDA_OR_FAIL(cudaMalloc(&c->d_s64, sizeof(double) * 3 * (size_t)n));
       CUDA_OR_FAIL(cudaMalloc(&c->d_perm, sizeof(int) * (size_t)n));
     }
@@ -406,8 +415,8 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
     CUDA_OR_FAIL(cudaGetLastError());
     if (n > 0) {
       k_scatter<<<(n + 255) / 256, 256, 0, ctx->stream>>>(c->d_xyz, c->d_w, n, gd, cid, rank,
-                                                          c->d_cell_start, c->d_pos, c->d_s64,
-                                                          c->d_perm);
+                                                          c->d_cell_start, c->d_pos, c->d_lo,
+                                                          c->d_s64, c->d_perm);
       CUDA_OR_FAIL(cudaGetLastError());
     }
     c->h_cell_start.resize(ncell + 1);

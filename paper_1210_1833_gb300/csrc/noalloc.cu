@@ -95,7 +95,7 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   const bool two_d = (kind == CUTE_R_MU || kind == CUTE_SIGMA_PI);
   const int acc = d->weighted ? 1 : 0;
   std::vector<DescInfo> dis(1, di);
-  ErrorParams ep = error_params(dis, d->edges0[d->n0]);
+  ErrorParams ep = error_params(dis, decision_reach(d));
 
   int hp = ctx->hp_override;
   if (!hp) hp = row_density(*di.A, *di.g) < 2000.0 ? 2 : 4;
@@ -146,28 +146,37 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
           items.push_back(item_record(c.x, c.y, sg[k], js, std::min(js + slice, sg[k].j1), 0));
     }
 
-  // scratch layout: counters | pair | item records | tables | bands | edges
+  // scratch layout: counters | pair | double-float pair | item records |
+  // tables | bands | edges (FP64, then hi + lo)
   const size_t o_cnt = 0;
   const size_t o_pair = na_align(o_cnt + kCounterWords * sizeof(unsigned long long));
-  const size_t o_items = na_align(o_pair + sizeof(PairDev));
+  const size_t o_pdf = na_align(o_pair + sizeof(PairDev));
+  const size_t o_items = na_align(o_pdf + sizeof(PairDF));
   const size_t o_lut = na_align(o_items + items.size() * sizeof(int4));
   const size_t o_band = na_align(o_lut + P.lut.size() * sizeof(uint32_t));
   const size_t o_e0 = na_align(o_band + P.band.size() * sizeof(float));
   const size_t o_e1 = na_align(o_e0 + P.E0.size() * sizeof(double));
-  const size_t total = na_align(o_e1 + P.E1.size() * sizeof(double));
+  const size_t o_e0df = na_align(o_e1 + P.E1.size() * sizeof(double));
+  const size_t o_e1df = na_align(o_e0df + P.E0df.size() * sizeof(float));
+  const size_t total = na_align(o_e1df + P.E1df.size() * sizeof(float));
   if (total > kNoAllocScratchBytes)
     return na_fail(ctx, CUTE_E_INVALID,
                    "request needs " + std::to_string(total) +
                        " bytes of scratch; cute_count_pairs_noalloc has 8 MiB (use fewer work "
                        "items: smaller catalogs, or cute_count_pairs)");
   unsigned char *dev = (unsigned char *)base;
+  pd.df = (const PairDF *)(dev + o_pdf);
+  const PairDF pdf = pair_df(di);
   std::vector<unsigned char> img(total, 0);  // counters start at zero
   std::memcpy(img.data() + o_pair, &pd, sizeof(PairDev));
+  std::memcpy(img.data() + o_pdf, &pdf, sizeof(PairDF));
   std::memcpy(img.data() + o_items, items.data(), items.size() * sizeof(int4));
   std::memcpy(img.data() + o_lut, P.lut.data(), P.lut.size() * sizeof(uint32_t));
   std::memcpy(img.data() + o_band, P.band.data(), P.band.size() * sizeof(float));
   std::memcpy(img.data() + o_e0, P.E0.data(), P.E0.size() * sizeof(double));
   std::memcpy(img.data() + o_e1, P.E1.data(), P.E1.size() * sizeof(double));
+  std::memcpy(img.data() + o_e0df, P.E0df.data(), P.E0df.size() * sizeof(float));
+  std::memcpy(img.data() + o_e1df, P.E1df.data(), P.E1df.size() * sizeof(float));
   NA_CUDA(cudaMemcpyAsync(dev, img.data(), total, cudaMemcpyHostToDevice, ctx->stream));
 
   const int nb = P.n0 * P.n1;
@@ -188,6 +197,8 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   p.mu_eps_base = P.mu_eps_base;
   p.E0 = (const double *)(dev + o_e0);
   p.E1 = (const double *)(dev + o_e1);
+  p.E0df = (const float2 *)(dev + o_e0df);
+  p.E1df = (const float2 *)(dev + o_e1df);
   p.n0 = P.n0;
   p.n1 = P.n1;
   p.slots1 = P.slots1;

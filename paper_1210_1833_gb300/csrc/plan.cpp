@@ -53,6 +53,8 @@ Plan::~Plan() {
   if (d_band) cudaFree(d_band);
   if (d_E0) cudaFree(d_E0);
   if (d_E1) cudaFree(d_E1);
+  if (d_E0df) cudaFree(d_E0df);
+  if (d_E1df) cudaFree(d_E1df);
 }
 
 // ------------------------------------------------------------------ error models
@@ -340,6 +342,18 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
   } else {
     out.E1.assign(2, 0.0);
   }
+  // the squared edges as FP32 hi + lo (E - hi is exact in FP64; lo holds
+  // it to 2^-24, so hi + lo is within 2^-48 E of E)
+  auto split = [](const std::vector<double> &E, std::vector<float> &out2) {
+    out2.resize(2 * E.size());
+    for (size_t k = 0; k < E.size(); k++) {
+      const float h = (float)E[k];
+      out2[2 * k] = h;
+      out2[2 * k + 1] = (float)(E[k] - (double)h);
+    }
+  };
+  split(out.E0, out.E0df);
+  split(out.E1, out.E1df);
 
   // axis specifications
   AxisSpec A0, A1;

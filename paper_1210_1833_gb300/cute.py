@@ -61,6 +61,7 @@ class Cosmology(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("candidate_pairs", ctypes.c_uint64), ("rechecked_pairs", ctypes.c_uint64),
+                ("fp64_pairs", ctypes.c_uint64),
                 ("pair_slots", ctypes.c_uint64), ("work_items", ctypes.c_uint64), ("launches", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("blocks", ctypes.c_int32),
                 ("home_per_lane", ctypes.c_int32), ("kernel_ms", ctypes.c_float)]

@@ -35,10 +35,13 @@ def oracle_count(kind, a, b=None, e0=None, e1=None, periodic=False, L=0.0, cells
 
 
 def edge_pairs_mono(rng, edges, n_per_edge, box=None, scale_eps=(0.0, 2.0**-40, -2.0**-40,
-                                                                   2.0**-30, -2.0**-30, 2.0**-22,
-                                                                   -2.0**-22)):
+                                                                   2.0**-36, -2.0**-36, 2.0**-34,
+                                                                   -2.0**-34, 2.0**-30, -2.0**-30,
+                                                                   2.0**-22, -2.0**-22)):
     """Points placed in pairs whose separations sit exactly on (or within a
-    hair of) every bin edge: the pairs the FP32 path must hand to FP64."""
+    hair of) every bin edge: the pairs the FP32 path must hand to the
+    re-test, on both sides of the double-float stage's margin (about 2^-36
+    relative) and of the FP32 error band."""
     pts = []
     for e in edges:
         if e <= 0:
@@ -63,7 +66,8 @@ def edge_pairs_mu(rng, mu_edges, r, n_per_edge, dist=1500.0):
     pts = []
     for m in mu_edges:
         for _ in range(n_per_edge):
-            for d in (0.0, 2.0**-40, -2.0**-40, 2.0**-28, -2.0**-28):
+            for d in (0.0, 2.0**-40, -2.0**-40, 2.0**-36, -2.0**-36, 2.0**-33, -2.0**-33,
+                      2.0**-28, -2.0**-28):
                 xi = rng.normal(size=3)
                 xi = xi / np.linalg.norm(xi) * dist
                 t = rng.normal(size=3)

@@ -162,6 +162,39 @@ def test_pairs_on_edges_mono(ctx):
                  oracle_count("mono", xb, None, ep, periodic=True, L=100.0))
     st = ctx.stats()
     assert st["rechecked_pairs"] > 0
+    # pairs exactly on edges need the FP64 formula; with uniform edges the
+    # double-float stage decides the rest
+    assert st["fp64_pairs"] > 0
+    if not getattr(ctx, "table_binning", False):
+        assert st["fp64_pairs"] < st["rechecked_pairs"]
+
+
+def test_pairs_on_edges_sigpi(ctx):
+    """(sigma, pi) pairs on (and a hair off) every sigma edge and every pi
+    edge, open and periodic."""
+    rng = np.random.default_rng(106)
+    es, ep = np.arange(16) * 2.0, np.arange(11) * 2.5
+    eps = (0.0, 2.0**-40, -2.0**-40, 2.0**-36, -2.0**-36, 2.0**-33, -2.0**-33, 2.0**-24,
+           -2.0**-24)
+    pts = []
+    for axis, edges in ((0, es), (1, ep)):
+        for e in edges[1:]:
+            for d in eps:
+                c = rng.uniform(20.0, 80.0, size=3)
+                phi = rng.uniform(0, 2 * np.pi)
+                if axis == 0:
+                    sig, pi = e * (1 + d), rng.uniform(0, ep[-1])
+                else:
+                    sig, pi = rng.uniform(0, es[-1]), e * (1 + d)
+                off = np.array([sig * np.cos(phi), sig * np.sin(phi), pi * rng.choice([-1, 1])])
+                pts += [c, c + off]
+    x = np.array(pts)
+    _assert_same(gpu_count(ctx, "sigpi", x, None, es, ep), oracle_count("sigpi", x, None, es, ep))
+    xb = np.mod(x + 55.0, 100.0)  # the same pairs, many across the box faces
+    xb[xb >= 100.0] = 0.0
+    _assert_same(gpu_count(ctx, "sigpi", xb, None, es, ep, periodic=True, L=100.0),
+                 oracle_count("sigpi", xb, None, es, ep, periodic=True, L=100.0))
+    assert ctx.stats()["fp64_pairs"] > 0
 
 
 def test_pairs_on_edges_mu(ctx):
@@ -170,6 +203,10 @@ def test_pairs_on_edges_mu(ctx):
     e1 = np.arange(41) / 40.0
     x = np.concatenate([edge_pairs_mu(rng, e1, r, 2) for r in (0.7, 3.0, 12.0, 77.0, 190.0)])
     _assert_same(gpu_count(ctx, "rmu", x, None, e0, e1), oracle_count("rmu", x, None, e0, e1))
+    st = ctx.stats()
+    assert st["fp64_pairs"] > 0
+    if not getattr(ctx, "table_binning", False):
+        assert st["fp64_pairs"] < st["rechecked_pairs"]
 
 
 def test_pairs_on_edges_theta(ctx):
@@ -187,6 +224,9 @@ def test_pairs_on_edges_theta(ctx):
             pts += [n1, n2 / np.linalg.norm(n2)]
     x = np.array(pts)
     _assert_same(gpu_count(ctx, "theta", x, None, chord), oracle_count("theta", x, None, chord))
+    # uniform chord edges (arithmetic binning and the double-float stage)
+    cu = np.linspace(0.0, chord[-1], 33)
+    _assert_same(gpu_count(ctx, "theta", x, None, cu), oracle_count("theta", x, None, cu))
 
 
 def test_periodic_faces_and_duplicates(ctx):
