@@ -109,7 +109,8 @@ def _kernel_hash():
     import glob
     import hashlib
     files = sorted(glob.glob(os.path.join(ROOT, "paper_1210_1833_gb300", "csrc", "count_*.cu*")) +
-                   [os.path.join(ROOT, "paper_1210_1833_gb300", "csrc", "cute_internal.h")])
+                   [os.path.join(ROOT, "paper_1210_1833_gb300", "csrc", f)
+                    for f in ("cute_internal.h", "df_stage.h")])
     h = hashlib.sha256()
     for f in files:
         h.update(open(f, "rb").read())
