@@ -11,6 +11,9 @@
 
 #include "count_kernel.cuh"
 
+#include <algorithm>
+#include <atomic>
+
 namespace cute {
 
 constexpr int kAccCount = 0, kAccWeighted = 1, kAccAdjoint = 2;
@@ -722,8 +725,21 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
 template <int KIND, bool PER, int HP, int ACC>
 cudaError_t launch_count_t(const KParams &p, int blocks, int threads, size_t smem, cudaStream_t st) {
   auto fn = k_count<KIND, PER, HP, ACC>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the shared-memory opt-in is a host call of a few microseconds: made once
+  // per instantiation and device, for the device's whole opt-in limit
+  static std::atomic<int> opted[kMaxDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices || !opted[dev].load()) {
+    int lim = 0;
+    e = cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             std::max(lim, (int)smem));
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kMaxDevices) opted[dev].store(1);
+  }
   fn<<<blocks, threads, smem, st>>>(p);
   return cudaGetLastError();
 }

@@ -75,6 +75,7 @@ constexpr int KMONO = 0, KRMU = 1, KSIGPI = 2, KTHETA = 3;
 constexpr int kSegSelf = 1;        // only j > i (unique pairs of a run with itself)
 constexpr int kSegNoSelfPair = 2;  // every j != i (full-stencil adjoint of an auto count)
 constexpr int kCounterWords = 7;  // work ticket + 6 statistics words
+constexpr int kMaxDevices = 64;   // per-device launch caches
 constexpr int kModeCross = 0, kModeAutoHalf = 1, kModeAutoFull = 2;
 
 // One pair set (cat_a, cat_b) of a (possibly batched) count, as the
