@@ -14,7 +14,7 @@
 
 namespace cute {
 cute_status catalog_stage(cute_ctx *ctx, Catalog &c, const double *xyz, const float *w);
-void catalog_release(Catalog &c);
+void catalog_release(cute_ctx *ctx, Catalog &c);
 cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const double reach[3],
                        int kreq);
 cute_status ensure_scratch(cute_ctx *ctx, size_t bytes);
@@ -96,6 +96,19 @@ cute_status cute_ctx_create(int device, void *cuda_stream, cute_ctx **out) {
     }
     ctx->own_stream = true;
   }
+  cudaMemPoolProps pp;
+  std::memset(&pp, 0, sizeof(pp));
+  pp.allocType = cudaMemAllocationTypePinned;
+  pp.location.type = cudaMemLocationTypeDevice;
+  pp.location.id = device;
+  uint64_t keep = UINT64_MAX;  // never trim the pool between requests
+  if (cudaMemPoolCreate(&ctx->pool, &pp) != cudaSuccess ||
+      cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->pool = nullptr;
+    cute_ctx_destroy(ctx);
+    return fail(nullptr, CUTE_E_UNSUPPORTED, "stream-ordered memory pools are not available");
+  }
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&ctx->d_ticket, 8 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess ||
@@ -115,11 +128,13 @@ cute_status cute_ctx_destroy(cute_ctx *ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ctx->plans.clear();
   ctx->clear_caches();
-  for (auto &kv : ctx->cats) catalog_release(kv.second);
+  for (auto &kv : ctx->cats) catalog_release(ctx, kv.second);
   ctx->cats.clear();
   cudaFree(ctx->d_ticket);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_scratch);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);  // pool blocks returned
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -162,7 +177,7 @@ cute_status cute_catalog_upload(cute_ctx *ctx, const double *xyz, const float *w
   cute_status st = catalog_stage(ctx, c, xyz, w);
   if (st != CUTE_OK) {
     std::string m = ctx->err;
-    catalog_release(c);
+    catalog_release(ctx, c);
     return fail(ctx, st, m);
   }
   ctx->cats[c.id] = c;
@@ -176,7 +191,7 @@ cute_status cute_catalog_free(cute_ctx *ctx, int32_t cat_id) {
   if (it == ctx->cats.end()) return fail(ctx, CUTE_E_STATE, "unknown catalog");
   CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
   ctx->clear_caches();
-  catalog_release(it->second);
+  catalog_release(ctx, it->second);
   ctx->cats.erase(it);
   return CUTE_OK;
 }
@@ -335,6 +350,13 @@ double decision_reach(const cute_pair_desc *d) {
   return r;
 }
 
+cudaError_t dev_alloc(cute_ctx *ctx, void **p, size_t bytes) {
+  return cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), ctx->pool, ctx->stream);
+}
+void dev_free(cute_ctx *ctx, void *p) {
+  if (p) cudaFreeAsync(p, ctx->stream);
+}
+
 // The double-float view of a pair set: remainders, and the error bounds of
 // its separation and line-of-sight components (df_stage.h).
 PairDF pair_df(const DescInfo &di) {
@@ -455,9 +477,10 @@ cute_status get_work(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, in
     T->ebase.push_back((int)entries);
   }
   T->nentries = (int)entries;
-  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_chunks, std::max<size_t>(nch, 1) * sizeof(int4)));
-  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_pdf, dis.size() * sizeof(PairDF)));
-  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_stencil, std::max<size_t>(nst, 1) * sizeof(int4)));
+  T->st = ctx->stream;
+  CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_chunks, std::max<size_t>(nch, 1) * sizeof(int4)));
+  CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_pdf, dis.size() * sizeof(PairDF)));
+  CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_stencil, std::max<size_t>(nst, 1) * sizeof(int4)));
   size_t oc = 0, os = 0;
   for (size_t i = 0; i < dis.size(); i++) {
     const DescInfo &di = dis[i];
@@ -502,25 +525,25 @@ cute_status get_work(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, in
   }
   CUDA_OR_FAIL(cudaMemcpyAsync(T->d_pdf, T->pdf.data(), T->pdf.size() * sizeof(PairDF),
                                cudaMemcpyHostToDevice, ctx->stream));
-  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_pairs, T->pairs.size() * sizeof(PairDev)));
+  CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_pairs, T->pairs.size() * sizeof(PairDev)));
   CUDA_OR_FAIL(cudaMemcpyAsync(T->d_pairs, T->pairs.data(), T->pairs.size() * sizeof(PairDev),
                                cudaMemcpyHostToDevice, ctx->stream));
-  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_work, T->work.size() * sizeof(PairWork)));
+  CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_work, T->work.size() * sizeof(PairWork)));
   CUDA_OR_FAIL(cudaMemcpyAsync(T->d_work, T->work.data(), T->work.size() * sizeof(PairWork),
                                cudaMemcpyHostToDevice, ctx->stream));
-  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_ebase, T->ebase.size() * sizeof(int)));
+  CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_ebase, T->ebase.size() * sizeof(int)));
   CUDA_OR_FAIL(cudaMemcpyAsync(T->d_ebase, T->ebase.data(), T->ebase.size() * sizeof(int),
                                cudaMemcpyHostToDevice, ctx->stream));
-  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_cnt, std::max(T->nentries, 1) * sizeof(int)));
-  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_bsum, work_bsum_words(T->nentries) * sizeof(long long)));
-  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_eprefix, (T->nentries + 1) * sizeof(long long)));
+  CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_cnt, std::max(T->nentries, 1) * sizeof(int)));
+  CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_bsum, work_bsum_words(T->nentries) * sizeof(long long)));
+  CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_eprefix, (T->nentries + 1) * sizeof(long long)));
   CUDA_OR_FAIL(work_count(T->d_work, T->d_ebase, (int)T->pairs.size(), T->nentries, slice,
                           T->d_cnt, T->d_bsum, T->d_eprefix, ctx->stream));
   // the item count sizes the record list: one round trip per work list
   CUDA_OR_FAIL(cudaMemcpyAsync(&T->items, T->d_eprefix + T->nentries, sizeof(long long),
                                cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
-  CUDA_OR_FAIL(cudaMalloc((void **)&T->d_items, std::max<long long>(T->items, 1) * sizeof(int4)));
+  CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_items, std::max<long long>(T->items, 1) * sizeof(int4)));
   CUDA_OR_FAIL(work_write(T->d_work, T->d_ebase, (int)T->pairs.size(), T->nentries, slice,
                           T->d_eprefix, T->d_items, ctx->stream));
   ctx->work_cache[key.str()] = T;

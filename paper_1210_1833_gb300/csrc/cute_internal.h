@@ -194,6 +194,7 @@ struct Plan;  // binning plan (plan.cpp)
 // and their prefix sums computed on the GPU.  Cached per set of catalogs and
 // launch shape.
 struct WorkSet {
+  cudaStream_t st = nullptr;       // the context's stream: device arrays are pool blocks
   std::vector<PairDev> pairs;
   std::vector<PairDF> pdf;
   std::vector<PairWork> work;
@@ -210,16 +211,10 @@ struct WorkSet {
   long long items = 0;             // work items
   int4 *d_items = nullptr;         // their records
   ~WorkSet() {
-    cudaFree(d_chunks);
-    cudaFree(d_stencil);
-    cudaFree(d_pairs);
-    cudaFree(d_pdf);
-    cudaFree(d_work);
-    cudaFree(d_ebase);
-    cudaFree(d_cnt);
-    cudaFree(d_bsum);
-    cudaFree(d_eprefix);
-    cudaFree(d_items);
+    for (void *q : {(void *)d_chunks, (void *)d_stencil, (void *)d_pairs, (void *)d_pdf,
+                    (void *)d_work, (void *)d_ebase, (void *)d_cnt, (void *)d_bsum,
+                    (void *)d_eprefix, (void *)d_items})
+      if (q) cudaFreeAsync(q, st);
   }
 };
 
@@ -229,6 +224,10 @@ struct cute_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // stream-ordered pool for catalogs, grids and work lists: freed blocks stay
+  // cached for the next request (no synchronising cudaMalloc/cudaFree per
+  // upload, grid or count)
+  cudaMemPool_t pool = nullptr;
   int sm_count = 0;
   size_t smem_optin = 0;
   std::string err;
@@ -310,6 +309,9 @@ cute_status validate_desc(cute_ctx *ctx, const cute_pair_desc *d, DescInfo &di);
 double row_density(const Catalog &A, const Geometry &g);
 ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax);
 double decision_reach(const cute_pair_desc *d);
+// device blocks from the context's pool, ordered on its stream
+cudaError_t dev_alloc(cute_ctx *ctx, void **p, size_t bytes);
+void dev_free(cute_ctx *ctx, void *p);
 PairDF pair_df(const DescInfo &di);
 
 // Home chunks of catalog A (plan.cpp): each row of cells cut into chunks of

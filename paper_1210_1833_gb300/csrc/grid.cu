@@ -227,11 +227,11 @@ cute_status ensure_scratch(cute_ctx *ctx, size_t bytes) {
 cute_status catalog_stage(cute_ctx *ctx, Catalog &c, const double *xyz, const float *w) {
   const long long n = c.n;
   if (n > 0) {
-    CUDA_OR_FAIL(cudaMalloc(&c.d_xyz, sizeof(double) * 3 * (size_t)n));
+    CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c.d_xyz, sizeof(double) * 3 * (size_t)n));
     CUDA_OR_FAIL(cudaMemcpyAsync(c.d_xyz, xyz, sizeof(double) * 3 * (size_t)n, cudaMemcpyDefault,
                                  ctx->stream));
     if (w) {
-      CUDA_OR_FAIL(cudaMalloc(&c.d_w, sizeof(float) * (size_t)n));
+      CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c.d_w, sizeof(float) * (size_t)n));
       CUDA_OR_FAIL(cudaMemcpyAsync(c.d_w, w, sizeof(float) * (size_t)n, cudaMemcpyDefault,
                                    ctx->stream));
     }
@@ -277,20 +277,20 @@ cute_status catalog_stage(cute_ctx *ctx, Catalog &c, const double *xyz, const fl
   return CUTE_OK;
 }
 
-static void free_grid(Catalog &c) {
-  cudaFree(c.d_pos); c.d_pos = nullptr;
-  cudaFree(c.d_lo); c.d_lo = nullptr;
-  cudaFree(c.d_s64); c.d_s64 = nullptr;
-  cudaFree(c.d_perm); c.d_perm = nullptr;
-  cudaFree(c.d_cell_start); c.d_cell_start = nullptr;
+static void free_grid(cute_ctx *ctx, Catalog &c) {
+  dev_free(ctx, c.d_pos); c.d_pos = nullptr;
+  dev_free(ctx, c.d_lo); c.d_lo = nullptr;
+  dev_free(ctx, c.d_s64); c.d_s64 = nullptr;
+  dev_free(ctx, c.d_perm); c.d_perm = nullptr;
+  dev_free(ctx, c.d_cell_start); c.d_cell_start = nullptr;
   c.h_cell_start.clear();
   c.geom = -1;
 }
 
-void catalog_release(Catalog &c) {
-  free_grid(c);
-  cudaFree(c.d_xyz); c.d_xyz = nullptr;
-  cudaFree(c.d_w); c.d_w = nullptr;
+void catalog_release(cute_ctx *ctx, Catalog &c) {
+  free_grid(ctx, c);
+  dev_free(ctx, c.d_xyz); c.d_xyz = nullptr;
+  dev_free(ctx, c.d_w); c.d_w = nullptr;
 }
 
 cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const double reach[3],
@@ -387,14 +387,14 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
   }
   // the FP32 frame spans at most xmax from its centre on each axis
   for (Catalog *c : cats) {
-    free_grid(*c);
+    free_grid(ctx, *c);
     const int n = (int)c->n;
-    CUDA_OR_FAIL(cudaMalloc(&c->d_cell_start, sizeof(int) * (size_t)(ncell + 1)));
+    CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c->d_cell_start, sizeof(int) * (size_t)(ncell + 1)));
     if (n > 0) {
-      CUDA_OR_FAIL(cudaMalloc(&c->d_pos, sizeof(float4) * (size_t)n));
-      CUDA_OR_FAIL(cudaMalloc(&c->d_lo, sizeof(float4) * (size_t)n));
-      CUDA_OR_FAIL(cudaMalloc(&c->d_s64, sizeof(double) * 3 * (size_t)n));
-      CUDA_OR_FAIL(cudaMalloc(&c->d_perm, sizeof(int) * (size_t)n));
+      CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c->d_pos, sizeof(float4) * (size_t)n));
+      CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c->d_lo, sizeof(float4) * (size_t)n));
+      CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c->d_s64, sizeof(double) * 3 * (size_t)n));
+      CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c->d_perm, sizeof(int) * (size_t)n));
     }
     const int nsb = (int)((ncell + kScanBlock - 1) / kScanBlock);
     size_t need = sizeof(int) * ((size_t)2 * n + (size_t)ncell + (size_t)nsb) + 256;
