@@ -135,6 +135,8 @@ cute_status cute_ctx_destroy(cute_ctx *ctx) {
   cudaFree(ctx->d_scratch);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);  // pool blocks returned
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  for (auto &kv : ctx->pinned_free) cudaFreeHost(kv.second);
+  ctx->pinned_free.clear();
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -356,6 +358,22 @@ cudaError_t dev_alloc(cute_ctx *ctx, void **p, size_t bytes) {
 void dev_free(cute_ctx *ctx, void *p) {
   if (p) cudaFreeAsync(p, ctx->stream);
 }
+cudaError_t pinned_get(cute_ctx *ctx, size_t n, int32_t **p, size_t *cap) {
+  auto it = ctx->pinned_free.lower_bound(n);
+  if (it != ctx->pinned_free.end()) {
+    *cap = it->first;
+    *p = it->second;
+    ctx->pinned_free.erase(it);
+    return cudaSuccess;
+  }
+  const size_t c = n + n / 4 + 16;
+  cudaError_t e = cudaMallocHost((void **)p, c * sizeof(int32_t));
+  if (e == cudaSuccess) *cap = c;
+  return e;
+}
+void pinned_put(cute_ctx *ctx, int32_t *p, size_t cap) {
+  if (p) ctx->pinned_free.emplace(cap, p);
+}
 
 // The double-float view of a pair set: remainders, and the error bounds of
 // its separation and line-of-sight components (df_stage.h).
@@ -467,7 +485,12 @@ cute_status get_work(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, in
     const DescInfo &di = dis[i];
     if (di.A->n > 0 && di.B->n > 0) {
       const int shape = (di.kind == CUTE_SIGMA_PI) ? kShapeDiskSlab : kShapeBall;
-      chunks_build(*di.g, di.A->h_cell_start, home_chunk, chunks[i]);
+      auto ci = di.A->chunk_cache.find(home_chunk);
+      if (ci == di.A->chunk_cache.end()) {
+        ci = di.A->chunk_cache.emplace(home_chunk, std::vector<int4>()).first;
+        chunks_build(*di.g, di.A->h_cell_start, home_chunk, ci->second);
+      }
+      chunks[i] = ci->second;
       stencil_build(*di.g, di.is_auto, full_stencil, shape, di.need, stencils[i]);
     }
     nch += chunks[i].size();

@@ -183,8 +183,11 @@ struct Catalog {
   double *d_s64 = nullptr;     // sorted FP64 SoA
   int32_t *d_perm = nullptr;   // sorted -> upload index
   int32_t *d_cell_start = nullptr;
-  std::vector<int32_t> h_cell_start;
+  int32_t *h_cell_start = nullptr;  // host copy (ncell + 1), pinned, the context's
+  size_t h_cap = 0;                 // ints in that pinned block
   int64_t occupied_cells = 0;  // cells holding at least one object
+  // home chunks of this grid per chunk size (built on first use)
+  mutable std::map<int, std::vector<int4>> chunk_cache;
 };
 
 struct Plan;  // binning plan (plan.cpp)
@@ -228,6 +231,9 @@ struct cute_ctx {
   // cached for the next request (no synchronising cudaMalloc/cudaFree per
   // upload, grid or count)
   cudaMemPool_t pool = nullptr;
+  // pinned host blocks for the grids' host copies of cell_start, kept for
+  // reuse by size
+  std::multimap<size_t, int32_t *> pinned_free;
   int sm_count = 0;
   size_t smem_optin = 0;
   std::string err;
@@ -312,13 +318,16 @@ double decision_reach(const cute_pair_desc *d);
 // device blocks from the context's pool, ordered on its stream
 cudaError_t dev_alloc(cute_ctx *ctx, void **p, size_t bytes);
 void dev_free(cute_ctx *ctx, void *p);
+// pinned host ints from the context's free blocks (at least n), and back
+cudaError_t pinned_get(cute_ctx *ctx, size_t n, int32_t **p, size_t *cap);
+void pinned_put(cute_ctx *ctx, int32_t *p, size_t cap);
 PairDF pair_df(const DescInfo &di);
 
 // Home chunks of catalog A (plan.cpp): each row of cells cut into chunks of
 // home_chunk objects (the last one of a row shorter), spanning at most
 // `maxrun` cells (chunks_maxrun).
 int chunks_maxrun(const Geometry &g);
-void chunks_build(const Geometry &g, const std::vector<int32_t> &csA, int home_chunk,
+void chunks_build(const Geometry &g, const int32_t *csA, int home_chunk,
                   std::vector<int4> &out);
 // Neighbour stencil (plan.cpp).  shape: the region of separations that can
 // fall in a bin, used to trim neighbour rows.  Auto counts without

@@ -196,6 +196,16 @@ __global__ void k_scatter(const double *__restrict__ xyz, const float *__restric
   perm[d] = i;
 }
 
+// cells holding at least one object (grid-stride, one atomic per warp)
+__global__ void k_occupied(const int *__restrict__ cnt, long long ncell, int *__restrict__ out) {
+  int c = 0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x)
+    c += cnt[q] > 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 // ------------------------------------------------------------------ host side
 static cute_status fail(cute_ctx *ctx, cute_status st, const std::string &m) {
   ctx->err = m;
@@ -283,7 +293,10 @@ static void free_grid(cute_ctx *ctx, Catalog &c) {
   dev_free(ctx, c.d_s64); c.d_s64 = nullptr;
   dev_free(ctx, c.d_perm); c.d_perm = nullptr;
   dev_free(ctx, c.d_cell_start); c.d_cell_start = nullptr;
-  c.h_cell_start.clear();
+  pinned_put(ctx, c.h_cell_start, c.h_cap);
+  c.h_cell_start = nullptr;
+  c.h_cap = 0;
+  c.chunk_cache.clear();
   c.geom = -1;
 }
 
@@ -397,7 +410,7 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
       CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c->d_perm, sizeof(int) * (size_t)n));
     }
     const int nsb = (int)((ncell + kScanBlock - 1) / kScanBlock);
-    size_t need = sizeof(int) * ((size_t)2 * n + (size_t)ncell + (size_t)nsb) + 256;
+    size_t need = sizeof(int) * ((size_t)2 * n + (size_t)ncell + (size_t)nsb + 1) + 256;
     cute_status st = ensure_scratch(ctx, need);
     if (st != CUTE_OK) return st;
     int *cid = (int *)ctx->d_scratch;
@@ -419,16 +432,24 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
                                                           c->d_s64, c->d_perm);
       CUDA_OR_FAIL(cudaGetLastError());
     }
-    c->h_cell_start.resize(ncell + 1);
-    CUDA_OR_FAIL(cudaMemcpyAsync(c->h_cell_start.data(), c->d_cell_start,
+    // host copy of cell_start and the occupied-cell count (after it), into
+    // a pinned block: every catalog's copies are in flight before one sync
+    int *occ = bsum + nsb;
+    CUDA_OR_FAIL(cudaMemsetAsync(occ, 0, sizeof(int), ctx->stream));
+    k_occupied<<<std::min<long long>((ncell + 255) / 256, 4LL * ctx->sm_count), 256, 0,
+                 ctx->stream>>>(cnt, ncell, occ);
+    CUDA_OR_FAIL(cudaGetLastError());
+    CUDA_OR_FAIL(pinned_get(ctx, (size_t)ncell + 2, &c->h_cell_start, &c->h_cap));
+    CUDA_OR_FAIL(cudaMemcpyAsync(c->h_cell_start, c->d_cell_start,
                                  sizeof(int) * (size_t)(ncell + 1), cudaMemcpyDeviceToHost,
                                  ctx->stream));
-    CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
-    c->occupied_cells = 0;
-    for (long long q = 0; q < ncell; q++) c->occupied_cells += c->h_cell_start[q + 1] > c->h_cell_start[q];
+    CUDA_OR_FAIL(cudaMemcpyAsync(c->h_cell_start + ncell + 1, occ, sizeof(int),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
     c->geom = g.id;
     c->grid_version = g.version;
   }
+  CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+  for (Catalog *c : cats) c->occupied_cells = c->h_cell_start[ncell + 1];
   ctx->geoms[g.id] = g;
   return CUTE_OK;
 }

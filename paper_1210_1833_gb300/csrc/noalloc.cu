@@ -136,7 +136,7 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   pw.periodic = di.g->periodic;
   // the item records, on the host (the same segments as the GPU builder)
   std::vector<int4> items;
-  const int32_t *csh = di.B->h_cell_start.data();
+  const int32_t *csh = di.B->h_cell_start;
   for (const int4 &c : chunks)
     for (const int4 &r : stencil) {
       Seg sg[3];

@@ -19,6 +19,8 @@
 // contiguous ranges of catalog B (work.cu turns them into work items).
 #include "cute_internal.h"
 
+#include <thread>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -569,13 +571,15 @@ int chunks_maxrun(const Geometry &g) {
 // last one of the row shorter); a chunk may straddle cells, so every lane's
 // home slots stay occupied, and its neighbour x-range is taken from its
 // first and last cells.
-void chunks_build(const Geometry &g, const std::vector<int32_t> &csA, int home_chunk,
-                  std::vector<int4> &out) {
-  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+// The rows of cells [r0, r1) (row = cy + ny * cz), in row order.
+static void chunks_rows(const Geometry &g, const int32_t *csA, int home_chunk, int64_t r0,
+                        int64_t r1, std::vector<int4> &out) {
+  const int nx = g.nc[0], ny = g.nc[1];
   const int maxrun = chunks_maxrun(g);
   auto cell = [&](int x, int y, int z) { return ((int64_t)z * ny + y) * nx + x; };
-  for (int cz = 0; cz < nz; cz++) {
-    for (int cy = 0; cy < ny; cy++) {
+  for (int64_t r = r0; r < r1; r++) {
+    {
+      const int cy = (int)(r % ny), cz = (int)(r / ny);
       const int row_lo = csA[cell(0, cy, cz)], row_hi = csA[cell(nx - 1, cy, cz) + 1];
       int pos = row_lo, cxc = 0;
       while (pos < row_hi) {
@@ -593,6 +597,31 @@ void chunks_build(const Geometry &g, const std::vector<int32_t> &csA, int home_c
       }
     }
   }
+}
+
+void chunks_build(const Geometry &g, const int32_t *csA, int home_chunk,
+                  std::vector<int4> &out) {
+  const int64_t rows = (int64_t)g.nc[1] * g.nc[2];
+  const int64_t cells = rows * g.nc[0];
+  // large grids: contiguous row ranges on a few threads, joined in order
+  int nt = 1;
+  if (cells >= (1 << 18)) {
+    nt = (int)std::min<int64_t>(8, std::max<unsigned>(1u, std::thread::hardware_concurrency()));
+    nt = (int)std::min<int64_t>(nt, rows);
+  }
+  if (nt <= 1) {
+    chunks_rows(g, csA, home_chunk, 0, rows, out);
+    return;
+  }
+  std::vector<std::vector<int4>> part(nt);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; t++)
+    th.emplace_back([&, t] { chunks_rows(g, csA, home_chunk, rows * t / nt, rows * (t + 1) / nt, part[t]); });
+  for (auto &x : th) x.join();
+  size_t tot = 0;
+  for (auto &v : part) tot += v.size();
+  out.reserve(out.size() + tot);
+  for (auto &v : part) out.insert(out.end(), v.begin(), v.end());
 }
 
 // Objects in cells |d| apart on an axis are at least (|d| - 1) a apart
