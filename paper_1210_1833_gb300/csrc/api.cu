@@ -663,6 +663,7 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
   std::memset(&p, 0, sizeof(p));
   p.items = pr.ts->d_items;
   p.total = pr.ts->items;
+  p.item_stride = 1;
   p.pairs = pr.ts->d_pairs;
   p.lut = P.d_lut;
   p.lut_words = (int)P.lut.size();
@@ -993,7 +994,11 @@ cute_status cute_autotune(cute_ctx *ctx, int32_t n, const cute_pair_desc *d, int
           if (ensure_scratch(ctx, cnt + ws + 256) != CUTE_OK) continue;
           pr.p.out_counts = (unsigned long long *)ctx->d_scratch;
           pr.p.out_wsum = acc ? (double *)((char *)ctx->d_scratch + ((cnt + 255) & ~(size_t)255)) : nullptr;
-          pr.p.total = std::min<long long>(pr.p.total, max_items);
+          // an evenly spread sample of the items (they run in home-row order)
+          if (pr.p.total > max_items) {
+            pr.p.item_stride = (pr.p.total + max_items - 1) / max_items;
+            pr.p.total = (pr.p.total + pr.p.item_stride - 1) / pr.p.item_stride;
+          }
           if (pr.p.total <= 0) continue;
           float ms = 0;
           for (int rep = 0; rep < 2; rep++) {  // the first run warms up

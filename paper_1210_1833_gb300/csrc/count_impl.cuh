@@ -595,13 +595,13 @@ __global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
   const int4 rec_none = make_int4(0, 0, 0, 0);
   unsigned long long tk = (lane == 0) ? atomicAdd(p.ticket, 1ull) : 0ull;
   long long it = (long long)__shfl_sync(kFull, tk, 0);
-  int4 rec_next = it < p.total ? p.items[it] : rec_none;
+  int4 rec_next = it < p.total ? p.items[it * p.item_stride] : rec_none;
   tk = (lane == 0 && it < p.total) ? atomicAdd(p.ticket, 1ull) : 0ull;
   for (;;) {
     if (it >= p.total) break;
     const int4 rec = rec_next;
     it = (long long)__shfl_sync(kFull, tk, 0);
-    rec_next = it < p.total ? p.items[it] : rec_none;
+    rec_next = it < p.total ? p.items[it * p.item_stride] : rec_none;
     tk = (lane == 0 && it < p.total) ? atomicAdd(p.ticket, 1ull) : 0ull;
     const int pi = (int)((unsigned)rec.w >> 16);
     if (pi != cur_pair) {

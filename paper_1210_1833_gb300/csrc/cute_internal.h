@@ -118,6 +118,8 @@ struct PairWork {
 struct KParams {
   const int4 *items;           // work item records
   long long total;             // work items handed out
+  long long item_stride;       // record of ticket t: items[t * item_stride] (1; the
+                               // autotuner times an evenly spread sample)
   const PairDev *pairs;
   const uint32_t *lut;         // table words, all axes
   int lut_words;

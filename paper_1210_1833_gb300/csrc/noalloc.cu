@@ -187,6 +187,7 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   std::memset(&p, 0, sizeof(p));
   p.items = (const int4 *)(dev + o_items);
   p.total = (long long)items.size();
+  p.item_stride = 1;
   p.pairs = (const PairDev *)(dev + o_pair);
   p.lut = (const uint32_t *)(dev + o_lut);
   p.lut_words = (int)P.lut.size();
