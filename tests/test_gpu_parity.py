@@ -304,3 +304,44 @@ def test_extent_limit_is_rejected(ctx):
     with pytest.raises(cute.CuteError):
         ctx.grid([a], [10.0] * 3)
     a.free()
+
+
+def test_catalog_churn_and_regrid(ctx):
+    """Catalogs, grids and work lists come from the context's memory pool and
+    pinned blocks: counts stay exact while catalogs of growing and shrinking
+    sizes are uploaded, re-gridded at other cell sizes (the cached home
+    chunks must follow) and freed in between, some living across rounds."""
+    rng = np.random.default_rng(109)
+    e0, e1 = np.linspace(0, 20, 9), np.linspace(0, 1, 5)
+    # (away from the observer at the origin: mu needs |x_i + x_j| > 0)
+    keep = rng.uniform(500, 620, size=(1500, 3))
+    ck = ctx.upload(keep)
+    for it, n in enumerate((800, 5000, 300, 3000, 1200)):
+        x = rng.uniform(500, 620, size=(n, 3))
+        cx = ctx.upload(x)
+        for cpr in (2, 4):
+            ctx.grid([ck, cx], [20.0] * 3, cpr)
+            got = ctx.count("mono", cx, ck, e0)
+            _assert_same(got, oracle_count("mono", x, keep, e0))
+            got = ctx.count("rmu", ck, None, e0, e1)
+            _assert_same(got, oracle_count("rmu", keep, None, e0, e1))
+        cx.free()
+    ck.free()
+    ctx.sync()
+
+
+def test_sparse_grid_many_cells(ctx):
+    """A sparse catalog on a grid of over 2^18 cells (home chunks built on
+    several host threads) counts exactly."""
+    rng = np.random.default_rng(110)
+    a = rng.uniform(0, 400, size=(3000, 3))
+    b = rng.uniform(0, 400, size=(2000, 3))
+    e = np.linspace(0, 20, 11)
+    ca, cb = ctx.upload(a), ctx.upload(b)
+    try:
+        ctx.grid([ca, cb], [20.0] * 3, 2)
+        _assert_same(ctx.count("mono", ca, None, e), oracle_count("mono", a, None, e))
+        _assert_same(ctx.count("mono", ca, cb, e), oracle_count("mono", a, b, e))
+    finally:
+        ca.free()
+        cb.free()
