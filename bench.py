@@ -111,9 +111,14 @@ def _kernel_hash():
     files = sorted(glob.glob(os.path.join(ROOT, "paper_1210_1833_gb300", "csrc", "count_*.cu*")) +
                    [os.path.join(ROOT, "paper_1210_1833_gb300", "csrc", f)
                     for f in ("cute_internal.h", "df_stage.h")])
+    import re
     h = hashlib.sha256()
     for f in files:
-        h.update(open(f, "rb").read())
+        # the code only: comments and whitespace do not change the kernel
+        src = open(f, encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

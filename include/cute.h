@@ -23,7 +23,8 @@
  *   - Bins are half-open, [e_b, e_{b+1}), compared on squared quantities
  *     (e_b * e_b in FP64).  Counts equal, bit for bit, those of the FP64
  *     canonical formulas below: pairs whose FP32 separation lies within a
- *     proven error bound of an edge are re-tested in FP64 on the GPU.
+ *     proven error bound of an edge are re-tested on the GPU (double-float
+ *     with a carried error bound, then FP64 for pairs within it).
  *   - Work is enqueued on the context's CUDA stream.  Calls that write to
  *     host memory synchronise that stream before returning.
  */

@@ -151,7 +151,7 @@ static __device__ __noinline__ void flush_wsum(const KParams &p, const WarpSmem 
 // Table binning (non-uniform edges): slot byte offset (slot * R * 4) of one
 // pair from its FP32 values -- the squared separation v (monopole, theta),
 // sigma^2 and pi^2, or r^2 and mu -- and whether it lies inside an edge's
-// FP32 error band (then it is re-tested in FP64).
+// FP32 error band (then it is re-tested).
 template <int KIND, int M0, int M1>
 __device__ __forceinline__ uint32_t table_slot(const KParams &p, uint32_t lut, uint32_t band,
                                                float a, float b, bool &near) {
@@ -204,7 +204,7 @@ __device__ __forceinline__ Rmu2 rmu_values2(float2 qx, float2 qy, float2 qz, flo
 // of sm_100+ (element-wise IEEE round-to-nearest: each element is rounded
 // as the scalar formula would be).  Each gives the byte offsets of the two
 // pairs' slots and a near score per pair: the pair lies inside an edge's
-// error band (and is re-tested in FP64) when its score reaches the kind's
+// error band (and is re-tested) when its score reaches the kind's
 // threshold, near_thr.  Monopole (and theta on chords):
 __device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2 qy, float2 qz,
                                             float2 nx, float2 ny, float2 nz, uint32_t stride,
@@ -316,7 +316,7 @@ __device__ __forceinline__ void arith_pair_out(float2 s2, uint32_t (&o)[2], int 
 // Score threshold of the arithmetic binning: |h| >= near_at of axis 0
 // (monopole, theta; sigma, pi with pi rescaled), or the smaller of near_at
 // of r and near_c of mu (r, mu: a few more flags than the exact per-axis
-// tests, all decided by the FP64 re-test).
+// tests, all decided by the re-test).
 template <int KIND>
 __device__ __forceinline__ float near_thr(const KParams &p) {
   if (KIND == KRMU) return fminf(p.ax[0].near_at, p.ax[1].near_c);
@@ -327,7 +327,7 @@ __device__ __forceinline__ float near_thr(const KParams &p) {
 // one shared-memory tile (cnt even; rows past the slice hold sentinels).
 // Two neighbours at a time: every binning of the 2 x HP pairs is issued
 // first, then the accumulation; pairs inside an edge's error band go to the
-// warp's FP64 queue (rare, so the enqueue sits behind one vote).  Plain
+// warp's re-test queue (rare, so the enqueue sits behind one vote).  Plain
 // counts with arithmetic binning add every pair to the slot its FP32 value
 // gives and vote on the step's largest near score; a flagged step (rare)
 // takes the near pairs' increments back before queueing them, so the

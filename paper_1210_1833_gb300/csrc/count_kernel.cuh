@@ -17,7 +17,9 @@
 //     flushed to uint64 in HBM before they could overflow;
 //   * pairs in a dirty cell are refined against the one edge's FP32 band,
 //     and pairs inside the band go to a per-warp queue that the warp
-//     re-tests in FP64 32 at a time with the canonical formulas.
+//     re-tests 32 at a time: a double-float stage with a carried error
+//     bound (df_stage.h), the canonical FP64 formulas for what it leaves
+//     open.
 #pragma once
 
 #include "cute_internal.h"

@@ -24,7 +24,7 @@ namespace cute {
 // proven FP32 error bound, lies strictly between the same two edges, so the
 // offset is the pair's slot.  Band k+1: the cell meets the error band of edge
 // k only; the offset is the slot just below edge k, values above the band
-// take the next slot, values inside it are re-tested in FP64.  The last band
+// take the next slot, values inside it are re-tested (double-float, then FP64).  The last band
 // index of an axis marks cells that always go to FP64.
 constexpr uint32_t kOffMask = 0xFFFFu;     // slot byte offset (bits 0..15)
 constexpr int kClassShift = 16;            // R_MU r entries: mu error class (bits 16..19)

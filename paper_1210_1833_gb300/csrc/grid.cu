@@ -1,11 +1,12 @@
 // grid.cu -- catalog staging and the counting-sort cell grid (Sec. 3.3).
 //
-// A catalog is kept twice on the device: FP64 in upload order (the
-// canonical coordinates the FP64 re-test reads) and, once a grid is built,
-// cell-sorted as FP32 (x, y, z, w) float4 offsets from the grid centre plus
-// a cell-sorted FP64 SoA copy.  The grid is a counting sort: cell id and
-// rank within the cell per object (one atomic per object), an exclusive
-// scan over cells, and a scatter.
+// A catalog is kept on the device FP64 in upload order and, once a grid is
+// built, cell-sorted as FP32 (x, y, z, w) float4 offsets from the grid
+// centre, their FP32 remainders (the re-test's double-float stage) and a
+// FP64 SoA copy (the canonical formulas).  The grid is a counting sort: cell
+// id and rank within the cell per object (one atomic per object), an
+// exclusive scan over cells, and a scatter.  Device blocks come from the
+// context's stream-ordered pool.
 #include "cute_internal.h"
 
 #include <cfloat>
