@@ -314,8 +314,12 @@ static bool make_arith(const double *e, int n, const AxisErr &err, double eta0, 
     double Tt = dx * inv + x * dinv + dc + kU * (std::fabs(t) + 1.0) + db;
     T = std::max(T, Tt);
   }
+  // T is taken with the doubled error of the separation (SqErr) or of the
+  // component (|dz|): that factor 2 is the margin over the analysed bound
+  // (a host check replaying the kernel's arithmetic on pairs around every
+  // edge finds no miss with thresholds at a tenth of this distance)
   p.thr_a = 0;
-  p.thr_b = (float)(2.0 * T + 1e-6);
+  p.thr_b = (float)(T + 1e-6);
   return p.thr_b < 0.2f;
 }
 
@@ -394,10 +398,13 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
       ok = make_arith(e0, n0, A0.err, ep.eta0, true, false, false, P0) &&
            make_arith(e1, n1, A0.err, ep.eta0, false, true, false, P1);
       if (ok) {
-        // mu bound in t units: n_mu * eps(r), eps(r) = a / r + b (see above)
+        // mu bound in t units: n_mu * eps(r), eps(r) = a / r + b (see
+        // above), without the final doubling: the 2 sqrt3 of the perturbed
+        // unit vectors is twice the first-order bound, and the 40 u rounding
+        // budget more than twice the rounding of the kernel's formula
         double lterm = (ep.lmin > 0) ? ep.eta_l / ep.lmin : INFINITY;
-        double a = 2.0 * 2.0 * std::sqrt(3.0) * ep.eta0 * (1.0 + 1e-5);
-        double b = 2.0 * (2.0 * std::sqrt(3.0) * (kU + lterm) + 40 * kU) + 1e-12;
+        double a = 2.0 * std::sqrt(3.0) * ep.eta0 * (1.0 + 1e-5);
+        double b = 2.0 * std::sqrt(3.0) * (kU + lterm) + 40 * kU + 1e-12;
         double nmu = n1 / (e1[n1] - e1[0]);
         P1.thr_a = (float)(nmu * a * 1.0001);
         P1.thr_b = (float)((double)P1.thr_b + nmu * b * 1.0001);

@@ -1,0 +1,376 @@
+// Host check of the counting kernel's FP32 binning with uniform edges: the
+// kernel's arithmetic (count_impl.cuh: mono_arith2, sigpi_arith2,
+// rmu_values2 + rmu_arith2, one element of each packed pair) is replayed
+// here in the same operation order with IEEE FP32 operations, the hardware
+// reciprocal square root replaced by 1/sqrt perturbed by up to its
+// documented 2^-22.9 relative error (at both extremes and at random), and
+// the near-edge thresholds taken from the host planner (plan_build).  On
+// pairs placed on and around every edge, open and periodic, every pair the
+// kernel would NOT flag as near must land in the slot of the canonical FP64
+// formulas (Sec. 2.2: squared separations against squared edges, minimum
+// image; Sec. 3.4: mu about the midpoint line of sight).
+// Prints "scenario cases flagged violations"; exits 1 on any violation.
+//
+// Build: g++ -O2 -std=c++17 -ffp-contract=off -I include -I <csrc>
+//        -I <cuda>/include fp32_band_check.cpp <csrc>/plan.cpp -L<cuda>/lib64 -lcudart
+#include "cute_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <random>
+#include <vector>
+
+using namespace cute;
+
+static const float kVFloor = 1e-30f, kMagic = 12582912.0f;
+static const uint32_t kMagicBits = 0x4B400000u;
+static const double kU32 = 5.9604644775390625e-08;
+
+// ---- IEEE FP32, rounded to nearest, never contracted
+static float fadd(float a, float b) { volatile float r = a + b; return r; }
+static float fmul(float a, float b) { volatile float r = a * b; return r; }
+static float ffma(float a, float b, float c) { return std::fma(a, b, c); }
+static uint32_t bits(float f) { uint32_t u; std::memcpy(&u, &f, 4); return u; }
+
+// the hardware rsqrt: any value within 2^-22.9 of 1/sqrt(x)
+static std::mt19937_64 g_rng(1210);
+static int g_mode = 0;  // 0 random, 1 low extreme, 2 high extreme
+// margin factor (first argument, default 1): thresholds f times as far from
+// 1/2 as the planner's (f < 1 probes how much of the margin is needed)
+static double g_f = 1.0;
+static void shrink(AxisPlan &a) {
+  a.near_at = (float)(0.5 - g_f * (0.5 - (double)a.near_at));
+  a.near_c = (float)(0.5 - g_f * (0.5 - (double)a.near_c));
+  a.thr_a = (float)(g_f * a.thr_a);
+}
+static float rsqrt_dev(float x) {
+  const double r = 1.0 / std::sqrt((double)x), e = std::ldexp(1.0, -23) * 1.0717;  // 2^-22.9
+  double f;
+  if (g_mode == 1) f = 1.0 - e;
+  else if (g_mode == 2) f = 1.0 + e;
+  else f = 1.0 + e * (2.0 * std::uniform_real_distribution<double>(0, 1)(g_rng) - 1.0);
+  return (float)(r * f);
+}
+
+struct Slot { int slot; float score; };
+
+// one pair, monopole / chord: q neighbour offsets, n = -(home - shift)
+static Slot mono_fp32(const AxisPlan &a, const float *q, const float *n) {
+  const float dx = fadd(q[0], n[0]), dy = fadd(q[1], n[1]), dz = fadd(q[2], n[2]);
+  const float v = ffma(dz, dz, ffma(dy, dy, ffma(dx, dx, kVFloor)));
+  const float x = fmul(v, rsqrt_dev(v));
+  float t = ffma(x, a.inv, a.cst);
+  t = std::fmin(t, a.thi);
+  const float tm = fadd(t, kMagic), fl = fadd(tm, -kMagic);
+  const float h = ffma(fl, -1.0f, t);
+  return {(int)(bits(tm) - kMagicBits) + 1, std::fabs(h)};
+}
+
+static Slot sigpi_fp32(const AxisPlan &a0, const AxisPlan &a1, int slots1, const float *q,
+                       const float *n) {
+  const float dx = fadd(q[0], n[0]), dy = fadd(q[1], n[1]), dz = fadd(q[2], n[2]);
+  const float v0 = ffma(dy, dy, ffma(dx, dx, kVFloor));
+  const float x0 = fmul(v0, rsqrt_dev(v0));
+  const float t0 = std::fmin(ffma(x0, a0.inv, a0.cst), a0.thi);
+  const float t1 = std::fmin(ffma(std::fabs(dz), a1.inv, a1.cst), a1.thi);
+  const float tm0 = fadd(t0, kMagic), tm1 = fadd(t1, kMagic);
+  const float f0 = fadd(tm0, -kMagic);
+  const float h0 = ffma(f0, -1.0f, t0), h1 = ffma(fadd(tm1, -kMagic), -1.0f, t1);
+  const float tc = ffma(f0, (float)slots1, tm1);
+  const float g1 = fmul(h1, a1.near_scale);
+  return {(int)(bits(tc) - kMagicBits) + slots1 + 1, std::fmax(std::fabs(h0), std::fabs(g1))};
+}
+
+// (r, mu): xi = home in the observer frame (FP32), aq = 4 |x_i|^2 (FP32)
+static Slot rmu_fp32(const AxisPlan &a0, const AxisPlan &a1, int slots1, const float *q,
+                     const float *n, const float *xi, float aq) {
+  const float dx = fadd(q[0], n[0]), dy = fadd(q[1], n[1]), dz = fadd(q[2], n[2]);
+  const float r2 = ffma(dz, dz, ffma(dy, dy, ffma(dx, dx, kVFloor)));
+  const float sx = ffma(dz, xi[2], ffma(dy, xi[1], fmul(dx, xi[0])));
+  const float sl = ffma(sx, 2.0f, r2);
+  const float l2 = ffma(sx, 4.0f, fadd(aq, r2));
+  const float rr = rsqrt_dev(r2);
+  const float pl = fmul(r2, l2);
+  const float mu = fmul(std::fabs(sl), rsqrt_dev(pl));
+  const float t0 = std::fmin(ffma(fmul(r2, rr), a0.inv, a0.cst), a0.thi);
+  const float t1 = std::fmin(ffma(mu, a1.inv, a1.cst), a1.thi);
+  const float tm0 = fadd(t0, kMagic), tm1 = fadd(t1, kMagic);
+  const float f0 = fadd(tm0, -kMagic);
+  const float h0 = ffma(f0, -1.0f, t0), h1 = ffma(fadd(tm1, -kMagic), -1.0f, t1);
+  const float tc = ffma(f0, (float)slots1, tm1);
+  const float sc = std::fmax(std::fabs(h0), ffma(rr, a1.thr_a, std::fabs(h1)));
+  return {(int)(bits(tc) - kMagicBits) + slots1 + 1, sc};
+}
+
+// ---- canonical FP64 (the oracle's definitions)
+static double wrap(double d, double L) {
+  if (L > 0) {
+    if (d > 0.5 * L) d -= L;
+    else if (d < -0.5 * L) d += L;
+  }
+  return d;
+}
+static int bin64(const std::vector<double> &E, double v) {
+  const int n = (int)E.size() - 1;
+  if (!(v >= E[0]) || !(v < E[n])) return -1;
+  int b = 0;
+  while (b + 1 <= n && v >= E[b + 1]) b++;
+  return b;
+}
+
+struct Tally {
+  long cases = 0, flagged = 0, bad = 0;
+  void add(bool near, int fp32, int canon) {
+    cases++;
+    if (near) { flagged++; return; }
+    if (fp32 != canon) {
+      if (bad < 5) std::printf("  violation: fp32 slot %d canonical %d\n", fp32, canon);
+      bad++;
+    }
+  }
+};
+
+// the library's per-component error bound (error_params): FP32 frame
+// offsets within xm of the centre, periodic image shifts
+static ErrorParams eparams(double xm, double L, double rmax, double absmax, double rmin) {
+  ErrorParams ep{0, 0, 0};
+  if (L > 0) {
+    const double dL = std::fabs((double)(float)L - L);
+    ep.eta0 = kU32 * (3.0 * xm + 2.0 * rmax) * 1.01 + dL * 1.01 + 1e-12 * (xm + L);
+  } else {
+    ep.eta0 = kU32 * 2.0 * xm * 1.01 + 1e-12 * xm;
+  }
+  ep.eta_l = kU32 * (4.0 * absmax + rmax) * 1.01 + ep.eta0 + kU32 * rmax;
+  ep.lmin = 2.0 * rmin - rmax;
+  return ep;
+}
+
+static void unit(std::mt19937_64 &g, double *u) {
+  std::normal_distribution<double> N(0, 1);
+  double s = 0;
+  for (int k = 0; k < 3; k++) { u[k] = N(g); s += u[k] * u[k]; }
+  s = std::sqrt(s);
+  for (int k = 0; k < 3; k++) u[k] /= s;
+}
+
+// relative offsets from an edge, both sides, across the FP32 error band
+static const double kOff[] = {0.0,   1e-8, -1e-8, 1e-7, -1e-7, 4e-7, -4e-7, 1e-6,  -1e-6,
+                              3e-6, -3e-6, 1e-5, -1e-5, 3e-5, -3e-5, 1e-4, -1e-4, 1e-3, -1e-3};
+
+// FP32 offsets of a pair as the kernel sees them: q = b - fo, n = -(a - fo - S)
+static void kernel_inputs(const double *a, const double *b, const double *fo, double L, float *q,
+                          float *n) {
+  for (int c = 0; c < 3; c++) {
+    const float pa = (float)(a[c] - fo[c]), pb = (float)(b[c] - fo[c]);
+    float S = 0.0f;
+    if (L > 0) {
+      const double d = b[c] - a[c];
+      if (d > 0.5 * L) S = -(float)L;        // neighbour's image at b - L
+      else if (d < -0.5 * L) S = (float)L;   // at b + L
+    }
+    q[c] = pb;
+    n[c] = -fadd(pa, -S);
+  }
+}
+
+static Tally run_mono(double step, int n, double L, double xm_spread, bool chord,
+                      std::mt19937_64 &g) {
+  std::vector<double> e(n + 1), E(n + 1);
+  for (int k = 0; k <= n; k++) { e[k] = k * step; E[k] = e[k] * e[k]; }
+  const double fo[3] = {chord ? 0.0 : (L > 0 ? 0.5 * L : 1234.5),
+                        chord ? 0.0 : (L > 0 ? 0.5 * L : -300.25),
+                        chord ? 0.97 : (L > 0 ? 0.5 * L : 77.0)};
+  const double xm = chord ? 1.0 : (L > 0 ? 0.5 * L : xm_spread + e[n]);
+  Plan P;
+  const std::string m = plan_build(chord ? KTHETA : KMONO, e.data(), n, nullptr, 1,
+                                   eparams(xm, L, e[n], 0, 0), 8192, 12288, true, P);
+  if (!m.empty() || P.ax[0].mode != kArith) { std::printf("  plan: %s\n", m.c_str()); return Tally{0, 0, 1}; }
+  shrink(P.ax[0]);
+  std::uniform_real_distribution<double> U(-1, 1);
+  Tally t;
+  for (int k = 1; k <= n; k++)
+    for (double off : kOff)
+      for (int rep = 0; rep < 24; rep++) {
+        double a[3], b[3], u[3];
+        const double s = e[k] * (1.0 + off);
+        if (chord) {
+          double v[3], w[3];
+          unit(g, v);
+          unit(g, w);
+          const double dot = w[0] * v[0] + w[1] * v[1] + w[2] * v[2];
+          double wn = 0;
+          for (int c = 0; c < 3; c++) { w[c] -= dot * v[c]; wn += w[c] * w[c]; }
+          wn = std::sqrt(wn);
+          const double ang = 2 * std::asin(std::min(1.0, s / 2));
+          for (int c = 0; c < 3; c++) {
+            a[c] = v[c];
+            b[c] = std::cos(ang) * v[c] + std::sin(ang) * w[c] / wn;
+          }
+        } else {
+          unit(g, u);
+          for (int c = 0; c < 3; c++) {
+            a[c] = L > 0 ? std::fmod(fo[c] + 0.5 * L * U(g) + 10 * L, L) : fo[c] + xm_spread * U(g);
+            b[c] = a[c] + u[c] * s;
+            if (L > 0) { b[c] = std::fmod(b[c] + 10 * L, L); if (b[c] >= L) b[c] = 0; }
+          }
+        }
+        float q[3], nn[3];
+        kernel_inputs(a, b, fo, L, q, nn);
+        double dd[3];
+        for (int c = 0; c < 3; c++) dd[c] = wrap(b[c] - a[c], L);
+        const int cb = bin64(E, (dd[0] * dd[0] + dd[1] * dd[1]) + dd[2] * dd[2]);
+        const int canon = cb < 0 ? -1 : cb + 1;
+        const Slot r = mono_fp32(P.ax[0], q, nn);
+        const int fp32 = (r.slot >= 1 && r.slot <= n) ? r.slot : -1;
+        t.add(r.score >= P.ax[0].near_at, fp32, canon);
+      }
+  return t;
+}
+
+static Tally run_sigpi(double s0, int n0, double s1, int n1, double L, std::mt19937_64 &g) {
+  std::vector<double> e0(n0 + 1), e1(n1 + 1), E0(n0 + 1), E1(n1 + 1);
+  for (int k = 0; k <= n0; k++) { e0[k] = k * s0; E0[k] = e0[k] * e0[k]; }
+  for (int k = 0; k <= n1; k++) { e1[k] = k * s1; E1[k] = e1[k] * e1[k]; }
+  const double fo[3] = {0.5 * L, 0.5 * L, 0.5 * L};
+  Plan P;
+  const std::string m = plan_build(KSIGPI, e0.data(), n0, e1.data(), n1,
+                                   eparams(0.5 * L, L, std::max(e0[n0], e1[n1]), 0, 0), 8192, 12288,
+                                   true, P);
+  if (!m.empty() || P.ax[0].mode != kArith) { std::printf("  plan: %s\n", m.c_str()); return Tally{0, 0, 1}; }
+  shrink(P.ax[0]);
+  shrink(P.ax[1]);
+  P.ax[1].near_scale = (float)((double)P.ax[0].near_at / (double)P.ax[1].near_at);
+  std::uniform_real_distribution<double> U(-1, 1), U01(0, 1);
+  Tally t;
+  for (int axis = 0; axis < 2; axis++)
+    for (int k = 1; k <= (axis ? n1 : n0); k++)
+      for (double off : kOff)
+        for (int rep = 0; rep < 16; rep++) {
+          const double ed = (axis ? e1[k] : e0[k]) * (1.0 + off);
+          const double sig = axis ? U01(g) * e0[n0] : ed, pi = axis ? ed : U01(g) * e1[n1];
+          const double phi = 6.283185307179586 * U01(g);
+          const double o3[3] = {sig * std::cos(phi), sig * std::sin(phi), U(g) > 0 ? pi : -pi};
+          double a[3], b[3];
+          for (int c = 0; c < 3; c++) {
+            a[c] = std::fmod(fo[c] + 0.5 * L * U(g) + 10 * L, L);
+            b[c] = std::fmod(a[c] + o3[c] + 10 * L, L);
+            if (b[c] >= L) b[c] = 0;
+          }
+          float q[3], nn[3];
+          kernel_inputs(a, b, fo, L, q, nn);
+          double dd[3];
+          for (int c = 0; c < 3; c++) dd[c] = wrap(b[c] - a[c], L);
+          const int bs = bin64(E0, dd[0] * dd[0] + dd[1] * dd[1]), bp = bin64(E1, dd[2] * dd[2]);
+          const int canon = (bs < 0 || bp < 0) ? -1 : (bs + 1) * (n1 + 2) + bp + 1;
+          const Slot r = sigpi_fp32(P.ax[0], P.ax[1], P.slots1, q, nn);
+          const int s0i = r.slot / P.slots1, s1i = r.slot % P.slots1;
+          const int fp32 = (s0i >= 1 && s0i <= n0 && s1i >= 1 && s1i <= n1) ? r.slot : -1;
+          t.add(r.score >= P.ax[0].near_at, fp32, canon);
+        }
+  return t;
+}
+
+// (r, mu) on a light-cone-like region: objects around centre fo (observer
+// at the origin), extent xm about fo
+static Tally run_rmu(const double *fo, double xm, double rmin, double absmax, double s0, int n0,
+                     int n1, std::mt19937_64 &g) {
+  std::vector<double> e0(n0 + 1), e1(n1 + 1), E0(n0 + 1), M(n1 + 1);
+  for (int k = 0; k <= n0; k++) { e0[k] = k * s0; E0[k] = e0[k] * e0[k]; }
+  for (int k = 0; k <= n1; k++) { e1[k] = (double)k / n1; M[k] = e1[k] * e1[k]; }
+  Plan P;
+  const std::string m = plan_build(KRMU, e0.data(), n0, e1.data(), n1,
+                                   eparams(xm, 0, e0[n0], absmax, rmin), 8192, 12288, true, P);
+  if (!m.empty() || P.ax[0].mode != kArith || P.ax[1].mode != kArith) {
+    std::printf("  plan: %s\n", m.c_str());
+    return Tally{0, 0, 1};
+  }
+  shrink(P.ax[0]);
+  shrink(P.ax[1]);
+  const float thr = std::fmin(P.ax[0].near_at, P.ax[1].near_c);
+  std::uniform_real_distribution<double> U(-1, 1);
+  Tally t;
+  const double rs[] = {0.4, 2.0, 4.999, 5.0, 12.5, 33.0, 77.0, 120.0, 180.0, 199.9, 200.0};
+  for (double r : rs)
+    for (int k = 0; k <= n1; k++)
+      for (double off : kOff)
+        for (int rep = 0; rep < 3; rep++) {
+          double xi[3], tt[3];
+          for (int c = 0; c < 3; c++) xi[c] = fo[c] + (xm - 210.0) * U(g);
+          unit(g, tt);
+          const double mm = std::min(std::max(e1[k] * (1.0 + off), 0.0), 1.0);
+          const double rr = (rep == 0 && k == 0) ? r * (1.0 + off) : r;
+          double s[3] = {0, 0, 0};
+          for (int it = 0; it < 8; it++) {
+            double l[3], ln = 0;
+            for (int c = 0; c < 3; c++) { l[c] = 2 * xi[c] + s[c]; ln += l[c] * l[c]; }
+            ln = std::sqrt(ln);
+            double dot = 0;
+            for (int c = 0; c < 3; c++) dot += tt[c] * l[c] / ln;
+            double tp[3], tn = 0;
+            for (int c = 0; c < 3; c++) { tp[c] = tt[c] - dot * l[c] / ln; tn += tp[c] * tp[c]; }
+            tn = std::sqrt(tn);
+            for (int c = 0; c < 3; c++)
+              s[c] = rr * (mm * l[c] / ln + std::sqrt(std::max(0.0, 1 - mm * mm)) * tp[c] / tn);
+          }
+          double xj[3];
+          for (int c = 0; c < 3; c++) xj[c] = xi[c] + s[c];
+          // canonical
+          const double sx = xj[0] - xi[0], sy = xj[1] - xi[1], sz = xj[2] - xi[2];
+          const double lx = xi[0] + xj[0], ly = xi[1] + xj[1], lz = xi[2] + xj[2];
+          const double r2 = (sx * sx + sy * sy) + sz * sz;
+          int canon = -1;
+          const int br = bin64(E0, r2);
+          if (br >= 0) {
+            int bm = 0;
+            if (r2 != 0.0) {
+              const double l2 = (lx * lx + ly * ly) + lz * lz;
+              const double sl = (sx * lx + sy * ly) + sz * lz;
+              const double qv = sl * sl, den = r2 * l2;
+              for (int mi = 1; mi <= n1 - 1; mi++)
+                if (qv >= M[mi] * den) bm = mi;
+            }
+            canon = (br + 1) * (n1 + 2) + bm + 1;
+          }
+          // the kernel's inputs
+          const double zero[3] = {0, 0, 0};
+          float q[3], nn[3], xf[3];
+          kernel_inputs(xi, xj, fo, 0.0, q, nn);
+          (void)zero;
+          for (int c = 0; c < 3; c++) xf[c] = (float)xi[c];
+          const float aq = (float)(4.0 * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]));
+          const Slot res = rmu_fp32(P.ax[0], P.ax[1], P.slots1, q, nn, xf, aq);
+          const int s0i = res.slot / P.slots1, s1i = res.slot % P.slots1;
+          const int fp32 = (s0i >= 1 && s0i <= n0 && s1i >= 1 && s1i <= n1) ? res.slot : -1;
+          t.add(res.score >= thr, fp32, canon);
+        }
+  return t;
+}
+
+int main(int argc, char **argv) {
+  if (argc > 1) g_f = std::atof(argv[1]);
+  std::mt19937_64 g(20121008);
+  long bad = 0;
+  auto report = [&](const char *name, const Tally &t) {
+    std::printf("%s %ld %ld %ld\n", name, t.cases, t.flagged, t.bad);
+    bad += t.bad;
+  };
+  for (g_mode = 0; g_mode < 3; g_mode++) {
+    char nm[64];
+    std::snprintf(nm, sizeof nm, "mono_periodic_r%d", g_mode);
+    report(nm, run_mono(5.0, 30, 2000.0, 0, false, g));
+    std::snprintf(nm, sizeof nm, "mono_periodic_small_r%d", g_mode);
+    report(nm, run_mono(5.0, 40, 1000.0, 0, false, g));
+    std::snprintf(nm, sizeof nm, "mono_open_r%d", g_mode);
+    report(nm, run_mono(2.5, 40, 0.0, 1400.0, false, g));
+    std::snprintf(nm, sizeof nm, "chord_r%d", g_mode);
+    report(nm, run_mono(0.0027, 64, 0.0, 0, true, g));
+    std::snprintf(nm, sizeof nm, "sigpi_periodic_r%d", g_mode);
+    report(nm, run_sigpi(3.0, 50, 3.0, 50, 1500.0, g));
+    const double fo[3] = {1250.0, 1083.0, 625.0};
+    std::snprintf(nm, sizeof nm, "rmu_lightcone_r%d", g_mode);
+    report(nm, run_rmu(fo, 1250.0, 1000.0, 2500.0, 5.0, 40, 40, g));
+  }
+  return bad ? 1 : 0;
+}

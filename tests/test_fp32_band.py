@@ -1,0 +1,62 @@
+"""Host check of the counting kernel's FP32 near-edge bands (uniform edges):
+tests/fp32_band_check.cpp replays the kernel's FP32 binning arithmetic (same
+operation order, IEEE roundings, the hardware reciprocal square root anywhere
+within its documented error) with the thresholds of the host planner, on
+pairs on and around every edge of the monopole, chord, (sigma, pi) and
+(r, mu) binnings; no pair the kernel would not re-test may fall in another
+slot than the canonical FP64 formulas give (Sec. 2.2, Sec. 3.4).  The check
+also runs with the thresholds' distance from 1/2 halved, so the planner's
+bounds keep at least a factor 2 over what these pairs need."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_1210_1833_gb300", "csrc")
+
+
+def _cuda_home():
+    for c in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if c and os.path.exists(os.path.join(c, "include", "cuda_runtime.h")):
+            return c
+    return None
+
+
+@pytest.fixture(scope="module")
+def exe(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    cuda = _cuda_home()
+    if cxx is None or cuda is None:
+        pytest.skip("needs a C++ compiler and the CUDA headers")
+    out = str(tmp_path_factory.mktemp("band") / "fp32_band_check")
+    lib = next((d for d in ("lib64", "lib", "targets/sbsa-linux/lib", "targets/x86_64-linux/lib")
+                if os.path.exists(os.path.join(cuda, d, "libcudart.so"))), "lib64")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-ffp-contract=off",
+                    "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+                    "-I", os.path.join(cuda, "include"),
+                    os.path.join(HERE, "fp32_band_check.cpp"), os.path.join(CSRC, "plan.cpp"),
+                    "-L", os.path.join(cuda, lib), "-lcudart", "-Wl,-rpath," + os.path.join(cuda, lib),
+                    "-o", out], check=True)
+    return out
+
+
+def _run(exe, factor):
+    r = subprocess.run([exe, str(factor)], capture_output=True, text=True)
+    rows = {}
+    for line in r.stdout.splitlines():
+        p = line.split()
+        if len(p) == 4 and p[1].isdigit():
+            rows[p[0]] = tuple(int(x) for x in p[1:])
+    return r.returncode, rows, r.stdout
+
+
+@pytest.mark.parametrize("factor", [1.0, 0.5])
+def test_no_unflagged_pair_is_misbinned(exe, factor):
+    rc, rows, out = _run(exe, factor)
+    assert len(rows) == 18, out  # 6 scenarios x 3 ways of rounding the rsqrt
+    for name, (cases, flagged, bad) in rows.items():
+        assert cases > 1000 and bad == 0, (name, out)
+    assert rc == 0, out
