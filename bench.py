@@ -110,7 +110,7 @@ def _kernel_hash():
     import hashlib
     files = sorted(glob.glob(os.path.join(ROOT, "paper_1210_1833_gb300", "csrc", "count_*.cu*")) +
                    [os.path.join(ROOT, "paper_1210_1833_gb300", "csrc", f)
-                    for f in ("cute_internal.h", "df_stage.h")])
+                    for f in ("cute_internal.h", "df_stage.h", "plan.cpp")])
     import re
     h = hashlib.sha256()
     for f in files:
