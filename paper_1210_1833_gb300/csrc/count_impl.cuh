@@ -327,11 +327,12 @@ __device__ __forceinline__ float near_thr(const KParams &p) {
 // one shared-memory tile (cnt even; rows past the slice hold sentinels).
 // Two neighbours at a time: every binning of the 2 x HP pairs is issued
 // first, then the accumulation; pairs inside an edge's error band go to the
-// warp's re-test queue (rare, so the enqueue sits behind one vote).  Plain
-// counts with arithmetic binning add every pair to the slot its FP32 value
-// gives and vote on the step's largest near score; a flagged step (rare)
-// takes the near pairs' increments back before queueing them, so the
-// common step carries no per-pair selects.
+// warp's re-test queue (rare, so the enqueue sits behind one vote).  With
+// arithmetic binning every pair goes to the slot its FP32 value gives and
+// the warp votes on the step's largest near score; a flagged step (rare)
+// takes the near pairs' contributions back (count, weight product or
+// gradient term) before queueing them, so the common step carries no
+// per-pair selects.  Table binning routes near pairs to slot 0 at once.
 // MASK: 1 -- only j > i counts (the home run against itself, unique pairs);
 //       2 -- every j != i counts (full-stencil adjoint of an auto count).
 template <int KIND, int HP, int M0, int M1, int MASK, int ACC>
@@ -341,7 +342,7 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
                                            unsigned &near_count) {
   constexpr int U = 8 / HP;  // neighbours per step: 8 pairs per lane per step
   constexpr int NP = U * HP;
-  constexpr bool kLazy = ACC == kAccCount && M0 == kArith;
+  constexpr bool kLazy = M0 == kArith;
   const float thr = near_thr<KIND>(p);
   const int slot_shift = 31 - __clz(p.R * 4);
   // Plain counts add straight to the lane's histogram copy: its shared
@@ -485,7 +486,30 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
 #pragma unroll
       for (int k = 0; k < NP; k++) {
         const bool nk = kLazy ? (sc[k] >= thr) : ((nmask >> k) & 1u) != 0u;
-        if (kLazy && nk) red_add_u32(off[k], 0xffffffffu);  // take back the FP32 slot's count
+        if (kLazy && nk) {
+          // take back what the FP32 slot received: its count, and the weight
+          // product (weighted) or the gradient term (adjoint), by the
+          // opposite float-float addition (exact up to the columns' own
+          // 2^-48 rounding)
+          if (ACC != kAccAdjoint)
+            red_add_u32(ACC == kAccCount ? off[k] : w.s_hist_lane + off[k], 0xffffffffu);
+          if (ACC == kAccWeighted) {
+            const float a = h.w[k % HP], b = wj[k / HP];
+            const float ph = __fmul_rn(a, b);
+            const float pl = __fmaf_rn(a, b, -ph);
+            const uint32_t c = w.s_wcol + 8u * (off[k] >> slot_shift);
+            float2 v = lds_f2(c);
+            ff_add(v.x, v.y, -ph, -pl);
+            sts_f2(c, v);
+          }
+          if (ACC == kAccAdjoint) {
+            const float2 gg = lds_f2(w.s_G + 8u * (off[k] >> slot_shift));
+            const float b = wj[k / HP];
+            const float th = __fmul_rn(b, gg.x);
+            const float tl = __fmaf_rn(b, gg.y, __fmaf_rn(b, gg.x, -th));
+            ff_add(h.gh[k % HP], h.gl[k % HP], -th, -tl);
+          }
+        }
         // (a padded home slot or tile row is never a pair, whatever its
         // arithmetic gave)
         if (nk && h.id[k % HP] != 0x7fffffff && gj0 + j + k / HP < w.gje) {
