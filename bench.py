@@ -481,14 +481,19 @@ def _row_monopole(ctx, dev, timed):
     A = ctx.upload(w.data, periodic=True, L=w.L)
     cnt = torch.zeros(len(w.edges0) - 1, dtype=torch.int64, device=f"cuda:{dev}")
 
+    cpr = [0]  # cells per reach: the library's density choice unless tuned
+
     def step():
-        ctx.grid([A], [w.edges0[-1]] * 3)
+        ctx.grid([A], [w.edges0[-1]] * 3, cpr[0])
         ctx.count("mono", A, None, w.edges0, out=cnt, want_oor=False)
 
-    # a small count: let the autotuner pick home objects, warps and slice
+    # a small count: let the autotuner pick the cell size, home objects,
+    # warps and slice
     ctx.grid([A], [w.edges0[-1]] * 3)
-    tuned = (ctx.autotune("mono", [(A, None)], w.edges0, tune_cells=False, max_items=1 << 30)
+    tuned = (ctx.autotune("mono", [(A, None)], w.edges0, tune_cells=True, max_items=1 << 30)
              if _ROW_TUNE else None)
+    if tuned:
+        cpr[0] = tuned["cells_per_reach"]
     t = timed(step)
     st = ctx.stats()
     out = {"monopole_c1_20k": {
