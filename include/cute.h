@@ -145,8 +145,9 @@ typedef struct {
    hot loop of Sec. 3.1-3.2).  Both catalogs need cell grids of the same
    geometry whose reach covers the largest edge on every axis.
    counts: n0 * n1 (n1 = 1 for 1-D kinds) uint64, host or device.
-   oor: if not NULL, receives the number of examined pairs that fall in no
-        bin (total pairs minus the sum of counts); host.
+   oor: if not NULL, receives the number of pairs that fall in no bin (all
+        pairs of the pair set, N_A N_B or N (N - 1) / 2, minus the sum of
+        counts); host.
    wsum: if d->weighted, n0 * n1 doubles (host or device) receiving the sum
         of w_i * w_j per bin, accurate to 1e-9 relative or better.
    Errors: CUTE_E_INVALID, CUTE_E_STATE (catalog or grid missing or on
