@@ -224,8 +224,10 @@ cute_status cute_set_timing(cute_ctx *ctx, int32_t on);
 
 /* Launch shape override for the counting kernel: home_per_lane in {2, 4}
    (objects of A held per lane; 0 = library default), warps_per_block
-   (0 = largest that fits), slice (neighbour objects per work item, 0 =
-   default, multiple of 64).  table_binning = 1 bins through lookup tables
+   (0 = library default: the most the kernel allows; at most 20 for plain
+   monopole and theta counts with 2 home objects per lane, 16 otherwise;
+   fewer if shared memory requires), slice (neighbour objects per work item, 0 = default, multiple
+   of 64).  table_binning = 1 bins through lookup tables
    even when the edges are uniform (0 = arithmetic binning for uniform
    edges).  Used by the autotuner and by tests of both binning paths. */
 cute_status cute_set_launch(cute_ctx *ctx, int32_t home_per_lane, int32_t warps_per_block,
@@ -233,7 +235,8 @@ cute_status cute_set_launch(cute_ctx *ctx, int32_t home_per_lane, int32_t warps_
 
 /* Autotuner: picks the launch shape of the counting kernel for the given
    descriptors (all sharing kind, edges and weighting) by timing candidates
-   on the GPU -- home objects per lane {2, 4}, warps per block {8, 12, 16}
+   on the GPU -- home objects per lane {2, 4}, warps per block {8, 12, 16,
+   20 where the kernel allows it}
    (within shared memory), neighbour slice {1024, 2048, 4096} -- each on at
    most max_items work items; if tune_cells, it also rebuilds the grids of
    the descriptors' catalogs at 2, 3 and 4 cells per reach and keeps the

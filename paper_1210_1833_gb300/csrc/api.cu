@@ -254,7 +254,7 @@ cute_status cute_set_launch(cute_ctx *ctx, int32_t hp, int32_t warps, int32_t sl
                             int32_t table_binning) {
   ENTER(ctx);
   if (hp != 0 && hp != 2 && hp != 4) return fail(ctx, CUTE_E_INVALID, "home_per_lane must be 0, 2 or 4");
-  if (warps < 0 || warps > 16) return fail(ctx, CUTE_E_INVALID, "warps_per_block must be 0..16");
+  if (warps < 0 || warps > 20) return fail(ctx, CUTE_E_INVALID, "warps_per_block must be 0..20");
   if (slice < 0 || slice % kTile) return fail(ctx, CUTE_E_INVALID, "slice must be a multiple of 64");
   ctx->hp_override = hp;
   ctx->warps_override = warps;
@@ -650,7 +650,9 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
   SmemLayout L = smem_layout((int)P.lut.size(), (int)P.band.size() / 2, P.nslots, P.R, pr.hp, acc);
   pr.acc = acc;
   size_t avail = ctx->smem_optin;
-  int warps = ctx->warps_override ? ctx->warps_override : (warps_tuned ? warps_tuned : 16);
+  const int wmax = count_max_warps(d[0].kind == CUTE_MONO || d[0].kind == CUTE_THETA, pr.hp, acc);
+  int warps = ctx->warps_override ? ctx->warps_override : (warps_tuned ? warps_tuned : wmax);
+  warps = std::min(warps, wmax);
   while (warps > 1 && (size_t)L.lut_bytes + (size_t)warps * L.warp_bytes > avail) warps--;
   if ((size_t)L.lut_bytes + (size_t)warps * L.warp_bytes > avail)
     return fail(ctx, CUTE_E_UNSUPPORTED,
@@ -980,7 +982,7 @@ cute_status cute_autotune(cute_ctx *ctx, int32_t n, const cute_pair_desc *d, int
   for (int k : ks) {
     if (tune_cells && (st = rebuild(k)) != CUTE_OK) break;
     for (int hp : {2, 4})
-      for (int warps : {8, 12, 16})
+      for (int warps : {8, 12, 16, 20})
         for (int slice : {1024, 2048, 4096}) {
           ctx->hp_override = hp;
           ctx->warps_override = warps;

@@ -567,7 +567,8 @@ __device__ __forceinline__ float shift_of(int code, float L) {
 }
 
 template <int KIND, bool PER, int HP, int ACC>
-__global__ void __launch_bounds__(512, 1) k_count(const KParams p) {
+__global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 1)
+    k_count(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const SmemLayout L = smem_layout(p.lut_words, p.band_words, p.nslots, p.R, HP, ACC);

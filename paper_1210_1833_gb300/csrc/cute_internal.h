@@ -76,6 +76,12 @@ constexpr int kSegSelf = 1;        // only j > i (unique pairs of a run with its
 constexpr int kSegNoSelfPair = 2;  // every j != i (full-stencil adjoint of an auto count)
 constexpr int kCounterWords = 7;  // work ticket + 6 statistics words
 constexpr int kMaxDevices = 64;   // per-device launch caches
+// Warps per block (one block per SM) the counting kernel is compiled for:
+// the plain monopole / chord count with two home objects per lane fits in
+// 96 registers and may run 20 warps; every other instantiation 16.
+constexpr int count_max_warps(int kernel_kind_mono, int hp, int acc) {
+  return (kernel_kind_mono && hp == 2 && acc == 0) ? 20 : 16;
+}
 constexpr int kModeCross = 0, kModeAutoHalf = 1, kModeAutoFull = 2;
 
 // One pair set (cat_a, cat_b) of a (possibly batched) count, as the

@@ -66,6 +66,24 @@ def test_mono_periodic_launch_shapes(ctx, cpr, hp):
     _assert_same(got, ref)
 
 
+def test_twenty_warps_where_allowed(ctx):
+    """The plain monopole kernel with two home objects per lane runs 20 warps
+    per block; other kernels clamp a request for 20 to 16.  Counts exact."""
+    table = ctx.table_binning if hasattr(ctx, "table_binning") else False
+    ctx.set_launch(home_per_lane=2, warps_per_block=20, table_binning=table)
+    try:
+        w = synthetic.c1_monopole_box(scale=0.3)
+        got = gpu_count(ctx, "mono", w.data, e0=w.edges0, periodic=True, L=w.L)
+        assert ctx.stats()["warps_per_block"] == 20
+        _assert_same(got, oracle_count("mono", w.data, e0=w.edges0, periodic=True, L=w.L))
+        v = synthetic.c2_rmu_lightcone(scale=0.004)
+        got = gpu_count(ctx, "rmu", v.data, v.randoms, v.edges0, v.edges1)
+        assert ctx.stats()["warps_per_block"] == 16
+        _assert_same(got, oracle_count("rmu", v.data, v.randoms, v.edges0, v.edges1, cells=True))
+    finally:
+        ctx.set_launch(table_binning=table)
+
+
 def test_mono_open_cross_and_auto(ctx):
     rng = np.random.default_rng(100)
     a = np.concatenate([rng.uniform(0, 300, size=(4000, 3)),
