@@ -105,6 +105,27 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def _cpu_model():
+    """The host CPU's model name (for the CPU baseline's record)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip().lower() == "model name":
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def _kernel_hash():
     import glob
     import hashlib
@@ -205,7 +226,7 @@ def run_reference(args, w, rank, world):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(w), sample="each step a bounded DR sample (below)"),
             "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": thr, "kind": "oracle",
-                             "sample": desc},
+                             "cpu": _cpu_model(), "sample": desc},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -368,7 +389,7 @@ def run_gpu(args, w, rank, world):
                          smax, src),
                      "kernel_ms": rr_ms, "candidate_pairs": state["rr_cand"]},
         "cpu_baseline": {"value": cpu_v, "unit": "pairs/s", "cores": cpu_thr, "kind": "oracle",
-                         "sample": cpu_desc},
+                         "cpu": _cpu_model(), "sample": cpu_desc},
         "e2e": {"value": e2e_value, "unit": "pairs/s", "ms_per_step": ms_e2e,
                 "h2d_bytes_per_step": int(w.data.nbytes + w.randoms.nbytes),
                 "d2h_bytes_per_step": int(3 * 8 * (len(w.edges0) - 1) * (len(w.edges1) - 1))},
