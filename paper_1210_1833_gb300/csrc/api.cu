@@ -426,12 +426,25 @@ ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax) {
   return ep;
 }
 
+// Per-warp budget of the count histogram's copies: plain counts take as
+// many copies (<= 32) as fit in 12 KB (fewer bank conflicts); weighted
+// counts, whose 32 float-float columns already take most of a warp's shared
+// memory and whose per-pair cost is the column update, keep about 1 KB so
+// that more warps fit.
+size_t hist_budget(const cute_pair_desc *d, int acc) {
+  if (acc != 1) return 12288;
+  const bool two_d = (d->kind == CUTE_R_MU || d->kind == CUTE_SIGMA_PI);
+  const size_t nslots = (size_t)(d->n0 + 2) * (two_d ? (size_t)(d->n1 + 2) : 1u);
+  return std::min<size_t>(12288, std::max<size_t>(1024, nslots * 4));
+}
+
 cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &ep, int hp,
-                     std::shared_ptr<Plan> &out) {
+                     int acc, std::shared_ptr<Plan> &out) {
   std::ostringstream key;
   key.precision(17);
+  const size_t hb = hist_budget(d, acc);
   key << d->kind << "|" << ep.eta0 << "|" << ep.eta_l << "|" << ep.lmin << "|" << hp << "|"
-      << ctx->table_binning << "|";
+      << ctx->table_binning << "|" << hb << "|";
   for (int k = 0; k <= d->n0; k++) key << d->edges0[k] << ",";
   if (d->kind == CUTE_R_MU || d->kind == CUTE_SIGMA_PI)
     for (int k = 0; k <= d->n1; k++) key << d->edges1[k] << ",";
@@ -443,7 +456,7 @@ cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &
   auto P = std::make_shared<Plan>();
   const bool two_d = (d->kind == CUTE_R_MU || d->kind == CUTE_SIGMA_PI);
   std::string m = plan_build((int)d->kind, d->edges0, d->n0, d->edges1, two_d ? d->n1 : 1, ep,
-                             two_d ? 8192 : 8192, 12288, !ctx->table_binning, *P);
+                             two_d ? 8192 : 8192, hb, !ctx->table_binning, *P);
   if (!m.empty()) return fail(ctx, CUTE_E_UNSUPPORTED, m);
   auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
     cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
@@ -642,7 +655,7 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
       warps_tuned = it->second.warps_per_block;
     }
   }
-  cute_status st = get_plan(ctx, &d[0], ep, pr.hp, pr.plan);
+  cute_status st = get_plan(ctx, &d[0], ep, pr.hp, acc, pr.plan);
   if (st != CUTE_OK) return st;
   st = get_work(ctx, pr.dis, pr.hp, slice, full_stencil, pr.ts);
   if (st != CUTE_OK) return st;
