@@ -427,22 +427,26 @@ ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax) {
 }
 
 // Per-warp budget of the count histogram's copies: plain counts take as
-// many copies (<= 32) as fit in 12 KB (fewer bank conflicts); weighted
-// counts, whose 32 float-float columns already take most of a warp's shared
-// memory and whose per-pair cost is the column update, keep about 1 KB so
-// that more warps fit.
-size_t hist_budget(const cute_pair_desc *d, int acc) {
-  if (acc != 1) return 12288;
+// many copies (<= 32) as fit in 12 KB (fewer bank conflicts), 4 KB for the
+// kernel that runs 20 warps (plain monopole / theta, two home objects per
+// lane) so that 20 warps fit beside the binning tables; weighted counts,
+// whose 32 float-float columns already take most of a warp's shared memory
+// and whose per-pair cost is the column update, keep about 1 KB so that
+// more warps fit.
+size_t hist_budget(const cute_pair_desc *d, int acc, int hp) {
   const bool two_d = (d->kind == CUTE_R_MU || d->kind == CUTE_SIGMA_PI);
   const size_t nslots = (size_t)(d->n0 + 2) * (two_d ? (size_t)(d->n1 + 2) : 1u);
-  return std::min<size_t>(12288, std::max<size_t>(1024, nslots * 4));
+  size_t want = 12288;
+  if (acc == 1) want = 1024;
+  else if (acc == 0 && count_max_warps(!two_d, hp, acc) > 16) want = 4096;
+  return std::min<size_t>(12288, std::max<size_t>(want, nslots * 4));
 }
 
 cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &ep, int hp,
                      int acc, std::shared_ptr<Plan> &out) {
   std::ostringstream key;
   key.precision(17);
-  const size_t hb = hist_budget(d, acc);
+  const size_t hb = hist_budget(d, acc, hp);
   key << d->kind << "|" << ep.eta0 << "|" << ep.eta_l << "|" << ep.lmin << "|" << hp << "|"
       << ctx->table_binning << "|" << hb << "|";
   for (int k = 0; k <= d->n0; k++) key << d->edges0[k] << ",";

@@ -20,7 +20,7 @@
 #include <mutex>
 
 namespace cute {
-size_t hist_budget(const cute_pair_desc *d, int acc);  // api.cu
+size_t hist_budget(const cute_pair_desc *d, int acc, int hp);  // api.cu
 cudaError_t launch_count_mono(const KParams &p, bool periodic, int acc, int hp, int blocks,
                               int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_count_sigpi(const KParams &p, bool periodic, int acc, int hp, int blocks,
@@ -105,7 +105,7 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   // binning plan, chunks and stencil on the host
   Plan P;
   std::string m = plan_build(kind, d->edges0, d->n0, d->edges1, two_d ? d->n1 : 1, ep, 8192,
-                             hist_budget(d, acc), !ctx->table_binning, P);
+                             hist_budget(d, acc, hp), !ctx->table_binning, P);
   if (!m.empty()) return na_fail(ctx, CUTE_E_UNSUPPORTED, m);
   std::vector<int4> chunks, stencil;
   if (di.A->n > 0 && di.B->n > 0) {
