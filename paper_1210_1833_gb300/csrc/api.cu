@@ -648,6 +648,10 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
       objs += (double)di.A->n;
     }
     pr.hp = (objs > 0 && dens / objs >= 2000.0) ? 4 : 2;
+    // plain monopole / theta counts: the two-per-lane kernel runs 20 warps,
+    // which outweighs the denser rows' case for four (c3 DD: 3.20 s against
+    // 3.32 s)
+    if (acc == 0 && (d[0].kind == CUTE_MONO || d[0].kind == CUTE_THETA)) pr.hp = 2;
   }
   int slice = ctx->slice_override ? ctx->slice_override : 2048;
   int warps_tuned = 0;

@@ -100,6 +100,7 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
 
   int hp = ctx->hp_override;
   if (!hp) hp = row_density(*di.A, *di.g) < 2000.0 ? 2 : 4;
+  if (!ctx->hp_override && acc == 0 && (kind == CUTE_MONO || kind == CUTE_THETA)) hp = 2;
   const int slice = ctx->slice_override ? ctx->slice_override : 2048;
 
   // binning plan, chunks and stencil on the host
