@@ -1,10 +1,13 @@
-// Host check of the counting kernel's FP32 binning with uniform edges: the
+// Host check of the counting kernel's FP32 binning.  Uniform edges: the
 // kernel's arithmetic (count_impl.cuh: mono_arith2, sigpi_arith2,
-// rmu_values2 + rmu_arith2, one element of each packed pair) is replayed
-// here in the same operation order with IEEE FP32 operations, the hardware
-// reciprocal square root replaced by 1/sqrt perturbed by up to its
-// documented 2^-22.9 relative error (at both extremes and at random), and
-// the near-edge thresholds taken from the host planner (plan_build).  On
+// rmu_values2 + rmu_arith2, one element of each packed pair); other edges:
+// the table path (the FP32 values of the table loop, then count_kernel.cuh's
+// lut_get, axis_resolve and mu_resolve on the planner's own table and band
+// arrays).  Both are replayed here in the same operation order with IEEE
+// FP32 operations, the hardware reciprocal square root replaced by 1/sqrt
+// perturbed by up to its documented 2^-22.9 relative error (at both
+// extremes and at random), and the near-edge thresholds taken from the host
+// planner (plan_build).  On
 // pairs placed on and around every edge, open and periodic, every pair the
 // kernel would NOT flag as near must land in the slot of the canonical FP64
 // formulas (Sec. 2.2: squared separations against squared edges, minimum
@@ -55,6 +58,107 @@ static float rsqrt_dev(float x) {
 }
 
 struct Slot { int slot; float score; };
+
+// ---- table binning
+static float f32_toward(double v, bool up) {
+  float f = (float)v;
+  if (up && (double)f < v) f = std::nextafter(f, INFINITY);
+  if (!up && (double)f > v) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+// bands of table axis `axis` f times as wide about their edges E (squared
+// edges; the mu axis scales the per-class bound instead)
+static void shrink_table(Plan &P, int axis, const std::vector<double> &E) {
+  if (g_f == 1.0) return;
+  AxisPlan &a = P.ax[axis];
+  if (P.kind == KRMU && axis == 1) {
+    P.mu_eps_base = (float)(g_f * P.mu_eps_base);
+    return;
+  }
+  for (int k = 0; k < (int)E.size(); k++) {
+    float &lo = P.band[2 * (a.band_off + 1 + k)], &hi = P.band[2 * (a.band_off + 1 + k) + 1];
+    if (!std::isfinite(lo) || !std::isfinite(hi)) continue;
+    lo = f32_toward(E[k] - g_f * (E[k] - (double)lo), false);
+    hi = f32_toward(E[k] + g_f * ((double)hi - E[k]), true);
+  }
+}
+static bool g_lut_oob = false;  // a table index outside the axis's cells
+static uint32_t lut_get(const Plan &P, const AxisPlan &a, float &v) {
+  v = std::fmin(v, a.vmax);  // fminf: NaN becomes vmax
+  uint32_t idx;
+  if (a.mode == kLutLinear) {
+    idx = bits(ffma(v, a.scale, 8388608.0f)) - 0x4B000000u;
+  } else {
+    const int i = (int)(bits(v) >> a.shift) - a.base;
+    idx = (uint32_t)std::max(i, 0);
+  }
+  if (idx >= (uint32_t)a.ncell) { g_lut_oob = true; return 0; }
+  return P.lut[a.lut_off + idx];
+}
+static uint32_t axis_resolve(const Plan &P, const AxisPlan &a, float v, uint32_t e,
+                             uint32_t stride, bool &near) {
+  const uint32_t b = e >> kBandShift, off = e & kOffMask;
+  float lo = INFINITY, hi = INFINITY;
+  if (b != 0u) { lo = P.band[2 * (a.band_off + b)]; hi = P.band[2 * (a.band_off + b) + 1]; }
+  const bool above = v > hi;
+  near = (v >= lo) && !above;
+  return above ? off + stride : off;
+}
+static uint32_t mu_resolve(const Plan &P, const AxisPlan &a, float mu, uint32_t e,
+                           uint32_t stride, float eps, bool &near) {
+  const uint32_t b = e >> kBandShift, off = e & kOffMask;
+  const float m = b != 0u ? P.band[2 * (a.band_off + b)] : INFINITY;
+  const float d = fadd(mu, -m);
+  near = std::fabs(d) <= eps;
+  return d > eps ? off + stride : off;
+}
+// slot and near flag of one pair from its FP32 table values (a, b)
+static int table_slot(const Plan &P, float a, float b, bool &near) {
+  const uint32_t stride0 = (uint32_t)P.slots1 * P.R * 4u, stride1 = (uint32_t)P.R * 4u;
+  uint32_t o;
+  if (P.kind == KMONO || P.kind == KTHETA) {
+    const uint32_t e0 = lut_get(P, P.ax[0], a);
+    o = axis_resolve(P, P.ax[0], a, e0, stride0, near);
+  } else {
+    const uint32_t e0 = lut_get(P, P.ax[0], a), e1 = lut_get(P, P.ax[1], b);
+    bool n0, n1;
+    o = axis_resolve(P, P.ax[0], a, e0, stride0, n0);
+    if (P.kind == KSIGPI) {
+      o += axis_resolve(P, P.ax[1], b, e1, stride1, n1);
+    } else {
+      uint32_t eb = bits(P.mu_eps_base) + (((e0 >> kClassShift) & 0xFu) << 23);
+      float eps;
+      std::memcpy(&eps, &eb, 4);
+      o += mu_resolve(P, P.ax[1], b, e1, stride1, eps, n1);
+    }
+    near = n0 || n1;
+  }
+  return (int)(o / ((uint32_t)P.R * 4u));
+}
+static Slot mono_table(const Plan &P, const float *q, const float *n) {
+  const float dx = fadd(q[0], n[0]), dy = fadd(q[1], n[1]), dz = fadd(q[2], n[2]);
+  const float v = ffma(dz, dz, ffma(dy, dy, fmul(dx, dx)));
+  bool near;
+  const int s = table_slot(P, v, v, near);
+  return {s, near ? 1.0f : 0.0f};
+}
+static Slot sigpi_table(const Plan &P, const float *q, const float *n) {
+  const float dx = fadd(q[0], n[0]), dy = fadd(q[1], n[1]), dz = fadd(q[2], n[2]);
+  bool near;
+  const int s = table_slot(P, ffma(dy, dy, fmul(dx, dx)), fmul(dz, dz), near);
+  return {s, near ? 1.0f : 0.0f};
+}
+static Slot rmu_table(const Plan &P, const float *q, const float *n, const float *xi, float aq) {
+  const float dx = fadd(q[0], n[0]), dy = fadd(q[1], n[1]), dz = fadd(q[2], n[2]);
+  const float r2 = ffma(dz, dz, ffma(dy, dy, ffma(dx, dx, kVFloor)));
+  const float sx = ffma(dz, xi[2], ffma(dy, xi[1], fmul(dx, xi[0])));
+  const float sl = ffma(sx, 2.0f, r2);
+  const float l2 = ffma(sx, 4.0f, fadd(aq, r2));
+  const float mu = fmul(std::fabs(sl), rsqrt_dev(fmul(r2, l2)));
+  bool near;
+  const int s = table_slot(P, r2, mu, near);
+  return {s, near ? 1.0f : 0.0f};
+}
 
 // one pair, monopole / chord: q neighbour offsets, n = -(home - shift)
 static Slot mono_fp32(const AxisPlan &a, const float *q, const float *n) {
@@ -175,10 +279,33 @@ static void kernel_inputs(const double *a, const double *b, const double *fo, do
   }
 }
 
-static Tally run_mono(double step, int n, double L, double xm_spread, bool chord,
-                      std::mt19937_64 &g) {
-  std::vector<double> e(n + 1), E(n + 1);
-  for (int k = 0; k <= n; k++) { e[k] = k * step; E[k] = e[k] * e[k]; }
+static std::vector<double> uniform(double step, int n) {
+  std::vector<double> e(n + 1);
+  for (int k = 0; k <= n; k++) e[k] = k * step;
+  return e;
+}
+static std::vector<double> logspace(double lo, double hi, int n) {
+  std::vector<double> e(n + 1);
+  for (int k = 0; k <= n; k++) e[k] = lo * std::pow(hi / lo, (double)k / n);
+  return e;
+}
+static std::vector<double> squares(const std::vector<double> &e) {
+  std::vector<double> E(e.size());
+  for (size_t k = 0; k < e.size(); k++) E[k] = e[k] * e[k];
+  return E;
+}
+static bool plan_ok(const std::string &m, const Plan &P, bool arith) {
+  const bool got = P.ax[0].mode == kArith;
+  if (m.empty() && got == arith) return true;
+  std::printf("  plan: %s (arithmetic binning %d, wanted %d)\n", m.c_str(), got, arith);
+  return false;
+}
+
+// edges e (uniform from 0: the arithmetic path; otherwise the table path)
+static Tally run_mono(const std::vector<double> &e, double L, double xm_spread, bool chord,
+                      bool arith, std::mt19937_64 &g) {
+  const int n = (int)e.size() - 1;
+  const std::vector<double> E = squares(e);
   const double fo[3] = {chord ? 0.0 : (L > 0 ? 0.5 * L : 1234.5),
                         chord ? 0.0 : (L > 0 ? 0.5 * L : -300.25),
                         chord ? 0.97 : (L > 0 ? 0.5 * L : 77.0)};
@@ -186,11 +313,12 @@ static Tally run_mono(double step, int n, double L, double xm_spread, bool chord
   Plan P;
   const std::string m = plan_build(chord ? KTHETA : KMONO, e.data(), n, nullptr, 1,
                                    eparams(xm, L, e[n], 0, 0), 8192, 12288, true, P);
-  if (!m.empty() || P.ax[0].mode != kArith) { std::printf("  plan: %s\n", m.c_str()); return Tally{0, 0, 1}; }
-  shrink(P.ax[0]);
+  if (!plan_ok(m, P, arith)) return Tally{0, 0, 1};
+  if (arith) shrink(P.ax[0]);
+  else shrink_table(P, 0, E);
   std::uniform_real_distribution<double> U(-1, 1);
   Tally t;
-  for (int k = 1; k <= n; k++)
+  for (int k = e[0] > 0 ? 0 : 1; k <= n; k++)
     for (double off : kOff)
       for (int rep = 0; rep < 24; rep++) {
         double a[3], b[3], u[3];
@@ -222,30 +350,35 @@ static Tally run_mono(double step, int n, double L, double xm_spread, bool chord
         for (int c = 0; c < 3; c++) dd[c] = wrap(b[c] - a[c], L);
         const int cb = bin64(E, (dd[0] * dd[0] + dd[1] * dd[1]) + dd[2] * dd[2]);
         const int canon = cb < 0 ? -1 : cb + 1;
-        const Slot r = mono_fp32(P.ax[0], q, nn);
+        const Slot r = arith ? mono_fp32(P.ax[0], q, nn) : mono_table(P, q, nn);
         const int fp32 = (r.slot >= 1 && r.slot <= n) ? r.slot : -1;
-        t.add(r.score >= P.ax[0].near_at, fp32, canon);
+        t.add(arith ? r.score >= P.ax[0].near_at : r.score > 0.0f, fp32, canon);
       }
   return t;
 }
 
-static Tally run_sigpi(double s0, int n0, double s1, int n1, double L, std::mt19937_64 &g) {
-  std::vector<double> e0(n0 + 1), e1(n1 + 1), E0(n0 + 1), E1(n1 + 1);
-  for (int k = 0; k <= n0; k++) { e0[k] = k * s0; E0[k] = e0[k] * e0[k]; }
-  for (int k = 0; k <= n1; k++) { e1[k] = k * s1; E1[k] = e1[k] * e1[k]; }
+static Tally run_sigpi(const std::vector<double> &e0, const std::vector<double> &e1, double L,
+                       bool arith, std::mt19937_64 &g) {
+  const int n0 = (int)e0.size() - 1, n1 = (int)e1.size() - 1;
+  const std::vector<double> E0 = squares(e0), E1 = squares(e1);
   const double fo[3] = {0.5 * L, 0.5 * L, 0.5 * L};
   Plan P;
   const std::string m = plan_build(KSIGPI, e0.data(), n0, e1.data(), n1,
                                    eparams(0.5 * L, L, std::max(e0[n0], e1[n1]), 0, 0), 8192, 12288,
                                    true, P);
-  if (!m.empty() || P.ax[0].mode != kArith) { std::printf("  plan: %s\n", m.c_str()); return Tally{0, 0, 1}; }
-  shrink(P.ax[0]);
-  shrink(P.ax[1]);
-  P.ax[1].near_scale = (float)((double)P.ax[0].near_at / (double)P.ax[1].near_at);
+  if (!plan_ok(m, P, arith)) return Tally{0, 0, 1};
+  if (arith) {
+    shrink(P.ax[0]);
+    shrink(P.ax[1]);
+    P.ax[1].near_scale = (float)((double)P.ax[0].near_at / (double)P.ax[1].near_at);
+  } else {
+    shrink_table(P, 0, E0);
+    shrink_table(P, 1, E1);
+  }
   std::uniform_real_distribution<double> U(-1, 1), U01(0, 1);
   Tally t;
   for (int axis = 0; axis < 2; axis++)
-    for (int k = 1; k <= (axis ? n1 : n0); k++)
+    for (int k = (axis ? e1 : e0)[0] > 0 ? 0 : 1; k <= (axis ? n1 : n0); k++)
       for (double off : kOff)
         for (int rep = 0; rep < 16; rep++) {
           const double ed = (axis ? e1[k] : e0[k]) * (1.0 + off);
@@ -264,34 +397,37 @@ static Tally run_sigpi(double s0, int n0, double s1, int n1, double L, std::mt19
           for (int c = 0; c < 3; c++) dd[c] = wrap(b[c] - a[c], L);
           const int bs = bin64(E0, dd[0] * dd[0] + dd[1] * dd[1]), bp = bin64(E1, dd[2] * dd[2]);
           const int canon = (bs < 0 || bp < 0) ? -1 : (bs + 1) * (n1 + 2) + bp + 1;
-          const Slot r = sigpi_fp32(P.ax[0], P.ax[1], P.slots1, q, nn);
+          const Slot r = arith ? sigpi_fp32(P.ax[0], P.ax[1], P.slots1, q, nn) : sigpi_table(P, q, nn);
           const int s0i = r.slot / P.slots1, s1i = r.slot % P.slots1;
           const int fp32 = (s0i >= 1 && s0i <= n0 && s1i >= 1 && s1i <= n1) ? r.slot : -1;
-          t.add(r.score >= P.ax[0].near_at, fp32, canon);
+          t.add(arith ? r.score >= P.ax[0].near_at : r.score > 0.0f, fp32, canon);
         }
   return t;
 }
 
 // (r, mu) on a light-cone-like region: objects around centre fo (observer
 // at the origin), extent xm about fo
-static Tally run_rmu(const double *fo, double xm, double rmin, double absmax, double s0, int n0,
-                     int n1, std::mt19937_64 &g) {
-  std::vector<double> e0(n0 + 1), e1(n1 + 1), E0(n0 + 1), M(n1 + 1);
-  for (int k = 0; k <= n0; k++) { e0[k] = k * s0; E0[k] = e0[k] * e0[k]; }
-  for (int k = 0; k <= n1; k++) { e1[k] = (double)k / n1; M[k] = e1[k] * e1[k]; }
+static Tally run_rmu(const double *fo, double xm, double rmin, double absmax,
+                     const std::vector<double> &e0, int n1, std::vector<double> rs, bool arith,
+                     std::mt19937_64 &g) {
+  const int n0 = (int)e0.size() - 1;
+  std::vector<double> e1(n1 + 1);
+  for (int k = 0; k <= n1; k++) e1[k] = (double)k / n1;
+  const std::vector<double> E0 = squares(e0), M = squares(e1);
   Plan P;
   const std::string m = plan_build(KRMU, e0.data(), n0, e1.data(), n1,
                                    eparams(xm, 0, e0[n0], absmax, rmin), 8192, 12288, true, P);
-  if (!m.empty() || P.ax[0].mode != kArith || P.ax[1].mode != kArith) {
-    std::printf("  plan: %s\n", m.c_str());
-    return Tally{0, 0, 1};
+  if (!plan_ok(m, P, arith) || (arith && P.ax[1].mode != kArith)) return Tally{0, 0, 1};
+  if (arith) {
+    shrink(P.ax[0]);
+    shrink(P.ax[1]);
+  } else {
+    shrink_table(P, 0, E0);
+    shrink_table(P, 1, M);
   }
-  shrink(P.ax[0]);
-  shrink(P.ax[1]);
   const float thr = std::fmin(P.ax[0].near_at, P.ax[1].near_c);
   std::uniform_real_distribution<double> U(-1, 1);
   Tally t;
-  const double rs[] = {0.4, 2.0, 4.999, 5.0, 12.5, 33.0, 77.0, 120.0, 180.0, 199.9, 200.0};
   for (double r : rs)
     for (int k = 0; k <= n1; k++)
       for (double off : kOff)
@@ -340,10 +476,11 @@ static Tally run_rmu(const double *fo, double xm, double rmin, double absmax, do
           (void)zero;
           for (int c = 0; c < 3; c++) xf[c] = (float)xi[c];
           const float aq = (float)(4.0 * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]));
-          const Slot res = rmu_fp32(P.ax[0], P.ax[1], P.slots1, q, nn, xf, aq);
+          const Slot res = arith ? rmu_fp32(P.ax[0], P.ax[1], P.slots1, q, nn, xf, aq)
+                                 : rmu_table(P, q, nn, xf, aq);
           const int s0i = res.slot / P.slots1, s1i = res.slot % P.slots1;
           const int fp32 = (s0i >= 1 && s0i <= n0 && s1i >= 1 && s1i <= n1) ? res.slot : -1;
-          t.add(res.score >= thr, fp32, canon);
+          t.add(arith ? res.score >= thr : res.score > 0.0f, fp32, canon);
         }
   return t;
 }
@@ -356,21 +493,43 @@ int main(int argc, char **argv) {
     std::printf("%s %ld %ld %ld\n", name, t.cases, t.flagged, t.bad);
     bad += t.bad;
   };
+  const std::vector<double> rs_u = {0.4, 2.0, 4.999, 5.0, 12.5, 33.0, 77.0, 120.0, 180.0, 199.9, 200.0};
+  const std::vector<double> r_log = logspace(1.0, 200.0, 20);
+  std::vector<double> rs_l = rs_u;
+  rs_l.insert(rs_l.end(), r_log.begin(), r_log.end());
+  // chords of log-spaced angles 0.01 .. 10 degrees
+  std::vector<double> chords = logspace(0.01, 10.0, 24);
+  for (double &c : chords) c = 2.0 * std::sin(0.5 * c * 3.141592653589793 / 180.0);
+  const double fo[3] = {1250.0, 1083.0, 625.0};
   for (g_mode = 0; g_mode < 3; g_mode++) {
     char nm[64];
     std::snprintf(nm, sizeof nm, "mono_periodic_r%d", g_mode);
-    report(nm, run_mono(5.0, 30, 2000.0, 0, false, g));
+    report(nm, run_mono(uniform(5.0, 30), 2000.0, 0, false, true, g));
     std::snprintf(nm, sizeof nm, "mono_periodic_small_r%d", g_mode);
-    report(nm, run_mono(5.0, 40, 1000.0, 0, false, g));
+    report(nm, run_mono(uniform(5.0, 40), 1000.0, 0, false, true, g));
     std::snprintf(nm, sizeof nm, "mono_open_r%d", g_mode);
-    report(nm, run_mono(2.5, 40, 0.0, 1400.0, false, g));
+    report(nm, run_mono(uniform(2.5, 40), 0.0, 1400.0, false, true, g));
     std::snprintf(nm, sizeof nm, "chord_r%d", g_mode);
-    report(nm, run_mono(0.0027, 64, 0.0, 0, true, g));
+    report(nm, run_mono(uniform(0.0027, 64), 0.0, 0, true, true, g));
     std::snprintf(nm, sizeof nm, "sigpi_periodic_r%d", g_mode);
-    report(nm, run_sigpi(3.0, 50, 3.0, 50, 1500.0, g));
-    const double fo[3] = {1250.0, 1083.0, 625.0};
+    report(nm, run_sigpi(uniform(3.0, 50), uniform(3.0, 50), 1500.0, true, g));
     std::snprintf(nm, sizeof nm, "rmu_lightcone_r%d", g_mode);
-    report(nm, run_rmu(fo, 1250.0, 1000.0, 2500.0, 5.0, 40, 40, g));
+    report(nm, run_rmu(fo, 1250.0, 1000.0, 2500.0, uniform(5.0, 40), 40, rs_u, true, g));
+    // the table path (edges not uniform from 0)
+    std::snprintf(nm, sizeof nm, "table_mono_periodic_r%d", g_mode);
+    report(nm, run_mono(logspace(0.1, 150.0, 20), 2000.0, 0, false, false, g));
+    std::snprintf(nm, sizeof nm, "table_mono_open_r%d", g_mode);
+    report(nm, run_mono(logspace(1.0, 200.0, 16), 0.0, 1400.0, false, false, g));
+    std::snprintf(nm, sizeof nm, "table_chord_r%d", g_mode);
+    report(nm, run_mono(chords, 0.0, 0, true, false, g));
+    std::snprintf(nm, sizeof nm, "table_sigpi_periodic_r%d", g_mode);
+    report(nm, run_sigpi(logspace(0.5, 60.0, 15), uniform(2.0, 30), 1500.0, false, g));
+    std::snprintf(nm, sizeof nm, "table_rmu_lightcone_r%d", g_mode);
+    report(nm, run_rmu(fo, 1250.0, 1000.0, 2500.0, r_log, 10, rs_l, false, g));
+  }
+  if (g_lut_oob) {
+    std::printf("table index outside the table\n");
+    bad++;
   }
   return bad ? 1 : 0;
 }

@@ -1,12 +1,15 @@
-"""Host check of the counting kernel's FP32 near-edge bands (uniform edges):
+"""Host check of the counting kernel's FP32 near-edge bands:
 tests/fp32_band_check.cpp replays the kernel's FP32 binning arithmetic (same
 operation order, IEEE roundings, the hardware reciprocal square root anywhere
-within its documented error) with the thresholds of the host planner, on
-pairs on and around every edge of the monopole, chord, (sigma, pi) and
-(r, mu) binnings; no pair the kernel would not re-test may fall in another
-slot than the canonical FP64 formulas give (Sec. 2.2, Sec. 3.4).  The check
-also runs with the thresholds' distance from 1/2 halved, so the planner's
-bounds keep at least a factor 2 over what these pairs need."""
+within its documented error) with the thresholds, tables and bands of the
+host planner, on pairs on and around every edge of the monopole, chord,
+(sigma, pi) and (r, mu) binnings -- uniform edges from 0 (binning by
+arithmetic) and log-spaced edges (the lookup-table path); no pair the kernel
+would not re-test may fall in another slot than the canonical FP64 formulas
+give (Sec. 2.2, Sec. 3.4).  The check also runs with the thresholds' (and
+bands') distance from the edge halved and at 0.3, so the planner's bounds
+keep a margin over what these pairs need; with the bands collapsed it must
+find misbinned pairs, so the replay does detect a too-narrow band."""
 import os
 import shutil
 import subprocess
@@ -53,10 +56,20 @@ def _run(exe, factor):
     return r.returncode, rows, r.stdout
 
 
-@pytest.mark.parametrize("factor", [1.0, 0.5])
+@pytest.mark.parametrize("factor", [1.0, 0.5, 0.3])
 def test_no_unflagged_pair_is_misbinned(exe, factor):
     rc, rows, out = _run(exe, factor)
-    assert len(rows) == 18, out  # 6 scenarios x 3 ways of rounding the rsqrt
+    # 11 scenarios (6 arithmetic, 5 table) x 3 ways of rounding the rsqrt
+    assert len(rows) == 33, out
+    assert sum(n.startswith("table_") for n in rows) == 15, out
     for name, (cases, flagged, bad) in rows.items():
         assert cases > 1000 and bad == 0, (name, out)
     assert rc == 0, out
+
+
+def test_collapsed_bands_are_caught(exe):
+    # thresholds at the edge itself: every scenario must show misbinned pairs
+    rc, rows, out = _run(exe, 0.0)
+    assert len(rows) == 33 and rc == 1, out
+    for name, (cases, flagged, bad) in rows.items():
+        assert bad > 0, (name, out)
