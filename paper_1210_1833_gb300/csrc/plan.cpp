@@ -318,7 +318,7 @@ static bool make_arith(const double *e, int n, const AxisErr &err, double eta0, 
   // component (|dz|): that factor 2 is the margin over the analysed bound
   // (a host check replaying the kernel's arithmetic on pairs around every
   // edge finds no miss with thresholds at 0.3 of this distance, the first
-  // ones at a quarter)
+  // ones near a quarter)
   p.thr_a = 0;
   p.thr_b = (float)(T + 1e-6);
   return p.thr_b < 0.2f;

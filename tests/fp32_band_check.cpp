@@ -497,8 +497,8 @@ int main(int argc, char **argv) {
   const std::vector<double> r_log = logspace(1.0, 200.0, 20);
   std::vector<double> rs_l = rs_u;
   rs_l.insert(rs_l.end(), r_log.begin(), r_log.end());
-  // chords of log-spaced angles 0.01 .. 10 degrees
-  std::vector<double> chords = logspace(0.01, 10.0, 24);
+  // chords of 64 log-spaced angles 0.01 .. 10 degrees (the w(theta) workload)
+  std::vector<double> chords = logspace(0.01, 10.0, 64);
   for (double &c : chords) c = 2.0 * std::sin(0.5 * c * 3.141592653589793 / 180.0);
   const double fo[3] = {1250.0, 1083.0, 625.0};
   for (g_mode = 0; g_mode < 3; g_mode++) {
