@@ -8,6 +8,8 @@ uniform periodic boxes (Eq. 12-13), the pair-total invariant, DR/RD symmetry,
 and the marginal relations between the (r,mu), (sigma,pi) and monopole
 histograms (Eq. 2, Eq. 4).
 """
+import functools
+import itertools
 import json
 import math
 import os
@@ -137,6 +139,100 @@ def test_rmu_matches_explicit_cosine():
     ok = r < 40
     h, _, _ = np.histogram2d(r[ok], np.minimum(mu[ok], 1.0 - 1e-15), bins=[e0, e1])
     assert c.tolist() == h.astype(np.int64).tolist()
+
+
+@functools.lru_cache(maxsize=1)
+def _mu_edge_pairs():
+    """Integer point pairs (x_i, x_j), both with z >= 1, whose separation
+    s = x_j - x_i makes exactly 60 degrees with the line of sight
+    l = x_i + x_j: 4 (s.l)^2 = |s|^2 |l|^2, i.e. mu = 1/2 exactly."""
+    g = np.array([v for v in itertools.product(range(-4, 5), repeat=3) if any(v)], dtype=np.int64)
+    sv, lv = np.repeat(g, len(g), axis=0), np.tile(g, (len(g), 1))
+    sl = (sv * lv).sum(1)
+    ok = ((lv - sv) % 2 == 0).all(1) & (sl != 0) & (4 * sl * sl == (sv * sv).sum(1) * (lv * lv).sum(1))
+    xi, xj = (lv[ok] - sv[ok]) // 2, (lv[ok] + sv[ok]) // 2
+    up = (xi[:, 2] >= 1) & (xj[:, 2] >= 1)
+    return xi[up], xj[up]
+
+
+def _exact_counts(kind, a, b, e0, e1, L):
+    """Brute-force histogram of integer points in exact integer arithmetic
+    (Eq. 11 with half-open bins on squared integer edges; (sigma, pi) along
+    z, Eq. 2; (r, mu) about the pair midpoint with mu edges k/4, compared as
+    16 (s.l)^2 >= k^2 |s|^2 |l|^2).  b None: unique pairs of a.  Also
+    returns how many pairs sit exactly on an edge."""
+    if b is None:
+        i, j = np.triu_indices(len(a), 1)
+        A, B = a[i], a[j]
+    else:
+        i, j = np.indices((len(a), len(b))).reshape(2, -1)
+        A, B = a[i], b[j]
+    E0 = np.asarray(e0, dtype=np.int64) ** 2
+
+    def bins(v, E):
+        return np.where((v >= E[0]) & (v < E[-1]), np.searchsorted(E, v, side="right") - 1, -1)
+
+    ties = 0
+    if kind == "rmu":
+        s, l = B - A, A + B
+        r2, l2, sl = (s * s).sum(1), (l * l).sum(1), (s * l).sum(1)
+        b0 = bins(r2, E0)
+        k4 = np.rint(np.asarray(e1) * 4).astype(np.int64)
+        assert np.array_equal(k4, np.asarray(e1) * 4)
+        q16, den = 16 * sl * sl, r2 * l2
+        b1 = np.zeros(len(r2), dtype=np.int64)
+        for k in range(1, len(k4) - 1):
+            b1 = np.where(q16 >= k4[k] ** 2 * den, k, b1)
+            ties += int(np.sum((q16 == k4[k] ** 2 * den) & (b0 >= 0) & (r2 > 0)))
+        b1 = np.where(r2 == 0, 0, b1)  # coincident points: no direction, mu bin 0
+        n1 = len(k4) - 1
+    else:
+        d = B - A
+        if L:
+            d = np.where(2 * d > L, d - L, np.where(2 * d < -L, d + L, d))
+        if kind == "mono":
+            b0, b1, n1 = bins((d * d).sum(1), E0), np.zeros(len(d), dtype=np.int64), 1
+        else:
+            E1 = np.asarray(e1, dtype=np.int64) ** 2
+            b0, b1, n1 = bins((d[:, :2] ** 2).sum(1), E0), bins(d[:, 2] ** 2, E1), len(E1) - 1
+            ties += int(np.isin(d[:, 2] ** 2, E1[1:]).sum())
+        ties += int(np.isin((d * d).sum(1) if kind == "mono" else (d[:, :2] ** 2).sum(1),
+                            E0[1:]).sum())
+    ok = (b0 >= 0) & (b1 >= 0)
+    h = np.bincount(b0[ok] * n1 + b1[ok], minlength=(len(E0) - 1) * n1)
+    return h.reshape(len(E0) - 1, n1), int((~ok).sum()), ties
+
+
+@pytest.mark.parametrize("kind,periodic", [("mono", False), ("mono", True), ("sigpi", False),
+                                           ("sigpi", True), ("rmu", False)])
+def test_integer_lattice_matches_exact_arithmetic(kind, periodic):
+    """Integer coordinates and edges make every FP64 quantity of the
+    canonical formulas exact, so the oracle must equal a brute force in
+    exact integer arithmetic, including the many pairs that sit exactly on
+    an edge (half-open bins); (sigma, pi) and (r, mu) have unequal bin
+    counts on the two axes, and (r, mu) includes pairs exactly on the
+    mu = 1/2 edge."""
+    rng = np.random.default_rng(22)
+    L = 24
+    e0 = [0, 1, 2, 3, 5, 8, 13]
+    e1 = {"sigpi": [0, 1, 3, 5, 7], "rmu": [0.0, 0.25, 0.5, 0.75, 1.0]}.get(kind)
+    if kind == "rmu":
+        pi_, pj = _mu_edge_pairs()
+        assert len(pi_) > 50
+        r = np.concatenate([rng.integers(-8, 9, size=(150, 2)), rng.integers(1, 9, size=(150, 1))], 1)
+        a, b = np.concatenate([pi_, r[:75]]), np.concatenate([pj, r[75:]])
+    else:
+        lo, hi = (0, L) if periodic else (-10, 11)
+        a, b = rng.integers(lo, hi, size=(160, 3)), rng.integers(lo, hi, size=(140, 3))
+    a, b = a.astype(np.int64), b.astype(np.int64)
+    for xa, xb in ((np.concatenate([a, b]), None), (a, b)):
+        ref, oor, ties = _exact_counts(kind, xa, xb, e0, e1, L if periodic else 0)
+        assert ties >= 50
+        c, o, _ = oracle.count(kind, xa.astype(np.float64),
+                               None if xb is None else xb.astype(np.float64), edges0=e0,
+                               edges1=e1, periodic=periodic, L=float(L))
+        assert c.tolist() == ref.tolist()
+        assert o == oor
 
 
 # ------------------------------------------------------------------ invariants
