@@ -247,6 +247,45 @@ def test_pairs_on_edges_theta(ctx):
     _assert_same(gpu_count(ctx, "theta", x, None, cu), oracle_count("theta", x, None, cu))
 
 
+@pytest.mark.parametrize("uniform", [True, False])
+def test_integer_lattice_ties(ctx, uniform):
+    """Integer coordinates and integer edges: every FP64 quantity of the
+    canonical formulas is exact, so thousands of pairs sit exactly on an
+    edge in FP64 (ties the FP32 bands must flag and the double-float stage
+    must leave to the FP64 formula); (sigma, pi) and (r, mu) have unequal bin
+    counts on the two axes; the (r, mu) pairs include pairs at exactly
+    mu = 1/2: s = 2m s0, l = x_i + x_j = 2q (1, 1, 0) with s0 at 60 degrees
+    to (1, 1, 0)."""
+    rng = np.random.default_rng(109)
+    e0 = np.arange(14.0) if uniform else np.array([0.0, 1, 2, 3, 5, 8, 13])
+    es = np.arange(10.0) if uniform else np.array([0.0, 1, 2, 3, 4, 6, 9])
+    ep = np.arange(8.0) if uniform else np.array([0.0, 1, 3, 5, 7])
+    L = 40.0
+    xo = rng.integers(100, 121, size=(700, 3)).astype(np.float64)
+    xp = rng.integers(0, 40, size=(700, 3)).astype(np.float64)
+    for x, per in ((xo, False), (xp, True)):
+        kw = dict(periodic=per, L=L if per else 0.0)
+        _assert_same(gpu_count(ctx, "mono", x, None, e0, **kw), oracle_count("mono", x, None, e0, **kw))
+        assert ctx.stats()["fp64_pairs"] > 0
+        _assert_same(gpu_count(ctx, "mono", x[:300], x[300:], e0, **kw),
+                     oracle_count("mono", x[:300], x[300:], e0, **kw))
+        _assert_same(gpu_count(ctx, "sigpi", x, None, es, ep, **kw),
+                     oracle_count("sigpi", x, None, es, ep, **kw))
+        assert ctx.stats()["fp64_pairs"] > 0
+    s0 = np.array([[1, 0, 1], [1, 0, -1], [0, 1, 1], [0, 1, -1]], dtype=np.float64)
+    pts = []
+    for q in range(300, 540, 20):
+        for m in (1, 2, 3, 4):
+            for v in s0:
+                pts += [q * np.array([1.0, 1.0, 0.0]) - m * v, q * np.array([1.0, 1.0, 0.0]) + m * v]
+    xr = np.concatenate([np.array(pts),
+                         np.concatenate([rng.integers(300, 341, size=(400, 2)),
+                                         rng.integers(-10, 11, size=(400, 1))], 1)])
+    e1 = np.array([0.0, 0.25, 0.5, 0.75, 1.0])
+    _assert_same(gpu_count(ctx, "rmu", xr, None, e0, e1), oracle_count("rmu", xr, None, e0, e1))
+    assert ctx.stats()["fp64_pairs"] > 0
+
+
 def test_periodic_faces_and_duplicates(ctx):
     rng = np.random.default_rng(105)
     L = 100.0
