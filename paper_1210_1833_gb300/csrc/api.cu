@@ -1033,7 +1033,7 @@ cute_status cute_autotune(cute_ctx *ctx, int32_t n, const cute_pair_desc *d, int
             CUDA_OR_FAIL(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
           }
           // compare by time per item so shapes with different item sizes
-          // are judged on the same work: scale to the full item count
+          // are compared on the same work: scale to the full item count
           const double full = (double)ms * ((double)pr.ts->items / (double)pr.p.total);
           if (full < best.ms) best = cute_tuning{k, hp, warps, slice, (float)full};
         }
