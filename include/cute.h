@@ -47,7 +47,7 @@ typedef enum {
   CUTE_E_CUDA = -3,        /* a CUDA runtime call failed                  */
   CUTE_E_STATE = -4,       /* object missing or in the wrong state        */
   CUTE_E_TIMEOUT = -5,     /* a bounded device-side wait gave up          */
-  CUTE_E_UNSUPPORTED = -6, /* valid request the library does not implement  */
+  CUTE_E_UNSUPPORTED = -6, /* valid request the library does not implement */
   CUTE_E_DEVICE = -7       /* a kernel reported an internal inconsistency */
 } cute_status;
 
