@@ -478,11 +478,21 @@ def _row_batched(ctx, dev, timed):
         "launches": {"batched": 1, "plain": len(pairs)}, "binned_pairs": binned,
         "binned_pairs_per_s": binned / (t_b / 1e3), "graph_replay": True,
         "batched_candidate_pairs": st["candidate_pairs"], "batched_kernel_ms": st["kernel_ms"],
+        "batched_recheck": _recheck(st),
         "batched_roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
                                           "sigpi_periodic")}
     for d, r in cats:
         d.free(); r.free()
     return out
+
+
+def _recheck(st):
+    """Fractions of a count's candidate pairs that were re-tested near an
+    edge, and that the FP64 formula decided (re-tested pairs the
+    double-float stage could not settle)."""
+    c = max(1, int(st.get("candidate_pairs", 0)))
+    return {"rechecked_fraction": int(st.get("rechecked_pairs", 0)) / c,
+            "fp64_fraction": int(st.get("fp64_pairs", 0)) / c}
 
 
 def _alu_roofline(cand_rate, kind):
@@ -519,7 +529,7 @@ def _row_monopole(ctx, dev, timed):
     st = ctx.stats()
     out = {"monopole_c1_20k": {
         "step_ms": t, "kernel_ms": st["kernel_ms"], "candidate_pairs": st["candidate_pairs"],
-        "binned_pairs": int(cnt.sum()), "tuned": tuned,
+        "binned_pairs": int(cnt.sum()), "tuned": tuned, "recheck": _recheck(st),
         "roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
                                   "mono_periodic")}}
     A.free()
@@ -579,7 +589,7 @@ def _row_pixel(ctx, dev, timed):
     out = {"pixel_map_c3_nside1024": {
         "objects": len(w.data), "pixels": int(state["cen"].shape[0]), "map_ms": t_map,
         "weighted_count_ms": t_cnt, "kernel_ms": st["kernel_ms"],
-        "candidate_pairs": st["candidate_pairs"],
+        "candidate_pairs": st["candidate_pairs"], "recheck": _recheck(st),
         "roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3), "theta")}}
     P.free()
     return out
@@ -602,7 +612,7 @@ def _row_angular(ctx, dev, timed):
         c, _, _ = ctx.count("theta", a, b, chord, want_oor=False)
         st = ctx.stats()
         res[name] = {"kernel_ms": st["kernel_ms"], "candidate_pairs": st["candidate_pairs"],
-                     "binned_pairs": int(c.sum()),
+                     "binned_pairs": int(c.sum()), "recheck": _recheck(st),
                      "roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
                                                "theta")}
     for c in (D, R, S):
@@ -634,6 +644,7 @@ def _row_weighted(ctx, dev, timed):
         "binned_pairs": binned, "plain_binned_pairs_per_s": binned / (t_plain / 1e3),
         "plain_candidate_pairs": st["candidate_pairs"], "plain_kernel_ms": st["kernel_ms"],
         "plain_home_per_lane": st["home_per_lane"], "plain_tuned": tuned,
+        "plain_recheck": _recheck(st),
         "plain_candidate_pairs_per_s": st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
         "plain_roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
                                         "mono_periodic")}

@@ -95,6 +95,13 @@ def test_counters_dropped_once_the_kernel_changes(tmp_path, monkeypatch):
     assert bench.traffic_record("k") is None and bench.counted_record("k", 1e12, 40.0) is None
 
 
+def test_recheck_fractions():
+    st = {"candidate_pairs": 4000, "rechecked_pairs": 40, "fp64_pairs": 2}
+    assert bench._recheck(st) == {"rechecked_fraction": 0.01, "fp64_fraction": 0.0005}
+    assert bench._recheck({"candidate_pairs": 0, "rechecked_pairs": 0, "fp64_pairs": 0}) == {
+        "rechecked_fraction": 0.0, "fp64_fraction": 0.0}
+
+
 def test_total_pairs_closed_form():
     assert bench.total_pairs(4, 3) == 6 + 12 + 3
     assert bench.total_pairs(500000, 2000000) == (
