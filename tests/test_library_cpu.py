@@ -1,5 +1,6 @@
 """Host-side checks of libcute_gb.so that need no GPU: the library loads,
-exports every entry point include/cute.h declares, and its host-only
+exports every entry point include/cute.h declares, the Python binding's
+ctypes signatures and struct mirrors match the header, and the host-only
 functions (estimators, angle -> chord) agree with the oracle."""
 import ctypes
 import os
@@ -119,3 +120,71 @@ def test_weighted_estimators_match_oracle():
         np.testing.assert_allclose(got, ref, rtol=1e-13, equal_nan=True)
     with pytest.raises(cute.CuteError):
         cute.estimator_weighted("periodic", DD, DR, RR, *args)
+
+
+# ------------------------------------------------------------------ ABI of the binding
+_SCALARS = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double,
+            "float": ctypes.c_float, "int": ctypes.c_int, "cute_boundary": ctypes.c_int,
+            "cute_kind": ctypes.c_int, "cute_estimator_kind": ctypes.c_int}
+
+
+def _prototypes():
+    txt = open(os.path.join(ROOT, "include", "cute.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for name, args in re.findall(r"(?:cute_status|const char \*)\s*(cute_[a-z0-9_]+)\s*\(([^)]*)\)\s*;",
+                                 txt, flags=re.S):
+        a = [x.strip() for x in args.split(",")]
+        out[name] = [] if a == ["void"] else a
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every prototype of include/cute.h against the binding's ctypes
+    argtypes: same number of arguments, pointers where the header has
+    pointers, and scalars of the header's width."""
+    L = cute.lib()
+    protos = _prototypes()
+    assert set(protos) == set(cute.SYMBOLS)
+    for name, args in protos.items():
+        at = getattr(L, name).argtypes
+        if not args:
+            assert not at, name
+            continue
+        assert at is not None and len(at) == len(args), name
+        for a, t in zip(args, at):
+            if "*" in a or "[" in a:
+                assert t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer), (name, a)
+            else:
+                base = a.replace("const ", "").split()[0]
+                assert t is _SCALARS[base], (name, a, t)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C layout: a small
+    C program compiled against include/cute.h prints sizeof and the offset
+    of every field the mirror names."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("needs a C compiler")
+    pairs = [(cute.PairDesc, "cute_pair_desc"), (cute.Stats, "cute_stats"),
+             (cute.Tuning, "cute_tuning"), (cute.Cosmology, "cute_cosmology")]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cute.h"', "int main(void) {"]
+    for py, c in pairs:
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (c, c))
+        for f, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (c, f, c, f))
+    lines += ["return 0;", "}"]
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict((" ".join(ln.split()[:2]), int(ln.split()[2]))
+               for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                        check=True).stdout.splitlines())
+    for py, c in pairs:
+        assert got[c + " sizeof"] == ctypes.sizeof(py), c
+        for f, _ in py._fields_:
+            assert got["%s %s" % (c, f)] == getattr(py, f).offset, (c, f)
