@@ -46,7 +46,7 @@ typedef enum {
   CUTE_E_OOM = -2,         /* device or host allocation failed            */
   CUTE_E_CUDA = -3,        /* a CUDA runtime call failed                  */
   CUTE_E_STATE = -4,       /* object missing or in the wrong state        */
-  CUTE_E_TIMEOUT = -5,     /* a bounded device-side wait gave up          */
+  CUTE_E_TIMEOUT = -5,     /* reserved: no kernel waits on another        */
   CUTE_E_UNSUPPORTED = -6, /* valid request the library does not implement */
   CUTE_E_DEVICE = -7       /* a kernel reported an internal inconsistency */
 } cute_status;
@@ -87,8 +87,7 @@ cute_status cute_ctx_destroy(cute_ctx *ctx);
 const char *cute_last_error(const cute_ctx *ctx);
 
 /* Wait for all work enqueued on the context's stream and return the first
-   deferred error a kernel reported (CUTE_E_TIMEOUT, CUTE_E_DEVICE) or a
-   CUDA error. */
+   deferred error a kernel reported (CUTE_E_DEVICE) or a CUDA error. */
 cute_status cute_sync(cute_ctx *ctx);
 
 /* ---------------------------------------------------------------- catalogs */
@@ -152,7 +151,7 @@ typedef struct {
         of w_i * w_j per bin, accurate to 1e-9 relative or better.
    Errors: CUTE_E_INVALID, CUTE_E_STATE (catalog or grid missing or on
    different geometries, reach too small), CUTE_E_UNSUPPORTED (kind not
-   defined for the boundary), CUTE_E_CUDA, CUTE_E_TIMEOUT. */
+   defined for the boundary), CUTE_E_CUDA, CUTE_E_DEVICE. */
 cute_status cute_count_pairs(cute_ctx *ctx, const cute_pair_desc *d, uint64_t *counts,
                              uint64_t *oor, double *wsum);
 
