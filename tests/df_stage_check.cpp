@@ -272,6 +272,127 @@ static Tally run_rmu(double dist, const double *fo, double xm, double am, double
   return t;
 }
 
+// ---- integer lattices: integer coordinates and edges make every FP64
+// quantity of the canonical formulas exact, so many pairs sit exactly on an
+// edge; the stage must leave those to FP64 or decide them exactly right.
+// Every pair of the points is checked; `ties` counts the exact ties.
+static std::vector<double> lattice(std::mt19937_64 &g, int n, const double lo[3], const double hi[3]) {
+  std::vector<double> p(3 * n);
+  for (int i = 0; i < n; i++)
+    for (int c = 0; c < 3; c++) {
+      std::uniform_int_distribution<int> U((int)lo[c], (int)hi[c] - 1);
+      p[3 * i + c] = U(g);
+    }
+  return p;
+}
+
+static Tally run_lattice_mono_sigpi(const Frame &F, bool sigpi, int n0, int n1,
+                                    const std::vector<double> &x, long &ties) {
+  const std::vector<double> E0 = sq_edges(1.0, n0), E1 = sq_edges(1.0, n1);
+  const std::vector<float> E0d = split_edges(E0), E1d = split_edges(E1);
+  const float eta = (float)dfs::eta_sep(F.xm, F.L);
+  const float Lh = (float)F.L, Ll = (float)(F.L - (double)Lh);
+  const int n = (int)x.size() / 3;
+  Tally t;
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++) {
+      float pa[3], la[3], pb[3], lb[3];
+      double dd[3];
+      for (int c = 0; c < 3; c++) {
+        split(x[3 * i + c], F.fo[c], pa[c], la[c]);
+        split(x[3 * j + c], F.fo[c], pb[c], lb[c]);
+        dd[c] = wrap(x[3 * j + c] - x[3 * i + c], F.L);
+      }
+      if (!sigpi) {
+        const double d2 = (dd[0] * dd[0] + dd[1] * dd[1]) + dd[2] * dd[2];
+        const int cb = bin64(E0, d2);
+        for (int k = 1; k <= n0; k++) ties += d2 == E0[k];
+        t.add(dfs::mono_slot(pa, la, pb, lb, eta, Lh, Ll, 1.0f, E0d.data(), n0), cb < 0 ? 0 : cb + 1);
+      } else {
+        const double sg2 = dd[0] * dd[0] + dd[1] * dd[1], pi2 = dd[2] * dd[2];
+        const int bs = bin64(E0, sg2), bp = bin64(E1, pi2);
+        for (int k = 1; k <= n0; k++) ties += sg2 == E0[k];
+        for (int k = 1; k <= n1; k++) ties += pi2 == E1[k];
+        const int canon = (bs < 0 || bp < 0) ? 0 : (bs + 1) * (n1 + 2) + bp + 1;
+        t.add(dfs::sigpi_slot(pa, la, pb, lb, eta, Lh, Ll, 1.0f, E0d.data(), n0, 1.0f, E1d.data(),
+                              n1),
+              canon);
+      }
+    }
+  return t;
+}
+
+// (r, mu) on a lattice far from the observer, with pairs at exactly mu = 1/2:
+// s = 2 m s0, l = x_i + x_j = 2 q (1, 1, 0), s0 at 60 degrees to (1, 1, 0)
+static Tally run_lattice_rmu(std::mt19937_64 &g, long &ties) {
+  const int n0 = 13, n1 = 4;
+  std::vector<double> x;
+  const int s0[4][3] = {{1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
+  for (int q = 300; q < 340; q += 8)
+    for (int m = 1; m <= 4; m++)
+      for (auto &v : s0)
+        for (int sg = -1; sg <= 1; sg += 2)
+          for (int c = 0; c < 3; c++) x.push_back((c < 2 ? q : 0) + sg * m * v[c]);
+  const double lo[3] = {300, 300, -10}, hi[3] = {341, 341, 11};
+  const std::vector<double> r = lattice(g, 200, lo, hi);
+  x.insert(x.end(), r.begin(), r.end());
+  const double fo[3] = {320.25, 319.5, 0.125};
+  double xm = 0, am = 0;
+  for (size_t i = 0; i < x.size(); i += 3) {
+    double a2 = 0;
+    for (int c = 0; c < 3; c++) {
+      xm = std::max(xm, std::fabs(x[i + c] - fo[c]));
+      a2 += x[i + c] * x[i + c];
+    }
+    am = std::max(am, std::sqrt(a2));
+  }
+  const double fom = std::max(std::fabs(fo[0]), std::max(std::fabs(fo[1]), std::fabs(fo[2])));
+  const std::vector<double> E0 = sq_edges(1.0, n0);
+  std::vector<double> M(n1 + 1);
+  for (int k = 0; k <= n1; k++) M[k] = ((double)k / n1) * ((double)k / n1);
+  const std::vector<float> E0d = split_edges(E0), Md = split_edges(M);
+  const float eta = (float)dfs::eta_sep(xm, 0.0), eta_l = (float)dfs::eta_los(xm, fom, am);
+  float fo2h[3], fo2l[3];
+  for (int c = 0; c < 3; c++) {
+    fo2h[c] = (float)(2 * fo[c]);
+    fo2l[c] = (float)(2 * fo[c] - (double)fo2h[c]);
+  }
+  const int n = (int)x.size() / 3;
+  Tally t;
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++) {
+      const double *xi = &x[3 * i], *xj = &x[3 * j];
+      const double sx = xj[0] - xi[0], sy = xj[1] - xi[1], sz = xj[2] - xi[2];
+      const double lx = xi[0] + xj[0], ly = xi[1] + xj[1], lz = xi[2] + xj[2];
+      const double r2 = (sx * sx + sy * sy) + sz * sz;
+      int canon = 0;
+      const int br = bin64(E0, r2);
+      for (int k = 1; k <= n0; k++) ties += r2 == E0[k];
+      if (br >= 0) {
+        int bm = 0;
+        if (r2 != 0.0) {
+          const double l2 = (lx * lx + ly * ly) + lz * lz;
+          const double sl = (sx * lx + sy * ly) + sz * lz;
+          const double qv = sl * sl, den = r2 * l2;
+          for (int m = 1; m <= n1 - 1; m++) {
+            if (qv >= M[m] * den) bm = m;
+            ties += qv == M[m] * den;
+          }
+        }
+        canon = (br + 1) * (n1 + 2) + bm + 1;
+      }
+      float pa[3], la[3], pb[3], lb[3];
+      for (int c = 0; c < 3; c++) {
+        split(xi[c], fo[c], pa[c], la[c]);
+        split(xj[c], fo[c], pb[c], lb[c]);
+      }
+      t.add(dfs::rmu_slot(pa, la, pb, lb, eta, eta_l, fo2h, fo2l, 1.0f, E0d.data(), n0, (float)n1,
+                          Md.data(), n1),
+            canon);
+    }
+  return t;
+}
+
 int main() {
   std::mt19937_64 g(20121008);
   long bad = 0;
@@ -312,6 +433,27 @@ int main() {
     const double fo[3] = {0.0, 0.0, 0.0};
     report("rmu_centred", run_rmu(1500.0, fo, 0.3 * 1500.0 + 200.0, 0.3 * 1500.0 + 200.0, 5.0, 40,
                                   40, g));
+  }
+  {
+    // lattices: "name cases decided mismatches", then "name_ties count"
+    long ties = 0;
+    const double lo[3] = {0, 0, 0}, hi[3] = {40, 40, 40};
+    const std::vector<double> xp = lattice(g, 320, lo, hi);
+    Frame F{{20.0, 20.0, 20.0}, 20.0, 40.0};
+    report("lattice_mono_periodic", run_lattice_mono_sigpi(F, false, 13, 1, xp, ties));
+    std::printf("lattice_mono_periodic_ties %ld\n", ties);
+    ties = 0;
+    const double olo[3] = {985, -315, 62}, ohi[3] = {1016, -284, 93};
+    Frame Fo{{1000.37, -299.81, 77.5}, 16.0, 0.0};
+    report("lattice_mono_open", run_lattice_mono_sigpi(Fo, false, 13, 1, lattice(g, 320, olo, ohi),
+                                                       ties));
+    std::printf("lattice_mono_open_ties %ld\n", ties);
+    ties = 0;
+    report("lattice_sigpi_periodic", run_lattice_mono_sigpi(F, true, 9, 7, xp, ties));
+    std::printf("lattice_sigpi_periodic_ties %ld\n", ties);
+    ties = 0;
+    report("lattice_rmu", run_lattice_rmu(g, ties));
+    std::printf("lattice_rmu_ties %ld\n", ties);
   }
   return bad ? 1 : 0;
 }
