@@ -485,6 +485,159 @@ static Tally run_rmu(const double *fo, double xm, double rmin, double absmax,
   return t;
 }
 
+// ---- integer lattices: integer coordinates and edges make the canonical
+// FP64 values exact, so many pairs sit exactly on an edge; each such pair
+// must be flagged (or land in its slot all the same).  Every pair of the
+// points is checked; `ties` counts the exact ties.
+static std::vector<double> lattice_pts(std::mt19937_64 &g, int n, const double lo[3],
+                                       const double hi[3]) {
+  std::vector<double> p(3 * n);
+  for (int i = 0; i < n; i++)
+    for (int c = 0; c < 3; c++) p[3 * i + c] = std::uniform_int_distribution<int>((int)lo[c], (int)hi[c] - 1)(g);
+  return p;
+}
+
+static Tally run_lattice_mono_sigpi(bool sigpi, bool arith, bool periodic, std::mt19937_64 &g,
+                                    long &ties) {
+  const std::vector<double> e0 = sigpi ? (arith ? uniform(1.0, 9) : std::vector<double>{0, 1, 2, 3, 4, 6, 9})
+                                       : (arith ? uniform(1.0, 13) : std::vector<double>{0, 1, 2, 3, 5, 8, 13});
+  const std::vector<double> e1 = arith ? uniform(1.0, 7) : std::vector<double>{0, 1, 3, 5, 7};
+  const int n0 = (int)e0.size() - 1, n1 = sigpi ? (int)e1.size() - 1 : 1;
+  const std::vector<double> E0 = squares(e0), E1 = squares(e1);
+  const double L = periodic ? 40.0 : 0.0;
+  const double fo[3] = {periodic ? 20.0 : 1000.37, periodic ? 20.0 : -299.81, periodic ? 20.0 : 77.5};
+  const double lo[3] = {periodic ? 0.0 : 985.0, periodic ? 0.0 : -315.0, periodic ? 0.0 : 62.0};
+  const double hi[3] = {periodic ? 40.0 : 1016.0, periodic ? 40.0 : -284.0, periodic ? 40.0 : 93.0};
+  const double xm = periodic ? 20.0 : 16.0;
+  Plan P;
+  const std::string m = sigpi ? plan_build(KSIGPI, e0.data(), n0, e1.data(), n1,
+                                           eparams(xm, L, std::max(e0[n0], e1[n1]), 0, 0), 8192,
+                                           12288, true, P)
+                              : plan_build(KMONO, e0.data(), n0, nullptr, 1,
+                                           eparams(xm, L, e0[n0], 0, 0), 8192, 12288, true, P);
+  if (!plan_ok(m, P, arith)) return Tally{0, 0, 1};
+  if (arith) {
+    shrink(P.ax[0]);
+    if (sigpi) {
+      shrink(P.ax[1]);
+      P.ax[1].near_scale = (float)((double)P.ax[0].near_at / (double)P.ax[1].near_at);
+    }
+  } else {
+    shrink_table(P, 0, E0);
+    if (sigpi) shrink_table(P, 1, E1);
+  }
+  const std::vector<double> x = lattice_pts(g, 320, lo, hi);
+  const int n = (int)x.size() / 3;
+  Tally t;
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++) {
+      float q[3], nn[3];
+      kernel_inputs(&x[3 * i], &x[3 * j], fo, L, q, nn);
+      double dd[3];
+      for (int c = 0; c < 3; c++) dd[c] = wrap(x[3 * j + c] - x[3 * i + c], L);
+      int canon;
+      Slot r;
+      if (!sigpi) {
+        const double d2 = (dd[0] * dd[0] + dd[1] * dd[1]) + dd[2] * dd[2];
+        for (int k = 1; k <= n0; k++) ties += d2 == E0[k];
+        const int cb = bin64(E0, d2);
+        canon = cb < 0 ? -1 : cb + 1;
+        r = arith ? mono_fp32(P.ax[0], q, nn) : mono_table(P, q, nn);
+        const int fp32 = (r.slot >= 1 && r.slot <= n0) ? r.slot : -1;
+        t.add(arith ? r.score >= P.ax[0].near_at : r.score > 0.0f, fp32, canon);
+      } else {
+        const double sg2 = dd[0] * dd[0] + dd[1] * dd[1], pi2 = dd[2] * dd[2];
+        for (int k = 1; k <= n0; k++) ties += sg2 == E0[k];
+        for (int k = 1; k <= n1; k++) ties += pi2 == E1[k];
+        const int bs = bin64(E0, sg2), bp = bin64(E1, pi2);
+        canon = (bs < 0 || bp < 0) ? -1 : (bs + 1) * (n1 + 2) + bp + 1;
+        r = arith ? sigpi_fp32(P.ax[0], P.ax[1], P.slots1, q, nn) : sigpi_table(P, q, nn);
+        const int s0i = r.slot / P.slots1, s1i = r.slot % P.slots1;
+        const int fp32 = (s0i >= 1 && s0i <= n0 && s1i >= 1 && s1i <= n1) ? r.slot : -1;
+        t.add(arith ? r.score >= P.ax[0].near_at : r.score > 0.0f, fp32, canon);
+      }
+    }
+  return t;
+}
+
+// (r, mu) far from the observer, with pairs at exactly mu = 1/2:
+// s = 2 m s0, l = x_i + x_j = 2 q (1, 1, 0), s0 at 60 degrees to (1, 1, 0)
+static Tally run_lattice_rmu(bool arith, std::mt19937_64 &g, long &ties) {
+  const std::vector<double> e0 = arith ? uniform(1.0, 13) : std::vector<double>{0, 1, 2, 3, 5, 8, 13};
+  const int n0 = (int)e0.size() - 1, n1 = 4;
+  std::vector<double> e1(n1 + 1);
+  for (int k = 0; k <= n1; k++) e1[k] = (double)k / n1;
+  const std::vector<double> E0 = squares(e0), M = squares(e1);
+  std::vector<double> x;
+  const int s0[4][3] = {{1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
+  for (int q = 300; q < 340; q += 8)
+    for (int m = 1; m <= 4; m++)
+      for (auto &v : s0)
+        for (int sg = -1; sg <= 1; sg += 2)
+          for (int c = 0; c < 3; c++) x.push_back((c < 2 ? q : 0) + sg * m * v[c]);
+  const double lo[3] = {300, 300, -10}, hi[3] = {341, 341, 11};
+  const std::vector<double> rp = lattice_pts(g, 200, lo, hi);
+  x.insert(x.end(), rp.begin(), rp.end());
+  const double fo[3] = {320.25, 319.5, 0.125};
+  double xm = 0, absmax = 0, rmin = 1e300;
+  for (size_t i = 0; i < x.size(); i += 3) {
+    double a2 = 0;
+    for (int c = 0; c < 3; c++) {
+      xm = std::max(xm, std::fabs(x[i + c] - fo[c]));
+      absmax = std::max(absmax, std::fabs(x[i + c]));
+      a2 += x[i + c] * x[i + c];
+    }
+    rmin = std::min(rmin, std::sqrt(a2));
+  }
+  Plan P;
+  const std::string m = plan_build(KRMU, e0.data(), n0, e1.data(), n1,
+                                   eparams(xm, 0, e0[n0], absmax, rmin), 8192, 12288, true, P);
+  if (!plan_ok(m, P, arith) || (arith && P.ax[1].mode != kArith)) return Tally{0, 0, 1};
+  if (arith) {
+    shrink(P.ax[0]);
+    shrink(P.ax[1]);
+  } else {
+    shrink_table(P, 0, E0);
+    shrink_table(P, 1, M);
+  }
+  const float thr = std::fmin(P.ax[0].near_at, P.ax[1].near_c);
+  const int n = (int)x.size() / 3;
+  Tally t;
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++) {
+      const double *xi = &x[3 * i], *xj = &x[3 * j];
+      const double sx = xj[0] - xi[0], sy = xj[1] - xi[1], sz = xj[2] - xi[2];
+      const double lx = xi[0] + xj[0], ly = xi[1] + xj[1], lz = xi[2] + xj[2];
+      const double r2 = (sx * sx + sy * sy) + sz * sz;
+      for (int k = 1; k <= n0; k++) ties += r2 == E0[k];
+      int canon = -1;
+      const int br = bin64(E0, r2);
+      if (br >= 0) {
+        int bm = 0;
+        if (r2 != 0.0) {
+          const double l2 = (lx * lx + ly * ly) + lz * lz;
+          const double sl = (sx * lx + sy * ly) + sz * lz;
+          const double qv = sl * sl, den = r2 * l2;
+          for (int mi = 1; mi <= n1 - 1; mi++) {
+            if (qv >= M[mi] * den) bm = mi;
+            ties += qv == M[mi] * den;
+          }
+        }
+        canon = (br + 1) * (n1 + 2) + bm + 1;
+      }
+      float q[3], nn[3], xf[3];
+      kernel_inputs(xi, xj, fo, 0.0, q, nn);
+      for (int c = 0; c < 3; c++) xf[c] = (float)xi[c];
+      const float aq = (float)(4.0 * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]));
+      const Slot res = arith ? rmu_fp32(P.ax[0], P.ax[1], P.slots1, q, nn, xf, aq)
+                             : rmu_table(P, q, nn, xf, aq);
+      const int s0i = res.slot / P.slots1, s1i = res.slot % P.slots1;
+      const int fp32 = (s0i >= 1 && s0i <= n0 && s1i >= 1 && s1i <= n1) ? res.slot : -1;
+      t.add(arith ? res.score >= thr : res.score > 0.0f, fp32, canon);
+    }
+  return t;
+}
+
 int main(int argc, char **argv) {
   if (argc > 1) g_f = std::atof(argv[1]);
   std::mt19937_64 g(20121008);
@@ -526,6 +679,26 @@ int main(int argc, char **argv) {
     report(nm, run_sigpi(logspace(0.5, 60.0, 15), uniform(2.0, 30), 1500.0, false, g));
     std::snprintf(nm, sizeof nm, "table_rmu_lightcone_r%d", g_mode);
     report(nm, run_rmu(fo, 1250.0, 1000.0, 2500.0, r_log, 10, rs_l, false, g));
+  }
+  // integer lattices ("name cases flagged violations", then "name_ties count")
+  for (g_mode = 0; g_mode < 3; g_mode++) {
+    struct L { const char *name; int kind; bool arith, periodic; };
+    const L ls[] = {{"lattice_mono_arith_periodic", 0, true, true},
+                    {"lattice_mono_arith_open", 0, true, false},
+                    {"lattice_mono_table_periodic", 0, false, true},
+                    {"lattice_mono_table_open", 0, false, false},
+                    {"lattice_sigpi_arith_periodic", 1, true, true},
+                    {"lattice_sigpi_table_periodic", 1, false, true},
+                    {"lattice_rmu_arith", 2, true, false},
+                    {"lattice_rmu_table", 2, false, false}};
+    for (const L &l : ls) {
+      long ties = 0;
+      char nm[80];
+      std::snprintf(nm, sizeof nm, "%s_r%d", l.name, g_mode);
+      report(nm, l.kind == 2 ? run_lattice_rmu(l.arith, g, ties)
+                             : run_lattice_mono_sigpi(l.kind == 1, l.arith, l.periodic, g, ties));
+      std::printf("%s_ties %ld\n", nm, ties);
+    }
   }
   if (g_lut_oob) {
     std::printf("table index outside the table\n");

@@ -4,9 +4,10 @@ operation order, IEEE roundings, the hardware reciprocal square root anywhere
 within its documented error) with the thresholds, tables and bands of the
 host planner, on pairs on and around every edge of the monopole, chord,
 (sigma, pi) and (r, mu) binnings -- uniform edges from 0 (binning by
-arithmetic) and log-spaced edges (the lookup-table path); no pair the kernel
-would not re-test may fall in another slot than the canonical FP64 formulas
-give (Sec. 2.2, Sec. 3.4).  The check also runs with the thresholds' (and
+arithmetic) and log-spaced edges (the lookup-table path) -- and on every
+pair of integer lattices, where hundreds of pairs sit exactly on an edge in
+FP64 (mu = 1/2 included); no pair the kernel would not re-test may fall in
+another slot than the canonical FP64 formulas give (Sec. 2.2, Sec. 3.4).  The check also runs with the thresholds' (and
 bands') distance from the edge halved and at 0.3, so the planner's bounds
 keep a margin over what these pairs need; with the bands collapsed it must
 find misbinned pairs, so the replay does detect a too-narrow band."""
@@ -48,28 +49,39 @@ def exe(tmp_path_factory):
 
 def _run(exe, factor):
     r = subprocess.run([exe, str(factor)], capture_output=True, text=True)
-    rows = {}
+    rows, ties = {}, {}
     for line in r.stdout.splitlines():
         p = line.split()
         if len(p) == 4 and p[1].isdigit():
             rows[p[0]] = tuple(int(x) for x in p[1:])
-    return r.returncode, rows, r.stdout
+        elif len(p) == 2 and p[0].endswith("_ties"):
+            ties[p[0][:-5]] = int(p[1])
+    return r.returncode, rows, r.stdout, ties
 
 
 @pytest.mark.parametrize("factor", [1.0, 0.5, 0.3])
 def test_no_unflagged_pair_is_misbinned(exe, factor):
-    rc, rows, out = _run(exe, factor)
-    # 11 scenarios (6 arithmetic, 5 table) x 3 ways of rounding the rsqrt
-    assert len(rows) == 33, out
+    rc, rows, out, ties = _run(exe, factor)
+    # 11 edge scenarios (6 arithmetic, 5 table) and 8 integer lattices, each
+    # with 3 ways of rounding the rsqrt
+    assert len(rows) == 57, out
     assert sum(n.startswith("table_") for n in rows) == 15, out
+    lattices = [n for n in rows if n.startswith("lattice_")]
+    assert len(lattices) == 24 and set(ties) == set(lattices), out
     for name, (cases, flagged, bad) in rows.items():
         assert cases > 1000 and bad == 0, (name, out)
+    # the lattices hold exact FP64 ties, every one of them flagged or binned right
+    assert all(ties[n] >= 100 for n in lattices), out
     assert rc == 0, out
 
 
 def test_collapsed_bands_are_caught(exe):
-    # thresholds at the edge itself: every scenario must show misbinned pairs
-    rc, rows, out = _run(exe, 0.0)
-    assert len(rows) == 33 and rc == 1, out
+    # thresholds at the edge itself: every edge scenario must show misbinned
+    # pairs (a lattice whose FP32 values are exact can keep its ties flagged
+    # even then, so the lattices are counted together)
+    rc, rows, out, _ = _run(exe, 0.0)
+    assert len(rows) == 57 and rc == 1, out
     for name, (cases, flagged, bad) in rows.items():
-        assert bad > 0, (name, out)
+        if not name.startswith("lattice_"):
+            assert bad > 0, (name, out)
+    assert sum(v[2] for n, v in rows.items() if n.startswith("lattice_")) > 0, out
