@@ -422,18 +422,17 @@ def run_extras(ctx, dev, reps=3, which="all"):
         return e0.elapsed_time(e1) / n
 
     out = {}
-    if which in ("all", "batched"):
-        out.update(_row_batched(ctx, dev, timed))
-    if which in ("all", "weighted"):
-        out.update(_row_weighted(ctx, dev, timed))
-    if which in ("all", "monopole"):
-        out.update(_row_monopole(ctx, dev, timed))
-    if which in ("all", "density"):
-        out.update(_row_density(ctx, dev, timed))
-    if which in ("all", "pixel"):
-        out.update(_row_pixel(ctx, dev, timed))
-    if which in ("angular",):  # minutes of work: only on request
-        out.update(_row_angular(ctx, dev, timed))
+    rows = [("batched", _row_batched), ("weighted", _row_weighted), ("monopole", _row_monopole),
+            ("density", _row_density), ("pixel", _row_pixel)]
+    if which == "angular":  # minutes of work: only on request
+        rows = [("angular", _row_angular)]
+    for name, fn in rows:
+        if which not in ("all", name):
+            continue
+        try:
+            out.update(fn(ctx, dev, timed))
+        except Exception as e:  # a failed row is reported, the headline line still prints
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
     return out
 
 

@@ -102,6 +102,29 @@ def test_recheck_fractions():
         "rechecked_fraction": 0.0, "fp64_fraction": 0.0}
 
 
+def test_a_failing_row_does_not_lose_the_others(monkeypatch):
+    class _Torch:
+        class cuda:
+            @staticmethod
+            def current_stream(dev):
+                return None
+    monkeypatch.setitem(sys.modules, "torch", _Torch)
+
+    def row(name):
+        return lambda ctx, dev, timed: {name: {"ok": True}}
+
+    def boom(ctx, dev, timed):
+        raise RuntimeError("no device")
+    for n in ("batched", "monopole", "density", "pixel", "angular"):
+        monkeypatch.setattr(bench, "_row_" + n, row(n))
+    monkeypatch.setattr(bench, "_row_weighted", boom)
+    out = bench.run_extras(None, 0)
+    assert set(out) == {"batched", "weighted", "monopole", "density", "pixel"}
+    assert out["weighted"] == {"error": "RuntimeError: no device"}
+    assert bench.run_extras(None, 0, which="angular") == {"angular": {"ok": True}}
+    assert bench.run_extras(None, 0, which="pixel") == {"pixel": {"ok": True}}
+
+
 def test_total_pairs_closed_form():
     assert bench.total_pairs(4, 3) == 6 + 12 + 3
     assert bench.total_pairs(500000, 2000000) == (
