@@ -151,7 +151,10 @@ typedef struct {
         of w_i * w_j per bin, accurate to 1e-9 relative or better.
    Errors: CUTE_E_INVALID, CUTE_E_STATE (catalog or grid missing or on
    different geometries, reach too small), CUTE_E_UNSUPPORTED (kind not
-   defined for the boundary), CUTE_E_CUDA, CUTE_E_DEVICE. */
+   defined for the boundary; bins the error analysis cannot serve, e.g. a
+   CUTE_R_MU count whose objects come closer to the observer than half the
+   largest r edge, where the line of sight x_i + x_j can vanish), CUTE_E_CUDA,
+   CUTE_E_DEVICE. */
 cute_status cute_count_pairs(cute_ctx *ctx, const cute_pair_desc *d, uint64_t *counts,
                              uint64_t *oor, double *wsum);
 
