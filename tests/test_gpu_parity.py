@@ -338,6 +338,23 @@ def test_invalid_requests_fail_cleanly(ctx):
     ctx.sync()
 
 
+def test_rmu_near_the_observer_is_refused(ctx):
+    """(r, mu) needs every object farther from the observer than half the
+    largest r edge (else the line of sight x_i + x_j of a pair within reach
+    can vanish): such a count is refused before any launch, and the same
+    objects moved away from the observer count exactly."""
+    rng = np.random.default_rng(111)
+    x = rng.uniform(-60.0, 60.0, size=(300, 3))
+    e0, e1 = np.linspace(0, 200, 41), np.linspace(0, 1, 41)
+    a = ctx.upload(x)
+    ctx.grid([a], [e0[-1]] * 3)
+    with pytest.raises(cute.CuteError):
+        ctx.count("rmu", a, None, e0, e1)
+    a.free()
+    far = x + np.array([900.0, 400.0, 300.0])
+    _assert_same(gpu_count(ctx, "rmu", far, None, e0, e1), oracle_count("rmu", far, None, e0, e1))
+
+
 def test_rmu_duplicates_and_log_bins(ctx):
     """(r, mu) on an open catalog with exact duplicates (separation 0: r bin
     0, mu bin 0) and on log-spaced r edges (table binning for r)."""
