@@ -20,11 +20,9 @@ bounded sample of the same workload on the host cores.
 """
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np

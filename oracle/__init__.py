@@ -11,7 +11,6 @@ Every function cites the passage of Alonso (2012) it follows; see oracle.c
 for the canonical formulas and the readings taken where the paper is silent.
 """
 import ctypes
-import os
 
 import numpy as np
 

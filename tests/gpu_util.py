@@ -5,7 +5,6 @@ import math
 import numpy as np
 
 import oracle
-from paper_1210_1833_gb300 import cute
 
 
 def reach_of(kind, e0, e1):
