@@ -182,10 +182,9 @@ cute_status cute_count_pairs_adjoint(cute_ctx *ctx, const cute_pair_desc *d, con
 /* Counts like cute_count_pairs, but allocates no device memory: for callers
    that cannot let a library call cudaMalloc when they count -- a framework
    whose caching allocator owns the device memory (a stray cudaMalloc
-   fragments its pool or fails once the pool has taken the device), code
-   running while a CUDA stream is captured, or loops where cudaMalloc and
-   cudaFree would synchronise the device.  The paper has no counterpart; it
-   is a deployment form of the counting kernel.
+   fragments its pool or fails once the pool has taken the device), or loops
+   where cudaMalloc and cudaFree would synchronise the device.  The paper has
+   no counterpart; it is a deployment form of the counting kernel.
    The catalogs and grids must already exist (upload and grid build allocate
    and are done beforehand).  counts (n0 * n1 uint64) and, if d->weighted,
    wsum (n0 * n1 doubles) must be device memory of the context's device;
@@ -195,8 +194,11 @@ cute_status cute_count_pairs_adjoint(cute_ctx *ctx, const cute_pair_desc *d, con
    a request whose scratch exceeds 8 MiB is rejected with CUTE_E_INVALID and
    a message naming the size (count smaller catalogs, or use
    cute_count_pairs).  The first call on a device looks up the array's
-   device address (cudaGetSymbolAddress) with that device current; make it
-   before any stream capture.  Every call shares the array and leaves its
+   device address (cudaGetSymbolAddress) with that device current.  Each
+   call builds its work-item records on the host (its host time grows with
+   the number of items) and copies them, with the binning tables, from
+   pageable host memory: that copy waits for the context's stream.  Every
+   call shares the array and leaves its
    contents behind (the counters are cleared at the start of each call):
    calls that overlap on the GPU -- on different streams or contexts -- race
    on it.  Asynchronous on the context's stream; cute_sync reports kernel

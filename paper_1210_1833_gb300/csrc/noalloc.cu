@@ -4,13 +4,15 @@
 // lists, work counters) in buffers it allocates and caches.  Some callers
 // cannot let a library allocate at the moment they count: a framework whose
 // caching allocator owns all device memory (a stray cudaMalloc fragments its
-// pool or fails once the pool has taken the device), code running while a
-// CUDA stream is being captured (allocation calls are not permitted then),
-// or latency-critical loops where cudaMalloc/cudaFree may synchronise the
-// whole device.  cute_count_pairs_noalloc serves them: the same counting
-// kernel, with its scratch in one fixed file-scope device array that every
-// call on a device shares.  The caller passes the outputs (device memory);
-// the catalogs and their grids are set up beforehand.
+// pool or fails once the pool has taken the device), or loops where
+// cudaMalloc/cudaFree would synchronise the whole device.
+// cute_count_pairs_noalloc serves them: the same counting kernel, with its
+// scratch in one fixed file-scope device array that every call on a device
+// shares.  The caller passes the outputs (device memory of the context's
+// device); the catalogs and their grids are set up beforehand.  Each call
+// builds its work-item records on the host (time grows with the number of
+// items) and copies them, with the tables, from pageable host memory, a copy
+// that waits for the context's stream.
 #include "cute_internal.h"
 #include "count_kernel.cuh"
 
@@ -52,13 +54,15 @@ static cute_status na_fail(cute_ctx *ctx, cute_status st, const std::string &m) 
       return na_fail(ctx, CUTE_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-static bool na_is_device(const void *p) {
+// device memory of `device` (or managed memory, which every device reaches)
+static bool na_is_device(const void *p, int device) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 static size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -69,7 +73,8 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   ctx->err.clear();
   NA_CUDA(cudaSetDevice(ctx->device));
   if (!d || !counts) return na_fail(ctx, CUTE_E_INVALID, "descriptor and counts are required");
-  if (!na_is_device(counts) || (d->weighted && (!wsum || !na_is_device(wsum))))
+  if (!na_is_device(counts, ctx->device) ||
+      (d->weighted && (!wsum || !na_is_device(wsum, ctx->device))))
     return na_fail(ctx, CUTE_E_INVALID, "outputs must be device memory of the context's device");
   if (ctx->device < 0 || ctx->device >= 256) return na_fail(ctx, CUTE_E_INVALID, "device index");
 

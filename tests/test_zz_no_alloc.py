@@ -1,6 +1,7 @@
 """cute_count_pairs_noalloc: the counting entry point for callers that cannot
 let the library allocate device memory when they count (a framework's
-caching allocator owning the device, stream capture, latency-critical loops).
+caching allocator owning the device, loops where cudaMalloc/cudaFree would
+synchronise the device).
 
 Through the C ABI, on two calls in a row, its counts must equal those of
 cute_count_pairs exactly (integer counts) and its weighted sums within the
@@ -93,4 +94,44 @@ def test_noalloc_rejects_host_outputs(ctx):
     st = cute.lib().cute_count_pairs_noalloc(ctx.handle, ctypes.byref(d),
                                              host.ctypes.data_as(ctypes.c_void_p), None)
     assert st == -1
+    a.free()
+
+
+def test_noalloc_sigpi_periodic_matches_count_pairs(ctx):
+    # the disk-slab stencil and the second edge table of the scratch layout
+    b = synthetic.c4_batched_sigpi(scale=0.02)[0]
+    e0, e1 = b.edges0, b.edges1
+    d = ctx.upload(b.data, periodic=True, L=b.L)
+    r = ctx.upload(b.randoms, periodic=True, L=b.L)
+    ctx.grid([d, r], [e0[-1], e0[-1], e1[-1]])
+    for bb in (None, r):
+        ref, _, _ = ctx.count("sigpi", d, bb, e0, e1)
+        assert int(ref.sum()) > 0
+        for _ in range(2):
+            got, _ = _noalloc(ctx, "sigpi", d, bb, e0, e1)
+            assert got.tolist() == ref.tolist()
+    d.free()
+    r.free()
+
+
+def test_noalloc_rejects_requests_beyond_its_scratch(ctx):
+    # a count whose work-item records alone exceed the fixed 8 MiB array is
+    # refused before anything is launched, with the size in the message
+    x = synthetic.uniform_box(1_000_000, 1000.0, np.random.default_rng(62))
+    a = ctx.upload(x, periodic=True, L=1000.0)
+    ctx.grid([a], [100.0] * 3, 4)
+    e = np.linspace(0.0, 100.0, 11)
+    d = ctx._desc("mono", a, None, np.ascontiguousarray(e), None, False)
+    counts = torch.zeros(10, dtype=torch.int64, device="cuda")
+    ctx.set_launch(slice=64)
+    try:
+        st = cute.lib().cute_count_pairs_noalloc(ctx.handle, ctypes.byref(d),
+                                                 ctypes.c_void_p(counts.data_ptr()), None)
+        msg = cute.lib().cute_last_error(ctx.handle).decode()
+    finally:
+        ctx.set_launch()
+    assert st == -1
+    assert "bytes of scratch" in msg
+    ctx.sync()
+    assert int(counts.sum()) == 0
     a.free()
