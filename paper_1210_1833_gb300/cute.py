@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -490,6 +491,28 @@ def version() -> str:
     return lib().cute_version().decode()
 
 
+class _HeldCatalogs:
+    """Catalogs a forward pass keeps for its backward.  They are freed when
+    the backward has used them, or, if no backward ever runs, when the
+    autograd graph that holds this object is released (weakref finaliser),
+    so an undifferentiated forward leaves nothing on the device."""
+
+    def __init__(self, *cats):
+        self.cats = [c for c in cats if c is not None]
+        self._fin = weakref.finalize(self, _HeldCatalogs._free, self.cats)
+
+    @staticmethod
+    def _free(cats):
+        for c in cats:
+            try:
+                c.free()
+            except Exception:  # the context may already be closed
+                pass
+
+    def release(self):
+        self._fin()
+
+
 def _make_weighted_count():
     import torch
 
@@ -521,6 +544,7 @@ def _make_weighted_count():
             ctx.count(kind, A, B, e0, e1, weighted=True, out=cnt, wsum_out=W, want_oor=False)
             if fctx.needs_input_grad[0] or fctx.needs_input_grad[1]:
                 fctx.cute = (ctx, kind, A, B, e0, e1, wa.dtype, None if wb is None else wb.dtype)
+                fctx.held = _HeldCatalogs(A, B)
             else:
                 A.free()
                 if B is not None:
@@ -535,9 +559,7 @@ def _make_weighted_count():
                 ga, gb = ctx.adjoint(kind, A, None, e0, e1, G=G), None
             else:
                 ga, gb = ctx.adjoint(kind, A, B, e0, e1, G=G, grad_b=True)
-            A.free()
-            if B is not None:
-                B.free()
+            fctx.held.release()
             fctx.cute = None
             return (ga.to(da), None if gb is None else gb.to(db)) + (None,) * 10
 

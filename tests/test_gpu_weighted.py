@@ -195,3 +195,28 @@ def test_autograd_weighted_count(ctx, cross):
                                   periodic=True, L=L)
         gotb = wb.grad.detach().cpu().numpy().astype(np.float64)
         assert np.all(np.abs(gotb - refb) <= 1e-6 * scaleb + 1e-30)
+
+
+def test_autograd_forward_without_backward_frees_catalogs(ctx):
+    """A forward whose output needs a gradient but is never differentiated
+    keeps its catalogs only while the autograd graph lives: dropping the
+    output frees them (catalog handles are issued in order, so the forward's
+    two catalogs are the two after a probe catalog)."""
+    import ctypes
+    import gc
+    x, w = _case(500, seed=36)
+    y, wy = _case(400, seed=37)
+    L = 400.0
+    e = np.arange(31) * 5.0
+    probe = ctx.upload(x[:10])
+    first = probe.id
+    probe.free()
+    wa = torch.tensor(w, device="cuda", requires_grad=True)
+    wb = torch.tensor(wy, device="cuda", requires_grad=True)
+    W = cute.CuteWeightedCount.apply(wa, wb, ctx, "mono", x, y, e, None, True, L, [e[-1]] * 3, 0)
+    n = ctypes.c_int64()
+    held = [first + 1, first + 2]
+    assert all(cute.lib().cute_catalog_size(ctx.handle, i, ctypes.byref(n)) == 0 for i in held)
+    del W
+    gc.collect()
+    assert all(cute.lib().cute_catalog_size(ctx.handle, i, ctypes.byref(n)) == -4 for i in held)
