@@ -4,7 +4,8 @@ segments that the library hands to the kernel (chunks_build, stencil_build,
 entry_segments, with cell grids that follow the grid contract) into object
 pairs, for the half stencil of auto counts, the full stencil of the adjoint
 and cross counts, periodic and open, ball, disk-slab and box reaches, two
-home-chunk sizes and grids that need the threaded chunk builder.  Every
+home-chunk sizes, 1 to 8 cells per reach, and grids that need the threaded
+chunk builder.  Every
 pair within reach must be met exactly once and through the image that puts
 it within reach; pairs beyond reach met twice (periodic half stencils) are
 out of range both times and only reported."""
@@ -40,8 +41,11 @@ def test_every_pair_within_reach_met_exactly_once(exe):
         p = line.split()
         if len(p) == 5 and p[1].isdigit():
             rows[p[0]] = tuple(int(x) for x in p[1:])
-    # 7 geometries x 2 chunk sizes x 3 pair-set modes
-    assert len(rows) == 42, r.stdout
+    # 7 geometries x 2 chunk sizes x 3 pair-set modes at 1-3 cells per
+    # reach, and 5 geometries x 2 x 3 at each of 4-8 cells per reach
+    assert len(rows) == 42 + 5 * 6 * 5, r.stdout
+    for k in range(4, 9):
+        assert sum(name.endswith("_k%d" % k) for name in rows) == 30
     for name, (enumerated, inreach, dup, bad) in rows.items():
         assert bad == 0, (name, r.stdout)
         assert inreach > 300 and enumerated >= inreach, name

@@ -242,5 +242,22 @@ int main() {
                  modes[m], 1500, 900, 2.0, rng);
     }
   }
+  // finer grids: 4 to 8 cells per reach (the range cute_grid_build accepts
+  // above the defaults, and where warm-up tuning may take a count)
+  for (int k = 4; k <= 8; k++)
+    for (int m = 0; m < 3; m++)
+      for (int hc : {64, 128}) {
+        std::string t = std::string(mn[m]) + "_hc" + std::to_string(hc) + "_k" + std::to_string(k);
+        bad += run(("periodic_ball_" + t).c_str(), true, 100, z0, box100, r12, kShapeBall, k, hc,
+                   modes[m], 1800, 1100, 1.5, rng);
+        bad += run(("periodic_diskslab_" + t).c_str(), true, 100, z0, box100, sp, kShapeDiskSlab,
+                   k, hc, modes[m], 1500, 900, 2.0, rng);
+        bad += run(("open_ball_" + t).c_str(), false, 0, olo, ohi, r12, kShapeBall, k, hc,
+                   modes[m], 1800, 1100, 1.5, rng);
+        bad += run(("open_box_" + t).c_str(), false, 0, olo, ohi, r12, kShapeBox, k, hc,
+                   modes[m], 1500, 900, 1.5, rng);
+        bad += run(("open_diskslab_" + t).c_str(), false, 0, olo, ohi, sp, kShapeDiskSlab, k, hc,
+                   modes[m], 1500, 900, 2.0, rng);
+      }
   return bad ? 1 : 0;
 }
