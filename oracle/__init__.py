@@ -233,64 +233,95 @@ def sky_to_xyz(ra_deg, dec_deg, z=None, omega_m=0.3, omega_l=0.7, w0=-1.0):
     return n * comoving_distance(z, omega_m, omega_l, w0)[:, None]
 
 
-def healpix_ang2pix_ring(nside, xyz):
-    """Pixel index (HEALPix RING scheme, Gorski et al. 2005) of unit vectors,
-    the pixelisation taken for the pixel maps of Sec. 3.4.2: equatorial belt
-    |z| <= 2/3 located by the two families of pixel edge lines, polar caps by
-    the same lines in sqrt(3 (1 - |z|)) scaled coordinates."""
-    xyz = np.asarray(xyz, dtype=np.float64)
-    ns = int(nside)
+# HEALPix (Gorski et al. 2005) through its planar projection (Calabretta &
+# Roukema 2007): with X = phi / (pi/4) and, in the equatorial belt
+# |z| <= 2/3, Y = 3 z / 2, or in the polar caps Y = +-(2 - sigma),
+# sigma = sqrt(3 (1 - |z|)), X pulled towards the centre X_f of its
+# quadrant by the factor sigma, the sphere maps onto 12 squares (diamonds)
+# and every pixel boundary onto one of the lines X + Y = 1 + 2k/nside,
+# X - Y = 1 + 2k/nside.  A point's pixel is then its cell (a, b) of that
+# lattice; the cell's centre sits at X_c = 1 + (a + b + 1)/nside,
+# Y_c = (a - b)/nside, on ring i = 2 nside - (a - b) (ring latitudes
+# Y_i = 2 - i/nside), and the RING index counts the rings above it and the
+# centres of its own ring with phi in [0, 2 pi) below its own (Gorski et al.
+# 2005: polar ring i holds 4i centres at phi = (j + 1/2) pi/(2i); belt rings
+# 4 nside centres, spaced pi/(2 nside), starting at phi = pi/(4 nside) when
+# i - nside is even and at phi = 0 when it is odd).
+def _hp_project(xyz):
+    """(X, Y) of unit vectors in the HEALPix projection, and the quadrant q
+    (0..3) of each point's phi."""
     x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
-    phi = np.arctan2(y, x)
-    phi = np.where(phi < 0, phi + 2 * np.pi, phi)
-    tt = np.mod(phi / (0.5 * np.pi), 4.0)
+    phi = np.mod(np.arctan2(y, x), 2 * np.pi)
+    X = phi / (np.pi / 4)
+    X = np.where(X >= 8.0, 0.0, X)
+    q = np.minimum(np.floor(X / 2).astype(np.int64), 3)
     za = np.abs(z)
-    npix, ncap = 12 * ns * ns, 2 * ns * (ns - 1)
-    out = np.empty(len(z), dtype=np.int64)
-    eq = za <= 2.0 / 3.0
-    # equatorial belt
-    t1, t2 = ns * (0.5 + tt[eq]), ns * z[eq] * 0.75
-    jp, jm = np.floor(t1 - t2).astype(np.int64), np.floor(t1 + t2).astype(np.int64)
-    ir = ns + 1 + jp - jm
-    kshift = 1 - (ir & 1)
-    ip = np.mod((jp + jm - ns + kshift + 1) // 2, 4 * ns)
-    out[eq] = ncap + (ir - 1) * 4 * ns + ip
-    # polar caps
-    pc = ~eq
-    tp = tt[pc] - np.floor(tt[pc])
-    tmp = ns * np.sqrt(3.0 * (1.0 - za[pc]))
-    jp, jm = np.floor(tp * tmp).astype(np.int64), np.floor((1.0 - tp) * tmp).astype(np.int64)
-    ir = jp + jm + 1
-    ip = np.mod(np.floor(tt[pc] * ir).astype(np.int64), 4 * ir)
-    out[pc] = np.where(z[pc] > 0, 2 * ir * (ir - 1) + ip, npix - 2 * ir * (ir + 1) + ip)
+    polar = za > 2.0 / 3.0
+    sigma = np.sqrt(3.0 * (1.0 - np.where(polar, za, 1.0)))
+    Xf = 2.0 * q + 1.0
+    Xp = np.where(polar, Xf + (X - Xf) * sigma, X)
+    Yp = np.where(polar, np.sign(z) * (2.0 - sigma), 1.5 * z)
+    return Xp, Yp, q
+
+
+def healpix_ang2pix_ring(nside, xyz):
+    """Pixel index (HEALPix RING scheme) of unit vectors, the pixelisation
+    taken for the pixel maps of Sec. 3.4.2: the lattice cell of the point in
+    the HEALPix projection, then its ring and its rank on the ring."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    N = int(nside)
+    X, Y, q = _hp_project(xyz)
+    a = np.floor((X + Y - 1.0) * N / 2.0).astype(np.int64)
+    b = np.floor((X - Y - 1.0) * N / 2.0).astype(np.int64)
+    i = 2 * N - (a - b)                      # ring of the cell's centre, 1 .. 4N-1
+    out = np.empty(len(X), dtype=np.int64)
+    north, south = i < N, i > 3 * N
+    belt = ~(north | south)
+    # polar rings: the centre's offset from its quadrant's face centre,
+    # u = X_c - X_f = (a + b + 1 - 2 q N)/N, ranks it among the quadrant's
+    # i centres (spaced 2/N around X_f)
+    for sel, ring, before in ((north, i, lambda r: 2 * r * (r - 1)),
+                              (south, 4 * N - i, lambda r: 12 * N * N - 2 * r * (r + 1))):
+        r, qs = ring[sel], q[sel]
+        m = qs * r + (r + a[sel] + b[sel] - 2 * qs * N) // 2
+        out[sel] = before(r) + m
+    # belt rings: centres spaced 2/N in X; rank = floor(X_c N / 2) with
+    # X_c N / 2 = (N + a + b + 1) / 2 taken modulo 4N (phi in [0, 2 pi))
+    ib = i[belt]
+    rank = np.mod((N + a[belt] + b[belt] + 1) // 2, 4 * N)
+    out[belt] = 2 * N * (N - 1) + 4 * N * (ib - N) + rank
     return out
 
 
 def healpix_pix2vec_ring(nside, pix):
-    """Centres of HEALPix RING pixels as unit vectors: ring i of the north
-    cap holds pixels 2i(i-1) .. 2i(i+1)-1 at z = 1 - i^2/(3 nside^2); the
-    belt rings hold 4 nside pixels at z = (2 nside - i) 2/(3 nside), every
-    other ring shifted by half a pixel; the south cap mirrors the north."""
-    ns = int(nside)
+    """Centres of HEALPix RING pixels as unit vectors: the ring found among
+    the rings' first indices, the centre placed in the HEALPix projection
+    (Y_i = 2 - i/nside; X spaced 2/nside), then mapped back to the sphere."""
+    N = int(nside)
     p = np.asarray(pix, dtype=np.int64)
-    npix, ncap = 12 * ns * ns, 2 * ns * (ns - 1)
+    rings = np.arange(1, 4 * N)
+    size = 4 * np.minimum(np.minimum(rings, 4 * N - rings), N)
+    first = np.concatenate([[0], np.cumsum(size)[:-1]])
+    k = np.searchsorted(first, p, side="right") - 1
+    i, m = rings[k], p - first[k]
+    Yc = 2.0 - i / N
+    Xc = np.empty(len(p))
+    polar = (i < N) | (i > 3 * N)
+    r = np.where(i < N, i, 4 * N - i)[polar]
+    q = m[polar] // r
+    Xc[polar] = 2.0 * q + 1.0 + (2.0 * (m[polar] - q * r) - r + 1.0) / N
+    # belt: first centre at X = 1/N when i - N is even, at X = 0 when odd
+    ib = i[~polar]
+    half = 1.0 - np.mod(ib - N, 2)
+    Xc[~polar] = (2.0 * m[~polar] + half) / N
     z = np.empty(len(p))
     phi = np.empty(len(p))
-    n = p < ncap
-    i = (1 + np.floor(np.sqrt(1 + 2 * p[n] + 0.5)).astype(np.int64)) // 2
-    j = p[n] + 1 - 2 * i * (i - 1)
-    z[n], phi[n] = 1.0 - i * i / (3.0 * ns * ns), (j - 0.5) * np.pi / (2.0 * i)
-    e = (p >= ncap) & (p < npix - ncap)
-    q = p[e] - ncap
-    i = q // (4 * ns) + ns
-    j = q % (4 * ns) + 1
-    shift = np.where((i + ns) & 1, 1.0, 0.5)
-    z[e], phi[e] = (2 * ns - i) * 2.0 / (3.0 * ns), (j - shift) * np.pi / (2.0 * ns)
-    s = p >= npix - ncap
-    q = npix - p[s]
-    i = (1 + np.floor(np.sqrt(2 * q - 1 + 0.5)).astype(np.int64)) // 2
-    j = 4 * i + 1 - (q - 2 * i * (i - 1))
-    z[s], phi[s] = -1.0 + i * i / (3.0 * ns * ns), (j - 0.5) * np.pi / (2.0 * i)
+    z[~polar] = Yc[~polar] / 1.5
+    phi[~polar] = Xc[~polar] * (np.pi / 4)
+    sig = 2.0 - np.abs(Yc[polar])
+    z[polar] = np.sign(Yc[polar]) * (1.0 - sig * sig / 3.0)
+    Xf = 2.0 * q + 1.0
+    phi[polar] = (Xf + (Xc[polar] - Xf) / sig) * (np.pi / 4)
     st = np.sqrt((1.0 - z) * (1.0 + z))
     return np.stack([st * np.cos(phi), st * np.sin(phi), z], axis=1)
 

@@ -44,7 +44,9 @@ def test_pixel_centres_match_oracle_and_round_trip(ctx, nside):
     pix = np.unique(np.random.default_rng(102).integers(0, npix, 50_000))
     pix = np.concatenate([[0, npix - 1], pix]) if npix > 2 else np.arange(npix)
     c = ctx.pixel_centres(nside, pix)
-    np.testing.assert_allclose(c, oracle.healpix_pix2vec_ring(nside, pix), rtol=0, atol=1e-15)
+    # the oracle places centres through the HEALPix projection, the library
+    # by the ring formulas: the two roundings differ by a few ulp
+    np.testing.assert_allclose(c, oracle.healpix_pix2vec_ring(nside, pix), rtol=0, atol=4e-15)
     m = ctx.pixel_map(c, None, nside)  # every centre falls in its own pixel
     assert np.array_equal(np.nonzero(m)[0], np.unique(pix))
     with pytest.raises(cute.CuteError):

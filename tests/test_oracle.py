@@ -510,6 +510,36 @@ def test_healpix_equal_area_and_locality():
     assert ang.max() < 1.5 * np.sqrt(4 * np.pi / 192)
 
 
+@pytest.mark.parametrize("nside", [1, 3, 8, 64])
+def test_healpix_points_inside_their_pixel(nside):
+    """Random points against the pixel geometry stated on the sphere (Gorski
+    et al. 2005): in the belt |z| <= 2/3 every pixel is a diamond in (phi, z)
+    with vertices pi/(4 nside) either side of its centre in phi and
+    2/(3 nside) above and below it in z, so each point must satisfy
+    |dphi| / (pi/(4 nside)) + |dz| / (2/(3 nside)) <= 1 about its pixel's
+    centre; everywhere, a pixel's north and south vertices lie on the
+    neighbouring rings, so the point's z lies between the latitudes of the
+    rings above and below its pixel's ring."""
+    rng = np.random.default_rng(85)
+    v = rng.normal(size=(400_000, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    p = oracle.healpix_ang2pix_ring(nside, v)
+    c = oracle.healpix_pix2vec_ring(nside, p)
+    belt = np.abs(v[:, 2]) <= 2.0 / 3.0
+    dphi = np.angle(np.exp(1j * (np.arctan2(v[:, 1], v[:, 0]) - np.arctan2(c[:, 1], c[:, 0]))))
+    dz = v[:, 2] - c[:, 2]
+    lhs = np.abs(dphi) / (np.pi / (4 * nside)) + np.abs(dz) / (2.0 / (3 * nside))
+    assert np.all(lhs[belt] <= 1.0 + 1e-9)
+    # ring latitudes z_i, i = 0 .. 4 nside (the poles at i = 0 and 4 nside)
+    i = np.arange(4 * nside + 1)
+    zr = np.where(i < nside, 1.0 - i * i / (3.0 * nside * nside),
+                  np.where(i > 3 * nside, -1.0 + (4 * nside - i) ** 2 / (3.0 * nside * nside),
+                           (2 * nside - i) * 2.0 / (3.0 * nside)))
+    ring = np.argmin(np.abs(zr[None, :] - c[:, 2:3]), axis=1)  # the centre's ring
+    assert np.all(zr[ring] == pytest.approx(c[:, 2], abs=1e-12))
+    assert np.all(v[:, 2] <= zr[ring - 1] + 1e-12) and np.all(v[:, 2] >= zr[ring + 1] - 1e-12)
+
+
 def test_weighted_estimators_reduce_to_unweighted():
     """Unit weights turn the weighted estimators into Eq. 14 / Eq. 15 on
     unique-pair counts."""

@@ -90,10 +90,14 @@ MUTANTS = {
     "dark_energy_sign": (PY, "a ** (3.0 * (1.0 + w0))", "a ** (3.0 * (1.0 - w0))", 1),
     "sky_y_uses_cos": (PY, "np.cos(dec) * np.sin(ra), np.sin(dec)", "np.cos(dec) * np.cos(ra), np.sin(dec)", 1),
     # pixel maps
-    "healpix_belt_slope": (PY, "ns * z[eq] * 0.75", "ns * z[eq] * 0.5", 1),
-    "healpix_cap_offset": (PY, "2 * ir * (ir - 1) + ip, npix", "2 * ir * (ir + 1) + ip, npix", 1),
-    "healpix_ring_z": (PY, "z[n], phi[n] = 1.0 - i * i / (3.0 * ns * ns)",
-                       "z[n], phi[n] = 1.0 - i * i / (2.0 * ns * ns)", 1),
+    "healpix_belt_slope": (PY, "np.sign(z) * (2.0 - sigma), 1.5 * z)",
+                           "np.sign(z) * (2.0 - sigma), 1.0 * z)", 1),
+    "healpix_cap_offset": (PY, "lambda r: 2 * r * (r - 1)", "lambda r: 2 * r * (r + 1)", 1),
+    "healpix_cap_sigma": (PY, "sigma = np.sqrt(3.0 * (1.0 - np.where(polar, za, 1.0)))",
+                          "sigma = np.sqrt(2.0 * (1.0 - np.where(polar, za, 1.0)))", 1),
+    "healpix_belt_shift": (PY, "half = 1.0 - np.mod(ib - N, 2)", "half = np.mod(ib - N, 2)", 1),
+    "healpix_ring_z": (PY, "z[polar] = np.sign(Yc[polar]) * (1.0 - sig * sig / 3.0)",
+                       "z[polar] = np.sign(Yc[polar]) * (1.0 - sig * sig / 2.0)", 1),
     "weighted_dd_norm": (PY, "dd = DD / (0.5 * (s_d * s_d - q_d))", "dd = DD / (s_d * s_d - q_d)", 1),
     "weighted_ls_dr": (PY, "out = (dd - 2.0 * dr + rr) / rr", "out = (dd - dr + rr) / rr", 1),
     # density grid (Sec. 3.4.4)
