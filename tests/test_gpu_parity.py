@@ -136,6 +136,40 @@ def test_trimmed_stencils_2d(ctx, cpr):
                                    L=b.L, cells=True))
 
 
+@pytest.mark.parametrize("cpr", [5, 6, 7, 8])
+@pytest.mark.parametrize("hp", [2, 4])
+def test_fine_cells_all_kinds(ctx, cpr, hp):
+    """5 to 8 cells per reach (warm-up tuning may pick 5 for the light cone;
+    cute_grid_build accepts up to 8): (r, mu) DD, DR and RR, periodic
+    (sigma, pi) auto and cross, theta auto and cross and the periodic
+    monopole, at 2 and 4 home objects per lane with a narrow neighbour
+    slice (many items per entry), against the oracle bit for bit."""
+    table = ctx.table_binning if hasattr(ctx, "table_binning") else False
+    ctx.set_launch(home_per_lane=hp, slice=256, table_binning=table)
+    try:
+        w = synthetic.c2_rmu_lightcone(scale=0.004)
+        for a, b in ((w.data, None), (w.data, w.randoms), (w.randoms, None)):
+            got = gpu_count(ctx, "rmu", a, b, w.edges0, w.edges1, cells_per_reach=cpr)
+            _assert_same(got, oracle_count("rmu", a, b, w.edges0, w.edges1, cells=True))
+        bx = synthetic.c4_batched_sigpi(n_boxes=1, scale=0.03)[0]
+        for b in (None, bx.randoms):
+            got = gpu_count(ctx, "sigpi", bx.data, b, bx.edges0, bx.edges1, periodic=True, L=bx.L,
+                            cells_per_reach=cpr)
+            _assert_same(got, oracle_count("sigpi", bx.data, b, bx.edges0, bx.edges1,
+                                           periodic=True, L=bx.L, cells=True))
+        a = synthetic.c3_angular(scale=0.0005)
+        chord = oracle.theta_to_chord(a.extra["theta_deg"])
+        for b in (None, a.randoms):
+            got = gpu_count(ctx, "theta", a.data, b, chord, cells_per_reach=cpr)
+            _assert_same(got, oracle_count("theta", a.data, b, chord, cells=True))
+        m = synthetic.c1_monopole_box(scale=0.2)
+        got = gpu_count(ctx, "mono", m.data, e0=m.edges0, periodic=True, L=m.L,
+                        cells_per_reach=cpr)
+        _assert_same(got, oracle_count("mono", m.data, e0=m.edges0, periodic=True, L=m.L))
+    finally:
+        ctx.set_launch(table_binning=table)
+
+
 @pytest.mark.parametrize("hp", [2, 4])
 def test_home_per_lane_all_kinds(ctx, hp):
     """Each home-objects-per-lane width is its own kernel instantiation:
