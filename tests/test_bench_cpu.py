@@ -119,7 +119,7 @@ def test_a_failing_row_does_not_lose_the_others(monkeypatch):
         monkeypatch.setattr(bench, "_row_" + n, row(n))
     monkeypatch.setattr(bench, "_row_weighted", boom)
     out = bench.run_extras(None, 0)
-    assert set(out) == {"batched", "weighted", "monopole", "density", "pixel"}
+    assert set(out) == {"batched", "weighted", "monopole", "density", "pixel", "angular"}
     assert out["weighted"] == {"error": "RuntimeError: no device"}
     assert bench.run_extras(None, 0, which="angular") == {"angular": {"ok": True}}
     assert bench.run_extras(None, 0, which="pixel") == {"pixel": {"ok": True}}
