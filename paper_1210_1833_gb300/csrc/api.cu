@@ -401,9 +401,29 @@ PairDF pair_df(const DescInfo &di) {
   return f;
 }
 
+PairDev pair_dev(const DescInfo &di, int out) {
+  PairDev pd;
+  std::memset(&pd, 0, sizeof(pd));
+  pd.posA = di.A->d_pos;
+  pd.posB = di.B->d_pos;
+  pd.qA = di.A->d_posq;
+  pd.qB = di.B->d_posq;
+  pd.q0 = di.g->q0;
+  pd.sA = di.A->d_s64;
+  pd.sB = di.B->d_s64;
+  pd.permA = di.A->d_perm;
+  pd.nA = (int32_t)di.A->n;
+  pd.nB = (int32_t)di.B->n;
+  pd.out = (int32_t)out;
+  pd.is_auto = di.is_auto;
+  pd.L32 = (float)di.g->L;
+  pd.L64 = di.g->periodic ? di.g->L : 0.0;
+  return pd;
+}
+
 ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax) {
-  ErrorParams ep{0, 0, 0};
-  double absmax = 0, rmin = 1e300;
+  ErrorParams ep{0, 0, 0, 0};
+  double rmin = 1e300;
   for (const DescInfo &di : dis) {
     const Geometry &g = *di.g;
     double xm = std::max(g.xmax[0], std::max(g.xmax[1], g.xmax[2]));
@@ -418,10 +438,10 @@ ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax) {
       e = kU32 * 2.0 * xm * 1.01 + 1e-12 * xm;
     }
     ep.eta0 = std::max(ep.eta0, e);
-    absmax = std::max(absmax, std::max(g.absmax[0], std::max(g.absmax[1], g.absmax[2])));
     rmin = std::min(rmin, g.rmin);
+    ep.qd = std::max(ep.qd, g.qd);
+    ep.q0 = std::max(ep.q0, g.q0);
   }
-  ep.eta_l = kU32 * (4.0 * absmax + rmax) * 1.01 + ep.eta0 + kU32 * rmax;
   ep.lmin = 2.0 * rmin - rmax;
   return ep;
 }
@@ -447,7 +467,8 @@ cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &
   std::ostringstream key;
   key.precision(17);
   const size_t hb = hist_budget(d, acc, hp);
-  key << d->kind << "|" << ep.eta0 << "|" << ep.eta_l << "|" << ep.lmin << "|" << hp << "|"
+  key << d->kind << "|" << ep.eta0 << "|" << ep.lmin << "|" << ep.qd << "|"
+      << ep.q0 << "|" << hp << "|"
       << ctx->table_binning << "|" << hb << "|";
   for (int k = 0; k <= d->n0; k++) key << d->edges0[k] << ",";
   if (d->kind == CUTE_R_MU || d->kind == CUTE_SIGMA_PI)
@@ -524,19 +545,7 @@ cute_status get_work(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, in
   size_t oc = 0, os = 0;
   for (size_t i = 0; i < dis.size(); i++) {
     const DescInfo &di = dis[i];
-    PairDev pd;
-    std::memset(&pd, 0, sizeof(pd));
-    pd.posA = di.A->d_pos;
-    pd.posB = di.B->d_pos;
-    pd.sA = di.A->d_s64;
-    pd.sB = di.B->d_s64;
-    pd.permA = di.A->d_perm;
-    pd.nA = (int32_t)di.A->n;
-    pd.nB = (int32_t)di.B->n;
-    pd.out = (int32_t)i;
-    pd.is_auto = di.is_auto;
-    pd.L32 = (float)di.g->L;
-    pd.L64 = di.g->periodic ? di.g->L : 0.0;
+    PairDev pd = pair_dev(di, (int)i);
     pd.df = T->d_pdf + i;
     T->pdf.push_back(pair_df(di));
     PairWork pw;
@@ -668,7 +677,8 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
   st = get_work(ctx, pr.dis, pr.hp, slice, full_stencil, pr.ts);
   if (st != CUTE_OK) return st;
   const Plan &P = *pr.plan;
-  SmemLayout L = smem_layout((int)P.lut.size(), (int)P.band.size() / 2, P.nslots, P.R, pr.hp, acc);
+  SmemLayout L = smem_layout((int)P.lut.size(), (int)P.band.size() / 2, P.nslots, P.R, pr.hp, acc,
+                             d[0].kind == CUTE_R_MU && acc != 0);
   pr.acc = acc;
   size_t avail = ctx->smem_optin;
   const int wmax = count_max_warps(d[0].kind == CUTE_MONO || d[0].kind == CUTE_THETA, pr.hp, acc);

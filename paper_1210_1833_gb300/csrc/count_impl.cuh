@@ -23,8 +23,8 @@ struct Home {
   static_assert(HP % 2 == 0, "home slots come in pairs (packed FP32 math)");
   // slots 2k and 2k+1 share a float2 (packed math); scalar access by slot
   float2 nx2[HP / 2], ny2[HP / 2], nz2[HP / 2];  // -(home position - image shift), grid frame
-  float2 ax2[HP / 2], ay2[HP / 2], az2[HP / 2];  // R_MU: x_i in the observer frame
-  float2 aq2[HP / 2];                            // R_MU: 4 |x_i|^2
+  float2 nq2[HP / 2];                            // R_MU: -q_i, q_i = |x_i|^2 - q0
+  float2 c2[HP / 2];                             // R_MU: k (2 q_i + 4 q0)
   float w[HP];                 // weight (0 when padded)
   float gh[HP], gl[HP];        // adjoint: float-float gradient accumulator
   int id[HP];                  // sorted index in A (INT_MAX when padded)
@@ -51,6 +51,7 @@ struct WarpSmem {
   int2 *queue;
   int qcap;
   float4 *tiles;
+  float *wtiles;               // R_MU weighted / adjoint: the tiles' weights
 };
 
 // ------------------------------------------------------------------ float-float
@@ -182,21 +183,22 @@ __device__ __forceinline__ uint32_t table_slot(const KParams &p, uint32_t lut, u
 }
 
 // (r, mu) values of two pairs in packed FP32: s = x_j - x_i, r^2 = s.s
-// (floored at 1e-30, so 1/r and mu stay finite),
-// s.l = 2 s.x_i + r^2 and l.l = 4 |x_i|^2 + 4 s.x_i + r^2 with l = x_i + x_j
-// (x_i in the observer frame), mu = |s.l| / sqrt(r^2 l.l).
+// (floored at 1e-30, so 1/r and mu stay finite); with l = x_i + x_j and the
+// per-object q = |x|^2 - q0 (observer frame), s.l = |x_j|^2 - |x_i|^2 =
+// q_j - q_i and l.l = 2|x_i|^2 + 2|x_j|^2 - r^2, formed scaled by k:
+// k l.l = k (2 q_j) + (k (2 q_i + 4 q0) - k r^2).  Then
+// |s.l| / sqrt(r^2 k l.l) = mu / sqrt(k).
 struct Rmu2 {
-  float2 r2, sl, l2;
+  float2 r2, sl, l2;  // r^2, s.l, k l.l
 };
-__device__ __forceinline__ Rmu2 rmu_values2(float2 qx, float2 qy, float2 qz, float2 nx, float2 ny,
-                                            float2 nz, float2 ax, float2 ay, float2 az,
-                                            float2 aq) {
+__device__ __forceinline__ Rmu2 rmu_values2(float2 qx, float2 qy, float2 qz, float2 qq, float2 nx,
+                                            float2 ny, float2 nz, float2 nqi, float2 ci,
+                                            float2 k2, float2 nk) {
   const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
   Rmu2 v;
   v.r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, make_float2(kVFloor, kVFloor))));
-  const float2 sx = __ffma2_rn(dz, az, __ffma2_rn(dy, ay, __fmul2_rn(dx, ax)));
-  v.sl = __ffma2_rn(sx, make_float2(2.0f, 2.0f), v.r2);
-  v.l2 = __ffma2_rn(sx, make_float2(4.0f, 4.0f), __fadd2_rn(aq, v.r2));
+  v.sl = __fadd2_rn(qq, nqi);
+  v.l2 = __ffma2_rn(qq, k2, __ffma2_rn(v.r2, nk, ci));
   return v;
 }
 
@@ -230,21 +232,25 @@ __device__ __forceinline__ float2 clampt(float2 t, float hi) {
   return make_float2(fminf(t.x, hi), fminf(t.y, hi));
 }
 __device__ __forceinline__ void rmu_arith2(const AxisPlan &a0, const AxisPlan &a1, float2 qx,
-                                           float2 qy, float2 qz, float2 nx, float2 ny, float2 nz,
-                                           float2 ax, float2 ay, float2 az, float2 aq,
+                                           float2 qy, float2 qz, float2 qq, float2 nx, float2 ny,
+                                           float2 nz, float2 nqi, float2 ci, float2 k2, float2 nk,
                                            float sl1, uint32_t stride1, uint32_t c,
                                            uint32_t &o0, uint32_t &o1, float2 &sc) {
-  const Rmu2 v = rmu_values2(qx, qy, qz, nx, ny, nz, ax, ay, az, aq);
+  const Rmu2 v = rmu_values2(qx, qy, qz, qq, nx, ny, nz, nqi, ci, k2, nk);
   const float2 r2 = v.r2, sl = v.sl, l2 = v.l2;
   const float2 rr = make_float2(rsqrt_hw(r2.x), rsqrt_hw(r2.y));
-  const float2 pl = __fmul2_rn(r2, l2);  // > 0 (or +inf for padded slots): mu finite
-  const float2 mu = __fmul2_rn(make_float2(fabsf(sl.x), fabsf(sl.y)),
-                               make_float2(rsqrt_hw(pl.x), rsqrt_hw(pl.y)));
-  // t >= -1/2 on both axes (e_0 = 0); clamped above only (mu too: a
-  // candidate beyond the reach may have l near 0, and a NaN clamps to thi)
+  // k l.l is positive for every pair within reach; a candidate beyond it
+  // (or a padded slot, whose k l.l is negative) may give a NaN, which the
+  // clamp below turns into the top slot
+  const float2 pl = __fmul2_rn(r2, l2);
+  // t >= -1/2 on both axes (e_0 = 0); clamped above only.  Axis 1: the
+  // scale k = 1/inv^2 makes |s.l| rsqrt(r^2 k l.l) = mu inv (cst + mu inv in
+  // one FMA)
   const float2 t0 = clampt(__ffma2_rn(__fmul2_rn(r2, rr), make_float2(a0.inv, a0.inv),
                                       make_float2(a0.cst, a0.cst)), a0.thi);
-  const float2 t1 = clampt(__ffma2_rn(mu, make_float2(a1.inv, a1.inv), make_float2(a1.cst, a1.cst)),
+  const float2 t1 = clampt(__ffma2_rn(make_float2(fabsf(sl.x), fabsf(sl.y)),
+                                      make_float2(rsqrt_hw(pl.x), rsqrt_hw(pl.y)),
+                                      make_float2(a1.cst, a1.cst)),
                            a1.thi);
   const float2 m2 = make_float2(kMagic, kMagic), nm2 = make_float2(-kMagic, -kMagic),
                neg = make_float2(-1.0f, -1.0f);
@@ -335,11 +341,13 @@ __device__ __forceinline__ float near_thr(const KParams &p) {
 // per-pair selects.  Table binning routes near pairs to slot 0 at once.
 // MASK: 1 -- only j > i counts (the home run against itself, unique pairs);
 //       2 -- every j != i counts (full-stencil adjoint of an auto count).
+// R_MU tiles hold (x, y, z, q); their weights (weighted, adjoint) come
+// from a tile of their own, wtile.
 template <int KIND, int HP, int M0, int M1, int MASK, int ACC>
 __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint32_t band,
                                            const PairDev &pd, const WarpSmem &w, uint32_t tile,
-                                           int cnt, int gj0, Home<HP> &h, int lane,
-                                           unsigned &near_count) {
+                                           uint32_t wtile, int cnt, int gj0, Home<HP> &h,
+                                           int lane, unsigned &near_count) {
   constexpr int U = 8 / HP;  // neighbours per step: 8 pairs per lane per step
   constexpr int NP = U * HP;
   constexpr bool kLazy = M0 == kArith;
@@ -356,6 +364,9 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
   // magic + rint(t0) * slots1 + rint(t1)
   const float sl1 = (float)p.slots1;
   const uint32_t c2d = ((uint32_t)p.slots1 + 1u - kMagicBits) * st1 + zoff;
+  // R_MU: k l.l = 2k q_j + (C_i - k r^2)
+  const float lk = p.ax[1].lsc;
+  const float2 k2 = make_float2(2.0f * lk, 2.0f * lk), nk = make_float2(-lk, -lk);
   for (int j = 0; j < cnt; j += U) {
     uint32_t off[NP];
     float sc[NP];  // arithmetic binning: near scores
@@ -364,7 +375,8 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const float4 q = lds_f4(tile + 16u * (j + u));
-      wj[u] = q.w;
+      if (KIND == KRMU && ACC != kAccCount) wj[u] = __uint_as_float(lds_u32(wtile + 4u * (j + u)));
+      else wj[u] = q.w;
       if constexpr ((KIND == KMONO || KIND == KTHETA) && M0 == kArith) {
         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
                      qz = make_float2(q.z, q.z);
@@ -394,8 +406,8 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
         for (int sp = 0; sp < HP / 2; sp++) {
           uint32_t o[2];
           float2 s2;
-          rmu_arith2(p.ax[0], p.ax[1], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], h.ax2[sp],
-                     h.ay2[sp], h.az2[sp], h.aq2[sp], sl1, st1, c2d, o[0], o[1], s2);
+          rmu_arith2(p.ax[0], p.ax[1], qx, qy, qz, make_float2(q.w, q.w), h.nx2[sp], h.ny2[sp],
+                     h.nz2[sp], h.nq2[sp], h.c2[sp], k2, nk, sl1, st1, c2d, o[0], o[1], s2);
           arith_pair_out<HP, MASK, kLazy>(s2, o, u, sp, gj0 + j + u, h, zoff, thr, off, sc, nmask);
         }
       } else {
@@ -407,8 +419,8 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
         for (int sp = 0; sp < HP / 2; sp++) {
           float2 va, vb;
           if constexpr (KIND == KRMU) {
-            const Rmu2 v = rmu_values2(qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], h.ax2[sp],
-                                       h.ay2[sp], h.az2[sp], h.aq2[sp]);
+            const Rmu2 v = rmu_values2(qx, qy, qz, make_float2(q.w, q.w), h.nx2[sp], h.ny2[sp],
+                                       h.nz2[sp], h.nq2[sp], h.c2[sp], k2, nk);
             const float2 pl = __fmul2_rn(v.r2, v.l2);
             va = v.r2;
             vb = __fmul2_rn(make_float2(fabsf(v.sl.x), fabsf(v.sl.y)),
@@ -528,36 +540,36 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
 template <int KIND, int HP, int M0, int M1, int ACC>
 __device__ __forceinline__ void tile_dispatch_mask(const KParams &p, uint32_t lut,
                                                    uint32_t band, const PairDev &pd,
-                                                   const WarpSmem &w, uint32_t tile, int cnt,
+                                                   const WarpSmem &w, uint32_t tile, uint32_t wtile, int cnt,
                                                    int gj0, Home<HP> &h, int lane, int mask,
                                                    unsigned &dc) {
-  if (mask == 1) tile_pairs<KIND, HP, M0, M1, 1, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, dc);
+  if (mask == 1) tile_pairs<KIND, HP, M0, M1, 1, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, dc);
   else if (ACC == kAccAdjoint && mask == 2)
-    tile_pairs<KIND, HP, M0, M1, 2, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, dc);
-  else tile_pairs<KIND, HP, M0, M1, 0, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, dc);
+    tile_pairs<KIND, HP, M0, M1, 2, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, dc);
+  else tile_pairs<KIND, HP, M0, M1, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, dc);
 }
 
 template <int KIND, int HP, int ACC>
 __device__ __forceinline__ void tile_dispatch(const KParams &p, uint32_t lut,
                                               uint32_t band, const PairDev &pd,
-                                              const WarpSmem &w, uint32_t tile, int cnt,
+                                              const WarpSmem &w, uint32_t tile, uint32_t wtile, int cnt,
                                               int gj0, Home<HP> &h, int lane, int mask,
                                               unsigned &dc) {
   const int m0 = p.ax[0].mode;
   if (KIND == KMONO || KIND == KTHETA) {
-    if (m0 == kArith) tile_dispatch_mask<KIND, HP, kArith, 0, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
-    else if (m0 == kLutLinear) tile_dispatch_mask<KIND, HP, kLutLinear, 0, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
-    else tile_dispatch_mask<KIND, HP, kLutLog, 0, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
+    if (m0 == kArith) tile_dispatch_mask<KIND, HP, kArith, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
+    else if (m0 == kLutLinear) tile_dispatch_mask<KIND, HP, kLutLinear, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
+    else tile_dispatch_mask<KIND, HP, kLutLog, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
   } else {
     const int m1 = p.ax[1].mode;
     if (m0 == kArith) {
-      tile_dispatch_mask<KIND, HP, kArith, kArith, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
+      tile_dispatch_mask<KIND, HP, kArith, kArith, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
     } else if (m0 == kLutLinear) {
-      if (m1 == kLutLinear) tile_dispatch_mask<KIND, HP, kLutLinear, kLutLinear, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
-      else tile_dispatch_mask<KIND, HP, kLutLinear, kLutLog, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
+      if (m1 == kLutLinear) tile_dispatch_mask<KIND, HP, kLutLinear, kLutLinear, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
+      else tile_dispatch_mask<KIND, HP, kLutLinear, kLutLog, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
     } else {
-      if (m1 == kLutLinear) tile_dispatch_mask<KIND, HP, kLutLog, kLutLinear, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
-      else tile_dispatch_mask<KIND, HP, kLutLog, kLutLog, ACC>(p, lut, band, pd, w, tile, cnt, gj0, h, lane, mask, dc);
+      if (m1 == kLutLinear) tile_dispatch_mask<KIND, HP, kLutLog, kLutLinear, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
+      else tile_dispatch_mask<KIND, HP, kLutLog, kLutLog, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
     }
   }
 }
@@ -571,7 +583,8 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
     k_count(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const SmemLayout L = smem_layout(p.lut_words, p.band_words, p.nslots, p.R, HP, ACC);
+  constexpr bool kWTile = KIND == KRMU && ACC != kAccCount;
+  const SmemLayout L = smem_layout(p.lut_words, p.band_words, p.nslots, p.R, HP, ACC, kWTile);
   uint32_t *lut = (uint32_t *)smem;
   for (int i = threadIdx.x; i < p.lut_words; i += blockDim.x) lut[i] = p.lut[i];
   float2 *band = (float2 *)(smem + align16(p.lut_words * 4));
@@ -599,6 +612,7 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
   w.queue = (int2 *)(wb + L.hist_bytes + 16);
   w.qcap = L.queue_cap;
   w.tiles = (float4 *)(wb + L.hist_bytes + L.queue_bytes);
+  w.wtiles = (float *)(wb + L.hist_bytes + L.queue_bytes + L.tile_bytes);
   w.s_hist_lane = smem_addr(w.hist_lane);
   w.s_wcol = smem_addr(w.wcol);
   w.s_G = smem_addr(w.G);
@@ -657,12 +671,20 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
     // the first tile is in flight while the home objects load
     const int nj = je - js;
     const int ntiles = (nj + kTile - 1) / kTile;
+    // R_MU tiles come from (x, y, z, q), and their weights from (x, y, z, w)
+    const float4 *srcB = KIND == KRMU ? pd.qB : pd.posB;
     auto load_tile = [&](int tt) {
       float4 *dst = w.tiles + (tt & 1) * kTile;
+      float *wdst = w.wtiles + (tt & 1) * kTile;
       for (int e = lane; e < kTile; e += 32) {
         const int g = js + tt * kTile + e;
-        if (g < je) cp_async16(dst + e, pd.posB + g);
-        else dst[e] = make_float4(kNbrFar, kNbrFar, kNbrFar, 0.0f);
+        if (g < je) {
+          cp_async16(dst + e, srcB + g);
+          if (kWTile) cp_async4(wdst + e, &pd.posB[g].w);
+        } else {
+          dst[e] = make_float4(kNbrFar, kNbrFar, kNbrFar, 0.0f);
+          if (kWTile) wdst[e] = 0.0f;
+        }
       }
       cp_async_commit();
     };
@@ -678,22 +700,20 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
       h.gh[s] = 0.0f;
       h.gl[s] = 0.0f;
       if (idx < he) {
-        const float4 a = pd.posA[idx];
+        const float4 a = KIND == KRMU ? pd.qA[idx] : pd.posA[idx];
         Home<HP>::put(h.nx2, s, -__fsub_rn(a.x, Sx));
         Home<HP>::put(h.ny2, s, -__fsub_rn(a.y, Sy));
         Home<HP>::put(h.nz2, s, -__fsub_rn(a.z, Sz));
-        h.w[s] = a.w;
+        h.w[s] = KIND == KRMU ? (ACC == kAccWeighted ? pd.posA[idx].w : 1.0f) : a.w;
         h.id[s] = idx;
         // candidate pairs: j in [js, je), with j > i (self) or j != i
         cand += mask == 1 ? (unsigned)max(0, je - max(js, idx + 1))
                           : (unsigned)(nj - (mask == 2 && idx >= js && idx < je ? 1 : 0));
         if (KIND == KRMU) {
-          const double X = pd.sA[idx], Y = pd.sA[(size_t)pd.nA + idx],
-                       Z = pd.sA[2 * (size_t)pd.nA + idx];
-          Home<HP>::put(h.ax2, s, (float)X);
-          Home<HP>::put(h.ay2, s, (float)Y);
-          Home<HP>::put(h.az2, s, (float)Z);
-          Home<HP>::put(h.aq2, s, (float)(4.0 * (X * X + Y * Y + Z * Z)));
+          // C_i = k (2 q_i + 4 q0), rounded once from FP64
+          Home<HP>::put(h.nq2, s, -a.w);
+          Home<HP>::put(h.c2, s, (float)((double)p.ax[1].lsc *
+                                         __dadd_rn(__dmul_rn(2.0, (double)a.w), __dmul_rn(4.0, pd.q0))));
         }
       } else {
         Home<HP>::put(h.nx2, s, -kHomeFar);
@@ -701,11 +721,9 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
         Home<HP>::put(h.nz2, s, -kHomeFar);
         h.w[s] = 0.0f;
         h.id[s] = 0x7fffffff;
-        if (KIND == KRMU) {  // x_i = 0 in the observer frame: l = s, mu = 1
-          Home<HP>::put(h.ax2, s, 0.0f);
-          Home<HP>::put(h.ay2, s, 0.0f);
-          Home<HP>::put(h.az2, s, 0.0f);
-          Home<HP>::put(h.aq2, s, 0.0f);
+        if (KIND == KRMU) {  // k l.l < 0: mu is NaN and clamps to the top slot
+          Home<HP>::put(h.nq2, s, 0.0f);
+          Home<HP>::put(h.c2, s, 0.0f);
         }
       }
     }
@@ -722,7 +740,8 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
       int cnt = min(kTile, nj - tt * kTile);
       cnt = (cnt + (8 / HP) - 1) & ~((8 / HP) - 1);  // whole steps; padded rows are sentinels
       tile_dispatch<KIND, HP, ACC>(p, s_lut, s_band, pd, w, smem_addr(w.tiles + (tt & 1) * kTile),
-                                   cnt, js + tt * kTile, h, lane, mask, near_count);
+                                   smem_addr(w.wtiles + (tt & 1) * kTile), cnt, js + tt * kTile,
+                                   h, lane, mask, near_count);
       __syncwarp();
     }
     if (ACC == kAccWeighted) flush_wsum(p, w, pd.out, lane);

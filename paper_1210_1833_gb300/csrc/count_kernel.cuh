@@ -131,13 +131,14 @@ struct SmemLayout {
   int queue_cap;      // per warp entries
   int queue_bytes;
   int tile_bytes;     // per warp (2 tiles)
+  int wtile_bytes;    // per warp (2 weight tiles: R_MU weighted / adjoint)
   int warp_bytes;     // per warp total
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
 __host__ __device__ inline SmemLayout smem_layout(int lut_words, int band_words, int nslots, int R,
-                                                  int HP, int acc) {
+                                                  int HP, int acc, bool wtile) {
   SmemLayout s;
   // block-wide: lookup tables, bands, and (adjoint) G per slot
   s.lut_bytes = align16(lut_words * 4) + align16(band_words * 8) + (acc == 2 ? align16(nslots * 8) : 0);
@@ -146,7 +147,8 @@ __host__ __device__ inline SmemLayout smem_layout(int lut_words, int band_words,
   s.queue_cap = 32 + 32 * 8;  // checked after every step of 8 pairs per lane
   s.queue_bytes = 16 + align16(s.queue_cap * 8);  // 16-byte header holds the count
   s.tile_bytes = 2 * kTile * 16;
-  s.warp_bytes = s.hist_bytes + s.queue_bytes + s.tile_bytes;
+  s.wtile_bytes = wtile ? 2 * kTile * 4 : 0;
+  s.warp_bytes = s.hist_bytes + s.queue_bytes + s.tile_bytes + s.wtile_bytes;
   return s;
 }
 
@@ -156,6 +158,10 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");

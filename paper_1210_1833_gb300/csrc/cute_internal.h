@@ -56,6 +56,10 @@ struct AxisPlan {
   float near_c = 0;
   // (sigma, pi), axis 1: near_at(axis 0) / near_at(axis 1) rounded up
   float near_scale = 1;
+  // (r, mu), axis 1: scale k of the squared line-of-sight length the kernel
+  // forms (k = 1/inv^2 rounded, so |s.l| / sqrt(r^2 k l^2) is mu * inv;
+  // 1 for tables)
+  float lsc = 1;
 };
 
 // Kinds as the kernels see them.
@@ -100,6 +104,10 @@ struct PairDF {
 
 struct PairDev {
   const float4 *posA, *posB;   // cell-sorted FP32 (x, y, z, w), grid frame
+  // R_MU: cell-sorted FP32 (x, y, z, q), q = |x|^2 - q0 in the observer frame
+  // (rounded once from FP64); null for periodic grids
+  const float4 *qA, *qB;
+  double q0;                   // R_MU: reference of q (the geometry's)
   const double *sA, *sB;       // cell-sorted FP64 SoA (x[n], y[n], z[n])
   const PairDF *df;            // double-float view (re-test first stage)
   const int32_t *permA;        // cell-sorted index -> upload index of A
@@ -171,6 +179,10 @@ struct Geometry {
   double fo[3] = {0, 0, 0};   // centre of the FP32 frame
   double absmax[3] = {0, 0, 0}; // largest |x| (observer frame) per axis
   double rmin = 0;            // smallest |x| over its catalogs (observer frame)
+  double rmax = 0;            // largest |x| over its catalogs (observer frame)
+  // R_MU: reference q0 of the squared distances q = |x|^2 - q0 (the middle
+  // of [rmin^2, rmax^2]) and a bound qd >= |q| over its catalogs
+  double q0 = 0, qd = 0;
   long long version = 0;
 };
 
@@ -182,11 +194,12 @@ struct Catalog {
   double *d_xyz = nullptr;     // upload order, row-major n x 3
   float *d_w = nullptr;        // upload order weights, or null
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, absmax[3] = {0, 0, 0};
-  double rmin = 0;
+  double rmin = 0, rmax = 0;   // smallest and largest |x| (observer frame)
   // grid
   int geom = -1;
   long long grid_version = 0;
   float4 *d_pos = nullptr;     // sorted FP32
+  float4 *d_posq = nullptr;    // sorted FP32 (x, y, z, |x|^2 - q0), open grids only
   float4 *d_lo = nullptr;      // sorted FP32 remainders of the frame offsets
   double *d_s64 = nullptr;     // sorted FP64 SoA
   int32_t *d_perm = nullptr;   // sorted -> upload index
@@ -302,8 +315,9 @@ struct Plan {
 
 struct ErrorParams {
   double eta0;      // per-component absolute FP32 error bound, without the |delta| term
-  double eta_l;     // R_MU: absolute error bound of the line-of-sight vector
   double lmin;      // R_MU: lower bound of |l| for pairs within reach
+  double qd;        // R_MU: bound on |q| = ||x|^2 - q0| over the catalogs
+  double q0;        // R_MU: largest reference q0 of the pair sets
 };
 
 // Build the binning plan.  hist_budget_bytes: per-warp histogram budget.
@@ -330,6 +344,8 @@ void dev_free(cute_ctx *ctx, void *p);
 cudaError_t pinned_get(cute_ctx *ctx, size_t n, int32_t **p, size_t *cap);
 void pinned_put(cute_ctx *ctx, int32_t *p, size_t cap);
 PairDF pair_df(const DescInfo &di);
+// The kernel's view of pair set `out` (catalogs, sizes, box, (r, mu) data).
+PairDev pair_dev(const DescInfo &di, int out);
 
 // Home chunks of catalog A (plan.cpp): each row of cells cut into chunks of
 // home_chunk objects (the last one of a row shorter), spanning at most

@@ -15,20 +15,20 @@ namespace cute {
 
 // ------------------------------------------------------------------ staging stats
 // Per-block partial reductions of a catalog: min/max per axis, max |x| per
-// axis, min |x|^2 (observer at the origin), and the number of coordinates
-// outside [0, L) (periodic) or not finite.
+// axis, min and max |x|^2 (observer at the origin), and the number of
+// coordinates outside [0, L) (periodic) or not finite.
 struct StageStats {
   double lo[3], hi[3], amax[3], r2min;
   unsigned long long bad;
-  double pad;
+  double r2max;
 };
 
 __global__ void k_stage_stats(const double *__restrict__ xyz, long long n, int periodic, double L,
                               StageStats *__restrict__ out) {
-  __shared__ double s_lo[3][256], s_hi[3][256], s_am[3][256], s_r2[256];
+  __shared__ double s_lo[3][256], s_hi[3][256], s_am[3][256], s_r2[256], s_r2x[256];
   __shared__ unsigned long long s_bad[256];
   double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-  double am[3] = {0, 0, 0}, r2m = DBL_MAX;
+  double am[3] = {0, 0, 0}, r2m = DBL_MAX, r2x = 0;
   unsigned long long bad = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -43,10 +43,12 @@ __global__ void k_stage_stats(const double *__restrict__ xyz, long long n, int p
       r2 += x * x;
     }
     r2m = fmin(r2m, r2);
+    r2x = fmax(r2x, r2);
   }
   int t = threadIdx.x;
   for (int k = 0; k < 3; k++) { s_lo[k][t] = lo[k]; s_hi[k][t] = hi[k]; s_am[k][t] = am[k]; }
   s_r2[t] = r2m;
+  s_r2x[t] = r2x;
   s_bad[t] = bad;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -57,6 +59,7 @@ __global__ void k_stage_stats(const double *__restrict__ xyz, long long n, int p
         s_am[k][t] = fmax(s_am[k][t], s_am[k][t + s]);
       }
       s_r2[t] = fmin(s_r2[t], s_r2[t + s]);
+      s_r2x[t] = fmax(s_r2x[t], s_r2x[t + s]);
       s_bad[t] += s_bad[t + s];
     }
     __syncthreads();
@@ -66,7 +69,7 @@ __global__ void k_stage_stats(const double *__restrict__ xyz, long long n, int p
     for (int k = 0; k < 3; k++) { st.lo[k] = s_lo[k][0]; st.hi[k] = s_hi[k][0]; st.amax[k] = s_am[k][0]; }
     st.r2min = s_r2[0];
     st.bad = s_bad[0];
-    st.pad = 0;
+    st.r2max = s_r2x[0];
     out[blockIdx.x] = st;
   }
 }
@@ -171,11 +174,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restri
   }
 }
 
+// posq (open grids): the FP32 offsets with q = |x|^2 - q0 (observer
+// frame, FP64, rounded once to FP32) in place of the weight, the per-object
+// half of the (r, mu) counts' s.l = |x_j|^2 - |x_i|^2.
 __global__ void k_scatter(const double *__restrict__ xyz, const float *__restrict__ w, int n,
                           GridDev g, const int *__restrict__ cid, const int *__restrict__ rank,
                           const int *__restrict__ start, float4 *__restrict__ pos,
                           float4 *__restrict__ lo, double *__restrict__ s64,
-                          int *__restrict__ perm) {
+                          int *__restrict__ perm, float4 *__restrict__ posq, double q0) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int d = start[cid[i]] + rank[i];
@@ -195,6 +201,10 @@ __global__ void k_scatter(const double *__restrict__ xyz, const float *__restric
   s64[(size_t)n + d] = y;
   s64[2 * (size_t)n + d] = z;
   perm[d] = i;
+  if (posq) {
+    const double q = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)), q0);
+    posq[d] = make_float4(p.x, p.y, p.z, (float)q);
+  }
 }
 
 // cells holding at least one object (grid-stride, one atomic per warp)
@@ -262,7 +272,7 @@ cute_status catalog_stage(cute_ctx *ctx, Catalog &c, const double *xyz, const fl
   }
   CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
   unsigned long long bad = 0;
-  double r2min = DBL_MAX;
+  double r2min = DBL_MAX, r2max = 0;
   for (int k = 0; k < 3; k++) { c.lo[k] = DBL_MAX; c.hi[k] = -DBL_MAX; c.absmax[k] = 0; }
   if (n > 0) {
     for (auto &p : part) {
@@ -272,6 +282,7 @@ cute_status catalog_stage(cute_ctx *ctx, Catalog &c, const double *xyz, const fl
         c.absmax[k] = std::max(c.absmax[k], p.amax[k]);
       }
       r2min = std::min(r2min, p.r2min);
+      r2max = std::max(r2max, p.r2max);
       bad += p.bad;
     }
   } else {
@@ -279,6 +290,7 @@ cute_status catalog_stage(cute_ctx *ctx, Catalog &c, const double *xyz, const fl
     r2min = 0;
   }
   c.rmin = std::sqrt(r2min);
+  c.rmax = std::sqrt(r2max);
   if (bad) {
     return fail(ctx, CUTE_E_INVALID,
                 c.boundary == CUTE_PERIODIC
@@ -290,6 +302,7 @@ cute_status catalog_stage(cute_ctx *ctx, Catalog &c, const double *xyz, const fl
 
 static void free_grid(cute_ctx *ctx, Catalog &c) {
   dev_free(ctx, c.d_pos); c.d_pos = nullptr;
+  dev_free(ctx, c.d_posq); c.d_posq = nullptr;
   dev_free(ctx, c.d_lo); c.d_lo = nullptr;
   dev_free(ctx, c.d_s64); c.d_s64 = nullptr;
   dev_free(ctx, c.d_perm); c.d_perm = nullptr;
@@ -319,6 +332,7 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
     lo[k] = DBL_MAX; hi[k] = -DBL_MAX; g.absmax[k] = 0;
   }
   g.rmin = DBL_MAX;
+  g.rmax = 0;
   bool any = false;
   for (Catalog *c : cats) {
     if (c->n == 0) continue;
@@ -329,11 +343,17 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
       g.absmax[k] = std::max(g.absmax[k], c->absmax[k]);
     }
     g.rmin = std::min(g.rmin, c->rmin);
+    g.rmax = std::max(g.rmax, c->rmax);
   }
   if (!any) {
     for (int k = 0; k < 3; k++) { lo[k] = 0; hi[k] = 1; }
     g.rmin = 0;
   }
+  // (r, mu): q = |x|^2 - q0 with q0 in the middle of the catalogs' range of
+  // |x|^2, so |q| <= qd; qd also covers the FP64 evaluation of |x|^2 - q0
+  // (four roundings of values up to rmax^2)
+  g.q0 = 0.5 * (g.rmin * g.rmin + g.rmax * g.rmax);
+  g.qd = 0.5 * (g.rmax * g.rmax - g.rmin * g.rmin) * (1.0 + 1e-12) + 1e-15 * g.rmax * g.rmax;
   for (int k = 0; k < 3; k++) {
     // cells no smaller than reach/k (with a relative margin that absorbs the
     // rounding of the cell assignment), so objects more than k cells apart
@@ -406,6 +426,7 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
     CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c->d_cell_start, sizeof(int) * (size_t)(ncell + 1)));
     if (n > 0) {
       CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c->d_pos, sizeof(float4) * (size_t)n));
+      if (!g.periodic) CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c->d_posq, sizeof(float4) * (size_t)n));
       CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c->d_lo, sizeof(float4) * (size_t)n));
       CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c->d_s64, sizeof(double) * 3 * (size_t)n));
       CUDA_OR_FAIL(dev_alloc(ctx, (void **)&c->d_perm, sizeof(int) * (size_t)n));
@@ -430,7 +451,7 @@ cute_status grid_build(cute_ctx *ctx, const std::vector<Catalog *> &cats, const 
     if (n > 0) {
       k_scatter<<<(n + 255) / 256, 256, 0, ctx->stream>>>(c->d_xyz, c->d_w, n, gd, cid, rank,
                                                           c->d_cell_start, c->d_pos, c->d_lo,
-                                                          c->d_s64, c->d_perm);
+                                                          c->d_s64, c->d_perm, c->d_posq, g.q0);
       CUDA_OR_FAIL(cudaGetLastError());
     }
     // host copy of cell_start and the occupied-cell count (after it), into

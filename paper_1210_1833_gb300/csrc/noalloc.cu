@@ -119,19 +119,7 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
     chunks_build(*di.g, di.A->h_cell_start, 32 * hp, chunks);
     stencil_build(*di.g, di.is_auto, false, shape, di.need, stencil);
   }
-  PairDev pd;
-  std::memset(&pd, 0, sizeof(pd));
-  pd.posA = di.A->d_pos;
-  pd.posB = di.B->d_pos;
-  pd.sA = di.A->d_s64;
-  pd.sB = di.B->d_s64;
-  pd.permA = di.A->d_perm;
-  pd.nA = (int32_t)di.A->n;
-  pd.nB = (int32_t)di.B->n;
-  pd.out = 0;
-  pd.is_auto = di.is_auto;
-  pd.L32 = (float)di.g->L;
-  pd.L64 = di.g->periodic ? di.g->L : 0.0;
+  PairDev pd = pair_dev(di, 0);
   PairWork pw;
   std::memset(&pw, 0, sizeof(pw));
   pw.nchunks = (int32_t)chunks.size();
@@ -219,7 +207,8 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   p.stats = (unsigned long long *)(dev + o_cnt) + 1;
   p.err = ctx->d_err;
 
-  SmemLayout L = smem_layout(p.lut_words, p.band_words, P.nslots, P.R, hp, acc);
+  SmemLayout L = smem_layout(p.lut_words, p.band_words, P.nslots, P.R, hp, acc,
+                             kind == CUTE_R_MU && acc != 0);
   const int wmax = count_max_warps(kind == CUTE_MONO || kind == CUTE_THETA, hp, acc);
   int warps = ctx->warps_override ? std::min(ctx->warps_override, wmax) : wmax;
   while (warps > 1 && (size_t)L.lut_bytes + (size_t)warps * L.warp_bytes > ctx->smem_optin) warps--;

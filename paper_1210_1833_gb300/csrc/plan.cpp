@@ -324,6 +324,42 @@ static bool make_arith(const double *e, int n, const AxisErr &err, double eta0, 
   return p.thr_b < 0.2f;
 }
 
+// ------------------------------------------------------------------ mu bound
+// Error of the kernel's FP32 mu about the midpoint line of sight (Sec. 2.1),
+// as eps(r) = a / r + b for a pair at separation r.  The kernel forms
+//   s.l = q_j - q_i            (q = |x|^2 - q0, rounded once from FP64;
+//                               |x_j|^2 - |x_i|^2 = (x_j - x_i).(x_j + x_i)),
+//   k l^2 = k (2 q_j) + (C_i - k r^2),  C_i = k (2 q_i + 4 q0) rounded once
+//                              (|l|^2 = 2|x_i|^2 + 2|x_j|^2 - r^2),
+//   mu k^-1/2 = |s.l| rsqrt(r^2 k l^2),
+// with r^2 from the FP32 separation.  Then
+//   * s.l: |dq_i| + |dq_j| <= 2 u qd (each q rounded to nearest once), over
+//     r |l| >= r lmin: 2 u qd / lmin per unit of 1/r, taken x 1.25 (the
+//     bound is rigorous; the margin absorbs the first-order products), and
+//     the subtraction's rounding, u |s.l| <= u r |l| (in the budget below);
+//   * r^2: mu ~ (r^2)^-1/2 takes half its relative error, err(r^2) / 2r^2
+//     (SqErr, already twice the first-order bound): 2 sqrt3 eta0 / r +
+//     2 sqrt3 u, the square's own rounding inside the budget;
+//   * k l^2: half its relative error eps_l, from the roundings of C_i (u of
+//     |2 q_i + 4 q0| <= 2 qd + 4 q0), of the two q's (2 u qd each, doubled),
+//     of the two FMAs (u of |C_i - k r^2| and u of k |l|^2 <= 4 k (q0 + qd))
+//     and r^2's error, over k |l|^2 >= k lmin^2; taken x 1.1;
+//   * 40 u for the other roundings (s.l, k, the product r^2 k l^2, rsqrtf's
+//     documented 2 ulp, the final FMA and r^2's rounding: about 10 u).
+// False when no lower bound of |l| exists (catalogs around the observer).
+static bool mu_bound(const ErrorParams &ep, double rmax, double &a, double &b) {
+  if (!(ep.lmin > 0)) return false;
+  const double s3 = std::sqrt(3.0);
+  const double P = 2.0 * ep.qd + 4.0 * ep.q0;
+  const SqErr r2err{3, ep.eta0};
+  const double eps_l = (kU * P + 4.0 * kU * ep.qd + kU * (P + rmax * rmax) +
+                        4.0 * kU * (ep.q0 + ep.qd) + r2err(rmax * rmax)) /
+                       (ep.lmin * ep.lmin) * (1.0 + 1e-6);
+  a = 2.0 * s3 * ep.eta0 * (1.0 + 1e-5) + 1.25 * 2.0 * kU * ep.qd / ep.lmin;
+  b = 2.0 * s3 * kU + 0.55 * eps_l + 40 * kU + 1e-12;
+  return std::isfinite(a) && std::isfinite(b);
+}
+
 // ------------------------------------------------------------------ plan
 std::string plan_build(int kind, const double *e0, int n0, const double *e1, int n1,
                        const ErrorParams &ep, int lut_budget_words, size_t hist_budget_bytes,
@@ -399,17 +435,19 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
       ok = make_arith(e0, n0, A0.err, ep.eta0, true, false, false, P0) &&
            make_arith(e1, n1, A0.err, ep.eta0, false, true, false, P1);
       if (ok) {
-        // mu bound in t units: n_mu * eps(r), eps(r) = a / r + b (see
-        // above), without the final doubling: the 2 sqrt3 of the perturbed
-        // unit vectors is twice the first-order bound, and the 40 u rounding
-        // budget more than twice the rounding of the kernel's formula
-        double lterm = (ep.lmin > 0) ? ep.eta_l / ep.lmin : INFINITY;
-        double a = 2.0 * std::sqrt(3.0) * ep.eta0 * (1.0 + 1e-5);
-        double b = 2.0 * std::sqrt(3.0) * (kU + lterm) + 40 * kU + 1e-12;
+        // mu bound in t units: n_mu * eps(r), eps(r) = a / r + b (mu_bound
+        // below), without the final doubling: the squared separation's
+        // bound is itself twice the first-order one, the q term is rigorous
+        // (x 1.25), and the 40 u rounding budget is four times the kernel's
+        double a = 0, b = 0;
+        const bool fin = mu_bound(ep, e0[n0], a, b);
         double nmu = n1 / (e1[n1] - e1[0]);
         P1.thr_a = (float)(nmu * a * 1.0001);
         P1.thr_b = (float)((double)P1.thr_b + nmu * b * 1.0001);
-        ok = std::isfinite(lterm) && (double)P1.thr_b < 0.2;
+        // the kernel forms k l^2 with k = 1/n_mu^2 in FP32 (its rounding,
+        // u/2 relative in mu, is inside the rounding budget)
+        P1.lsc = (float)(1.0 / (nmu * nmu));
+        ok = fin && (double)P1.thr_b < 0.2;
       }
     }
     if (ok) {
@@ -428,21 +466,17 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
     }
   }
 
-  // mu: FP32 mu = |sl| * rsqrt(r^2 l^2) with sl = 2 s.x_i + r^2 and
-  // l^2 = 4|x_i|^2 + 4 s.x_i + r^2 (l = 2 x_i + s).  |d mu| <= 2 sqrt3
-  // (eta_s/r + eta_l/|l|) from the perturbed unit vectors, plus 40 u of FP32
-  // rounding (dot products, sums, rsqrtf's documented 2 ulp, final product,
-  // the kernel's subtraction of the edge), plus the FP64 canonical rounding;
-  // doubled.  The bound grows as 1/r: each r slot carries an error class c
-  // (bound = base * 2^c, base = the bound at r_max), r slots below
-  // r_floor = max(first nonzero edge, r_max / 40) are always re-tested in
-  // FP64, and the mu table is classified with the largest bound in use.
+  // mu on the tables: the bound a / r + b of mu_bound, doubled.  It grows
+  // as 1/r: each r slot carries an error class c (bound = base * 2^c, base =
+  // the bound at r_max), r slots below r_floor = max(first nonzero edge,
+  // r_max / 40) are always re-tested in FP64, and the mu table is classified
+  // with the largest bound in use.
   std::vector<int> always_slot(n0 + 2, 0), cls_slot(n0 + 2, 0);
   if (kind == KRMU) {
-    double lterm = (ep.lmin > 0) ? ep.eta_l / ep.lmin : INFINITY;
+    double ma = 0, mb = 0;
+    if (!mu_bound(ep, e0[n0], ma, mb)) return "(r, mu) catalogs too close to the observer";
     auto eps_at = [&](double r) {
-      return r > 0 ? 2.0 * (2.0 * std::sqrt(3.0) * ((ep.eta0 + kU * r) / r + lterm) + 40 * kU) + 1e-12
-                   : INFINITY;
+      return r > 0 ? 2.0 * (ma / r + mb) + 1e-12 : INFINITY;
     };
     double r_floor = e0[n0] / 40.0;
     for (int k = 1; k <= n0; k++)

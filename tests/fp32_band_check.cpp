@@ -148,12 +148,31 @@ static Slot sigpi_table(const Plan &P, const float *q, const float *n) {
   const int s = table_slot(P, ffma(dy, dy, fmul(dx, dx)), fmul(dz, dz), near);
   return {s, near ? 1.0f : 0.0f};
 }
-static Slot rmu_table(const Plan &P, const float *q, const float *n, const float *xi, float aq) {
+// (r, mu) inputs of one pair: q = |x|^2 - q0 of both objects (FP64, rounded
+// once to FP32, as the grid build stores them) and C_i = k (2 q_i + 4 q0)
+// (FP64, rounded once, as the kernel forms it per home object)
+struct RmuIn {
+  float qi, qj, ci, k;
+};
+static RmuIn rmu_inputs(const double *xi, const double *xj, double q0, float k) {
+  auto q = [&](const double *x) { return (float)(((x[0] * x[0] + x[1] * x[1]) + x[2] * x[2]) - q0); };
+  RmuIn r;
+  r.qi = q(xi);
+  r.qj = q(xj);
+  r.k = k;
+  r.ci = (float)((double)k * (2.0 * (double)r.qi + 4.0 * q0));
+  return r;
+}
+// s.l = q_j - q_i and k l.l = 2k q_j + (C_i - k r^2)
+static void rmu_sl_l2(const RmuIn &in, float r2, float &sl, float &l2) {
+  sl = fadd(in.qj, -in.qi);
+  l2 = ffma(in.qj, 2.0f * in.k, ffma(r2, -in.k, in.ci));
+}
+static Slot rmu_table(const Plan &P, const float *q, const float *n, const RmuIn &in) {
   const float dx = fadd(q[0], n[0]), dy = fadd(q[1], n[1]), dz = fadd(q[2], n[2]);
   const float r2 = ffma(dz, dz, ffma(dy, dy, ffma(dx, dx, kVFloor)));
-  const float sx = ffma(dz, xi[2], ffma(dy, xi[1], fmul(dx, xi[0])));
-  const float sl = ffma(sx, 2.0f, r2);
-  const float l2 = ffma(sx, 4.0f, fadd(aq, r2));
+  float sl, l2;
+  rmu_sl_l2(in, r2, sl, l2);
   const float mu = fmul(std::fabs(sl), rsqrt_dev(fmul(r2, l2)));
   bool near;
   const int s = table_slot(P, r2, mu, near);
@@ -187,19 +206,17 @@ static Slot sigpi_fp32(const AxisPlan &a0, const AxisPlan &a1, int slots1, const
   return {(int)(bits(tc) - kMagicBits) + slots1 + 1, std::fmax(std::fabs(h0), std::fabs(g1))};
 }
 
-// (r, mu): xi = home in the observer frame (FP32), aq = 4 |x_i|^2 (FP32)
+// (r, mu) with uniform edges: axis 1 takes t = |s.l| rsqrt(r^2 k l.l) + cst
 static Slot rmu_fp32(const AxisPlan &a0, const AxisPlan &a1, int slots1, const float *q,
-                     const float *n, const float *xi, float aq) {
+                     const float *n, const RmuIn &in) {
   const float dx = fadd(q[0], n[0]), dy = fadd(q[1], n[1]), dz = fadd(q[2], n[2]);
   const float r2 = ffma(dz, dz, ffma(dy, dy, ffma(dx, dx, kVFloor)));
-  const float sx = ffma(dz, xi[2], ffma(dy, xi[1], fmul(dx, xi[0])));
-  const float sl = ffma(sx, 2.0f, r2);
-  const float l2 = ffma(sx, 4.0f, fadd(aq, r2));
+  float sl, l2;
+  rmu_sl_l2(in, r2, sl, l2);
   const float rr = rsqrt_dev(r2);
   const float pl = fmul(r2, l2);
-  const float mu = fmul(std::fabs(sl), rsqrt_dev(pl));
   const float t0 = std::fmin(ffma(fmul(r2, rr), a0.inv, a0.cst), a0.thi);
-  const float t1 = std::fmin(ffma(mu, a1.inv, a1.cst), a1.thi);
+  const float t1 = std::fmin(ffma(std::fabs(sl), rsqrt_dev(pl), a1.cst), a1.thi);
   const float tm0 = fadd(t0, kMagic), tm1 = fadd(t1, kMagic);
   const float f0 = fadd(tm0, -kMagic);
   const float h0 = ffma(f0, -1.0f, t0), h1 = ffma(fadd(tm1, -kMagic), -1.0f, t1);
@@ -237,16 +254,21 @@ struct Tally {
 };
 
 // the library's per-component error bound (error_params): FP32 frame
-// offsets within xm of the centre, periodic image shifts
-static ErrorParams eparams(double xm, double L, double rmax, double absmax, double rmin) {
-  ErrorParams ep{0, 0, 0};
+// offsets within xm of the centre, periodic image shifts; for (r, mu) the
+// geometry's q0 and qd from the smallest and largest |x| (grid_build)
+static double rmu_q0(double rmin, double robs) { return 0.5 * (rmin * rmin + robs * robs); }
+static ErrorParams eparams(double xm, double L, double rmax, double absmax, double rmin,
+                           double robs = 0) {
+  ErrorParams ep{0, 0, 0, 0};
+  ep.q0 = rmu_q0(rmin, robs);
+  ep.qd = 0.5 * (robs * robs - rmin * rmin) * (1.0 + 1e-12) + 1e-15 * robs * robs;
   if (L > 0) {
     const double dL = std::fabs((double)(float)L - L);
     ep.eta0 = kU32 * (3.0 * xm + 2.0 * rmax) * 1.01 + dL * 1.01 + 1e-12 * (xm + L);
   } else {
     ep.eta0 = kU32 * 2.0 * xm * 1.01 + 1e-12 * xm;
   }
-  ep.eta_l = kU32 * (4.0 * absmax + rmax) * 1.01 + ep.eta0 + kU32 * rmax;
+  (void)absmax;
   ep.lmin = 2.0 * rmin - rmax;
   return ep;
 }
@@ -407,7 +429,7 @@ static Tally run_sigpi(const std::vector<double> &e0, const std::vector<double> 
 
 // (r, mu) on a light-cone-like region: objects around centre fo (observer
 // at the origin), extent xm about fo
-static Tally run_rmu(const double *fo, double xm, double rmin, double absmax,
+static Tally run_rmu(const double *fo, double xm, double rmin, double robs, double absmax,
                      const std::vector<double> &e0, int n1, std::vector<double> rs, bool arith,
                      std::mt19937_64 &g) {
   const int n0 = (int)e0.size() - 1;
@@ -415,8 +437,8 @@ static Tally run_rmu(const double *fo, double xm, double rmin, double absmax,
   for (int k = 0; k <= n1; k++) e1[k] = (double)k / n1;
   const std::vector<double> E0 = squares(e0), M = squares(e1);
   Plan P;
-  const std::string m = plan_build(KRMU, e0.data(), n0, e1.data(), n1,
-                                   eparams(xm, 0, e0[n0], absmax, rmin), 8192, 12288, true, P);
+  const ErrorParams ep = eparams(xm, 0, e0[n0], absmax, rmin, robs);
+  const std::string m = plan_build(KRMU, e0.data(), n0, e1.data(), n1, ep, 8192, 12288, true, P);
   if (!plan_ok(m, P, arith) || (arith && P.ax[1].mode != kArith)) return Tally{0, 0, 1};
   if (arith) {
     shrink(P.ax[0]);
@@ -432,8 +454,12 @@ static Tally run_rmu(const double *fo, double xm, double rmin, double absmax,
     for (int k = 0; k <= n1; k++)
       for (double off : kOff)
         for (int rep = 0; rep < 3; rep++) {
-          double xi[3], tt[3];
-          for (int c = 0; c < 3; c++) xi[c] = fo[c] + (xm - 210.0) * U(g);
+          // x_i in the shell, far enough inside it that x_j = x_i + s is too
+          double xi[3], tt[3], ri = 0;
+          do {
+            for (int c = 0; c < 3; c++) xi[c] = fo[c] + (xm - 210.0) * U(g);
+            ri = std::sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+          } while (ri < rmin + 201.0 || ri > robs - 201.0);
           unit(g, tt);
           const double mm = std::min(std::max(e1[k] * (1.0 + off), 0.0), 1.0);
           const double rr = (rep == 0 && k == 0) ? r * (1.0 + off) : r;
@@ -470,14 +496,11 @@ static Tally run_rmu(const double *fo, double xm, double rmin, double absmax,
             canon = (br + 1) * (n1 + 2) + bm + 1;
           }
           // the kernel's inputs
-          const double zero[3] = {0, 0, 0};
-          float q[3], nn[3], xf[3];
+          float q[3], nn[3];
           kernel_inputs(xi, xj, fo, 0.0, q, nn);
-          (void)zero;
-          for (int c = 0; c < 3; c++) xf[c] = (float)xi[c];
-          const float aq = (float)(4.0 * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]));
-          const Slot res = arith ? rmu_fp32(P.ax[0], P.ax[1], P.slots1, q, nn, xf, aq)
-                                 : rmu_table(P, q, nn, xf, aq);
+          const RmuIn in = rmu_inputs(xi, xj, ep.q0, P.ax[1].lsc);
+          const Slot res = arith ? rmu_fp32(P.ax[0], P.ax[1], P.slots1, q, nn, in)
+                                 : rmu_table(P, q, nn, in);
           const int s0i = res.slot / P.slots1, s1i = res.slot % P.slots1;
           const int fp32 = (s0i >= 1 && s0i <= n0 && s1i >= 1 && s1i <= n1) ? res.slot : -1;
           t.add(arith ? res.score >= thr : res.score > 0.0f, fp32, canon);
@@ -579,7 +602,7 @@ static Tally run_lattice_rmu(bool arith, std::mt19937_64 &g, long &ties) {
   const std::vector<double> rp = lattice_pts(g, 200, lo, hi);
   x.insert(x.end(), rp.begin(), rp.end());
   const double fo[3] = {320.25, 319.5, 0.125};
-  double xm = 0, absmax = 0, rmin = 1e300;
+  double xm = 0, absmax = 0, rmin = 1e300, robs = 0;
   for (size_t i = 0; i < x.size(); i += 3) {
     double a2 = 0;
     for (int c = 0; c < 3; c++) {
@@ -588,10 +611,11 @@ static Tally run_lattice_rmu(bool arith, std::mt19937_64 &g, long &ties) {
       a2 += x[i + c] * x[i + c];
     }
     rmin = std::min(rmin, std::sqrt(a2));
+    robs = std::max(robs, std::sqrt(a2));
   }
   Plan P;
-  const std::string m = plan_build(KRMU, e0.data(), n0, e1.data(), n1,
-                                   eparams(xm, 0, e0[n0], absmax, rmin), 8192, 12288, true, P);
+  const ErrorParams ep = eparams(xm, 0, e0[n0], absmax, rmin, robs);
+  const std::string m = plan_build(KRMU, e0.data(), n0, e1.data(), n1, ep, 8192, 12288, true, P);
   if (!plan_ok(m, P, arith) || (arith && P.ax[1].mode != kArith)) return Tally{0, 0, 1};
   if (arith) {
     shrink(P.ax[0]);
@@ -625,12 +649,11 @@ static Tally run_lattice_rmu(bool arith, std::mt19937_64 &g, long &ties) {
         }
         canon = (br + 1) * (n1 + 2) + bm + 1;
       }
-      float q[3], nn[3], xf[3];
+      float q[3], nn[3];
       kernel_inputs(xi, xj, fo, 0.0, q, nn);
-      for (int c = 0; c < 3; c++) xf[c] = (float)xi[c];
-      const float aq = (float)(4.0 * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]));
-      const Slot res = arith ? rmu_fp32(P.ax[0], P.ax[1], P.slots1, q, nn, xf, aq)
-                             : rmu_table(P, q, nn, xf, aq);
+      const RmuIn in = rmu_inputs(xi, xj, ep.q0, P.ax[1].lsc);
+      const Slot res = arith ? rmu_fp32(P.ax[0], P.ax[1], P.slots1, q, nn, in)
+                             : rmu_table(P, q, nn, in);
       const int s0i = res.slot / P.slots1, s1i = res.slot % P.slots1;
       const int fp32 = (s0i >= 1 && s0i <= n0 && s1i >= 1 && s1i <= n1) ? res.slot : -1;
       t.add(arith ? res.score >= thr : res.score > 0.0f, fp32, canon);
@@ -667,7 +690,7 @@ int main(int argc, char **argv) {
     std::snprintf(nm, sizeof nm, "sigpi_periodic_r%d", g_mode);
     report(nm, run_sigpi(uniform(3.0, 50), uniform(3.0, 50), 1500.0, true, g));
     std::snprintf(nm, sizeof nm, "rmu_lightcone_r%d", g_mode);
-    report(nm, run_rmu(fo, 1250.0, 1000.0, 2500.0, uniform(5.0, 40), 40, rs_u, true, g));
+    report(nm, run_rmu(fo, 1250.0, 1000.0, 2500.0, 2500.0, uniform(5.0, 40), 40, rs_u, true, g));
     // the table path (edges not uniform from 0)
     std::snprintf(nm, sizeof nm, "table_mono_periodic_r%d", g_mode);
     report(nm, run_mono(logspace(0.1, 150.0, 20), 2000.0, 0, false, false, g));
@@ -678,7 +701,7 @@ int main(int argc, char **argv) {
     std::snprintf(nm, sizeof nm, "table_sigpi_periodic_r%d", g_mode);
     report(nm, run_sigpi(logspace(0.5, 60.0, 15), uniform(2.0, 30), 1500.0, false, g));
     std::snprintf(nm, sizeof nm, "table_rmu_lightcone_r%d", g_mode);
-    report(nm, run_rmu(fo, 1250.0, 1000.0, 2500.0, r_log, 10, rs_l, false, g));
+    report(nm, run_rmu(fo, 1250.0, 1000.0, 2500.0, 2500.0, r_log, 10, rs_l, false, g));
   }
   // integer lattices ("name cases flagged violations", then "name_ties count")
   for (g_mode = 0; g_mode < 3; g_mode++) {
