@@ -227,6 +227,38 @@ __device__ __forceinline__ void mono_arith2(const AxisPlan &a, float2 qx, float2
   o1 = __float_as_uint(tm.y) * stride + c;
 }
 
+// Log-spaced edges (kArithLog), monopole and chords, two pairs at once:
+// v clamped below at vlo (where t = -1: slot 0), t = A log2(v) +
+// (D v + B) v + C by the hardware log2 (PTX lg2.approx.ftz.f32), clamped
+// above to thi; the pair is near an edge when |h| + thr_a / sqrt(v)
+// reaches near_c (the bound falls as 1/sqrt(v); one FMA per pair).
+__device__ __forceinline__ float lg2_hw(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ void mono_log2(const AxisPlan &a, float2 qx, float2 qy, float2 qz,
+                                          float2 nx, float2 ny, float2 nz, uint32_t stride,
+                                          uint32_t c, uint32_t &o0, uint32_t &o1, float2 &sc) {
+  const float2 dx = __fadd2_rn(qx, nx), dy = __fadd2_rn(qy, ny), dz = __fadd2_rn(qz, nz);
+  float2 v = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+  v.x = fmaxf(v.x, a.vlo);
+  v.y = fmaxf(v.y, a.vlo);
+  const float2 lg = make_float2(lg2_hw(v.x), lg2_hw(v.y));
+  const float2 rr = make_float2(rsqrt_hw(v.x), rsqrt_hw(v.y));
+  const float2 pv = __ffma2_rn(v, __ffma2_rn(v, make_float2(a.ld, a.ld), make_float2(a.lb, a.lb)),
+                               make_float2(a.cst, a.cst));
+  float2 t = __ffma2_rn(lg, make_float2(a.inv, a.inv), pv);
+  t.x = fminf(t.x, a.thi);  // above the last edge (and far sentinels): the top slot
+  t.y = fminf(t.y, a.thi);
+  const float2 tm = __fadd2_rn(t, make_float2(kMagic, kMagic));
+  const float2 fl = __fadd2_rn(tm, make_float2(-kMagic, -kMagic));
+  const float2 h = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), t);
+  sc = make_float2(fmaf(rr.x, a.thr_a, fabsf(h.x)), fmaf(rr.y, a.thr_a, fabsf(h.y)));
+  o0 = __float_as_uint(tm.x) * stride + c;
+  o1 = __float_as_uint(tm.y) * stride + c;
+}
+
 // Two (r, mu) pairs at once with uniform edges on both axes.
 __device__ __forceinline__ float2 clampt(float2 t, float hi) {
   return make_float2(fminf(t.x, hi), fminf(t.y, hi));
@@ -323,8 +355,9 @@ __device__ __forceinline__ void arith_pair_out(float2 s2, uint32_t (&o)[2], int 
 // (monopole, theta; sigma, pi with pi rescaled), or the smaller of near_at
 // of r and near_c of mu (r, mu: a few more flags than the exact per-axis
 // tests, all decided by the re-test).
-template <int KIND>
+template <int KIND, int M0>
 __device__ __forceinline__ float near_thr(const KParams &p) {
+  if (M0 == kArithLog) return p.ax[0].near_c;
   if (KIND == KRMU) return fminf(p.ax[0].near_at, p.ax[1].near_c);
   return p.ax[0].near_at;
 }
@@ -350,8 +383,8 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
                                            int lane, unsigned &near_count) {
   constexpr int U = 8 / HP;  // neighbours per step: 8 pairs per lane per step
   constexpr int NP = U * HP;
-  constexpr bool kLazy = M0 == kArith;
-  const float thr = near_thr<KIND>(p);
+  constexpr bool kLazy = M0 == kArith || M0 == kArithLog;
+  const float thr = near_thr<KIND, M0>(p);
   const int slot_shift = 31 - __clz(p.R * 4);
   // Plain counts add straight to the lane's histogram copy: its shared
   // address is folded into the offset constants (slot k = bits - magic + 1
@@ -386,6 +419,16 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
           float2 s2;
           mono_arith2(p.ax[0], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], st0, c1d, o[0], o[1],
                       s2);
+          arith_pair_out<HP, MASK, kLazy>(s2, o, u, sp, gj0 + j + u, h, zoff, thr, off, sc, nmask);
+        }
+      } else if constexpr ((KIND == KMONO || KIND == KTHETA) && M0 == kArithLog) {
+        const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
+                     qz = make_float2(q.z, q.z);
+#pragma unroll
+        for (int sp = 0; sp < HP / 2; sp++) {
+          uint32_t o[2];
+          float2 s2;
+          mono_log2(p.ax[0], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], st0, c1d, o[0], o[1], s2);
           arith_pair_out<HP, MASK, kLazy>(s2, o, u, sp, gj0 + j + u, h, zoff, thr, off, sc, nmask);
         }
       } else if constexpr (KIND == KSIGPI && M0 == kArith) {
@@ -558,6 +601,7 @@ __device__ __forceinline__ void tile_dispatch(const KParams &p, uint32_t lut,
   const int m0 = p.ax[0].mode;
   if (KIND == KMONO || KIND == KTHETA) {
     if (m0 == kArith) tile_dispatch_mask<KIND, HP, kArith, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
+    else if (m0 == kArithLog) tile_dispatch_mask<KIND, HP, kArithLog, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
     else if (m0 == kLutLinear) tile_dispatch_mask<KIND, HP, kLutLinear, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
     else tile_dispatch_mask<KIND, HP, kLutLog, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
   } else {

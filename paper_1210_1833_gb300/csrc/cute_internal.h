@@ -32,6 +32,7 @@ constexpr int kBandShift = 20;             // band index (bits 20..31)
 constexpr int kLutLinear = 0;              // idx = rne(v * scale)
 constexpr int kLutLog = 1;                 // idx = max((bits(v) >> shift) - base, 0)
 constexpr int kArith = 2;                  // uniform edges: bin = floor((x - e0) / delta)
+constexpr int kArithLog = 3;               // log-spaced edges: t from log2(v) (monopole, chords)
 
 struct AxisPlan {
   int mode = 0;
@@ -56,6 +57,9 @@ struct AxisPlan {
   float near_c = 0;
   // (sigma, pi), axis 1: near_at(axis 0) / near_at(axis 1) rounded up
   float near_scale = 1;
+  // kArithLog: t = inv log2(max(v, vlo)) + (ld v + lb) v + cst, clamped
+  // above to thi; near when |h| + thr_a / sqrt(v) reaches near_c (as mu)
+  float lb = 0, ld = 0, vlo = 0;
   // (r, mu), axis 1: scale k of the squared line-of-sight length the kernel
   // forms (k = 1/inv^2 rounded, so |s.l| / sqrt(r^2 k l^2) is mu * inv;
   // 1 for tables)

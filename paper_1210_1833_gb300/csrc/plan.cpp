@@ -324,6 +324,132 @@ static bool make_arith(const double *e, int n, const AxisErr &err, double eta0, 
   return p.thr_b < 0.2f;
 }
 
+// ------------------------------------------------------------------ log-spaced edges
+// Edges uniform in a logarithm -- log r bins (ln r = ln(v)/2), and angles
+// log-spaced in theta binned on squared chords c^2, where theta = 2 asin(c/2)
+// makes ln theta = ln(c^2)/2 + g(c^2/4) with g(y) = ln(asin(sqrt y)/sqrt y)
+// = y/6 + 11 y^2/180 + ... smooth and small -- take
+//   t(v) = A log2(v) + (D v + B) v + C,  v the squared separation,
+// fitted (least squares, long double) so that t(E_k) = k - 1/2 at the
+// canonical boundaries E_k = fl(e_k^2); db is the largest miss there,
+// measured with the FP32 constants the kernel uses.  With t monotone, a
+// pair whose FP32 t lies farther than db + (its error) from every
+// half-integer is binned as the canonical formula bins it.
+//
+// The error of the FP32 t at v (in t units) is
+//   t'(v) err(v) + A e_lg + (rounding of the three FMAs) + db,
+// with err(v) the squared separation's bound (SqErr, already doubled),
+// e_lg(v) = 2^-21 + 2^-22 |log2 v| for the hardware log2 (lg2.approx: an
+// absolute part, and about two ulp of the FP32 result; a GPU test measures
+// it over every FP32 input of the range in use), and t'(v) = A/(v ln 2) +
+// |B| + 2|D| v.  Its A/(v ln 2) err(v) part falls as 1/sqrt(v): the bound is taken
+// as thr_a / sqrt(v) + thr_b, thr_b the parts that do not fall and thr_a the
+// smallest constant that covers the rest at every v (sampled on a fine log
+// grid), raised by the relative error of the FP32 v (the kernel takes
+// 1/sqrt(v) from the FP32 v) and rsqrtf's 2 ulp.
+// v is clamped below at vlo, where t(vlo) = -1 (slot 0, far from edge 0).
+static bool solve_ld(int m, long double M[4][5], long double *x) {
+  for (int c = 0; c < m; c++) {
+    int piv = c;
+    for (int r = c + 1; r < m; r++)
+      if (fabsl(M[r][c]) > fabsl(M[piv][c])) piv = r;
+    if (!(fabsl(M[piv][c]) > 0)) return false;
+    for (int k = 0; k <= m; k++) std::swap(M[c][k], M[piv][k]);
+    for (int r = 0; r < m; r++) {
+      if (r == c) continue;
+      const long double f = M[r][c] / M[c][c];
+      for (int k = c; k <= m; k++) M[r][k] -= f * M[c][k];
+    }
+  }
+  for (int c = 0; c < m; c++) x[c] = M[c][m] / M[c][c];
+  return true;
+}
+
+static long double logt(const AxisPlan &p, long double v) {
+  return (long double)p.inv * log2l(v) + ((long double)p.ld * v + (long double)p.lb) * v +
+         (long double)p.cst;
+}
+
+static bool make_logarith(const double *e, int n, const SqErr &err, AxisPlan &p) {
+  if (n < 2 || !(e[0] > 0)) return false;
+  std::vector<long double> E(n + 1);
+  for (int k = 0; k <= n; k++) E[k] = (long double)(e[k] * e[k]);  // canonical FP64 squares
+  // unknowns: A (log2 v), C (1), B (v), D (v^2); fewer with few edges
+  const int m = std::min(4, n + 1);
+  long double sc[4] = {0, 0, 0, 0};
+  auto col = [&](int j, long double v) -> long double {
+    return j == 0 ? log2l(v) : (j == 1 ? 1.0L : (j == 2 ? v : v * v));
+  };
+  for (int j = 0; j < m; j++)
+    for (int k = 0; k <= n; k++) sc[j] = std::max(sc[j], fabsl(col(j, E[k])));
+  long double M[4][5] = {};
+  for (int k = 0; k <= n; k++) {
+    long double f[4];
+    for (int j = 0; j < m; j++) f[j] = col(j, E[k]) / sc[j];
+    for (int a = 0; a < m; a++) {
+      for (int b = 0; b < m; b++) M[a][b] += f[a] * f[b];
+      M[a][m] += f[a] * ((long double)k - 0.5L);
+    }
+  }
+  long double x[4] = {0, 0, 0, 0};
+  if (!solve_ld(m, M, x)) return false;
+  p = AxisPlan();
+  p.mode = kArithLog;
+  p.nb = n;
+  p.inv = (float)(x[0] / sc[0]);
+  p.cst = (float)(x[1] / sc[1]);
+  p.lb = m > 2 ? (float)(x[2] / sc[2]) : 0.0f;
+  p.ld = m > 3 ? (float)(x[3] / sc[3]) : 0.0f;
+  if (!(p.inv > 0)) return false;
+  // the miss at the boundaries, with the FP32 constants
+  long double db = 0;
+  for (int k = 0; k <= n; k++) db = std::max(db, fabsl(logt(p, E[k]) - ((long double)k - 0.5L)));
+  if (!(db < 0.01L)) return false;
+  // vlo: t(vlo) = -1, below E_0 (bisection on the monotone model)
+  long double lo = E[0] * 1e-12L, hi = E[0];
+  if (!(logt(p, lo) < -1.0L)) return false;
+  for (int it = 0; it < 200; it++) {
+    const long double mid = sqrtl(lo * hi);
+    if (logt(p, mid) < -1.0L) lo = mid; else hi = mid;
+  }
+  p.vlo = (float)hi;
+  const double vlo = (double)p.vlo;
+  if (!(logt(p, vlo) > -1.2L && logt(p, vlo) < -0.8L)) return false;
+  p.thi = (float)n;
+  // the value at which t reaches n + 1/2 (beyond it the clamp holds t at n)
+  long double vtop = E[n];
+  while (logt(p, vtop) < (long double)n + 0.5L && vtop < 1e30L) vtop *= 1.01L;
+  const double A = p.inv, B = std::fabs((double)p.lb), D = std::fabs((double)p.ld);
+  auto elg = [](double v) {
+    return std::ldexp(1.0, -21) + std::ldexp(1.0, -22) * std::fabs(std::log2(v));
+  };
+  // FP32 rounding of the three FMAs: u of |D v + B|, u of |(.) v + C| and
+  // u of |t|, the latter two below |C| + B v + D v^2 + n + 2
+  auto rnd = [&](double v) {
+    return kU * (std::fabs((double)p.cst) + B * v + D * v * v + n + 2.0) * 2.0 * 1.01 +
+           kU * (D * v + B) * v * 1.01;
+  };
+  const double vt = (double)vtop;
+  double thr_b = (B + 2.0 * D * vt) * err(vt) + A * elg(vt) + rnd(vt) + (double)db + 1e-7;
+  // rounding parts that do not fall with v: the err(v)/v constant part
+  // 2 ((c+1) u + 2 sqrt3 u + 4e-16) through A / ln 2
+  thr_b += A / std::log(2.0) * 2.0 * (4.0 * kU * 1.01 + 2.0 * std::sqrt(3.0) * kU * 1.0001 + 4e-16);
+  double thr_a = 0, maxrel = 0;
+  for (int i = 0; i <= 4000; i++) {
+    const double v = vlo * std::pow(vt / vlo, i / 4000.0);
+    const double T = (A / (v * std::log(2.0)) + B + 2.0 * D * v) * err(v) + A * elg(v) + rnd(v) +
+                     (double)db + 1e-7;
+    thr_a = std::max(thr_a, (T - thr_b) * std::sqrt(v));
+    maxrel = std::max(maxrel, err(v) / v);
+  }
+  thr_a = std::max(thr_a, 0.0) * (1.0 + maxrel + 4.0 * kU) * 1.0001;
+  p.thr_a = (float)thr_a;
+  p.thr_b = (float)thr_b;
+  p.near_c = f32_down(0.5 - thr_b - std::ldexp(1.0, -22));
+  // the bands must stay narrow where pairs are binned: at E_0
+  return thr_a / std::sqrt((double)E[0]) + thr_b < 0.2;
+}
+
 // ------------------------------------------------------------------ mu bound
 // Error of the kernel's FP32 mu about the midpoint line of sight (Sec. 2.1),
 // as eps(r) = a / r + b for a pair at separation r.  The kernel forms
@@ -459,6 +585,16 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
       if (kind == KSIGPI) P1.near_scale = f32_up((double)P0.near_at / (double)P1.near_at);
       out.ax[0] = P0;
       out.ax[1] = two_d ? P1 : AxisPlan();
+      out.lut.clear();
+      out.band.assign(2, 0.0f);
+      out.dirty_frac[0] = out.dirty_frac[1] = 0;
+      return "";
+    }
+    // log-spaced monopole or chord edges: arithmetic on log2 of the square
+    AxisPlan PL;
+    if ((kind == KMONO || kind == KTHETA) && make_logarith(e0, n0, A0.err.sq, PL)) {
+      out.ax[0] = PL;
+      out.ax[1] = AxisPlan();
       out.lut.clear();
       out.band.assign(2, 0.0f);
       out.dirty_frac[0] = out.dirty_frac[1] = 0;

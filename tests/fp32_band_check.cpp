@@ -57,6 +57,21 @@ static float rsqrt_dev(float x) {
   return (float)(r * f);
 }
 
+// the hardware log2 (lg2.approx): any value within 2^-22 + 2^-23 |log2 x|
+// of log2(x) -- half the bound the planner assumes; tests/test_gpu_approx.py
+// finds the hardware within 0.49 of the planner's bound over every FP32
+// input in [2^-60, 2^70) (as the reciprocal square root is replayed at its
+// documented bound, not at the planner's)
+static float lg2_dev(float x) {
+  const double r = std::log2((double)x),
+               e = std::ldexp(1.0, -22) + std::ldexp(1.0, -23) * std::fabs(r);
+  double f;
+  if (g_mode == 1) f = -e;
+  else if (g_mode == 2) f = e;
+  else f = e * (2.0 * std::uniform_real_distribution<double>(0, 1)(g_rng) - 1.0);
+  return (float)(r + f);
+}
+
 struct Slot { int slot; float score; };
 
 // ---- table binning
@@ -191,6 +206,18 @@ static Slot mono_fp32(const AxisPlan &a, const float *q, const float *n) {
   return {(int)(bits(tm) - kMagicBits) + 1, std::fabs(h)};
 }
 
+// log-spaced edges: t = A log2(max(v, vlo)) + (D v + B) v + C
+static Slot mono_log_fp32(const AxisPlan &a, const float *q, const float *n) {
+  const float dx = fadd(q[0], n[0]), dy = fadd(q[1], n[1]), dz = fadd(q[2], n[2]);
+  const float v = std::fmax(ffma(dz, dz, ffma(dy, dy, fmul(dx, dx))), a.vlo);
+  const float lg = lg2_dev(v), rr = rsqrt_dev(v);
+  const float pv = ffma(v, ffma(v, a.ld, a.lb), a.cst);
+  const float t = std::fmin(ffma(lg, a.inv, pv), a.thi);
+  const float tm = fadd(t, kMagic), fl = fadd(tm, -kMagic);
+  const float h = ffma(fl, -1.0f, t);
+  return {(int)(bits(tm) - kMagicBits) + 1, ffma(rr, a.thr_a, std::fabs(h))};
+}
+
 static Slot sigpi_fp32(const AxisPlan &a0, const AxisPlan &a1, int slots1, const float *q,
                        const float *n) {
   const float dx = fadd(q[0], n[0]), dy = fadd(q[1], n[1]), dz = fadd(q[2], n[2]);
@@ -322,10 +349,21 @@ static bool plan_ok(const std::string &m, const Plan &P, bool arith) {
   std::printf("  plan: %s (arithmetic binning %d, wanted %d)\n", m.c_str(), got, arith);
   return false;
 }
+// binning path of a monopole / chord scenario: uniform edges by arithmetic,
+// log-spaced edges by arithmetic on log2, or the tables
+constexpr int kWantTable = -1;
+static bool mode_ok(const std::string &m, const Plan &P, int want) {
+  const int got = P.ax[0].mode;
+  const bool ok = want == kWantTable ? (got == kLutLinear || got == kLutLog) : got == want;
+  if (m.empty() && ok) return true;
+  std::printf("  plan: %s (mode %d, wanted %d)\n", m.c_str(), got, want);
+  return false;
+}
 
 // edges e (uniform from 0: the arithmetic path; otherwise the table path)
 static Tally run_mono(const std::vector<double> &e, double L, double xm_spread, bool chord,
-                      bool arith, std::mt19937_64 &g) {
+                      int want, std::mt19937_64 &g) {
+  const bool arith = want != kWantTable, logm = want == kArithLog;
   const int n = (int)e.size() - 1;
   const std::vector<double> E = squares(e);
   const double fo[3] = {chord ? 0.0 : (L > 0 ? 0.5 * L : 1234.5),
@@ -334,8 +372,8 @@ static Tally run_mono(const std::vector<double> &e, double L, double xm_spread, 
   const double xm = chord ? 1.0 : (L > 0 ? 0.5 * L : xm_spread + e[n]);
   Plan P;
   const std::string m = plan_build(chord ? KTHETA : KMONO, e.data(), n, nullptr, 1,
-                                   eparams(xm, L, e[n], 0, 0), 8192, 12288, true, P);
-  if (!plan_ok(m, P, arith)) return Tally{0, 0, 1};
+                                   eparams(xm, L, e[n], 0, 0), 8192, 12288, arith, P);
+  if (!mode_ok(m, P, want)) return Tally{0, 0, 1};
   if (arith) shrink(P.ax[0]);
   else shrink_table(P, 0, E);
   std::uniform_real_distribution<double> U(-1, 1);
@@ -372,9 +410,12 @@ static Tally run_mono(const std::vector<double> &e, double L, double xm_spread, 
         for (int c = 0; c < 3; c++) dd[c] = wrap(b[c] - a[c], L);
         const int cb = bin64(E, (dd[0] * dd[0] + dd[1] * dd[1]) + dd[2] * dd[2]);
         const int canon = cb < 0 ? -1 : cb + 1;
-        const Slot r = arith ? mono_fp32(P.ax[0], q, nn) : mono_table(P, q, nn);
+        const Slot r = logm ? mono_log_fp32(P.ax[0], q, nn)
+                            : (arith ? mono_fp32(P.ax[0], q, nn) : mono_table(P, q, nn));
         const int fp32 = (r.slot >= 1 && r.slot <= n) ? r.slot : -1;
-        t.add(arith ? r.score >= P.ax[0].near_at : r.score > 0.0f, fp32, canon);
+        t.add(logm ? r.score >= P.ax[0].near_c
+                   : (arith ? r.score >= P.ax[0].near_at : r.score > 0.0f),
+              fp32, canon);
       }
   return t;
 }
@@ -520,10 +561,13 @@ static std::vector<double> lattice_pts(std::mt19937_64 &g, int n, const double l
   return p;
 }
 
+// logm: monopole edges 1, 2, 4, ..., 32 (log-spaced: arithmetic on log2)
 static Tally run_lattice_mono_sigpi(bool sigpi, bool arith, bool periodic, std::mt19937_64 &g,
-                                    long &ties) {
-  const std::vector<double> e0 = sigpi ? (arith ? uniform(1.0, 9) : std::vector<double>{0, 1, 2, 3, 4, 6, 9})
-                                       : (arith ? uniform(1.0, 13) : std::vector<double>{0, 1, 2, 3, 5, 8, 13});
+                                    long &ties, bool logm = false) {
+  const std::vector<double> e0 =
+      sigpi ? (arith ? uniform(1.0, 9) : std::vector<double>{0, 1, 2, 3, 4, 6, 9})
+            : (logm ? std::vector<double>{1, 2, 4, 8, 16}
+                    : (arith ? uniform(1.0, 13) : std::vector<double>{0, 1, 2, 3, 5, 8, 13}));
   const std::vector<double> e1 = arith ? uniform(1.0, 7) : std::vector<double>{0, 1, 3, 5, 7};
   const int n0 = (int)e0.size() - 1, n1 = sigpi ? (int)e1.size() - 1 : 1;
   const std::vector<double> E0 = squares(e0), E1 = squares(e1);
@@ -538,8 +582,8 @@ static Tally run_lattice_mono_sigpi(bool sigpi, bool arith, bool periodic, std::
                                            12288, true, P)
                               : plan_build(KMONO, e0.data(), n0, nullptr, 1,
                                            eparams(xm, L, e0[n0], 0, 0), 8192, 12288, true, P);
-  if (!plan_ok(m, P, arith)) return Tally{0, 0, 1};
-  if (arith) {
+  if (logm ? !mode_ok(m, P, kArithLog) : !plan_ok(m, P, arith)) return Tally{0, 0, 1};
+  if (arith || logm) {
     shrink(P.ax[0]);
     if (sigpi) {
       shrink(P.ax[1]);
@@ -549,7 +593,8 @@ static Tally run_lattice_mono_sigpi(bool sigpi, bool arith, bool periodic, std::
     shrink_table(P, 0, E0);
     if (sigpi) shrink_table(P, 1, E1);
   }
-  const std::vector<double> x = lattice_pts(g, 320, lo, hi);
+  // (exact ties at 1, 4, 16, 64, 256 are rarer than at every integer: more points)
+  const std::vector<double> x = lattice_pts(g, logm ? 900 : 320, lo, hi);
   const int n = (int)x.size() / 3;
   Tally t;
   for (int i = 0; i < n; i++)
@@ -565,9 +610,12 @@ static Tally run_lattice_mono_sigpi(bool sigpi, bool arith, bool periodic, std::
         for (int k = 1; k <= n0; k++) ties += d2 == E0[k];
         const int cb = bin64(E0, d2);
         canon = cb < 0 ? -1 : cb + 1;
-        r = arith ? mono_fp32(P.ax[0], q, nn) : mono_table(P, q, nn);
+        r = logm ? mono_log_fp32(P.ax[0], q, nn)
+                 : (arith ? mono_fp32(P.ax[0], q, nn) : mono_table(P, q, nn));
         const int fp32 = (r.slot >= 1 && r.slot <= n0) ? r.slot : -1;
-        t.add(arith ? r.score >= P.ax[0].near_at : r.score > 0.0f, fp32, canon);
+        t.add(logm ? r.score >= P.ax[0].near_c
+                   : (arith ? r.score >= P.ax[0].near_at : r.score > 0.0f),
+              fp32, canon);
       } else {
         const double sg2 = dd[0] * dd[0] + dd[1] * dd[1], pi2 = dd[2] * dd[2];
         for (int k = 1; k <= n0; k++) ties += sg2 == E0[k];
@@ -680,24 +728,31 @@ int main(int argc, char **argv) {
   for (g_mode = 0; g_mode < 3; g_mode++) {
     char nm[64];
     std::snprintf(nm, sizeof nm, "mono_periodic_r%d", g_mode);
-    report(nm, run_mono(uniform(5.0, 30), 2000.0, 0, false, true, g));
+    report(nm, run_mono(uniform(5.0, 30), 2000.0, 0, false, kArith, g));
     std::snprintf(nm, sizeof nm, "mono_periodic_small_r%d", g_mode);
-    report(nm, run_mono(uniform(5.0, 40), 1000.0, 0, false, true, g));
+    report(nm, run_mono(uniform(5.0, 40), 1000.0, 0, false, kArith, g));
     std::snprintf(nm, sizeof nm, "mono_open_r%d", g_mode);
-    report(nm, run_mono(uniform(2.5, 40), 0.0, 1400.0, false, true, g));
+    report(nm, run_mono(uniform(2.5, 40), 0.0, 1400.0, false, kArith, g));
     std::snprintf(nm, sizeof nm, "chord_r%d", g_mode);
-    report(nm, run_mono(uniform(0.0027, 64), 0.0, 0, true, true, g));
+    report(nm, run_mono(uniform(0.0027, 64), 0.0, 0, true, kArith, g));
     std::snprintf(nm, sizeof nm, "sigpi_periodic_r%d", g_mode);
     report(nm, run_sigpi(uniform(3.0, 50), uniform(3.0, 50), 1500.0, true, g));
     std::snprintf(nm, sizeof nm, "rmu_lightcone_r%d", g_mode);
     report(nm, run_rmu(fo, 1250.0, 1000.0, 2500.0, 2500.0, uniform(5.0, 40), 40, rs_u, true, g));
     // the table path (edges not uniform from 0)
     std::snprintf(nm, sizeof nm, "table_mono_periodic_r%d", g_mode);
-    report(nm, run_mono(logspace(0.1, 150.0, 20), 2000.0, 0, false, false, g));
+    report(nm, run_mono(logspace(0.1, 150.0, 20), 2000.0, 0, false, kWantTable, g));
     std::snprintf(nm, sizeof nm, "table_mono_open_r%d", g_mode);
-    report(nm, run_mono(logspace(1.0, 200.0, 16), 0.0, 1400.0, false, false, g));
+    report(nm, run_mono(logspace(1.0, 200.0, 16), 0.0, 1400.0, false, kWantTable, g));
     std::snprintf(nm, sizeof nm, "table_chord_r%d", g_mode);
-    report(nm, run_mono(chords, 0.0, 0, true, false, g));
+    report(nm, run_mono(chords, 0.0, 0, true, kWantTable, g));
+    // log-spaced edges by arithmetic on log2 of the square
+    std::snprintf(nm, sizeof nm, "log_mono_periodic_r%d", g_mode);
+    report(nm, run_mono(logspace(0.1, 150.0, 20), 2000.0, 0, false, kArithLog, g));
+    std::snprintf(nm, sizeof nm, "log_mono_open_r%d", g_mode);
+    report(nm, run_mono(logspace(1.0, 200.0, 16), 0.0, 1400.0, false, kArithLog, g));
+    std::snprintf(nm, sizeof nm, "log_chord_r%d", g_mode);
+    report(nm, run_mono(chords, 0.0, 0, true, kArithLog, g));
     std::snprintf(nm, sizeof nm, "table_sigpi_periodic_r%d", g_mode);
     report(nm, run_sigpi(logspace(0.5, 60.0, 15), uniform(2.0, 30), 1500.0, false, g));
     std::snprintf(nm, sizeof nm, "table_rmu_lightcone_r%d", g_mode);
@@ -713,13 +768,16 @@ int main(int argc, char **argv) {
                     {"lattice_sigpi_arith_periodic", 1, true, true},
                     {"lattice_sigpi_table_periodic", 1, false, true},
                     {"lattice_rmu_arith", 2, true, false},
-                    {"lattice_rmu_table", 2, false, false}};
+                    {"lattice_rmu_table", 2, false, false},
+                    {"lattice_mono_log_periodic", 3, false, true},
+                    {"lattice_mono_log_open", 3, false, false}};
     for (const L &l : ls) {
       long ties = 0;
       char nm[80];
       std::snprintf(nm, sizeof nm, "%s_r%d", l.name, g_mode);
       report(nm, l.kind == 2 ? run_lattice_rmu(l.arith, g, ties)
-                             : run_lattice_mono_sigpi(l.kind == 1, l.arith, l.periodic, g, ties));
+                             : run_lattice_mono_sigpi(l.kind == 1, l.arith, l.periodic, g, ties,
+                                                      l.kind == 3));
       std::printf("%s_ties %ld\n", nm, ties);
     }
   }

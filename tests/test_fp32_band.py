@@ -62,16 +62,18 @@ def _run(exe, factor):
 @pytest.mark.parametrize("factor", [1.0, 0.5, 0.3])
 def test_no_unflagged_pair_is_misbinned(exe, factor):
     rc, rows, out, ties = _run(exe, factor)
-    # 11 edge scenarios (6 arithmetic, 5 table) and 8 integer lattices, each
-    # with 3 ways of rounding the rsqrt
-    assert len(rows) == 57, out
+    # 14 edge scenarios (6 arithmetic, 5 table, 3 log-spaced) and 10 integer
+    # lattices, each with 3 ways of rounding the rsqrt (and the log2)
+    assert len(rows) == 72, out
     assert sum(n.startswith("table_") for n in rows) == 15, out
+    assert sum(n.startswith("log_") or "_log_" in n for n in rows) == 15, out
     lattices = [n for n in rows if n.startswith("lattice_")]
-    assert len(lattices) == 24 and set(ties) == set(lattices), out
+    assert len(lattices) == 30 and set(ties) == set(lattices), out
     for name, (cases, flagged, bad) in rows.items():
         assert cases > 1000 and bad == 0, (name, out)
     # the lattices hold exact FP64 ties, every one of them flagged or binned right
-    assert all(ties[n] >= 100 for n in lattices), out
+    # (the log-spaced edges 1, 2, 4, 8, 16 have fewer exact ties)
+    assert all(ties[n] >= (60 if "_log_" in n else 100) for n in lattices), out
     assert rc == 0, out
 
 
@@ -80,7 +82,7 @@ def test_collapsed_bands_are_caught(exe):
     # pairs (a lattice whose FP32 values are exact can keep its ties flagged
     # even then, so the lattices are counted together)
     rc, rows, out, _ = _run(exe, 0.0)
-    assert len(rows) == 57 and rc == 1, out
+    assert len(rows) == 72 and rc == 1, out
     for name, (cases, flagged, bad) in rows.items():
         if not name.startswith("lattice_"):
             assert bad > 0, (name, out)
