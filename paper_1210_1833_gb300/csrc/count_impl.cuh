@@ -70,7 +70,7 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float ph, float pl)
 // draining): the double-float stage, then the FP64 formula for the pairs
 // it leaves open.  Every lane must call it.
 template <int KIND, int ACC>
-__device__ __noinline__ void process_queue(const KParams &p, const PairDev &pd, const WarpSmem &w,
+__device__ __forceinline__ void process_queue(const KParams &p, const PairDev &pd, const WarpSmem &w,
                                            int lane, bool drain) {
   __syncwarp();
   int n = *w.qcnt;
@@ -112,7 +112,7 @@ __device__ __noinline__ void process_queue(const KParams &p, const PairDev &pd, 
 }
 
 // add the warp's histogram to output `out` in HBM and clear it
-static __device__ __noinline__ void flush_hist(const KParams &p, const WarpSmem &w, int out, int lane) {
+static __device__ __forceinline__ void flush_hist(const KParams &p, const WarpSmem &w, int out, int lane) {
   __syncwarp();
   const int nb = p.n0 * p.n1;
   for (int b = lane; b < nb; b += 32) {
@@ -128,7 +128,7 @@ static __device__ __noinline__ void flush_hist(const KParams &p, const WarpSmem 
 }
 
 // add the warp's float-float weighted columns to output `out` and clear them
-static __device__ __noinline__ void flush_wsum(const KParams &p, const WarpSmem &w, int out,
+static __device__ __forceinline__ void flush_wsum(const KParams &p, const WarpSmem &w, int out,
                                                int lane) {
   __syncwarp();
   const int nb = p.n0 * p.n1;
