@@ -212,6 +212,107 @@ __global__ void __launch_bounds__(128, 6) k_lagcorr(const float *__restrict__ de
   }
 }
 
+
+// k_lagcorr_w: the lag sums again, one warp per work unit -- a window of
+// NCH x XL consecutive lags of one (dy, dz) column -- and z slab, for grids of
+// n = 32 XL points per row.  No shared memory and no block barriers: each
+// lane loads its XL-point block of the row pair's A row and of its B row at
+// the window's offset (float4 loads from the L2-resident grid; the warps of
+// a block take neighbouring units over the same rows, so the A rows are
+// L1 hits for all but one of them), and takes the rest of the B window from
+// the next lanes by shuffle, one block per chunk of XL lags:
+//   C[w + c XL + j] += sum_i A[x_i] B[x_i + w + c XL + j],  i, j < XL,
+// over the blocks of lanes l + c and l + c + 1.  FP32 partials over 32 rows
+// are summed across the warp and folded into float-float per lag.
+template <int XL, int NCH>
+__global__ void __launch_bounds__(128) k_lagcorr_w(const float *__restrict__ delta, int n,
+                                                   const int4 *__restrict__ units, int nunits,
+                                                   const int4 *__restrict__ cols, int zslab,
+                                                   double *__restrict__ out, int out_stride) {
+  constexpr int K = XL * NCH;        // lags of a window
+  constexpr int KF = (K + 31) / 32;  // float-float lag sums per lane
+  constexpr int kFold = 32;          // rows per FP32 partial
+  const int lane = threadIdx.x & 31;
+  const int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (u >= nunits) return;  // whole warps: no barrier follows
+  const int4 un = units[u];  // (column, first lag w, chunks, 0)
+  const int4 col = cols[un.x];
+  const int dy = col.x, dz = col.y, w0 = un.y, nch = un.z;
+  const int z0 = blockIdx.y * zslab, z1 = min(n, z0 + zslab);
+  const int xa = XL * lane;
+  // this lane's block of the B row starts at x = xa + w0 (w0 a multiple of 4)
+  int xb = xa + w0;
+  xb = xb < 0 ? xb + n : (xb >= n ? xb - n : xb);
+  float acc[K], fh[KF], fl[KF];
+#pragma unroll
+  for (int k = 0; k < K; k++) acc[k] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < KF; k++) fh[k] = fl[k] = 0.0f;
+  auto fold = [&]() {
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      float v = acc[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == (k & 31)) ff_acc(fh[k >> 5], fl[k >> 5], v);
+      acc[k] = 0.0f;
+    }
+  };
+  int since = 0;
+  for (int z = z0; z < z1; z++) {
+    const int zb = wrapi(z + dz, n);
+    for (int y = 0; y < n; y++) {
+      const int yb = wrapi(y + dy, n);
+      const float *A = delta + ((long long)z * n + y) * n;
+      const float *B = delta + ((long long)zb * n + yb) * n;
+      float a[XL], own[XL], cur[XL], nxt[XL];
+#pragma unroll
+      for (int q = 0; q < XL / 4; q++) {
+        *(float4 *)&a[4 * q] = __ldg((const float4 *)(A + xa + 4 * q));
+        int x = xb + 4 * q;
+        x = x >= n ? x - n : x;
+        *(float4 *)&own[4 * q] = __ldg((const float4 *)(B + x));
+      }
+#pragma unroll
+      for (int t = 0; t < XL; t++) {
+        cur[t] = own[t];
+        nxt[t] = __shfl_sync(0xffffffffu, own[t], (lane + 1) & 31);
+      }
+#pragma unroll
+      for (int c = 0; c < NCH; c++) {
+        if (c >= nch) break;
+#pragma unroll
+        for (int i = 0; i < XL; i++)
+#pragma unroll
+          for (int j = 0; j < XL; j++) {
+            const float b = (i + j < XL) ? cur[i + j] : nxt[i + j - XL];
+            acc[c * XL + j] = fmaf(a[i], b, acc[c * XL + j]);
+          }
+        if (c + 1 < NCH && c + 1 < nch) {
+#pragma unroll
+          for (int t = 0; t < XL; t++) {
+            cur[t] = nxt[t];
+            nxt[t] = __shfl_sync(0xffffffffu, own[t], (lane + c + 2) & 31);
+          }
+        }
+      }
+      if (++since == kFold) {
+        fold();
+        since = 0;
+      }
+    }
+  }
+  fold();
+  const int dxmin = col.z, dxmax = col.w;
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    const int dx = w0 + k;
+    if (lane == (k & 31) && k < nch * XL && dx >= dxmin && dx <= dxmax)
+      atomicAdd(&out[(size_t)un.x * out_stride + (dx - dxmin)],
+                (double)fh[k >> 5] + (double)fl[k >> 5]);
+  }
+}
+
 }  // namespace
 
 }  // namespace cute
@@ -257,6 +358,23 @@ extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, co
     }
   int maxw = 1;
   for (const int4 &c : cols) maxw = std::max(maxw, c.w - c.z + 1);
+  // rows of 128, 256 or 384 points: k_lagcorr_w, one warp per window
+  // of K = XL NCH lags of a column (XL = n / 32 points per lane); the
+  // windows start at the column's first lag rounded down to a multiple of 4
+  const int XL = ngrid / 32;
+  const bool warp_kernel = (XL == 4 || XL == 8 || XL == 12);
+  const int NCH = XL == 4 ? 10 : (XL == 8 ? 5 : 3);
+  std::vector<int4> units;
+  if (warp_kernel) {
+    for (size_t c = 0; c < cols.size(); c++) {
+      const int lo = cols[c].z, hi = cols[c].w;
+      const int w0 = lo >= 0 ? lo & ~3 : -((-lo + 3) & ~3);
+      for (int w = w0; w <= hi; w += XL * NCH) {
+        const int nch = std::min(NCH, (hi - w + XL) / XL);  // chunks reaching hi
+        units.push_back(make_int4((int)c, w, nch, 0));
+      }
+    }
+  }
   const long long m = (long long)ngrid * ngrid * ngrid;
   const bool dev = [&] {
     cudaPointerAttributes at;
@@ -268,7 +386,7 @@ extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, co
   const size_t xb = (size_t)n_obj * 3 * sizeof(double), wb = w ? (size_t)n_obj * sizeof(float) : 0;
   const size_t ob = cols.size() * (size_t)maxw * sizeof(double);
   const size_t need = 256 + m * sizeof(double) + m * sizeof(float) + cols.size() * sizeof(int4) +
-                      ob + (dev ? 0 : xb + wb) + 1024;
+                      ob + (dev ? 0 : xb + wb) + units.size() * sizeof(int4) + 2048;
   char *buf = nullptr;
   if (cudaMalloc(&buf, need) != cudaSuccess) return fail(CUTE_E_OOM, "cudaMalloc");
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
@@ -281,8 +399,9 @@ extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, co
   const float *d_w = w;
   cudaStream_t st = ctx->stream;
   cudaError_t e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+  int4 *d_units = (int4 *)((char *)d_out + al(ob));
   if (!dev) {
-    char *p = (char *)d_out + al(ob);
+    char *p = (char *)d_units + al(units.size() * sizeof(int4));
     d_xyz = (const double *)p;
     d_w = w ? (const float *)(p + al(xb)) : nullptr;
     if (e == cudaSuccess) e = cudaMemcpyAsync((void *)d_xyz, xyz, xb, cudaMemcpyHostToDevice, st);
@@ -301,6 +420,8 @@ extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, co
   if (e == cudaSuccess) e = cudaMemsetAsync(d_out, 0, ob, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_cols, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !units.empty())
+    e = cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
   // total weight for the mean density
   double wsum = (double)n_obj;
   if (w) {
@@ -323,7 +444,23 @@ extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, co
     k_delta<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(d_rho, m, (double)m / wsum, d_delta);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && warp_kernel) {
+    // four warps (units) per block; z slabs of n / 16 rows
+    const int zslab = std::max(1, ngrid / 16);
+    dim3 grid((unsigned)((units.size() + 3) / 4), (unsigned)((ngrid + zslab - 1) / zslab));
+    ctx->stats = cute_stats{};
+    cudaMemsetAsync(ctx->d_ticket, 0, kCounterWords * sizeof(unsigned long long), st);
+    ctx->stats.launches = 1;
+    ctx->stats.blocks = (int)(grid.x * grid.y);
+    ctx->stats.warps_per_block = 4;
+    if (ctx->timing) cudaEventRecord(ctx->ev0, st);
+    const int nu = (int)units.size();
+    if (XL == 4) k_lagcorr_w<4, 10><<<grid, 128, 0, st>>>(d_delta, ngrid, d_units, nu, d_cols, zslab, d_out, maxw);
+    else if (XL == 8) k_lagcorr_w<8, 5><<<grid, 128, 0, st>>>(d_delta, ngrid, d_units, nu, d_cols, zslab, d_out, maxw);
+    else k_lagcorr_w<12, 3><<<grid, 128, 0, st>>>(d_delta, ngrid, d_units, nu, d_cols, zslab, d_out, maxw);
+    if (ctx->timing) cudaEventRecord(ctx->ev1, st);
+    e = cudaGetLastError();
+  } else if (e == cudaSuccess) {
     const int zslab = std::max(1, ngrid / 8);
     // 16 lags per warp, as many warps as the widest column's window needs
     // (it starts at dxmin rounded down to a multiple of 4); warps past a

@@ -56,3 +56,27 @@ def test_density_grid_device_inputs_and_errors(ctx):
     bad[3, 1] = L                                            # outside [0, L)
     with pytest.raises(cute.CuteError):
         ctx.density_grid_xi(bad, L, 32, edges)
+
+
+@pytest.mark.parametrize("ngrid", [128, 256, 384])
+def test_density_grid_warp_kernel_matches_oracle(ctx, ngrid):
+    """Rows of 128, 256 and 384 points take the warp-per-lag-window kernel
+    (the bench's 256^3 grid among them); lags reach 45 grid steps, so the
+    longest lag columns span three windows of the kernel.  The oracle's lag
+    sums come from the FFT form (lag_xi_fft, pinned to the direct sums)."""
+    rng = np.random.default_rng(120 + ngrid)
+    L = 400.0
+    x = np.concatenate([synthetic.uniform_box(40000, L, rng),
+                        synthetic.blobs_box(300, 100, L, 6.0, rng)])
+    w = rng.uniform(0.5, 2.0, len(x)).astype(np.float32)
+    a = L / ngrid
+    edges = np.linspace(0.0, 45.5 * a, 12)
+    xi, lags = ctx.density_grid_xi(x, L, ngrid, edges, weights=w)
+    rho = oracle.tsc_density(x, L, ngrid, w)
+    delta = rho / rho.mean() - 1.0
+    ref, ref_lags = oracle.lag_xi_fft(delta, L, edges)
+    np.testing.assert_array_equal(lags, ref_lags)
+    scale = float(np.mean(delta * delta))
+    m = ~np.isnan(ref)
+    assert np.array_equal(np.isnan(xi), np.isnan(ref))
+    assert np.all(np.abs(xi[m] - ref[m]) <= 1e-5 * scale)

@@ -597,3 +597,28 @@ def test_lag_xi_of_a_plane_wave():
                     ref_c[b] += 1
     np.testing.assert_allclose(lags, ref_c)
     np.testing.assert_allclose(xi, ref_s / ref_c, rtol=1e-12, atol=1e-14)
+
+
+def test_lag_xi_fft_equals_the_direct_lag_sums():
+    """The FFT form of the lag sums (correlation theorem) against the direct
+    products of shifted grids, on a clustered field, on the plane wave's
+    closed form, and with lags reaching past half the edge range."""
+    rng = np.random.default_rng(31)
+    n, L = 24, 48.0
+    x = np.concatenate([rng.uniform(0, L, (3000, 3)), (rng.normal(L / 2, 3.0, (600, 3)) % L)])
+    rho = oracle.tsc_density(x, L, n)
+    delta = rho / rho.mean() - 1.0
+    edges = np.array([0.0, 2.5, 5.0, 9.0, 14.0, 20.0])
+    xi_d, c_d = oracle.lag_xi(delta, L, edges)
+    xi_f, c_f = oracle.lag_xi_fft(delta, L, edges)
+    np.testing.assert_array_equal(c_f, c_d)
+    np.testing.assert_allclose(xi_f, xi_d, rtol=1e-11, atol=1e-13 * float(np.mean(delta ** 2)))
+    # the plane wave: <delta(x) delta(x + d)> = A^2/2 cos(2 pi k.d / n)
+    n, L, A = 16, 32.0, 0.7
+    k = np.array([1, 2, 3])
+    idx = np.indices((n, n, n))
+    wave = A * np.cos(2 * np.pi * (k[0] * idx[2] + k[1] * idx[1] + k[2] * idx[0]) / n)
+    edges = np.array([0.0, 3.0, 6.0, 9.5])
+    xi_w, _ = oracle.lag_xi_fft(wave, L, edges)
+    xi_ref, _ = oracle.lag_xi(wave, L, edges)
+    np.testing.assert_allclose(xi_w, xi_ref, rtol=1e-12, atol=1e-14)
