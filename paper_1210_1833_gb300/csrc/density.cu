@@ -213,44 +213,30 @@ __global__ void __launch_bounds__(128, 6) k_lagcorr(const float *__restrict__ de
 }
 
 
-// k_lagcorr_w: the lag sums again, one warp per work unit -- a window of
-// NCH x XL consecutive lags of one (dy, dz) column -- and z slab, for grids of
-// n = 32 XL points per row.  No shared memory and no block barriers: each
-// lane loads its XL-point block of the row pair's A row and of its B row at
-// the window's offset (float4 loads from the L2-resident grid; the warps of
-// a block take neighbouring units over the same rows, so the A rows are
-// L1 hits for all but one of them), and takes the rest of the B window from
-// the next lanes by shuffle, one block per chunk of XL lags:
+// k_lagcorr_w: the lag sums again, one warp per work unit -- a window of at
+// most NCH x XL consecutive lags of one (dy, dz) column -- and z slab, for
+// grids of n = 32 XL points per row.  No shared memory and no block
+// barriers: each lane loads its XL-point block of the row pair's A row and
+// of its B row at the window's offset (float4 loads from the L2-resident
+// grid; the warps of a block take neighbouring units over the same rows, so
+// the A rows are L1 hits for all but one of them), and takes the rest of the
+// B window from the next lanes by shuffle, one block per chunk of XL lags:
 //   C[w + c XL + j] += sum_i A[x_i] B[x_i + w + c XL + j],  i, j < XL,
-// over the blocks of lanes l + c and l + c + 1.  FP32 partials over 32 rows
-// are summed across the warp and folded into float-float per lag.
-template <int XL, int NCH>
-__global__ void __launch_bounds__(128) k_lagcorr_w(const float *__restrict__ delta, int n,
-                                                   const int4 *__restrict__ units, int nunits,
-                                                   const int4 *__restrict__ cols, int zslab,
-                                                   double *__restrict__ out, int out_stride) {
-  constexpr int K = XL * NCH;        // lags of a window
-  constexpr int KF = (K + 31) / 32;  // float-float lag sums per lane
-  constexpr int kFold = 32;          // rows per FP32 partial
-  const int lane = threadIdx.x & 31;
-  const int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (u >= nunits) return;  // whole warps: no barrier follows
-  const int4 un = units[u];  // (column, first lag w, chunks, 0)
-  const int4 col = cols[un.x];
-  const int dy = col.x, dz = col.y, w0 = un.y, nch = un.z;
-  const int z0 = blockIdx.y * zslab, z1 = min(n, z0 + zslab);
-  const int xa = XL * lane;
-  // this lane's block of the B row starts at x = xa + w0 (w0 a multiple of 4)
-  int xb = xa + w0;
-  xb = xb < 0 ? xb + n : (xb >= n ? xb - n : xb);
-  float acc[K], fh[KF], fl[KF];
+// over the blocks of lanes l + c and l + c + 1.  The row loop is compiled
+// per number of chunks NC (fixed for a warp), so every chunk, shuffle and
+// register is static.  FP32 partials over 32 rows are summed across the warp
+// and folded into float-float per lag.
+template <int XL, int K, int NC>
+__device__ __forceinline__ void lag_rows(const float *__restrict__ delta, int n, int dy, int dz,
+                                         int z0, int z1, int xa, int xb, int lane, float (&fh)[(K + 31) / 32],
+                                         float (&fl)[(K + 31) / 32]) {
+  constexpr int kFold = 32;  // rows per FP32 partial
+  float acc[NC * XL];
 #pragma unroll
-  for (int k = 0; k < K; k++) acc[k] = 0.0f;
-#pragma unroll
-  for (int k = 0; k < KF; k++) fh[k] = fl[k] = 0.0f;
+  for (int k = 0; k < NC * XL; k++) acc[k] = 0.0f;
   auto fold = [&]() {
 #pragma unroll
-    for (int k = 0; k < K; k++) {
+    for (int k = 0; k < NC * XL; k++) {
       float v = acc[k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -261,34 +247,31 @@ __global__ void __launch_bounds__(128) k_lagcorr_w(const float *__restrict__ del
   int since = 0;
   for (int z = z0; z < z1; z++) {
     const int zb = wrapi(z + dz, n);
-    for (int y = 0; y < n; y++) {
-      const int yb = wrapi(y + dy, n);
-      const float *A = delta + ((long long)z * n + y) * n;
-      const float *B = delta + ((long long)zb * n + yb) * n;
-      float a[XL], own[XL], cur[XL], nxt[XL];
+    const float *A = delta + (long long)z * n * n + xa;
+    for (int y = 0; y < n; y++, A += n) {
+      const float *B = delta + ((long long)zb * n + wrapi(y + dy, n)) * n;
+      float a[XL], own[XL];
 #pragma unroll
       for (int q = 0; q < XL / 4; q++) {
-        *(float4 *)&a[4 * q] = __ldg((const float4 *)(A + xa + 4 * q));
-        int x = xb + 4 * q;
-        x = x >= n ? x - n : x;
-        *(float4 *)&own[4 * q] = __ldg((const float4 *)(B + x));
+        *(float4 *)&a[4 * q] = __ldg((const float4 *)(A + 4 * q));
+        const int x = xb + 4 * q;
+        *(float4 *)&own[4 * q] = __ldg((const float4 *)(B + (x >= n ? x - n : x)));
       }
+      // the window of chunk c: blocks of lanes l + c (cur) and l + c + 1 (nxt)
+      float cur[XL], nxt[XL];
 #pragma unroll
       for (int t = 0; t < XL; t++) {
         cur[t] = own[t];
         nxt[t] = __shfl_sync(0xffffffffu, own[t], (lane + 1) & 31);
       }
 #pragma unroll
-      for (int c = 0; c < NCH; c++) {
-        if (c >= nch) break;
+      for (int c = 0; c < NC; c++) {
 #pragma unroll
         for (int i = 0; i < XL; i++)
 #pragma unroll
-          for (int j = 0; j < XL; j++) {
-            const float b = (i + j < XL) ? cur[i + j] : nxt[i + j - XL];
-            acc[c * XL + j] = fmaf(a[i], b, acc[c * XL + j]);
-          }
-        if (c + 1 < NCH && c + 1 < nch) {
+          for (int j = 0; j < XL; j++)
+            acc[c * XL + j] = fmaf(a[i], (i + j < XL) ? cur[i + j] : nxt[i + j - XL], acc[c * XL + j]);
+        if (c + 1 < NC) {
 #pragma unroll
           for (int t = 0; t < XL; t++) {
             cur[t] = nxt[t];
@@ -303,6 +286,39 @@ __global__ void __launch_bounds__(128) k_lagcorr_w(const float *__restrict__ del
     }
   }
   fold();
+}
+
+template <int XL, int NCH>
+__global__ void __launch_bounds__(128) k_lagcorr_w(const float *__restrict__ delta, int n,
+                                                   const int4 *__restrict__ units, int nunits,
+                                                   const int4 *__restrict__ cols, int zslab,
+                                                   double *__restrict__ out, int out_stride) {
+  constexpr int K = XL * NCH;        // lags of a window
+  constexpr int KF = (K + 31) / 32;  // float-float lag sums per lane
+  const int lane = threadIdx.x & 31;
+  const int u = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (u >= nunits) return;  // whole warps: no barrier follows
+  const int4 un = units[u];  // (column, first lag w, chunks, 0)
+  const int4 col = cols[un.x];
+  const int w0 = un.y, nch = un.z;
+  const int z0 = blockIdx.x * zslab, z1 = min(n, z0 + zslab);
+  const int xa = XL * lane;
+  // this lane's block of the B row starts at x = xa + w0 (w0 a multiple of 4)
+  int xb = xa + w0;
+  xb = xb < 0 ? xb + n : (xb >= n ? xb - n : xb);
+  float fh[KF], fl[KF];
+#pragma unroll
+  for (int k = 0; k < KF; k++) fh[k] = fl[k] = 0.0f;
+  switch (nch) {
+#define LAG_CASE(c)                                                                           \
+  case c:                                                                                     \
+    if (c <= NCH) lag_rows<XL, K, (c <= NCH ? c : 1)>(delta, n, col.x, col.y, z0, z1, xa, xb, lane, fh, fl); \
+    break;
+    LAG_CASE(1) LAG_CASE(2) LAG_CASE(3) LAG_CASE(4) LAG_CASE(5)
+    LAG_CASE(6) LAG_CASE(7) LAG_CASE(8) LAG_CASE(9) LAG_CASE(10)
+#undef LAG_CASE
+    default: break;
+  }
   const int dxmin = col.z, dxmax = col.w;
 #pragma unroll
   for (int k = 0; k < K; k++) {
@@ -374,6 +390,10 @@ extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, co
         units.push_back(make_int4((int)c, w, nch, 0));
       }
     }
+    // longest windows first (blocks start in launch order: the short ones
+    // fill in behind them instead of trailing)
+    std::stable_sort(units.begin(), units.end(),
+                     [](const int4 &p, const int4 &q) { return p.z > q.z; });
   }
   const long long m = (long long)ngrid * ngrid * ngrid;
   const bool dev = [&] {
@@ -447,7 +467,8 @@ extern "C" cute_status cute_density_grid_xi(cute_ctx *ctx, const double *xyz, co
   if (e == cudaSuccess && warp_kernel) {
     // four warps (units) per block; z slabs of n / 16 rows
     const int zslab = std::max(1, ngrid / 16);
-    dim3 grid((unsigned)((units.size() + 3) / 4), (unsigned)((ngrid + zslab - 1) / zslab));
+    // grid x: z slabs, y: groups of four units (the same rows for the four)
+    dim3 grid((unsigned)((ngrid + zslab - 1) / zslab), (unsigned)((units.size() + 3) / 4));
     ctx->stats = cute_stats{};
     cudaMemsetAsync(ctx->d_ticket, 0, kCounterWords * sizeof(unsigned long long), st);
     ctx->stats.launches = 1;
