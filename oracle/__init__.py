@@ -406,7 +406,7 @@ def lag_xi_fft(delta, L, edges):
     nb = len(e2) - 1
     R = int(np.floor(edges[-1] / a))
     f = np.fft.rfftn(np.asarray(delta, dtype=np.float64))
-    C = np.fft.irfftn(f * np.conj(f), s=delta.shape)
+    C = np.fft.irfftn(f * np.conj(f), s=delta.shape, axes=(0, 1, 2))
     del f
     s, c = np.zeros(nb), np.zeros(nb)
     for dz in range(0, R + 1):

@@ -422,7 +422,7 @@ PairDev pair_dev(const DescInfo &di, int out) {
 }
 
 ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax) {
-  ErrorParams ep{0, 0, 0, 0};
+  ErrorParams ep{0, 0, 0, 0, 0};
   double rmin = 1e300;
   for (const DescInfo &di : dis) {
     const Geometry &g = *di.g;
@@ -438,6 +438,7 @@ ErrorParams error_params(const std::vector<DescInfo> &dis, double rmax) {
       e = kU32 * 2.0 * xm * 1.01 + 1e-12 * xm;
     }
     ep.eta0 = std::max(ep.eta0, e);
+    ep.xm = std::max(ep.xm, xm);
     rmin = std::min(rmin, g.rmin);
     ep.qd = std::max(ep.qd, g.qd);
     ep.q0 = std::max(ep.q0, g.q0);
@@ -467,7 +468,7 @@ cute_status get_plan(cute_ctx *ctx, const cute_pair_desc *d, const ErrorParams &
   std::ostringstream key;
   key.precision(17);
   const size_t hb = hist_budget(d, acc, hp);
-  key << d->kind << "|" << ep.eta0 << "|" << ep.lmin << "|" << ep.qd << "|"
+  key << d->kind << "|" << ep.eta0 << "|" << ep.lmin << "|" << ep.xm << "|" << ep.qd << "|"
       << ep.q0 << "|" << hp << "|"
       << ctx->table_binning << "|" << hb << "|";
   for (int k = 0; k <= d->n0; k++) key << d->edges0[k] << ",";
@@ -705,6 +706,7 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
   p.band = (const float2 *)P.d_band;
   p.band_words = (int)P.band.size() / 2;
   p.mu_eps_base = P.mu_eps_base;
+  p.far = P.far;
   p.E0 = P.d_E0;
   p.E1 = P.d_E1;
   p.E0df = (const float2 *)P.d_E0df;

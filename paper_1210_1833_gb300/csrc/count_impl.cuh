@@ -237,6 +237,7 @@ __device__ __forceinline__ float lg2_hw(float x) {
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+template <bool CLAMP>
 __device__ __forceinline__ void mono_log2(const AxisPlan &a, float2 qx, float2 qy, float2 qz,
                                           float2 nx, float2 ny, float2 nz, uint32_t stride,
                                           uint32_t c, uint32_t &o0, uint32_t &o1, float2 &sc) {
@@ -249,8 +250,10 @@ __device__ __forceinline__ void mono_log2(const AxisPlan &a, float2 qx, float2 q
   const float2 pv = __ffma2_rn(v, __ffma2_rn(v, make_float2(a.ld, a.ld), make_float2(a.lb, a.lb)),
                                make_float2(a.cst, a.cst));
   float2 t = __ffma2_rn(lg, make_float2(a.inv, a.inv), pv);
-  t.x = fminf(t.x, a.thi);  // above the last edge (and far sentinels): the top slot
-  t.y = fminf(t.y, a.thi);
+  if (CLAMP) {  // above the last edge (and far sentinels): the top slot
+    t.x = fminf(t.x, a.thi);
+    t.y = fminf(t.y, a.thi);
+  }  // (kArithLogU: the spare slots above the last bin hold every t)
   const float2 tm = __fadd2_rn(t, make_float2(kMagic, kMagic));
   const float2 fl = __fadd2_rn(tm, make_float2(-kMagic, -kMagic));
   const float2 h = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), t);
@@ -357,7 +360,7 @@ __device__ __forceinline__ void arith_pair_out(float2 s2, uint32_t (&o)[2], int 
 // tests, all decided by the re-test).
 template <int KIND, int M0>
 __device__ __forceinline__ float near_thr(const KParams &p) {
-  if (M0 == kArithLog) return p.ax[0].near_c;
+  if (M0 == kArithLog || M0 == kArithLogU) return p.ax[0].near_c;
   if (KIND == KRMU) return fminf(p.ax[0].near_at, p.ax[1].near_c);
   return p.ax[0].near_at;
 }
@@ -383,7 +386,7 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
                                            int lane, unsigned &near_count) {
   constexpr int U = 8 / HP;  // neighbours per step: 8 pairs per lane per step
   constexpr int NP = U * HP;
-  constexpr bool kLazy = M0 == kArith || M0 == kArithLog;
+  constexpr bool kLazy = M0 == kArith || M0 == kArithLog || M0 == kArithLogU;
   const float thr = near_thr<KIND, M0>(p);
   const int slot_shift = 31 - __clz(p.R * 4);
   // Plain counts add straight to the lane's histogram copy: its shared
@@ -421,14 +424,16 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
                       s2);
           arith_pair_out<HP, MASK, kLazy>(s2, o, u, sp, gj0 + j + u, h, zoff, thr, off, sc, nmask);
         }
-      } else if constexpr ((KIND == KMONO || KIND == KTHETA) && M0 == kArithLog) {
+      } else if constexpr ((KIND == KMONO || KIND == KTHETA) &&
+                           (M0 == kArithLog || M0 == kArithLogU)) {
         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y),
                      qz = make_float2(q.z, q.z);
 #pragma unroll
         for (int sp = 0; sp < HP / 2; sp++) {
           uint32_t o[2];
           float2 s2;
-          mono_log2(p.ax[0], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], st0, c1d, o[0], o[1], s2);
+          mono_log2<M0 == kArithLog>(p.ax[0], qx, qy, qz, h.nx2[sp], h.ny2[sp], h.nz2[sp], st0,
+                                     c1d, o[0], o[1], s2);
           arith_pair_out<HP, MASK, kLazy>(s2, o, u, sp, gj0 + j + u, h, zoff, thr, off, sc, nmask);
         }
       } else if constexpr (KIND == KSIGPI && M0 == kArith) {
@@ -602,6 +607,7 @@ __device__ __forceinline__ void tile_dispatch(const KParams &p, uint32_t lut,
   if (KIND == KMONO || KIND == KTHETA) {
     if (m0 == kArith) tile_dispatch_mask<KIND, HP, kArith, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
     else if (m0 == kArithLog) tile_dispatch_mask<KIND, HP, kArithLog, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
+    else if (m0 == kArithLogU) tile_dispatch_mask<KIND, HP, kArithLogU, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
     else if (m0 == kLutLinear) tile_dispatch_mask<KIND, HP, kLutLinear, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
     else tile_dispatch_mask<KIND, HP, kLutLog, 0, ACC>(p, lut, band, pd, w, tile, wtile, cnt, gj0, h, lane, mask, dc);
   } else {
@@ -726,7 +732,7 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
           cp_async16(dst + e, srcB + g);
           if (kWTile) cp_async4(wdst + e, &pd.posB[g].w);
         } else {
-          dst[e] = make_float4(kNbrFar, kNbrFar, kNbrFar, 0.0f);
+          dst[e] = make_float4(-p.far, -p.far, -p.far, 0.0f);
           if (kWTile) wdst[e] = 0.0f;
         }
       }
@@ -760,9 +766,9 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
                                          __dadd_rn(__dmul_rn(2.0, (double)a.w), __dmul_rn(4.0, pd.q0))));
         }
       } else {
-        Home<HP>::put(h.nx2, s, -kHomeFar);
-        Home<HP>::put(h.ny2, s, -kHomeFar);
-        Home<HP>::put(h.nz2, s, -kHomeFar);
+        Home<HP>::put(h.nx2, s, -p.far);
+        Home<HP>::put(h.ny2, s, -p.far);
+        Home<HP>::put(h.nz2, s, -p.far);
         h.w[s] = 0.0f;
         h.id[s] = 0x7fffffff;
         if (KIND == KRMU) {  // k l.l < 0: mu is NaN and clamps to the top slot

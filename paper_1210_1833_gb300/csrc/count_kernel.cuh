@@ -30,16 +30,16 @@ namespace cute {
 constexpr int kTile = 64;          // neighbour objects per shared-memory tile
 constexpr unsigned kFull = 0xffffffffu;
 
-// FP32 sentinels for padded home slots and tile rows: far from everything
-// and from each other, so every pair involving one is out of range.
-// The grid frame holds |x| <= 1e8 (checked when the grid is built; image
-// shifts of a periodic box add at most 2e8), so every pair with a sentinel is
-// more than 5e8 apart: beyond any reach, with squared
-// separations and (r, mu) products that stay finite in FP32, and (r, mu)
-// sentinels give mu = 1 (see the padded home slots), which the top clamp
-// keeps away from every edge band.
-constexpr float kHomeFar = 1.0e9f;
-constexpr float kNbrFar = -1.0e9f;
+// FP32 sentinels for padded home slots (+far on every axis) and tile rows
+// (-far), far = KParams::far: far from everything and from each other, so
+// every pair involving one is out of range.  The default far = 1e9: the grid
+// frame holds |x| <= 1e8 (checked when the grid is built; image shifts of a
+// periodic box add at most 2e8), so every pair with a sentinel is more than
+// 5e8 apart, beyond any reach, with squared separations and (r, mu) products
+// that stay finite in FP32 ((r, mu) padded home slots give a NaN mu, which
+// the top clamp turns into the top slot).  Chord counts binned by kArithLogU
+// take far = 1.25 (frame half-extent + reach) instead, the planner's bound on
+// the values their spare slots must hold.
 
 // ------------------------------------------------------------------ work entries
 // One contiguous range [j0, j1) of catalog B that a home chunk meets, with

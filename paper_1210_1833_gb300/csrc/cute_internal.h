@@ -33,6 +33,8 @@ constexpr int kLutLinear = 0;              // idx = rne(v * scale)
 constexpr int kLutLog = 1;                 // idx = max((bits(v) >> shift) - base, 0)
 constexpr int kArith = 2;                  // uniform edges: bin = floor((x - e0) / delta)
 constexpr int kArithLog = 3;               // log-spaced edges: t from log2(v) (monopole, chords)
+constexpr int kArithLogU = 4;              // the same without the upper clamp: spare slots above
+                                           // the last bin hold every t a pair can reach
 
 struct AxisPlan {
   int mode = 0;
@@ -146,6 +148,9 @@ struct KParams {
                                // mu bands hold (edge, edge)
   int band_words;              // float2 entries in band
   float mu_eps_base;           // R_MU: mu error bound of class 0 (class c: x 2^c)
+  // padded home slots sit at +far and padded tile rows at -far on every axis
+  // of the FP32 grid frame: beyond any reach, every product finite
+  float far;
   const double *E0, *E1;       // FP64 squared edges (mu: squared mu edges)
   const float2 *E0df, *E1df;   // the same as FP32 hi + lo
   int n0, n1;                  // bins per axis (n1 = 1 for 1-D kinds)
@@ -306,6 +311,7 @@ struct Plan {
   std::vector<uint32_t> lut;        // all axes
   std::vector<float> band;          // (lo, hi) per band, both axes
   float mu_eps_base = 0;            // R_MU
+  float far = 1.0e9f;               // padding sentinel magnitude (KParams::far)
   std::vector<double> E0, E1;       // FP64 squared edges
   double dirty_frac[2] = {0, 0};    // expected fraction of pairs in dirty cells
   // device copies
@@ -322,6 +328,7 @@ struct ErrorParams {
   double lmin;      // R_MU: lower bound of |l| for pairs within reach
   double qd;        // R_MU: bound on |q| = ||x|^2 - q0| over the catalogs
   double q0;        // R_MU: largest reference q0 of the pair sets
+  double xm;        // largest |x - frame centre| per axis over the pair sets (FP32 frame)
 };
 
 // Build the binning plan.  hist_budget_bytes: per-warp histogram budget.

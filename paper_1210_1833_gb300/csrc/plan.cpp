@@ -450,6 +450,34 @@ static bool make_logarith(const double *e, int n, const SqErr &err, AxisPlan &p)
   return thr_a / std::sqrt((double)E[0]) + thr_b < 0.2;
 }
 
+// Chords with log-spaced edges may drop the upper clamp of t (one
+// instruction per pair) when every t the kernel can form fits in spare
+// histogram slots above the last bin.  The values the kernel forms lie in
+// [vlo, vmax], vmax the squared separation of a padded home slot (+far on
+// every axis) and a padded tile row (-far): 12 far^2, with far = 1.25 (xm +
+// reach) -- every padded pair is then more than the reach apart (each axis
+// at least far - xm > reach / sqrt 3) -- and the fitted t, sampled over that
+// range, stays in [-1.2, tmax]; slots up to rint(tmax + 1/2) + 2 hold them
+// all (the FP32 t is within a few 1e-5 of the model).  Returns the slots
+// needed (0 when it does not apply).
+static int logarith_top(const AxisPlan &p, double xm, double reach, float &far_out) {
+  const double far = 1.25 * (xm + reach) * (1.0 + 1e-6) + 1e-30;
+  const float farf = f32_up(far);
+  const long double vmax = 12.0L * (long double)farf * (long double)farf * (1.0L + 1e-6L);
+  long double tmax = -1e30L, tmin = 1e30L;
+  const long double vlo = (long double)p.vlo;
+  if (!(vmax > vlo)) return 0;
+  for (int i = 0; i <= 20000; i++) {
+    const long double v = vlo * powl(vmax / vlo, (long double)i / 20000.0L);
+    const long double t = logt(p, v);
+    tmax = std::max(tmax, t);
+    tmin = std::min(tmin, t);
+  }
+  if (!(tmin >= -1.2L) || !(tmax < 4000.0L)) return 0;
+  far_out = farf;
+  return (int)floorl(tmax + 0.5L) + 4;
+}
+
 // ------------------------------------------------------------------ mu bound
 // Error of the kernel's FP32 mu about the midpoint line of sight (Sec. 2.1),
 // as eps(r) = a / r + b for a pair at separation r.  The kernel forms
@@ -593,6 +621,20 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
     // log-spaced monopole or chord edges: arithmetic on log2 of the square
     AxisPlan PL;
     if ((kind == KMONO || kind == KTHETA) && make_logarith(e0, n0, A0.err.sq, PL)) {
+      // (not for weighted counts, planned with a 1 KB histogram budget: their
+      // float-float column per slot and lane would grow with the spare slots)
+      if (kind == KTHETA && hist_budget_bytes >= 4096) {
+        float far = 0;
+        const int need = logarith_top(PL, ep.xm, e0[n0], far);
+        int Ru = 32;
+        while (Ru > 1 && (size_t)need * Ru * 4 > hist_budget_bytes) Ru >>= 1;
+        // only when as many histogram copies fit as with the clamp
+        if (need > 0 && Ru >= out.R && (size_t)need * Ru * 4 <= kOffMask) {
+          PL.mode = kArithLogU;
+          out.nslots = need;
+          out.far = far;
+        }
+      }
       out.ax[0] = PL;
       out.ax[1] = AxisPlan();
       out.lut.clear();

@@ -212,7 +212,8 @@ static Slot mono_log_fp32(const AxisPlan &a, const float *q, const float *n) {
   const float v = std::fmax(ffma(dz, dz, ffma(dy, dy, fmul(dx, dx))), a.vlo);
   const float lg = lg2_dev(v), rr = rsqrt_dev(v);
   const float pv = ffma(v, ffma(v, a.ld, a.lb), a.cst);
-  const float t = std::fmin(ffma(lg, a.inv, pv), a.thi);
+  float t = ffma(lg, a.inv, pv);
+  if (a.mode == kArithLog) t = std::fmin(t, a.thi);  // kArithLogU: no upper clamp
   const float tm = fadd(t, kMagic), fl = fadd(tm, -kMagic);
   const float h = ffma(fl, -1.0f, t);
   return {(int)(bits(tm) - kMagicBits) + 1, ffma(rr, a.thr_a, std::fabs(h))};
@@ -286,7 +287,8 @@ struct Tally {
 static double rmu_q0(double rmin, double robs) { return 0.5 * (rmin * rmin + robs * robs); }
 static ErrorParams eparams(double xm, double L, double rmax, double absmax, double rmin,
                            double robs = 0) {
-  ErrorParams ep{0, 0, 0, 0};
+  ErrorParams ep{0, 0, 0, 0, 0};
+  ep.xm = xm;
   ep.q0 = rmu_q0(rmin, robs);
   ep.qd = 0.5 * (robs * robs - rmin * rmin) * (1.0 + 1e-12) + 1e-15 * robs * robs;
   if (L > 0) {
@@ -363,17 +365,41 @@ static bool mode_ok(const std::string &m, const Plan &P, int want) {
 // edges e (uniform from 0: the arithmetic path; otherwise the table path)
 static Tally run_mono(const std::vector<double> &e, double L, double xm_spread, bool chord,
                       int want, std::mt19937_64 &g) {
-  const bool arith = want != kWantTable, logm = want == kArithLog;
+  const bool arith = want != kWantTable, logm = want == kArithLog || want == kArithLogU;
   const int n = (int)e.size() - 1;
   const std::vector<double> E = squares(e);
   const double fo[3] = {chord ? 0.0 : (L > 0 ? 0.5 * L : 1234.5),
                         chord ? 0.0 : (L > 0 ? 0.5 * L : -300.25),
                         chord ? 0.97 : (L > 0 ? 0.5 * L : 77.0)};
-  const double xm = chord ? 1.0 : (L > 0 ? 0.5 * L : xm_spread + e[n]);
+  // unclamped log chords: points on a cap within 18 degrees of +z (pairs up to
+  // 10 degrees apart stay within 0.6 of the frame centre on every axis)
+  const bool cap = chord && want == kArithLogU;
+  const double xm = cap ? 0.6 : (chord ? 1.0 : (L > 0 ? 0.5 * L : xm_spread + e[n]));
   Plan P;
+  // (the chord counts' kernel keeps 4 KB of histogram copies per warp)
   const std::string m = plan_build(chord ? KTHETA : KMONO, e.data(), n, nullptr, 1,
-                                   eparams(xm, L, e[n], 0, 0), 8192, 12288, arith, P);
+                                   eparams(xm, L, e[n], 0, 0), 8192, chord ? 4096 : 12288, arith,
+                                   P);
   if (!mode_ok(m, P, want)) return Tally{0, 0, 1};
+  if (want == kArithLogU) {
+    // every value the kernel can form, padded pairs included (up to 12
+    // far^2), must take a slot inside the planner's histogram
+    Tally range;
+    const double vlo = P.ax[0].vlo, vmax = 12.0 * (double)P.far * (double)P.far;
+    const float far_q[3] = {-P.far, -P.far, -P.far}, far_n[3] = {-P.far, -P.far, -P.far};
+    for (int i = 0; i <= 200000; i++) {
+      const double v = i < 200000 ? vlo * std::pow(vmax / vlo, i / 200000.0) : vmax;
+      // a separation of length sqrt(v) along one axis, or the padded pair
+      float q[3] = {(float)std::sqrt(v), 0.0f, 0.0f}, nn[3] = {0.0f, 0.0f, 0.0f};
+      const Slot r = i < 200000 ? mono_log_fp32(P.ax[0], q, nn) : mono_log_fp32(P.ax[0], far_q, far_n);
+      range.cases++;
+      if (r.slot < 0 || r.slot >= P.nslots) {
+        if (range.bad < 5) std::printf("  slot %d outside [0, %d) at v %g\n", r.slot, P.nslots, v);
+        range.bad++;
+      }
+    }
+    if (range.bad) return range;
+  }
   if (arith) shrink(P.ax[0]);
   else shrink_table(P, 0, E);
   std::uniform_real_distribution<double> U(-1, 1);
@@ -386,6 +412,7 @@ static Tally run_mono(const std::vector<double> &e, double L, double xm_spread, 
         if (chord) {
           double v[3], w[3];
           unit(g, v);
+          while (cap && v[2] < std::cos(18.0 * 3.141592653589793 / 180.0)) unit(g, v);
           unit(g, w);
           const double dot = w[0] * v[0] + w[1] * v[1] + w[2] * v[2];
           double wn = 0;
@@ -752,7 +779,7 @@ int main(int argc, char **argv) {
     std::snprintf(nm, sizeof nm, "log_mono_open_r%d", g_mode);
     report(nm, run_mono(logspace(1.0, 200.0, 16), 0.0, 1400.0, false, kArithLog, g));
     std::snprintf(nm, sizeof nm, "log_chord_r%d", g_mode);
-    report(nm, run_mono(chords, 0.0, 0, true, kArithLog, g));
+    report(nm, run_mono(chords, 0.0, 0, true, kArithLogU, g));
     std::snprintf(nm, sizeof nm, "table_sigpi_periodic_r%d", g_mode);
     report(nm, run_sigpi(logspace(0.5, 60.0, 15), uniform(2.0, 30), 1500.0, false, g));
     std::snprintf(nm, sizeof nm, "table_rmu_lightcone_r%d", g_mode);
