@@ -460,6 +460,8 @@ size_t hist_budget(const cute_pair_desc *d, int acc, int hp) {
   size_t want = 12288;
   if (acc == 1) want = 1024;
   else if (acc == 0 && count_max_warps(!two_d, hp, acc) > 16) want = 4096;
+  // integer weights: two histograms (counts, weight products) in the same 4 KB
+  else if (acc == 3) want = count_max_warps(!two_d, hp, acc) > 16 ? 2048 : 6144;
   return std::min<size_t>(12288, std::max<size_t>(want, nslots * 4));
 }
 
@@ -607,7 +609,7 @@ std::string tuning_key(const std::vector<DescInfo> &dis, int acc, bool full_sten
   // by problem shape (kind, sizes, cell grid), so re-uploaded catalogs of
   // the same workload keep their tuning
   std::ostringstream k;
-  k << acc << "|" << full_stencil << "|";
+  k << (acc == 3 ? 1 : acc) << "|" << full_stencil << "|";  // integer weights: a weighted count
   for (const DescInfo &di : dis)
     k << di.kind << ":" << di.is_auto << ":" << di.A->n << ":" << di.B->n << ":" << di.g->nc[0]
       << "x" << di.g->nc[1] << "x" << di.g->nc[2] << ",";
@@ -647,6 +649,18 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
     }
   }
   ErrorParams ep = error_params(pr.dis, decision_reach(&d[0]));
+  // weighted monopole / chord counts whose catalogs hold integer weights in
+  // [0, 2048] (counts per pixel or cell) sum the weight products in integer
+  // histograms: exact, and without the float-float columns
+  unsigned wpmax = 0;
+  if (acc == 1 && (d[0].kind == CUTE_MONO || d[0].kind == CUTE_THETA)) {
+    bool ints = true;
+    for (const DescInfo &di : pr.dis) {
+      if (di.A->wint < 0 || di.B->wint < 0) ints = false;
+      else wpmax = std::max(wpmax, (unsigned)di.A->wint * (unsigned)di.B->wint);
+    }
+    if (ints) acc = 3;
+  }
   // home objects per lane: 4 when home cells hold enough objects to fill
   // 128-object chunks, else 2
   pr.hp = ctx->hp_override;
@@ -661,7 +675,7 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
     // plain monopole / theta counts: the two-per-lane kernel runs 20 warps,
     // which outweighs the denser rows' case for four (c3 DD: 3.20 s against
     // 3.32 s)
-    if (acc == 0 && (d[0].kind == CUTE_MONO || d[0].kind == CUTE_THETA)) pr.hp = 2;
+    if ((acc == 0 || acc == 3) && (d[0].kind == CUTE_MONO || d[0].kind == CUTE_THETA)) pr.hp = 2;
   }
   int slice = ctx->slice_override ? ctx->slice_override : 2048;
   int warps_tuned = 0;
@@ -672,6 +686,14 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
       if (!ctx->slice_override) slice = it->second.slice;
       warps_tuned = it->second.warps_per_block;
     }
+  }
+  if (acc == 3) {
+    // one item adds at most 2 (32 / R) HP slice products to a weight-sum copy
+    // (R >= 1): the slice keeps that below 2^32, else float-float columns
+    const unsigned long long per = 2ull * 32 * (unsigned long long)pr.hp * std::max(wpmax, 1u);
+    const long long smax = (long long)(0xFFFFFFFFull / per) / kTile * kTile;
+    if (smax < kTile) acc = 1;
+    else slice = (int)std::min<long long>(slice, smax);
   }
   cute_status st = get_plan(ctx, &d[0], ep, pr.hp, acc, pr.plan);
   if (st != CUTE_OK) return st;
@@ -707,6 +729,7 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
   p.band_words = (int)P.band.size() / 2;
   p.mu_eps_base = P.mu_eps_base;
   p.far = P.far;
+  p.wpmax = wpmax;
   p.E0 = P.d_E0;
   p.E1 = P.d_E1;
   p.E0df = (const float2 *)P.d_E0df;

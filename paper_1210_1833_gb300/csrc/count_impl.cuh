@@ -6,7 +6,9 @@
 //   kAccWeighted -- counts and, per bin, the sum of w_i w_j (the pixel and
 //                   density-grid weights of Sec. 3.4);
 //   kAccAdjoint  -- d/dw_i of sum_b G_b W_b = sum_j w_j G[bin(i, j)] for
-//                   every home object i (no counts).
+//                   every home object i (no counts);
+//   kAccIntWeighted -- counts and weight sums for integer weights, in
+//                   integer histograms (monopole and chord counts).
 #pragma once
 
 #include "count_kernel.cuh"
@@ -17,6 +19,10 @@
 namespace cute {
 
 constexpr int kAccCount = 0, kAccWeighted = 1, kAccAdjoint = 2;
+// integer weights (all weights integers in [0, 2048], e.g. counts per pixel):
+// counts, and the weight products w_i w_j -- exact integers below 2^22 -- in
+// a second uint32 histogram, flushed to FP64 as exact sums
+constexpr int kAccIntWeighted = 3;
 
 template <int HP>
 struct Home {
@@ -39,6 +45,8 @@ struct Home {
 struct WarpSmem {
   int gje;                     // end of the current item's neighbour range
   uint32_t *hist;
+  uint32_t *whist;             // integer weights: the weight-product histogram
+  uint32_t s_dw;               // its byte offset from the count histogram
   char *hist_lane;
   uint32_t s_hist_lane;        // shared-space address of hist_lane
   uint32_t s_wcol;             // shared-space address of wcol
@@ -90,7 +98,7 @@ __device__ __forceinline__ void process_queue(const KParams &p, const PairDev &p
       bool in = s0 >= 1 && s0 <= p.n0 && (p.slots1 == 1 || (s1 >= 1 && s1 <= p.n1));
       int b = (s0 - 1) * p.n1 + (p.slots1 == 1 ? 0 : s1 - 1);
       if (ACC != kAccAdjoint) atomicAdd(&w.hist[s * p.R + (lane & (p.R - 1))], 1u);
-      if (ACC == kAccWeighted && in) {
+      if ((ACC == kAccWeighted || ACC == kAccIntWeighted) && in) {
         double prod = (double)pd.posA[e.x].w * (double)pd.posB[e.y].w;  // exact
         atomicAdd(&p.out_wsum[(size_t)pd.out * nb + b], prod);
       }
@@ -124,6 +132,24 @@ static __device__ __forceinline__ void flush_hist(const KParams &p, const WarpSm
   }
   __syncwarp();
   for (int i = lane; i < p.nslots * p.R; i += 32) w.hist[i] = 0;
+  __syncwarp();
+}
+
+// integer weights: add the warp's weight-product histogram to output `out`
+// (exact: a uint64 sum of integers, below 2^53) and clear it
+static __device__ __forceinline__ void flush_whist(const KParams &p, const WarpSmem &w, int out,
+                                                   int lane) {
+  __syncwarp();
+  const int nb = p.n0 * p.n1;
+  for (int b = lane; b < nb; b += 32) {
+    int b0 = b / p.n1, b1 = b - b0 * p.n1;
+    int s = (b0 + 1) * p.slots1 + (p.slots1 > 1 ? b1 + 1 : 0);
+    unsigned long long sum = 0;
+    for (int r = 0; r < p.R; r++) sum += w.whist[s * p.R + r];
+    if (sum) atomicAdd(&p.out_wsum[(size_t)out * nb + b], (double)sum);
+  }
+  __syncwarp();
+  for (int i = lane; i < p.nslots * p.R; i += 32) w.whist[i] = 0;
   __syncwarp();
 }
 
@@ -393,7 +419,8 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
   // address is folded into the offset constants (slot k = bits - magic + 1
   // on each axis), and a pair that is not counted here goes to slot 0
   // (below range, never reported).
-  const uint32_t zoff = (ACC == kAccCount) ? w.s_hist_lane : 0u;
+  constexpr bool kDirect = ACC == kAccCount || ACC == kAccIntWeighted;  // offsets are addresses
+  const uint32_t zoff = kDirect ? w.s_hist_lane : 0u;
   const uint32_t st0 = (uint32_t)p.slots1 * p.R * 4u, st1 = (uint32_t)p.R * 4u;
   const uint32_t c1d = (1u - kMagicBits) * st0 + zoff;
   // 2-D: slot (rint(t0) + 1) * slots1 + rint(t1) + 1 from the bits of
@@ -501,7 +528,16 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
     }
     if (ACC != kAccAdjoint) {
 #pragma unroll
-      for (int k = 0; k < NP; k++) red_add1(ACC == kAccCount ? off[k] : w.s_hist_lane + off[k]);
+      for (int k = 0; k < NP; k++) red_add1(kDirect ? off[k] : w.s_hist_lane + off[k]);
+    }
+    if (ACC == kAccIntWeighted) {
+      // the weight product, an exact integer below 2^22: its bits from
+      // p + 2^23 (exact), added to the weight histogram (same slot offset)
+#pragma unroll
+      for (int k = 0; k < NP; k++) {
+        const float pw = __fadd_rn(__fmul_rn(h.w[k % HP], wj[k / HP]), 8388608.0f);
+        red_add_u32(off[k] + w.s_dw, __float_as_uint(pw) - 0x4B000000u);
+      }
     }
     if (ACC == kAccWeighted) {
       // lane-private float-float column: a read-modify-write, no atomics
@@ -552,7 +588,11 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
           // opposite float-float addition (exact up to the columns' own
           // 2^-48 rounding)
           if (ACC != kAccAdjoint)
-            red_add_u32(ACC == kAccCount ? off[k] : w.s_hist_lane + off[k], 0xffffffffu);
+            red_add_u32(kDirect ? off[k] : w.s_hist_lane + off[k], 0xffffffffu);
+          if (ACC == kAccIntWeighted) {
+            const float pw = __fadd_rn(__fmul_rn(h.w[k % HP], wj[k / HP]), 8388608.0f);
+            red_add_u32(off[k] + w.s_dw, 0x4B000000u - __float_as_uint(pw));
+          }
           if (ACC == kAccWeighted) {
             const float a = h.w[k % HP], b = wj[k / HP];
             const float ph = __fmul_rn(a, b);
@@ -653,6 +693,8 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
   unsigned char *wb = smem + L.lut_bytes + (size_t)warp * L.warp_bytes;
   WarpSmem w;
   w.hist = (uint32_t *)wb;
+  w.s_dw = (uint32_t)align16(p.nslots * p.R * 4);
+  w.whist = (uint32_t *)(wb + w.s_dw);
   w.hist_lane = (char *)wb + (lane & (p.R - 1)) * 4;
   w.wstride = p.nslots + 1;  // odd stride: the flush reads across columns conflict-free
   w.wall = (float2 *)(wb + align16(p.nslots * p.R * 4));
@@ -668,6 +710,8 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
   w.s_G = smem_addr(w.G);
   const uint32_t s_lut = smem_addr(lut), s_band = smem_addr(band);
   for (int i = lane; i < p.nslots * p.R; i += 32) w.hist[i] = 0u;
+  if (ACC == kAccIntWeighted)
+    for (int i = lane; i < p.nslots * p.R; i += 32) w.whist[i] = 0u;
   if (ACC == kAccWeighted)
     for (int i = lane; i < 32 * w.wstride; i += 32) w.wall[i] = make_float2(0.0f, 0.0f);
   if (lane == 0) *w.qcnt = 0;
@@ -676,7 +720,7 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
   constexpr int CH = 32 * HP;
   int cur_pair = -1;
   PairDev pd;
-  unsigned long long acc = 0, items = 0, slots = 0, cand = 0;
+  unsigned long long acc = 0, accw = 0, items = 0, slots = 0, cand = 0;
   unsigned near_count = 0;
   // Work items in a two-deep pipeline: while an item runs, the record of
   // the next one is in flight and the ticket of the one after it has been
@@ -697,7 +741,8 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
       if (cur_pair >= 0) {
         process_queue<KIND, ACC>(p, pd, w, lane, true);
         if (ACC != kAccAdjoint) flush_hist(p, w, pd.out, lane);
-        acc = 0;
+        if (ACC == kAccIntWeighted) flush_whist(p, w, pd.out, lane);
+        acc = accw = 0;
       }
       cur_pair = pi;
       pd = p.pairs[cur_pair];
@@ -708,12 +753,17 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
     // uint32 overflow guard: increments a copy can receive from this item
     if (ACC != kAccAdjoint) {
       const unsigned long long bound = 2ull * (32 / p.R) * HP * (unsigned long long)(je - js);
-      if (acc + bound > 0xFFFFFFFFull) {
+      // (integer weights: each increment of the weight histogram is at most
+      // the largest product; the host keeps one item's total below 2^32)
+      const unsigned long long bw = ACC == kAccIntWeighted ? bound * p.wpmax : 0ull;
+      if (acc + bound > 0xFFFFFFFFull || accw + bw > 0xFFFFFFFFull) {
         process_queue<KIND, ACC>(p, pd, w, lane, true);
         flush_hist(p, w, pd.out, lane);
-        acc = 0;
+        if (ACC == kAccIntWeighted) flush_whist(p, w, pd.out, lane);
+        acc = accw = 0;
       }
       acc += bound;
+      accw += bw;
     }
     items++;
     slots += (unsigned long long)(32 * HP) * (unsigned long long)((je - js + (8 / HP) - 1) & ~((8 / HP) - 1));
@@ -807,6 +857,7 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
   if (cur_pair >= 0) {
     process_queue<KIND, ACC>(p, pd, w, lane, true);
     if (ACC != kAccAdjoint) flush_hist(p, w, pd.out, lane);
+    if (ACC == kAccIntWeighted) flush_whist(p, w, pd.out, lane);
   }
   if (lane == 0 && items) atomicAdd(&p.stats[1], items);
   if (lane == 0 && slots) atomicAdd(&p.stats[3], slots);
@@ -848,6 +899,10 @@ cudaError_t launch_count_hp(const KParams &p, int hp, int blocks, int threads, s
 template <int KIND, bool PER>
 cudaError_t launch_count_acc(const KParams &p, int acc, int hp, int blocks, int threads,
                              size_t smem, cudaStream_t st) {
+  if constexpr (KIND == KMONO) {
+    if (acc == kAccIntWeighted)
+      return launch_count_hp<KIND, PER, kAccIntWeighted>(p, hp, blocks, threads, smem, st);
+  }
   if (acc == kAccWeighted) return launch_count_hp<KIND, PER, kAccWeighted>(p, hp, blocks, threads, smem, st);
   if (acc == kAccAdjoint) return launch_count_hp<KIND, PER, kAccAdjoint>(p, hp, blocks, threads, smem, st);
   return launch_count_hp<KIND, PER, kAccCount>(p, hp, blocks, threads, smem, st);

@@ -142,8 +142,10 @@ __host__ __device__ inline SmemLayout smem_layout(int lut_words, int band_words,
   SmemLayout s;
   // block-wide: lookup tables, bands, and (adjoint) G per slot
   s.lut_bytes = align16(lut_words * 4) + align16(band_words * 8) + (acc == 2 ? align16(nslots * 8) : 0);
-  // per warp: the count histogram, and (weighted) 32 float-float columns
-  s.hist_bytes = align16(nslots * R * 4) + (acc == 1 ? align16(32 * (nslots + 1) * 8) : 0);
+  // per warp: the count histogram, and (weighted) 32 float-float columns or
+  // (integer weights) a second histogram of the weight products
+  s.hist_bytes = align16(nslots * R * 4) + (acc == 1 ? align16(32 * (nslots + 1) * 8) : 0) +
+                 (acc == 3 ? align16(nslots * R * 4) : 0);
   s.queue_cap = 32 + 32 * 8;  // checked after every step of 8 pairs per lane
   s.queue_bytes = 16 + align16(s.queue_cap * 8);  // 16-byte header holds the count
   s.tile_bytes = 2 * kTile * 16;

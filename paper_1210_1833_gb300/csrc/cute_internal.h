@@ -151,6 +151,9 @@ struct KParams {
   // padded home slots sit at +far and padded tile rows at -far on every axis
   // of the FP32 grid frame: beyond any reach, every product finite
   float far;
+  // integer weights (kAccIntWeighted): the largest weight product, for the
+  // uint32 overflow guard of the per-bin weight sums
+  unsigned wpmax;
   const double *E0, *E1;       // FP64 squared edges (mu: squared mu edges)
   const float2 *E0df, *E1df;   // the same as FP32 hi + lo
   int n0, n1;                  // bins per axis (n1 = 1 for 1-D kinds)
@@ -204,6 +207,9 @@ struct Catalog {
   float *d_w = nullptr;        // upload order weights, or null
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, absmax[3] = {0, 0, 0};
   double rmin = 0, rmax = 0;   // smallest and largest |x| (observer frame)
+  // weights that are all integers in [0, 2048] (counts per pixel or cell):
+  // their largest value; -1 for other weights or none
+  int wint = -1;
   // grid
   int geom = -1;
   long long grid_version = 0;

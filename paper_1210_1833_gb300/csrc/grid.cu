@@ -10,6 +10,7 @@
 #include "cute_internal.h"
 
 #include <cfloat>
+#include <cstring>
 
 namespace cute {
 
@@ -71,6 +72,28 @@ __global__ void k_stage_stats(const double *__restrict__ xyz, long long n, int p
     st.bad = s_bad[0];
     st.r2max = s_r2x[0];
     out[blockIdx.x] = st;
+  }
+}
+
+// Integer weights: out[0] = the largest weight's bits (non-negative floats
+// order like their bits), out[1] = the number of weights that are not
+// integers in [0, 2048].
+__global__ void k_weight_stats(const float *__restrict__ w, long long n,
+                               unsigned *__restrict__ out) {
+  unsigned mx = 0, bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float v = w[i];
+    if (!(v >= 0.0f && v <= 2048.0f) || v != rintf(v)) bad++;
+    else mx = max(mx, __float_as_uint(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], mx);
+    if (bad) atomicAdd(&out[1], bad);
   }
 }
 
@@ -291,6 +314,20 @@ cute_status catalog_stage(cute_ctx *ctx, Catalog &c, const double *xyz, const fl
   }
   c.rmin = std::sqrt(r2min);
   c.rmax = std::sqrt(r2max);
+  c.wint = -1;
+  if (w && n > 0) {
+    st = ensure_scratch(ctx, 2 * sizeof(unsigned));
+    if (st != CUTE_OK) return st;
+    unsigned h[2] = {0, 0};
+    CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_scratch, 0, 2 * sizeof(unsigned), ctx->stream));
+    k_weight_stats<<<blocks, 256, 0, ctx->stream>>>(c.d_w, n, (unsigned *)ctx->d_scratch);
+    CUDA_OR_FAIL(cudaGetLastError());
+    CUDA_OR_FAIL(cudaMemcpyAsync(h, ctx->d_scratch, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
+    float mx;
+    std::memcpy(&mx, &h[0], 4);
+    if (h[1] == 0) c.wint = (int)mx;
+  }
   if (bad) {
     return fail(ctx, CUTE_E_INVALID,
                 c.boundary == CUTE_PERIODIC

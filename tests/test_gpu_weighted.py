@@ -220,3 +220,47 @@ def test_autograd_forward_without_backward_frees_catalogs(ctx):
     del W
     gc.collect()
     assert all(cute.lib().cute_catalog_size(ctx.handle, i, ctypes.byref(n)) == -4 for i in held)
+
+
+@pytest.mark.parametrize("wmax", [40, 300])
+@pytest.mark.parametrize("periodic", [True, False])
+def test_integer_weights_exact(ctx, periodic, wmax):
+    """Weights that are all integers in [0, 2048] (counts per pixel or cell)
+    take the integer weight histograms: W_b is then an exact integer sum and
+    equals the oracle's bit for bit, auto and cross, monopole and chords.
+    Weights up to 300 make the library shorten the neighbour slices so that
+    one work item cannot overflow a 32-bit weight sum."""
+    rng = np.random.default_rng(40 + wmax)
+    x, _ = _case(5000, seed=41)
+    w = rng.integers(0, wmax + 1, len(x)).astype(np.float32)
+    L = 400.0
+    e = np.arange(31) * 5.0
+    a, _ = _upload(ctx, x, w, periodic, L, e[-1])
+    c, oor, ws = ctx.count("mono", a, None, e, weighted=True)
+    rc, roor, rws = oracle.count("mono", x, edges0=e, periodic=periodic, L=L, wa=w, weighted=True)
+    assert c.tolist() == rc.tolist() and oor == roor
+    np.testing.assert_array_equal(ws, rws)
+    a.free()
+    # cross count, and chords between unit vectors (log-spaced angles)
+    y = synthetic.uniform_box(3000, L, rng)
+    wy = rng.integers(1, wmax + 1, len(y)).astype(np.float32)
+    a, b = _upload(ctx, x, w, periodic, L, e[-1], y=y, wy=wy)
+    c, oor, ws = ctx.count("mono", a, b, e, weighted=True)
+    rc, roor, rws = oracle.count("mono", x, y, edges0=e, periodic=periodic, L=L, wa=w, wb=wy,
+                                 weighted=True)
+    assert c.tolist() == rc.tolist() and oor == roor
+    np.testing.assert_array_equal(ws, rws)
+    a.free(); b.free()
+    if not periodic:
+        u = rng.normal(size=(4000, 3))
+        u[:, 2] = np.abs(u[:, 2]) + 2.0
+        u /= np.linalg.norm(u, axis=1)[:, None]
+        wu = rng.integers(0, wmax + 1, len(u)).astype(np.float32)
+        ch = cute.theta_to_chord(np.logspace(-1, 1.3, 21))
+        p = ctx.upload(u, weights=wu)
+        ctx.grid([p], [ch[-1]] * 3)
+        c, oor, ws = ctx.count("theta", p, None, ch, weighted=True)
+        rc, roor, rws = oracle.count("theta", u, edges0=ch, wa=wu, weighted=True)
+        assert c.tolist() == rc.tolist() and oor == roor
+        np.testing.assert_array_equal(ws, rws)
+        p.free()
