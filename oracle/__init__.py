@@ -365,65 +365,54 @@ def tsc_density(xyz, L, n, w=None):
     return rho
 
 
+def _lag_bins(delta, L, edges, lag_sum):
+    """xi per bin from the lag sums lag_sum(dz, dy, dx) = sum_x delta(x)
+    delta(x + d) over every lag vector d of the half space with a|d| below
+    the last edge, binned by a^2 |d|^2 on the squared edges (half-open);
+    mean over the bin's lags and the grid's points.  Returns (xi, lags)."""
+    n = delta.shape[0]
+    a = L / n
+    e2 = np.asarray(edges, dtype=np.float64) ** 2
+    nb = len(e2) - 1
+    R = int(np.floor(edges[-1] / a))
+    s, c = np.zeros(nb), np.zeros(nb)
+    for dz in range(0, R + 1):
+        for dy in range(-R, R + 1):
+            for dx in range(-R, R + 1):
+                if (dz, dy) == (0, 0) and dx <= 0:
+                    continue
+                if dz == 0 and dy < 0:
+                    continue
+                r2 = (dx * dx + dy * dy + dz * dz) * a * a
+                if r2 < e2[0] or r2 >= e2[-1]:
+                    continue
+                b = int(np.searchsorted(e2, r2, side="right")) - 1
+                s[b] += lag_sum(dz, dy, dx)
+                c[b] += 1
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(c > 0, s / (c * delta.size), np.nan), c
+
+
 def lag_xi(delta, L, edges):
     """xi(r) = <delta(x) delta(x + r)> over the pairs of distinct grid points
     of a periodic grid whose separation falls in each bin (Sec. 3.4.4): for
     every lag vector d of the half space with a|d| below the last edge, the
     product sum of delta with delta shifted by d, binned by a^2 |d|^2 on the
     squared edges (half-open).  Returns (xi, lags per bin)."""
-    n = delta.shape[0]
-    a = L / n
-    e2 = np.asarray(edges, dtype=np.float64) ** 2
-    nb = len(e2) - 1
-    R = int(np.floor(edges[-1] / a))
-    s, c = np.zeros(nb), np.zeros(nb)
-    for dz in range(0, R + 1):
-        for dy in range(-R, R + 1):
-            for dx in range(-R, R + 1):
-                if (dz, dy) == (0, 0) and dx <= 0:
-                    continue
-                if dz == 0 and dy < 0:
-                    continue
-                r2 = (dx * dx + dy * dy + dz * dz) * a * a
-                if r2 < e2[0] or r2 >= e2[-1]:
-                    continue
-                b = int(np.searchsorted(e2, r2, side="right")) - 1
-                s[b] += float(np.sum(delta * np.roll(delta, (-dz, -dy, -dx), axis=(0, 1, 2))))
-                c[b] += 1
-    with np.errstate(invalid="ignore", divide="ignore"):
-        return np.where(c > 0, s / (c * delta.size), np.nan), c
+    return _lag_bins(delta, L, edges, lambda dz, dy, dx: float(
+        np.sum(delta * np.roll(delta, (-dz, -dy, -dx), axis=(0, 1, 2)))))
 
 
 def lag_xi_fft(delta, L, edges):
     """The same estimate as lag_xi with the lag sums taken from the circular
     autocorrelation of the grid: sum_x delta(x) delta(x + d) is the inverse
     FFT of |FFT(delta)|^2 at d (the correlation theorem; FP64, numpy's FFT
-    as the library step), over the same half-space lags and half-open bins
-    on a^2 |d|^2.  For grids where the direct sum of lag_xi is too slow."""
+    as the library step).  For grids where the direct sums are too slow."""
     n = delta.shape[0]
-    a = L / n
-    e2 = np.asarray(edges, dtype=np.float64) ** 2
-    nb = len(e2) - 1
-    R = int(np.floor(edges[-1] / a))
     f = np.fft.rfftn(np.asarray(delta, dtype=np.float64))
     C = np.fft.irfftn(f * np.conj(f), s=delta.shape, axes=(0, 1, 2))
     del f
-    s, c = np.zeros(nb), np.zeros(nb)
-    for dz in range(0, R + 1):
-        for dy in range(-R, R + 1):
-            for dx in range(-R, R + 1):
-                if (dz, dy) == (0, 0) and dx <= 0:
-                    continue
-                if dz == 0 and dy < 0:
-                    continue
-                r2 = (dx * dx + dy * dy + dz * dz) * a * a
-                if r2 < e2[0] or r2 >= e2[-1]:
-                    continue
-                b = int(np.searchsorted(e2, r2, side="right")) - 1
-                s[b] += float(C[dz % n, dy % n, dx % n])
-                c[b] += 1
-    with np.errstate(invalid="ignore", divide="ignore"):
-        return np.where(c > 0, s / (c * delta.size), np.nan), c
+    return _lag_bins(delta, L, edges, lambda dz, dy, dx: float(C[dz % n, dy % n, dx % n]))
 
 
 def density_grid_xi(xyz, L, n, edges, w=None):
