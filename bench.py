@@ -440,7 +440,8 @@ _ROW_SCALE = 1.0  # --row with --scale: a smaller copy of the row's workload (pr
 def _row_batched(ctx, dev, timed):
     import torch
     out = {}
-    boxes = synthetic.c4_batched_sigpi()
+    # (--row batched --scale s: the first 64 s boxes, for profiling)
+    boxes = synthetic.c4_batched_sigpi(n_boxes=max(1, int(round(64 * _ROW_SCALE))))
     e0, e1 = boxes[0].edges0, boxes[0].edges1
     reach = [e0[-1], e0[-1], e1[-1]]
     cats, pairs = [], []
@@ -470,7 +471,8 @@ def _row_batched(ctx, dev, timed):
     torch.cuda.synchronize()
     st = ctx.stats()
     binned = sum(int(c.sum()) for c in ctx.count_batched("sigpi", pairs, e0, e1, device=True))
-    out["batched_sigpi_64_boxes"] = {
+    name = "batched_sigpi_64_boxes" if len(boxes) == 64 else "batched_sigpi_%d_boxes" % len(boxes)
+    out[name] = {
         "batched_ms": t_b, "plain_ms": t_p, "plain_over_batched": t_p / t_b,
         "launches": {"batched": 1, "plain": len(pairs)}, "binned_pairs": binned,
         "binned_pairs_per_s": binned / (t_b / 1e3), "graph_replay": True,
