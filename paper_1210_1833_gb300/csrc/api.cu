@@ -1035,11 +1035,19 @@ cute_status cute_autotune(cute_ctx *ctx, int32_t n, const cute_pair_desc *d, int
   const int save_hp = ctx->hp_override, save_w = ctx->warps_override, save_s = ctx->slice_override;
   cute_tuning best{k0, 0, 0, 0, INFINITY};
   cute_status st = CUTE_OK;
+  // small counts (fewer than 1e10 object pairs in all) also try short
+  // slices: more, shorter work items per warp balance a launch of a few
+  // thousand items (c1: 20k objects, 57 -> 44 us at 64 neighbours)
+  double npairs = 0;
+  for (int i = 0; i < n; i++)
+    npairs += (double)ctx->cats[d[i].cat_a].n * (double)ctx->cats[d[i].cat_b].n;
+  const std::vector<int> slices = npairs < 1e10 ? std::vector<int>{64, 256, 1024, 2048, 4096}
+                                                : std::vector<int>{1024, 2048, 4096};
   for (int k : ks) {
     if (tune_cells && (st = rebuild(k)) != CUTE_OK) break;
     for (int hp : {2, 4})
       for (int warps : {8, 12, 16, 20})
-        for (int slice : {1024, 2048, 4096}) {
+        for (int slice : slices) {
           ctx->hp_override = hp;
           ctx->warps_override = warps;
           ctx->slice_override = slice;
