@@ -255,7 +255,7 @@ def run_gpu(args, w, rank, world):
     r_pin = torch.from_numpy(w.randoms).pin_memory()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")  # 256 MB
     state = {"cand": 0, "kms": [], "rr_cand": 0, "rr_ms": [], "inrange": 0, "rechecked": 0, "fp64": 0,
-             "slots": 0, "per": {}}
+             "slots": 0, "per": {}, "stencil": 0}
 
     def step(dsrc, rsrc, record):
         cd = ctx.upload(dsrc)
@@ -271,6 +271,7 @@ def run_gpu(args, w, rank, world):
             if record:
                 st = ctx.stats()
                 state["cand"] += st["candidate_pairs"]
+                state["stencil"] += st["stencil_pairs"]
                 state["kms"].append(st["kernel_ms"])
                 state["per"].setdefault(name, []).append(st["kernel_ms"])
                 state["rechecked"] += st["rechecked_pairs"]
@@ -371,6 +372,7 @@ def run_gpu(args, w, rank, world):
                    "parallelism": "replicas" if world > 1 else "single",
                    "cells_per_reach": args.cpr, "autotuned": tuning or None},
         "pairs": {"candidate_per_step": cand_per_step,
+                  "stencil_per_step": state["stencil"] / args.steps,
                   "in_range_per_step": inrange_per_step,
                   "all_pairs_per_step": total_pairs(nd, nr),
                   "candidate_pairs_per_s": world * cand_per_step / (ms / 1e3),
@@ -612,6 +614,7 @@ def _row_angular(ctx, dev, timed):
         c, _, _ = ctx.count("theta", a, b, chord, want_oor=False)
         st = ctx.stats()
         res[name] = {"kernel_ms": st["kernel_ms"], "candidate_pairs": st["candidate_pairs"],
+                     "stencil_pairs": st["stencil_pairs"],
                      "binned_pairs": int(c.sum()), "recheck": _recheck(st),
                      "roofline": _alu_roofline(st["candidate_pairs"] / (st["kernel_ms"] / 1e3),
                                                "theta")}

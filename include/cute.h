@@ -208,7 +208,8 @@ cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_desc *d, uin
 
 /* Statistics of the last count call on ctx. */
 typedef struct {
-  uint64_t candidate_pairs; /* pairs examined by the FP32 path              */
+  uint64_t candidate_pairs; /* pairs examined by the FP32 path (after the
+                               neighbour cull; see stencil_pairs)           */
   uint64_t rechecked_pairs; /* of those, re-tested near an edge            */
   uint64_t fp64_pairs;      /* of those, decided by the FP64 formula (the
                                double-float stage left them open)          */
@@ -219,6 +220,10 @@ typedef struct {
   int32_t warps_per_block, blocks, home_per_lane;
   float kernel_ms;          /* device time of the counting kernel(s), if
                                timing was enabled with cute_set_timing     */
+  uint64_t stencil_pairs;   /* pairs the cell stencil presented (Sec. 3.3),
+                               before the kernel dropped the neighbours
+                               beyond the reach of a home chunk's bounding
+                               box: candidate_pairs <= stencil_pairs        */
 } cute_stats;
 cute_status cute_last_stats(cute_ctx *ctx, cute_stats *out);
 

@@ -267,7 +267,7 @@ cute_status cute_last_stats(cute_ctx *ctx, cute_stats *out) {
   ENTER(ctx);
   if (!out) return fail(ctx, CUTE_E_INVALID, "out is NULL");
   CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
-  unsigned long long h[kCounterWords] = {0, 0, 0, 0, 0, 0, 0};
+  unsigned long long h[kCounterWords] = {0};
   CUDA_OR_FAIL(cudaMemcpy(h, ctx->d_ticket, sizeof(h), cudaMemcpyDeviceToHost));
   ctx->stats.rechecked_pairs = h[1];
   ctx->stats.fp64_pairs = h[6];
@@ -589,10 +589,13 @@ cute_status get_work(cute_ctx *ctx, const std::vector<DescInfo> &dis, int hp, in
   CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_cnt, std::max(T->nentries, 1) * sizeof(int)));
   CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_bsum, work_bsum_words(T->nentries) * sizeof(long long)));
   CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_eprefix, (T->nentries + 1) * sizeof(long long)));
+  CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_spairs, sizeof(unsigned long long)));
   CUDA_OR_FAIL(work_count(T->d_work, T->d_ebase, (int)T->pairs.size(), T->nentries, slice,
-                          T->d_cnt, T->d_bsum, T->d_eprefix, ctx->stream));
+                          T->d_cnt, T->d_bsum, T->d_eprefix, T->d_spairs, ctx->stream));
   // the item count sizes the record list: one round trip per work list
   CUDA_OR_FAIL(cudaMemcpyAsync(&T->items, T->d_eprefix + T->nentries, sizeof(long long),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_OR_FAIL(cudaMemcpyAsync(&T->stencil_pairs, T->d_spairs, sizeof(unsigned long long),
                                cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_OR_FAIL(cudaStreamSynchronize(ctx->stream));
   CUDA_OR_FAIL(dev_alloc(ctx, (void **)&T->d_items, std::max<long long>(T->items, 1) * sizeof(int4)));
@@ -730,6 +733,7 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
   p.mu_eps_base = P.mu_eps_base;
   p.far = P.far;
   p.wpmax = wpmax;
+  cull_params(pr.dis, d, n, p);
   p.E0 = P.d_E0;
   p.E1 = P.d_E1;
   p.E0df = (const float2 *)P.d_E0df;
@@ -826,6 +830,7 @@ cute_status count_driver(cute_ctx *ctx, int n, const cute_pair_desc *d, uint64_t
   ctx->stats.warps_per_block = pr.warps;
   ctx->stats.blocks = pr.blocks;
   ctx->stats.home_per_lane = pr.hp;
+  ctx->stats.stencil_pairs = pr.ts->stencil_pairs;
   // batched counts into device outputs: replay a captured graph
   bool all_dev = n > 1 && oor == nullptr;
   for (int i = 0; all_dev && i < n; i++)
@@ -914,6 +919,7 @@ static cute_status adjoint_pass(cute_ctx *ctx, const cute_pair_desc *d, const do
   CUDA_OR_FAIL(cudaMemsetAsync(ctx->d_ticket, 0, sizeof(unsigned long long), ctx->stream));
   pr.p.G = d_G;
   pr.p.grad = d_grad;
+  ctx->stats.stencil_pairs += pr.ts->stencil_pairs;
   ctx->stats.warps_per_block = pr.warps;
   ctx->stats.blocks = pr.blocks;
   ctx->stats.home_per_lane = pr.hp;

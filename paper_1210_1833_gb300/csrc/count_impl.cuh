@@ -60,6 +60,10 @@ struct WarpSmem {
   int qcap;
   float4 *tiles;
   float *wtiles;               // R_MU weighted / adjoint: the tiles' weights
+  uint32_t s_box;              // the item's home box, negated: (-lo.xyz, carried rows),
+                               // (-hi.xyz, end of the run's real rows)
+  uint32_t s_cidx;             // neighbour index of each culled row, by row of the
+                               // tile buffer (INT_MAX: padding row)
 };
 
 // ------------------------------------------------------------------ float-float
@@ -401,7 +405,10 @@ __device__ __forceinline__ float near_thr(const KParams &p) {
 // takes the near pairs' contributions back (count, weight product or
 // gradient term) before queueing them, so the common step carries no
 // per-pair selects.  Table binning routes near pairs to slot 0 at once.
-// MASK: 1 -- only j > i counts (the home run against itself, unique pairs);
+// MASK: 0 -- every pair counts; the rows are culled rows of a tile buffer
+//            from its row gj0 on (their neighbour indices in s_cidx, the
+//            end of the real rows in the box words);
+//       1 -- only j > i counts (the home run against itself, unique pairs);
 //       2 -- every j != i counts (full-stencil adjoint of an auto count).
 // R_MU tiles hold (x, y, z, q); their weights (weighted, adjoint) come
 // from a tile of their own, wtile.
@@ -579,6 +586,10 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
     // rare: pairs inside an edge's error band join the warp's re-test queue;
     // the queue only grows here, so it is drained here when it holds 32
     if (flagged) {
+      // pairs with the padding rows past this item's rows are never queued
+      // (a culled run: rows past the end of its real rows; the neighbour
+      // index of a queued pair's row is looked up only then)
+      const int lim = MASK == 0 ? (int)lds_u32(w.s_box + 28u) : w.gje;
 #pragma unroll
       for (int k = 0; k < NP; k++) {
         const bool nk = kLazy ? (sc[k] >= thr) : ((nmask >> k) & 1u) != 0u;
@@ -612,10 +623,13 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
         }
         // (a padded home slot or tile row is never a pair, whatever its
         // arithmetic gave)
-        if (nk && h.id[k % HP] != 0x7fffffff && gj0 + j + k / HP < w.gje) {
+        const int gjk = gj0 + j + k / HP;
+        if (nk && h.id[k % HP] != 0x7fffffff && gjk < lim) {
           near_count++;
           int pos = atomicAdd(w.qcnt, 1);
-          if (pos < w.qcap) w.queue[pos] = make_int2(h.id[k % HP], gj0 + j + k / HP);
+          if (pos < w.qcap)
+            w.queue[pos] = make_int2(h.id[k % HP],
+                                     MASK == 0 ? (int)lds_u32(w.s_cidx + 4u * gjk) : gjk);
           else atomicCAS(p.err, 0, (int)CUTE_E_DEVICE);
         }
       }
@@ -668,6 +682,143 @@ __device__ __forceinline__ float shift_of(int code, float L) {
   return code == 1 ? L : (code == 2 ? -L : 0.0f);
 }
 
+// Neighbour cull of two rows at once (packed FP32): row q is kept unless
+// its distance from the home box exceeds the reach, the gap on each axis
+// being max(lo - q, q - hi, 0); sigma, pi: the x-y gap against sigma's
+// reach and the z gap against pi's.  The box comes negated (nlo = -lo,
+// nhi = -hi), so q - lo and q - hi are additions: the same roundings as
+// lo - q (its exact negation) and q - hi.  p.cull_r2 and p.cull_pi are
+// widened on the host past the FP32 frame's rounding and this arithmetic's
+// own, so no pair within reach is dropped.
+template <int KIND>
+__device__ __forceinline__ void cull_keep2(const KParams &p, float4 qa, float4 qb, float4 nlo,
+                                           float4 nhi, bool &ka, bool &kb) {
+  auto gap = [](float a, float b, float nl, float nh, float2 &g) {
+    const float2 q = make_float2(a, b);
+    const float2 tl = __fadd2_rn(q, make_float2(nl, nl));  // q - lo
+    const float2 th = __fadd2_rn(q, make_float2(nh, nh));  // q - hi
+    g = make_float2(fmaxf(fmaxf(-tl.x, th.x), 0.0f), fmaxf(fmaxf(-tl.y, th.y), 0.0f));
+  };
+  float2 gx, gy, gz;
+  gap(qa.x, qb.x, nlo.x, nhi.x, gx);
+  gap(qa.y, qb.y, nlo.y, nhi.y, gy);
+  gap(qa.z, qb.z, nlo.z, nhi.z, gz);
+  if (KIND == KSIGPI) {
+    const float2 s2 = __ffma2_rn(gy, gy, __fmul2_rn(gx, gx));
+    ka = s2.x <= p.cull_r2 && gz.x <= p.cull_pi;
+    kb = s2.y <= p.cull_r2 && gz.y <= p.cull_pi;
+  } else {
+    const float2 d2 = __ffma2_rn(gz, gz, __ffma2_rn(gy, gy, __fmul2_rn(gx, gx)));
+    ka = d2.x <= p.cull_r2;
+    kb = d2.y <= p.cull_r2;
+  }
+}
+
+// One landed tile of a culled item, compacted in place: the rows within
+// reach of the home box move to the front of the tile (a ballot and a
+// prefix count place them; a tile kept whole stays where it is), right
+// behind the rows carried from the tile before into the buffer's kTilePre
+// leading rows.  Sets the run to pair -- rows [base, base + m), whole steps
+// (the item's last tile pads to a step with sentinel rows) -- and leaves in
+// the box words the rows short of a step and where they start, for
+// cull_carry.  Nothing of this lives in registers across the pairing.
+// cand gains this lane's evaluated pairs, slots the pair slots run.
+template <int KIND, int HP, int ACC>
+__device__ __forceinline__ void cull_compact(const KParams &p, const WarpSmem &w, int tt, int js,
+                                             int je, bool last, const Home<HP> &h, int lane,
+                                             unsigned long long &cand, unsigned long long &slots,
+                                             int &base, int &m) {
+  constexpr bool kWTile = KIND == KRMU && ACC != kAccCount;
+  constexpr int U = 8 / HP;  // rows per step of tile_pairs
+  static_assert(kTile == 64, "two rows per lane");
+  static_assert(U <= kTilePre && U <= kTileRows - kTilePre - kTile, "carry and padding room");
+  const uint32_t B = smem_addr(w.tiles + (tt & 1) * kTileRows);
+  const uint32_t WB = smem_addr(w.wtiles + (tt & 1) * kTileRows);
+  const int g0 = js + tt * kTile;
+  const uint32_t ra = (uint32_t)(kTilePre + lane), rb = ra + 32u;  // this lane's rows
+  const float4 qa = lds_f4(B + 16u * ra), qb = lds_f4(B + 16u * rb);
+  const float4 nlo = lds_f4(w.s_box), nhi = lds_f4(w.s_box + 16u);
+  const int nbuf = __float_as_int(nlo.w);  // rows carried in
+  bool ka, kb;
+  cull_keep2<KIND>(p, qa, qb, nlo, nhi, ka, kb);
+  const unsigned ba = __ballot_sync(kFull, ka && g0 + lane < je);
+  const unsigned bb = __ballot_sync(kFull, kb && g0 + lane + 32 < je);
+  int kept;
+  if ((ba & bb) == kFull) {  // every row kept: in place already
+    sts_u32(w.s_cidx + 4u * ra, (uint32_t)(g0 + lane));
+    sts_u32(w.s_cidx + 4u * rb, (uint32_t)(g0 + lane + 32));
+    kept = kTile;
+  } else {
+    const float wa = kWTile ? __uint_as_float(lds_u32(WB + 4u * ra)) : 0.0f;
+    const float wb = kWTile ? __uint_as_float(lds_u32(WB + 4u * rb)) : 0.0f;
+    const unsigned below = (1u << lane) - 1u;
+    const int na = __popc(ba);
+    __syncwarp();  // every row read before any moves
+    if ((ba >> lane) & 1u) {
+      const uint32_t r = (uint32_t)(kTilePre + __popc(ba & below));
+      sts_f4(B + 16u * r, qa);
+      sts_u32(w.s_cidx + 4u * r, (uint32_t)(g0 + lane));
+      if (kWTile) sts_u32(WB + 4u * r, __float_as_uint(wa));
+    }
+    if ((bb >> lane) & 1u) {
+      const uint32_t r = (uint32_t)(kTilePre + na + __popc(bb & below));
+      sts_f4(B + 16u * r, qb);
+      sts_u32(w.s_cidx + 4u * r, (uint32_t)(g0 + lane + 32));
+      if (kWTile) sts_u32(WB + 4u * r, __float_as_uint(wb));
+    }
+    kept = na + __popc(bb);
+  }
+  int nv = 0;  // this lane's occupied home slots: its evaluated pairs
+#pragma unroll
+  for (int s = 0; s < HP; s++) nv += h.id[s] != 0x7fffffff;
+  cand += (unsigned)(kept * nv);
+  base = kTilePre - nbuf;
+  const int n = nbuf + kept;  // the run: rows [base, base + n)
+  m = last ? (n + U - 1) & ~(U - 1) : n & ~(U - 1);
+  slots += (unsigned)(32 * HP * m);
+  if (last && lane < m - n) {
+    const uint32_t r = (uint32_t)(base + n + lane);
+    sts_f4(B + 16u * r, make_float4(-p.far, -p.far, -p.far, 0.0f));
+    sts_u32(w.s_cidx + 4u * r, 0x7fffffffu);
+    if (kWTile) sts_u32(WB + 4u * r, 0u);
+  }
+  if (lane == 0) {  // the rows short of a step (for cull_carry), the end of the real rows
+    sts_u32(w.s_box + 12u, (uint32_t)(last ? 0 : n - m));
+    sts_u32(w.s_box + 28u, (uint32_t)(base + n));
+  }
+  __syncwarp();
+}
+
+// After the run of tile tt is paired: its rows short of a step move to the
+// other buffer's rows [kTilePre - rem, kTilePre), which the cp.async of the
+// next tile does not write; their indices may overlap the targets in
+// s_cidx, so every lane reads before any lane writes.  rem becomes the
+// next tile's carried-in count.
+template <int KIND, int ACC>
+__device__ __forceinline__ void cull_carry(const WarpSmem &w, int tt, int lane) {
+  constexpr bool kWTile = KIND == KRMU && ACC != kAccCount;
+  __syncwarp();
+  const int rem = (int)lds_u32(w.s_box + 12u);
+  if (rem == 0) return;
+  const uint32_t f = lds_u32(w.s_box + 28u) - (uint32_t)rem + (uint32_t)lane;
+  const uint32_t B = smem_addr(w.tiles + (tt & 1) * kTileRows);
+  const uint32_t WB = smem_addr(w.wtiles + (tt & 1) * kTileRows);
+  float4 cq = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  uint32_t ci = 0u, cw = 0u;
+  if (lane < rem) {
+    cq = lds_f4(B + 16u * f);
+    ci = lds_u32(w.s_cidx + 4u * f);
+    if (kWTile) cw = lds_u32(WB + 4u * f);
+  }
+  __syncwarp();
+  if (lane < rem) {
+    const uint32_t t = (uint32_t)(kTilePre - rem + lane);
+    sts_f4(smem_addr(w.tiles + ((tt + 1) & 1) * kTileRows) + 16u * t, cq);
+    sts_u32(w.s_cidx + 4u * t, ci);
+    if (kWTile) sts_u32(smem_addr(w.wtiles + ((tt + 1) & 1) * kTileRows) + 4u * t, cw);
+  }
+}
+
 template <int KIND, bool PER, int HP, int ACC>
 __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 1)
     k_count(const KParams p) {
@@ -705,6 +856,8 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
   w.qcap = L.queue_cap;
   w.tiles = (float4 *)(wb + L.hist_bytes + L.queue_bytes);
   w.wtiles = (float *)(wb + L.hist_bytes + L.queue_bytes + L.tile_bytes);
+  w.s_box = smem_addr(wb + L.hist_bytes + L.queue_bytes + L.tile_bytes + L.wtile_bytes);
+  w.s_cidx = w.s_box + 32u;
   w.s_hist_lane = smem_addr(w.hist_lane);
   w.s_wcol = smem_addr(w.wcol);
   w.s_G = smem_addr(w.G);
@@ -717,7 +870,6 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
   if (lane == 0) *w.qcnt = 0;
   __syncthreads();
 
-  constexpr int CH = 32 * HP;
   int cur_pair = -1;
   PairDev pd;
   unsigned long long acc = 0, accw = 0, items = 0, slots = 0, cand = 0;
@@ -766,7 +918,11 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
       accw += bw;
     }
     items++;
-    slots += (unsigned long long)(32 * HP) * (unsigned long long)((je - js + (8 / HP) - 1) & ~((8 / HP) - 1));
+    // Rows of other cells (and every row of a cross count) go through the
+    // neighbour cull; the home run against its own cells does not.
+    const bool cull = !(mask == 1 || (ACC == kAccAdjoint && mask == 2));
+    if (!cull)
+      slots += (unsigned long long)(32 * HP) * (unsigned long long)((je - js + (8 / HP) - 1) & ~((8 / HP) - 1));
 
     // the first tile is in flight while the home objects load
     const int nj = je - js;
@@ -774,8 +930,8 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
     // R_MU tiles come from (x, y, z, q), and their weights from (x, y, z, w)
     const float4 *srcB = KIND == KRMU ? pd.qB : pd.posB;
     auto load_tile = [&](int tt) {
-      float4 *dst = w.tiles + (tt & 1) * kTile;
-      float *wdst = w.wtiles + (tt & 1) * kTile;
+      float4 *dst = w.tiles + (tt & 1) * kTileRows + kTilePre;
+      float *wdst = w.wtiles + (tt & 1) * kTileRows + kTilePre;
       for (int e = lane; e < kTile; e += 32) {
         const int g = js + tt * kTile + e;
         if (g < je) {
@@ -806,9 +962,11 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
         Home<HP>::put(h.nz2, s, -__fsub_rn(a.z, Sz));
         h.w[s] = KIND == KRMU ? (ACC == kAccWeighted ? pd.posA[idx].w : 1.0f) : a.w;
         h.id[s] = idx;
-        // candidate pairs: j in [js, je), with j > i (self) or j != i
-        cand += mask == 1 ? (unsigned)max(0, je - max(js, idx + 1))
-                          : (unsigned)(nj - (mask == 2 && idx >= js && idx < je ? 1 : 0));
+        // candidate pairs of the rows not culled: j in [js, je), with j > i
+        // (self) or j != i
+        if (!cull)
+          cand += mask == 1 ? (unsigned)max(0, je - max(js, idx + 1))
+                            : (unsigned)(nj - (mask == 2 && idx >= js && idx < je ? 1 : 0));
         if (KIND == KRMU) {
           // C_i = k (2 q_i + 4 q0), rounded once from FP64
           Home<HP>::put(h.nq2, s, -a.w);
@@ -828,6 +986,34 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
       }
     }
     w.gje = je;
+    if (cull) {
+      // bounding box of the home objects in the image frame (x_i - shift),
+      // kept in shared memory beside the culled rows
+      float bl[3] = {3.0e38f, 3.0e38f, 3.0e38f}, bh[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+#pragma unroll
+      for (int s = 0; s < HP; s++) {
+        if (h.id[s] != 0x7fffffff) {
+          const float c[3] = {-Home<HP>::get(h.nx2, s), -Home<HP>::get(h.ny2, s),
+                              -Home<HP>::get(h.nz2, s)};
+#pragma unroll
+          for (int k = 0; k < 3; k++) {
+            bl[k] = fminf(bl[k], c[k]);
+            bh[k] = fmaxf(bh[k], c[k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          bl[k] = fminf(bl[k], __shfl_xor_sync(kFull, bl[k], o));
+          bh[k] = fmaxf(bh[k], __shfl_xor_sync(kFull, bh[k], o));
+        }
+      if (lane == 0) {  // negated: (-lo, carried rows 0), (-hi, -)
+        sts_f4(w.s_box, make_float4(-bl[0], -bl[1], -bl[2], 0.0f));
+        sts_f4(w.s_box + 16u, make_float4(-bh[0], -bh[1], -bh[2], 0.0f));
+      }
+    }
 
     for (int tt = 0; tt < ntiles; tt++) {
       if (tt + 1 < ntiles) {
@@ -837,11 +1023,23 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
         cp_async_wait<0>();
       }
       __syncwarp();
-      int cnt = min(kTile, nj - tt * kTile);
-      cnt = (cnt + (8 / HP) - 1) & ~((8 / HP) - 1);  // whole steps; padded rows are sentinels
-      tile_dispatch<KIND, HP, ACC>(p, s_lut, s_band, pd, w, smem_addr(w.tiles + (tt & 1) * kTile),
-                                   smem_addr(w.wtiles + (tt & 1) * kTile), cnt, js + tt * kTile,
-                                   h, lane, mask, near_count);
+      // the run to pair: the landed tile, or its culled rows (one dispatch
+      // for both, so the pairing loop is compiled once per mask)
+      const uint32_t B = smem_addr(w.tiles + (tt & 1) * kTileRows);
+      const uint32_t WB = smem_addr(w.wtiles + (tt & 1) * kTileRows);
+      int first = kTilePre, cnt, gj0 = js + tt * kTile;
+      if (!cull) {
+        cnt = min(kTile, nj - tt * kTile);
+        cnt = (cnt + (8 / HP) - 1) & ~((8 / HP) - 1);  // whole steps; padded rows are sentinels
+      } else {
+        cull_compact<KIND, HP, ACC>(p, w, tt, js, je, tt + 1 == ntiles, h, lane, cand, slots,
+                                    first, cnt);
+        gj0 = first;  // (culled rows: their indices are in s_cidx)
+      }
+      if (cnt > 0)
+        tile_dispatch<KIND, HP, ACC>(p, s_lut, s_band, pd, w, B + 16u * first, WB + 4u * first,
+                                     cnt, gj0, h, lane, cull ? 0 : mask, near_count);
+      if (cull && tt + 1 < ntiles) cull_carry<KIND, ACC>(w, tt, lane);
       __syncwarp();
     }
     if (ACC == kAccWeighted) flush_wsum(p, w, pd.out, lane);

@@ -28,6 +28,10 @@
 namespace cute {
 
 constexpr int kTile = 64;          // neighbour objects per shared-memory tile
+// A tile buffer holds kTilePre rows before the tile (culled rows carried
+// from the tile before) and room after it to pad the last step.
+constexpr int kTilePre = 4;
+constexpr int kTileRows = kTilePre + kTile + 4;
 constexpr unsigned kFull = 0xffffffffu;
 
 // FP32 sentinels for padded home slots (+far on every axis) and tile rows
@@ -132,6 +136,7 @@ struct SmemLayout {
   int queue_bytes;
   int tile_bytes;     // per warp (2 tiles)
   int wtile_bytes;    // per warp (2 weight tiles: R_MU weighted / adjoint)
+  int cull_bytes;     // per warp: the home box, the culled rows' neighbour indices
   int warp_bytes;     // per warp total
 };
 
@@ -148,9 +153,10 @@ __host__ __device__ inline SmemLayout smem_layout(int lut_words, int band_words,
                  (acc == 3 ? align16(nslots * R * 4) : 0);
   s.queue_cap = 32 + 32 * 8;  // checked after every step of 8 pairs per lane
   s.queue_bytes = 16 + align16(s.queue_cap * 8);  // 16-byte header holds the count
-  s.tile_bytes = 2 * kTile * 16;
-  s.wtile_bytes = wtile ? 2 * kTile * 4 : 0;
-  s.warp_bytes = s.hist_bytes + s.queue_bytes + s.tile_bytes + s.wtile_bytes;
+  s.tile_bytes = 2 * kTileRows * 16;
+  s.wtile_bytes = wtile ? 2 * kTileRows * 4 : 0;
+  s.cull_bytes = 32 + kTileRows * 4;
+  s.warp_bytes = s.hist_bytes + s.queue_bytes + s.tile_bytes + s.wtile_bytes + s.cull_bytes;
   return s;
 }
 
@@ -187,6 +193,14 @@ __device__ __forceinline__ float2 lds_f2(uint32_t a) {
 }
 __device__ __forceinline__ void sts_f2(uint32_t a, float2 v) {
   asm volatile("st.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void sts_f4(uint32_t a, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(a), "r"(v) : "memory");
 }
 __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
   uint32_t v;

@@ -154,6 +154,11 @@ struct KParams {
   // integer weights (kAccIntWeighted): the largest weight product, for the
   // uint32 overflow guard of the per-bin weight sums
   unsigned wpmax;
+  // neighbour cull: a tile row of another cell is skipped when its FP32
+  // distance from the bounding box of the item's home objects exceeds the
+  // reach -- squared, cull_r2 (sigma, pi: cull_r2 in x-y and cull_pi along
+  // z) -- both widened past every rounding of the FP32 frame (cull_params)
+  float cull_r2, cull_pi;
   const double *E0, *E1;       // FP64 squared edges (mu: squared mu edges)
   const float2 *E0df, *E1df;   // the same as FP32 hi + lo
   int n0, n1;                  // bins per axis (n1 = 1 for 1-D kinds)
@@ -249,10 +254,14 @@ struct WorkSet {
   long long *d_eprefix = nullptr;  // nentries + 1
   long long items = 0;             // work items
   int4 *d_items = nullptr;         // their records
+  // pairs the items present (candidate pairs before the kernel's neighbour
+  // cull): host copy, and the device word the work builder sums into
+  unsigned long long stencil_pairs = 0;
+  unsigned long long *d_spairs = nullptr;
   ~WorkSet() {
     for (void *q : {(void *)d_chunks, (void *)d_stencil, (void *)d_pairs, (void *)d_pdf,
                     (void *)d_work, (void *)d_ebase, (void *)d_cnt, (void *)d_bsum,
-                    (void *)d_eprefix, (void *)d_items})
+                    (void *)d_eprefix, (void *)d_items, (void *)d_spairs})
       if (q) cudaFreeAsync(q, st);
   }
 };
@@ -363,6 +372,8 @@ void pinned_put(cute_ctx *ctx, int32_t *p, size_t cap);
 PairDF pair_df(const DescInfo &di);
 // The kernel's view of pair set `out` (catalogs, sizes, box, (r, mu) data).
 PairDev pair_dev(const DescInfo &di, int out);
+// The neighbour cull's radii for the pair sets of one launch (KParams).
+void cull_params(const std::vector<DescInfo> &dis, const cute_pair_desc *d, int n, KParams &p);
 
 // Home chunks of catalog A (plan.cpp): each row of cells cut into chunks of
 // home_chunk objects (the last one of a row shorter), spanning at most
@@ -380,11 +391,12 @@ void stencil_build(const Geometry &g, bool is_auto, bool full_stencil, int shape
 // Work entries on the GPU (work.cu): work_count computes the item count of
 // every entry and their exclusive prefix sums into eprefix[0..nentries]
 // (bsum needs work_bsum_words(nentries) words); work_write then writes the
-// item records of every entry at its prefix.
+// item records of every entry at its prefix.  work_count also sums into
+// *spairs the pairs the entries present to the counting kernel.
 int work_bsum_words(int nentries);
 cudaError_t work_count(const PairWork *d_pairs, const int *d_ebase, int npairs, int nentries,
                        int slice, int *d_cnt, long long *d_bsum, long long *d_eprefix,
-                       cudaStream_t st);
+                       unsigned long long *d_spairs, cudaStream_t st);
 cudaError_t work_write(const PairWork *d_pairs, const int *d_ebase, int npairs, int nentries,
                        int slice, const long long *d_eprefix, int4 *d_items, cudaStream_t st);
 

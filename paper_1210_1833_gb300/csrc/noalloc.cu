@@ -192,6 +192,7 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   p.band_words = (int)P.band.size() / 2;
   p.mu_eps_base = P.mu_eps_base;
   p.far = P.far;
+  cull_params(std::vector<DescInfo>{di}, d, 1, p);
   p.E0 = (const double *)(dev + o_e0);
   p.E1 = (const double *)(dev + o_e1);
   p.E0df = (const float2 *)(dev + o_e0df);

@@ -777,6 +777,36 @@ std::string plan_build(int kind, const double *e0, int n0, const double *e1, int
   return "";
 }
 
+// The neighbour cull keeps a row whose FP32 gap vector g to the home box
+// (computed from FP32 frame offsets) has |g|^2 <= cull_r2.  Each component
+// of a pair's separation in FP32 differs from the exact one by at most
+// e = u (3 xm + 2 L): the neighbour's offset (u xm), the home's offset
+// (u xm), its image x - S in FP32 (u (xm + L)) and the FP32 box size
+// (u L); the gap of a pair's neighbour is at most the FP32 separation, so
+// |g| <= |s| + sqrt(3) e, and the gap's own FP32 arithmetic (one
+// subtraction, a product and two fused adds) adds under 5u relative.
+// Radii (r + 2e)(1 + 1e-5), squared and rounded up, therefore keep every
+// pair with |s| <= r: the cull drops only pairs beyond the last edge.
+void cull_params(const std::vector<DescInfo> &dis, const cute_pair_desc *d, int n, KParams &p) {
+  double xm = 0.0, L = 0.0, r0 = 0.0, r1 = 0.0;
+  for (const DescInfo &di : dis) {
+    xm = std::max(xm, std::max(di.g->xmax[0], std::max(di.g->xmax[1], di.g->xmax[2])));
+    if (di.g->periodic) L = std::max(L, di.g->L);
+  }
+  for (int i = 0; i < n; i++) {
+    r0 = std::max(r0, d[i].edges0[d[i].n0]);
+    if (d[i].kind == CUTE_SIGMA_PI) r1 = std::max(r1, d[i].edges1[d[i].n1]);
+  }
+  const double e = kU * (3.0 * xm + 2.0 * L);
+  auto up = [](double v) {
+    float f = (float)v;
+    return (double)f < v ? std::nextafter(f, INFINITY) : f;
+  };
+  const double c0 = (r0 + 2.0 * e) * (1.0 + 1e-5);
+  p.cull_r2 = up(c0 * c0);
+  p.cull_pi = d[0].kind == CUTE_SIGMA_PI ? up((r1 + 2.0 * e) * (1.0 + 1e-5)) : INFINITY;
+}
+
 // ------------------------------------------------------------------ work decomposition
 // A home chunk spans at most this many cells of its row: on a periodic
 // axis the chunk's neighbour x-range (its cells widened by k on each side)

@@ -21,17 +21,30 @@ constexpr int kScanThreads = 256;
 constexpr int kScanPer = 16;                        // entries per thread
 constexpr int kScanBlock = kScanThreads * kScanPer;  // entries per block
 
+// Items of entry e, and the pairs its segments present to the counting
+// kernel: every (home, neighbour) pair, j > i on the home run's own cells
+// (kSegSelf), without i = j on a full stencil's home row (kSegNoSelfPair).
 __device__ __forceinline__ int entry_items(const PairWork *__restrict__ pairs,
                                            const int *__restrict__ ebase, int npairs, int e,
-                                           int slice) {
+                                           int slice, unsigned long long &npair) {
   const int pi = pair_of_entry(ebase, npairs, e);
   const PairWork &pd = pairs[pi];
   const int local = e - ebase[pi];
   const int ci = local / pd.nstencil, ri = local - ci * pd.nstencil;
+  const int4 c = pd.chunks[ci];
   Seg s[3];
-  const int ns = entry_segments(pd, pd.csB, pd.chunks[ci], pd.stencil[ri], s);
+  const int ns = entry_segments(pd, pd.csB, c, pd.stencil[ri], s);
   int items = 0;
-  for (int k = 0; k < ns; k++) items += (s[k].j1 - s[k].j0 + slice - 1) / slice;
+  for (int k = 0; k < ns; k++) {
+    items += (s[k].j1 - s[k].j0 + slice - 1) / slice;
+    if (s[k].flags & kSegSelf) {
+      for (int i = c.x; i < c.y; i++) npair += (unsigned)max(0, s[k].j1 - max(s[k].j0, i + 1));
+    } else {
+      npair += (unsigned long long)(c.y - c.x) * (unsigned)(s[k].j1 - s[k].j0);
+      if (s[k].flags & kSegNoSelfPair)
+        npair -= (unsigned)max(0, min(c.y, s[k].j1) - max(c.x, s[k].j0));
+    }
+  }
   return items;
 }
 
@@ -58,13 +71,15 @@ __device__ long long block_scan(long long v, long long &excl) {
 
 __global__ void __launch_bounds__(kScanThreads) k_entry_counts(
     const PairWork *__restrict__ pairs, const int *__restrict__ ebase, int npairs, int nentries,
-    int slice, int *__restrict__ cnt, long long *__restrict__ bsum) {
+    int slice, int *__restrict__ cnt, long long *__restrict__ bsum,
+    unsigned long long *__restrict__ spairs) {
   const int base = blockIdx.x * kScanBlock;
   long long sum = 0;
+  unsigned long long np = 0;
   for (int k = 0; k < kScanPer; k++) {
     const int e = base + k * kScanThreads + threadIdx.x;  // coalesced stores
     if (e < nentries) {
-      const int c = entry_items(pairs, ebase, npairs, e, slice);
+      const int c = entry_items(pairs, ebase, npairs, e, slice, np);
       cnt[e] = c;
       sum += c;
     }
@@ -72,6 +87,8 @@ __global__ void __launch_bounds__(kScanThreads) k_entry_counts(
   long long excl;
   const long long tot = block_scan(sum, excl);
   if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+  for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(kFull, np, o);
+  if ((threadIdx.x & 31) == 0 && np) atomicAdd(spairs, np);
 }
 
 // exclusive scan of the block sums, in place, by one block
@@ -137,11 +154,13 @@ int work_bsum_words(int nentries) { return std::max(1, (nentries + kScanBlock - 
 
 cudaError_t work_count(const PairWork *d_pairs, const int *d_ebase, int npairs, int nentries,
                        int slice, int *d_cnt, long long *d_bsum, long long *d_eprefix,
-                       cudaStream_t st) {
+                       unsigned long long *d_spairs, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(d_spairs, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
   if (nentries <= 0) return cudaMemsetAsync(d_eprefix, 0, sizeof(long long), st);
   const int nblocks = work_bsum_words(nentries);
   k_entry_counts<<<nblocks, kScanThreads, 0, st>>>(d_pairs, d_ebase, npairs, nentries, slice,
-                                                   d_cnt, d_bsum);
+                                                   d_cnt, d_bsum, d_spairs);
   k_scan_bsums<<<1, kScanThreads, 0, st>>>(d_bsum, nblocks);
   k_scan_entries<<<nblocks, kScanThreads, 0, st>>>(d_cnt, d_bsum, nentries, nblocks, d_eprefix);
   return cudaGetLastError();

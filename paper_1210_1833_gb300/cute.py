@@ -65,7 +65,8 @@ class Stats(ctypes.Structure):
                 ("fp64_pairs", ctypes.c_uint64),
                 ("pair_slots", ctypes.c_uint64), ("work_items", ctypes.c_uint64), ("launches", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("blocks", ctypes.c_int32),
-                ("home_per_lane", ctypes.c_int32), ("kernel_ms", ctypes.c_float)]
+                ("home_per_lane", ctypes.c_int32), ("kernel_ms", ctypes.c_float),
+                ("stencil_pairs", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

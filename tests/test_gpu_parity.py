@@ -122,6 +122,33 @@ def test_rmu_lightcone_small(ctx):
         _assert_same(got, ref)
 
 
+def test_neighbour_cull(ctx):
+    """The kernel drops neighbour rows beyond the reach of a home chunk's
+    bounding box: fewer pairs evaluated than the stencil presented, never
+    fewer than the pairs binned, and the counts still the oracle's.  The
+    light-cone DR and RR at 2 and 4 home objects per lane, and the periodic
+    monopole (image shifts move the home box)."""
+    table = ctx.table_binning if hasattr(ctx, "table_binning") else False
+    w = synthetic.c2_rmu_lightcone(scale=0.01)
+    m = synthetic.c1_monopole_box(scale=0.5)
+    try:
+        for hp in (2, 4):
+            ctx.set_launch(home_per_lane=hp, table_binning=table)
+            for a, b in ((w.data, w.randoms), (w.randoms, None)):
+                got = gpu_count(ctx, "rmu", a, b, w.edges0, w.edges1, cells_per_reach=4)
+                st = ctx.stats()
+                _assert_same(got, oracle_count("rmu", a, b, w.edges0, w.edges1, cells=True))
+                binned = int(got[0].sum())
+                assert binned <= st["candidate_pairs"] < 0.95 * st["stencil_pairs"]
+            got = gpu_count(ctx, "mono", m.data, e0=m.edges0, periodic=True, L=m.L,
+                            cells_per_reach=3)
+            st = ctx.stats()
+            _assert_same(got, oracle_count("mono", m.data, e0=m.edges0, periodic=True, L=m.L))
+            assert int(got[0].sum()) <= st["candidate_pairs"] < st["stencil_pairs"]
+    finally:
+        ctx.set_launch(table_binning=table)
+
+
 @pytest.mark.parametrize("cpr", [3, 4])
 def test_trimmed_stencils_2d(ctx, cpr):
     """Neighbour rows trimmed to the reach ball (r, mu) or disk x slab
