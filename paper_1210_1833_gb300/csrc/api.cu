@@ -704,7 +704,8 @@ cute_status prepare(cute_ctx *ctx, int n, const cute_pair_desc *d, int acc, bool
   if (st != CUTE_OK) return st;
   const Plan &P = *pr.plan;
   SmemLayout L = smem_layout((int)P.lut.size(), (int)P.band.size() / 2, P.nslots, P.R, pr.hp, acc,
-                             d[0].kind == CUTE_R_MU && acc != 0);
+                             d[0].kind == CUTE_R_MU && acc != 0,
+                             d[0].kind == CUTE_R_MU || acc != 0);
   pr.acc = acc;
   size_t avail = ctx->smem_optin;
   const int wmax = count_max_warps(d[0].kind == CUTE_MONO || d[0].kind == CUTE_THETA, pr.hp, acc);

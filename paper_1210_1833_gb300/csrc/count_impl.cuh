@@ -406,8 +406,9 @@ __device__ __forceinline__ float near_thr(const KParams &p) {
 // gradient term) before queueing them, so the common step carries no
 // per-pair selects.  Table binning routes near pairs to slot 0 at once.
 // MASK: 0 -- every pair counts; the rows are culled rows of a tile buffer
-//            from its row gj0 on (their neighbour indices in s_cidx, the
-//            end of the real rows in the box words);
+//            from its row gj0 on (their neighbour indices in s_cidx or
+//            the rows' weight words, the end of the real rows in the box
+//            words);
 //       1 -- only j > i counts (the home run against itself, unique pairs);
 //       2 -- every j != i counts (full-stencil adjoint of an auto count).
 // R_MU tiles hold (x, y, z, q); their weights (weighted, adjoint) come
@@ -427,6 +428,9 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
   // on each axis), and a pair that is not counted here goes to slot 0
   // (below range, never reported).
   constexpr bool kDirect = ACC == kAccCount || ACC == kAccIntWeighted;  // offsets are addresses
+  // culled rows of plain counts but (r, mu) carry their neighbour index in
+  // the weight word (unused there); the others keep it in s_cidx
+  constexpr bool kIdxRow = ACC == kAccCount && KIND != KRMU;
   const uint32_t zoff = kDirect ? w.s_hist_lane : 0u;
   const uint32_t st0 = (uint32_t)p.slots1 * p.R * 4u, st1 = (uint32_t)p.R * 4u;
   const uint32_t c1d = (1u - kMagicBits) * st0 + zoff;
@@ -628,8 +632,11 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
           near_count++;
           int pos = atomicAdd(w.qcnt, 1);
           if (pos < w.qcap)
-            w.queue[pos] = make_int2(h.id[k % HP],
-                                     MASK == 0 ? (int)lds_u32(w.s_cidx + 4u * gjk) : gjk);
+            w.queue[pos] = make_int2(
+                h.id[k % HP],
+                MASK != 0 ? gjk
+                          : (int)lds_u32(kIdxRow ? tile + 16u * (uint32_t)(j + k / HP) + 12u
+                                                 : w.s_cidx + 4u * gjk));
           else atomicCAS(p.err, 0, (int)CUTE_E_DEVICE);
         }
       }
@@ -729,9 +736,11 @@ __device__ __forceinline__ void cull_compact(const KParams &p, const WarpSmem &w
                                              unsigned long long &cand, unsigned long long &slots,
                                              int &base, int &m) {
   constexpr bool kWTile = KIND == KRMU && ACC != kAccCount;
+  constexpr bool kIdxRow = ACC == kAccCount && KIND != KRMU;
   constexpr int U = 8 / HP;  // rows per step of tile_pairs
   static_assert(kTile == 64, "two rows per lane");
-  static_assert(U <= kTilePre && U <= kTileRows - kTilePre - kTile, "carry and padding room");
+  static_assert(U - 1 <= kTilePre && U - 1 <= kTileRows - kTilePre - kTile,
+                "carry and padding room");
   const uint32_t B = smem_addr(w.tiles + (tt & 1) * kTileRows);
   const uint32_t WB = smem_addr(w.wtiles + (tt & 1) * kTileRows);
   const int g0 = js + tt * kTile;
@@ -745,8 +754,8 @@ __device__ __forceinline__ void cull_compact(const KParams &p, const WarpSmem &w
   const unsigned bb = __ballot_sync(kFull, kb && g0 + lane + 32 < je);
   int kept;
   if ((ba & bb) == kFull) {  // every row kept: in place already
-    sts_u32(w.s_cidx + 4u * ra, (uint32_t)(g0 + lane));
-    sts_u32(w.s_cidx + 4u * rb, (uint32_t)(g0 + lane + 32));
+    sts_u32(kIdxRow ? B + 16u * ra + 12u : w.s_cidx + 4u * ra, (uint32_t)(g0 + lane));
+    sts_u32(kIdxRow ? B + 16u * rb + 12u : w.s_cidx + 4u * rb, (uint32_t)(g0 + lane + 32));
     kept = kTile;
   } else {
     const float wa = kWTile ? __uint_as_float(lds_u32(WB + 4u * ra)) : 0.0f;
@@ -756,14 +765,16 @@ __device__ __forceinline__ void cull_compact(const KParams &p, const WarpSmem &w
     __syncwarp();  // every row read before any moves
     if ((ba >> lane) & 1u) {
       const uint32_t r = (uint32_t)(kTilePre + __popc(ba & below));
-      sts_f4(B + 16u * r, qa);
-      sts_u32(w.s_cidx + 4u * r, (uint32_t)(g0 + lane));
+      const int gi = g0 + lane;
+      sts_f4(B + 16u * r, kIdxRow ? make_float4(qa.x, qa.y, qa.z, __int_as_float(gi)) : qa);
+      if (!kIdxRow) sts_u32(w.s_cidx + 4u * r, (uint32_t)gi);
       if (kWTile) sts_u32(WB + 4u * r, __float_as_uint(wa));
     }
     if ((bb >> lane) & 1u) {
       const uint32_t r = (uint32_t)(kTilePre + na + __popc(bb & below));
-      sts_f4(B + 16u * r, qb);
-      sts_u32(w.s_cidx + 4u * r, (uint32_t)(g0 + lane + 32));
+      const int gi = g0 + lane + 32;
+      sts_f4(B + 16u * r, kIdxRow ? make_float4(qb.x, qb.y, qb.z, __int_as_float(gi)) : qb);
+      if (!kIdxRow) sts_u32(w.s_cidx + 4u * r, (uint32_t)gi);
       if (kWTile) sts_u32(WB + 4u * r, __float_as_uint(wb));
     }
     kept = na + __popc(bb);
@@ -776,10 +787,9 @@ __device__ __forceinline__ void cull_compact(const KParams &p, const WarpSmem &w
   const int n = nbuf + kept;  // the run: rows [base, base + n)
   m = last ? (n + U - 1) & ~(U - 1) : n & ~(U - 1);
   slots += (unsigned)(32 * HP * m);
-  if (last && lane < m - n) {
+  if (last && lane < m - n) {  // (never queued: past the real rows)
     const uint32_t r = (uint32_t)(base + n + lane);
     sts_f4(B + 16u * r, make_float4(-p.far, -p.far, -p.far, 0.0f));
-    sts_u32(w.s_cidx + 4u * r, 0x7fffffffu);
     if (kWTile) sts_u32(WB + 4u * r, 0u);
   }
   if (lane == 0) {  // the rows short of a step (for cull_carry), the end of the real rows
@@ -797,6 +807,7 @@ __device__ __forceinline__ void cull_compact(const KParams &p, const WarpSmem &w
 template <int KIND, int ACC>
 __device__ __forceinline__ void cull_carry(const WarpSmem &w, int tt, int lane) {
   constexpr bool kWTile = KIND == KRMU && ACC != kAccCount;
+  constexpr bool kIdxRow = ACC == kAccCount && KIND != KRMU;
   __syncwarp();
   const int rem = (int)lds_u32(w.s_box + 12u);
   if (rem == 0) return;
@@ -807,14 +818,14 @@ __device__ __forceinline__ void cull_carry(const WarpSmem &w, int tt, int lane) 
   uint32_t ci = 0u, cw = 0u;
   if (lane < rem) {
     cq = lds_f4(B + 16u * f);
-    ci = lds_u32(w.s_cidx + 4u * f);
+    if (!kIdxRow) ci = lds_u32(w.s_cidx + 4u * f);
     if (kWTile) cw = lds_u32(WB + 4u * f);
   }
   __syncwarp();
   if (lane < rem) {
     const uint32_t t = (uint32_t)(kTilePre - rem + lane);
     sts_f4(smem_addr(w.tiles + ((tt + 1) & 1) * kTileRows) + 16u * t, cq);
-    sts_u32(w.s_cidx + 4u * t, ci);
+    if (!kIdxRow) sts_u32(w.s_cidx + 4u * t, ci);
     if (kWTile) sts_u32(smem_addr(w.wtiles + ((tt + 1) & 1) * kTileRows) + 4u * t, cw);
   }
 }
@@ -825,7 +836,9 @@ __global__ void __launch_bounds__(32 * count_max_warps(KIND == KMONO, HP, ACC), 
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr bool kWTile = KIND == KRMU && ACC != kAccCount;
-  const SmemLayout L = smem_layout(p.lut_words, p.band_words, p.nslots, p.R, HP, ACC, kWTile);
+  constexpr bool kIdxRow = ACC == kAccCount && KIND != KRMU;  // culled rows' index: weight word
+  const SmemLayout L = smem_layout(p.lut_words, p.band_words, p.nslots, p.R, HP, ACC, kWTile,
+                                   !kIdxRow);
   uint32_t *lut = (uint32_t *)smem;
   for (int i = threadIdx.x; i < p.lut_words; i += blockDim.x) lut[i] = p.lut[i];
   float2 *band = (float2 *)(smem + align16(p.lut_words * 4));

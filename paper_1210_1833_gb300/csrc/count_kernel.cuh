@@ -29,9 +29,10 @@ namespace cute {
 
 constexpr int kTile = 64;          // neighbour objects per shared-memory tile
 // A tile buffer holds kTilePre rows before the tile (culled rows carried
-// from the tile before) and room after it to pad the last step.
-constexpr int kTilePre = 4;
-constexpr int kTileRows = kTilePre + kTile + 4;
+// from the tile before: fewer than a step, at most 3) and room after it to
+// pad the last step.
+constexpr int kTilePre = 3;
+constexpr int kTileRows = kTilePre + kTile + 3;
 constexpr unsigned kFull = 0xffffffffu;
 
 // FP32 sentinels for padded home slots (+far on every axis) and tile rows
@@ -137,13 +138,14 @@ struct SmemLayout {
   int tile_bytes;     // per warp (2 tiles)
   int wtile_bytes;    // per warp (2 weight tiles: R_MU weighted / adjoint)
   int cull_bytes;     // per warp: the home box, the culled rows' neighbour indices
+                      // (plain counts but (r, mu): in the rows' weight words)
   int warp_bytes;     // per warp total
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
 __host__ __device__ inline SmemLayout smem_layout(int lut_words, int band_words, int nslots, int R,
-                                                  int HP, int acc, bool wtile) {
+                                                  int HP, int acc, bool wtile, bool idx_array) {
   SmemLayout s;
   // block-wide: lookup tables, bands, and (adjoint) G per slot
   s.lut_bytes = align16(lut_words * 4) + align16(band_words * 8) + (acc == 2 ? align16(nslots * 8) : 0);
@@ -155,8 +157,11 @@ __host__ __device__ inline SmemLayout smem_layout(int lut_words, int band_words,
   s.queue_bytes = 16 + align16(s.queue_cap * 8);  // 16-byte header holds the count
   s.tile_bytes = 2 * kTileRows * 16;
   s.wtile_bytes = wtile ? 2 * kTileRows * 4 : 0;
-  s.cull_bytes = 32 + kTileRows * 4;
-  s.warp_bytes = s.hist_bytes + s.queue_bytes + s.tile_bytes + s.wtile_bytes + s.cull_bytes;
+  s.cull_bytes = align16(32 + (idx_array ? kTileRows * 4 : 0));
+  // every region, and so every warp's block, starts on a 16-byte boundary
+  // (cp.async and float4 rows)
+  s.warp_bytes = align16(s.hist_bytes + s.queue_bytes + s.tile_bytes + s.wtile_bytes +
+                         s.cull_bytes);
   return s;
 }
 

@@ -210,7 +210,7 @@ extern "C" cute_status cute_count_pairs_noalloc(cute_ctx *ctx, const cute_pair_d
   p.err = ctx->d_err;
 
   SmemLayout L = smem_layout(p.lut_words, p.band_words, P.nslots, P.R, hp, acc,
-                             kind == CUTE_R_MU && acc != 0);
+                             kind == CUTE_R_MU && acc != 0, kind == CUTE_R_MU || acc != 0);
   const int wmax = count_max_warps(kind == CUTE_MONO || kind == CUTE_THETA, hp, acc);
   int warps = ctx->warps_override ? std::min(ctx->warps_override, wmax) : wmax;
   while (warps > 1 && (size_t)L.lut_bytes + (size_t)warps * L.warp_bytes > ctx->smem_optin) warps--;
