@@ -7,11 +7,12 @@ bins on [0, 1] with the midpoint line of sight; DD, DR and RR, then the
 Landy-Szalay estimator.  Synthetic, seeded (paper_1210_1833_gb300.synthetic).
 
 One step = the whole hot path: catalog upload/conversion, cell-grid build
-for both catalogs, the DD, DR and RR counting kernels, and the estimator.
+for both catalogs, the DD, DR and RR counts (one batched persistent launch
+of the counting kernel), and the estimator.
 `value` is pairs binned per second (pairs that fall in a bin of DD, DR or
 RR) with the catalogs already in HBM; it does not depend on how many
 candidate pairs the neighbour search examines.  The roofline is taken on the
-candidate pairs the dominant kernel examines.  `e2e` is the same step
+counting launch, over the candidate pairs it evaluates.  `e2e` is the same step
 through the public API from pinned host memory with the xi read back.  L2 is
 flushed between timed steps.
 
@@ -254,33 +255,37 @@ def run_gpu(args, w, rank, world):
     d_pin = torch.from_numpy(w.data).pin_memory()
     r_pin = torch.from_numpy(w.randoms).pin_memory()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")  # 256 MB
+    # (rr_*: the counting launch the roofline is taken on, all of the step's
+    # counts in one launch)
     state = {"cand": 0, "kms": [], "rr_cand": 0, "rr_ms": [], "inrange": 0, "rechecked": 0, "fp64": 0,
              "slots": 0, "per": {}, "stencil": 0}
+
+    names = [n for n in ("DD", "DR", "RR") if not args.only or n in args.only.split(",")]
+    label = "+".join(names)
 
     def step(dsrc, rsrc, record):
         cd = ctx.upload(dsrc)
         cr = ctx.upload(rsrc)
         ctx.grid([cd, cr], reach, args.cpr)
-        res = {}
-        for name, a, b in (("DD", cd, None), ("DR", cd, cr), ("RR", cr, None)):
-            if args.only and name not in args.only.split(","):
-                res[name] = np.ones((len(w.edges0) - 1, len(w.edges1) - 1), np.uint64)
-                continue
-            c, _, _ = ctx.count("rmu", a, b, w.edges0, w.edges1, want_oor=False)
-            res[name] = c
-            if record:
-                st = ctx.stats()
-                state["cand"] += st["candidate_pairs"]
-                state["stencil"] += st["stencil_pairs"]
-                state["kms"].append(st["kernel_ms"])
-                state["per"].setdefault(name, []).append(st["kernel_ms"])
-                state["rechecked"] += st["rechecked_pairs"]
-                state["fp64"] += st["fp64_pairs"]
-                state["slots"] += st["pair_slots"]
-                state["inrange"] += int(c.sum())
-                if name == "RR":
-                    state["rr_cand"] = st["candidate_pairs"]
-                    state["rr_ms"].append(st["kernel_ms"])
+        sets = {"DD": (cd, None), "DR": (cd, cr), "RR": (cr, None)}
+        # the step's counts in one persistent launch (one work list, one
+        # round trip, one tail): the library's batched call
+        got = ctx.count_batched("rmu", [sets[n] for n in names], w.edges0, w.edges1)
+        res = {n: np.ones((len(w.edges0) - 1, len(w.edges1) - 1), np.uint64)
+               for n in ("DD", "DR", "RR")}
+        res.update(dict(zip(names, got)))
+        if record:
+            st = ctx.stats()
+            state["cand"] += st["candidate_pairs"]
+            state["stencil"] += st["stencil_pairs"]
+            state["kms"].append(st["kernel_ms"])
+            state["per"].setdefault(label, []).append(st["kernel_ms"])
+            state["rechecked"] += st["rechecked_pairs"]
+            state["fp64"] += st["fp64_pairs"]
+            state["slots"] += st["pair_slots"]
+            state["inrange"] += int(sum(int(c.sum()) for c in got))
+            state["rr_cand"] = st["candidate_pairs"]
+            state["rr_ms"].append(st["kernel_ms"])
         xi = cute.estimator("ls", res["DD"], res["DR"], res["RR"], nd, nr)
         cd.free()
         cr.free()
@@ -322,13 +327,25 @@ def run_gpu(args, w, rank, world):
             if best is None or dt < best[0]:
                 best = (dt, cpr)
         args.cpr = best[1]
-        cd, cr = ctx.upload(d_dev), ctx.upload(r_dev)
-        ctx.grid([cd, cr], reach, args.cpr)
-        for name, a, b in (("DD", cd, None), ("DR", cd, cr), ("RR", cr, None)):
-            tuning[name] = ctx.autotune("rmu", [(a, b)], w.edges0, w.edges1, tune_cells=False,
-                                        max_items=30000)
-        cd.free()
-        cr.free()
+        # then the launch's home objects per lane and neighbour slice, also
+        # by whole steps (a sample of work items misjudges the neighbour
+        # cull, which culls less around wider home chunks)
+        best = None
+        for hp in (2, 4):
+            for sl in (1024, 4096):
+                ctx.set_launch(home_per_lane=hp, slice=sl)
+                dts = []
+                for _ in range(2):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    step(d_dev, r_dev, False)
+                    torch.cuda.synchronize()
+                    dts.append(time.perf_counter() - t0)
+                if best is None or min(dts) < best[0]:
+                    best = (min(dts), hp, sl)
+        ctx.set_launch(home_per_lane=best[1], slice=best[2])
+        tuning[label] = {"home_per_lane": best[1], "slice": best[2],
+                         "warps_per_block": "library default", "by": "whole steps"}
         tuning["cells_per_reach"] = args.cpr
         step(d_dev, r_dev, False)
         torch.cuda.synchronize()
@@ -364,10 +381,10 @@ def run_gpu(args, w, rank, world):
         cpu_v, cpu_thr, cpu_desc = None, None, "skipped (--no-cpu)"
     else:
         cpu_v, cpu_thr, cpu_desc = cpu_oracle_rate(w, target_s=12.0)
-    # upload stats x2; grid x2 (assign, 3 scan passes, scatter); per count
-    # (x3) the work list (entry counts, 2 scan passes, record write) and the
-    # counting kernel
-    launches_per_step = 2 + 2 * 5 + 3 * 5
+    # upload stats x2; grid x2 (assign, 3 scan passes, scatter); the work
+    # list (entry counts, 2 scan passes, record write) and the one counting
+    # launch of DD, DR and RR
+    launches_per_step = 2 + 2 * 5 + 5
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -387,9 +404,12 @@ def run_gpu(args, w, rank, world):
                   "fp64_fraction": state["fp64"] / max(1, state["cand"]),
                   "slot_utilisation": state["cand"] / max(1, state["slots"]),
                   "count_kernel_ms_per_step": float(np.sum(state["kms"])) / args.steps},
-        "roofline": {"bound": "alu", "kernel": "k_count<R_MU> (RR)", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "k_count<R_MU> (%s, one launch)" % label,
+                     "achieved": achieved,
                      "peak": peak_tinst, "unit": "Tinst/s", "frac": achieved / peak_tinst,
-                     "traffic": traffic_record("k_count_rmu_RR_c2"), "i_pair": I_PAIR["rmu"],
+                     "traffic": traffic_record("k_count_rmu_c2_step" if label == "DD+DR+RR"
+                                               else "k_count_rmu_RR_c2"),
+                     "i_pair": I_PAIR["rmu"],
                      "counted": counted_record("k_count_rmu_RR_c2", rr_rate, peak_tinst),
                      "peak_note": "152 SMs x 128 FP32 lanes x %.0f MHz (%s max clock)" % (
                          smax, src),
@@ -403,6 +423,7 @@ def run_gpu(args, w, rank, world):
         "clocks": clocks,
     }
     if not args.no_extras and not args.only:
+        ctx.set_launch()  # the rows take their own launch shapes
         line["rows"] = run_extras(ctx, dev)
     print(json.dumps(line), flush=True)
     ctx.close()
