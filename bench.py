@@ -319,13 +319,15 @@ def run_gpu(args, w, rank, world):
         for cpr in (3, 4, 5):
             args.cpr = cpr
             step(d_dev, r_dev, False)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            step(d_dev, r_dev, False)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            if best is None or dt < best[0]:
-                best = (dt, cpr)
+            dts = []
+            for _ in range(2):  # the faster of two: one step is noisy at the 1 % level
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                step(d_dev, r_dev, False)
+                torch.cuda.synchronize()
+                dts.append(time.perf_counter() - t0)
+            if best is None or min(dts) < best[0]:
+                best = (min(dts), cpr)
         args.cpr = best[1]
         # then the launch's home objects per lane and neighbour slice, also
         # by whole steps (a sample of work items misjudges the neighbour

@@ -111,6 +111,29 @@ def test_c2_rmu_lightcone_full(c2_expected, cpr, tuned):
         _c2_counts(ctx, w, exp, cpr, tuned)
 
 
+@pytest.mark.parametrize("cpr", [3, 4, 5])
+def test_c2_rmu_lightcone_batched_full(c2_expected, cpr):
+    """The bench's step: DD, DR and RR of the full light cone in one batched
+    launch, at every launch shape its warm-up may choose by whole steps
+    (cells per reach 3, 4, 5; 2 or 4 home objects per lane; slices of 1024
+    or 4096 neighbours), each equal to the oracle's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w, exp = c2_expected
+    e0, e1 = w.edges0, w.edges1
+    with cute.Context(0) as ctx:
+        D, R = ctx.upload(w.data), ctx.upload(w.randoms)
+        ctx.grid([D, R], [e0[-1]] * 3, cpr)
+        for hp in (2, 4):
+            for sl in (1024, 4096):
+                ctx.set_launch(home_per_lane=hp, slice=sl)
+                got = ctx.count_batched("rmu", [(D, None), (D, R), (R, None)], e0, e1)
+                for name, c in zip(("DD", "DR", "RR"), got):
+                    _match(c, exp[name])
+        D.free()
+        R.free()
+
+
 def _c2_counts(ctx, w, exp, cpr, tuned):
     e0, e1 = w.edges0, w.edges1
     D, R = ctx.upload(w.data), ctx.upload(w.randoms)
