@@ -400,6 +400,7 @@ def run_gpu(args, w, rank, world):
                   "in_range_per_step": inrange_per_step,
                   "all_pairs_per_step": total_pairs(nd, nr),
                   "candidate_pairs_per_s": world * cand_per_step / (ms / 1e3),
+                  "stencil_pairs_per_s": world * state["stencil"] / args.steps / (ms / 1e3),
                   "all_pairs_per_s": world * total_pairs(nd, nr) / (ms / 1e3),
                   "count_kernel_ms": {k: float(np.mean(v)) for k, v in state["per"].items()},
                   "rechecked_fraction": state["rechecked"] / max(1, state["cand"]),
