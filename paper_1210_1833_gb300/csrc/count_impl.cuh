@@ -14,6 +14,7 @@
 #include "count_kernel.cuh"
 
 #include <algorithm>
+#include <type_traits>
 #include <atomic>
 
 namespace cute {
@@ -588,15 +589,25 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
       flagged = __any_sync(kFull, nmask != 0u);
     }
     // rare: pairs inside an edge's error band join the warp's re-test queue;
-    // the queue only grows here, so it is drained here when it holds 32
+    // the queue only grows here, so it is drained here when it holds 32.
+    // A flagged step usually holds one near pair in the whole warp, and the
+    // warp issues whatever any lane needs: so only the step positions k near
+    // in some lane are handled (the lanes' near masks OR-ed across the
+    // warp), each with its own compile-time k, so off[k] and sc[k] stay
+    // in registers.
     if (flagged) {
       // pairs with the padding rows past this item's rows are never queued
       // (a culled run: rows past the end of its real rows; the neighbour
       // index of a queued pair's row is looked up only then)
       const int lim = MASK == 0 ? (int)lds_u32(w.s_box + 28u) : w.gje;
+      unsigned lm = 0;  // this lane's near positions
 #pragma unroll
-      for (int k = 0; k < NP; k++) {
-        const bool nk = kLazy ? (sc[k] >= thr) : ((nmask >> k) & 1u) != 0u;
+      for (int k = 0; k < NP; k++)
+        if (kLazy ? (sc[k] >= thr) : ((nmask >> k) & 1u) != 0u) lm |= 1u << k;
+      unsigned wm = __reduce_or_sync(kFull, lm);  // the warp's
+      auto near_pair = [&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const bool nk = ((lm >> k) & 1u) != 0u;
         if (kLazy && nk) {
           // take back what the FP32 slot received: its count, and the weight
           // product (weighted) or the gradient term (adjoint), by the
@@ -638,6 +649,21 @@ __device__ __forceinline__ void tile_pairs(const KParams &p, uint32_t lut, uint3
                           : (int)lds_u32(kIdxRow ? tile + 16u * (uint32_t)(j + k / HP) + 12u
                                                  : w.s_cidx + 4u * gjk));
           else atomicCAS(p.err, 0, (int)CUTE_E_DEVICE);
+        }
+      };
+      static_assert(NP == 8, "eight step positions");
+      while (wm) {  // warp-uniform
+        const int k = __ffs(wm) - 1;
+        wm &= wm - 1u;
+        switch (k) {
+          case 0: near_pair(std::integral_constant<int, 0>{}); break;
+          case 1: near_pair(std::integral_constant<int, 1>{}); break;
+          case 2: near_pair(std::integral_constant<int, 2>{}); break;
+          case 3: near_pair(std::integral_constant<int, 3>{}); break;
+          case 4: near_pair(std::integral_constant<int, 4>{}); break;
+          case 5: near_pair(std::integral_constant<int, 5>{}); break;
+          case 6: near_pair(std::integral_constant<int, 6>{}); break;
+          default: near_pair(std::integral_constant<int, 7>{}); break;
         }
       }
       __syncwarp();
