@@ -10,6 +10,7 @@
 // depends on the host beyond the chunk and stencil lists.
 #include "cute_internal.h"
 #include "count_kernel.cuh"
+#include "work_pairs.h"
 
 #include <algorithm>
 
@@ -37,13 +38,7 @@ __device__ __forceinline__ int entry_items(const PairWork *__restrict__ pairs,
   int items = 0;
   for (int k = 0; k < ns; k++) {
     items += (s[k].j1 - s[k].j0 + slice - 1) / slice;
-    if (s[k].flags & kSegSelf) {
-      for (int i = c.x; i < c.y; i++) npair += (unsigned)max(0, s[k].j1 - max(s[k].j0, i + 1));
-    } else {
-      npair += (unsigned long long)(c.y - c.x) * (unsigned)(s[k].j1 - s[k].j0);
-      if (s[k].flags & kSegNoSelfPair)
-        npair -= (unsigned)max(0, min(c.y, s[k].j1) - max(c.x, s[k].j0));
-    }
+    npair += segment_pairs(c, s[k]);
   }
   return items;
 }

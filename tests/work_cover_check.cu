@@ -4,8 +4,9 @@
 // no smaller than reach / k on each axis, x cut 8 times finer, a periodic
 // axis at least 2k + 1 cells), the home chunks (chunks_build), the stencil
 // rows (stencil_build) and every entry's segments (entry_segments) are
-// expanded into the object pairs they hand to the kernel, and each pair's
-// multiplicity is checked: every pair within reach exactly once -- unordered
+// expanded into the object pairs they hand to the kernel -- their number
+// must equal the work builder's count of them (work_pairs.h: segment_pairs,
+// the stencil_pairs statistic) -- and each pair's multiplicity is checked: every pair within reach exactly once -- unordered
 // pairs for the half stencil of an auto count, ordered pairs i != j for the
 // full stencil (the adjoint), every (a, b) for a cross count -- and with the
 // periodic image the segment gives it (the kernel's separation
@@ -19,6 +20,7 @@
 // Prints "scenario pairs_enumerated pairs_in_reach duplicates_beyond_reach
 // violations"; exits 1 on any violation.
 #include "count_kernel.cuh"
+#include "work_pairs.h"
 
 #include <algorithm>
 #include <cmath>
@@ -162,12 +164,14 @@ static long run(const char *name, bool periodic, double L, const double lo[3], c
   pd.periodic = periodic;
   std::vector<unsigned char> mult((size_t)nA * nB, 0), hit((size_t)nA * nB, 0);
   long enumerated = 0, bad = 0, dup = 0;
+  unsigned long long presented = 0;  // the work builder's count of the same pairs
   for (const int4 &c : chunks) {
     if (c.y - c.x > home_chunk) bad++;
     for (const int4 &r : stencil) {
       Seg s[3];
       const int ns = entry_segments(pd, pd.csB, c, r, s);
       for (int k = 0; k < ns; k++) {
+        presented += segment_pairs(c, s[k]);
         const int code = (s[k].flags >> 8) & 63;
         double S[3];
         for (int a = 0; a < 3; a++) {
@@ -189,6 +193,10 @@ static long run(const char *name, bool periodic, double L, const double lo[3], c
           }
       }
     }
+  }
+  if (presented != (unsigned long long)enumerated) {
+    std::printf("  stencil pairs %llu, enumerated %ld\n", presented, enumerated);
+    bad++;
   }
   long inreach = 0;
   for (int i = 0; i < nA; i++)
